@@ -1,0 +1,493 @@
+"""Pins of the FP64 CPU oracle against facts that do not come from the oracle itself:
+published known-answer vectors, optics closed forms, invariants and brute force.
+
+A plausible slip anywhere in the oracle (a dropped term, a wrong sign or index, a transposed
+operand) should fail one of these.  No test here needs a GPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2107_11008_gb300 import scenes as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_table(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append(line.split())
+    return rows
+
+
+# ------------------------------------------------------------------------------------------
+# RNG and spectrum
+# ------------------------------------------------------------------------------------------
+
+def test_philox_known_answers():
+    """Philox4x32-10 reproduces the Random123 known-answer vectors (Salmon et al. 2011)."""
+    for row in _read_table("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in row]
+        ctr = np.array(v[0:4], np.uint32)
+        key = v[4] | (v[5] << 32)
+        out = O.philox(ctr, key)[0]
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_cie_fit_against_tabulated_cie1931():
+    """The multi-lobe CIE fit lands within a few percent of the published 1931 table."""
+    for row in _read_table("cie1931_2deg_samples.txt"):
+        lam, xb, yb, zb = map(float, row)
+        got = O.cie_xyz(lam)
+        np.testing.assert_allclose(got, [xb, yb, zb], atol=0.04)
+
+
+def test_srgb_matrix_maps_d65_white_to_equal_rgb():
+    """Linear sRGB of the D65 white point (x=0.3127, y=0.3290, Y=1) is (1,1,1) (IEC 61966-2-1)."""
+    x, y = 0.3127, 0.3290
+    xyz = np.array([x / y, 1.0, (1 - x - y) / y])
+    np.testing.assert_allclose(O.xyz_to_rgb(xyz), [1, 1, 1], atol=2e-3)
+    # primaries: sRGB red primary chromaticity (0.64, 0.33) maps to a pure red
+    xr, yr = 0.64, 0.33
+    r = O.xyz_to_rgb(np.array([xr / yr, 1.0, (1 - xr - yr) / yr]))
+    assert r[0] > 0 and abs(r[1]) < 2e-3 * r[0] and abs(r[2]) < 2e-3 * r[0]
+
+
+def test_spectral_weights_white_and_single_bin():
+    w, lam = O.spectral_weights(8)
+    np.testing.assert_allclose(w.mean(0), [1, 1, 1], rtol=1e-12)
+    np.testing.assert_allclose(lam, 400 + (np.arange(8) + 0.5) * 37.5)
+    # long wavelengths weigh toward red, short toward blue
+    assert w[-2, 0] > w[-2, 2] and w[0, 2] > w[0, 0]
+    w1, _ = O.spectral_weights(1)
+    np.testing.assert_array_equal(w1, [[1, 1, 1]])
+
+
+# ------------------------------------------------------------------------------------------
+# Fresnel and Snell (Hecht, Optics, Sec. 4.6)
+# ------------------------------------------------------------------------------------------
+
+def _fresnel_sine_law(ti, n):
+    """Fresnel's sine/tangent laws in angle form (an independent statement of the same physics)."""
+    tt = math.asin(math.sin(ti) / n)
+    if ti == 0:
+        r = ((n - 1) / (n + 1)) ** 2
+        return r, r
+    rs = (math.sin(ti - tt) / math.sin(ti + tt)) ** 2
+    rp = (math.tan(ti - tt) / math.tan(ti + tt)) ** 2
+    return rs, rp
+
+
+def test_fresnel_normal_incidence():
+    for n in (1.33, 1.5, 1.9):
+        assert O.fresnel(1.0, 1.0, n) == pytest.approx(((n - 1) / (n + 1)) ** 2, rel=1e-14)
+        assert O.fresnel(1.0, n, 1.0) == pytest.approx(((n - 1) / (n + 1)) ** 2, rel=1e-14)
+
+
+def test_fresnel_matches_sine_tangent_laws_and_brewster():
+    n = 1.5
+    for deg in (10, 30, 45, 60, 75, 85):
+        ti = math.radians(deg)
+        rs, rp = _fresnel_sine_law(ti, n)
+        assert O.fresnel(math.cos(ti), 1.0, n) == pytest.approx(0.5 * (rs + rp), rel=1e-12)
+    tb = math.atan(n)  # Brewster: Rp = 0, so R = Rs / 2
+    rs, rp = _fresnel_sine_law(tb, n)
+    assert rp < 1e-25
+    assert O.fresnel(math.cos(tb), 1.0, n) == pytest.approx(0.5 * rs, rel=1e-12)
+
+
+def test_total_internal_reflection_threshold():
+    n = 1.5
+    tc = math.asin(1 / n)
+    assert O.fresnel(math.cos(tc + 1e-6), n, 1.0) == 1.0
+    assert O.fresnel(math.cos(tc - 1e-3), n, 1.0) < 1.0
+    # grazing incidence from outside reflects everything
+    assert O.fresnel(1e-9, 1.0, n) == pytest.approx(1.0, abs=1e-7)
+
+
+def test_snell_angles_vector_form():
+    n = 1.5
+    normal = np.array([0.0, 1.0, 0.0])
+    for deg in (0, 15, 40, 70, 89):
+        ti = math.radians(deg)
+        d = np.array([math.sin(ti), -math.cos(ti), 0.0])
+        t = O.refract(d, normal, 1.0 / n)
+        assert t is not None
+        assert np.linalg.norm(t) == pytest.approx(1.0, abs=1e-14)
+        assert math.asin(min(1.0, abs(t[0]))) == pytest.approx(math.asin(math.sin(ti) / n), abs=1e-12)
+        assert t[1] < 0 and t[2] == 0
+    # leaving glass beyond the critical angle -> None (TIR)
+    ti = math.asin(1 / n) + 0.01
+    assert O.refract(np.array([math.sin(ti), -math.cos(ti), 0.0]), normal, n) is None
+
+
+# ------------------------------------------------------------------------------------------
+# Geometry: BVH vs brute force, watertight shared edges
+# ------------------------------------------------------------------------------------------
+
+def _soup_scene(n_tris, seed):
+    rng = np.random.default_rng(seed)
+    b = S.SceneBuilder()
+    m = b.material(S.Material(S.MAT_DIFFUSE))
+    c = rng.uniform(-1, 1, (n_tris, 1, 3))
+    p = c + rng.normal(0, 0.15, (n_tris, 3, 3))
+    mesh = S.Mesh(p.reshape(-1, 3), np.arange(3 * n_tris).reshape(-1, 3), None, None)
+    b.add(mesh, m)
+    return b.build(S.Camera((0, 0, 5), (0, 0, 0), (0, 1, 0), 40, 8, 8))
+
+
+@pytest.mark.parametrize("n_tris", [1, 7, 200])
+def test_oracle_bvh_matches_brute_force(n_tris):
+    sc = _soup_scene(n_tris, n_tris)
+    o = O.OracleScene(sc)
+    rng = np.random.default_rng(1)
+    org = rng.uniform(-3, 3, (20000, 3))
+    tgt = rng.uniform(-1, 1, (20000, 3))
+    # half of the rays aim at random points inside random triangles
+    P32 = sc.positions.astype(np.float64)[sc.indices]
+    k = rng.integers(0, n_tris, 10000)
+    bc = rng.dirichlet([1, 1, 1], 10000)
+    tgt[:10000] = np.einsum("ij,ijk->ik", bc, P32[k])
+    d = tgt - org
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    t0, i0, _, _ = o.intersect(org, d, brute=True)
+    t1, i1, _, _ = o.intersect(org, d, brute=False)
+    np.testing.assert_array_equal(i0, i1)
+    np.testing.assert_array_equal(t0, t1)
+    assert (i0 >= 0).mean() > 0.05
+    # every reported hit is the closest: no triangle hit strictly earlier (checked one by one)
+    P = sc.positions.astype(np.float64)[sc.indices]
+    for k in np.flatnonzero(i0 >= 0)[:200]:
+        v0, v1, v2 = P[:, 0], P[:, 1], P[:, 2]
+        e1, e2 = v1 - v0, v2 - v0
+        pv = np.cross(d[k], e2)
+        det = np.einsum("ij,ij->i", e1, pv)
+        ok = det != 0
+        tv = org[k] - v0
+        u = np.einsum("ij,ij->i", tv, pv) / np.where(ok, det, 1)
+        qv = np.cross(tv, e1)
+        v = (qv @ d[k]) / np.where(ok, det, 1)
+        t = np.einsum("ij,ij->i", e2, qv) / np.where(ok, det, 1)
+        inside = ok & (u >= 0) & (v >= 0) & (u + v <= 1) & (t > 0)
+        assert t[inside].min() == pytest.approx(t0[k], rel=1e-12)
+
+
+def test_closed_mesh_shared_edges_and_vertices_never_leak():
+    """Rays aimed exactly at shared edges and vertices of a closed icosphere always hit it."""
+    b = S.SceneBuilder()
+    b.add(S.icosphere(3), b.material(S.Material(S.MAT_DIELECTRIC)))
+    sc = b.build(S.Camera((0, 0, 5), (0, 0, 0), (0, 1, 0), 40, 8, 8))
+    o = O.OracleScene(sc)
+    P = sc.positions.astype(np.float64)
+    idx = sc.indices
+    targets = np.concatenate([P, 0.5 * (P[idx[:, 0]] + P[idx[:, 1]]), 0.5 * (P[idx[:, 1]] + P[idx[:, 2]])])
+    rng = np.random.default_rng(3)
+    org = targets * 3.0 + rng.normal(0, 0.3, targets.shape)
+    d = targets - org
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    _, tri, _, amb = o.intersect(org, d)
+    assert (tri >= 0).all()
+    # from inside as well
+    _, tri2, _, _ = o.intersect(np.zeros_like(targets) + 1e-3, targets / np.linalg.norm(targets, axis=1)[:, None])
+    assert (tri2 >= 0).all()
+    # the shared points are flagged as ambiguous (an edge within tolerance)
+    assert (amb[: len(P)] & 1).all()
+
+
+# ------------------------------------------------------------------------------------------
+# Transport closed forms
+# ------------------------------------------------------------------------------------------
+
+def _plane_point_light(width=32, height=32, albedo=0.5, I=20.0, lp=(0.7, 3.0, 0.4), env=(0, 0, 0)):
+    b = S.SceneBuilder()
+    m = b.material(S.Material(S.MAT_DIFFUSE, albedo=(albedo,) * 3))
+    b.add(S.quad((-10, 0, -10), (0, 0, 20), (20, 0, 0)), m)
+    b.lights.append(S.Light(S.LIGHT_POINT, lp, power=(I,) * 3))
+    cam = S.Camera((0.0, 2.0, 4.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 40.0, width, height)
+    return b.build(cam, env=env)
+
+
+def test_point_light_over_plane_closed_form():
+    """L = (rho/pi) I cos(theta) / r^2 at every camera path's first hit (no occluders)."""
+    sc = _plane_point_light()
+    o = O.OracleScene(sc)
+    _, rec = o.trace_camera(spp=4, max_depth=3)
+    p = rec["p0"]
+    hit = rec["first_tri"] >= 0
+    assert hit.mean() > 0.5
+    lp = np.asarray(O.f32([0.7, 3.0, 0.4]))
+    w = lp - p[hit]
+    r = np.linalg.norm(w, axis=1)
+    expect = (0.5 / math.pi) * 20.0 * (w[:, 1] / r) / r ** 2
+    np.testing.assert_allclose(rec["L"][hit][:, 0], expect, rtol=1e-9)
+    # the plane is y = 0 and the hit points are on it
+    np.testing.assert_allclose(p[hit][:, 1], 0.0, atol=1e-12)
+    # misses get the (black) environment
+    assert (rec["L"][~hit] == 0).all()
+
+
+def test_white_furnace_diffuse_convex_object():
+    """env = 1, no lights: a convex albedo-rho object returns exactly rho, the background 1."""
+    for rho in (1.0, 0.5):
+        b = S.SceneBuilder()
+        b.add(S.icosphere(2), b.material(S.Material(S.MAT_DIFFUSE, albedo=(rho,) * 3)))
+        sc = b.build(S.Camera((0, 0, 3.5), (0, 0, 0), (0, 1, 0), 40, 24, 24), env=(1, 1, 1))
+        o = O.OracleScene(sc)
+        _, rec = o.trace_camera(spp=8, max_depth=4)
+        hit = rec["first_tri"] >= 0
+        assert 0.2 < hit.mean() < 0.9
+        np.testing.assert_allclose(rec["L"][hit], rho, rtol=0, atol=1e-7 if rho == 0.5 else 0)
+        np.testing.assert_array_equal(rec["L"][~hit], 1.0)
+
+
+def test_white_furnace_glass_sphere_conserves_energy():
+    """env = 1, glass sphere only: every path returns 1 unless it is still inside at max depth."""
+    b = S.SceneBuilder()
+    b.add(S.icosphere(3), b.material(S.Material(S.MAT_DIELECTRIC, cauchy_a=1.5)))
+    sc = b.build(S.Camera((0, 0, 3.5), (0, 0, 0), (0, 1, 0), 40, 24, 24), env=(1, 1, 1))
+    o = O.OracleScene(sc)
+    _, rec = o.trace_camera(spp=16, max_depth=64)
+    L = rec["L"][:, 0]
+    assert set(np.unique(L)) <= {0.0, 1.0}
+    assert L.mean() >= 1 - 1e-3
+    assert (rec["n_specular"] >= 2).mean() > 0.3
+
+
+def _slab_scene(theta_deg, thickness=0.5, n=1.5, cauchy_b=0.0, disk_radius=0.0):
+    b = S.SceneBuilder()
+    b.add(S.box((-6, 0, -6), (6, thickness, 6)), b.material(S.Material(S.MAT_DIELECTRIC, cauchy_a=n, cauchy_b=cauchy_b)))
+    b.add(S.quad((-20, -1, -20), (0, 0, 40), (40, 0, 0)), b.material(S.Material(S.MAT_DIFFUSE, albedo=(0.5,) * 3)))
+    th = math.radians(theta_deg)
+    d = (math.sin(th), -math.cos(th), 0.0)
+    c = (-2.0 * math.tan(th), thickness + 2.0, 0.0)
+    b.lights.append(S.Light(S.LIGHT_DISK, c, d, power=(1.0,) * 3, radius=disk_radius))
+    return b.build(S.Camera((0, 6, 8), (0, 0, 0), (0, 1, 0), 40, 16, 16)), c, d
+
+
+@pytest.mark.parametrize("theta_deg", [0.0, 20.0, 45.0, 70.0])
+def test_slab_lateral_shift(theta_deg):
+    """A forced-transmission path through a slab exits parallel, displaced by t (tan th - tan th_t)."""
+    t, n = 0.5, 1.5
+    sc, c, d = _slab_scene(theta_deg, t, n)
+    o = O.OracleScene(sc)
+    _, rec = o.trace_lights(64, max_depth=6, flags=O.FLAG_FORCE_TRANSMIT)
+    c, d = O.f32(c), O.f32(d)
+    th = math.atan2(d[0], -d[1])
+    tt = math.asin(math.sin(th) / n)
+    x_top = c[0] + (c[1] - t) * math.tan(th)
+    # through the slab at the refracted angle, exit at y = 0, then 1 m down to the receiver at y = -1;
+    # each new ray starts eps = 1e-4 past the surface along its normal (the self-intersection rule)
+    eps = 1e-4
+    expect = x_top + (t - eps) * math.tan(tt) + (1.0 - eps) * math.tan(th)
+    assert (rec["n_specular"] == 2).all()
+    np.testing.assert_allclose(rec["x"][:, 0], expect, atol=1e-9)
+    np.testing.assert_allclose(rec["x"][:, 1], -1.0, atol=1e-12)
+    # lateral shift of the exit ray measured perpendicular to it (the slab formula, Hecht Sec. 5.2),
+    # up to the offsets' O(eps) displacement
+    shift = (x_top + 1.0 * math.tan(th) + t * math.tan(th) - rec["x"][0, 0]) * math.cos(th)
+    assert shift == pytest.approx(t * math.sin(th) * (1 - math.cos(th) / math.sqrt(n * n - math.sin(th) ** 2)),
+                                  abs=3 * eps)
+
+
+def test_slab_dispersion_per_bin_cauchy():
+    """With 8 bins the transmitted spot of bin b follows Snell with Cauchy n(lambda_b)."""
+    A, B, t = 1.5, 0.004, 0.5
+    sc, c, d = _slab_scene(50.0, t, A, cauchy_b=B)
+    o = O.OracleScene(sc)
+    _, rec = o.trace_lights(4000, max_depth=6, nbins=8, flags=O.FLAG_FORCE_TRANSMIT)
+    c, d = O.f32(c), O.f32(d)
+    A32, B32 = (float(np.float32(A)), float(np.float32(B)))
+    th = math.atan2(d[0], -d[1])
+    x_top = c[0] + (c[1] - t) * math.tan(th)
+    _, lam = O.spectral_weights(8)
+    seen = set()
+    for b in range(8):
+        sel = rec["bin"] == b
+        if not sel.any():
+            continue
+        seen.add(b)
+        n = A32 + B32 / (lam[b] * 1e-3) ** 2
+        tt = math.asin(math.sin(th) / n)
+        expect = x_top + (t - 1e-4) * math.tan(tt) + (1.0 - 1e-4) * math.tan(th)
+        np.testing.assert_allclose(rec["x"][sel, 0], expect, atol=1e-9)
+    assert len(seen) == 8
+    # the published Cauchy values for this glass
+    assert A + B / 0.41875 ** 2 == pytest.approx(1.5228, abs=1e-4)
+    assert A + B / 0.68125 ** 2 == pytest.approx(1.5086, abs=1e-4)
+
+
+def test_slab_fresnel_transmitted_fraction():
+    """Normal incidence on a slab: the fraction reaching the receiver is (1-R)/(1+R), R=((n-1)/(n+1))^2,
+    summing all internal bounces; checked within 4 binomial sigma."""
+    sc, _, _ = _slab_scene(0.0, 0.5, 1.5)
+    o = O.OracleScene(sc)
+    N = 200000
+    _, rec = o.trace_lights(N, max_depth=64)
+    reached = ~np.isnan(rec["x"][:, 0])
+    R = 0.04
+    p = (1 - R) / (1 + R)
+    sig = math.sqrt(p * (1 - p) / N)
+    assert abs(reached.mean() - p) < 4 * sig
+    # first-event transmit probability is 1 - R
+    assert abs((rec["n_specular"][reached] == 2).mean() * reached.mean() - (1 - R) ** 2) < 4 * sig
+
+
+def test_ball_lens_focus():
+    """A thin collimated beam through a glass ball (n=1.5, D=2) focuses f = nD/(4(n-1)) = 1.5 from the
+    centre; the smallest RMS spot on a receiver swept along the axis lies within 3 % of f."""
+    zs = np.arange(1.30, 1.71, 0.02)
+    rms = []
+    for z in zs:
+        b = S.SceneBuilder()
+        b.add(S.icosphere(5), b.material(S.Material(S.MAT_DIELECTRIC, cauchy_a=1.5)))
+        b.add(S.quad((-3, -z, -3), (0, 0, 6), (6, 0, 0)), b.material(S.Material(S.MAT_DIFFUSE)))
+        b.lights.append(S.Light(S.LIGHT_DISK, (0.0, 3.0, 0.0), (0.0, -1.0, 0.0), power=(1.0,) * 3, radius=0.1))
+        sc = b.build(S.Camera((0, 0, 6), (0, 0, 0), (0, 1, 0), 40, 8, 8))
+        _, rec = O.OracleScene(sc).trace_lights(6000, max_depth=8, flags=O.FLAG_FORCE_TRANSMIT)
+        sel = rec["n_specular"] == 2
+        x = rec["x"][sel]
+        rms.append(math.sqrt(np.mean(x[:, 0] ** 2 + x[:, 2] ** 2)))
+    zbest = zs[int(np.argmin(rms))]
+    assert abs(zbest - 1.5) <= 0.03 * 1.5
+    assert rms[0] > 2 * min(rms) and rms[-1] > 2 * min(rms)
+
+
+def test_splat_normalisation_matches_direct_lighting():
+    """Light tracing with splats of directly lit points reproduces the camera estimator of direct light
+    (pinhole importance 1/(A_pix cos^3)), and its error falls like 1/N."""
+    sc = _plane_point_light(width=16, height=16)
+    o = O.OracleScene(sc)
+    acc, _ = o.trace_camera(spp=256, max_depth=1, records=False)
+    ref = acc / 256
+    errs = []
+    for n in (1 << 18, 1 << 20):
+        accl, _ = o.trace_lights(n, max_depth=2, flags=O.FLAG_SPLAT_DIRECT, records=False, seed=7)
+        img = accl / n
+        errs.append(np.mean((img - ref) ** 2))
+        assert img.sum() == pytest.approx(ref.sum(), rel=0.02)
+    assert 2.5 < errs[0] / errs[1] < 6.0
+
+
+def test_caustic_decomposition_matches_path_traced_caustic():
+    """Camera paths that reach the area light through glass after one diffuse bounce (E D S+ L) estimate
+    the same light as the splatted light paths (L S+ D E): the two totals agree statistically."""
+    b = S.SceneBuilder()
+    b.add(S.icosphere(3), b.material(S.Material(S.MAT_DIELECTRIC, cauchy_a=1.5)))
+    b.add(S.quad((-10, -1, -10), (0, 0, 20), (20, 0, 0)), b.material(S.Material(S.MAT_DIFFUSE, albedo=(0.8,) * 3)))
+    b.add_rect_light((-1.75, 4.0, -3.5), (1.5, 0, 0), (0, 0, 1.5), (5.0, 5.0, 5.0))
+    sc = b.build(S.Camera((0.0, 2.0, 5.0), (0.0, -0.6, 0.5), (0, 1, 0), 45, 24, 24))
+    o = O.OracleScene(sc)
+    spp = 2048
+    a_std, _ = o.trace_camera(spp=spp, max_depth=4, records=False, seed=3)
+    a_ds, _ = o.trace_camera(spp=spp, max_depth=4, records=False, seed=3, flags=O.FLAG_EMITTER_AFTER_DS)
+    pt = (a_ds - a_std) / spp
+    nl = 1 << 21
+    al, _ = o.trace_lights(nl, max_depth=4, records=False, seed=5)
+    lt = al / nl
+    assert lt.sum() > 0.05 * a_std.sum() / spp
+    assert pt.sum() == pytest.approx(lt.sum(), rel=0.08)
+
+
+def test_caustic_softness_grows_with_light_size():
+    """Sec. III, Fig. 4: a larger light source gives softer caustics.  The median radius of the
+    focused spot (light through a glass ball onto a floor near its focus) grows with the light size."""
+    radii = []
+    for size in (0.2, 0.8, 2.0):
+        b = S.SceneBuilder()
+        b.add(S.icosphere(4), b.material(S.Material(S.MAT_DIELECTRIC, cauchy_a=1.5)))
+        b.add(S.quad((-6, -1.5, -6), (0, 0, 12), (12, 0, 0)), b.material(S.Material(S.MAT_DIFFUSE)))
+        b.add_rect_light((-size / 2, 6.0, -size / 2), (size, 0, 0), (0, 0, size), (1.0,) * 3)
+        sc = b.build(S.Camera((0, 1, 6), (0, -1, 0), (0, 1, 0), 40, 8, 8))
+        _, rec = O.OracleScene(sc).trace_lights(200000, max_depth=8)
+        x = rec["x"][(rec["n_specular"] == 2)]
+        x = x[~np.isnan(x[:, 0])]
+        assert len(x) > 2000
+        radii.append(float(np.median(np.hypot(x[:, 0], x[:, 2]))))
+    assert radii[0] * 1.2 < radii[1] and radii[1] * 1.2 < radii[2]
+
+
+# ------------------------------------------------------------------------------------------
+# Estimator bookkeeping
+# ------------------------------------------------------------------------------------------
+
+def test_sample_ranges_compose():
+    """Chunked accumulation over sample offsets equals one pass (checkpoint/resume through counters)."""
+    sc = S.ball_on_plane(16, 16)
+    o = O.OracleScene(sc)
+    full, r_full = o.trace_camera(spp=8, max_depth=8)
+    a, r_a = o.trace_camera(spp=3, max_depth=8)
+    b, r_b = o.trace_camera(spp=5, max_depth=8, sample_offset=3)
+    np.testing.assert_allclose(a + b, full, rtol=1e-12, atol=1e-15)
+    Lf = r_full["L"].reshape(16 * 16, 8, 3)
+    np.testing.assert_array_equal(Lf[:, :3], r_a["L"].reshape(256, 3, 3))
+    np.testing.assert_array_equal(Lf[:, 3:], r_b["L"].reshape(256, 5, 3))
+
+
+def test_window_matches_full_frame():
+    sc = S.ball_on_plane(16, 16)
+    o = O.OracleScene(sc)
+    _, rf = o.trace_camera(spp=2, max_depth=8)
+    _, rw = o.trace_camera(spp=2, max_depth=8, window=(4, 12, 5, 9))
+    full = rf["L"].reshape(16, 16, 2, 3)[5:9, 4:12]
+    np.testing.assert_array_equal(full.reshape(-1, 3), rw["L"])
+
+
+def test_ground_truth_buffers_on_ball_and_plane():
+    """Depth is the Euclidean distance to the analytic plane / sphere, normals are the analytic ones,
+    the transparent mask is the analytic sphere silhouette (away from its edge), depth_norm uses 10 m."""
+    sc = S.ball_on_plane(48, 48)
+    o = O.OracleScene(sc)
+    g = o.resolve(None, None, 1, 0)
+    cam = sc.camera
+    eye = np.asarray(O.f32(cam.eye))
+    f = O.f32(cam.look) - eye
+    f /= np.linalg.norm(f)
+    r = np.cross(f, O.f32(cam.up))
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    th = math.tan(math.radians(float(np.float32(cam.vfov_deg))) / 2)
+    ys, xs = np.mgrid[0:48, 0:48]
+    sx, sy = (xs + 0.5) / 48, (ys + 0.5) / 48
+    d = (2 * sx - 1)[..., None] * th * r + (1 - 2 * sy)[..., None] * th * u + f
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    # analytic sphere |eye + t d| = 1
+    bq = (d @ eye)
+    disc = bq ** 2 - (eye @ eye - 1)
+    t_sph = np.where(disc > 0, -bq - np.sqrt(np.maximum(disc, 0)), np.inf)
+    t_pl = np.where(d[..., 1] < 0, (-1 - eye[1]) / np.where(d[..., 1] < 0, d[..., 1], -1), np.inf)
+    inside = disc > 0.02  # well inside the silhouette
+    p_pl = eye + np.where(np.isfinite(t_pl), t_pl, 0)[..., None] * d
+    on_plane = np.isfinite(t_pl) & (np.abs(p_pl[..., 0]) < 9.9) & (np.abs(p_pl[..., 2]) < 9.9)
+    outside = (disc < -0.02) & on_plane
+    assert inside.any() and outside.any()
+    np.testing.assert_array_equal(g["mask"][inside], 1)
+    np.testing.assert_array_equal(g["mask"][outside], 0)
+    np.testing.assert_array_equal(g["instance"][inside], 0)
+    np.testing.assert_array_equal(g["instance"][outside], 1)
+    np.testing.assert_allclose(g["depth"][outside], t_pl[outside], rtol=1e-9)
+    # facets lie inside the sphere by at most the sagitta; grazing rays see it magnified, so check
+    # depth where the ray meets the sphere steeply
+    steep = disc > 0.15
+    np.testing.assert_allclose(g["depth"][steep], t_sph[steep], atol=1e-2)
+    np.testing.assert_allclose(g["depth_norm"][outside], np.minimum(t_pl[outside] / 10, 1), rtol=1e-9)
+    np.testing.assert_allclose(g["n_world"][outside], np.broadcast_to([0, 1, 0], g["n_world"][outside].shape),
+                               atol=1e-12)
+    p = eye + t_sph[..., None] * d
+    np.testing.assert_allclose(g["n_world"][inside], p[inside], atol=3e-2)
+    # camera-space normals are a rotation of world-space ones and face the camera (+z toward the eye)
+    np.testing.assert_allclose(np.linalg.norm(g["n_cam"][inside], axis=-1), 1.0, atol=1e-12)
+    assert (g["n_cam"][inside][:, 2] > 0).all()
+    # rays past the plane's far edge miss: no ids, infinite depth, depth_norm 1
+    miss = (disc < -0.02) & ~np.isfinite(t_pl)
+    assert miss.any()
+    np.testing.assert_array_equal(g["instance"][miss], -1)
+    np.testing.assert_array_equal(g["tri"][miss], -1)
+    assert np.isinf(g["depth"][miss]).all() and (g["depth_norm"][miss] == 1).all()
+    # albedo of glass is 1, of the plane its albedo
+    np.testing.assert_allclose(g["albedo"][inside], 1.0)
+    np.testing.assert_allclose(g["albedo"][outside], 0.5)
