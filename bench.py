@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the spectral glass path/light tracer on one GB300 per rank.
+
+Workload (one "step" = one frame of the whole hot path): the 512x512 glass scene -- four
+procedural transparent meshes of ~20k triangles (sphere, hollow cylinder glass, torus,
+superellipsoid) with random pose from seed 0 over a checkered floor and back wall, a 1x1 m
+rect light, Cauchy glass A=1.5 B=0.004 um^2 over 8 wavelength bins, max depth 12.  Per step:
+LBVH build from device-resident triangles, 256 camera samples per pixel (67.1M camera paths),
+4M light paths splatted as caustics, and the resolve pass with every ground-truth buffer.
+
+Metric: Mpaths/s (camera + light paths per second, all ranks) with frames/s beside it.
+Multi-GPU: each rank renders its own frame of the same scene with a disjoint sample range
+(no data-path collective; weak scaling).  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpaths/s and frames/s at 512^2 glass scene"
+UNIT = "Mpaths/s"
+WORKLOAD = ("glass_scene_512: 4 glass meshes x ~20k tris (sphere, hollow cylinder, torus, superellipsoid; seed 0) "
+            "over checkered floor+wall, 1x1 m rect light, Cauchy A=1.5 B=0.004, 8 bins, depth 12, "
+            "256 spp + 4M light paths, LBVH build + resolve per frame")
+# FP32 work per traversal step: a node visit tests two child boxes, each slab
+# test being 3 axes x 2 planes x (sub + mul); a watertight triangle test is ~43 flops.
+FLOPS_PER_NODE = 24
+FLOPS_PER_TRI = 43
+BYTES_PER_NODE = 64
+BYTES_PER_TRI = 48
+# our kernels per step: LBVH build (bounds init, gather, morton, 4 x (hist, scan, scatter),
+# reorder, karras, refit, depth) + camera + lights + resolve
+LAUNCHES_PER_STEP = 18 + 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--spp", type=int, default=256)
+    ap.add_argument("--light-paths", type=int, default=1 << 22)
+    ap.add_argument("--res", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.lines = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:  # noqa: BLE001
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:  # noqa: BLE001
+        return {}
+
+
+def cpu_baseline(scene, spp_full, nl_full, seconds, depth=12, nbins=8):
+    """The FP64 oracle, as it stands, on a bounded sample of the same frame (rows of pixels at 4 spp
+    plus light paths), on this host's cores."""
+    import oracle as O
+
+    cores = len(os.sched_getaffinity(0))
+    orc = O.OracleScene(scene)
+    W = scene.camera.width
+    # calibrate on a tiny sample, then size the sample to about `seconds`
+    t0 = time.perf_counter()
+    orc.trace_camera(1, depth, nbins=nbins, window=(0, W, W // 2, W // 2 + 2), records=False, n_threads=cores)
+    t_small = max(time.perf_counter() - t0, 1e-3)
+    per_path = t_small / (2 * W)
+    spp = 4
+    rows = max(1, min(scene.camera.height, int(0.85 * seconds / (per_path * W * spp))))
+    y0 = max(0, W // 2 - rows // 2)
+    n_light = max(4096, int(0.15 * seconds / max(per_path, 1e-9)))
+    t0 = time.perf_counter()
+    orc.trace_camera(spp, depth, nbins=nbins, window=(0, W, y0, y0 + rows), records=False, n_threads=cores)
+    t_cam = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    orc.trace_lights(n_light, depth, nbins=nbins, records=False, n_threads=cores)
+    t_light = time.perf_counter() - t0
+    paths = rows * W * spp + n_light
+    return {"value": paths / (t_cam + t_light) / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{rows} rows x {W} px x {spp} spp camera paths + {n_light} light paths of the same frame "
+                      f"({t_cam + t_light:.1f} s on {cores} cores); full frame is {spp_full} spp + {nl_full} light paths",
+            "seconds": t_cam + t_light}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2107_11008_gb300 import scenes as S
+
+    sc = S.glass_scene(0, width=args.res, height=args.res)
+    # each step: a bounded sample of the frame; sized so that warmup + steps stay within minutes
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals, secs = [], []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(sc, args.spp, args.light_paths, per_step)
+        if i >= args.warmup:
+            vals.append(r["value"])
+            secs.append(r["seconds"])
+            cb = r
+    v = statistics.mean(vals)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD + " (oracle on a bounded sample of the frame per step)",
+                       "resolution": args.res},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_2107_11008_gb300 import renderer as R
+    from paper_2107_11008_gb300 import scenes as S
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    res, spp, nl, depth, nbins = args.res, args.spp, args.light_paths, 12, 8
+    scene = S.glass_scene(0, width=res, height=res)
+    host_arrays = R.SceneArrays(scene, "cpu")
+    dev_arrays = R.SceneArrays(scene, dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = R.Context(local, stream)
+    frame = R.Frame(res, res, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    sample_offset = rank * spp  # disjoint sample ranges per rank
+
+    def step(arrays, ev=None):
+        if ev:
+            ev[0].record(stream)
+        gs = R.GpuScene(ctx, arrays)
+        if ev:
+            ev[1].record(stream)
+        frame.zero_accumulators()
+        R.trace_camera(ctx, gs, frame, spp, depth, nbins, seed=1, sample_offset=sample_offset)
+        if ev:
+            ev[2].record(stream)
+        R.trace_lights(ctx, gs, frame, nl, depth, nbins, seed=2, path_offset=rank * nl)
+        if ev:
+            ev[3].record(stream)
+        R.resolve(ctx, gs, frame, spp, nl)
+        if ev:
+            ev[4].record(stream)
+        gs.free()
+
+    for _ in range(args.warmup):
+        step(dev_arrays)
+    ctx.sync_status()
+
+    # traversal work per launch (untimed pass with counters on)
+    counters = torch.zeros(3, dtype=torch.int64, device=dev)
+    gs = R.GpuScene(ctx, dev_arrays)
+    R.N.sc_set_counters(ctx.handle, counters.data_ptr())
+    frame.zero_accumulators()
+    R.trace_camera(ctx, gs, frame, spp, depth, nbins, seed=1, sample_offset=sample_offset)
+    torch.cuda.synchronize(dev)
+    cam_counts = counters.cpu().tolist()
+    counters.zero_()
+    R.trace_lights(ctx, gs, frame, nl, depth, nbins, seed=2)
+    torch.cuda.synchronize(dev)
+    light_counts = counters.cpu().tolist()
+    R.N.sc_set_counters(ctx.handle, None)
+    gs.free()
+
+    # timed region: K steps, L2 flushed between steps, CUDA events on the launching stream
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    for k in range(args.steps):
+        flush.zero_()
+        step(dev_arrays, evs[k])
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ctx.sync_status()
+    if world > 1:
+        dist.barrier()
+    step_ms = [e[0].elapsed_time(e[4]) for e in evs]
+    build_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    cam_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    light_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    resolve_ms = [e[3].elapsed_time(e[4]) for e in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    paths_per_step = res * res * spp + nl
+    value = world * paths_per_step / (ms_per_step * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: H2D of the scene, D2H of the frame outputs
+    e2e_steps = min(3, args.steps)
+    outs = ("rgb", "depth", "normal_world", "normal_camera", "instance_id", "mask", "caustic_mask", "albedo")
+    pinned = {k: torch.empty(frame[k].shape, dtype=frame[k].dtype, pin_memory=True) for k in outs}
+    d2h = sum(p.numel() * p.element_size() for p in pinned.values())
+    h2d = host_arrays.nbytes()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step(host_arrays)
+        for k in outs:
+            pinned[k].copy_(frame[k], non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * paths_per_step / e2e_s / 1e6
+
+    pk = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
+    cam_s = statistics.mean(cam_ms) * 1e-3
+    cam_flops = cam_counts[1] * FLOPS_PER_NODE + cam_counts[2] * FLOPS_PER_TRI
+    cam_bytes = cam_counts[1] * BYTES_PER_NODE + cam_counts[2] * BYTES_PER_TRI
+    achieved = cam_flops / cam_s / 1e12
+    if rank == 0:
+        cb = None
+        if not args.no_cpu_baseline and world == 1:
+            try:
+                cb = cpu_baseline(scene, spp, nl, args.cpu_seconds)
+                cb.pop("seconds", None)
+            except Exception as e:  # noqa: BLE001
+                cb = {"value": None, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                      "sample": f"failed: {e}"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "resolution": res, "spp": spp, "light_paths": nl, "max_depth": depth,
+                       "wavelength_bins": nbins, "triangles": scene.n_tris, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MB write)"},
+            "frames_per_s": world * 1e3 / ms_per_step,
+            "camera_mpaths_s": world * res * res * spp / (statistics.mean(cam_ms) * 1e-3) / 1e6,
+            "light_mpaths_s": world * nl / (statistics.mean(light_ms) * 1e-3) / 1e6,
+            "phase_ms": {"lbvh_build": statistics.mean(build_ms), "trace_camera": statistics.mean(cam_ms),
+                         "trace_lights": statistics.mean(light_ms), "resolve": statistics.mean(resolve_ms)},
+            "traversal": {"camera": {"queries": cam_counts[0], "nodes": cam_counts[1], "tris": cam_counts[2]},
+                          "lights": {"queries": light_counts[0], "nodes": light_counts[1], "tris": light_counts[2]},
+                          "camera_grays_s": cam_counts[0] / cam_s / 1e9,
+                          "camera_l2_side_gbs": cam_bytes / cam_s / 1e9},
+            "roofline": {"kernel": "k_trace_camera", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                         "peak_source": f"FP32: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (MEASURED_PEAKS sm_max)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cb,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,251 @@
+/*
+ * supercaustics.h -- C ABI of the GB300 (sm_103a) spectral glass path/light tracer.
+ *
+ * The library renders the kind of image SuperCaustics (arXiv 2107.11008) generates:
+ * transparent objects with refraction, reflection, dispersion and caustics (Abstract;
+ * Sec. III), together with pixel-aligned ground truth (Sec. III-D: depth normalised by a
+ * 10 m range, world/camera-space normals, object masks, caustic mask).  The paper's
+ * renderer is an engine with hardware ray tracing; here every step is a hand-written CUDA
+ * kernel: LBVH build over Morton codes, watertight BVH traversal, a persistent camera path
+ * tracer, a light tracer that splats caustics, and the resolve pass.
+ *
+ * Conventions for every entry point:
+ *   - Returns SC_OK (0) or a negative SC_ERR_* code; sc_last_error() gives a message.
+ *     No C++ exception crosses the ABI.
+ *   - Work is enqueued asynchronously on the context's stream.  Errors detected by a kernel
+ *     (traversal stack overflow, watchdog) are latched in a device status word and
+ *     reported by sc_sync_status(), which synchronises the stream.
+ *   - "device" pointers are CUDA global-memory addresses on the context's device; "host"
+ *     pointers are ordinary CPU memory.  The caller owns every buffer it passes in; the
+ *     library owns scenes (BVH, triangles) and its scratch, allocated through the
+ *     context's allocator callback (or cudaMallocAsync on the context stream when none is
+ *     given).
+ *   - All floating-point work is FP32.  Images are row-major, y = 0 at the top row.
+ */
+#ifndef SUPERCAUSTICS_H
+#define SUPERCAUSTICS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SC_ABI_VERSION 1
+
+#define SC_OK 0
+#define SC_ERR_INVALID_ARG (-1)
+#define SC_ERR_CUDA (-2)
+#define SC_ERR_OOM (-3)
+#define SC_ERR_STACK_OVERFLOW (-4)
+#define SC_ERR_TIMEOUT (-5)
+#define SC_ERR_QUEUE_OVERFLOW (-6)
+#define SC_ERR_UNSUPPORTED (-7)
+
+/* device status bits latched by kernels (sc_sync_status maps them to the codes above) */
+#define SC_STATUS_STACK_OVERFLOW 1u
+#define SC_STATUS_WATCHDOG 2u
+#define SC_STATUS_QUEUE_OVERFLOW 4u
+
+typedef struct sc_ctx sc_ctx;
+typedef struct sc_scene sc_scene;
+
+/* Allocator callback pair.  alloc returns device memory of at least `bytes` (256-byte
+ * aligned) usable on the context stream, or NULL; free releases it. */
+typedef void *(*sc_alloc_fn)(size_t bytes, void *user);
+typedef void (*sc_free_fn)(void *ptr, void *user);
+
+enum { SC_MAT_DIFFUSE = 0, SC_MAT_DIELECTRIC = 1, SC_MAT_EMISSIVE = 2 };
+enum { SC_LIGHT_POINT = 0, SC_LIGHT_RECT = 1, SC_LIGHT_DISK = 2 };
+
+/* Test hooks of the estimators (0 in production). */
+enum {
+  SC_FLAG_FORCE_TRANSMIT = 1,   /* dielectrics refract unless totally internally reflecting */
+  SC_FLAG_SPLAT_DIRECT = 2,     /* light tracer also splats paths with no specular event */
+  SC_FLAG_EMITTER_AFTER_DS = 4  /* camera paths count emitters reached as E D S+ L */
+};
+
+/* Surface description (Sec. III-C lists the glass and backdrop properties the paper varies).
+ * DIFFUSE: Lambert albedo; if checker_scale > 0, albedo alternates with albedo2 on a
+ * checkerboard of checker_scale squares per unit of the surface uv.  DIELECTRIC: glass with
+ * Cauchy index n(lambda) = cauchy_a + cauchy_b / lambda_um^2.  EMISSIVE: one-sided emitter
+ * of radiance `emission` along the triangle winding normal. */
+typedef struct {
+  int32_t kind;
+  float albedo[3];
+  float albedo2[3];
+  float checker_scale;
+  float cauchy_a, cauchy_b;
+  float emission[3];
+} sc_material;
+
+/* Light sources (Sec. III-C "lighting"; Fig. 4: softness follows the source size).
+ * POINT: p = position, power = intensity (W/sr).  RECT: p = corner, u, v = edges,
+ * power = radiance, emitting along u x v.  DISK: collimated beam for optics tests:
+ * p = centre, u = direction, radius, power = irradiance. */
+typedef struct {
+  int32_t kind;
+  float p[3], u[3], v[3];
+  float power[3];
+  float radius;
+} sc_light;
+
+/* Pinhole camera: eye, look-at point, up vector, vertical field of view in degrees. */
+typedef struct {
+  float eye[3], look[3], up[3];
+  float vfov_deg;
+  int32_t width, height;
+} sc_camera;
+
+/* Scene description.  Geometry arrays are world-space triangles:
+ *   positions  n_verts*3 float, normals n_verts*3 float or NULL (a zero vertex normal makes
+ *   its triangles flat), uvs n_verts*2 float or NULL, indices n_tris*3 int32 (winding gives
+ *   the geometric normal), tri_object n_tris int32 object id.
+ * When geometry_on_device is nonzero those five arrays are device pointers, otherwise host.
+ * object_material, materials and lights are always host arrays.  Everything is copied
+ * during sc_build_scene; the caller may free it afterwards. */
+typedef struct {
+  int32_t n_verts, n_tris;
+  const float *positions;
+  const float *normals;
+  const float *uvs;
+  const int32_t *indices;
+  const int32_t *tri_object;
+  int32_t n_objects;
+  const int32_t *object_material;
+  int32_t n_materials;
+  const sc_material *materials;
+  int32_t n_lights;
+  const sc_light *lights;
+  float env[3];
+  sc_camera camera;
+  int32_t geometry_on_device;
+} sc_scene_desc;
+
+/* Camera estimator parameters.  Sample s of pixel p draws Philox4x32-10 with key = seed and
+ * counter (p, s, depth, tag | scene_index << 8), so ranges of sample_offset compose exactly. */
+typedef struct {
+  int32_t spp, sample_offset, max_depth, n_bins;
+  uint64_t seed;
+  int32_t scene_index, flags;
+} sc_trace_params;
+
+/* Light tracer parameters: paths path_offset .. path_offset + n_paths - 1. */
+typedef struct {
+  int64_t n_paths, path_offset;
+  int32_t max_depth, n_bins;
+  uint64_t seed;
+  int32_t scene_index, flags;
+} sc_light_params;
+
+/* Resolve: divide accumulators by their totals and derive the ground-truth buffers. */
+typedef struct {
+  double spp_total;          /* camera samples accumulated per pixel */
+  double light_paths_total;  /* light paths accumulated (0 = no caustic buffer) */
+  float depth_range;         /* Sec. III-D depth range, 10 m by default */
+  float tau_rel;             /* caustic mask threshold relative to direct luminance */
+} sc_resolve_params;
+
+/* One record per camera path (debug / parity output). */
+typedef struct {
+  float L[3];           /* path radiance times the spectral weight of its bin */
+  uint32_t first_tri;   /* first hit triangle (input order), 0xFFFFFFFF = miss */
+  uint32_t signature;   /* FNV-1a over hit triangles and scattering decisions */
+  uint32_t n_queries;   /* closest-hit queries traced */
+  uint32_t bin;         /* wavelength bin */
+  uint32_t n_specular;  /* dielectric events */
+} sc_path_record;
+
+/* One record per light path (debug / parity output). */
+typedef struct {
+  float C[3];           /* splatted contribution (before division by the path count) */
+  int32_t pixel;        /* splat target y*W+x, -1 = none */
+  float x[3];           /* receiver point (first diffuse hit after glass), NaN = none */
+  uint32_t signature;
+  uint32_t n_specular;
+  uint32_t bin;
+  uint32_t pad[2];
+} sc_light_record;
+
+/* Frame buffers, all device pointers owned by the caller, any may be NULL (not produced).
+ * float4 buffers hold rgb (or xyz) in .xyz.  width/height must match the scene camera. */
+typedef struct {
+  float *accum_camera;      /* float4[W*H], radiance sums added by sc_trace_camera */
+  float *accum_caustic;     /* float4[W*H], splat sums added by sc_trace_lights */
+  float *rgb;               /* float4[W*H] direct + caustic */
+  float *direct;            /* float4[W*H] camera estimator / spp_total */
+  float *caustic;           /* float4[W*H] splats / light_paths_total */
+  int32_t *instance_id;     /* int32[W*H] object id of the pixel-centre hit, -1 = miss */
+  int32_t *tri_id;          /* int32[W*H] triangle id (input order), -1 = miss */
+  uint8_t *mask;            /* uint8[W*H] 1 = transparent object */
+  uint8_t *caustic_mask;    /* uint8[W*H] non-local caustic (on a non-glass surface) */
+  uint8_t *local_caustic_mask; /* uint8[W*H] caustic seen through glass (always 0) */
+  float *depth;             /* float[W*H] Euclidean distance, +inf = miss */
+  float *depth_norm;        /* float[W*H] min(depth / depth_range, 1) */
+  float *normal_world;      /* float4[W*H] shading normal facing the camera, w = 1 on hit */
+  float *normal_camera;     /* float4[W*H] the same in camera space (x right, y up, z to eye) */
+  float *albedo;            /* float4[W*H] first-hit albedo (glass 1, miss 0) */
+  sc_path_record *path_records;    /* [H][W][spp] of the last sc_trace_camera call, or NULL */
+  sc_light_record *light_records;  /* [n_paths] of the last sc_trace_lights call, or NULL */
+  int32_t width, height;
+} sc_frame;
+
+/* Read-only summary of a built scene. */
+typedef struct {
+  int32_t n_tris, n_nodes, n_materials, n_lights;
+  int64_t bvh_bytes;   /* nodes + reordered triangles + shading attributes */
+  int32_t max_depth;   /* deepest leaf of the BVH */
+  int32_t pad;
+} sc_scene_info;
+
+/* --- context ------------------------------------------------------------------------- */
+int sc_abi_version(void);
+/* sizes of the public structs in this order: material, light, camera, scene_desc,
+ * trace_params, light_params, resolve_params, path_record, light_record, frame,
+ * scene_info; returns the count written (<= n). */
+int sc_struct_sizes(int32_t *out, int32_t n);
+/* Create a context on `device` using `stream` (a cudaStream_t, NULL = legacy default). */
+int sc_create(int device, void *stream, sc_alloc_fn alloc, sc_free_fn free_fn, void *user, sc_ctx **out);
+int sc_destroy(sc_ctx *ctx);
+int sc_set_stream(sc_ctx *ctx, void *stream);
+const char *sc_last_error(const sc_ctx *ctx);
+/* Synchronise the stream and report (then clear) latched device status bits. */
+int sc_sync_status(sc_ctx *ctx);
+/* Optional traversal work counters: a device uint64[3] that sc_trace_camera and
+ * sc_trace_lights add to while set: [0] traversal queries (closest + any hit), [1] BVH
+ * nodes visited (each = two child-box tests), [2] triangle tests.  NULL switches counting
+ * off.  The caller owns the buffer and zeroes it. */
+int sc_set_counters(sc_ctx *ctx, uint64_t *counters);
+
+/* --- scene: LBVH build (Karras 2012 hierarchy over 30-bit Morton codes) ------------------ */
+int sc_build_scene(sc_ctx *ctx, const sc_scene_desc *desc, sc_scene **out);
+int sc_free_scene(sc_ctx *ctx, sc_scene *scene);
+int sc_scene_get_info(const sc_scene *scene, sc_scene_info *info);
+/* Copy the BVH to host memory for inspection: nodes_host receives n_nodes * 64 bytes
+ * (float4 c0 x/y bounds, float4 c1 x/y bounds, float4 z bounds, int4 children; a child
+ * < 0 is leaf ~k), tris_host n_tris * 48 bytes (three float4 vertices in leaf order, .w
+ * of the first holding the input triangle index as int bits).  Synchronises. */
+int sc_scene_export_bvh(sc_ctx *ctx, const sc_scene *scene, void *nodes_host, void *tris_host);
+
+/* --- queries --------------------------------------------------------------------------- */
+/* Closest hit for n rays.  rays: device float[n][8] = (ox,oy,oz,tmax, dx,dy,dz,0);
+ * hits: device float[n][4] = (t, tri as int bits (input order, -1 miss), b1, b2). */
+int sc_intersect(sc_ctx *ctx, const sc_scene *scene, const float *rays, int64_t n, float *hits);
+/* Any hit with t in (0, tmax): occluded[i] = 1/0.  Same ray layout. */
+int sc_occluded(sc_ctx *ctx, const sc_scene *scene, const float *rays, int64_t n, int32_t *occluded);
+/* Philox4x32-10 of n device counters (uint32[n][4]) under `key`, into device out[n][4]. */
+int sc_philox4x32_10(sc_ctx *ctx, const uint32_t *counters, uint64_t key, int64_t n, uint32_t *out);
+
+/* --- estimators ------------------------------------------------------------------------ */
+/* Camera path tracer: adds spp samples per pixel into frame->accum_camera. */
+int sc_trace_camera(sc_ctx *ctx, const sc_scene *scene, const sc_trace_params *params, const sc_frame *frame);
+/* Light tracer: traces n_paths light paths and splats caustics into frame->accum_caustic. */
+int sc_trace_lights(sc_ctx *ctx, const sc_scene *scene, const sc_light_params *params, const sc_frame *frame);
+/* Resolve: rgb/direct/caustic from the accumulators, plus the pixel-centre ground truth. */
+int sc_resolve(sc_ctx *ctx, const sc_scene *scene, const sc_resolve_params *params, const sc_frame *frame);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

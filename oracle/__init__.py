@@ -22,7 +22,7 @@ FLAG_SPLAT_DIRECT = 2
 FLAG_EMITTER_AFTER_DS = 4
 
 AMB_NAMES = {1: "edge", 2: "tgap", 4: "graze", 8: "fresnel", 16: "tir", 32: "shadow", 64: "splat",
-             128: "checker", 256: "fixup"}
+             128: "checker", 256: "fixup", 512: "sensitive"}
 
 
 def build(force: bool = False) -> str:
@@ -36,12 +36,24 @@ def build(force: bool = False) -> str:
 
 
 class Tolerances(C.Structure):
+    """Base tolerances of the ambiguity classifier; each specular event before a decision
+    multiplies its tolerance by ``growth`` (FP32 error compounds along glass chains)."""
     _fields_ = [("pos", C.c_double), ("t", C.c_double), ("cosg", C.c_double), ("fres", C.c_double),
-                ("tir", C.c_double), ("px", C.c_double)]
+                ("tir", C.c_double), ("px", C.c_double), ("growth", C.c_double), ("sens_delta", C.c_double),
+                ("sens_rel", C.c_double)]
 
 
-def default_tol() -> Tolerances:
-    return Tolerances(2e-5, 1e-5, 1e-4, 1e-4, 1e-5, 1e-3)
+# sens_delta: every recorded path is re-traced twice with its ray nudged by +-1e-6 (relative) after
+# each scattering event; a path whose signature or radiance (beyond sens_rel) moves is flagged
+# "sensitive" -- float32 cannot be expected to follow it decision for decision.
+DEFAULT_TOL = dict(pos=2e-5, t=1e-5, cosg=1e-4, fres=1e-4, tir=1e-5, px=1e-3, growth=1.0, sens_delta=1e-6,
+                   sens_rel=1e-4)
+
+
+def default_tol(**kw) -> Tolerances:
+    d = dict(DEFAULT_TOL)
+    d.update(kw)
+    return Tolerances(**d)
 
 
 class CamParams(C.Structure):
@@ -53,7 +65,9 @@ class CamParams(C.Structure):
 
 class PathRec(C.Structure):
     _fields_ = [("L", C.c_double * 3), ("p0", C.c_double * 3), ("first_tri", C.c_int32), ("n_queries", C.c_int32),
-                ("signature", C.c_uint32), ("amb", C.c_int32), ("bin", C.c_int32), ("n_specular", C.c_int32)]
+                ("signature", C.c_uint32), ("amb", C.c_int32), ("bin", C.c_int32), ("n_specular", C.c_int32),
+                ("min_ratio", C.c_double), ("ratio_nspec", C.c_int32), ("ratio_kind", C.c_int32),
+                ("kmin", C.c_double * 9), ("knspec", C.c_int32 * 9), ("pad2", C.c_int32)]
 
 
 class LightParams(C.Structure):
@@ -64,7 +78,9 @@ class LightParams(C.Structure):
 
 class LightRec(C.Structure):
     _fields_ = [("C", C.c_double * 3), ("x", C.c_double * 3), ("pixel", C.c_int32), ("amb", C.c_int32),
-                ("signature", C.c_uint32), ("n_specular", C.c_int32), ("bin", C.c_int32), ("pad", C.c_int32)]
+                ("signature", C.c_uint32), ("n_specular", C.c_int32), ("bin", C.c_int32), ("pad", C.c_int32),
+                ("min_ratio", C.c_double), ("ratio_nspec", C.c_int32), ("ratio_kind", C.c_int32),
+                ("kmin", C.c_double * 9), ("knspec", C.c_int32 * 9), ("pad2", C.c_int32)]
 
 
 class ResolveParams(C.Structure):
@@ -176,8 +192,11 @@ class OracleScene:
     def trace_camera(self, spp, max_depth, nbins=1, seed=0, sample_offset=0, scene_index=0, flags=0, window=None,
                      records=True, accum=None, n_threads=0, brute=False, tol=None):
         x0, x1, y0, y1 = window if window is not None else (0, self.W, 0, self.H)
+        tol = tol or default_tol()
+        if not records:
+            tol.sens_delta = 0.0  # the re-traces only classify recorded paths
         P = CamParams(spp, sample_offset, max_depth, nbins, seed, scene_index, flags, x0, x1, y0, y1, n_threads,
-                      int(brute), tol or default_tol())
+                      int(brute), tol)
         if accum is None:
             accum = np.zeros((self.H, self.W, 3))
         recs = (PathRec * ((y1 - y0) * (x1 - x0) * spp))() if records else None
@@ -186,8 +205,10 @@ class OracleScene:
 
     def trace_lights(self, n_paths, max_depth, nbins=1, seed=0, path_offset=0, scene_index=0, flags=0,
                      records=True, accum=None, n_threads=0, brute=False, tol=None):
-        P = LightParams(n_paths, path_offset, max_depth, nbins, seed, scene_index, flags, n_threads, int(brute),
-                        tol or default_tol())
+        tol = tol or default_tol()
+        if not records:
+            tol.sens_delta = 0.0
+        P = LightParams(n_paths, path_offset, max_depth, nbins, seed, scene_index, flags, n_threads, int(brute), tol)
         if accum is None:
             accum = np.zeros((self.H, self.W, 3))
         recs = (LightRec * n_paths)() if records else None

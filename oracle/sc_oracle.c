@@ -49,7 +49,7 @@ enum { LIGHT_POINT = 0, LIGHT_RECT = 1, LIGHT_DISK = 2 };
 enum { FLAG_FORCE_TRANSMIT = 1, FLAG_SPLAT_DIRECT = 2, FLAG_EMITTER_AFTER_DS = 4 };
 enum {
   AMB_EDGE = 1, AMB_TGAP = 2, AMB_GRAZE = 4, AMB_FRESNEL = 8, AMB_TIR = 16,
-  AMB_SHADOW = 32, AMB_SPLAT = 64, AMB_CHECKER = 128, AMB_FIXUP = 256
+  AMB_SHADOW = 32, AMB_SPLAT = 64, AMB_CHECKER = 128, AMB_FIXUP = 256, AMB_SENSITIVE = 512
 };
 enum { EV_MISS = 0xFFFFFFFFu, EV_REFLECT = 1, EV_REFRACT = 2, EV_LIT = 3, EV_UNLIT = 4, EV_FIXUP = 7 };
 
@@ -235,15 +235,22 @@ typedef struct {
 } scene;
 
 typedef struct {
-  double pos;   /* edge/near-miss distance, relative to max(1,|p|inf) */
-  double t;     /* relative t gap */
-  double cosg;  /* |cos| against the geometric normal */
-  double fres;  /* |u - R| */
-  double tir;   /* |cos_t^2| */
-  double px;    /* splat distance to a pixel border, in pixels */
+  double pos;    /* edge / near-miss / checker distance, relative to max(1,|p|inf) */
+  double t;      /* relative gap between the two closest hits */
+  double cosg;   /* |cos| against the geometric normal, |u - R| style direction margins */
+  double fres;   /* |u - R| of a Fresnel draw */
+  double tir;    /* |cos_t^2| near total internal reflection */
+  double px;     /* splat distance to a pixel border, in pixels */
+  double growth; /* each specular event before a decision multiplies its tolerance by this */
+  double sens_delta; /* relative size of the ray perturbations of the sensitivity re-traces (0 = off) */
+  double sens_rel;   /* a re-trace moving the radiance by more than this (relative) flags the path */
 } tolerances;
 
-static const tolerances DEFAULT_TOL = {2e-5, 1e-5, 1e-4, 1e-4, 1e-5, 1e-3};
+static const tolerances DEFAULT_TOL = {2e-5, 1e-5, 1e-4, 1e-4, 1e-5, 1e-3, 1.0, 0.0, 1e-4};
+
+/* near misses are tracked inside this window (relative), wider than any tolerance */
+#define NM_WIN 1e-3
+#define T_WIN 1e-3
 
 static int cmp_axis;
 static const double *cmp_cent;
@@ -296,14 +303,14 @@ ORC_API void *orc_scene_create(int nv, const float *pos, const float *nrm, const
   (void)nv; (void)nobj;
   scene *s = calloc(1, sizeof(scene));
   s->nt = nt;
-  s->v = malloc(sizeof(v3) * 3 * (size_t)nt);
-  s->n = malloc(sizeof(v3) * 3 * (size_t)nt);
-  s->uv = malloc(sizeof(double) * 6 * (size_t)nt);
-  s->smooth = malloc(sizeof(int) * (size_t)nt);
-  s->mat = malloc(sizeof(int) * (size_t)nt);
-  s->obj = malloc(sizeof(int) * (size_t)nt);
-  s->alt = malloc(sizeof(double) * 3 * (size_t)nt);
-  s->ng = malloc(sizeof(v3) * (size_t)nt);
+  s->v = malloc(sizeof(v3) * 3 * (size_t)(nt > 0 ? nt : 1));
+  s->n = malloc(sizeof(v3) * 3 * (size_t)(nt > 0 ? nt : 1));
+  s->uv = malloc(sizeof(double) * 6 * (size_t)(nt > 0 ? nt : 1));
+  s->smooth = malloc(sizeof(int) * (size_t)(nt > 0 ? nt : 1));
+  s->mat = malloc(sizeof(int) * (size_t)(nt > 0 ? nt : 1));
+  s->obj = malloc(sizeof(int) * (size_t)(nt > 0 ? nt : 1));
+  s->alt = malloc(sizeof(double) * 3 * (size_t)(nt > 0 ? nt : 1));
+  s->ng = malloc(sizeof(v3) * (size_t)(nt > 0 ? nt : 1));
   for (int t = 0; t < nt; ++t) {
     int sm = 1;
     for (int j = 0; j < 3; ++j) {
@@ -355,7 +362,7 @@ ORC_API void *orc_scene_create(int nv, const float *pos, const float *nrm, const
   s->W = W; s->H = H; s->aspect = (double)W / (double)H;
   s->env = V(env[0], env[1], env[2]);
   /* BVH with boxes padded so that near misses are still visited */
-  s->box_pad = 4.0 * DEFAULT_TOL.pos;
+  s->box_pad = 2.0 * NM_WIN;
   s->nodes = malloc(sizeof(bnode) * (size_t)(2 * (nt > 0 ? nt : 1)));
   s->tri_order = malloc(sizeof(int) * (size_t)(nt > 0 ? nt : 1));
   double *cent = malloc(sizeof(double) * 3 * (size_t)(nt > 0 ? nt : 1));
@@ -379,13 +386,42 @@ ORC_API void orc_scene_destroy(void *p) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
-/* ray / triangle (Moller-Trumbore 1997, FP64, inclusive edges) with decision margins           */
+/* decision margins: how far each discrete decision of a path was from flipping                */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+  const tolerances *tol;
+  int nspec;         /* specular events so far */
+  int amb;           /* flags of decisions inside their (grown) tolerance */
+  double min_ratio;  /* smallest margin / base tolerance over the path */
+  int ratio_nspec;   /* specular events before that decision */
+  int ratio_kind;    /* its flag */
+  double kmin[9];    /* smallest margin / base tolerance per decision kind (bit index of the flag) */
+  int knspec[9];     /* specular events before it */
+} actx;
+
+static void actx_init(actx *a, const tolerances *tol) {
+  a->tol = tol; a->nspec = 0; a->amb = 0; a->min_ratio = INFINITY; a->ratio_nspec = 0; a->ratio_kind = 0;
+  for (int i = 0; i < 9; ++i) { a->kmin[i] = INFINITY; a->knspec[i] = 0; }
+}
+/* margin m against base tolerance b: flagged when m < b * growth^nspec */
+static void note(actx *a, double m, double b, int flag) {
+  double r = m / b;
+  if (r < a->min_ratio) { a->min_ratio = r; a->ratio_nspec = a->nspec; a->ratio_kind = flag; }
+  int k = __builtin_ctz((unsigned)flag);
+  if (r < a->kmin[k]) { a->kmin[k] = r; a->knspec[k] = a->nspec; }
+  if (r < pow(a->tol->growth, a->nspec)) a->amb |= flag;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* ray / triangle (Moller-Trumbore 1997, FP64, inclusive edges)                                */
 /* ------------------------------------------------------------------------------------------ */
 typedef struct { v3 o, d; } ray;
 typedef struct {
-  int tri;       /* -1 = miss */
+  int tri;        /* -1 = miss */
   double t, b1, b2;
-  int amb;
+  double m_edge;  /* distance (world units) to flipping the hit triangle: own edges, closer near misses */
+  double m_tgap;  /* relative gap to the second closest hit */
+  double scale;   /* max(1, |p|inf) at the decision point */
 } hit;
 
 /* plane intersection: returns 0 if the ray is parallel to the triangle's plane */
@@ -424,102 +460,137 @@ static int box_hit(const bnode *nd, ray r, double tmax) {
   return 1;
 }
 
+#define NEAR_MAX 16
 typedef struct {
-  int best; double bt, bu, bv, bmargin;
-  double t2;     /* second closest hit */
-  double tnear;  /* closest near miss */
-  double tol_abs;
+  int best; double bt, bu, bv, bmargin, bscale;
+  double t2;                        /* second closest hit */
+  int nn;                           /* near misses kept (closest in t) */
+  double nt[NEAR_MAX], nd[NEAR_MAX], ns[NEAR_MAX];
 } closest_state;
 
-static void closest_test(const scene *s, int t, ray r, closest_state *cs, const tolerances *tol) {
+static void closest_test(const scene *s, int t, ray r, closest_state *cs) {
   double tt, u, v;
   if (!mt(s, t, r, &tt, &u, &v)) return;
   if (!(tt > 0.0)) return;
   v3 p = add(r.o, mul(r.d, tt));
   double m = edge_margin(s, t, u, v);
-  double scale = tol->pos * fmax(1.0, maxabs(p));
+  double scale = fmax(1.0, maxabs(p));
   if (m >= 0.0) {
     if (tt < cs->bt || (tt == cs->bt && t < cs->best)) {
       if (cs->best >= 0) cs->t2 = fmin(cs->t2, cs->bt);
-      cs->best = t; cs->bt = tt; cs->bu = u; cs->bv = v; cs->bmargin = m; cs->tol_abs = scale;
+      cs->best = t; cs->bt = tt; cs->bu = u; cs->bv = v; cs->bmargin = m; cs->bscale = scale;
     } else {
       cs->t2 = fmin(cs->t2, tt);
     }
-  } else if (m > -scale) {
-    cs->tnear = fmin(cs->tnear, tt);
+  } else if (-m < NM_WIN * scale) {
+    /* keep the near misses with the smallest t */
+    int slot = cs->nn < NEAR_MAX ? cs->nn++ : -1;
+    if (slot < 0) {
+      int worst = 0;
+      for (int i = 1; i < NEAR_MAX; ++i) if (cs->nt[i] > cs->nt[worst]) worst = i;
+      if (cs->nt[worst] <= tt) return;
+      slot = worst;
+    }
+    cs->nt[slot] = tt; cs->nd[slot] = -m; cs->ns[slot] = scale;
   }
 }
 
-static hit closest(const scene *s, ray r, int brute, const tolerances *tol) {
-  closest_state cs = {-1, INFINITY, 0, 0, 0, INFINITY, INFINITY, 0};
+static hit closest(const scene *s, ray r, int brute) {
+  closest_state cs;
+  cs.best = -1; cs.bt = INFINITY; cs.bu = cs.bv = cs.bmargin = 0; cs.bscale = 1; cs.t2 = INFINITY; cs.nn = 0;
   if (brute || s->nnodes == 0) {
-    for (int t = 0; t < s->nt; ++t) closest_test(s, t, r, &cs, tol);
+    for (int t = 0; t < s->nt; ++t) closest_test(s, t, r, &cs);
   } else {
     int stack[128], sp = 0;
     stack[sp++] = 0;
     while (sp) {
       const bnode *nd = &s->nodes[stack[--sp]];
-      if (!box_hit(nd, r, cs.bt * (1.0 + 4.0 * tol->t) + 1e-12)) continue;
+      if (!box_hit(nd, r, cs.bt * (1.0 + 4.0 * T_WIN) + 1e-12)) continue;
       if (nd->left < 0) {
-        for (int i = nd->first; i < nd->first + nd->count; ++i) closest_test(s, s->tri_order[i], r, &cs, tol);
+        for (int i = nd->first; i < nd->first + nd->count; ++i) closest_test(s, s->tri_order[i], r, &cs);
       } else {
         stack[sp++] = nd->left;
         stack[sp++] = nd->right;
       }
     }
   }
-  hit h = {cs.best, cs.bt, cs.bu, cs.bv, 0};
+  hit h;
+  h.tri = cs.best; h.t = cs.bt; h.b1 = cs.bu; h.b2 = cs.bv;
+  h.m_edge = INFINITY; h.m_tgap = INFINITY; h.scale = cs.bscale;
   if (cs.best >= 0) {
-    if (cs.bmargin < cs.tol_abs) h.amb |= AMB_EDGE;
-    if (cs.tnear <= cs.bt * (1.0 + tol->t)) h.amb |= AMB_EDGE;
-    if (cs.t2 <= cs.bt * (1.0 + tol->t)) h.amb |= AMB_TGAP;
-  } else if (cs.tnear < INFINITY) {
-    h.amb |= AMB_EDGE;
+    h.m_edge = cs.bmargin;
+    for (int i = 0; i < cs.nn; ++i)
+      if (cs.nt[i] <= cs.bt * (1.0 + T_WIN)) h.m_edge = fmin(h.m_edge, cs.nd[i]);
+    if (cs.t2 < INFINITY) h.m_tgap = (cs.t2 - cs.bt) / cs.bt;
+  } else {
+    for (int i = 0; i < cs.nn; ++i)
+      if (cs.nd[i] < h.m_edge) { h.m_edge = cs.nd[i]; h.scale = cs.ns[i]; }
   }
   return h;
 }
 
-/* any hit with t in (0, tmax): returns 1 if occluded; sets *amb if the answer could flip */
-static void any_test(const scene *s, int t, ray r, double tmax, int *hitany, int *robust, int *amb,
-                     const tolerances *tol) {
+/* closest hit plus its margins noted in the path context */
+static hit closest_noted(const scene *s, ray r, int brute, actx *a) {
+  hit h = closest(s, r, brute);
+  const tolerances *tol = a->tol;
+  note(a, h.m_edge, tol->pos * h.scale, AMB_EDGE);
+  note(a, h.m_tgap, tol->t, AMB_TGAP);
+  return h;
+}
+
+/* any hit with t in (0, tmax); *margin = world distance to flipping the answer (inf if robust) */
+typedef struct {
+  int hitany, robust;
+  double margin;  /* relative to scale */
+  double tgap;    /* relative distance of a hit / near miss to tmax */
+} occ_state;
+
+static void any_test(const scene *s, int t, ray r, double tmax, occ_state *os) {
   double tt, u, v;
   if (!mt(s, t, r, &tt, &u, &v)) return;
   if (!(tt > 0.0)) return;
+  if (tt >= tmax * (1.0 + T_WIN)) return;
   v3 p = add(r.o, mul(r.d, tt));
   double m = edge_margin(s, t, u, v);
-  double scale = tol->pos * fmax(1.0, maxabs(p));
-  int near_end = fabs(tt - tmax) <= tol->t * tmax;
-  if (tt >= tmax && !near_end) return;
+  double scale = fmax(1.0, maxabs(p));
+  double gap = fabs(tt - tmax) / tmax;
   if (m >= 0.0 && tt < tmax) {
-    *hitany = 1;
-    if (m >= scale && !near_end) *robust = 1;
-    else *amb = 1;
-  } else if (m > -scale || near_end) {
-    if (m > -scale) *amb = 1;
+    os->hitany = 1;
+    if (m >= NM_WIN * scale && gap >= T_WIN) { os->robust = 1; return; }
   }
+  if (fabs(m) < NM_WIN * scale) os->margin = fmin(os->margin, fabs(m) / scale);
+  if (m >= 0.0 || fabs(m) < NM_WIN * scale) os->tgap = fmin(os->tgap, gap);
 }
 
-static int occluded(const scene *s, ray r, double tmax, int brute, int *amb_out, const tolerances *tol) {
-  int hitany = 0, robust = 0, amb = 0;
+static int occluded_m(const scene *s, ray r, double tmax, int brute, double *margin, double *tgap) {
+  occ_state os = {0, 0, INFINITY, INFINITY};
   if (brute || s->nnodes == 0) {
-    for (int t = 0; t < s->nt && !robust; ++t) any_test(s, t, r, tmax, &hitany, &robust, &amb, tol);
+    for (int t = 0; t < s->nt && !os.robust; ++t) any_test(s, t, r, tmax, &os);
   } else {
     int stack[128], sp = 0;
     stack[sp++] = 0;
-    while (sp && !robust) {
+    while (sp && !os.robust) {
       const bnode *nd = &s->nodes[stack[--sp]];
-      if (!box_hit(nd, r, tmax * (1.0 + 4.0 * tol->t))) continue;
+      if (!box_hit(nd, r, tmax * (1.0 + 4.0 * T_WIN))) continue;
       if (nd->left < 0) {
-        for (int i = nd->first; i < nd->first + nd->count && !robust; ++i)
-          any_test(s, s->tri_order[i], r, tmax, &hitany, &robust, &amb, tol);
+        for (int i = nd->first; i < nd->first + nd->count && !os.robust; ++i) any_test(s, s->tri_order[i], r, tmax, &os);
       } else {
         stack[sp++] = nd->left;
         stack[sp++] = nd->right;
       }
     }
   }
-  *amb_out = robust ? 0 : amb;
-  return hitany;
+  *margin = os.robust ? INFINITY : os.margin;
+  *tgap = os.robust ? INFINITY : os.tgap;
+  return os.hitany;
+}
+
+static int occluded_noted(const scene *s, ray r, double tmax, int brute, actx *a) {
+  double m, g;
+  int occ = occluded_m(s, r, tmax, brute, &m, &g);
+  note(a, m, a->tol->pos, AMB_SHADOW);
+  note(a, g, a->tol->t, 32);
+  return occ;
 }
 
 ORC_API void orc_intersect(void *sp, int64_t n, const double *rays, int brute, double *t_out, int *tri_out,
@@ -527,10 +598,12 @@ ORC_API void orc_intersect(void *sp, int64_t n, const double *rays, int brute, d
   const scene *s = sp;
   for (int64_t i = 0; i < n; ++i) {
     ray r = {V(rays[6 * i], rays[6 * i + 1], rays[6 * i + 2]), V(rays[6 * i + 3], rays[6 * i + 4], rays[6 * i + 5])};
-    hit h = closest(s, r, brute, &DEFAULT_TOL);
+    actx a;
+    actx_init(&a, &DEFAULT_TOL);
+    hit h = closest_noted(s, r, brute, &a);
     t_out[i] = h.t; tri_out[i] = h.tri;
     if (b_out) { b_out[2 * i] = h.b1; b_out[2 * i + 1] = h.b2; }
-    if (amb_out) amb_out[i] = h.amb;
+    if (amb_out) amb_out[i] = a.amb;
   }
 }
 
@@ -539,9 +612,10 @@ ORC_API void orc_occluded(void *sp, int64_t n, const double *rays, const double 
   const scene *s = sp;
   for (int64_t i = 0; i < n; ++i) {
     ray r = {V(rays[6 * i], rays[6 * i + 1], rays[6 * i + 2]), V(rays[6 * i + 3], rays[6 * i + 4], rays[6 * i + 5])};
-    int a = 0;
-    occ[i] = occluded(s, r, tmax[i], brute, &a, &DEFAULT_TOL);
-    if (amb) amb[i] = a;
+    actx a;
+    actx_init(&a, &DEFAULT_TOL);
+    occ[i] = occluded_noted(s, r, tmax[i], brute, &a);
+    if (amb) amb[i] = a.amb;
   }
 }
 
@@ -583,7 +657,7 @@ static v3 offset_along(v3 p, v3 ng, v3 dir) {
   return add(p, mul(ng, sgn * eps_of(p)));
 }
 
-static v3 albedo_at(const scene *s, int tri, const surf *f, int *amb, const tolerances *tol) {
+static v3 albedo_at(const scene *s, int tri, const surf *f, actx *a) {
   const material *m = &s->mats[f->mat];
   if (m->checker <= 0) return m->a1;
   double b0 = 1.0 - f->u - f->v;
@@ -591,15 +665,18 @@ static v3 albedo_at(const scene *s, int tri, const surf *f, int *amb, const tole
   double su = (b0 * q[0] + f->u * q[2] + f->v * q[4]) * m->checker;
   double sv = (b0 * q[1] + f->u * q[3] + f->v * q[5]) * m->checker;
   double fu = floor(su), fv = floor(sv);
-  double band = tol->pos * fmax(1.0, maxabs(f->p)) * m->checker;
-  if (su - fu < band || fu + 1 - su < band || sv - fv < band || fv + 1 - sv < band) *amb |= AMB_CHECKER;
+  if (a) {
+    /* distance to the nearest cell border, in world units of the surface */
+    double du = fmin(su - fu, fu + 1 - su) / m->checker, dv = fmin(sv - fv, fv + 1 - sv) / m->checker;
+    note(a, fmin(du, dv), a->tol->pos * fmax(1.0, maxabs(f->p)), AMB_CHECKER);
+  }
   long parity = ((long)fu + (long)fv) & 1;
   return parity ? m->a2 : m->a1;
 }
 
 /* dielectric scatter; returns the new direction and whether it reflected */
 static v3 dielectric(const surf *f, v3 d, double n_lambda, double u0, int flags, int *reflected, int *fixup,
-                     int *amb, const tolerances *tol) {
+                     actx *a) {
   int entering = f->cosg < 0;
   double n_i = entering ? 1.0 : n_lambda, n_t = entering ? n_lambda : 1.0;
   double eta = n_i / n_t;
@@ -608,20 +685,21 @@ static v3 dielectric(const surf *f, v3 d, double n_lambda, double u0, int flags,
   for (int pass = 0; pass < 2; ++pass) {
     v3 n = pass == 0 ? f->nsf : f->ngf;
     double cos_i = -dot(d, n);
+    if (pass == 0) note(a, fabs(cos_i), a->tol->cosg, AMB_FIXUP);
     if (pass == 0 && cos_i <= 0) { *fixup = 1; continue; }
     double k = 1.0 - eta * eta * (1.0 - cos_i * cos_i);
-    if (fabs(k) < tol->tir) *amb |= AMB_TIR;
+    note(a, fabs(k), a->tol->tir, AMB_TIR);
     double R = 1.0;
     if (k >= 0) {
       R = fresnel(cos_i, sqrt(k), n_i, n_t);
-      if (fabs(u0 - R) < tol->fres) *amb |= AMB_FRESNEL;
+      if (!(flags & FLAG_FORCE_TRANSMIT)) note(a, fabs(u0 - R), a->tol->fres, AMB_FRESNEL);
     }
     int refl = (k < 0) || (!(flags & FLAG_FORCE_TRANSMIT) && u0 < R);
     if (refl) out = normalize(add(d, mul(n, 2.0 * cos_i)));
     else out = normalize(add(mul(d, eta), mul(n, eta * cos_i - sqrt(k))));
     *reflected = refl;
     double side = dot(out, f->ngf);
-    if (fabs(side) < tol->cosg) *amb |= AMB_FIXUP;
+    note(a, fabs(side), a->tol->cosg, AMB_FIXUP);
     int ok = refl ? side > 0 : side < 0;
     if (ok || pass == 1) break;
     *fixup = 1;
@@ -647,6 +725,10 @@ typedef struct {
   int32_t first_tri, n_queries;
   uint32_t signature;
   int32_t amb, bin, n_specular;
+  double min_ratio;
+  int32_t ratio_nspec, ratio_kind;
+  double kmin[9];
+  int32_t knspec[9], pad2;
 } path_rec;
 
 typedef struct {
@@ -664,6 +746,10 @@ typedef struct {
   int32_t pixel, amb;
   uint32_t signature;
   int32_t n_specular, bin, pad;
+  double min_ratio;
+  int32_t ratio_nspec, ratio_kind;
+  double kmin[9];
+  int32_t knspec[9], pad2;
 } light_rec;
 
 static uint32_t fnv(uint32_t h, uint32_t w) { return (h ^ w) * 16777619u; }
@@ -676,8 +762,8 @@ static ray camera_ray(const scene *s, double sx, double sy) {
 }
 
 /* next-event estimate at a diffuse vertex (without the throughput) */
-static v3 nee(const scene *s, const surf *f, v3 albedo, const uint32_t x[4], int brute, int *lit, int *amb,
-              const tolerances *tol) {
+static v3 nee(const scene *s, const surf *f, v3 albedo, const uint32_t x[4], int brute, int *lit, actx *a) {
+  const tolerances *tol = a->tol;
   *lit = 0;
   if (s->nlights == 0) return V(0, 0, 0);
   int j = choose(x[0], s->nlights);
@@ -690,12 +776,13 @@ static v3 nee(const scene *s, const surf *f, v3 albedo, const uint32_t x[4], int
     double d2 = dot(w, w);
     w = mul(w, 1.0 / sqrt(d2));
     double cs = dot(f->nsf, w), cg = dot(f->ngf, w);
-    if (fabs(cg) < tol->cosg || fabs(cs) < tol->cosg) *amb |= AMB_GRAZE;
+    note(a, fabs(cg), tol->cosg, AMB_GRAZE);
+    note(a, fabs(cs), tol->cosg, 4);
     if (!(cs > 0 && cg > 0)) return V(0, 0, 0);
     geo = cs / d2;
   } else if (L->kind == LIGHT_RECT) {
-    double a = u01(x[1]), b = u01(x[2]);
-    lp = add(add(L->p, mul(L->u, a)), mul(L->v, b));
+    double ua = u01(x[1]), ub = u01(x[2]);
+    lp = add(add(L->p, mul(L->u, ua)), mul(L->v, ub));
     le = L->power;
     v3 c = cross(L->u, L->v);
     double area = len(c);
@@ -704,7 +791,9 @@ static v3 nee(const scene *s, const surf *f, v3 albedo, const uint32_t x[4], int
     double d2 = dot(w, w);
     w = mul(w, 1.0 / sqrt(d2));
     double cs = dot(f->nsf, w), cg = dot(f->ngf, w), cl = -dot(nl, w);
-    if (fabs(cg) < tol->cosg || fabs(cs) < tol->cosg || fabs(cl) < tol->cosg) *amb |= AMB_GRAZE;
+    note(a, fabs(cg), tol->cosg, 4);
+    note(a, fabs(cs), tol->cosg, 4);
+    note(a, fabs(cl), tol->cosg, 4);
     if (!(cs > 0 && cg > 0 && cl > 0)) return V(0, 0, 0);
     geo = cs * cl * area / d2;
   } else {
@@ -715,38 +804,60 @@ static v3 nee(const scene *s, const surf *f, v3 albedo, const uint32_t x[4], int
   v3 w = sub(lp, sr.o);
   double dist = len(w);
   sr.d = mul(w, 1.0 / dist);
-  int a = 0;
-  int occ = occluded(s, sr, dist * (1.0 - 1e-4), brute, &a, tol);
-  if (a) *amb |= AMB_SHADOW;
+  int occ = occluded_noted(s, sr, dist * (1.0 - 1e-4), brute, a);
   if (occ) return V(0, 0, 0);
   *lit = 1;
   return mul(hadamard(albedo, le), geo * (double)s->nlights / PI);
 }
 
-static void camera_path(const scene *s, const cam_params *P, const double *wts, int px, int py, int sample,
-                        path_rec *rec) {
-  const tolerances *tol = &P->tol;
+/* Sensitivity re-trace: the same path with its ray nudged after every scattering event by a
+ * deterministic pseudo-random offset of relative size delta (a few float32 ulps or more).  A path
+ * whose decisions or radiance move under such nudges cannot be reproduced by a float32 tracer
+ * decision for decision, whatever its local margins. */
+static void nudge(ray *r, double delta, uint64_t seed, uint32_t c0, uint32_t c1, int k) {
+  if (delta == 0.0) return;
+  uint32_t x[4], y[4];
+  draw(seed, c0, c1, (uint32_t)k, 7, 0, x);
+  draw(seed, c0, c1, (uint32_t)k, 8, 0, y);
+  v3 a = V(2.0 * u01(x[0]) - 1.0, 2.0 * u01(x[1]) - 1.0, 2.0 * u01(x[2]) - 1.0);
+  v3 b = V(2.0 * u01(y[0]) - 1.0, 2.0 * u01(y[1]) - 1.0, 2.0 * u01(y[2]) - 1.0);
+  r->o = add(r->o, mul(a, delta * fmax(1.0, maxabs(r->o))));
+  r->d = normalize(add(r->d, mul(b, delta)));
+}
+
+static int sensitive3(const double *a, const double *b, double rel) {
+  for (int c = 0; c < 3; ++c) {
+    double sc = fmax(fmax(fabs(a[c]), fabs(b[c])), 1e-6);
+    if (fabs(a[c] - b[c]) > rel * sc) return 1;
+  }
+  return 0;
+}
+
+static void camera_path_impl(const scene *s, const cam_params *P, const double *wts, int px, int py,
+                             int sample, double delta, path_rec *rec) {
+  actx a;
+  actx_init(&a, &P->tol);
   uint32_t pix = (uint32_t)(py * s->W + px);
   uint32_t x[4];
   draw(P->seed, pix, (uint32_t)sample, 0, 0, (uint32_t)P->scene_index, x);
   int bin = choose(x[2], P->nbins > 0 ? P->nbins : 1);
   ray r = camera_ray(s, (px + u01(x[0])) / s->W, (py + u01(x[1])) / s->H);
+  nudge(&r, delta, P->seed ^ 0xA5A5A5A5ull, pix, (uint32_t)sample, 0);
   v3 beta = V(1, 1, 1), L = V(0, 0, 0);
-  int spec_only = 1, diffuse_first = 0, n_diffuse = 0, nspec = 0, amb = 0, q = 0;
+  int spec_only = 1, diffuse_first = 0, n_diffuse = 0, q = 0;
   uint32_t sig = 2166136261u;
   rec->first_tri = -1;
   rec->p0[0] = rec->p0[1] = rec->p0[2] = NAN;
   int last_specular = 0;
   for (int k = 0; k < P->max_depth; ++k) {
-    hit h = closest(s, r, P->brute, tol);
+    hit h = closest_noted(s, r, P->brute, &a);
     ++q;
-    amb |= h.amb;
     sig = fnv(sig, h.tri < 0 ? EV_MISS : (uint32_t)h.tri);
     if (k == 0) rec->first_tri = h.tri;
     if (h.tri < 0) { L = add(L, hadamard(beta, s->env)); break; }
     surf f = interact(s, r, h);
     if (k == 0) { rec->p0[0] = f.p.x; rec->p0[1] = f.p.y; rec->p0[2] = f.p.z; }
-    if (fabs(f.cosg) < tol->cosg) amb |= AMB_GRAZE;
+    note(&a, fabs(f.cosg), P->tol.cosg, AMB_GRAZE);
     const material *m = &s->mats[f.mat];
     if (m->kind == MAT_EMISSIVE) {
       int count = spec_only || ((P->flags & FLAG_EMITTER_AFTER_DS) && diffuse_first && n_diffuse == 1 &&
@@ -759,21 +870,22 @@ static void camera_path(const scene *s, const cam_params *P, const double *wts, 
     if (m->kind == MAT_DIELECTRIC) {
       int refl, fix;
       double n_l = cauchy(m->A, m->B, bin, P->nbins);
-      v3 d = dielectric(&f, r.d, n_l, u01(xs[0]), P->flags, &refl, &fix, &amb, tol);
+      v3 d = dielectric(&f, r.d, n_l, u01(xs[0]), P->flags, &refl, &fix, &a);
       sig = fnv(sig, refl ? EV_REFLECT : EV_REFRACT);
       if (fix) sig = fnv(sig, EV_FIXUP);
-      ++nspec;
+      ++a.nspec;
       last_specular = 1;
       r.o = offset_along(f.p, f.ng, d);
       r.d = d;
+      nudge(&r, delta, P->seed ^ 0xA5A5A5A5ull, pix, (uint32_t)sample, k + 1);
       continue;
     }
     /* diffuse */
-    v3 alb = albedo_at(s, h.tri, &f, &amb, tol);
+    v3 alb = albedo_at(s, h.tri, &f, &a);
     uint32_t xn[4];
     draw(P->seed, pix, (uint32_t)sample, (uint32_t)(k + 1), 2, (uint32_t)P->scene_index, xn);
     int lit;
-    v3 e = nee(s, &f, alb, xn, P->brute, &lit, &amb, tol);
+    v3 e = nee(s, &f, alb, xn, P->brute, &lit, &a);
     sig = fnv(sig, lit ? EV_LIT : EV_UNLIT);
     L = add(L, hadamard(beta, e));
     if (k == 0) diffuse_first = 1;
@@ -783,7 +895,7 @@ static void camera_path(const scene *s, const cam_params *P, const double *wts, 
     if (k == P->max_depth - 1) break;
     v3 d = cosine_dir(f.nsf, u01(xs[1]), u01(xs[2]));
     double side = dot(d, f.ngf);
-    if (fabs(side) < tol->cosg) amb |= AMB_FIXUP;
+    note(&a, fabs(side), P->tol.cosg, AMB_FIXUP);
     if (!(side > 0)) {
       d = cosine_dir(f.ngf, u01(xs[1]), u01(xs[2]));
       sig = fnv(sig, EV_FIXUP);
@@ -791,30 +903,47 @@ static void camera_path(const scene *s, const cam_params *P, const double *wts, 
     beta = hadamard(beta, alb);
     r.o = add(f.p, mul(f.ngf, eps_of(f.p)));
     r.d = d;
+    nudge(&r, delta, P->seed ^ 0xA5A5A5A5ull, pix, (uint32_t)sample, k + 1);
   }
   v3 w = V(wts[3 * bin], wts[3 * bin + 1], wts[3 * bin + 2]);
   L = hadamard(L, w);
   rec->L[0] = L.x; rec->L[1] = L.y; rec->L[2] = L.z;
   rec->n_queries = q;
   rec->signature = sig;
-  rec->amb = amb;
+  rec->amb = a.amb;
   rec->bin = bin;
-  rec->n_specular = nspec;
+  rec->n_specular = a.nspec;
+  rec->min_ratio = a.min_ratio;
+  rec->ratio_nspec = a.ratio_nspec;
+  rec->ratio_kind = a.ratio_kind;
+  for (int i = 0; i < 9; ++i) { rec->kmin[i] = a.kmin[i]; rec->knspec[i] = a.knspec[i]; }
+}
+
+static void camera_path(const scene *s, const cam_params *P, const double *wts, int px, int py, int sample,
+                        path_rec *rec) {
+  camera_path_impl(s, P, wts, px, py, sample, 0.0, rec);
+  if (P->tol.sens_delta > 0) {
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      path_rec alt;
+      camera_path_impl(s, P, wts, px, py, sample, sgn * P->tol.sens_delta, &alt);
+      if (alt.signature != rec->signature || sensitive3(alt.L, rec->L, P->tol.sens_rel)) rec->amb |= AMB_SENSITIVE;
+    }
+  }
 }
 
 /* ------------------------------------------------------------------------------------------ */
 /* light path (caustics)                                                                       */
 /* ------------------------------------------------------------------------------------------ */
-static void light_path(const scene *s, const light_params *P, const double *wts, int64_t idx, double *accum,
-                       light_rec *rec) {
-  const tolerances *tol = &P->tol;
+static void light_path_impl(const scene *s, const light_params *P, const double *wts, int64_t idx, double delta,
+                            double *accum, light_rec *rec) {
+  actx a;
+  actx_init(&a, &P->tol);
   uint32_t lo = (uint32_t)idx, hi = (uint32_t)((uint64_t)idx >> 32);
   uint32_t xe[4], xd[4];
   draw(P->seed, lo, hi, 0, 4, (uint32_t)P->scene_index, xe);
   draw(P->seed, lo, hi, 0, 3, (uint32_t)P->scene_index, xd);
   int bin = choose(xe[3], P->nbins > 0 ? P->nbins : 1);
   uint32_t sig = 2166136261u;
-  int amb = 0, nspec = 0;
   rec->pixel = -1;
   rec->C[0] = rec->C[1] = rec->C[2] = 0;
   rec->x[0] = rec->x[1] = rec->x[2] = NAN;
@@ -848,13 +977,13 @@ static void light_path(const scene *s, const light_params *P, const double *wts,
       beta = mul(L->power, PI * L->radius * L->radius * s->nlights);
     }
     int had_spec = 0;
+    nudge(&r, delta, P->seed ^ 0x5A5A5A5Aull, lo, hi, 0);
     for (int k = 0; k < P->max_depth; ++k) {
-      hit h = closest(s, r, P->brute, tol);
-      amb |= h.amb;
+      hit h = closest_noted(s, r, P->brute, &a);
       sig = fnv(sig, h.tri < 0 ? EV_MISS : (uint32_t)h.tri);
       if (h.tri < 0) break;
       surf f = interact(s, r, h);
-      if (fabs(f.cosg) < tol->cosg) amb |= AMB_GRAZE;
+      note(&a, fabs(f.cosg), P->tol.cosg, AMB_GRAZE);
       const material *m = &s->mats[f.mat];
       if (m->kind == MAT_EMISSIVE) break;
       if (m->kind == MAT_DIELECTRIC) {
@@ -862,24 +991,26 @@ static void light_path(const scene *s, const light_params *P, const double *wts,
         draw(P->seed, lo, hi, (uint32_t)(k + 1), 3, (uint32_t)P->scene_index, xs);
         int refl, fix;
         double n_l = cauchy(m->A, m->B, bin, P->nbins);
-        v3 d = dielectric(&f, r.d, n_l, u01(xs[0]), P->flags, &refl, &fix, &amb, tol);
+        v3 d = dielectric(&f, r.d, n_l, u01(xs[0]), P->flags, &refl, &fix, &a);
         sig = fnv(sig, refl ? EV_REFLECT : EV_REFRACT);
         if (fix) sig = fnv(sig, EV_FIXUP);
-        ++nspec;
+        ++a.nspec;
         had_spec = 1;
         r.o = offset_along(f.p, f.ng, d);
         r.d = d;
+        nudge(&r, delta, P->seed ^ 0x5A5A5A5Aull, lo, hi, k + 1);
         continue;
       }
       /* diffuse receiver */
       if (!had_spec && !(P->flags & FLAG_SPLAT_DIRECT)) break;
       rec->x[0] = f.p.x; rec->x[1] = f.p.y; rec->x[2] = f.p.z;
-      v3 alb = albedo_at(s, h.tri, &f, &amb, tol);
+      v3 alb = albedo_at(s, h.tri, &f, &a);
       v3 wc = sub(s->eye, f.p);
       double dc = len(wc);
       wc = mul(wc, 1.0 / dc);
       double cs = dot(f.nsf, wc), cg = dot(f.ngf, wc);
-      if (fabs(cg) < tol->cosg || fabs(cs) < tol->cosg) amb |= AMB_GRAZE;
+      note(&a, fabs(cg), P->tol.cosg, 4);
+      note(&a, fabs(cs), P->tol.cosg, 4);
       if (!(cs > 0 && cg > 0)) { sig = fnv(sig, EV_UNLIT); break; }
       v3 wv = mul(wc, -1.0);
       double cc = dot(wv, s->f);
@@ -887,7 +1018,7 @@ static void light_path(const scene *s, const light_params *P, const double *wts,
       double sx = (dot(wv, s->r) / cc / (s->th * s->aspect) + 1.0) * 0.5;
       double sy = (1.0 - dot(wv, s->u) / cc / s->th) * 0.5;
       double fx = sx * s->W, fy = sy * s->H;
-      if (fabs(fx - floor(fx + 0.5)) < tol->px || fabs(fy - floor(fy + 0.5)) < tol->px) amb |= AMB_SPLAT;
+      note(&a, fmin(fabs(fx - floor(fx + 0.5)), fabs(fy - floor(fy + 0.5))), P->tol.px, AMB_SPLAT);
       if (!(sx >= 0 && sx < 1 && sy >= 0 && sy < 1)) { sig = fnv(sig, EV_UNLIT); break; }
       int ix = (int)floor(fx), iy = (int)floor(fy);
       if (ix >= s->W) ix = s->W - 1;
@@ -897,9 +1028,7 @@ static void light_path(const scene *s, const light_params *P, const double *wts,
       v3 w = sub(s->eye, sr.o);
       double dist = len(w);
       sr.d = mul(w, 1.0 / dist);
-      int a = 0;
-      int occ = occluded(s, sr, dist * (1.0 - 1e-4), P->brute, &a, tol);
-      if (a) amb |= AMB_SHADOW;
+      int occ = occluded_noted(s, sr, dist * (1.0 - 1e-4), P->brute, &a);
       if (occ) { sig = fnv(sig, EV_UNLIT); break; }
       sig = fnv(sig, EV_LIT);
       double apix = (2.0 * s->th * s->aspect / s->W) * (2.0 * s->th / s->H);
@@ -916,9 +1045,26 @@ static void light_path(const scene *s, const light_params *P, const double *wts,
     }
   }
 done:
-  rec->amb = amb;
+  rec->amb = a.amb;
   rec->signature = sig;
-  rec->n_specular = nspec;
+  rec->n_specular = a.nspec;
+  rec->min_ratio = a.min_ratio;
+  rec->ratio_nspec = a.ratio_nspec;
+  rec->ratio_kind = a.ratio_kind;
+  for (int i = 0; i < 9; ++i) { rec->kmin[i] = a.kmin[i]; rec->knspec[i] = a.knspec[i]; }
+}
+
+static void light_path(const scene *s, const light_params *P, const double *wts, int64_t idx, double *accum,
+                       light_rec *rec) {
+  light_path_impl(s, P, wts, idx, 0.0, accum, rec);
+  if (P->tol.sens_delta > 0) {
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      light_rec alt;
+      light_path_impl(s, P, wts, idx, sgn * P->tol.sens_delta, NULL, &alt);
+      if (alt.signature != rec->signature || alt.pixel != rec->pixel || sensitive3(alt.C, rec->C, P->tol.sens_rel))
+        rec->amb |= AMB_SENSITIVE;
+    }
+  }
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -1069,14 +1215,16 @@ ORC_API void orc_resolve(void *sp, const resolve_params *P, const double *acc_ca
         o->caustic[c] = (acc_caus && P->light_paths_total > 0) ? acc_caus[3 * i + c] / P->light_paths_total : 0.0;
         o->rgb[c] = o->direct[c] + o->caustic[c];
       }
+      actx a;
+      actx_init(&a, &DEFAULT_TOL);
       ray r = camera_ray(s, (px + 0.5) / s->W, (py + 0.5) / s->H);
-      hit h = closest(s, r, P->brute, &DEFAULT_TOL);
-      o->amb = h.amb;
+      hit h = closest_noted(s, r, P->brute, &a);
       if (h.tri < 0) {
-        o->instance = -1; o->tri = -1; o->depth = INFINITY; o->depth_norm = 1.0;
+        o->instance = -1; o->tri = -1; o->depth = INFINITY; o->depth_norm = 1.0; o->amb = a.amb;
         continue;
       }
       surf f = interact(s, r, h);
+      note(&a, fabs(f.cosg), DEFAULT_TOL.cosg, 4);
       const material *m = &s->mats[f.mat];
       o->instance = s->obj[h.tri];
       o->tri = h.tri;
@@ -1086,9 +1234,8 @@ ORC_API void orc_resolve(void *sp, const resolve_params *P, const double *acc_ca
       v3 n = f.nsf;
       o->n_world[0] = n.x; o->n_world[1] = n.y; o->n_world[2] = n.z;
       o->n_cam[0] = dot(n, s->r); o->n_cam[1] = dot(n, s->u); o->n_cam[2] = -dot(n, s->f);
-      int amb = 0;
-      v3 alb = m->kind == MAT_DIFFUSE ? albedo_at(s, h.tri, &f, &amb, &DEFAULT_TOL) : V(1, 1, 1);
-      o->amb |= amb;
+      v3 alb = m->kind == MAT_DIFFUSE ? albedo_at(s, h.tri, &f, &a) : V(1, 1, 1);
+      o->amb = a.amb;
       o->albedo[0] = alb.x; o->albedo[1] = alb.y; o->albedo[2] = alb.z;
       double yc = luminance(o->caustic), yd = luminance(o->direct);
       o->caustic_mask = (m->kind != MAT_DIELECTRIC) && (yc > P->tau_rel * fmax(yd, 1e-3));

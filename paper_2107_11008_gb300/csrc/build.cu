@@ -1,0 +1,381 @@
+// build.cu -- LBVH construction on sm_103a.
+//
+// Steps (one kernel each, all on the caller's stream):
+//   1. gather: triangles from the indexed arrays into float4 vertex triples, shading
+//      attributes, centroids, and the centroid bounds (block reduce + sortable-int atomics).
+//   2. morton: 30-bit Morton code of each centroid in the normalised bounds (10 bits/axis).
+//   3. radix sort of (code, index), least-significant digit first, 4 passes of 8 bits; each
+//      pass is histogram -> exclusive scan -> stable scatter (the tile is ranked by 8 one-bit
+//      stable splits in shared memory), so equal codes keep input order.
+//   4. reorder: triangles into leaf order.
+//   5. hierarchy: Karras (HPG 2012) -- internal node i covers a key range found from the
+//      longest-common-prefix function delta(i, j) (ties broken by index).
+//   6. refit: each leaf climbs to the root; the second arrival at a node merges both boxes
+//      (ordering through __threadfence + an atomic counter per node).
+#include <cfloat>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace sc {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kTile = kSortThreads * kSortItems;
+
+size_t sort_blocks(int32_t n) { return (size_t)((n + kTile - 1) / kTile); }
+
+// order-preserving float <-> uint32 map for atomic min/max
+__device__ __forceinline__ uint32_t f2key(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+__global__ void k_init_bounds(uint32_t *bounds, int32_t *depth) {
+  const int i = threadIdx.x;
+  if (i < 3) bounds[i] = 0xFFFFFFFFu;
+  else if (i < 6) bounds[i] = 0u;
+  if (i == 0) *depth = 0;
+}
+
+__global__ void k_gather(BuildBuffers b) {
+  __shared__ float red[6][32];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+  if (t < b.n_tris) {
+    const int i0 = b.indices[3 * t], i1 = b.indices[3 * t + 1], i2 = b.indices[3 * t + 2];
+    const int vi[3] = {i0, i1, i2};
+    float3 c = f3(0.f, 0.f, 0.f);
+    for (int j = 0; j < 3; ++j) {
+      const float3 p = f3(b.positions + 3 * vi[j]);
+      b.tris_in[3 * t + j] = make_float4(p.x, p.y, p.z, j == 0 ? __int_as_float(t) : 0.0f);
+      c = c + p;
+      const float3 n = b.normals ? f3(b.normals + 3 * vi[j]) : f3(0.f, 0.f, 0.f);
+      const float ux = b.uvs ? b.uvs[2 * vi[j]] : 0.0f;
+      b.shade[3 * t + j] = make_float4(n.x, n.y, n.z, ux);
+    }
+    const int obj = b.tri_object[t];
+    const int mat = (obj >= 0 && obj < b.n_objects) ? b.object_material[obj] : 0;
+    b.shade2[t] = make_float4(b.uvs ? b.uvs[2 * i0 + 1] : 0.0f, b.uvs ? b.uvs[2 * i1 + 1] : 0.0f,
+                              b.uvs ? b.uvs[2 * i2 + 1] : 0.0f, __int_as_float(mat));
+    b.tri_obj[t] = obj;
+    c = c * (1.0f / 3.0f);
+    b.centroids[t] = make_float4(c.x, c.y, c.z, 0.0f);
+    lo[0] = hi[0] = c.x;
+    lo[1] = hi[1] = c.y;
+    lo[2] = hi[2] = c.z;
+  }
+  // warp then block reduction of the centroid bounds
+  for (int k = 0; k < 3; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xFFFFFFFFu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xFFFFFFFFu, hi[k], o));
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0)
+    for (int k = 0; k < 3; ++k) {
+      red[k][warp] = lo[k];
+      red[3 + k][warp] = hi[k];
+    }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int k = threadIdx.x;
+    float v = red[k][0];
+    for (int w = 1; w < nw; ++w) v = k < 3 ? fminf(v, red[k][w]) : fmaxf(v, red[k][w]);
+    if (v != FLT_MAX && v != -FLT_MAX) {
+      if (k < 3) atomicMin(&b.bounds[k], f2key(v));
+      else atomicMax(&b.bounds[k], f2key(v));
+    }
+  }
+}
+
+// spread the low 10 bits of v to every third bit
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  v = (v * 0x00010001u) & 0xFF0000FFu;
+  v = (v * 0x00000101u) & 0x0F00F00Fu;
+  v = (v * 0x00000011u) & 0xC30C30C3u;
+  v = (v * 0x00000005u) & 0x49249249u;
+  return v;
+}
+
+__global__ void k_morton(BuildBuffers b) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b.n_tris) return;
+  const float3 lo = f3(key2f(b.bounds[0]), key2f(b.bounds[1]), key2f(b.bounds[2]));
+  const float3 hi = f3(key2f(b.bounds[3]), key2f(b.bounds[4]), key2f(b.bounds[5]));
+  const float4 c = b.centroids[t];
+  const float cc[3] = {c.x, c.y, c.z}, l[3] = {lo.x, lo.y, lo.z}, h[3] = {hi.x, hi.y, hi.z};
+  uint32_t q[3];
+  for (int k = 0; k < 3; ++k) {
+    const float ext = h[k] - l[k];
+    const float u = ext > 0.0f ? (cc[k] - l[k]) / ext : 0.5f;
+    q[k] = (uint32_t)fminf(fmaxf(u * 1024.0f, 0.0f), 1023.0f);
+  }
+  b.keys[t] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+  b.vals[t] = (uint32_t)t;
+}
+
+__global__ void k_sort_hist(const uint32_t *keys, int32_t n, int shift, uint32_t *hist, int nblocks) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * kTile;
+  for (int j = 0; j < kSortItems; ++j) {
+    const int i = base + j * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of a 256-thread block; returns the prefix, *total gets the sum
+__device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t *warp_sums, uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t s = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0u;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < (int)(blockDim.x >> 5)) warp_sums[lane] = s;  // inclusive
+  }
+  __syncthreads();
+  const uint32_t before = warp == 0 ? 0u : warp_sums[warp - 1];
+  *total = warp_sums[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+// single-block exclusive scan over n words (digit-major histogram)
+__global__ void k_scan(uint32_t *data, int n) {
+  __shared__ uint32_t ws[32];
+  uint32_t carry = 0;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const uint32_t v = i < n ? data[i] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_scan(v, ws, &total);
+    if (i < n) data[i] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void k_sort_scatter(const uint32_t *keys, const uint32_t *vals, uint32_t *keys_out, uint32_t *vals_out,
+                               int32_t n, int shift, const uint32_t *hist, int nblocks) {
+  __shared__ uint32_t sk[2][kTile];
+  __shared__ uint32_t sv[2][kTile];
+  __shared__ uint32_t ws[32];
+  __shared__ uint32_t start[256];
+  __shared__ uint32_t cnt[256];
+  const int base = blockIdx.x * kTile;
+  const int count = min(kTile, n - base);
+  // load; padding items get digit 0xFF so that they sort last and are never written
+  for (int j = 0; j < kSortItems; ++j) {
+    const int l = j * kSortThreads + threadIdx.x;
+    const int i = base + l;
+    sk[0][l] = i < n ? keys[i] : 0xFFFFFFFFu;
+    sv[0][l] = i < n ? vals[i] : 0xFFFFFFFFu;
+  }
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  int cur = 0;
+  // 8 stable one-bit splits on the digit; thread t owns items 8t .. 8t+7 (in tile order)
+  for (int bit = 0; bit < 8; ++bit) {
+    uint32_t zeros = 0;
+    uint32_t k[kSortItems], v[kSortItems];
+    for (int j = 0; j < kSortItems; ++j) {
+      k[j] = sk[cur][threadIdx.x * kSortItems + j];
+      v[j] = sv[cur][threadIdx.x * kSortItems + j];
+      zeros += ((k[j] >> (shift + bit)) & 1u) ? 0u : 1u;
+    }
+    uint32_t total_zeros;
+    const uint32_t zpre = block_scan(zeros, ws, &total_zeros);
+    uint32_t z = zpre, o = total_zeros + threadIdx.x * kSortItems - zpre;
+    for (int j = 0; j < kSortItems; ++j) {
+      const bool one = (k[j] >> (shift + bit)) & 1u;
+      const uint32_t dst = one ? o++ : z++;
+      sk[cur ^ 1][dst] = k[j];
+      sv[cur ^ 1][dst] = v[j];
+    }
+    cur ^= 1;
+    __syncthreads();
+  }
+  // local digit starts
+  for (int j = 0; j < kSortItems; ++j) {
+    const int l = threadIdx.x * kSortItems + j;
+    if (l < count) atomicAdd(&cnt[(sk[cur][l] >> shift) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  uint32_t tot;
+  const uint32_t ex = block_scan(cnt[threadIdx.x], ws, &tot);
+  start[threadIdx.x] = ex;
+  __syncthreads();
+  for (int j = 0; j < kSortItems; ++j) {
+    const int l = j * kSortThreads + threadIdx.x;
+    if (l < count) {
+      const uint32_t key = sk[cur][l];
+      const uint32_t d = (key >> shift) & 0xFFu;
+      const uint32_t pos = hist[d * nblocks + blockIdx.x] + (uint32_t)l - start[d];
+      keys_out[pos] = key;
+      vals_out[pos] = sv[cur][l];
+    }
+  }
+}
+
+__global__ void k_reorder(BuildBuffers b, const uint32_t *order) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.n_tris) return;
+  const uint32_t t = order[k];
+  b.tris[3 * k] = b.tris_in[3 * t];
+  b.tris[3 * k + 1] = b.tris_in[3 * t + 1];
+  b.tris[3 * k + 2] = b.tris_in[3 * t + 2];
+}
+
+// longest common prefix of sorted keys i and j (index bits break ties), -1 outside
+__device__ __forceinline__ int delta(const uint32_t *keys, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  const uint32_t a = keys[i], b = keys[j];
+  if (a == b) return 32 + __clz((uint32_t)i ^ (uint32_t)j);
+  return __clz(a ^ b);
+}
+
+__global__ void k_karras(BuildBuffers b, const uint32_t *keys) {
+  const int n = b.n_tris;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  const int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+  const int dmin = delta(keys, n, i, i - d);
+  int lmax = 2;
+  while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+  const int j = i + l * d;
+  const int dnode = delta(keys, n, i, j);
+  int s = 0;
+  for (int div = 2;; div <<= 1) {
+    const int t = (l + div - 1) / div;
+    if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    if (t <= 1) break;
+  }
+  const int gamma = i + s * d + min(d, 0);
+  const int lo = min(i, j), hi = max(i, j);
+  const int left = (lo == gamma) ? ~gamma : gamma;
+  const int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+  b.nodes[4 * i + 3] = make_float4(__int_as_float(left), __int_as_float(right), 0.0f, 0.0f);
+  // parents: internal nodes at [0, n-1), leaves at [n-1, 2n-1)
+  const int pl = left < 0 ? (n - 1) + ~left : left;
+  const int pr = right < 0 ? (n - 1) + ~right : right;
+  b.parents[pl] = (i << 1) | 0;
+  b.parents[pr] = (i << 1) | 1;
+  b.flags[i] = 0;
+}
+
+__device__ __forceinline__ void store_box(float4 *nodes, int parent, int slot, float3 lo, float3 hi) {
+  float4 *nd = nodes + 4 * parent;
+  if (slot == 0) {
+    nd[0] = make_float4(lo.x, hi.x, lo.y, hi.y);
+    reinterpret_cast<float2 *>(&nd[2])[0] = make_float2(lo.z, hi.z);
+  } else {
+    nd[1] = make_float4(lo.x, hi.x, lo.y, hi.y);
+    reinterpret_cast<float2 *>(&nd[2])[1] = make_float2(lo.z, hi.z);
+  }
+}
+
+__global__ void k_refit(BuildBuffers b) {
+  const int n = b.n_tris;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float3 v0 = xyz(b.tris[3 * k]), v1 = xyz(b.tris[3 * k + 1]), v2 = xyz(b.tris[3 * k + 2]);
+  float3 lo = f3(fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z)));
+  float3 hi = f3(fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z)));
+  if (n == 1) {
+    // a single triangle: a root whose two slots both hold that leaf (a slab test cannot
+    // reject an inverted box, so no empty slot is used)
+    store_box(b.nodes, 0, 0, lo, hi);
+    store_box(b.nodes, 0, 1, lo, hi);
+    b.nodes[3] = make_float4(__int_as_float(~0), __int_as_float(~0), 0.0f, 0.0f);
+    return;
+  }
+  int link = b.parents[(n - 1) + k];
+  int depth = 1;
+  for (;;) {
+    const int parent = link >> 1, slot = link & 1;
+    store_box(b.nodes, parent, slot, lo, hi);
+    __threadfence();
+    if (atomicAdd(&b.flags[parent], 1) == 0) return;  // the sibling finishes this node
+    __threadfence();
+    const float4 a = __ldcg(&b.nodes[4 * parent]), c = __ldcg(&b.nodes[4 * parent + 1]);
+    const float4 z = __ldcg(&b.nodes[4 * parent + 2]);
+    lo = f3(fminf(a.x, c.x), fminf(a.z, c.z), fminf(z.x, z.z));
+    hi = f3(fmaxf(a.y, c.y), fmaxf(a.w, c.w), fmaxf(z.y, z.w));
+    if (parent == 0) break;
+    link = b.parents[parent];
+    ++depth;
+  }
+}
+
+// depth of every leaf (walk to the root); keeps the maximum
+__global__ void k_depth(BuildBuffers b) {
+  const int n = b.n_tris;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n || n < 2) return;
+  int node = (n - 1) + k, d = 0;
+  while (true) {
+    const int p = b.parents[node] >> 1;
+    ++d;
+    if (p == 0) break;
+    node = p;
+    if (d > 4 * 64) break;
+  }
+  atomicMax(b.depth, d);
+}
+
+#define SC_TRY(x)                              \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) return e_;          \
+  } while (0)
+
+cudaError_t launch_build(const BuildBuffers &b, cudaStream_t s) {
+  const int n = b.n_tris;
+  if (n <= 0) return cudaSuccess;
+  const int T = 256, G = (n + T - 1) / T;
+  k_init_bounds<<<1, 32, 0, s>>>(b.bounds, b.depth);
+  k_gather<<<G, T, 0, s>>>(b);
+  k_morton<<<G, T, 0, s>>>(b);
+  SC_TRY(cudaGetLastError());
+  const int nb = (int)sort_blocks(n);
+  uint32_t *ka = b.keys, *kb = b.keys_alt, *va = b.vals, *vb = b.vals_alt;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 8 * pass;
+    k_sort_hist<<<nb, kSortThreads, 0, s>>>(ka, n, shift, b.hist, nb);
+    k_scan<<<1, 1024, 0, s>>>(b.hist, 256 * nb);
+    k_sort_scatter<<<nb, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, b.hist, nb);
+    uint32_t *t = ka; ka = kb; kb = t;
+    t = va; va = vb; vb = t;
+  }
+  SC_TRY(cudaGetLastError());
+  // after an even number of passes the sorted data is back in keys / vals
+  k_reorder<<<G, T, 0, s>>>(b, va);
+  if (n > 1) {
+    const int Gi = (n - 1 + T - 1) / T;
+    k_karras<<<Gi, T, 0, s>>>(b, ka);
+  }
+  k_refit<<<G, T, 0, s>>>(b);
+  k_depth<<<G, T, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+}  // namespace sc

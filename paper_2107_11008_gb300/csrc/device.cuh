@@ -1,0 +1,506 @@
+// device.cuh -- device-side building blocks of the sm_103a path/light tracer.
+//
+// Layout in HBM (all 16-byte aligned):
+//   nodes   float4[4 * n_nodes]  binary BVH node = both child boxes + child refs (64 B):
+//           (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y) (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//           (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z) (child0, child1 as int bits, -, -)
+//           a child >= 0 is an internal node, < 0 is leaf ~k (one triangle, leaf order k).
+//   tris    float4[3 * n_tris]   vertices in leaf order; tris[3k].w = input triangle id bits.
+//   shade   float4[3 * n_tris]   per input triangle: (normal_j.xyz, uv_j.x) for j = 0..2.
+//   shade2  float4[n_tris]       (uv0.y, uv1.y, uv2.y, material id bits).
+//   tri_obj int32[n_tris]        object id per input triangle.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "supercaustics.h"
+
+namespace sc {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr int kStack = 64;
+constexpr uint32_t kMiss = 0xFFFFFFFFu;
+constexpr int kMaxBins = 64;
+// traversal watchdog: node visits per query before the query is abandoned
+constexpr int kMaxVisits = 1 << 22;
+
+enum : uint32_t { EV_REFLECT = 1, EV_REFRACT = 2, EV_LIT = 3, EV_UNLIT = 4, EV_FIXUP = 7 };
+
+// ------------------------------------------------------------------------------------------
+// float3 algebra
+// ------------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__host__ __device__ __forceinline__ float3 f3(const float *p) { return make_float3(p[0], p[1], p[2]); }
+__device__ __forceinline__ float3 xyz(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 operator*(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float length(float3 a) { return sqrtf(dot(a, a)); }
+__device__ __forceinline__ float3 normalize(float3 a) { return a * (1.0f / sqrtf(dot(a, a))); }
+__device__ __forceinline__ float maxabs(float3 a) { return fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))); }
+__device__ __forceinline__ float comp(float3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64 multiplies
+// with Weyl key bumps.  Counter word 3 carries tag | scene << 8.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t tag,
+                                      uint32_t scene) {
+  return philox(make_uint4(c0, c1, c2, tag | (scene << 8)), (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+// 24-bit uniform in [0,1), exact in FP32
+__device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+// floor(u * n) in exact integer arithmetic
+__device__ __forceinline__ int choose(uint32_t x, int n) {
+  return (int)(((uint64_t)(x >> 8) * (uint64_t)n) >> 24);
+}
+__device__ __forceinline__ uint32_t fnv(uint32_t h, uint32_t w) { return (h ^ w) * 16777619u; }
+
+// ------------------------------------------------------------------------------------------
+// Spectrum: bin centres over 400-700 nm; RGB weight = linear sRGB of the multi-lobe CIE 1931
+// fit (Wyman, Sloan, Shirley, JCGT 2013), normalised to mean 1 per channel over the bins.
+// ------------------------------------------------------------------------------------------
+// The table is tiny (one entry per bin, built once per block), so it is evaluated in FP64: the
+// XYZ -> RGB rows cancel strongly for some bins and FP32 would leave ~1e-4 relative error there.
+__device__ __forceinline__ double lobe(double lam, double mu, double s1, double s2) {
+  const double t = (lam - mu) / (lam < mu ? s1 : s2);
+  return exp(-0.5 * t * t);
+}
+__device__ __forceinline__ void bin_rgb(int b, int nbins, double out[3]) {
+  const double lam = 400.0 + (b + 0.5) * 300.0 / nbins;
+  const double X = 1.056 * lobe(lam, 599.8, 37.9, 31.0) + 0.362 * lobe(lam, 442.0, 16.0, 26.7) -
+                   0.065 * lobe(lam, 501.1, 20.4, 26.2);
+  const double Y = 0.821 * lobe(lam, 568.8, 46.9, 40.5) + 0.286 * lobe(lam, 530.9, 16.3, 31.1);
+  const double Z = 1.217 * lobe(lam, 437.0, 11.8, 36.0) + 0.681 * lobe(lam, 459.0, 26.0, 13.8);
+  out[0] = 3.2404542 * X - 1.5371385 * Y - 0.4985314 * Z;
+  out[1] = -0.9692660 * X + 1.8760108 * Y + 0.0415560 * Z;
+  out[2] = 0.0556434 * X - 0.2040259 * Y + 1.0572252 * Z;
+}
+// Fills w[0..nbins) (shared memory); call from every thread of the block.
+__device__ __forceinline__ void spectral_table(float3 *w, int nbins) {
+  if (nbins <= 1) {
+    if (threadIdx.x == 0) w[0] = f3(1.f, 1.f, 1.f);
+    __syncthreads();
+    return;
+  }
+  if (threadIdx.x == 0) {
+    double mean[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < nbins; ++b) {
+      double c[3];
+      bin_rgb(b, nbins, c);
+      for (int k = 0; k < 3; ++k) mean[k] += c[k] / nbins;
+    }
+    for (int b = 0; b < nbins; ++b) {
+      double c[3];
+      bin_rgb(b, nbins, c);
+      w[b] = f3((float)(c[0] / mean[0]), (float)(c[1] / mean[1]), (float)(c[2] / mean[2]));
+    }
+  }
+  __syncthreads();
+}
+__device__ __forceinline__ float cauchy(float A, float B, int bin, int nbins) {
+  if (nbins <= 1) return A;
+  const float lum = (400.0f + (bin + 0.5f) * 300.0f / nbins) * 1e-3f;
+  return A + B / (lum * lum);
+}
+
+// ------------------------------------------------------------------------------------------
+// Scene as seen by kernels
+// ------------------------------------------------------------------------------------------
+struct Cam {
+  float3 eye, f, r, u;
+  float th, aspect;
+  int W, H;
+};
+__device__ __forceinline__ Cam make_cam(const sc_camera &c) {
+  Cam k;
+  k.eye = f3(c.eye);
+  k.f = normalize(f3(c.look) - k.eye);
+  k.r = normalize(cross(k.f, f3(c.up)));
+  k.u = cross(k.r, k.f);
+  k.th = tanf(0.5f * c.vfov_deg * (kPi / 180.0f));
+  k.W = c.width;
+  k.H = c.height;
+  k.aspect = (float)c.width / (float)c.height;
+  return k;
+}
+__device__ __forceinline__ float3 cam_dir(const Cam &c, float sx, float sy) {
+  return normalize(c.r * ((2.0f * sx - 1.0f) * c.th * c.aspect) + c.u * ((1.0f - 2.0f * sy) * c.th) + c.f);
+}
+
+struct DevScene {
+  const float4 *nodes;
+  const float4 *tris;
+  const float4 *shade;
+  const float4 *shade2;
+  const int32_t *tri_obj;
+  const sc_material *mats;
+  const sc_light *lights;
+  int32_t n_tris, n_nodes, n_mats, n_lights;
+  float env[3];
+  sc_camera cam;
+};
+
+// ------------------------------------------------------------------------------------------
+// Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2013), both faces, FP32 with an
+// FP64 recomputation of an edge function that evaluates to exactly zero.
+// ------------------------------------------------------------------------------------------
+struct WRay {
+  float3 o, d, inv;
+  int kx, ky, kz;
+  float Sx, Sy, Sz;
+};
+__device__ __forceinline__ WRay make_wray(float3 o, float3 d) {
+  WRay w;
+  w.o = o;
+  w.d = d;
+  // a zero component gets a huge finite reciprocal: with 1/0 = inf, a ray lying in a box face
+  // plane would give (l - o) * inf = NaN and the slab test would wrongly reject the box
+  w.inv = f3(d.x != 0.0f ? 1.0f / d.x : copysignf(1e30f, d.x), d.y != 0.0f ? 1.0f / d.y : copysignf(1e30f, d.y),
+             d.z != 0.0f ? 1.0f / d.z : copysignf(1e30f, d.z));
+  const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+  w.kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+  w.kx = w.kz == 2 ? 0 : w.kz + 1;
+  w.ky = w.kx == 2 ? 0 : w.kx + 1;
+  if (comp(d, w.kz) < 0.0f) {
+    const int t = w.kx;
+    w.kx = w.ky;
+    w.ky = t;
+  }
+  const float dz = comp(d, w.kz);
+  w.Sx = comp(d, w.kx) / dz;
+  w.Sy = comp(d, w.ky) / dz;
+  w.Sz = 1.0f / dz;
+  return w;
+}
+
+// Returns true and (t, b1, b2) if the ray meets the triangle at 0 < t.
+__device__ __forceinline__ bool tri_test(const WRay &w, float3 v0, float3 v1, float3 v2, float &t, float &b1,
+                                         float &b2) {
+  const float3 A = v0 - w.o, B = v1 - w.o, C = v2 - w.o;
+  const float Akz = comp(A, w.kz), Bkz = comp(B, w.kz), Ckz = comp(C, w.kz);
+  const float Ax = comp(A, w.kx) - w.Sx * Akz, Ay = comp(A, w.ky) - w.Sy * Akz;
+  const float Bx = comp(B, w.kx) - w.Sx * Bkz, By = comp(B, w.ky) - w.Sy * Bkz;
+  const float Cx = comp(C, w.kx) - w.Sx * Ckz, Cy = comp(C, w.ky) - w.Sy * Ckz;
+  // edge functions without contraction so that a shared edge evaluates to exact negatives
+  float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  if (U == 0.0f || V == 0.0f || W == 0.0f) {
+    U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+    V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+    W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+  }
+  if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+  const float det = U + V + W;
+  if (det == 0.0f) return false;
+  const float T = U * (w.Sz * Akz) + V * (w.Sz * Bkz) + W * (w.Sz * Ckz);
+  t = T / det;
+  if (!(t > 0.0f)) return false;
+  b1 = V / det;
+  b2 = W / det;
+  return true;
+}
+
+// slab test of one box against [0, tmax]
+__device__ __forceinline__ bool box_test(const WRay &w, float lx, float hx, float ly, float hy, float lz, float hz,
+                                         float tmax, float &tnear) {
+  const float tx0 = (lx - w.o.x) * w.inv.x, tx1 = (hx - w.o.x) * w.inv.x;
+  const float ty0 = (ly - w.o.y) * w.inv.y, ty1 = (hy - w.o.y) * w.inv.y;
+  const float tz0 = (lz - w.o.z) * w.inv.z, tz1 = (hz - w.o.z) * w.inv.z;
+  const float t0 = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+  // Ize (2013): widen the far bound by 2*gamma(3) so rounding never culls a real hit
+  const float t1 = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax)) * 1.0000004f;
+  tnear = t0;
+  return t0 <= t1;
+}
+
+struct Hit {
+  float t, b1, b2;
+  int prim;     // leaf order, -1 = miss
+  uint32_t id;  // input triangle id
+};
+
+// Work done by traversal queries (node visits = internal nodes loaded, each with two box tests).
+struct TravCount {
+  unsigned nodes = 0, tris = 0, queries = 0;
+};
+
+// Closest hit (ties on equal t go to the lowest input id).  Sets status bits on overflow.
+static __device__ __noinline__ Hit closest_hit(const DevScene &S, float3 o, float3 d, float tmax, unsigned *status,
+                                               TravCount &tc) {
+  ++tc.queries;
+  Hit h;
+  h.t = tmax;
+  h.prim = -1;
+  h.id = kMiss;
+  h.b1 = h.b2 = 0.0f;
+  if (S.n_tris <= 0) return h;
+  const WRay w = make_wray(o, d);
+  int stack[kStack];
+  int sp = 0;
+  int node = 0;
+  int visits = 0;
+  for (;;) {
+    ++tc.nodes;
+    if (++visits > kMaxVisits) {
+      atomicOr(status, SC_STATUS_WATCHDOG);
+      h.prim = -1;
+      h.id = kMiss;
+      return h;
+    }
+    const float4 n0 = __ldg(&S.nodes[4 * node + 0]);
+    const float4 n1 = __ldg(&S.nodes[4 * node + 1]);
+    const float4 n2 = __ldg(&S.nodes[4 * node + 2]);
+    const float4 n3 = __ldg(&S.nodes[4 * node + 3]);
+    const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+    float ta, tb;
+    const float tcull = h.t;
+    bool ha = box_test(w, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull, ta);
+    bool hb = box_test(w, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull, tb);
+    // leaves are tested right away
+    if (ha && c0 < 0) {
+      const int k = ~c0;
+      const float4 a = __ldg(&S.tris[3 * k]), b = __ldg(&S.tris[3 * k + 1]), c = __ldg(&S.tris[3 * k + 2]);
+      float t, b1, b2;
+      ++tc.tris;
+      if (tri_test(w, xyz(a), xyz(b), xyz(c), t, b1, b2)) {
+        const uint32_t id = (uint32_t)__float_as_int(a.w);
+        if (t < h.t || (t == h.t && id < h.id)) {
+          h.t = t; h.b1 = b1; h.b2 = b2; h.prim = k; h.id = id;
+        }
+      }
+      ha = false;
+    }
+    if (hb && c1 < 0) {
+      const int k = ~c1;
+      const float4 a = __ldg(&S.tris[3 * k]), b = __ldg(&S.tris[3 * k + 1]), c = __ldg(&S.tris[3 * k + 2]);
+      float t, b1, b2;
+      ++tc.tris;
+      if (tri_test(w, xyz(a), xyz(b), xyz(c), t, b1, b2)) {
+        const uint32_t id = (uint32_t)__float_as_int(a.w);
+        if (t < h.t || (t == h.t && id < h.id)) {
+          h.t = t; h.b1 = b1; h.b2 = b2; h.prim = k; h.id = id;
+        }
+      }
+      hb = false;
+    }
+    if (ha && hb) {
+      const bool a_first = ta <= tb;
+      if (sp >= kStack) {
+        atomicOr(status, SC_STATUS_STACK_OVERFLOW);
+        h.prim = -1;
+        h.id = kMiss;
+        return h;
+      }
+      stack[sp++] = a_first ? c1 : c0;
+      node = a_first ? c0 : c1;
+    } else if (ha) {
+      node = c0;
+    } else if (hb) {
+      node = c1;
+    } else {
+      if (sp == 0) break;
+      node = stack[--sp];
+    }
+  }
+  if (h.prim < 0) h.t = tmax;
+  return h;
+}
+
+// Any hit with 0 < t < tmax.
+static __device__ __noinline__ bool any_hit(const DevScene &S, float3 o, float3 d, float tmax, unsigned *status,
+                                            TravCount &tc) {
+  ++tc.queries;
+  if (S.n_tris <= 0) return false;
+  const WRay w = make_wray(o, d);
+  int stack[kStack];
+  int sp = 0;
+  int node = 0;
+  int visits = 0;
+  for (;;) {
+    ++tc.nodes;
+    if (++visits > kMaxVisits) {
+      atomicOr(status, SC_STATUS_WATCHDOG);
+      return false;
+    }
+    const float4 n0 = __ldg(&S.nodes[4 * node + 0]);
+    const float4 n1 = __ldg(&S.nodes[4 * node + 1]);
+    const float4 n2 = __ldg(&S.nodes[4 * node + 2]);
+    const float4 n3 = __ldg(&S.nodes[4 * node + 3]);
+    const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+    float ta, tb;
+    bool ha = box_test(w, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmax, ta);
+    bool hb = box_test(w, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmax, tb);
+    if (ha && c0 < 0) {
+      const int k = ~c0;
+      float t, b1, b2;
+      ++tc.tris;
+      if (tri_test(w, xyz(__ldg(&S.tris[3 * k])), xyz(__ldg(&S.tris[3 * k + 1])), xyz(__ldg(&S.tris[3 * k + 2])), t,
+                   b1, b2) &&
+          t < tmax)
+        return true;
+      ha = false;
+    }
+    if (hb && c1 < 0) {
+      const int k = ~c1;
+      float t, b1, b2;
+      ++tc.tris;
+      if (tri_test(w, xyz(__ldg(&S.tris[3 * k])), xyz(__ldg(&S.tris[3 * k + 1])), xyz(__ldg(&S.tris[3 * k + 2])), t,
+                   b1, b2) &&
+          t < tmax)
+        return true;
+      hb = false;
+    }
+    if (ha && hb) {
+      if (sp >= kStack) {
+        atomicOr(status, SC_STATUS_STACK_OVERFLOW);
+        return false;
+      }
+      stack[sp++] = c1;
+      node = c0;
+    } else if (ha) {
+      node = c0;
+    } else if (hb) {
+      node = c1;
+    } else {
+      if (sp == 0) return false;
+      node = stack[--sp];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Surface interaction
+// ------------------------------------------------------------------------------------------
+struct Surf {
+  float3 p, ng, ns, ngf, nsf;
+  float cosg;
+  int mat;
+  uint32_t id;
+  float b1, b2;
+};
+
+__device__ __forceinline__ Surf interact(const DevScene &S, float3 d, const Hit &h) {
+  Surf f;
+  const float4 a = __ldg(&S.tris[3 * h.prim]), b = __ldg(&S.tris[3 * h.prim + 1]), c = __ldg(&S.tris[3 * h.prim + 2]);
+  const float3 v0 = xyz(a), v1 = xyz(b), v2 = xyz(c);
+  const float b0 = 1.0f - h.b1 - h.b2;
+  f.b1 = h.b1;
+  f.b2 = h.b2;
+  f.id = h.id;
+  f.p = v0 * b0 + v1 * h.b1 + v2 * h.b2;
+  f.ng = normalize(cross(v1 - v0, v2 - v0));
+  const float4 s0 = __ldg(&S.shade[3 * h.id]), s1 = __ldg(&S.shade[3 * h.id + 1]), s2 = __ldg(&S.shade[3 * h.id + 2]);
+  const float4 m = __ldg(&S.shade2[h.id]);
+  f.mat = __float_as_int(m.w);
+  const float3 n0 = xyz(s0), n1 = xyz(s1), n2 = xyz(s2);
+  const bool flat = (n0.x == 0.f && n0.y == 0.f && n0.z == 0.f) || (n1.x == 0.f && n1.y == 0.f && n1.z == 0.f) ||
+                    (n2.x == 0.f && n2.y == 0.f && n2.z == 0.f);
+  if (flat) {
+    f.ns = f.ng;
+  } else {
+    f.ns = normalize(n0 * b0 + n1 * h.b1 + n2 * h.b2);
+    if (dot(f.ns, f.ng) < 0.0f) f.ns = f.ns * -1.0f;
+  }
+  f.cosg = dot(d, f.ng);
+  const float side = f.cosg < 0.0f ? 1.0f : -1.0f;
+  f.ngf = f.ng * side;
+  f.nsf = f.ns * side;
+  return f;
+}
+
+__device__ __forceinline__ float eps_of(float3 p) { return 1e-4f * fmaxf(1.0f, maxabs(p)); }
+__device__ __forceinline__ float3 offset_along(float3 p, float3 ng, float3 dir) {
+  return p + ng * ((dot(dir, ng) >= 0.0f ? 1.0f : -1.0f) * eps_of(p));
+}
+
+__device__ __forceinline__ float3 albedo_at(const DevScene &S, const sc_material &m, const Surf &f) {
+  if (!(m.checker_scale > 0.0f)) return f3(m.albedo);
+  const float4 s0 = __ldg(&S.shade[3 * f.id]), s1 = __ldg(&S.shade[3 * f.id + 1]), s2 = __ldg(&S.shade[3 * f.id + 2]);
+  const float4 m2 = __ldg(&S.shade2[f.id]);
+  const float b0 = 1.0f - f.b1 - f.b2;
+  const float su = (b0 * s0.w + f.b1 * s1.w + f.b2 * s2.w) * m.checker_scale;
+  const float sv = (b0 * m2.x + f.b1 * m2.y + f.b2 * m2.z) * m.checker_scale;
+  const long parity = ((long)floorf(su) + (long)floorf(sv)) & 1;
+  return parity ? f3(m.albedo2) : f3(m.albedo);
+}
+
+// Fresnel reflectance of unpolarised light (average of s and p), Hecht "Optics" Sec. 4.6
+__device__ __forceinline__ float fresnel(float cos_i, float cos_t, float n_i, float n_t) {
+  const float rs = (n_i * cos_i - n_t * cos_t) / (n_i * cos_i + n_t * cos_t);
+  const float rp = (n_i * cos_t - n_t * cos_i) / (n_i * cos_t + n_t * cos_i);
+  return 0.5f * (rs * rs + rp * rp);
+}
+
+// Dielectric scatter: Snell refraction or reflection chosen with probability R (u0 < R);
+// on the wrong side of the geometric normal, repeated with the geometric normal.
+__device__ __forceinline__ float3 dielectric(const Surf &f, float3 d, float n_lambda, float u0, int flags,
+                                             bool &reflected, bool &fixup) {
+  const bool entering = f.cosg < 0.0f;
+  const float n_i = entering ? 1.0f : n_lambda, n_t = entering ? n_lambda : 1.0f;
+  const float eta = n_i / n_t;
+  float3 out = d;
+  fixup = false;
+  reflected = false;
+  for (int pass = 0; pass < 2; ++pass) {
+    const float3 n = pass == 0 ? f.nsf : f.ngf;
+    const float cos_i = -dot(d, n);
+    if (pass == 0 && cos_i <= 0.0f) {
+      fixup = true;
+      continue;
+    }
+    const float k = 1.0f - eta * eta * (1.0f - cos_i * cos_i);
+    float R = 1.0f;
+    if (k >= 0.0f) R = fresnel(cos_i, sqrtf(k), n_i, n_t);
+    const bool refl = (k < 0.0f) || (!(flags & SC_FLAG_FORCE_TRANSMIT) && u0 < R);
+    if (refl)
+      out = normalize(d + n * (2.0f * cos_i));
+    else
+      out = normalize(d * eta + n * (eta * cos_i - sqrtf(k)));
+    reflected = refl;
+    const float side = dot(out, f.ngf);
+    const bool ok = refl ? side > 0.0f : side < 0.0f;
+    if (ok || pass == 1) break;
+    fixup = true;
+  }
+  return out;
+}
+
+// orthonormal basis around unit n (Duff et al., "Building an Orthonormal Basis, Revisited",
+// JCGT 2017) and a cosine-weighted direction about n
+__device__ __forceinline__ void onb(float3 n, float3 &t1, float3 &t2) {
+  const float sign = copysignf(1.0f, n.z);
+  const float a = -1.0f / (sign + n.z);
+  const float b = n.x * n.y * a;
+  t1 = f3(1.0f + sign * n.x * n.x * a, sign * b, -sign * n.x);
+  t2 = f3(b, sign + n.y * n.y * a, -n.y);
+}
+__device__ __forceinline__ float3 cosine_dir(float3 n, float u1, float u2) {
+  float3 t1, t2;
+  onb(n, t1, t2);
+  const float r = sqrtf(u1);
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  return normalize(t1 * (r * c) + t2 * (r * s) + n * sqrtf(fmaxf(0.0f, 1.0f - u1)));
+}
+
+}  // namespace sc

@@ -1,0 +1,55 @@
+// internal.h -- launchers shared between the CUDA translation units (not part of the ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "supercaustics.h"
+
+namespace sc {
+
+struct DevScene;
+
+// ---- LBVH build (build.cu) ----------------------------------------------------------------
+struct BuildBuffers {
+  // inputs (device)
+  const float *positions, *normals, *uvs;
+  const int32_t *indices, *tri_object, *object_material;
+  int32_t n_tris, n_objects;
+  // outputs (device, owned by the scene)
+  float4 *nodes;   // 4 * max(n_tris - 1, 1)
+  float4 *tris;    // 3 * n_tris (leaf order)
+  float4 *shade;   // 3 * n_tris (input order)
+  float4 *shade2;  // n_tris
+  int32_t *tri_obj;
+  // scratch (device)
+  float4 *tris_in;       // 3 * n_tris (input order)
+  float4 *centroids;     // n_tris
+  uint32_t *bounds;      // 6 sortable words (min xyz, max xyz)
+  uint32_t *keys, *keys_alt;
+  uint32_t *vals, *vals_alt;
+  uint32_t *hist;        // 256 * sort_blocks
+  int32_t *parents;      // (n_tris - 1) internal + n_tris leaves, parent << 1 | slot
+  int32_t *flags;        // n_tris - 1
+  int32_t *depth;        // 1 word: deepest leaf
+};
+size_t sort_blocks(int32_t n);
+cudaError_t launch_build(const BuildBuffers &b, cudaStream_t s);
+
+// ---- renderer (render.cu) -----------------------------------------------------------------
+cudaError_t launch_trace_camera(const DevScene &S, const sc_trace_params &p, const sc_frame &f, unsigned *status,
+                                unsigned *ticket, unsigned long long *counters, int grid, cudaStream_t s);
+cudaError_t launch_trace_lights(const DevScene &S, const sc_light_params &p, const sc_frame &f, unsigned *status,
+                                unsigned long long *ticket, unsigned long long *counters, int grid,
+                                cudaStream_t s);
+cudaError_t launch_resolve(const DevScene &S, const sc_resolve_params &p, const sc_frame &f, unsigned *status,
+                           cudaStream_t s);
+cudaError_t launch_intersect(const DevScene &S, const float *rays, int64_t n, float *hits, unsigned *status,
+                             cudaStream_t s);
+cudaError_t launch_occluded(const DevScene &S, const float *rays, int64_t n, int32_t *occ, unsigned *status,
+                            cudaStream_t s);
+const void *camera_kernel_ptr();
+const void *light_kernel_ptr();
+cudaError_t launch_philox(const uint32_t *ctr, uint64_t key, int64_t n, uint32_t *out, cudaStream_t s);
+
+}  // namespace sc

@@ -1,0 +1,233 @@
+"""ctypes binding of ``include/supercaustics.h`` (argument marshalling only).
+
+Every function here forwards to the entry point of the same name in ``libsupercaustics.so`` and
+raises ``ScError`` on a negative status.  No step of the renderer runs in Python: if the library
+is missing the import of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+P = C.POINTER
+
+SC_OK = 0
+ERRORS = {-1: "SC_ERR_INVALID_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_OOM", -4: "SC_ERR_STACK_OVERFLOW",
+          -5: "SC_ERR_TIMEOUT", -6: "SC_ERR_QUEUE_OVERFLOW", -7: "SC_ERR_UNSUPPORTED"}
+SC_FLAG_FORCE_TRANSMIT = 1
+SC_FLAG_SPLAT_DIRECT = 2
+SC_FLAG_EMITTER_AFTER_DS = 4
+
+
+class ScError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sc_material(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("albedo", C.c_float * 3), ("albedo2", C.c_float * 3),
+                ("checker_scale", C.c_float), ("cauchy_a", C.c_float), ("cauchy_b", C.c_float),
+                ("emission", C.c_float * 3)]
+
+
+class sc_light(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("p", C.c_float * 3), ("u", C.c_float * 3), ("v", C.c_float * 3),
+                ("power", C.c_float * 3), ("radius", C.c_float)]
+
+
+class sc_camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("look", C.c_float * 3), ("up", C.c_float * 3), ("vfov_deg", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class sc_scene_desc(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_tris", C.c_int32), ("positions", C.c_void_p), ("normals", C.c_void_p),
+                ("uvs", C.c_void_p), ("indices", C.c_void_p), ("tri_object", C.c_void_p),
+                ("n_objects", C.c_int32), ("object_material", C.c_void_p), ("n_materials", C.c_int32),
+                ("materials", P(sc_material)), ("n_lights", C.c_int32), ("lights", P(sc_light)),
+                ("env", C.c_float * 3), ("camera", sc_camera), ("geometry_on_device", C.c_int32)]
+
+
+class sc_trace_params(C.Structure):
+    _fields_ = [("spp", C.c_int32), ("sample_offset", C.c_int32), ("max_depth", C.c_int32), ("n_bins", C.c_int32),
+                ("seed", C.c_uint64), ("scene_index", C.c_int32), ("flags", C.c_int32)]
+
+
+class sc_light_params(C.Structure):
+    _fields_ = [("n_paths", C.c_int64), ("path_offset", C.c_int64), ("max_depth", C.c_int32), ("n_bins", C.c_int32),
+                ("seed", C.c_uint64), ("scene_index", C.c_int32), ("flags", C.c_int32)]
+
+
+class sc_resolve_params(C.Structure):
+    _fields_ = [("spp_total", C.c_double), ("light_paths_total", C.c_double), ("depth_range", C.c_float),
+                ("tau_rel", C.c_float)]
+
+
+class sc_path_record(C.Structure):
+    _fields_ = [("L", C.c_float * 3), ("first_tri", C.c_uint32), ("signature", C.c_uint32),
+                ("n_queries", C.c_uint32), ("bin", C.c_uint32), ("n_specular", C.c_uint32)]
+
+
+class sc_light_record(C.Structure):
+    _fields_ = [("C", C.c_float * 3), ("pixel", C.c_int32), ("x", C.c_float * 3), ("signature", C.c_uint32),
+                ("n_specular", C.c_uint32), ("bin", C.c_uint32), ("pad", C.c_uint32 * 2)]
+
+
+FRAME_FIELDS = ["accum_camera", "accum_caustic", "rgb", "direct", "caustic", "instance_id", "tri_id", "mask",
+                "caustic_mask", "local_caustic_mask", "depth", "depth_norm", "normal_world", "normal_camera",
+                "albedo", "path_records", "light_records"]
+
+
+class sc_frame(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in FRAME_FIELDS] + [("width", C.c_int32), ("height", C.c_int32)]
+
+
+class sc_scene_info(C.Structure):
+    _fields_ = [("n_tris", C.c_int32), ("n_nodes", C.c_int32), ("n_materials", C.c_int32), ("n_lights", C.c_int32),
+                ("bvh_bytes", C.c_int64), ("max_depth", C.c_int32), ("pad", C.c_int32)]
+
+
+STRUCTS = [sc_material, sc_light, sc_camera, sc_scene_desc, sc_trace_params, sc_light_params, sc_resolve_params,
+           sc_path_record, sc_light_record, sc_frame, sc_scene_info]
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+# exported entry points and their signatures
+SIGNATURES = {
+    "sc_abi_version": (C.c_int, []),
+    "sc_struct_sizes": (C.c_int, [P(C.c_int32), C.c_int32]),
+    "sc_create": (C.c_int, [C.c_int, C.c_void_p, ALLOC_FN, FREE_FN, C.c_void_p, P(C.c_void_p)]),
+    "sc_destroy": (C.c_int, [C.c_void_p]),
+    "sc_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sc_last_error": (C.c_char_p, [C.c_void_p]),
+    "sc_sync_status": (C.c_int, [C.c_void_p]),
+    "sc_set_counters": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sc_build_scene": (C.c_int, [C.c_void_p, P(sc_scene_desc), P(C.c_void_p)]),
+    "sc_free_scene": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sc_scene_get_info": (C.c_int, [C.c_void_p, P(sc_scene_info)]),
+    "sc_scene_export_bvh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sc_intersect": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "sc_occluded": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "sc_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int64, C.c_void_p]),
+    "sc_trace_camera": (C.c_int, [C.c_void_p, C.c_void_p, P(sc_trace_params), P(sc_frame)]),
+    "sc_trace_lights": (C.c_int, [C.c_void_p, C.c_void_p, P(sc_light_params), P(sc_frame)]),
+    "sc_resolve": (C.c_int, [C.c_void_p, C.c_void_p, P(sc_resolve_params), P(sc_frame)]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libsupercaustics.so (building it first if asked); raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"libsupercaustics.so not built ({path}); run paper_2107_11008_gb300.build")
+        _build.build_library()
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    sizes = (C.c_int32 * len(STRUCTS))()
+    k = lib.sc_struct_sizes(sizes, len(STRUCTS))
+    want = [C.sizeof(s) for s in STRUCTS]
+    if k != len(STRUCTS) or list(sizes) != want:
+        raise ImportError(f"supercaustics ABI layout mismatch: library {list(sizes)} vs binding {want}")
+    _lib = lib
+    return lib
+
+
+def check(code: int, ctx=None):
+    if code != SC_OK:
+        msg = load().sc_last_error(ctx).decode() if ctx else ""
+        raise ScError(code, msg)
+    return code
+
+
+# --- thin wrappers, same names as the C entry points ------------------------------------------
+def sc_abi_version() -> int:
+    return load().sc_abi_version()
+
+
+def sc_create(device, stream, alloc=None, free=None, user=None):
+    out = C.c_void_p()
+    a = alloc if alloc is not None else ALLOC_FN()
+    f = free if free is not None else FREE_FN()
+    check(load().sc_create(device, stream, a, f, user, C.byref(out)))
+    return out.value
+
+
+def sc_destroy(ctx):
+    return check(load().sc_destroy(ctx))
+
+
+def sc_set_stream(ctx, stream):
+    return check(load().sc_set_stream(ctx, stream), ctx)
+
+
+def sc_last_error(ctx) -> str:
+    return load().sc_last_error(ctx).decode()
+
+
+def sc_sync_status(ctx):
+    return check(load().sc_sync_status(ctx), ctx)
+
+
+def sc_set_counters(ctx, counters_dev):
+    return check(load().sc_set_counters(ctx, counters_dev), ctx)
+
+
+def sc_build_scene(ctx, desc: sc_scene_desc):
+    out = C.c_void_p()
+    check(load().sc_build_scene(ctx, C.byref(desc), C.byref(out)), ctx)
+    return out.value
+
+
+def sc_free_scene(ctx, scene):
+    return check(load().sc_free_scene(ctx, scene), ctx)
+
+
+def sc_scene_get_info(scene) -> sc_scene_info:
+    info = sc_scene_info()
+    check(load().sc_scene_get_info(scene, C.byref(info)))
+    return info
+
+
+def sc_scene_export_bvh(ctx, scene, nodes_host, tris_host):
+    return check(load().sc_scene_export_bvh(ctx, scene, nodes_host, tris_host), ctx)
+
+
+def sc_intersect(ctx, scene, rays_dev, n, hits_dev):
+    return check(load().sc_intersect(ctx, scene, rays_dev, n, hits_dev), ctx)
+
+
+def sc_occluded(ctx, scene, rays_dev, n, occ_dev):
+    return check(load().sc_occluded(ctx, scene, rays_dev, n, occ_dev), ctx)
+
+
+def sc_philox4x32_10(ctx, ctr_dev, key, n, out_dev):
+    return check(load().sc_philox4x32_10(ctx, ctr_dev, key, n, out_dev), ctx)
+
+
+def sc_trace_camera(ctx, scene, params: sc_trace_params, frame: sc_frame):
+    return check(load().sc_trace_camera(ctx, scene, C.byref(params), C.byref(frame)), ctx)
+
+
+def sc_trace_lights(ctx, scene, params: sc_light_params, frame: sc_frame):
+    return check(load().sc_trace_lights(ctx, scene, C.byref(params), C.byref(frame)), ctx)
+
+
+def sc_resolve(ctx, scene, params: sc_resolve_params, frame: sc_frame):
+    return check(load().sc_resolve(ctx, scene, C.byref(params), C.byref(frame)), ctx)

@@ -1,0 +1,418 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on seeded inputs.
+
+Bar (the benchmark spec): bit-exact hit-triangle ids / mask / id buffers away from grazing cases,
+per-path radiance within 1e-4 relative, image MSE within 1e-5 at equal spp and seed.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2107_11008_gb300 import native as N  # noqa: E402
+from paper_2107_11008_gb300 import renderer as R  # noqa: E402
+from paper_2107_11008_gb300 import scenes as S  # noqa: E402
+
+from .parity import MAX_AMBIGUOUS_GLASS, MSE, compare_camera, compare_lights, rel_close  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = R.Context(0)
+    yield c
+    c.close()
+
+
+def _soup(n_tris, seed, spread=0.15):
+    rng = np.random.default_rng(seed)
+    b = S.SceneBuilder()
+    m = b.material(S.Material(S.MAT_DIFFUSE))
+    c = rng.uniform(-1, 1, (n_tris, 1, 3))
+    p = c + rng.normal(0, spread, (n_tris, 3, 3))
+    b.add(S.Mesh(p.reshape(-1, 3), np.arange(3 * n_tris).reshape(-1, 3), None, None), m)
+    return b.build(S.Camera((0, 0, 5), (0, 0, 0), (0, 1, 0), 40, 8, 8))
+
+
+def _small_glass(width=50, height=38, tris=2000, n_objects=3, seed=1):
+    return S.glass_scene(seed=seed, width=width, height=height, n_objects=n_objects, tris_per_object=tris)
+
+
+# ------------------------------------------------------------------------------------------
+# Philox, LBVH, queries
+# ------------------------------------------------------------------------------------------
+
+def test_philox_matches_oracle_bit_exact(ctx):
+    rng = np.random.default_rng(0)
+    n = 1 << 20
+    ctr = rng.integers(0, 2 ** 32, (n, 4), dtype=np.uint64).astype(np.uint32)
+    for key in (0, 0xFFFFFFFFFFFFFFFF, 0x299F31D0A4093822, 12345):
+        g = R.philox(ctx, torch.from_numpy(ctr.view(np.int32)).cuda(), key).cpu().numpy().view(np.uint32)
+        np.testing.assert_array_equal(g, O.philox(ctr, key))
+
+
+def _check_bvh(gs, sc):
+    nodes, tris = gs.export_bvh()
+    n = sc.n_tris
+    info = gs.info()
+    assert info.n_tris == n
+    # leaf order is a permutation of the input triangles with unchanged vertices
+    ids = tris[:, 3].view(np.int32)
+    assert sorted(ids.tolist()) == list(range(n))
+    P = sc.positions[sc.indices]  # (n,3,3)
+    np.testing.assert_array_equal(tris[:, [0, 1, 2]], P[ids, 0])
+    np.testing.assert_array_equal(tris[:, [4, 5, 6]], P[ids, 1])
+    np.testing.assert_array_equal(tris[:, [8, 9, 10]], P[ids, 2])
+    if n == 1:
+        return
+    assert nodes.shape[0] == n - 1
+    ch = nodes[:, 12:14].copy().view(np.int32)
+    refs = ch.ravel()
+    internal = refs[refs >= 0]
+    leaves = ~refs[refs < 0]
+    assert sorted(internal.tolist()) == list(range(1, n - 1))  # every internal node but the root once
+    assert sorted(leaves.tolist()) == list(range(n))  # every leaf once
+
+    def slot_box(i, s):
+        nd = nodes[i]
+        if s == 0:
+            return np.array([nd[0], nd[2], nd[8]]), np.array([nd[1], nd[3], nd[9]])
+        return np.array([nd[4], nd[6], nd[10]]), np.array([nd[5], nd[7], nd[11]])
+
+    for i in range(n - 1):
+        for s in range(2):
+            lo, hi = slot_box(i, s)
+            c = ch[i, s]
+            if c < 0:
+                v = tris[~c].reshape(3, 4)[:, :3]
+                np.testing.assert_array_equal(lo, v.min(0))
+                np.testing.assert_array_equal(hi, v.max(0))
+            else:
+                lo0, hi0 = slot_box(c, 0)
+                lo1, hi1 = slot_box(c, 1)
+                np.testing.assert_array_equal(lo, np.minimum(lo0, lo1))
+                np.testing.assert_array_equal(hi, np.maximum(hi0, hi1))
+    assert 1 <= info.max_depth <= 64
+
+
+@pytest.mark.parametrize("n_tris", [1, 2, 3, 7, 200, 2049, 5000])
+def test_lbvh_invariants_soup(ctx, n_tris):
+    sc = _soup(n_tris, n_tris)
+    gs = R.GpuScene(ctx, sc)
+    ctx.sync_status()
+    _check_bvh(gs, sc)
+
+
+def test_lbvh_invariants_meshes(ctx):
+    for sc in (S.ball_on_plane(), _small_glass()):
+        gs = R.GpuScene(ctx, sc)
+        ctx.sync_status()
+        _check_bvh(gs, sc)
+
+
+def test_lbvh_duplicate_centroids():
+    """Many triangles with identical centroids (equal Morton codes) still give a valid tree."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = R.Context(0)
+    b = S.SceneBuilder()
+    m = b.material(S.Material(S.MAT_DIFFUSE))
+    rng = np.random.default_rng(5)
+    p = np.repeat(rng.normal(0, 0.1, (1, 3, 3)), 300, axis=0) + rng.normal(0, 1e-9, (300, 3, 3))
+    b.add(S.Mesh(p.reshape(-1, 3), np.arange(900).reshape(-1, 3), None, None), m)
+    sc = b.build(S.Camera((0, 0, 5), (0, 0, 0), (0, 1, 0), 40, 8, 8))
+    gs = R.GpuScene(c, sc)
+    c.sync_status()
+    _check_bvh(gs, sc)
+
+
+def _random_rays(sc, n, seed):
+    rng = np.random.default_rng(seed)
+    P = sc.positions.astype(np.float64)[sc.indices]
+    org = rng.uniform(-3, 3, (n, 3))
+    k = rng.integers(0, sc.n_tris, n)
+    bc = rng.dirichlet([1, 1, 1], n)
+    tgt = np.einsum("ij,ijk->ik", bc, P[k])
+    tgt[: n // 4] = rng.uniform(-1, 1, (n // 4, 3))
+    d = tgt - org
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return org.astype(np.float32), d.astype(np.float32)
+
+
+@pytest.mark.parametrize("n_tris", [1, 7, 200, 5000])
+def test_closest_hit_matches_oracle_brute_force(ctx, n_tris):
+    sc = _soup(n_tris, 100 + n_tris)
+    gs = R.GpuScene(ctx, sc)
+    org, d = _random_rays(sc, 20000, n_tris)
+    t, tri, _, _ = R.intersect(ctx, gs, torch.from_numpy(org).cuda(), torch.from_numpy(d).cuda())
+    ctx.sync_status()
+    t, tri = t.cpu().numpy(), tri.cpu().numpy()
+    orc = O.OracleScene(sc)
+    ot, otri, _, amb = orc.intersect(org.astype(np.float64), d.astype(np.float64), brute=True)
+    ok = amb == 0
+    assert ok.mean() > 0.99
+    np.testing.assert_array_equal(tri[ok], otri[ok])
+    hit = ok & (otri >= 0)
+    assert hit.mean() > 0.3
+    # FP32 t = T / det: relative error grows with the distance/size ratio of the triangle
+    assert rel_close(t[hit], ot[hit], 1e-4).all()
+
+
+def test_watertight_shared_edges_and_vertices(ctx):
+    """Rays through the exact shared vertices and edge midpoints of a closed mesh never leak."""
+    b = S.SceneBuilder()
+    b.add(S.icosphere(4), b.material(S.Material(S.MAT_DIELECTRIC)))
+    sc = b.build(S.Camera((0, 0, 5), (0, 0, 0), (0, 1, 0), 40, 8, 8))
+    gs = R.GpuScene(ctx, sc)
+    P = sc.positions
+    idx = sc.indices
+    targets = np.concatenate([P, 0.5 * (P[idx[:, 0]] + P[idx[:, 1]]), 0.5 * (P[idx[:, 1]] + P[idx[:, 2]]),
+                              0.5 * (P[idx[:, 2]] + P[idx[:, 0]])]).astype(np.float32)
+    rng = np.random.default_rng(2)
+    org = (targets * 3.0 + rng.normal(0, 0.5, targets.shape)).astype(np.float32)
+    d = targets - org
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    _, tri, _, _ = R.intersect(ctx, gs, torch.from_numpy(org).cuda(), torch.from_numpy(d).cuda())
+    assert (tri.cpu().numpy() >= 0).all()
+    inner = np.zeros_like(targets)
+    di = targets / np.linalg.norm(targets, axis=1, keepdims=True)
+    _, tri2, _, _ = R.intersect(ctx, gs, torch.from_numpy(inner).cuda(), torch.from_numpy(di.astype(np.float32)).cuda())
+    assert (tri2.cpu().numpy() >= 0).all()
+
+
+def test_occluded_matches_oracle(ctx):
+    sc = _soup(300, 7)
+    gs = R.GpuScene(ctx, sc)
+    org, d = _random_rays(sc, 20000, 9)
+    tmax = np.random.default_rng(3).uniform(0.5, 6.0, len(org)).astype(np.float32)
+    occ = R.occluded(ctx, gs, torch.from_numpy(org).cuda(), torch.from_numpy(d).cuda(),
+                     torch.from_numpy(tmax).cuda()).cpu().numpy()
+    ctx.sync_status()
+    oocc, amb = O.OracleScene(sc).occluded(org.astype(np.float64), d.astype(np.float64), tmax.astype(np.float64),
+                                           brute=True)
+    ok = amb == 0
+    assert ok.mean() > 0.99
+    np.testing.assert_array_equal(occ[ok], oocc[ok])
+    assert 0.05 < occ.mean() < 0.95
+
+
+# ------------------------------------------------------------------------------------------
+# Estimators
+# ------------------------------------------------------------------------------------------
+
+def _render(ctx, sc, spp, depth, n_bins=1, n_light=0, seed=0, flags=0, lflags=0, records=True):
+    gs = R.GpuScene(ctx, sc)
+    fr = R.Frame(sc.camera.width, sc.camera.height)
+    if records:
+        fr.alloc_path_records(spp)
+        if n_light:
+            fr.alloc_light_records(n_light)
+    if spp:
+        R.trace_camera(ctx, gs, fr, spp, depth, n_bins, seed, flags=flags)
+    if n_light:
+        R.trace_lights(ctx, gs, fr, n_light, depth, n_bins, seed, flags=lflags)
+    R.resolve(ctx, gs, fr, spp, n_light)
+    ctx.sync_status()
+    return gs, fr
+
+
+def test_camera_parity_ball_on_plane(ctx):
+    """64x64, 16 spp, depth 8, one glass icosphere (1280 tris) on a plane, point light."""
+    sc = S.ball_on_plane()
+    spp, depth = 16, 8
+    _, fr = _render(ctx, sc, spp, depth)
+    g = R.path_records_numpy(fr.path_records)
+    acc, rec = O.OracleScene(sc).trace_camera(spp, depth)
+    stats = compare_camera(g, rec, max_ambiguous=0.01)
+    img = fr["direct"][..., :3].cpu().numpy()
+    assert np.mean((img - acc / spp) ** 2) <= MSE
+    assert stats["ambiguous"] < 0.01
+    # the glass is actually exercised
+    assert (rec["n_specular"] >= 2).mean() > 0.1
+
+
+def test_camera_parity_dispersive_glass_scene_ragged(ctx):
+    """Several glass meshes with Cauchy dispersion (8 bins) over a checkered backdrop under a rect light;
+    50x38 (ragged against the 8x4 warp tiles), 4 spp, depth 12."""
+    sc = _small_glass()
+    spp, depth, nb = 4, 12, 8
+    _, fr = _render(ctx, sc, spp, depth, n_bins=nb, seed=11)
+    g = R.path_records_numpy(fr.path_records)
+    acc, rec = O.OracleScene(sc).trace_camera(spp, depth, nbins=nb, seed=11)
+    compare_camera(g, rec, max_ambiguous=MAX_AMBIGUOUS_GLASS)
+    img = fr["direct"][..., :3].cpu().numpy()
+    assert np.mean((img - acc / spp) ** 2) <= MSE
+    assert len(np.unique(rec["bin"])) == nb
+
+
+def test_light_parity_ball_on_plane(ctx):
+    sc = S.ball_on_plane()
+    n = 1 << 18
+    _, fr = _render(ctx, sc, 0, 8, n_light=n, records=True)
+    g = R.light_records_numpy(fr.light_records)
+    acc, rec = O.OracleScene(sc).trace_lights(n, 8)
+    compare_lights(g, rec)
+    img = fr["accum_caustic"][..., :3].cpu().numpy() / n
+    assert np.mean((img - acc / n) ** 2) <= MSE
+
+
+def test_light_parity_rect_light_dispersion(ctx):
+    sc = _small_glass(40, 40)
+    n = 1 << 17
+    _, fr = _render(ctx, sc, 0, 12, n_bins=8, n_light=n, seed=3)
+    g = R.light_records_numpy(fr.light_records)
+    acc, rec = O.OracleScene(sc).trace_lights(n, 12, nbins=8, seed=3)
+    st = compare_lights(g, rec, max_ambiguous=MAX_AMBIGUOUS_GLASS)
+    assert st["splatted"] > 0.002
+    img = fr["accum_caustic"][..., :3].cpu().numpy() / n
+    assert np.mean((img - acc / n) ** 2) <= MSE
+
+
+def test_resolve_ground_truth_parity(ctx):
+    sc = S.ball_on_plane(48, 40)
+    spp, n = 8, 1 << 16
+    _, fr = _render(ctx, sc, spp, 8, n_light=n)
+    orc = O.OracleScene(sc)
+    acc, _ = orc.trace_camera(spp, 8, records=False)
+    accl, _ = orc.trace_lights(n, 8, records=False)
+    g = orc.resolve(acc, accl, spp, n)
+    ok = g["amb"] == 0
+    assert ok.mean() > 0.98
+    for k in ("instance_id", "tri_id", "mask"):
+        ok_key = {"instance_id": "instance", "tri_id": "tri", "mask": "mask"}[k]
+        np.testing.assert_array_equal(fr[k].cpu().numpy()[ok], g[ok_key][ok])
+    hit = ok & (g["tri"] >= 0)
+    np.testing.assert_allclose(fr["depth"].cpu().numpy()[hit], g["depth"][hit], rtol=1e-5)
+    np.testing.assert_allclose(fr["depth_norm"].cpu().numpy()[hit], g["depth_norm"][hit], rtol=1e-5)
+    np.testing.assert_allclose(fr["normal_world"].cpu().numpy()[..., :3][hit], g["n_world"][hit], atol=1e-5)
+    np.testing.assert_allclose(fr["normal_camera"].cpu().numpy()[..., :3][hit], g["n_cam"][hit], atol=1e-5)
+    np.testing.assert_allclose(fr["albedo"].cpu().numpy()[..., :3][hit], g["albedo"][hit], atol=1e-6)
+    miss = ok & (g["tri"] < 0)
+    assert np.isinf(fr["depth"].cpu().numpy()[miss]).all()
+    np.testing.assert_allclose(fr["rgb"].cpu().numpy()[..., :3], g["rgb"], atol=3e-3)
+    # caustic mask: equal wherever the luminance is not within 1e-3 relative of the threshold
+    yc = g["caustic"] @ np.array([0.2126, 0.7152, 0.0722])
+    yd = g["direct"] @ np.array([0.2126, 0.7152, 0.0722])
+    thr = 0.25 * np.maximum(yd, 1e-3)
+    clear = ok & (np.abs(yc - thr) > 1e-3 * thr + 1e-6)
+    np.testing.assert_array_equal(fr["caustic_mask"].cpu().numpy()[clear], g["caustic_mask"][clear])
+
+
+def test_sample_offsets_compose(ctx):
+    sc = S.ball_on_plane(32, 24)
+    gs = R.GpuScene(ctx, sc)
+    a = R.Frame(32, 24, fields=("accum_camera",))
+    b = R.Frame(32, 24, fields=("accum_camera",))
+    a.alloc_path_records(8)
+    R.trace_camera(ctx, gs, a, 8, 8)
+    b.alloc_path_records(3)
+    R.trace_camera(ctx, gs, b, 3, 8)
+    pa = R.path_records_numpy(a.path_records)
+    pb = R.path_records_numpy(b.path_records)
+    b.alloc_path_records(5)
+    R.trace_camera(ctx, gs, b, 5, 8, sample_offset=3)
+    pc = R.path_records_numpy(b.path_records)
+    ctx.sync_status()
+    La = pa["L"].reshape(-1, 8, 3)
+    np.testing.assert_array_equal(La[:, :3], pb["L"].reshape(-1, 3, 3))
+    np.testing.assert_array_equal(La[:, 3:], pc["L"].reshape(-1, 5, 3))
+    np.testing.assert_allclose(a["accum_camera"].cpu().numpy(), b["accum_camera"].cpu().numpy(), rtol=1e-5,
+                               atol=1e-6)
+
+
+def test_gpu_white_furnace_and_point_light_closed_form(ctx):
+    b = S.SceneBuilder()
+    b.add(S.icosphere(2), b.material(S.Material(S.MAT_DIFFUSE, albedo=(0.5,) * 3)))
+    sc = b.build(S.Camera((0, 0, 3.5), (0, 0, 0), (0, 1, 0), 40, 24, 24), env=(1, 1, 1))
+    _, fr = _render(ctx, sc, 8, 4)
+    g = R.path_records_numpy(fr.path_records)
+    hit = g["first_tri"] >= 0
+    np.testing.assert_allclose(g["L"][hit], 0.5, rtol=1e-6)
+    np.testing.assert_array_equal(g["L"][~hit], 1.0)
+
+
+def test_gpu_ball_lens_focus(ctx):
+    """Collimated beam through a glass ball (n=1.5, D=2): smallest spot within 3 % of f = 1.5."""
+    zs = np.arange(1.36, 1.65, 0.02)
+    rms = []
+    for z in zs:
+        b = S.SceneBuilder()
+        b.add(S.icosphere(5), b.material(S.Material(S.MAT_DIELECTRIC, cauchy_a=1.5)))
+        b.add(S.quad((-3, -z, -3), (0, 0, 6), (6, 0, 0)), b.material(S.Material(S.MAT_DIFFUSE)))
+        b.lights.append(S.Light(S.LIGHT_DISK, (0.0, 3.0, 0.0), (0.0, -1.0, 0.0), power=(1.0,) * 3, radius=0.1))
+        sc = b.build(S.Camera((0, 0, 6), (0, 0, 0), (0, 1, 0), 40, 8, 8))
+        _, fr = _render(ctx, sc, 0, 8, n_light=8192, lflags=N.SC_FLAG_FORCE_TRANSMIT)
+        g = R.light_records_numpy(fr.light_records)
+        x = g["x"][g["n_specular"] == 2]
+        rms.append(math.sqrt(float(np.mean(x[:, 0] ** 2 + x[:, 2] ** 2))))
+    assert abs(zs[int(np.argmin(rms))] - 1.5) <= 0.045
+
+
+# ------------------------------------------------------------------------------------------
+# Edge cases and errors
+# ------------------------------------------------------------------------------------------
+
+def test_degenerate_sizes(ctx):
+    # 1x1 image, one triangle, zero samples and zero light paths are valid no-ops or tiny renders
+    b = S.SceneBuilder()
+    b.add(S.Mesh(np.array([[-1, -1, 0], [1, -1, 0], [0, 1, 0]], float), np.array([[0, 1, 2]]), None, None),
+          b.material(S.Material(S.MAT_DIFFUSE)))
+    b.lights.append(S.Light(S.LIGHT_POINT, (0, 0, 3), power=(1, 1, 1)))
+    sc = b.build(S.Camera((0, 0, 4), (0, 0, 0), (0, 1, 0), 30, 1, 1))
+    _, fr = _render(ctx, sc, 4, 3, n_light=100)
+    g = R.path_records_numpy(fr.path_records)
+    _, rec = O.OracleScene(sc).trace_camera(4, 3)
+    compare_camera(g, rec)
+    gs = R.GpuScene(ctx, sc)
+    fr2 = R.Frame(1, 1)
+    R.trace_camera(ctx, gs, fr2, 0, 3)
+    R.trace_lights(ctx, gs, fr2, 0, 3)
+    ctx.sync_status()
+    assert float(fr2["accum_camera"].abs().sum()) == 0.0
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    sc = S.ball_on_plane(16, 16)
+    gs = R.GpuScene(ctx, sc)
+    wrong = R.Frame(8, 8)
+    with pytest.raises(N.ScError) as e:
+        R.trace_camera(ctx, gs, wrong, 1, 4)
+    assert e.value.code == -1
+    good = R.Frame(16, 16)
+    for nb in (0, 65):
+        with pytest.raises(N.ScError):
+            R.trace_camera(ctx, gs, good, 1, 4, n_bins=nb)
+    with pytest.raises(N.ScError):
+        R.trace_lights(ctx, gs, good, -1, 4)
+    bad = S.ball_on_plane(16, 16)
+    bad.indices = bad.indices.copy()
+    bad.indices[0, 0] = 10 ** 6
+    with pytest.raises(N.ScError):
+        R.GpuScene(ctx, bad)
+    ctx.sync_status()
+
+
+# ------------------------------------------------------------------------------------------
+# Full-size workload: 512x512 dispersive glass scene, sampled rows checked path by path
+# ------------------------------------------------------------------------------------------
+
+def test_full_size_glass_scene_sampled_rows(ctx):
+    sc = S.glass_scene(0)
+    spp, depth, nb = 2, 12, 8
+    gs = R.GpuScene(ctx, sc)
+    fr = R.Frame(512, 512, fields=("accum_camera",))
+    fr.alloc_path_records(spp)
+    R.trace_camera(ctx, gs, fr, spp, depth, nb, 0)
+    ctx.sync_status()
+    g = R.path_records_numpy(fr.path_records)
+    rows = [0, 137, 300, 511]
+    orc = O.OracleScene(sc)
+    for y in rows:
+        _, rec = orc.trace_camera(spp, depth, nbins=nb, window=(0, 512, y, y + 1))
+        sel = slice(y * 512 * spp, (y + 1) * 512 * spp)
+        compare_camera({k: v[sel] for k, v in g.items()}, rec, max_ambiguous=MAX_AMBIGUOUS_GLASS)
