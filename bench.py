@@ -129,15 +129,19 @@ def cpu_baseline(scene, spp_full, nl_full, seconds, depth=12, nbins=8):
 
     cores = len(os.sched_getaffinity(0))
     orc = O.OracleScene(scene)
-    W = scene.camera.width
-    # calibrate on a tiny sample, then size the sample to about `seconds`
+    W, H = scene.camera.width, scene.camera.height
+    # calibrate on a 1-spp band of rows, then size the sample (rows x spp) to about `seconds`
+    band = max(1, H // 8)
     t0 = time.perf_counter()
-    orc.trace_camera(1, depth, nbins=nbins, window=(0, W, W // 2, W // 2 + 2), records=False, n_threads=cores)
-    t_small = max(time.perf_counter() - t0, 1e-3)
-    per_path = t_small / (2 * W)
-    spp = 4
-    rows = max(1, min(scene.camera.height, int(0.85 * seconds / (per_path * W * spp))))
-    y0 = max(0, W // 2 - rows // 2)
+    orc.trace_camera(1, depth, nbins=nbins, window=(0, W, H // 2 - band // 2, H // 2 - band // 2 + band),
+                     records=False, n_threads=cores)
+    per_path = max(time.perf_counter() - t0, 1e-3) / (band * W)
+    budget = 0.85 * seconds / per_path  # camera paths that fit
+    if budget >= W * H:
+        rows, spp = H, int(max(1, min(spp_full, budget // (W * H))))
+    else:
+        rows, spp = max(1, int(budget // W)), 1
+    y0 = max(0, H // 2 - rows // 2)
     n_light = max(4096, int(0.15 * seconds / max(per_path, 1e-9)))
     t0 = time.perf_counter()
     orc.trace_camera(spp, depth, nbins=nbins, window=(0, W, y0, y0 + rows), records=False, n_threads=cores)

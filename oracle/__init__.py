@@ -47,7 +47,7 @@ class Tolerances(C.Structure):
 # each scattering event; a path whose signature or radiance (beyond sens_rel) moves is flagged
 # "sensitive" -- float32 cannot be expected to follow it decision for decision.
 DEFAULT_TOL = dict(pos=2e-5, t=1e-5, cosg=1e-4, fres=1e-4, tir=1e-5, px=1e-3, growth=1.0, sens_delta=1e-6,
-                   sens_rel=1e-4)
+                   sens_rel=5e-5)
 
 
 def default_tol(**kw) -> Tolerances:

@@ -6,7 +6,7 @@ image MSE within 1e-5 at equal samples and seed.  The ambiguous set is where an 
 FP64 evaluation may legitimately take different discrete decisions (near-edge hits, Fresnel
 draws within 1e-4 of R, grazing cosines, shadow rays skimming an edge, splats on a pixel border)
 and must stay below 0.5 % of the paths.  Paths whose FP64 re-traces under +-1e-6 ray nudges
-change (long chains through curved glass, where rounding is amplified) are also excluded; that
+change (signature, or radiance by more than 5e-5) (long chains through curved glass, where rounding is amplified) are also excluded; that
 share depends on the scene (about 0.4 % for one glass ball, a few percent for several
 overlapping glass objects) and each test states its bound.
 """
@@ -15,8 +15,8 @@ import numpy as np
 REL = 1e-4
 MSE = 1e-5
 MAX_AMBIGUOUS = 0.005
-# scenes with several overlapping glass objects
-MAX_AMBIGUOUS_GLASS = 0.06
+# scenes with several overlapping glass objects (rows crossing glass exclude more)
+MAX_AMBIGUOUS_GLASS = 0.10
 
 
 def rel_close(a, b, rel=REL, floor=1e-6):
