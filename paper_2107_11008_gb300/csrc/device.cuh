@@ -244,9 +244,12 @@ struct TravCount {
   unsigned nodes = 0, tris = 0, queries = 0;
 };
 
-// Closest hit (ties on equal t go to the lowest input id).  Sets status bits on overflow.
-static __device__ __noinline__ Hit closest_hit(const DevScene &S, float3 o, float3 d, float tmax, unsigned *status,
-                                               TravCount &tc) {
+// Closest hit (anyhit = false; ties on equal t go to the lowest input id) or any hit with
+// 0 < t < tmax (anyhit = true; returns the first one found).  One traversal loop serves both so
+// that lanes of a warp tracing shadow rays and extension rays stay in the same loop.  Stack
+// overflow and the visit watchdog latch a status bit and abandon the query (reported as a miss).
+static __device__ __forceinline__ Hit trace(const DevScene &S, float3 o, float3 d, float tmax, bool anyhit,
+                                         unsigned *status, TravCount &tc) {
   ++tc.queries;
   Hit h;
   h.t = tmax;
@@ -265,6 +268,7 @@ static __device__ __noinline__ Hit closest_hit(const DevScene &S, float3 o, floa
       atomicOr(status, SC_STATUS_WATCHDOG);
       h.prim = -1;
       h.id = kMiss;
+      h.t = tmax;
       return h;
     }
     const float4 n0 = __ldg(&S.nodes[4 * node + 0]);
@@ -273,35 +277,28 @@ static __device__ __noinline__ Hit closest_hit(const DevScene &S, float3 o, floa
     const float4 n3 = __ldg(&S.nodes[4 * node + 3]);
     const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
     float ta, tb;
-    const float tcull = h.t;
-    bool ha = box_test(w, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull, ta);
-    bool hb = box_test(w, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull, tb);
-    // leaves are tested right away
-    if (ha && c0 < 0) {
-      const int k = ~c0;
-      const float4 a = __ldg(&S.tris[3 * k]), b = __ldg(&S.tris[3 * k + 1]), c = __ldg(&S.tris[3 * k + 2]);
-      float t, b1, b2;
-      ++tc.tris;
-      if (tri_test(w, xyz(a), xyz(b), xyz(c), t, b1, b2)) {
-        const uint32_t id = (uint32_t)__float_as_int(a.w);
-        if (t < h.t || (t == h.t && id < h.id)) {
-          h.t = t; h.b1 = b1; h.b2 = b2; h.prim = k; h.id = id;
+    bool ha = box_test(w, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, h.t, ta);
+    bool hb = box_test(w, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, h.t, tb);
+    // leaves (one triangle each) are tested right away
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const bool hit_box = side == 0 ? ha : hb;
+      const int c = side == 0 ? c0 : c1;
+      if (hit_box && c < 0) {
+        const int k = ~c;
+        const float4 a = __ldg(&S.tris[3 * k]), b = __ldg(&S.tris[3 * k + 1]), cc = __ldg(&S.tris[3 * k + 2]);
+        float t, b1, b2;
+        ++tc.tris;
+        if (tri_test(w, xyz(a), xyz(b), xyz(cc), t, b1, b2)) {
+          const uint32_t id = (uint32_t)__float_as_int(a.w);
+          if (t < h.t || (!anyhit && t == h.t && id < h.id)) {
+            h.t = t; h.b1 = b1; h.b2 = b2; h.prim = k; h.id = id;
+            if (anyhit) return h;
+          }
         }
+        if (side == 0) ha = false;
+        else hb = false;
       }
-      ha = false;
-    }
-    if (hb && c1 < 0) {
-      const int k = ~c1;
-      const float4 a = __ldg(&S.tris[3 * k]), b = __ldg(&S.tris[3 * k + 1]), c = __ldg(&S.tris[3 * k + 2]);
-      float t, b1, b2;
-      ++tc.tris;
-      if (tri_test(w, xyz(a), xyz(b), xyz(c), t, b1, b2)) {
-        const uint32_t id = (uint32_t)__float_as_int(a.w);
-        if (t < h.t || (t == h.t && id < h.id)) {
-          h.t = t; h.b1 = b1; h.b2 = b2; h.prim = k; h.id = id;
-        }
-      }
-      hb = false;
     }
     if (ha && hb) {
       const bool a_first = ta <= tb;
@@ -309,6 +306,7 @@ static __device__ __noinline__ Hit closest_hit(const DevScene &S, float3 o, floa
         atomicOr(status, SC_STATUS_STACK_OVERFLOW);
         h.prim = -1;
         h.id = kMiss;
+        h.t = tmax;
         return h;
       }
       stack[sp++] = a_first ? c1 : c0;
@@ -326,66 +324,13 @@ static __device__ __noinline__ Hit closest_hit(const DevScene &S, float3 o, floa
   return h;
 }
 
-// Any hit with 0 < t < tmax.
-static __device__ __noinline__ bool any_hit(const DevScene &S, float3 o, float3 d, float tmax, unsigned *status,
-                                            TravCount &tc) {
-  ++tc.queries;
-  if (S.n_tris <= 0) return false;
-  const WRay w = make_wray(o, d);
-  int stack[kStack];
-  int sp = 0;
-  int node = 0;
-  int visits = 0;
-  for (;;) {
-    ++tc.nodes;
-    if (++visits > kMaxVisits) {
-      atomicOr(status, SC_STATUS_WATCHDOG);
-      return false;
-    }
-    const float4 n0 = __ldg(&S.nodes[4 * node + 0]);
-    const float4 n1 = __ldg(&S.nodes[4 * node + 1]);
-    const float4 n2 = __ldg(&S.nodes[4 * node + 2]);
-    const float4 n3 = __ldg(&S.nodes[4 * node + 3]);
-    const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-    float ta, tb;
-    bool ha = box_test(w, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmax, ta);
-    bool hb = box_test(w, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmax, tb);
-    if (ha && c0 < 0) {
-      const int k = ~c0;
-      float t, b1, b2;
-      ++tc.tris;
-      if (tri_test(w, xyz(__ldg(&S.tris[3 * k])), xyz(__ldg(&S.tris[3 * k + 1])), xyz(__ldg(&S.tris[3 * k + 2])), t,
-                   b1, b2) &&
-          t < tmax)
-        return true;
-      ha = false;
-    }
-    if (hb && c1 < 0) {
-      const int k = ~c1;
-      float t, b1, b2;
-      ++tc.tris;
-      if (tri_test(w, xyz(__ldg(&S.tris[3 * k])), xyz(__ldg(&S.tris[3 * k + 1])), xyz(__ldg(&S.tris[3 * k + 2])), t,
-                   b1, b2) &&
-          t < tmax)
-        return true;
-      hb = false;
-    }
-    if (ha && hb) {
-      if (sp >= kStack) {
-        atomicOr(status, SC_STATUS_STACK_OVERFLOW);
-        return false;
-      }
-      stack[sp++] = c1;
-      node = c0;
-    } else if (ha) {
-      node = c0;
-    } else if (hb) {
-      node = c1;
-    } else {
-      if (sp == 0) return false;
-      node = stack[--sp];
-    }
-  }
+__device__ __forceinline__ Hit closest_hit(const DevScene &S, float3 o, float3 d, float tmax, unsigned *status,
+                                           TravCount &tc) {
+  return trace(S, o, d, tmax, false, status, tc);
+}
+__device__ __forceinline__ bool any_hit(const DevScene &S, float3 o, float3 d, float tmax, unsigned *status,
+                                        TravCount &tc) {
+  return trace(S, o, d, tmax, true, status, tc).prim >= 0;
 }
 
 // ------------------------------------------------------------------------------------------

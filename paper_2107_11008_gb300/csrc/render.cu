@@ -15,163 +15,244 @@
 namespace sc {
 
 constexpr int kBlock = 128;
+// resident blocks per SM the camera kernel is compiled for (register budget = 64K / (128 * this))
+#ifndef SC_CAM_MIN_BLOCKS
+#define SC_CAM_MIN_BLOCKS 1
+#endif
 
-struct PathOut {
-  float3 L;
-  uint32_t first, sig, nq, nspec;
+// Camera paths as a per-lane state machine.  Every loop iteration each live lane traces exactly
+// one ray -- an extension ray or the shadow ray of its pending next-event estimate -- through the
+// same traversal call, then advances its path by one event.  A lane whose path ends starts its
+// pixel's next sample at once, and a lane whose pixel is done takes the next pixel from a global
+// ticket (warp-aggregated), so lanes never wait for the longest path of their warp.  The event
+// order, and therefore every random number, decision and signature, is that of the
+// straightforward per-path loop: hit -> (emission | dielectric scatter | NEE -> shadow result
+// -> bounce).
+enum : int { M_IDLE = 0, M_EXTEND = 1, M_SHADOW = 2 };
+enum : uint32_t {
+  F_SPEC_ONLY = 1u, F_DIFFUSE_FIRST = 2u, F_LAST_SPECULAR = 4u, F_FIXUP = 8u, F_HAS_NEXT = 16u
 };
 
-// One camera path of pixel (px, py), global sample index `sample`.
-__device__ __forceinline__ PathOut camera_path(const DevScene &S, const Cam &cam, const float3 *wts,
-                                               const sc_trace_params &P, int px, int py, uint32_t sample,
-                                               unsigned *status, uint32_t &bin_out, TravCount &tc) {
-  const uint32_t pix = (uint32_t)(py * cam.W + px);
-  const uint4 x0 = draw(P.seed, pix, sample, 0u, 0u, (uint32_t)P.scene_index);
-  const int bin = choose(x0.z, P.n_bins > 0 ? P.n_bins : 1);
-  bin_out = (uint32_t)bin;
-  float3 o = cam.eye;
-  float3 d = cam_dir(cam, (px + u01(x0.x)) / cam.W, (py + u01(x0.y)) / cam.H);
-  float3 beta = f3(1.f, 1.f, 1.f), L = f3(0.f, 0.f, 0.f);
-  bool spec_only = true, diffuse_first = false, last_specular = false;
-  int n_diffuse = 0;
-  PathOut out;
-  out.sig = 2166136261u;
-  out.first = kMiss;
-  out.nq = 0;
-  out.nspec = 0;
-  const float3 env = f3(S.env);
-  for (int k = 0; k < P.max_depth; ++k) {
-    const Hit h = closest_hit(S, o, d, 3.0e38f, status, tc);
-    ++out.nq;
-    out.sig = fnv(out.sig, h.id);
-    if (k == 0) out.first = h.id;
-    if (h.prim < 0) {
-      L = L + beta * env;
-      break;
-    }
-    const Surf f = interact(S, d, h);
-    const sc_material m = S.mats[f.mat];
-    if (m.kind == SC_MAT_EMISSIVE) {
-      const bool count = spec_only || ((P.flags & SC_FLAG_EMITTER_AFTER_DS) && diffuse_first && n_diffuse == 1 &&
-                                       last_specular);
-      if (f.cosg < 0.0f && count) L = L + beta * f3(m.emission);
-      break;
-    }
-    const uint4 xs = draw(P.seed, pix, sample, (uint32_t)(k + 1), 1u, (uint32_t)P.scene_index);
-    if (m.kind == SC_MAT_DIELECTRIC) {
-      bool refl, fix;
-      const float nl = cauchy(m.cauchy_a, m.cauchy_b, bin, P.n_bins);
-      const float3 nd = dielectric(f, d, nl, u01(xs.x), P.flags, refl, fix);
-      out.sig = fnv(out.sig, refl ? EV_REFLECT : EV_REFRACT);
-      if (fix) out.sig = fnv(out.sig, EV_FIXUP);
-      ++out.nspec;
-      last_specular = true;
-      o = offset_along(f.p, f.ng, nd);
-      d = nd;
-      continue;
-    }
-    // diffuse: next-event estimation
-    const float3 alb = albedo_at(S, m, f);
-    bool lit = false;
-    if (S.n_lights > 0) {
-      const uint4 xn = draw(P.seed, pix, sample, (uint32_t)(k + 1), 2u, (uint32_t)P.scene_index);
-      const int j = choose(xn.x, S.n_lights);
-      const sc_light Lg = S.lights[j];
-      float3 lp, le = f3(Lg.power);
-      float geo = 0.0f;
-      bool ok = false;
-      if (Lg.kind == SC_LIGHT_POINT) {
-        lp = f3(Lg.p);
-        float3 w = lp - f.p;
-        const float d2 = dot(w, w);
-        w = w * (1.0f / sqrtf(d2));
-        const float cs = dot(f.nsf, w), cg = dot(f.ngf, w);
-        ok = cs > 0.0f && cg > 0.0f;
-        geo = cs / d2;
-      } else if (Lg.kind == SC_LIGHT_RECT) {
-        const float3 eu = f3(Lg.u), ev = f3(Lg.v);
-        lp = f3(Lg.p) + eu * u01(xn.y) + ev * u01(xn.z);
-        const float3 c = cross(eu, ev);
-        const float area = length(c);
-        const float3 nlt = c * (1.0f / area);
-        float3 w = lp - f.p;
-        const float d2 = dot(w, w);
-        w = w * (1.0f / sqrtf(d2));
-        const float cs = dot(f.nsf, w), cg = dot(f.ngf, w), cl = -dot(nlt, w);
-        ok = cs > 0.0f && cg > 0.0f && cl > 0.0f;
-        geo = cs * cl * area / d2;
-      }
-      if (ok) {
-        const float3 so = f.p + f.ngf * eps_of(f.p);
-        const float3 wv = lp - so;
-        const float dist = length(wv);
-        if (!any_hit(S, so, wv * (1.0f / dist), dist * (1.0f - 1e-4f), status, tc)) {
-          lit = true;
-          L = L + beta * (alb * le) * (geo * (float)S.n_lights / kPi);
-        }
-      }
-    }
-    out.sig = fnv(out.sig, lit ? EV_LIT : EV_UNLIT);
-    if (k == 0) diffuse_first = true;
-    ++n_diffuse;
-    spec_only = false;
-    last_specular = false;
-    if (k == P.max_depth - 1) break;
-    float3 nd = cosine_dir(f.nsf, u01(xs.y), u01(xs.z));
-    if (!(dot(nd, f.ngf) > 0.0f)) {
-      nd = cosine_dir(f.ngf, u01(xs.y), u01(xs.z));
-      out.sig = fnv(out.sig, EV_FIXUP);
-    }
-    beta = beta * alb;
-    o = f.p + f.ngf * eps_of(f.p);
-    d = nd;
-  }
-  out.L = L * wts[bin];
-  return out;
-}
-
-// Persistent camera kernel: each warp takes 8x4 pixel tiles from a global ticket and each
-// lane traces every sample of its pixel, accumulating in registers (no atomics, fixed order).
-__global__ void __launch_bounds__(kBlock) k_trace_camera(DevScene S, sc_trace_params P, sc_frame F,
+__global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS) k_trace_camera(DevScene S, sc_trace_params P, sc_frame F,
                                                          unsigned *status, unsigned *ticket,
                                                          unsigned long long *counters) {
   TravCount tc;
   __shared__ float3 wts[kMaxBins];
   spectral_table(wts, P.n_bins);
   const Cam cam = make_cam(S.cam);
-  const int tiles_x = (cam.W + 7) / 8, tiles_y = (cam.H + 3) / 4;
-  const unsigned n_tiles = (unsigned)(tiles_x * tiles_y);
+  const int tiles_x = (cam.W + 7) / 8;
+  const unsigned n_tiles = (unsigned)(tiles_x * ((cam.H + 3) / 4));
+  const unsigned n_tickets = n_tiles * 32u;
   const int lane = threadIdx.x & 31;
+  const float3 env = f3(S.env);
+  const int nb = P.n_bins > 0 ? P.n_bins : 1;
+
+  // pixel state
+  int px = 0, py = 0, pix = -1, s = 0;
+  bool done = false;
+  float3 acc = f3(0.f, 0.f, 0.f);
+  // path state
+  int mode = M_IDLE, k = 0, bin = 0, n_diffuse = 0;
+  uint32_t fl = 0, sig = 0, first = kMiss, nq = 0, nspec = 0;
+  float3 o = f3(0.f, 0.f, 0.f), d = o, beta = o, L = o, nee = o, o2 = o, d2 = o;
+  float tmax = 3.0e38f;
+
   for (;;) {
-    unsigned tile = 0;
-    if (lane == 0) tile = atomicAdd(ticket, 1u);
-    tile = __shfl_sync(0xFFFFFFFFu, tile, 0);
-    if (tile >= n_tiles) break;
-    const int px = (int)(tile % tiles_x) * 8 + (lane & 7);
-    const int py = (int)(tile / tiles_x) * 4 + (lane >> 3);
-    if (px >= cam.W || py >= cam.H) continue;
-    float3 acc = f3(0.f, 0.f, 0.f);
-    const int pix = py * cam.W + px;
-    for (int s = 0; s < P.spp; ++s) {
-      uint32_t bin;
-      const PathOut po = camera_path(S, cam, wts, P, px, py, (uint32_t)(P.sample_offset + s), status, bin, tc);
-      acc = acc + po.L;
-      if (F.path_records) {
-        sc_path_record r;
-        r.L[0] = po.L.x; r.L[1] = po.L.y; r.L[2] = po.L.z;
-        r.first_tri = po.first;
-        r.signature = po.sig;
-        r.n_queries = po.nq;
-        r.bin = bin;
-        r.n_specular = po.nspec;
-        F.path_records[(int64_t)pix * P.spp + s] = r;
+    // ---- refill: next sample of this pixel, or the next pixel ----
+    if (mode == M_IDLE && pix >= 0 && s >= P.spp) {
+      if (F.accum_camera) {
+        float4 *a = reinterpret_cast<float4 *>(F.accum_camera) + pix;
+        float4 v = *a;
+        v.x += acc.x; v.y += acc.y; v.z += acc.z;
+        *a = v;
+      }
+      pix = -1;
+    }
+    const bool want = mode == M_IDLE && pix < 0 && !done;
+    const unsigned wmask = __ballot_sync(0xFFFFFFFFu, want);
+    if (wmask) {
+      const int leader = __ffs(wmask) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(ticket, (unsigned)__popc(wmask));
+      base = __shfl_sync(0xFFFFFFFFu, base, leader);
+      if (want) {
+        const unsigned t = base + (unsigned)__popc(wmask & ((1u << lane) - 1u));
+        bool got = false;
+        if (t < n_tickets) {
+          const unsigned tile = t >> 5, in = t & 31u;
+          px = (int)(tile % tiles_x) * 8 + (int)(in & 7u);
+          py = (int)(tile / tiles_x) * 4 + (int)(in >> 3);
+          got = px < cam.W && py < cam.H;
+        } else {
+          done = true;
+        }
+        if (got) {
+          pix = py * cam.W + px;
+          s = 0;
+          acc = f3(0.f, 0.f, 0.f);
+        }
       }
     }
-    if (F.accum_camera) {
-      float4 *a = reinterpret_cast<float4 *>(F.accum_camera) + pix;
-      float4 v = *a;
-      v.x += acc.x; v.y += acc.y; v.z += acc.z;
-      *a = v;
+    if (mode == M_IDLE && pix >= 0 && s < P.spp) {
+      // start sample s: primary ray (tag 0: jitter x, jitter y, wavelength bin)
+      const uint4 x0 = draw(P.seed, (uint32_t)pix, (uint32_t)(P.sample_offset + s), 0u, 0u, (uint32_t)P.scene_index);
+      bin = choose(x0.z, nb);
+      o = cam.eye;
+      d = cam_dir(cam, (px + u01(x0.x)) / cam.W, (py + u01(x0.y)) / cam.H);
+      tmax = 3.0e38f;
+      beta = f3(1.f, 1.f, 1.f);
+      L = f3(0.f, 0.f, 0.f);
+      fl = F_SPEC_ONLY;
+      n_diffuse = 0;
+      sig = 2166136261u;
+      first = kMiss;
+      nq = 0;
+      nspec = 0;
+      k = 0;
+      mode = M_EXTEND;
+    }
+    if (__all_sync(0xFFFFFFFFu, mode == M_IDLE && done)) break;
+    if (mode == M_IDLE) continue;  // a lane whose ticket fell outside the image retries
+
+    // ---- one ray per lane ----
+    const Hit h = trace(S, o, d, tmax, mode == M_SHADOW, status, tc);
+
+    bool finish = false;
+    if (mode == M_SHADOW) {
+      const bool lit = h.prim < 0;
+      if (lit) L = L + nee;
+      sig = fnv(sig, lit ? EV_LIT : EV_UNLIT);
+      if (fl & F_FIXUP) sig = fnv(sig, EV_FIXUP);
+      if (fl & F_HAS_NEXT) {
+        o = o2;
+        d = d2;
+        tmax = 3.0e38f;
+        mode = M_EXTEND;
+      } else {
+        finish = true;
+      }
+    } else {
+      ++nq;
+      sig = fnv(sig, h.id);
+      if (k == 0) first = h.id;
+      if (h.prim < 0) {
+        L = L + beta * env;
+        finish = true;
+      } else {
+        const Surf f = interact(S, d, h);
+        const sc_material m = S.mats[f.mat];
+        if (m.kind == SC_MAT_EMISSIVE) {
+          const bool count = (fl & F_SPEC_ONLY) || ((P.flags & SC_FLAG_EMITTER_AFTER_DS) && (fl & F_DIFFUSE_FIRST) &&
+                                                    n_diffuse == 1 && (fl & F_LAST_SPECULAR));
+          if (f.cosg < 0.0f && count) L = L + beta * f3(m.emission);
+          finish = true;
+        } else {
+          const uint32_t pixu = (uint32_t)pix, smp = (uint32_t)(P.sample_offset + s);
+          const uint4 xs = draw(P.seed, pixu, smp, (uint32_t)(k + 1), 1u, (uint32_t)P.scene_index);
+          if (m.kind == SC_MAT_DIELECTRIC) {
+            bool refl, fix;
+            const float nl = cauchy(m.cauchy_a, m.cauchy_b, bin, P.n_bins);
+            const float3 nd = dielectric(f, d, nl, u01(xs.x), P.flags, refl, fix);
+            sig = fnv(sig, refl ? EV_REFLECT : EV_REFRACT);
+            if (fix) sig = fnv(sig, EV_FIXUP);
+            ++nspec;
+            fl |= F_LAST_SPECULAR;
+            o = offset_along(f.p, f.ng, nd);
+            d = nd;
+            ++k;
+            if (k >= P.max_depth) finish = true;
+          } else {
+            // diffuse: next-event estimate (shadow ray traced next iteration), then the bounce
+            const float3 alb = albedo_at(S, m, f);
+            bool need_shadow = false;
+            float3 so = f3(0.f, 0.f, 0.f), sd = so;
+            float sdist = 0.0f;
+            if (S.n_lights > 0) {
+              const uint4 xn = draw(P.seed, pixu, smp, (uint32_t)(k + 1), 2u, (uint32_t)P.scene_index);
+              const sc_light Lg = S.lights[choose(xn.x, S.n_lights)];
+              float3 lp = f3(0.f, 0.f, 0.f);
+              float geo = 0.0f;
+              bool ok = false;
+              if (Lg.kind == SC_LIGHT_POINT) {
+                lp = f3(Lg.p);
+                float3 w = lp - f.p;
+                const float d2l = dot(w, w);
+                w = w * (1.0f / sqrtf(d2l));
+                const float cs = dot(f.nsf, w), cg = dot(f.ngf, w);
+                ok = cs > 0.0f && cg > 0.0f;
+                geo = cs / d2l;
+              } else if (Lg.kind == SC_LIGHT_RECT) {
+                const float3 eu = f3(Lg.u), ev = f3(Lg.v);
+                lp = f3(Lg.p) + eu * u01(xn.y) + ev * u01(xn.z);
+                const float3 c = cross(eu, ev);
+                const float area = length(c);
+                const float3 nlt = c * (1.0f / area);
+                float3 w = lp - f.p;
+                const float d2l = dot(w, w);
+                w = w * (1.0f / sqrtf(d2l));
+                const float cs = dot(f.nsf, w), cg = dot(f.ngf, w), cl = -dot(nlt, w);
+                ok = cs > 0.0f && cg > 0.0f && cl > 0.0f;
+                geo = cs * cl * area / d2l;
+              }
+              if (ok) {
+                so = f.p + f.ngf * eps_of(f.p);
+                const float3 wv = lp - so;
+                sdist = length(wv);
+                sd = wv * (1.0f / sdist);
+                nee = beta * (alb * f3(Lg.power)) * (geo * (float)S.n_lights / kPi);
+                need_shadow = true;
+              }
+            }
+            if (k == 0) fl |= F_DIFFUSE_FIRST;
+            ++n_diffuse;
+            fl &= ~(F_SPEC_ONLY | F_LAST_SPECULAR | F_FIXUP | F_HAS_NEXT);
+            if (k < P.max_depth - 1) {
+              float3 nd = cosine_dir(f.nsf, u01(xs.y), u01(xs.z));
+              if (!(dot(nd, f.ngf) > 0.0f)) {
+                nd = cosine_dir(f.ngf, u01(xs.y), u01(xs.z));
+                fl |= F_FIXUP;
+              }
+              beta = beta * alb;
+              o2 = f.p + f.ngf * eps_of(f.p);
+              d2 = nd;
+              fl |= F_HAS_NEXT;
+            }
+            ++k;
+            if (need_shadow) {
+              o = so;
+              d = sd;
+              tmax = sdist * (1.0f - 1e-4f);
+              mode = M_SHADOW;
+            } else {
+              sig = fnv(sig, EV_UNLIT);
+              if (fl & F_FIXUP) sig = fnv(sig, EV_FIXUP);
+              if (fl & F_HAS_NEXT) {
+                o = o2;
+                d = d2;
+                tmax = 3.0e38f;
+              } else {
+                finish = true;
+              }
+            }
+          }
+        }
+      }
+    }
+    if (finish) {
+      const float3 Lw = L * wts[bin];
+      acc = acc + Lw;
+      if (F.path_records) {
+        sc_path_record r;
+        r.L[0] = Lw.x; r.L[1] = Lw.y; r.L[2] = Lw.z;
+        r.first_tri = first;
+        r.signature = sig;
+        r.n_queries = nq;
+        r.bin = (uint32_t)bin;
+        r.n_specular = nspec;
+        F.path_records[(int64_t)pix * P.spp + s] = r;
+      }
+      ++s;
+      mode = M_IDLE;
     }
   }
   if (counters) {
