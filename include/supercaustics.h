@@ -228,6 +228,31 @@ int sc_scene_get_info(const sc_scene *scene, sc_scene_info *info);
  * of the first holding the input triangle index as int bits).  Synchronises. */
 int sc_scene_export_bvh(sc_ctx *ctx, const sc_scene *scene, void *nodes_host, void *tris_host);
 
+/* --- LBVH build without device allocation --------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot allocate
+ * device memory while they run (a fixed, pre-committed memory budget, or no tolerance for the
+ * synchronisation that freeing device memory can cause).  It runs the same LBVH kernels as
+ * sc_build_scene, but into buffers the caller owns, with its scratch in one static __device__
+ * array of SC_NOALLOC_MAX_TRIS triangles' worth (about 3 MB, held by every GPU that loads the
+ * library until the process exits).  It calls no cudaMalloc / cudaFree and no allocating
+ * library routine.
+ *   Inputs (device): positions n_verts*3, normals or NULL, uvs or NULL, indices n_tris*3,
+ *   tri_object n_tris, object_material n_objects -- as in sc_scene_desc, all indices valid.
+ *   Outputs (device, caller-owned, 16-byte aligned): nodes 16*max(n_tris-1,1) floats,
+ *   tris 12*n_tris floats, shade 12*n_tris floats, shade2 4*n_tris floats, tri_obj n_tris ints,
+ *   laid out exactly as in sc_scene_export_bvh (nodes, tris) and the scene's internal tables.
+ * Returns SC_ERR_INVALID_ARG (with a message) if n_tris is outside [1, SC_NOALLOC_MAX_TRIS].
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device made current) and caches it; make that first call before any stream capture.
+ * Every call shares the one array and it keeps the last call's contents (each build overwrites
+ * what it reads), so calls that overlap on the GPU -- other streams, other host threads --
+ * race: serialise them. */
+#define SC_NOALLOC_MAX_TRIS 32768
+int sc_build_bvh_noalloc(sc_ctx *ctx, const float *positions, const float *normals, const float *uvs,
+                         const int32_t *indices, const int32_t *tri_object, const int32_t *object_material,
+                         int32_t n_objects, int32_t n_tris, float *nodes, float *tris, float *shade,
+                         float *shade2, int32_t *tri_obj);
+
 /* --- queries --------------------------------------------------------------------------- */
 /* Closest hit for n rays.  rays: device float[n][8] = (ox,oy,oz,tmax, dx,dy,dz,0);
  * hits: device float[n][4] = (t, tri as int bits (input order, -1 miss), b1, b2). */

@@ -76,6 +76,13 @@ bool valid_scene(const sc_scene *s) { return s && s->dev.nodes; }
 
 }  // namespace
 
+namespace sc {
+// context accessors for the other translation units
+int ctx_device(const sc_ctx *c) { return c->device; }
+cudaStream_t ctx_stream(const sc_ctx *c) { return c->stream; }
+void ctx_set_error(sc_ctx *c, const std::string &msg) { c->err = msg; }
+}  // namespace sc
+
 extern "C" {
 
 int sc_abi_version(void) { return SC_ABI_VERSION; }

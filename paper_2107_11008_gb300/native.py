@@ -110,6 +110,7 @@ SIGNATURES = {
     "sc_free_scene": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sc_scene_get_info": (C.c_int, [C.c_void_p, P(sc_scene_info)]),
     "sc_scene_export_bvh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sc_build_bvh_noalloc": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.c_int32, C.c_int32] + [C.c_void_p] * 5),
     "sc_intersect": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "sc_occluded": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "sc_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int64, C.c_void_p]),
