@@ -37,9 +37,9 @@ FLOPS_PER_NODE = 24
 FLOPS_PER_TRI = 43
 BYTES_PER_NODE = 64
 BYTES_PER_TRI = 48
-# our kernels per step: LBVH build (bounds init, gather, morton, 4 x (hist, scan, scatter),
+# our kernels per step: LBVH build (bounds init, gather, morton, 8 x (hist, scan, scatter),
 # reorder, karras, refit, depth) + camera + lights + resolve
-LAUNCHES_PER_STEP = 18 + 3
+LAUNCHES_PER_STEP = 30 + 3
 
 
 def parse():

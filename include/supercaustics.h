@@ -233,7 +233,7 @@ int sc_scene_export_bvh(sc_ctx *ctx, const sc_scene *scene, void *nodes_host, vo
  * device memory while they run (a fixed, pre-committed memory budget, or no tolerance for the
  * synchronisation that freeing device memory can cause).  It runs the same LBVH kernels as
  * sc_build_scene, but into buffers the caller owns, with its scratch in one static __device__
- * array of SC_NOALLOC_MAX_TRIS triangles' worth (about 3 MB, held by every GPU that loads the
+ * array of SC_NOALLOC_MAX_TRIS triangles' worth (about 3.3 MB, held by every GPU that loads the
  * library until the process exits).  It calls no cudaMalloc / cudaFree and no allocating
  * library routine.
  *   Inputs (device): positions n_verts*3, normals or NULL, uvs or NULL, indices n_tris*3,

@@ -257,7 +257,7 @@ int sc_build_scene(sc_ctx *c, const sc_scene_desc *d, sc_scene **out) {
   T.take<float4>(sizeof(float4) * 3 * nt);
   T.take<float4>(sizeof(float4) * nt);
   T.take<uint32_t>(sizeof(uint32_t) * 8);
-  for (int k = 0; k < 4; ++k) T.take<uint32_t>(sizeof(uint32_t) * nt);
+  for (int k = 0; k < 4; ++k) T.take<unsigned long long>(sizeof(unsigned long long) * nt);
   T.take<uint32_t>(sizeof(uint32_t) * 256 * nb);
   T.take<int32_t>(sizeof(int32_t) * 2 * nt);
   T.take<int32_t>(sizeof(int32_t) * nt);
@@ -308,8 +308,8 @@ int sc_build_scene(sc_ctx *c, const sc_scene_desc *d, sc_scene **out) {
   b.tris_in = U.take<float4>(sizeof(float4) * 3 * nt);
   b.centroids = U.take<float4>(sizeof(float4) * nt);
   b.bounds = U.take<uint32_t>(sizeof(uint32_t) * 8);
-  b.keys = U.take<uint32_t>(sizeof(uint32_t) * nt);
-  b.keys_alt = U.take<uint32_t>(sizeof(uint32_t) * nt);
+  b.keys = U.take<unsigned long long>(sizeof(unsigned long long) * nt);
+  b.keys_alt = U.take<unsigned long long>(sizeof(unsigned long long) * nt);
   b.vals = U.take<uint32_t>(sizeof(uint32_t) * nt);
   b.vals_alt = U.take<uint32_t>(sizeof(uint32_t) * nt);
   b.hist = U.take<uint32_t>(sizeof(uint32_t) * 256 * nb);

@@ -3,8 +3,10 @@
 // Steps (one kernel each, all on the caller's stream):
 //   1. gather: triangles from the indexed arrays into float4 vertex triples, shading
 //      attributes, centroids, and the centroid bounds (block reduce + sortable-int atomics).
-//   2. morton: 30-bit Morton code of each centroid in the normalised bounds (10 bits/axis).
-//   3. radix sort of (code, index), least-significant digit first, 4 passes of 8 bits; each
+//   2. morton: 63-bit Morton code of each centroid in the normalised bounds (21 bits/axis;
+//      10 bits/axis would give ~2 cm cells over a 20 m backdrop, coarser than the glass
+//      triangles, and a poor hierarchy over them).
+//   3. radix sort of (code, index), least-significant digit first, 8 passes of 8 bits; each
 //      pass is histogram -> exclusive scan -> stable scatter (the tile is ranked by 8 one-bit
 //      stable splits in shared memory), so equal codes keep input order.
 //   4. reorder: triangles into leaf order.
@@ -20,7 +22,7 @@
 namespace sc {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;
+constexpr int kSortItems = 4;
 constexpr int kTile = kSortThreads * kSortItems;
 
 size_t sort_blocks(int32_t n) { return (size_t)((n + kTile - 1) / kTile); }
@@ -93,12 +95,14 @@ __global__ void k_gather(BuildBuffers b) {
   }
 }
 
-// spread the low 10 bits of v to every third bit
-__device__ __forceinline__ uint32_t spread3(uint32_t v) {
-  v = (v * 0x00010001u) & 0xFF0000FFu;
-  v = (v * 0x00000101u) & 0x0F00F00Fu;
-  v = (v * 0x00000011u) & 0xC30C30C3u;
-  v = (v * 0x00000005u) & 0x49249249u;
+// spread the low 21 bits of v to every third bit of a 64-bit word
+__device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
+  v &= 0x1FFFFFull;
+  v = (v | (v << 32)) & 0x1F00000000FFFFull;
+  v = (v | (v << 16)) & 0x1F0000FF0000FFull;
+  v = (v | (v << 8)) & 0x100F00F00F00F00Full;
+  v = (v | (v << 4)) & 0x10C30C30C30C30C3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
   return v;
 }
 
@@ -113,20 +117,20 @@ __global__ void k_morton(BuildBuffers b) {
   for (int k = 0; k < 3; ++k) {
     const float ext = h[k] - l[k];
     const float u = ext > 0.0f ? (cc[k] - l[k]) / ext : 0.5f;
-    q[k] = (uint32_t)fminf(fmaxf(u * 1024.0f, 0.0f), 1023.0f);
+    q[k] = (uint32_t)fminf(fmaxf(u * 2097152.0f, 0.0f), 2097151.0f);
   }
   b.keys[t] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
   b.vals[t] = (uint32_t)t;
 }
 
-__global__ void k_sort_hist(const uint32_t *keys, int32_t n, int shift, uint32_t *hist, int nblocks) {
+__global__ void k_sort_hist(const unsigned long long *keys, int32_t n, int shift, uint32_t *hist, int nblocks) {
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
   const int base = blockIdx.x * kTile;
   for (int j = 0; j < kSortItems; ++j) {
     const int i = base + j * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xFFu], 1u);
+    if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 0xFFu], 1u);
   }
   __syncthreads();
   hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
@@ -171,9 +175,9 @@ __global__ void k_scan(uint32_t *data, int n) {
   }
 }
 
-__global__ void k_sort_scatter(const uint32_t *keys, const uint32_t *vals, uint32_t *keys_out, uint32_t *vals_out,
-                               int32_t n, int shift, const uint32_t *hist, int nblocks) {
-  __shared__ uint32_t sk[2][kTile];
+__global__ void k_sort_scatter(const unsigned long long *keys, const uint32_t *vals, unsigned long long *keys_out,
+                               uint32_t *vals_out, int32_t n, int shift, const uint32_t *hist, int nblocks) {
+  __shared__ unsigned long long sk[2][kTile];
   __shared__ uint32_t sv[2][kTile];
   __shared__ uint32_t ws[32];
   __shared__ uint32_t start[256];
@@ -184,7 +188,7 @@ __global__ void k_sort_scatter(const uint32_t *keys, const uint32_t *vals, uint3
   for (int j = 0; j < kSortItems; ++j) {
     const int l = j * kSortThreads + threadIdx.x;
     const int i = base + l;
-    sk[0][l] = i < n ? keys[i] : 0xFFFFFFFFu;
+    sk[0][l] = i < n ? keys[i] : ~0ull;
     sv[0][l] = i < n ? vals[i] : 0xFFFFFFFFu;
   }
   cnt[threadIdx.x] = 0;
@@ -193,17 +197,18 @@ __global__ void k_sort_scatter(const uint32_t *keys, const uint32_t *vals, uint3
   // 8 stable one-bit splits on the digit; thread t owns items 8t .. 8t+7 (in tile order)
   for (int bit = 0; bit < 8; ++bit) {
     uint32_t zeros = 0;
-    uint32_t k[kSortItems], v[kSortItems];
+    unsigned long long k[kSortItems];
+    uint32_t v[kSortItems];
     for (int j = 0; j < kSortItems; ++j) {
       k[j] = sk[cur][threadIdx.x * kSortItems + j];
       v[j] = sv[cur][threadIdx.x * kSortItems + j];
-      zeros += ((k[j] >> (shift + bit)) & 1u) ? 0u : 1u;
+      zeros += ((k[j] >> (shift + bit)) & 1ull) ? 0u : 1u;
     }
     uint32_t total_zeros;
     const uint32_t zpre = block_scan(zeros, ws, &total_zeros);
     uint32_t z = zpre, o = total_zeros + threadIdx.x * kSortItems - zpre;
     for (int j = 0; j < kSortItems; ++j) {
-      const bool one = (k[j] >> (shift + bit)) & 1u;
+      const bool one = (k[j] >> (shift + bit)) & 1ull;
       const uint32_t dst = one ? o++ : z++;
       sk[cur ^ 1][dst] = k[j];
       sv[cur ^ 1][dst] = v[j];
@@ -214,7 +219,7 @@ __global__ void k_sort_scatter(const uint32_t *keys, const uint32_t *vals, uint3
   // local digit starts
   for (int j = 0; j < kSortItems; ++j) {
     const int l = threadIdx.x * kSortItems + j;
-    if (l < count) atomicAdd(&cnt[(sk[cur][l] >> shift) & 0xFFu], 1u);
+    if (l < count) atomicAdd(&cnt[(uint32_t)(sk[cur][l] >> shift) & 0xFFu], 1u);
   }
   __syncthreads();
   uint32_t tot;
@@ -224,8 +229,8 @@ __global__ void k_sort_scatter(const uint32_t *keys, const uint32_t *vals, uint3
   for (int j = 0; j < kSortItems; ++j) {
     const int l = j * kSortThreads + threadIdx.x;
     if (l < count) {
-      const uint32_t key = sk[cur][l];
-      const uint32_t d = (key >> shift) & 0xFFu;
+      const unsigned long long key = sk[cur][l];
+      const uint32_t d = (uint32_t)(key >> shift) & 0xFFu;
       const uint32_t pos = hist[d * nblocks + blockIdx.x] + (uint32_t)l - start[d];
       keys_out[pos] = key;
       vals_out[pos] = sv[cur][l];
@@ -243,14 +248,14 @@ __global__ void k_reorder(BuildBuffers b, const uint32_t *order) {
 }
 
 // longest common prefix of sorted keys i and j (index bits break ties), -1 outside
-__device__ __forceinline__ int delta(const uint32_t *keys, int n, int i, int j) {
+__device__ __forceinline__ int delta(const unsigned long long *keys, int n, int i, int j) {
   if (j < 0 || j >= n) return -1;
-  const uint32_t a = keys[i], b = keys[j];
-  if (a == b) return 32 + __clz((uint32_t)i ^ (uint32_t)j);
-  return __clz(a ^ b);
+  const unsigned long long a = keys[i], b = keys[j];
+  if (a == b) return 64 + __clz((uint32_t)i ^ (uint32_t)j);
+  return __clzll(a ^ b);
 }
 
-__global__ void k_karras(BuildBuffers b, const uint32_t *keys) {
+__global__ void k_karras(BuildBuffers b, const unsigned long long *keys) {
   const int n = b.n_tris;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
@@ -357,14 +362,15 @@ cudaError_t launch_build(const BuildBuffers &b, cudaStream_t s) {
   k_morton<<<G, T, 0, s>>>(b);
   SC_TRY(cudaGetLastError());
   const int nb = (int)sort_blocks(n);
-  uint32_t *ka = b.keys, *kb = b.keys_alt, *va = b.vals, *vb = b.vals_alt;
-  for (int pass = 0; pass < 4; ++pass) {
+  unsigned long long *ka = b.keys, *kb = b.keys_alt;
+  uint32_t *va = b.vals, *vb = b.vals_alt;
+  for (int pass = 0; pass < 8; ++pass) {
     const int shift = 8 * pass;
     k_sort_hist<<<nb, kSortThreads, 0, s>>>(ka, n, shift, b.hist, nb);
     k_scan<<<1, 1024, 0, s>>>(b.hist, 256 * nb);
     k_sort_scatter<<<nb, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, b.hist, nb);
-    uint32_t *t = ka; ka = kb; kb = t;
-    t = va; va = vb; vb = t;
+    unsigned long long *tk = ka; ka = kb; kb = tk;
+    uint32_t *tv = va; va = vb; vb = tv;
   }
   SC_TRY(cudaGetLastError());
   // after an even number of passes the sorted data is back in keys / vals

@@ -324,6 +324,92 @@ static __device__ __forceinline__ Hit trace(const DevScene &S, float3 o, float3 
   return h;
 }
 
+// Resumable form of trace(): the query's state lives with the caller and each call visits at
+// most `budget` nodes, so a persistent kernel can interleave other lanes' shading with long
+// traversals.  Results are identical to trace() (same visit order, same tie-break).
+struct TravState {
+  Hit h;
+  int node, sp, visits;
+  bool anyhit;
+};
+__device__ __forceinline__ void trav_begin(TravState &ts, float tmax, bool anyhit) {
+  ts.h.t = tmax;
+  ts.h.prim = -1;
+  ts.h.id = kMiss;
+  ts.h.b1 = ts.h.b2 = 0.0f;
+  ts.node = 0;
+  ts.sp = 0;
+  ts.visits = 0;
+  ts.anyhit = anyhit;
+}
+// Returns true when the query is complete (ts.h holds the answer; prim < 0 = miss).
+__device__ __forceinline__ bool trav_step(const DevScene &S, const WRay &w, float tmax, TravState &ts, int *stack,
+                                          int budget, unsigned *status, TravCount &tc) {
+  if (S.n_tris <= 0) return true;
+  for (int it = 0; it < budget; ++it) {
+    ++tc.nodes;
+    if (++ts.visits > kMaxVisits) {
+      atomicOr(status, SC_STATUS_WATCHDOG);
+      ts.h.prim = -1;
+      ts.h.id = kMiss;
+      ts.h.t = tmax;
+      return true;
+    }
+    const int node = ts.node;
+    const float4 n0 = __ldg(&S.nodes[4 * node + 0]);
+    const float4 n1 = __ldg(&S.nodes[4 * node + 1]);
+    const float4 n2 = __ldg(&S.nodes[4 * node + 2]);
+    const float4 n3 = __ldg(&S.nodes[4 * node + 3]);
+    const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+    float ta, tb;
+    bool ha = box_test(w, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, ts.h.t, ta);
+    bool hb = box_test(w, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, ts.h.t, tb);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const bool hit_box = side == 0 ? ha : hb;
+      const int c = side == 0 ? c0 : c1;
+      if (hit_box && c < 0) {
+        const int k = ~c;
+        const float4 a = __ldg(&S.tris[3 * k]), b = __ldg(&S.tris[3 * k + 1]), cc = __ldg(&S.tris[3 * k + 2]);
+        float t, b1, b2;
+        ++tc.tris;
+        if (tri_test(w, xyz(a), xyz(b), xyz(cc), t, b1, b2)) {
+          const uint32_t id = (uint32_t)__float_as_int(a.w);
+          if (t < ts.h.t || (!ts.anyhit && t == ts.h.t && id < ts.h.id)) {
+            ts.h.t = t; ts.h.b1 = b1; ts.h.b2 = b2; ts.h.prim = k; ts.h.id = id;
+            if (ts.anyhit) return true;
+          }
+        }
+        if (side == 0) ha = false;
+        else hb = false;
+      }
+    }
+    if (ha && hb) {
+      const bool a_first = ta <= tb;
+      if (ts.sp >= kStack) {
+        atomicOr(status, SC_STATUS_STACK_OVERFLOW);
+        ts.h.prim = -1;
+        ts.h.id = kMiss;
+        ts.h.t = tmax;
+        return true;
+      }
+      stack[ts.sp++] = a_first ? c1 : c0;
+      ts.node = a_first ? c0 : c1;
+    } else if (ha) {
+      ts.node = c0;
+    } else if (hb) {
+      ts.node = c1;
+    } else {
+      if (ts.sp == 0) {
+        if (ts.h.prim < 0) ts.h.t = tmax;
+        return true;
+      }
+      ts.node = stack[--ts.sp];
+    }
+  }
+  return false;
+}
+
 __device__ __forceinline__ Hit closest_hit(const DevScene &S, float3 o, float3 d, float tmax, unsigned *status,
                                            TravCount &tc) {
   return trace(S, o, d, tmax, false, status, tc);

@@ -26,7 +26,7 @@ struct BuildBuffers {
   float4 *tris_in;       // 3 * n_tris (input order)
   float4 *centroids;     // n_tris
   uint32_t *bounds;      // 6 sortable words (min xyz, max xyz)
-  uint32_t *keys, *keys_alt;
+  unsigned long long *keys, *keys_alt;  // 63-bit Morton codes
   uint32_t *vals, *vals_alt;
   uint32_t *hist;        // 256 * sort_blocks
   int32_t *parents;      // (n_tris - 1) internal + n_tris leaves, parent << 1 | slot

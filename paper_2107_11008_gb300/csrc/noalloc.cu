@@ -18,12 +18,13 @@ namespace {
 constexpr int kNoAllocMaxTris = SC_NOALLOC_MAX_TRIS;
 
 constexpr size_t al(size_t x) { return (x + 255) & ~size_t(255); }
-constexpr size_t kSortTile = 2048;  // keys per radix-sort block (build.cu)
+constexpr size_t kSortTile = 1024;  // keys per radix-sort block (build.cu)
 constexpr size_t kBlocksMax = (kNoAllocMaxTris + kSortTile - 1) / kSortTile;
 constexpr size_t kScratchBytes = al(sizeof(float4) * 3 * kNoAllocMaxTris)   // triangles in input order
                                  + al(sizeof(float4) * kNoAllocMaxTris)      // centroids
                                  + al(sizeof(uint32_t) * 8)                  // centroid bounds
-                                 + 4 * al(sizeof(uint32_t) * kNoAllocMaxTris)  // keys / values, ping-pong
+                                 + 2 * al(sizeof(unsigned long long) * kNoAllocMaxTris)  // keys, ping-pong
+                                 + 2 * al(sizeof(uint32_t) * kNoAllocMaxTris)  // values, ping-pong
                                  + al(sizeof(uint32_t) * 256 * kBlocksMax)   // digit histograms
                                  + al(sizeof(int32_t) * 2 * kNoAllocMaxTris)   // parent links
                                  + al(sizeof(int32_t) * kNoAllocMaxTris)     // refit counters
@@ -115,8 +116,8 @@ extern "C" int sc_build_bvh_noalloc(sc_ctx *ctx, const float *positions, const f
   b.tris_in = c.take<float4>(sizeof(float4) * 3 * kNoAllocMaxTris);
   b.centroids = c.take<float4>(sizeof(float4) * kNoAllocMaxTris);
   b.bounds = c.take<uint32_t>(sizeof(uint32_t) * 8);
-  b.keys = c.take<uint32_t>(sizeof(uint32_t) * kNoAllocMaxTris);
-  b.keys_alt = c.take<uint32_t>(sizeof(uint32_t) * kNoAllocMaxTris);
+  b.keys = c.take<unsigned long long>(sizeof(unsigned long long) * kNoAllocMaxTris);
+  b.keys_alt = c.take<unsigned long long>(sizeof(unsigned long long) * kNoAllocMaxTris);
   b.vals = c.take<uint32_t>(sizeof(uint32_t) * kNoAllocMaxTris);
   b.vals_alt = c.take<uint32_t>(sizeof(uint32_t) * kNoAllocMaxTris);
   b.hist = c.take<uint32_t>(sizeof(uint32_t) * 256 * kBlocksMax);

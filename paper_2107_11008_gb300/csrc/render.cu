@@ -19,6 +19,10 @@ constexpr int kBlock = 128;
 #ifndef SC_CAM_MIN_BLOCKS
 #define SC_CAM_MIN_BLOCKS 1
 #endif
+// node visits per traversal chunk in the camera kernel
+#ifndef SC_TRAV_CHUNK
+#define SC_TRAV_CHUNK 16
+#endif
 
 // Camera paths as a per-lane state machine.  Every loop iteration each live lane traces exactly
 // one ray -- an extension ray or the shadow ray of its pending next-event estimate -- through the
@@ -56,6 +60,10 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS) k_trace_camera(DevS
   uint32_t fl = 0, sig = 0, first = kMiss, nq = 0, nspec = 0;
   float3 o = f3(0.f, 0.f, 0.f), d = o, beta = o, L = o, nee = o, o2 = o, d2 = o;
   float tmax = 3.0e38f;
+  // traversal state, kept across chunks
+  TravState ts;
+  bool tracing = false;
+  int stack[kStack];
 
   for (;;) {
     // ---- refill: next sample of this pixel, or the next pixel ----
@@ -114,8 +122,16 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS) k_trace_camera(DevS
     if (__all_sync(0xFFFFFFFFu, mode == M_IDLE && done)) break;
     if (mode == M_IDLE) continue;  // a lane whose ticket fell outside the image retries
 
-    // ---- one ray per lane ----
-    const Hit h = trace(S, o, d, tmax, mode == M_SHADOW, status, tc);
+    // ---- advance this lane's ray by at most SC_TRAV_CHUNK node visits; lanes whose query
+    // completes shade below while the others keep traversing on the next iteration ----
+    if (!tracing) {
+      trav_begin(ts, tmax, mode == M_SHADOW);
+      tracing = true;
+    }
+    if (!trav_step(S, make_wray(o, d), tmax, ts, stack, SC_TRAV_CHUNK, status, tc)) continue;
+    tracing = false;
+    ++tc.queries;
+    const Hit h = ts.h;
 
     bool finish = false;
     if (mode == M_SHADOW) {
