@@ -47,6 +47,10 @@ extern "C" {
 #define SC_STATUS_STACK_OVERFLOW 1u
 #define SC_STATUS_WATCHDOG 2u
 #define SC_STATUS_QUEUE_OVERFLOW 4u
+/* only in a library built with -DSC_CHECKED: an index failed its range check (the access was
+ * skipped and the path abandoned); sc_last_error names the check site, value and thread */
+#define SC_STATUS_BOUNDS 8u
+#define SC_ERR_BOUNDS (-8)
 
 typedef struct sc_ctx sc_ctx;
 typedef struct sc_scene sc_scene;
@@ -269,6 +273,27 @@ int sc_trace_camera(sc_ctx *ctx, const sc_scene *scene, const sc_trace_params *p
 int sc_trace_lights(sc_ctx *ctx, const sc_scene *scene, const sc_light_params *params, const sc_frame *frame);
 /* Resolve: rgb/direct/caustic from the accumulators, plus the pixel-centre ground truth. */
 int sc_resolve(sc_ctx *ctx, const sc_scene *scene, const sc_resolve_params *params, const sc_frame *frame);
+
+/* --- batched camera tracing ----------------------------------------------------------------
+ * A dataset generator renders many randomised scenes (Sec. III-A, Sec. IV-A: thousands of
+ * images from hundreds of scenarios).  These calls trace the camera estimator of n scenes of
+ * any size and resolution in ONE kernel launch: one block per chunk of 16 8x4-pixel tiles of a
+ * scene, its lanes taking pixels of the chunk dynamically, so small and large scenes share the
+ * GPU without a launch per scene.  scenes: n built scenes; frames: n host structs (device buffers as for
+ * sc_trace_camera; accum_camera is added to, path_records optional); params as for
+ * sc_trace_camera except that scene i draws its random numbers with scene index
+ * params->scene_index + i.  Results equal n separate sc_trace_camera calls made with those
+ * scene indices.  The scene and frame tables are copied during the call. */
+int sc_trace_batch(sc_ctx *ctx, const sc_scene *const *scenes, const sc_frame *frames, int32_t n,
+                   const sc_trace_params *params);
+/* The same launch captured once into a CUDA graph and replayed by sc_batch_launch (the
+ * scenes and frame buffers must outlive the batch; their contents may change between
+ * launches).  The graph runs on the context stream of the launch call. */
+typedef struct sc_batch sc_batch;
+int sc_batch_create(sc_ctx *ctx, const sc_scene *const *scenes, const sc_frame *frames, int32_t n,
+                    const sc_trace_params *params, sc_batch **out);
+int sc_batch_launch(sc_ctx *ctx, sc_batch *batch);
+int sc_batch_destroy(sc_ctx *ctx, sc_batch *batch);
 
 #ifdef __cplusplus
 }

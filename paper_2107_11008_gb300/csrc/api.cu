@@ -163,12 +163,17 @@ int sc_sync_status(sc_ctx *c) {
   if (!c) return SC_ERR_INVALID_ARG;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "sc_sync_status");
-  unsigned st = 0;
-  e = cudaMemcpy(&st, c->d_words, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  unsigned w[16] = {0};
+  e = cudaMemcpy(w, c->d_words, sizeof(w), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e, "sc_sync_status");
+  const unsigned st = w[0];
   if (st) {
     cudaMemsetAsync(c->d_words, 0, sizeof(unsigned), c->stream);
+    cudaMemsetAsync(c->d_words + 8, 0, 3 * sizeof(unsigned), c->stream);
     cudaStreamSynchronize(c->stream);
+    if (st & SC_STATUS_BOUNDS)
+      return fail(c, SC_ERR_BOUNDS, "range check failed at site " + std::to_string(w[8]) + ": value " +
+                                        std::to_string((int)w[9]) + ", thread " + std::to_string(w[10]));
     if (st & SC_STATUS_STACK_OVERFLOW) return fail(c, SC_ERR_STACK_OVERFLOW, "traversal stack overflow");
     if (st & SC_STATUS_WATCHDOG) return fail(c, SC_ERR_TIMEOUT, "traversal watchdog expired");
     if (st & SC_STATUS_QUEUE_OVERFLOW) return fail(c, SC_ERR_QUEUE_OVERFLOW, "work queue overflow");
@@ -437,6 +442,122 @@ int sc_trace_lights(sc_ctx *c, const sc_scene *s, const sc_light_params *p, cons
                                           reinterpret_cast<unsigned long long *>(c->d_words + 2), c->counters, grid,
                                           c->stream);
   return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_trace_lights");
+}
+
+// ---- batched camera tracing -----------------------------------------------------------------
+struct sc_batch {
+  sc::BatchEntry *table = nullptr;  // device
+  int n = 0;
+  unsigned total = 0;
+  sc_trace_params params{};
+  cudaStream_t capture = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static int batch_table(sc_ctx *c, const sc_scene *const *scenes, const sc_frame *frames, int32_t n,
+                       const sc_trace_params *p, sc::BatchEntry **out, unsigned *total) {
+  if (!c || !scenes || !frames || n < 1 || !p) return fail(c, SC_ERR_INVALID_ARG, "batch: null argument or n < 1");
+  if (p->spp < 0 || p->sample_offset < 0 || p->max_depth < 0 || p->n_bins < 1 || p->n_bins > sc::kMaxBins)
+    return fail(c, SC_ERR_INVALID_ARG, "batch: bad parameters (n_bins must be 1..64)");
+  sc::BatchEntry *h = new (std::nothrow) sc::BatchEntry[n];
+  if (!h) return fail(c, SC_ERR_OOM, "batch: host table");
+  unsigned begin = 0;
+  for (int i = 0; i < n; ++i) {
+    const sc_scene *s = scenes[i];
+    if (!valid_scene(s) || frames[i].width != s->dev.cam.width || frames[i].height != s->dev.cam.height) {
+      delete[] h;
+      return fail(c, SC_ERR_INVALID_ARG, "batch: scene " + std::to_string(i) + " invalid or its frame size differs");
+    }
+    const unsigned t = sc::scene_blocks(s->dev.cam);
+    if (begin > 0x7FFFFFFFu - t) {
+      delete[] h;
+      return fail(c, SC_ERR_INVALID_ARG, "batch: more than 2^31 - 1 blocks of work");
+    }
+    std::memset(&h[i], 0, sizeof(h[i]));
+    h[i].S = s->dev;
+    h[i].F = frames[i];
+    h[i].begin = begin;
+    begin += t;
+  }
+  sc::BatchEntry *d = static_cast<sc::BatchEntry *>(dalloc(c, sizeof(sc::BatchEntry) * n));
+  if (!d) {
+    delete[] h;
+    return fail(c, SC_ERR_OOM, "batch: device table");
+  }
+  cudaError_t e = cudaMemcpyAsync(d, h, sizeof(sc::BatchEntry) * n, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // the host table is freed below
+  delete[] h;
+  if (e != cudaSuccess) {
+    dfree(c, d);
+    return cuda_fail(c, e, "batch");
+  }
+  *out = d;
+  *total = begin;
+  return SC_OK;
+}
+
+int sc_trace_batch(sc_ctx *c, const sc_scene *const *scenes, const sc_frame *frames, int32_t n,
+                   const sc_trace_params *p) {
+  sc::BatchEntry *tab = nullptr;
+  unsigned total = 0;
+  int r = batch_table(c, scenes, frames, n, p, &tab, &total);
+  if (r) return r;
+  cudaError_t e = p->spp > 0 ? sc::launch_trace_batch(tab, n, total, *p, c->d_words, c->counters, c->stream)
+                             : cudaSuccess;
+  dfree(c, tab);
+  return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_trace_batch");
+}
+
+int sc_batch_create(sc_ctx *c, const sc_scene *const *scenes, const sc_frame *frames, int32_t n,
+                    const sc_trace_params *p, sc_batch **out) {
+  if (!out) return fail(c, SC_ERR_INVALID_ARG, "sc_batch_create: null output");
+  *out = nullptr;
+  sc_batch *b = new (std::nothrow) sc_batch;
+  if (!b) return fail(c, SC_ERR_OOM, "sc_batch_create: host allocation");
+  int r = batch_table(c, scenes, frames, n, p, &b->table, &b->total);
+  if (r) {
+    delete b;
+    return r;
+  }
+  b->n = n;
+  b->params = *p;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t el = b->params.spp > 0 ? sc::launch_trace_batch(b->table, n, b->total, b->params, c->d_words,
+                                                                c->counters, b->capture)
+                                       : cudaSuccess;
+    e = cudaStreamEndCapture(b->capture, &b->graph);
+    if (el != cudaSuccess) e = el;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    dfree(c, b->table);
+    delete b;
+    return cuda_fail(c, e, "sc_batch_create");
+  }
+  *out = b;
+  return SC_OK;
+}
+
+int sc_batch_launch(sc_ctx *c, sc_batch *b) {
+  if (!c || !b || !b->exec) return fail(c, SC_ERR_INVALID_ARG, "sc_batch_launch: null argument");
+  cudaError_t e = cudaGraphLaunch(b->exec, c->stream);
+  return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_batch_launch");
+}
+
+int sc_batch_destroy(sc_ctx *c, sc_batch *b) {
+  if (!c || !b) return fail(c, SC_ERR_INVALID_ARG, "sc_batch_destroy: null argument");
+  cudaStreamSynchronize(c->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  dfree(c, b->table);
+  delete b;
+  return SC_OK;
 }
 
 int sc_resolve(sc_ctx *c, const sc_scene *s, const sc_resolve_params *p, const sc_frame *f) {

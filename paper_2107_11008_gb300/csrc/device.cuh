@@ -26,6 +26,24 @@ constexpr int kMaxVisits = 1 << 22;
 
 enum : uint32_t { EV_REFLECT = 1, EV_REFRACT = 2, EV_LIT = 3, EV_UNLIT = 4, EV_FIXUP = 7 };
 
+// Checked builds (-DSC_CHECKED): SC_IN_RANGE(status, site, v, n) is false when v is outside
+// [0, n); the first failure stores (site, v, thread) in status[8..10] and sets
+// SC_STATUS_BOUNDS, and the caller skips the access.  Release builds compile it to `true`.
+#ifdef SC_CHECKED
+__device__ __forceinline__ bool sc_in_range(unsigned *status, unsigned site, long long v, long long n) {
+  if (v >= 0 && v < n) return true;
+  atomicOr(status, SC_STATUS_BOUNDS);
+  if (atomicCAS(status + 8, 0u, site) == 0u) {
+    status[9] = (unsigned)v;
+    status[10] = blockIdx.x * blockDim.x + threadIdx.x;
+  }
+  return false;
+}
+#define SC_IN_RANGE(status, site, v, n) sc_in_range((status), (site), (long long)(v), (long long)(n))
+#else
+#define SC_IN_RANGE(status, site, v, n) true
+#endif
+
 // ------------------------------------------------------------------------------------------
 // float3 algebra
 // ------------------------------------------------------------------------------------------
@@ -157,6 +175,23 @@ struct DevScene {
   int32_t n_tris, n_nodes, n_mats, n_lights;
   float env[3];
   sc_camera cam;
+};
+
+// Work tickets of a scene (32 per 8x4 pixel tile) and the blocks of a batched launch over it.
+constexpr unsigned kBatchChunk = 512;  // tickets (16 tiles) per block of a batched launch
+__host__ __device__ __forceinline__ unsigned scene_tickets(const sc_camera &c) {
+  return (unsigned)(((c.width + 7) / 8) * ((c.height + 3) / 4)) * 32u;
+}
+__host__ __device__ __forceinline__ unsigned scene_blocks(const sc_camera &c) {
+  return (scene_tickets(c) + kBatchChunk - 1) / kBatchChunk;
+}
+
+// One scene of a batched launch: its tables, its frame buffers and its first block.
+struct BatchEntry {
+  DevScene S;
+  sc_frame F;
+  unsigned begin;
+  unsigned pad[3];
 };
 
 // ------------------------------------------------------------------------------------------
@@ -356,6 +391,12 @@ __device__ __forceinline__ bool trav_step(const DevScene &S, const WRay &w, floa
       return true;
     }
     const int node = ts.node;
+    if (!SC_IN_RANGE(status, 1, node, S.n_nodes)) {
+      ts.h.prim = -1;
+      ts.h.id = kMiss;
+      ts.h.t = tmax;
+      return true;
+    }
     const float4 n0 = __ldg(&S.nodes[4 * node + 0]);
     const float4 n1 = __ldg(&S.nodes[4 * node + 1]);
     const float4 n2 = __ldg(&S.nodes[4 * node + 2]);
@@ -370,6 +411,12 @@ __device__ __forceinline__ bool trav_step(const DevScene &S, const WRay &w, floa
       const int c = side == 0 ? c0 : c1;
       if (hit_box && c < 0) {
         const int k = ~c;
+        if (!SC_IN_RANGE(status, 2, k, S.n_tris)) {
+          ts.h.prim = -1;
+          ts.h.id = kMiss;
+          ts.h.t = tmax;
+          return true;
+        }
         const float4 a = __ldg(&S.tris[3 * k]), b = __ldg(&S.tris[3 * k + 1]), cc = __ldg(&S.tris[3 * k + 2]);
         float t, b1, b2;
         ++tc.tris;

@@ -50,6 +50,10 @@ cudaError_t launch_occluded(const DevScene &S, const float *rays, int64_t n, int
                             cudaStream_t s);
 const void *camera_kernel_ptr();
 const void *light_kernel_ptr();
+struct BatchEntry;
+// one block per kBatchChunk tickets of each scene; tab[i].begin = first block of scene i
+cudaError_t launch_trace_batch(const BatchEntry *tab, int n, unsigned total_blocks, const sc_trace_params &p,
+                               unsigned *status, unsigned long long *counters, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint64_t key, int64_t n, uint32_t *out, cudaStream_t s);
 
 }  // namespace sc

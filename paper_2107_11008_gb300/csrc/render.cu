@@ -37,19 +37,44 @@ enum : uint32_t {
   F_SPEC_ONLY = 1u, F_DIFFUSE_FIRST = 2u, F_LAST_SPECULAR = 4u, F_FIXUP = 8u, F_HAS_NEXT = 16u
 };
 
-__global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS) k_trace_camera(DevScene S, sc_trace_params P, sc_frame F,
-                                                         unsigned *status, unsigned *ticket,
-                                                         unsigned long long *counters) {
+// BATCH = false: one scene (S0, F0), persistent grid, tickets from the global counter.
+// BATCH = true: one block per chunk of kBatchChunk tickets of one scene of tab[0..n_tab):
+// tab[i].begin is the first block of scene i.  The block loads its scene's record into shared
+// memory once and its lanes take tickets of the chunk from a shared counter, so the per-lane
+// work is exactly the single-scene path; the block scheduler balances scenes of uneven size.
+// Scene i draws its random numbers with scene index P.scene_index + i.
+template <bool BATCH>
+__global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS)
+    k_trace_camera_t(DevScene S0, sc_trace_params P, sc_frame F0, const BatchEntry *tab, int n_tab,
+                     unsigned total_tickets, unsigned *status, unsigned *ticket, unsigned long long *counters) {
   TravCount tc;
   __shared__ float3 wts[kMaxBins];
-  spectral_table(wts, P.n_bins);
+  __shared__ BatchEntry blk;
+  __shared__ unsigned blk_scene, blk_ticket, blk_end;
+  if (BATCH && threadIdx.x == 0) {
+    int lo = 0, hi = n_tab - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tab[mid].begin <= blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    blk = tab[lo];
+    blk_scene = (unsigned)lo;
+    const unsigned first = (blockIdx.x - blk.begin) * kBatchChunk;
+    blk_ticket = first;
+    blk_end = min(first + kBatchChunk, scene_tickets(blk.S.cam));
+  }
+  spectral_table(wts, P.n_bins);  // ends with __syncthreads
+  const DevScene S = BATCH ? blk.S : S0;
+  const sc_frame F = BATCH ? blk.F : F0;
   const Cam cam = make_cam(S.cam);
   const int tiles_x = (cam.W + 7) / 8;
-  const unsigned n_tiles = (unsigned)(tiles_x * ((cam.H + 3) / 4));
-  const unsigned n_tickets = n_tiles * 32u;
+  const unsigned n_tickets = BATCH ? blk_end : (unsigned)(tiles_x * ((cam.H + 3) / 4)) * 32u;
+  if (BATCH) ticket = &blk_ticket;
   const int lane = threadIdx.x & 31;
   const float3 env = f3(S.env);
   const int nb = P.n_bins > 0 ? P.n_bins : 1;
+  const int scene_index = BATCH ? P.scene_index + (int)blk_scene : P.scene_index;
 
   // pixel state
   int px = 0, py = 0, pix = -1, s = 0;
@@ -68,7 +93,7 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS) k_trace_camera(DevS
   for (;;) {
     // ---- refill: next sample of this pixel, or the next pixel ----
     if (mode == M_IDLE && pix >= 0 && s >= P.spp) {
-      if (F.accum_camera) {
+      if (F.accum_camera && SC_IN_RANGE(status, 4, pix, cam.W * cam.H)) {
         float4 *a = reinterpret_cast<float4 *>(F.accum_camera) + pix;
         float4 v = *a;
         v.x += acc.x; v.y += acc.y; v.z += acc.z;
@@ -103,7 +128,7 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS) k_trace_camera(DevS
     }
     if (mode == M_IDLE && pix >= 0 && s < P.spp) {
       // start sample s: primary ray (tag 0: jitter x, jitter y, wavelength bin)
-      const uint4 x0 = draw(P.seed, (uint32_t)pix, (uint32_t)(P.sample_offset + s), 0u, 0u, (uint32_t)P.scene_index);
+      const uint4 x0 = draw(P.seed, (uint32_t)pix, (uint32_t)(P.sample_offset + s), 0u, 0u, (uint32_t)scene_index);
       bin = choose(x0.z, nb);
       o = cam.eye;
       d = cam_dir(cam, (px + u01(x0.x)) / cam.W, (py + u01(x0.y)) / cam.H);
@@ -154,9 +179,11 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS) k_trace_camera(DevS
       if (h.prim < 0) {
         L = L + beta * env;
         finish = true;
+      } else if (!SC_IN_RANGE(status, 5, h.prim, S.n_tris) || !SC_IN_RANGE(status, 6, h.id, S.n_tris)) {
+        finish = true;
       } else {
         const Surf f = interact(S, d, h);
-        const sc_material m = S.mats[f.mat];
+        const sc_material m = S.mats[SC_IN_RANGE(status, 7, f.mat, S.n_mats) ? f.mat : 0];
         if (m.kind == SC_MAT_EMISSIVE) {
           const bool count = (fl & F_SPEC_ONLY) || ((P.flags & SC_FLAG_EMITTER_AFTER_DS) && (fl & F_DIFFUSE_FIRST) &&
                                                     n_diffuse == 1 && (fl & F_LAST_SPECULAR));
@@ -164,7 +191,7 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS) k_trace_camera(DevS
           finish = true;
         } else {
           const uint32_t pixu = (uint32_t)pix, smp = (uint32_t)(P.sample_offset + s);
-          const uint4 xs = draw(P.seed, pixu, smp, (uint32_t)(k + 1), 1u, (uint32_t)P.scene_index);
+          const uint4 xs = draw(P.seed, pixu, smp, (uint32_t)(k + 1), 1u, (uint32_t)scene_index);
           if (m.kind == SC_MAT_DIELECTRIC) {
             bool refl, fix;
             const float nl = cauchy(m.cauchy_a, m.cauchy_b, bin, P.n_bins);
@@ -184,7 +211,7 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS) k_trace_camera(DevS
             float3 so = f3(0.f, 0.f, 0.f), sd = so;
             float sdist = 0.0f;
             if (S.n_lights > 0) {
-              const uint4 xn = draw(P.seed, pixu, smp, (uint32_t)(k + 1), 2u, (uint32_t)P.scene_index);
+              const uint4 xn = draw(P.seed, pixu, smp, (uint32_t)(k + 1), 2u, (uint32_t)scene_index);
               const sc_light Lg = S.lights[choose(xn.x, S.n_lights)];
               float3 lp = f3(0.f, 0.f, 0.f);
               float geo = 0.0f;
@@ -257,7 +284,7 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS) k_trace_camera(DevS
     if (finish) {
       const float3 Lw = L * wts[bin];
       acc = acc + Lw;
-      if (F.path_records) {
+      if (F.path_records && SC_IN_RANGE(status, 9, (int64_t)pix * P.spp + s, (int64_t)cam.W * cam.H * P.spp)) {
         sc_path_record r;
         r.L[0] = Lw.x; r.L[1] = Lw.y; r.L[2] = Lw.z;
         r.first_tri = first;
@@ -484,7 +511,7 @@ __global__ void k_philox(const uint4 *ctr, uint64_t key, int64_t n, uint4 *out) 
   out[i] = philox(ctr[i], (uint32_t)key, (uint32_t)(key >> 32));
 }
 
-const void *camera_kernel_ptr() { return reinterpret_cast<const void *>(&k_trace_camera); }
+const void *camera_kernel_ptr() { return reinterpret_cast<const void *>(&k_trace_camera_t<false>); }
 const void *light_kernel_ptr() { return reinterpret_cast<const void *>(&k_trace_lights); }
 
 static int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -493,7 +520,16 @@ cudaError_t launch_trace_camera(const DevScene &S, const sc_trace_params &p, con
                                 unsigned *ticket, unsigned long long *counters, int grid, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  k_trace_camera<<<grid, kBlock, 0, s>>>(S, p, f, status, ticket, counters);
+  k_trace_camera_t<false><<<grid, kBlock, 0, s>>>(S, p, f, nullptr, 0, 0u, status, ticket, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_batch(const BatchEntry *tab, int n, unsigned total_blocks, const sc_trace_params &p,
+                               unsigned *status, unsigned long long *counters, cudaStream_t s) {
+  if (total_blocks == 0) return cudaSuccess;
+  DevScene none{};
+  sc_frame nof{};
+  k_trace_camera_t<true><<<total_blocks, kBlock, 0, s>>>(none, p, nof, tab, n, 0u, status, nullptr, counters);
   return cudaGetLastError();
 }
 

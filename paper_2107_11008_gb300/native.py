@@ -15,7 +15,7 @@ P = C.POINTER
 
 SC_OK = 0
 ERRORS = {-1: "SC_ERR_INVALID_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_OOM", -4: "SC_ERR_STACK_OVERFLOW",
-          -5: "SC_ERR_TIMEOUT", -6: "SC_ERR_QUEUE_OVERFLOW", -7: "SC_ERR_UNSUPPORTED"}
+          -5: "SC_ERR_TIMEOUT", -6: "SC_ERR_QUEUE_OVERFLOW", -7: "SC_ERR_UNSUPPORTED", -8: "SC_ERR_BOUNDS"}
 SC_FLAG_FORCE_TRANSMIT = 1
 SC_FLAG_SPLAT_DIRECT = 2
 SC_FLAG_EMITTER_AFTER_DS = 4
@@ -117,6 +117,11 @@ SIGNATURES = {
     "sc_trace_camera": (C.c_int, [C.c_void_p, C.c_void_p, P(sc_trace_params), P(sc_frame)]),
     "sc_trace_lights": (C.c_int, [C.c_void_p, C.c_void_p, P(sc_light_params), P(sc_frame)]),
     "sc_resolve": (C.c_int, [C.c_void_p, C.c_void_p, P(sc_resolve_params), P(sc_frame)]),
+    "sc_trace_batch": (C.c_int, [C.c_void_p, P(C.c_void_p), P(sc_frame), C.c_int32, P(sc_trace_params)]),
+    "sc_batch_create": (C.c_int, [C.c_void_p, P(C.c_void_p), P(sc_frame), C.c_int32, P(sc_trace_params),
+                                  P(C.c_void_p)]),
+    "sc_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sc_batch_destroy": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -232,3 +237,32 @@ def sc_trace_lights(ctx, scene, params: sc_light_params, frame: sc_frame):
 
 def sc_resolve(ctx, scene, params: sc_resolve_params, frame: sc_frame):
     return check(load().sc_resolve(ctx, scene, C.byref(params), C.byref(frame)), ctx)
+
+
+def _tables(scenes, frames):
+    n = len(scenes)
+    if len(frames) != n:
+        raise ValueError("one frame per scene")
+    sa = (C.c_void_p * n)(*scenes)
+    fa = (sc_frame * n)(*frames)
+    return n, sa, fa
+
+
+def sc_trace_batch(ctx, scenes, frames, params: sc_trace_params):
+    n, sa, fa = _tables(scenes, frames)
+    return check(load().sc_trace_batch(ctx, sa, fa, n, C.byref(params)), ctx)
+
+
+def sc_batch_create(ctx, scenes, frames, params: sc_trace_params):
+    n, sa, fa = _tables(scenes, frames)
+    out = C.c_void_p()
+    check(load().sc_batch_create(ctx, sa, fa, n, C.byref(params), C.byref(out)), ctx)
+    return out.value
+
+
+def sc_batch_launch(ctx, batch):
+    return check(load().sc_batch_launch(ctx, batch), ctx)
+
+
+def sc_batch_destroy(ctx, batch):
+    return check(load().sc_batch_destroy(ctx, batch), ctx)

@@ -277,3 +277,34 @@ def philox(ctx: Context, counters: torch.Tensor, key: int) -> torch.Tensor:
     out = torch.empty_like(c)
     N.sc_philox4x32_10(ctx.handle, c.data_ptr(), key, c.shape[0], out.data_ptr())
     return out
+
+
+def trace_batch(ctx: Context, scenes, frames, spp: int, max_depth: int, n_bins: int = 1, seed: int = 0,
+                sample_offset: int = 0, scene_index: int = 0, flags: int = 0):
+    """Camera paths of many scenes in one persistent launch (scene i uses scene index scene_index + i)."""
+    p = N.sc_trace_params(spp, sample_offset, max_depth, n_bins, seed, scene_index, flags)
+    N.sc_trace_batch(ctx.handle, [g.handle for g in scenes], [f.struct() for f in frames], p)
+
+
+class Batch:
+    """The batched launch captured once as a CUDA graph; ``launch()`` replays it."""
+
+    def __init__(self, ctx: Context, scenes, frames, spp: int, max_depth: int, n_bins: int = 1, seed: int = 0,
+                 sample_offset: int = 0, scene_index: int = 0, flags: int = 0):
+        self.ctx, self.scenes, self.frames = ctx, list(scenes), list(frames)
+        p = N.sc_trace_params(spp, sample_offset, max_depth, n_bins, seed, scene_index, flags)
+        self.handle = N.sc_batch_create(ctx.handle, [g.handle for g in self.scenes], [f.struct() for f in self.frames], p)
+
+    def launch(self):
+        N.sc_batch_launch(self.ctx.handle, self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.sc_batch_destroy(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

@@ -1,0 +1,90 @@
+"""Batched camera tracing (many scenes of uneven size, one persistent launch; CUDA-graph replay)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2107_11008_gb300 import renderer as R  # noqa: E402
+from paper_2107_11008_gb300 import scenes as S  # noqa: E402
+
+from .parity import MAX_AMBIGUOUS_GLASS, compare_camera  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = R.Context(0)
+    yield c
+    c.close()
+
+
+def _scenes():
+    # uneven triangle counts and ragged resolutions, 1-6 objects each
+    return [S.random_scene(i, resolutions=(13, 24, 40), tri_range=(300, 4000)) for i in range(6)]
+
+
+def test_batch_equals_separate_launches(ctx):
+    scs = _scenes()
+    gss = [R.GpuScene(ctx, s) for s in scs]
+    spp, depth = 3, 12
+    fb = [R.Frame(s.camera.width, s.camera.height, fields=("accum_camera",)) for s in scs]
+    for f in fb:
+        f.alloc_path_records(spp)
+    R.trace_batch(ctx, gss, fb, spp, depth, seed=4, scene_index=10)
+    ctx.sync_status()
+    for i, (s, g) in enumerate(zip(scs, gss)):
+        f1 = R.Frame(s.camera.width, s.camera.height, fields=("accum_camera",))
+        f1.alloc_path_records(spp)
+        R.trace_camera(ctx, g, f1, spp, depth, seed=4, scene_index=10 + i)
+        ctx.sync_status()
+        np.testing.assert_array_equal(fb[i].path_records.cpu().numpy(), f1.path_records.cpu().numpy())
+        np.testing.assert_array_equal(fb[i]["accum_camera"].cpu().numpy(), f1["accum_camera"].cpu().numpy())
+
+
+def test_batch_member_matches_oracle(ctx):
+    scs = _scenes()
+    gss = [R.GpuScene(ctx, s) for s in scs]
+    spp, depth = 4, 12
+    fb = [R.Frame(s.camera.width, s.camera.height, fields=("accum_camera",)) for s in scs]
+    for f in fb:
+        f.alloc_path_records(spp)
+    R.trace_batch(ctx, gss, fb, spp, depth, seed=9)
+    ctx.sync_status()
+    for i in (0, 5):
+        g = R.path_records_numpy(fb[i].path_records)
+        _, rec = O.OracleScene(scs[i]).trace_camera(spp, depth, seed=9, scene_index=i)
+        compare_camera(g, rec, max_ambiguous=MAX_AMBIGUOUS_GLASS)
+
+
+def test_batch_graph_replays(ctx):
+    scs = _scenes()[:4]
+    gss = [R.GpuScene(ctx, s) for s in scs]
+    fb = [R.Frame(s.camera.width, s.camera.height, fields=("accum_camera",)) for s in scs]
+    b = R.Batch(ctx, gss, fb, 2, 8, seed=1)
+    b.launch()
+    ctx.sync_status()
+    once = [f["accum_camera"].clone() for f in fb]
+    b.launch()
+    ctx.sync_status()
+    for f, o in zip(fb, once):
+        np.testing.assert_array_equal(f["accum_camera"].cpu().numpy(), 2 * o.cpu().numpy())
+    ref = [R.Frame(s.camera.width, s.camera.height, fields=("accum_camera",)) for s in scs]
+    R.trace_batch(ctx, gss, ref, 2, 8, seed=1)
+    ctx.sync_status()
+    for r, o in zip(ref, once):
+        np.testing.assert_array_equal(r["accum_camera"].cpu().numpy(), o.cpu().numpy())
+    b.close()
+
+
+def test_batch_rejects_mismatched_frames(ctx):
+    from paper_2107_11008_gb300 import native as N
+
+    scs = _scenes()[:2]
+    gss = [R.GpuScene(ctx, s) for s in scs]
+    bad = [R.Frame(7, 7, fields=("accum_camera",)) for _ in scs]
+    with pytest.raises(N.ScError):
+        R.trace_batch(ctx, gss, bad, 1, 4)
