@@ -1,0 +1,127 @@
+/*
+ * sc_unet.h -- C ABI of the BF16 U-Net denoiser trained and run on the GB300 tensor cores.
+ *
+ * The paper evaluates its images with a U-Net (Sec. IV-A, after Ronneberger et al. 2015); here a
+ * U-Net of that family denoises low-sample renders.  Its input is 11 channels per pixel:
+ * log1p of the noisy linear RGB (3), the first-hit albedo (3), the first-hit normal (3), the
+ * normalised depth (1) and the object mask (1), i.e. the ground-truth buffers of Sec. III-D.
+ * Its output is 3 channels: log1p of the denoised RGB.
+ *
+ * Architecture (fixed): 4 levels of widths 32, 48, 64, 128.  Encoder level l: [2x2 max pool if
+ * l > 0] -> 3x3 conv + ReLU -> 3x3 conv + ReLU.  Decoder level l (deepest first): 2x2 stride-2
+ * transposed conv -> concatenate [upsampled, encoder output of level l] -> 3x3 conv + ReLU ->
+ * 3x3 conv + ReLU.  Output: 1x1 conv.  Zero padding; max-pool ties go to the first element of
+ * the window in row-major order; 585,363 parameters.
+ *
+ * Loss (training): 0.16 * mean |p - t| + 0.84 * (1 - mean SSIM(p, t)), SSIM of Wang et al.
+ * (2004) over valid 11x11 Gaussian windows (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2, averaged over
+ * windows, channels and images.  Optimiser: Adam, beta1 0.9, beta2 0.999, eps 1e-8, bias
+ * corrected.
+ *
+ * Precision: weights and activations are BF16, every contraction accumulates in FP32 on the
+ * tensor cores (tcgen05.mma), biases, gradients of parameters, Adam state and master weights
+ * are FP32.
+ *
+ * Parameters are exchanged as one flat FP32 vector: the tensors below in this order, each
+ * row-major (C order):
+ *   for l = 0..3:  enc{l}_c1_w (c_l, 3, 3, cin) , enc{l}_c1_b (c_l),
+ *                  enc{l}_c2_w (c_l, 3, 3, c_l), enc{l}_c2_b (c_l)       (cin = 11, then c_{l-1})
+ *   for l = 2..0:  up{l}_w (c_{l+1}, 2, 2, c_l), up{l}_b (c_l),
+ *                  dec{l}_c1_w (c_l, 3, 3, 2 c_l), dec{l}_c1_b (c_l),
+ *                  dec{l}_c2_w (c_l, 3, 3, c_l), dec{l}_c2_b (c_l)
+ *   out_w (3, 32), out_b (3)
+ * Conv weight w[o][dy][dx][c] multiplies input pixel (y + dy - 1, x + dx - 1); transposed-conv
+ * weight w[c][a][e][o] maps input pixel (y, x) to output pixel (2y + a, 2x + e).
+ *
+ * Conventions: as in supercaustics.h (status codes, asynchronous work on the context stream,
+ * caller-owned device buffers).  Images are NHWC FP32, H and W multiples of 8 and >= 16.
+ */
+#ifndef SC_UNET_H
+#define SC_UNET_H
+
+#include "supercaustics.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SC_UNET_IN_CH 11
+#define SC_UNET_OUT_CH 3
+#define SC_UNET_LEVELS 4
+
+typedef struct sc_unet sc_unet;
+
+/* Number of FP32 values in the flat parameter vector (585,363). */
+int sc_unet_param_count(int64_t *count);
+
+/* Creates a network with workspace for up to max_batch images of height x width.
+ * Parameters start at zero; Adam moments at zero, step 0. */
+int sc_unet_create(sc_ctx *ctx, int32_t max_batch, int32_t height, int32_t width, sc_unet **out);
+int sc_unet_destroy(sc_ctx *ctx, sc_unet *net);
+
+/* Copies the flat FP32 parameters in (device pointer) and refreshes the BF16 copies the kernels
+ * read.  Resets the Adam moments and the step count. */
+int sc_unet_set_params(sc_ctx *ctx, sc_unet *net, const float *params);
+/* Copies the flat FP32 master parameters out (device pointer, sc_unet_param_count floats). */
+int sc_unet_get_params(sc_ctx *ctx, const sc_unet *net, float *params);
+/* Gradient of the last sc_unet_loss_grad, same flat layout (device pointers). */
+int sc_unet_get_grads(sc_ctx *ctx, const sc_unet *net, float *grads);
+int sc_unet_set_grads(sc_ctx *ctx, sc_unet *net, const float *grads);
+
+/* Inference: x [n, H, W, 11] FP32 (device) -> y [n, H, W, 3] FP32 (device); 1 <= n <= max_batch. */
+int sc_unet_forward(sc_ctx *ctx, sc_unet *net, const float *x, int32_t n, float *y);
+
+/* Forward, loss against target [n, H, W, 3] FP32 (device), and backward; the parameter gradient
+ * is kept inside (sc_unet_get_grads).  y (optional, device) receives the prediction, loss
+ * (optional, device) one FP32 value. */
+int sc_unet_loss_grad(sc_ctx *ctx, sc_unet *net, const float *x, const float *target, int32_t n, float *y,
+                      float *loss);
+
+/* One Adam step with the stored gradient (step count += 1) and refresh of the BF16 copies. */
+int sc_unet_adam(sc_ctx *ctx, sc_unet *net, float lr);
+
+/* sc_unet_loss_grad followed by sc_unet_adam. */
+int sc_unet_train_step(sc_ctx *ctx, sc_unet *net, const float *x, const float *target, int32_t n, float lr,
+                       float *loss);
+
+/* The loss alone: pred, target [n, h, w, 3] FP32 (device); loss (device, 1 float, optional);
+ * grad (device, [n, h, w, 3] FP32, optional) = d loss / d pred.  h, w >= 11. */
+int sc_ssim_l1_loss(sc_ctx *ctx, const float *pred, const float *target, int32_t n, int32_t h, int32_t w,
+                    float *loss, float *grad);
+
+/* Builds the 11-channel network input from a rendered frame's buffers (supercaustics.h
+ * sc_frame: rgb, albedo, normal, depth_norm, mask) for image `index` of a batch:
+ * x + index * H * W * 11 receives [log1p(max(rgb, 0)), albedo, normal, depth_norm, mask != 0]. */
+int sc_unet_pack_frame(sc_ctx *ctx, const sc_frame *frame, float *x, int32_t index);
+
+/* Internal tensors, for inspection by tests: id below, level 0..3. */
+enum {
+  SC_UNET_BUF_INPUT = 0,  /* BF16 network input, 16 channels (11 + zero padding), level 0 */
+  SC_UNET_BUF_ENC1 = 1,   /* BF16 output of encoder conv 1 (after ReLU) */
+  SC_UNET_BUF_ENC2 = 2,   /* BF16 output of encoder conv 2 (after ReLU): the skip tensor */
+  SC_UNET_BUF_POOL = 3,   /* BF16 max-pooled input of encoder level l >= 1 */
+  SC_UNET_BUF_UP = 4,     /* BF16 transposed-conv output at level l <= 2 */
+  SC_UNET_BUF_DEC1 = 5,   /* BF16 decoder conv 1 output (after ReLU), l <= 2 */
+  SC_UNET_BUF_DEC2 = 6,   /* BF16 decoder conv 2 output (after ReLU), l <= 2 */
+  SC_UNET_BUF_OUT = 7,    /* FP32 network output, 3 channels, level 0 */
+  SC_UNET_BUF_GOUT = 8,   /* BF16 d loss / d output, 8 channels (3 + zero padding), level 0 */
+  SC_UNET_BUF_GDEC2 = 9,  /* BF16 d loss / d (pre-ReLU) decoder conv 2 output, l <= 2 */
+  SC_UNET_BUF_GDEC1 = 10, /* BF16 d loss / d (pre-ReLU) decoder conv 1 output, l <= 2 */
+  SC_UNET_BUF_GUP = 11,   /* BF16 d loss / d transposed-conv output, l <= 2 */
+  SC_UNET_BUF_GSKIP = 12, /* FP32 d loss / d skip tensor through the concatenation, l <= 2 */
+  SC_UNET_BUF_GENC2 = 13, /* BF16 d loss / d (pre-ReLU) encoder conv 2 output */
+  SC_UNET_BUF_GENC1 = 14  /* BF16 d loss / d (pre-ReLU) encoder conv 1 output */
+};
+typedef struct {
+  int32_t dtype;    /* 0 BF16, 1 FP32 */
+  int32_t n, h, w;  /* images of the last call, geometry of the level */
+  int32_t c;        /* logical channels */
+} sc_unet_buffer_info;
+int sc_unet_buffer(const sc_unet *net, int32_t id, int32_t level, sc_unet_buffer_info *info);
+/* Copies the buffer densely ([n, h, w, c], its dtype) to dst (device). */
+int sc_unet_copy_buffer(sc_ctx *ctx, const sc_unet *net, int32_t id, int32_t level, void *dst);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -81,6 +81,9 @@ namespace sc {
 int ctx_device(const sc_ctx *c) { return c->device; }
 cudaStream_t ctx_stream(const sc_ctx *c) { return c->stream; }
 void ctx_set_error(sc_ctx *c, const std::string &msg) { c->err = msg; }
+void *ctx_alloc(sc_ctx *c, size_t bytes) { return dalloc(c, bytes); }
+void ctx_free(sc_ctx *c, void *p) { dfree(c, p); }
+unsigned *ctx_status(sc_ctx *c) { return c->d_words; }
 }  // namespace sc
 
 extern "C" {

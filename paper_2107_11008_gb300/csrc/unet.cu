@@ -1,0 +1,1233 @@
+// unet.cu -- the BF16 U-Net denoiser (include/sc_unet.h): forward, L1 + SSIM loss, backward,
+// Adam, all on the GPU.  Every convolution (forward, data gradient, weight gradient), the
+// transposed convolutions and the 1x1 output layer run through the tcgen05 GEMM of
+// unet_gemm.cuh; pooling, the loss, the weight-gradient reduction and Adam are plain CUDA.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "sc_unet.h"
+#include "unet_gemm.cuh"
+
+namespace sc {
+int ctx_device(const sc_ctx *c);
+cudaStream_t ctx_stream(const sc_ctx *c);
+void ctx_set_error(sc_ctx *c, const std::string &msg);
+void *ctx_alloc(sc_ctx *c, size_t bytes);
+void ctx_free(sc_ctx *c, void *p);
+unsigned *ctx_status(sc_ctx *c);
+}  // namespace sc
+
+namespace sc {
+namespace unet {
+
+constexpr int kLevels = 4;
+constexpr int kChans[kLevels] = {32, 48, 64, 128};
+constexpr int kInCh = 11, kInPad = 16, kOutCh = 3, kGyCh = 8;
+constexpr double kL1W = 0.16, kSsimW = 0.84;
+constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
+
+// ---------------------------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------------------------
+
+// x [P][11] FP32 -> [P][16] BF16 (channels 11..15 zero)
+__global__ void k_pack_input(const float *x, bf16 *out, int64_t P) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = i < kInCh ? x[p * kInCh + i] : 0.0f;
+  uint4 *o = reinterpret_cast<uint4 *>(out + p * kInPad);
+  o[0] = pack8(v);
+  o[1] = pack8(v + 8);
+}
+
+// 11-channel network input from a frame's buffers
+__global__ void k_pack_frame(const float4 *rgb, const float4 *albedo, const float4 *normal, const float *depth_norm,
+                             const uint8_t *mask, float *x, int64_t P) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float4 c = rgb[p], a = albedo[p], n = normal[p];
+  float *o = x + p * kInCh;
+  o[0] = log1pf(fmaxf(c.x, 0.0f));
+  o[1] = log1pf(fmaxf(c.y, 0.0f));
+  o[2] = log1pf(fmaxf(c.z, 0.0f));
+  o[3] = a.x;
+  o[4] = a.y;
+  o[5] = a.z;
+  o[6] = n.x;
+  o[7] = n.y;
+  o[8] = n.z;
+  o[9] = depth_norm[p];
+  o[10] = mask[p] ? 1.0f : 0.0f;
+}
+
+// 2x2 stride-2 max pool of a channel slice: src (h x w, stride cs, offset co) -> dst [P/4][C]
+__global__ void k_pool(const bf16 *src, int cs, int co, int C, int n, int h, int w, bf16 *dst) {
+  const int groups = C / 8;
+  const int64_t total = (int64_t)n * (h / 2) * (w / 2) * groups;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int g = (int)(i % groups);
+  const int64_t q = i / groups;
+  const int ho = h / 2, wo = w / 2;
+  const int x = (int)(q % wo), y = (int)((q / wo) % ho), img = (int)(q / ((int64_t)wo * ho));
+  float best[8];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t pix = (int64_t)(img * h + 2 * y + (k >> 1)) * w + 2 * x + (k & 1);
+    float v[8];
+    unpack8(ldg16(src + pix * cs + co + g * 8), v);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) best[j] = k == 0 ? v[j] : fmaxf(best[j], v[j]);
+  }
+  *reinterpret_cast<uint4 *>(dst + q * C + g * 8) = pack8(best);
+}
+
+enum { KIND_BIAS = 0, KIND_CONV = 1, KIND_UP = 2, KIND_OUT = 3 };
+
+// Sum of the K-split partial products in a fixed order, scattered to the flat FP32 gradient.
+// part[(s * Mpad + r) * np + n]; rows r: conv (tap * cin_p + c) | ones; up: c | ones;
+// out: c | ones.
+__global__ void k_wgrad_reduce(const float *part, int splits, int Mpad, int np, int rows, int kind, int cout, int cin,
+                               int cin_p, float *gw, float *gb) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)(rows + 1) * np) return;
+  const int r = (int)(i / np), n = (int)(i % np);
+  auto sum = [&](int rr, int nn) {
+    float s = 0.0f;
+    for (int k = 0; k < splits; ++k) s += part[((int64_t)k * Mpad + rr) * np + nn];
+    return s;
+  };
+  if (kind == KIND_CONV) {
+    if (n >= cout) return;
+    if (r == rows) {
+      gb[n] = sum(r, n);
+      return;
+    }
+    const int tap = r / cin_p, c = r - tap * cin_p;
+    if (c < cin) gw[((int64_t)n * 9 + tap) * cin + c] = sum(r, n);
+  } else if (kind == KIND_UP) {
+    if (n >= 4 * cout) return;
+    if (r == rows) {
+      if (n < cout) {
+        float s = 0.0f;
+        for (int ae = 0; ae < 4; ++ae) s += sum(r, ae * cout + n);
+        gb[n] = s;
+      }
+      return;
+    }
+    const int ae = n / cout, o = n - ae * cout;
+    gw[((int64_t)r * 4 + ae) * cout + o] = sum(r, n);
+  } else {  // KIND_OUT
+    if (n >= cout) return;
+    if (r == rows) gb[n] = sum(r, n);
+    else gw[(int64_t)n * cin + r] = sum(r, n);
+  }
+}
+
+struct Seg {
+  int64_t off;
+  int32_t count, kind, cout, cin, cin_p, first_block;
+  bf16 *wf, *wd;
+};
+
+// One bias-corrected Adam step over every parameter (update != 0), then the BF16 copies:
+// wf = the layout the forward GEMM reads as B, wd = the layout of the data-gradient GEMM.
+__global__ void k_adam(const Seg *segs, int nseg, float *p, const float *g, float *m, float *v, float lr, float bc1,
+                       float bc2, int update) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].first_block <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const Seg S = segs[lo];
+  const int i = ((int)blockIdx.x - S.first_block) * blockDim.x + threadIdx.x;
+  if (i >= S.count) return;
+  const int64_t k = S.off + i;
+  float w = p[k];
+  if (update) {
+    const float gk = g[k];
+    const float mk = 0.9f * m[k] + 0.1f * gk;
+    const float vk = 0.999f * v[k] + 0.001f * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    w -= lr * (mk / bc1) / (sqrtf(vk / bc2) + 1e-8f);
+    p[k] = w;
+  }
+  const bf16 b = __float2bfloat16_rn(w);
+  if (S.kind == KIND_CONV) {
+    const int o = i / (9 * S.cin), rem = i - o * 9 * S.cin, tap = rem / S.cin, c = rem - tap * S.cin;
+    S.wf[((int64_t)o * 9 + tap) * S.cin_p + c] = b;
+    if (S.wd) S.wd[((int64_t)c * 9 + tap) * S.cout + o] = b;
+  } else if (S.kind == KIND_UP) {
+    const int c = i / (4 * S.cout), rem = i - c * 4 * S.cout;
+    S.wf[(int64_t)rem * S.cin + c] = b;
+    S.wd[i] = b;
+  } else if (S.kind == KIND_OUT) {
+    const int o = i / S.cin, c = i - o * S.cin;
+    S.wf[i] = b;
+    S.wd[(int64_t)c * kGyCh + o] = b;
+  }
+}
+
+// ---- loss --------------------------------------------------------------------------------
+constexpr int kSTW = 32, kSTH = 8, kWin = 11;
+__constant__ float c_gauss[kWin];
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// SSIM of each valid 11x11 window and d SSIM / d (mu_x, E[x^2], E[xy]) of that window.
+// Grid: (ceil(Wv / 32), ceil(Hv / 8), n), 256 threads; Wv = w - 10, Hv = h - 10.
+__global__ void __launch_bounds__(256) k_ssim_fwd(const float *p, const float *t, int h, int w, float *dmx,
+                                                  float *dexx, float *dexy, double *part) {
+  __shared__ float sp[kSTH + 10][kSTW + 10], st[kSTH + 10][kSTW + 10];
+  __shared__ float hz[5][kSTH + 10][kSTW];
+  __shared__ double red[256];
+  const int Hv = h - 10, Wv = w - 10;
+  const int x0 = blockIdx.x * kSTW, y0 = blockIdx.y * kSTH, img = blockIdx.z;
+  const int tx = threadIdx.x % kSTW, ty = threadIdx.x / kSTW;
+  const int wx = x0 + tx, wy = y0 + ty;
+  double acc = 0.0;
+  for (int ch = 0; ch < 3; ++ch) {
+    for (int i = threadIdx.x; i < (kSTH + 10) * (kSTW + 10); i += 256) {
+      const int r = i / (kSTW + 10), cc = i % (kSTW + 10);
+      const int yy = y0 + r, xx = x0 + cc;
+      const bool in = yy < h && xx < w;
+      const int64_t idx = ((int64_t)(img * h + yy) * w + xx) * 3 + ch;
+      sp[r][cc] = in ? p[idx] : 0.0f;
+      st[r][cc] = in ? t[idx] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (kSTH + 10) * kSTW; i += 256) {
+      const int r = i / kSTW, cc = i % kSTW;
+      float a = 0, b = 0, aa = 0, bb = 0, ab = 0;
+#pragma unroll
+      for (int k = 0; k < kWin; ++k) {
+        const float g = c_gauss[k], u = sp[r][cc + k], q = st[r][cc + k];
+        a += g * u;
+        b += g * q;
+        aa += g * u * u;
+        bb += g * q * q;
+        ab += g * u * q;
+      }
+      hz[0][r][cc] = a;
+      hz[1][r][cc] = b;
+      hz[2][r][cc] = aa;
+      hz[3][r][cc] = bb;
+      hz[4][r][cc] = ab;
+    }
+    __syncthreads();
+    float mx = 0, my = 0, exx = 0, eyy = 0, exy = 0;
+#pragma unroll
+    for (int k = 0; k < kWin; ++k) {
+      const float g = c_gauss[k];
+      mx += g * hz[0][ty + k][tx];
+      my += g * hz[1][ty + k][tx];
+      exx += g * hz[2][ty + k][tx];
+      eyy += g * hz[3][ty + k][tx];
+      exy += g * hz[4][ty + k][tx];
+    }
+    if (wx < Wv && wy < Hv) {
+      const float a1 = 2.0f * mx * my + kC1;
+      const float a2 = 2.0f * (exy - mx * my) + kC2;
+      const float b1 = mx * mx + my * my + kC1;
+      const float b2 = (exx - mx * mx) + (eyy - my * my) + kC2;
+      const float S = a1 * a2 / (b1 * b2);
+      const int64_t o = ((int64_t)(img * Hv + wy) * Wv + wx) * 3 + ch;
+      dmx[o] = (2.0f * my * a2 - 2.0f * my * a1) / (b1 * b2) - S * (2.0f * mx / b1 - 2.0f * mx / b2);
+      dexx[o] = -S / b2;
+      dexy[o] = 2.0f * a1 / (b1 * b2);
+      acc += S;
+    }
+    __syncthreads();
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+}
+
+// d loss / d pred per pixel: the adjoint of the window blurs applied to the three coefficient
+// maps plus the L1 term.  Grid: (ceil(w / 32), ceil(h / 8), n), 256 threads.
+__global__ void __launch_bounds__(256) k_ssim_bwd(const float *p, const float *t, int h, int w, const float *dmx,
+                                                  const float *dexx, const float *dexy, float inv_px, float inv_win,
+                                                  float *grad, bf16 *gy8, double *part) {
+  __shared__ float wm[3][kSTH + 10][kSTW + 10];
+  __shared__ float hz[3][kSTH + 10][kSTW];
+  __shared__ double red[256];
+  const int Hv = h - 10, Wv = w - 10;
+  const int x0 = blockIdx.x * kSTW, y0 = blockIdx.y * kSTH, img = blockIdx.z;
+  const int tx = threadIdx.x % kSTW, ty = threadIdx.x / kSTW;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool in = x < w && y < h;
+  const int64_t pix = ((int64_t)(img * h + y) * w + x);
+  float gout[3] = {0.0f, 0.0f, 0.0f};
+  double acc = 0.0;
+  for (int ch = 0; ch < 3; ++ch) {
+    // window maps over rows y0-10 .. y0+7, cols x0-10 .. x0+31
+    for (int i = threadIdx.x; i < (kSTH + 10) * (kSTW + 10); i += 256) {
+      const int r = i / (kSTW + 10), cc = i % (kSTW + 10);
+      const int wy = y0 - 10 + r, wx = x0 - 10 + cc;
+      const bool ok = wy >= 0 && wy < Hv && wx >= 0 && wx < Wv;
+      const int64_t o = ((int64_t)(img * Hv + wy) * Wv + wx) * 3 + ch;
+      wm[0][r][cc] = ok ? dmx[o] : 0.0f;
+      wm[1][r][cc] = ok ? dexx[o] : 0.0f;
+      wm[2][r][cc] = ok ? dexy[o] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (kSTH + 10) * kSTW; i += 256) {
+      const int r = i / kSTW, cc = i % kSTW;
+      float a = 0, b = 0, c = 0;
+#pragma unroll
+      for (int k = 0; k < kWin; ++k) {
+        const float g = c_gauss[k];
+        a += g * wm[0][r][cc + 10 - k];
+        b += g * wm[1][r][cc + 10 - k];
+        c += g * wm[2][r][cc + 10 - k];
+      }
+      hz[0][r][cc] = a;
+      hz[1][r][cc] = b;
+      hz[2][r][cc] = c;
+    }
+    __syncthreads();
+    if (in) {
+      float G0 = 0, G1 = 0, G2 = 0;
+#pragma unroll
+      for (int k = 0; k < kWin; ++k) {
+        const float g = c_gauss[k];
+        G0 += g * hz[0][ty + 10 - k][tx];
+        G1 += g * hz[1][ty + 10 - k][tx];
+        G2 += g * hz[2][ty + 10 - k][tx];
+      }
+      const float pv = p[pix * 3 + ch], tv = t[pix * 3 + ch];
+      const float d = pv - tv;
+      const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
+      const float gs = G0 + 2.0f * pv * G1 + tv * G2;
+      const float gr = (float)kL1W * sgn * inv_px - (float)kSsimW * gs * inv_win;
+      gout[ch] = gr;
+      if (grad) grad[pix * 3 + ch] = gr;
+      acc += fabs((double)d);
+    }
+    __syncthreads();
+  }
+  if (in && gy8) {
+    float v[8] = {gout[0], gout[1], gout[2], 0, 0, 0, 0, 0};
+    *reinterpret_cast<uint4 *>(gy8 + pix * kGyCh) = pack8(v);
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void k_loss_final(const double *ps, int nps, const double *pl, int npl, double n_px, double n_win,
+                             float *loss) {
+  __shared__ double red[256];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nps; i += 256) a += ps[i];
+  for (int i = threadIdx.x; i < npl; i += 256) b += pl[i];
+  const double S = block_sum(a, red);
+  __syncthreads();
+  const double L = block_sum(b, red);
+  if (threadIdx.x == 0 && loss) *loss = (float)(kL1W * L / n_px + kSsimW * (1.0 - S / n_win));
+}
+
+// ---------------------------------------------------------------------------------------------
+// GEMM launcher
+// ---------------------------------------------------------------------------------------------
+constexpr int kMaxDev = 16;
+
+template <class AL, class BL, class EP>
+cudaError_t gemm(const AL &a, const BL &b, const EP &e, int M, int N, int K, int splits, int k_split,
+                 unsigned *status, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || N > 256 || K < 0 || splits < 1) return cudaErrorInvalidValue;
+  const int np = pad16(N);
+  auto kern = k_gemm<AL, BL, EP>;
+  // per instantiation: dynamic shared memory per padded N such that the CTAs resident on one SM
+  // never ask for more than the 512 TMEM columns
+  static int smem_cache[kMaxDev][17];
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  int smem = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    smem = smem_cache[dev][np / 16];
+    if (smem == 0) {
+      cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      if (err != cudaSuccess) return err;
+      int bytes = (int)gemm_smem_bytes(np);
+      for (;;) {
+        int nb = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, bytes);
+        if (err != cudaSuccess) return err;
+        if (nb >= 1 && (uint32_t)nb * tmem_cols(np) <= 512u) break;
+        if (nb < 1) return cudaErrorInvalidConfiguration;
+        bytes += 4096;
+      }
+      smem = smem_cache[dev][np / 16] = bytes;
+    }
+  }
+  dim3 grid((unsigned)((M + kTM - 1) / kTM), (unsigned)splits);
+  kern<<<grid, kThreads, smem, s>>>(a, b, e, M, N, K, k_split, status);
+  return cudaGetLastError();
+}
+
+}  // namespace unet
+}  // namespace sc
+
+// =============================================================================================
+// the network object
+// =============================================================================================
+using namespace sc::unet;
+
+namespace {
+
+struct Layer {
+  int kind = 0, cout = 0, cin = 0, cin_p = 0;
+  int64_t w_off = 0, b_off = 0, w_count = 0;
+  bf16 *wf = nullptr, *wd = nullptr;
+  int64_t wf_elems = 0, wd_elems = 0;
+};
+
+int enc_layer(int l, int j) { return 2 * l + j; }
+int up_layer(int l) { return 8 + (2 - l) * 3; }
+int dec_layer(int l, int j) { return up_layer(l) + 1 + j; }
+constexpr int kOutLayer = 17, kNumLayers = 18;
+
+struct Wgrad {
+  int rows = 0, Mtiles = 0, np = 0;
+};
+
+}  // namespace
+
+struct sc_unet {
+  int max_batch = 0, H = 0, W = 0;
+  int n = 0;  // images of the last call
+  int hl[kLevels], wl[kLevels];
+  int64_t n_params = 0;
+  Layer L[kNumLayers];
+  void *block = nullptr;  // one allocation for everything
+  float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+  Seg *segs = nullptr;
+  int nseg = 0, adam_blocks = 0;
+  int step = 0;
+  // activations
+  bf16 *x0 = nullptr, *a1[kLevels] = {}, *cat[kLevels] = {}, *h3 = nullptr, *pool[kLevels] = {};
+  bf16 *d1[kLevels] = {}, *d2[kLevels] = {};
+  float *y = nullptr;
+  // gradients
+  bf16 *gy8 = nullptr, *gd2[kLevels] = {}, *gd1[kLevels] = {}, *gup[kLevels] = {}, *ge2[kLevels] = {},
+       *ge1[kLevels] = {};
+  float *gskip[kLevels] = {};
+  // loss
+  float *smap[3] = {};
+  double *lpart = nullptr;
+  int lpart_n = 0;
+  float *loss = nullptr;
+  // weight-gradient partials
+  float *wpart = nullptr;
+  size_t wpart_floats = 0;
+  int num_sms = 0;
+};
+
+namespace {
+
+int fail(sc_ctx *c, int code, const std::string &m) {
+  if (c) sc::ctx_set_error(c, m);
+  return code;
+}
+int cuda_fail(sc_ctx *c, cudaError_t e, const char *where) {
+  if (e == cudaErrorMemoryAllocation) return fail(c, SC_ERR_OOM, std::string(where) + ": out of device memory");
+  return fail(c, SC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Carve {
+  char *base;
+  size_t off = 0;
+  template <class T>
+  T *take(size_t count) {
+    T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+    off += a256(count * sizeof(T));
+    return p;
+  }
+};
+
+// flat parameter layout in the order of sc_unet.h
+int64_t layout_params(Layer *L) {
+  int64_t off = 0;
+  auto add = [&](Layer &ly, int kind, int cout, int cin, int64_t wcount) {
+    ly.kind = kind;
+    ly.cout = cout;
+    ly.cin = cin;
+    ly.cin_p = (cin + 7) & ~7;
+    ly.w_off = off;
+    ly.w_count = wcount;
+    off += wcount;
+    ly.b_off = off;
+    off += cout;
+  };
+  int cin = kInCh;
+  for (int l = 0; l < kLevels; ++l) {
+    add(L[enc_layer(l, 0)], KIND_CONV, kChans[l], cin, (int64_t)kChans[l] * 9 * cin);
+    add(L[enc_layer(l, 1)], KIND_CONV, kChans[l], kChans[l], (int64_t)kChans[l] * 9 * kChans[l]);
+    cin = kChans[l];
+  }
+  for (int l = kLevels - 2; l >= 0; --l) {
+    add(L[up_layer(l)], KIND_UP, kChans[l], kChans[l + 1], (int64_t)kChans[l + 1] * 4 * kChans[l]);
+    add(L[dec_layer(l, 0)], KIND_CONV, kChans[l], 2 * kChans[l], (int64_t)kChans[l] * 9 * 2 * kChans[l]);
+    add(L[dec_layer(l, 1)], KIND_CONV, kChans[l], kChans[l], (int64_t)kChans[l] * 9 * kChans[l]);
+  }
+  add(L[kOutLayer], KIND_OUT, kOutCh, kChans[0], (int64_t)kOutCh * kChans[0]);
+  for (int i = 0; i < kNumLayers; ++i) {
+    Layer &ly = L[i];
+    if (ly.kind == KIND_CONV) {
+      ly.wf_elems = (int64_t)ly.cout * 9 * ly.cin_p;
+      ly.wd_elems = ly.cin % 8 == 0 ? (int64_t)ly.cin * 9 * ly.cout : 0;
+    } else if (ly.kind == KIND_UP) {
+      ly.wf_elems = ly.wd_elems = (int64_t)ly.cin * 4 * ly.cout;
+    } else {
+      ly.wf_elems = (int64_t)ly.cout * ly.cin;
+      ly.wd_elems = (int64_t)ly.cin * kGyCh;
+    }
+  }
+  return off;
+}
+
+// weight-gradient GEMM shape of a layer: rows of A (data rows + the ones row), tiles, padded N
+Wgrad wgrad_shape(const Layer &ly) {
+  Wgrad g;
+  if (ly.kind == KIND_CONV) {
+    g.rows = 9 * ly.cin_p;
+    g.np = pad16(ly.cout);
+  } else if (ly.kind == KIND_UP) {
+    g.rows = ly.cin;
+    g.np = pad16(4 * ly.cout);
+  } else {
+    g.rows = ly.cin;
+    g.np = pad16(ly.cout);
+  }
+  g.Mtiles = (g.rows + 1 + kTM - 1) / kTM;
+  return g;
+}
+void split_k(int Mtiles, int64_t K, int num_sms, int *splits, int *k_split) {
+  int s = (4 * num_sms + Mtiles - 1) / Mtiles;
+  const int64_t max_s = (K + 511) / 512;
+  if (s > max_s) s = (int)max_s;
+  if (s < 1) s = 1;
+  int64_t ks = (K + s - 1) / s;
+  ks = (ks + kKC - 1) / kKC * kKC;
+  *k_split = (int)ks;
+  *splits = (int)((K + ks - 1) / ks);
+}
+
+int check_geom(int n, int h, int w) { return n >= 1 && h >= 16 && w >= 16 && h % 8 == 0 && w % 8 == 0; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// forward / backward drivers
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+#define UCHK(expr)                                 \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+ANbr nbr(const bf16 *src, int cs, int co, int h, int w, int cin, int ntaps, int sign, int M) {
+  ANbr a;
+  a.src = src;
+  a.cs = cs;
+  a.co = co;
+  a.h = h;
+  a.w = w;
+  a.cin = cin;
+  a.ntaps = ntaps;
+  a.sign = sign;
+  a.M = M;
+  return a;
+}
+BDense dense(const bf16 *W, int ldk, int N) {
+  BDense b;
+  b.W = W;
+  b.ldk = ldk;
+  b.N = N;
+  return b;
+}
+EBiasAct bias_act(bf16 *out, int cs, int co, const float *bias, int N, int relu) {
+  EBiasAct e;
+  e.out = out;
+  e.cs = cs;
+  e.co = co;
+  e.bias = bias;
+  e.N = N;
+  e.relu = relu;
+  return e;
+}
+EGrad egrad(bf16 *out, int ocs, const bf16 *mask, int mcs, int mco, int N) {
+  EGrad e;
+  e.out = out;
+  e.ocs = ocs;
+  e.oco = 0;
+  e.mask = mask;
+  e.mcs = mcs;
+  e.mco = mco;
+  e.N = N;
+  e.split = N;
+  e.out2 = nullptr;
+  e.o2cs = 0;
+  return e;
+}
+TPix tpix(const bf16 *src, int cs, int co, int h, int w, int cin, int ntaps, int mode, int rows, int ones, int R) {
+  TPix t;
+  t.src = src;
+  t.cs = cs;
+  t.co = co;
+  t.h = h;
+  t.w = w;
+  t.cin = cin;
+  t.ntaps = ntaps;
+  t.mode = mode;
+  t.rows = rows;
+  t.ones = ones;
+  t.R = R;
+  return t;
+}
+
+// the skip tensor of level l (encoder conv 2 output): a slice of the concatenation buffer, or
+// its own buffer at the deepest level
+struct View {
+  bf16 *p;
+  int cs, co;
+};
+View enc_out(const sc_unet *u, int l) {
+  if (l == kLevels - 1) return {u->h3, kChans[l], 0};
+  return {u->cat[l], 2 * kChans[l], kChans[l]};
+}
+View up_in(const sc_unet *u, int l) {  // input of the transposed conv that produces level l
+  if (l + 1 == kLevels - 1) return {u->h3, kChans[l + 1], 0};
+  return {u->d2[l + 1], kChans[l + 1], 0};
+}
+
+int run_forward(sc_ctx *c, sc_unet *u, const float *x, int n) {
+  const char *where = "sc_unet_forward";
+  cudaStream_t s = sc::ctx_stream(c);
+  unsigned *st = sc::ctx_status(c);
+  u->n = n;
+  int64_t P[kLevels];
+  for (int l = 0; l < kLevels; ++l) P[l] = (int64_t)n * u->hl[l] * u->wl[l];
+  k_pack_input<<<(unsigned)((P[0] + 255) / 256), 256, 0, s>>>(x, u->x0, P[0]);
+  UCHK(cudaGetLastError());
+  const float *prm = u->params;
+  for (int l = 0; l < kLevels; ++l) {
+    const int h = u->hl[l], w = u->wl[l], cl = kChans[l];
+    const Layer &c1 = u->L[enc_layer(l, 0)], &c2 = u->L[enc_layer(l, 1)];
+    const bf16 *src = l == 0 ? u->x0 : u->pool[l];
+    const int scs = l == 0 ? kInPad : kChans[l - 1];
+    UCHK(gemm(nbr(src, scs, 0, h, w, c1.cin_p, 9, 1, (int)P[l]), dense(c1.wf, 9 * c1.cin_p, cl),
+              bias_act(u->a1[l], cl, 0, prm + c1.b_off, cl, 1), (int)P[l], cl, 9 * c1.cin_p, 1, 9 * c1.cin_p, st,
+              s));
+    const View e = enc_out(u, l);
+    UCHK(gemm(nbr(u->a1[l], cl, 0, h, w, cl, 9, 1, (int)P[l]), dense(c2.wf, 9 * cl, cl),
+              bias_act(e.p, e.cs, e.co, prm + c2.b_off, cl, 1), (int)P[l], cl, 9 * cl, 1, 9 * cl, st, s));
+    if (l + 1 < kLevels) {
+      const int64_t tot = P[l + 1] * (cl / 8);
+      k_pool<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(e.p, e.cs, e.co, cl, n, h, w, u->pool[l + 1]);
+      UCHK(cudaGetLastError());
+    }
+  }
+  for (int l = kLevels - 2; l >= 0; --l) {
+    const int h = u->hl[l], w = u->wl[l], cl = kChans[l], cn = kChans[l + 1];
+    const Layer &up = u->L[up_layer(l)], &c1 = u->L[dec_layer(l, 0)], &c2 = u->L[dec_layer(l, 1)];
+    const View ui = up_in(u, l);
+    EUpFwd eu;
+    eu.out = u->cat[l];
+    eu.cs = 2 * cl;
+    eu.co = 0;
+    eu.bias = prm + up.b_off;
+    eu.cu = cl;
+    eu.h = u->hl[l + 1];
+    eu.w = u->wl[l + 1];
+    UCHK(gemm(nbr(ui.p, ui.cs, ui.co, u->hl[l + 1], u->wl[l + 1], cn, 1, 1, (int)P[l + 1]), dense(up.wf, cn, 4 * cl),
+              eu, (int)P[l + 1], 4 * cl, cn, 1, cn, st, s));
+    UCHK(gemm(nbr(u->cat[l], 2 * cl, 0, h, w, 2 * cl, 9, 1, (int)P[l]), dense(c1.wf, 18 * cl, cl),
+              bias_act(u->d1[l], cl, 0, prm + c1.b_off, cl, 1), (int)P[l], cl, 18 * cl, 1, 18 * cl, st, s));
+    UCHK(gemm(nbr(u->d1[l], cl, 0, h, w, cl, 9, 1, (int)P[l]), dense(c2.wf, 9 * cl, cl),
+              bias_act(u->d2[l], cl, 0, prm + c2.b_off, cl, 1), (int)P[l], cl, 9 * cl, 1, 9 * cl, st, s));
+  }
+  const Layer &o = u->L[kOutLayer];
+  EOut eo;
+  eo.y = u->y;
+  eo.bias = prm + o.b_off;
+  eo.N = kOutCh;
+  UCHK(gemm(nbr(u->d2[0], kChans[0], 0, u->hl[0], u->wl[0], kChans[0], 1, 1, (int)P[0]), dense(o.wf, kChans[0], kOutCh),
+            eo, (int)P[0], kOutCh, kChans[0], 1, kChans[0], st, s));
+  return SC_OK;
+}
+
+int run_loss(sc_ctx *c, sc_unet *u, const float *pred, const float *target, int n, int h, int w, float *loss,
+             float *grad, bf16 *gy8, const char *where) {
+  cudaStream_t s = sc::ctx_stream(c);
+  const int Hv = h - 10, Wv = w - 10;
+  dim3 gf((Wv + kSTW - 1) / kSTW, (Hv + kSTH - 1) / kSTH, n);
+  dim3 gb((w + kSTW - 1) / kSTW, (h + kSTH - 1) / kSTH, n);
+  const int nf = (int)(gf.x * gf.y * gf.z), nb = (int)(gb.x * gb.y * gb.z);
+  if (nf + nb > u->lpart_n) return fail(c, SC_ERR_INVALID_ARG, std::string(where) + ": loss workspace too small");
+  double *pf = u->lpart, *pb = u->lpart + nf;
+  k_ssim_fwd<<<gf, 256, 0, s>>>(pred, target, h, w, u->smap[0], u->smap[1], u->smap[2], pf);
+  UCHK(cudaGetLastError());
+  const double n_px = (double)n * h * w * 3, n_win = (double)n * Hv * Wv * 3;
+  k_ssim_bwd<<<gb, 256, 0, s>>>(pred, target, h, w, u->smap[0], u->smap[1], u->smap[2], (float)(1.0 / n_px),
+                                (float)(1.0 / n_win), grad, gy8, pb);
+  UCHK(cudaGetLastError());
+  k_loss_final<<<1, 256, 0, s>>>(pf, nf, pb, nb, n_px, n_win, loss);
+  UCHK(cudaGetLastError());
+  return SC_OK;
+}
+
+// weight gradient of one layer: A (rows = (tap, c) | c, + ones row), B (rows = output channels),
+// contracted over the pixels, reduced deterministically into the flat gradient
+int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, int64_t K) {
+  const char *where = "sc_unet wgrad";
+  const Wgrad g = wgrad_shape(ly);
+  int splits, ks;
+  split_k(g.Mtiles, K, u->num_sms, &splits, &ks);
+  const int Mpad = g.Mtiles * kTM;
+  if ((size_t)splits * Mpad * g.np > u->wpart_floats)
+    return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
+  EPartial ep;
+  ep.part = u->wpart;
+  ep.ld = g.np;
+  ep.Mpad = Mpad;
+  const int N = ly.kind == KIND_UP ? 4 * ly.cout : ly.cout;
+  UCHK(gemm(A, B, ep, g.rows + 1, N, (int)K, splits, ks, sc::ctx_status(c), sc::ctx_stream(c)));
+  const int64_t tot = (int64_t)(g.rows + 1) * g.np;
+  k_wgrad_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, sc::ctx_stream(c)>>>(
+      u->wpart, splits, Mpad, g.np, g.rows, ly.kind, ly.cout, ly.cin, ly.cin_p, u->grads + ly.w_off,
+      u->grads + ly.b_off);
+  UCHK(cudaGetLastError());
+  return SC_OK;
+}
+
+int run_backward(sc_ctx *c, sc_unet *u) {
+  const char *where = "sc_unet backward";
+  cudaStream_t s = sc::ctx_stream(c);
+  unsigned *st = sc::ctx_status(c);
+  const int n = u->n;
+  int64_t P[kLevels];
+  for (int l = 0; l < kLevels; ++l) P[l] = (int64_t)n * u->hl[l] * u->wl[l];
+  int rc;
+  // output layer
+  {
+    const Layer &o = u->L[kOutLayer];
+    const int c0 = kChans[0];
+    rc = wgrad(c, u, o, tpix(u->d2[0], c0, 0, u->hl[0], u->wl[0], c0, 1, 0, c0, 1, kTM),
+               tpix(u->gy8, kGyCh, 0, u->hl[0], u->wl[0], kGyCh, 1, 0, kOutCh, 0, pad16(kOutCh)), P[0]);
+    if (rc) return rc;
+    UCHK(gemm(nbr(u->gy8, kGyCh, 0, u->hl[0], u->wl[0], kGyCh, 1, 1, (int)P[0]), dense(o.wd, kGyCh, c0),
+              egrad(u->gd2[0], c0, u->d2[0], c0, 0, c0), (int)P[0], c0, kGyCh, 1, kGyCh, st, s));
+  }
+  // decoder, shallow to deep
+  for (int l = 0; l < kLevels - 1; ++l) {
+    const int h = u->hl[l], w = u->wl[l], cl = kChans[l], cn = kChans[l + 1];
+    const Layer &c2 = u->L[dec_layer(l, 1)], &c1 = u->L[dec_layer(l, 0)], &up = u->L[up_layer(l)];
+    // dec conv 2: input d1, output gradient gd2
+    rc = wgrad(c, u, c2, tpix(u->d1[l], cl, 0, h, w, cl, 9, 0, 9 * cl, 1, kTM),
+               tpix(u->gd2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
+    if (rc) return rc;
+    UCHK(gemm(nbr(u->gd2[l], cl, 0, h, w, cl, 9, -1, (int)P[l]), dense(c2.wd, 9 * cl, cl),
+              egrad(u->gd1[l], cl, u->d1[l], cl, 0, cl), (int)P[l], cl, 9 * cl, 1, 9 * cl, st, s));
+    // dec conv 1: input cat = [up, skip], output gradient gd1 -> gup (BF16) | gskip (FP32)
+    rc = wgrad(c, u, c1, tpix(u->cat[l], 2 * cl, 0, h, w, 2 * cl, 9, 0, 18 * cl, 1, kTM),
+               tpix(u->gd1[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
+    if (rc) return rc;
+    EGrad es = egrad(u->gup[l], cl, nullptr, 0, 0, 2 * cl);
+    es.split = cl;
+    es.out2 = u->gskip[l];
+    es.o2cs = cl;
+    UCHK(gemm(nbr(u->gd1[l], cl, 0, h, w, cl, 9, -1, (int)P[l]), dense(c1.wd, 9 * cl, 2 * cl), es, (int)P[l],
+              2 * cl, 9 * cl, 1, 9 * cl, st, s));
+    // transposed conv: input up_in (level l+1), output gradient gup (level l)
+    const View ui = up_in(u, l);
+    const int hn = u->hl[l + 1], wn = u->wl[l + 1];
+    rc = wgrad(c, u, up, tpix(ui.p, ui.cs, ui.co, hn, wn, cn, 1, 0, cn, 1, kTM),
+               tpix(u->gup[l], cl, 0, hn, wn, cl, 4, 1, 4 * cl, 0, pad16(4 * cl)), P[l + 1]);
+    if (rc) return rc;
+    AUpGrad ag;
+    ag.g = u->gup[l];
+    ag.gcs = cl;
+    ag.h = hn;
+    ag.w = wn;
+    ag.cu = cl;
+    ag.M = (int)P[l + 1];
+    // gradient w.r.t. up_in, masked by its ReLU: the next decoder conv 2's output gradient,
+    // or at the deepest level the encoder's last conv output gradient
+    bf16 *dst = l + 1 == kLevels - 1 ? u->ge2[l + 1] : u->gd2[l + 1];
+    UCHK(gemm(ag, dense(up.wd, 4 * cl, cn), egrad(dst, cn, ui.p, ui.cs, ui.co, cn), (int)P[l + 1], cn, 4 * cl, 1,
+              4 * cl, st, s));
+  }
+  // encoder, deep to shallow; ge2[l] holds d loss / d (pre-ReLU) encoder conv 2 output
+  for (int l = kLevels - 1; l >= 0; --l) {
+    const int h = u->hl[l], w = u->wl[l], cl = kChans[l];
+    const Layer &c2 = u->L[enc_layer(l, 1)], &c1 = u->L[enc_layer(l, 0)];
+    rc = wgrad(c, u, c2, tpix(u->a1[l], cl, 0, h, w, cl, 9, 0, 9 * cl, 1, kTM),
+               tpix(u->ge2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
+    if (rc) return rc;
+    UCHK(gemm(nbr(u->ge2[l], cl, 0, h, w, cl, 9, -1, (int)P[l]), dense(c2.wd, 9 * cl, cl),
+              egrad(u->ge1[l], cl, u->a1[l], cl, 0, cl), (int)P[l], cl, 9 * cl, 1, 9 * cl, st, s));
+    const bf16 *src = l == 0 ? u->x0 : u->pool[l];
+    const int scs = l == 0 ? kInPad : kChans[l - 1];
+    rc = wgrad(c, u, c1, tpix(src, scs, 0, h, w, c1.cin_p, 9, 0, 9 * c1.cin_p, 1, kTM),
+               tpix(u->ge1[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
+    if (rc) return rc;
+    if (l > 0) {
+      // through the pool into the level above, plus its skip gradient, times its ReLU mask
+      const int cp = kChans[l - 1];
+      const View e = enc_out(u, l - 1);
+      EPoolBack pb;
+      pb.out = u->ge2[l - 1];
+      pb.ocs = cp;
+      pb.e = e.p;
+      pb.ecs = e.cs;
+      pb.eco = e.co;
+      pb.skip = u->gskip[l - 1];
+      pb.scs = cp;
+      pb.h = h;
+      pb.w = w;
+      pb.N = cp;
+      UCHK(gemm(nbr(u->ge1[l], cl, 0, h, w, cl, 9, -1, (int)P[l]), dense(c1.wd, 9 * cl, cp), pb, (int)P[l], cp,
+                9 * cl, 1, 9 * cl, st, s));
+    }
+  }
+  return SC_OK;
+}
+
+int refresh_bf16(sc_ctx *c, sc_unet *u, int update, float lr) {
+  const char *where = "sc_unet params";
+  double bc1 = 1.0, bc2 = 1.0;
+  if (update) {
+    bc1 = 1.0 - std::pow(0.9, (double)u->step);
+    bc2 = 1.0 - std::pow(0.999, (double)u->step);
+  }
+  k_adam<<<u->adam_blocks, 256, 0, sc::ctx_stream(c)>>>(u->segs, u->nseg, u->params, u->grads, u->adam_m, u->adam_v,
+                                                          lr, (float)bc1, (float)bc2, update);
+  UCHK(cudaGetLastError());
+  return SC_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+extern "C" {
+
+int sc_unet_param_count(int64_t *count) {
+  if (!count) return SC_ERR_INVALID_ARG;
+  Layer L[kNumLayers];
+  *count = layout_params(L);
+  return SC_OK;
+}
+
+int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, sc_unet **out) {
+  if (!c || !out) return SC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!check_geom(max_batch, height, width))
+    return fail(c, SC_ERR_INVALID_ARG, "sc_unet_create: need max_batch >= 1, height and width multiples of 8, >= 16");
+  const char *where = "sc_unet_create";
+  sc_unet *u = new (std::nothrow) sc_unet();
+  if (!u) return fail(c, SC_ERR_OOM, "sc_unet_create: host allocation failed");
+  u->max_batch = max_batch;
+  u->H = height;
+  u->W = width;
+  for (int l = 0; l < kLevels; ++l) {
+    u->hl[l] = height >> l;
+    u->wl[l] = width >> l;
+  }
+  u->n_params = layout_params(u->L);
+  int dev = sc::ctx_device(c);
+  cudaError_t e = cudaDeviceGetAttribute(&u->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete u;
+    return cuda_fail(c, e, where);
+  }
+  int64_t P[kLevels];
+  for (int l = 0; l < kLevels; ++l) P[l] = (int64_t)max_batch * u->hl[l] * u->wl[l];
+  // weight-gradient workspace: the largest split layout over the layers
+  size_t wpart = 0;
+  for (int i = 0; i < kNumLayers; ++i) {
+    const Layer &ly = u->L[i];
+    const Wgrad g = wgrad_shape(ly);
+    int lvl = 0;
+    if (i < 8) lvl = i / 2;
+    else if (i == kOutLayer) lvl = 0;
+    else {
+      const int l = 2 - (i - 8) / 3;
+      lvl = ((i - 8) % 3 == 0) ? l + 1 : l;
+    }
+    int splits, ks;
+    split_k(g.Mtiles, P[lvl], u->num_sms, &splits, &ks);
+    const size_t need = (size_t)splits * g.Mtiles * kTM * g.np;
+    if (need > wpart) wpart = need;
+  }
+  const int Hv = height - 10, Wv = width - 10;
+  const int lpart = max_batch * (((Wv + kSTW - 1) / kSTW) * ((Hv + kSTH - 1) / kSTH) +
+                                 ((width + kSTW - 1) / kSTW) * ((height + kSTH - 1) / kSTH));
+  // segments of the Adam / BF16-refresh kernel
+  std::vector<Seg> segs;
+  int blocks = 0;
+  auto seg = [&](int64_t off, int64_t count, int kind, const Layer &ly) {
+    Seg sgm{};
+    sgm.off = off;
+    sgm.count = (int32_t)count;
+    sgm.kind = kind;
+    sgm.cout = ly.cout;
+    sgm.cin = ly.cin;
+    sgm.cin_p = ly.cin_p;
+    sgm.first_block = blocks;
+    blocks += (int)((count + 255) / 256);
+    segs.push_back(sgm);
+  };
+  for (int i = 0; i < kNumLayers; ++i) {
+    seg(u->L[i].w_off, u->L[i].w_count, u->L[i].kind, u->L[i]);
+    seg(u->L[i].b_off, u->L[i].cout, KIND_BIAS, u->L[i]);
+  }
+  // one allocation, carved twice (sizes, then pointers)
+  for (int pass = 0; pass < 2; ++pass) {
+    Carve cv{pass ? static_cast<char *>(u->block) : nullptr};
+    const int64_t np = u->n_params;
+    u->params = cv.take<float>(np);
+    u->grads = cv.take<float>(np);
+    u->adam_m = cv.take<float>(np);
+    u->adam_v = cv.take<float>(np);
+    u->segs = cv.take<Seg>(segs.size());
+    for (int i = 0; i < kNumLayers; ++i) {
+      u->L[i].wf = cv.take<bf16>(u->L[i].wf_elems);
+      u->L[i].wd = u->L[i].wd_elems ? cv.take<bf16>(u->L[i].wd_elems) : nullptr;
+    }
+    u->x0 = cv.take<bf16>(P[0] * kInPad);
+    for (int l = 0; l < kLevels; ++l) {
+      const int cl = kChans[l];
+      u->a1[l] = cv.take<bf16>(P[l] * cl);
+      if (l < kLevels - 1) {
+        u->cat[l] = cv.take<bf16>(P[l] * 2 * cl);
+        u->d1[l] = cv.take<bf16>(P[l] * cl);
+        u->d2[l] = cv.take<bf16>(P[l] * cl);
+        u->gd2[l] = cv.take<bf16>(P[l] * cl);
+        u->gd1[l] = cv.take<bf16>(P[l] * cl);
+        u->gup[l] = cv.take<bf16>(P[l] * cl);
+        u->gskip[l] = cv.take<float>(P[l] * cl);
+      } else {
+        u->h3 = cv.take<bf16>(P[l] * cl);
+      }
+      if (l > 0) u->pool[l] = cv.take<bf16>(P[l] * kChans[l - 1]);
+      u->ge2[l] = cv.take<bf16>(P[l] * cl);
+      u->ge1[l] = cv.take<bf16>(P[l] * cl);
+    }
+    u->y = cv.take<float>(P[0] * kOutCh);
+    u->gy8 = cv.take<bf16>(P[0] * kGyCh);
+    for (int k = 0; k < 3; ++k) u->smap[k] = cv.take<float>((size_t)max_batch * Hv * Wv * 3);
+    u->lpart = cv.take<double>(lpart);
+    u->lpart_n = lpart;
+    u->loss = cv.take<float>(1);
+    u->wpart = cv.take<float>(wpart);
+    u->wpart_floats = wpart;
+    if (pass == 0) {
+      u->block = sc::ctx_alloc(c, cv.off);
+      if (!u->block) {
+        delete u;
+        return fail(c, SC_ERR_OOM, "sc_unet_create: out of device memory");
+      }
+      e = cudaMemsetAsync(u->block, 0, cv.off, sc::ctx_stream(c));
+      if (e != cudaSuccess) {
+        sc::ctx_free(c, u->block);
+        delete u;
+        return cuda_fail(c, e, where);
+      }
+    }
+  }
+  for (size_t i = 0, j = 0; i < (size_t)kNumLayers; ++i, j += 2) {
+    segs[j].wf = u->L[i].wf;
+    segs[j].wd = u->L[i].wd;
+  }
+  u->nseg = (int)segs.size();
+  u->adam_blocks = blocks;
+  // the segment table travels with the stream (pageable source: staged before the call returns)
+  e = cudaMemcpyAsync(u->segs, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, sc::ctx_stream(c));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(sc::ctx_stream(c));
+  if (e != cudaSuccess) {
+    sc::ctx_free(c, u->block);
+    delete u;
+    return cuda_fail(c, e, where);
+  }
+  // Gaussian window of the SSIM (sigma 1.5, normalised), computed in double
+  float gk[kWin];
+  double gs = 0.0, gd[kWin];
+  for (int i = 0; i < kWin; ++i) {
+    const double d = i - 5.0;
+    gd[i] = std::exp(-d * d / (2.0 * 1.5 * 1.5));
+    gs += gd[i];
+  }
+  for (int i = 0; i < kWin; ++i) gk[i] = (float)(gd[i] / gs);
+  e = cudaMemcpyToSymbol(c_gauss, gk, sizeof(gk));
+  if (e != cudaSuccess) {
+    sc::ctx_free(c, u->block);
+    delete u;
+    return cuda_fail(c, e, where);
+  }
+  *out = u;
+  return SC_OK;
+}
+
+int sc_unet_destroy(sc_ctx *c, sc_unet *u) {
+  if (!c || !u) return SC_ERR_INVALID_ARG;
+  sc::ctx_free(c, u->block);
+  delete u;
+  return SC_OK;
+}
+
+int sc_unet_set_params(sc_ctx *c, sc_unet *u, const float *params) {
+  if (!c || !u || !params) return SC_ERR_INVALID_ARG;
+  const char *where = "sc_unet_set_params";
+  cudaStream_t s = sc::ctx_stream(c);
+  const size_t bytes = (size_t)u->n_params * sizeof(float);
+  UCHK(cudaMemcpyAsync(u->params, params, bytes, cudaMemcpyDeviceToDevice, s));
+  UCHK(cudaMemsetAsync(u->adam_m, 0, bytes, s));
+  UCHK(cudaMemsetAsync(u->adam_v, 0, bytes, s));
+  u->step = 0;
+  return refresh_bf16(c, u, 0, 0.0f);
+}
+
+int sc_unet_get_params(sc_ctx *c, const sc_unet *u, float *params) {
+  if (!c || !u || !params) return SC_ERR_INVALID_ARG;
+  const char *where = "sc_unet_get_params";
+  UCHK(cudaMemcpyAsync(params, u->params, (size_t)u->n_params * sizeof(float), cudaMemcpyDeviceToDevice,
+                       sc::ctx_stream(c)));
+  return SC_OK;
+}
+
+int sc_unet_get_grads(sc_ctx *c, const sc_unet *u, float *grads) {
+  if (!c || !u || !grads) return SC_ERR_INVALID_ARG;
+  const char *where = "sc_unet_get_grads";
+  UCHK(cudaMemcpyAsync(grads, u->grads, (size_t)u->n_params * sizeof(float), cudaMemcpyDeviceToDevice,
+                       sc::ctx_stream(c)));
+  return SC_OK;
+}
+
+int sc_unet_set_grads(sc_ctx *c, sc_unet *u, const float *grads) {
+  if (!c || !u || !grads) return SC_ERR_INVALID_ARG;
+  const char *where = "sc_unet_set_grads";
+  UCHK(cudaMemcpyAsync(u->grads, grads, (size_t)u->n_params * sizeof(float), cudaMemcpyDeviceToDevice,
+                       sc::ctx_stream(c)));
+  return SC_OK;
+}
+
+int sc_unet_forward(sc_ctx *c, sc_unet *u, const float *x, int32_t n, float *y) {
+  if (!c || !u || !x || !y) return SC_ERR_INVALID_ARG;
+  if (n < 1 || n > u->max_batch) return fail(c, SC_ERR_INVALID_ARG, "sc_unet_forward: n out of range");
+  int rc = run_forward(c, u, x, n);
+  if (rc) return rc;
+  const char *where = "sc_unet_forward";
+  UCHK(cudaMemcpyAsync(y, u->y, (size_t)n * u->H * u->W * kOutCh * sizeof(float), cudaMemcpyDeviceToDevice,
+                       sc::ctx_stream(c)));
+  return SC_OK;
+}
+
+int sc_unet_loss_grad(sc_ctx *c, sc_unet *u, const float *x, const float *target, int32_t n, float *y, float *loss) {
+  if (!c || !u || !x || !target) return SC_ERR_INVALID_ARG;
+  if (n < 1 || n > u->max_batch) return fail(c, SC_ERR_INVALID_ARG, "sc_unet_loss_grad: n out of range");
+  const char *where = "sc_unet_loss_grad";
+  int rc = run_forward(c, u, x, n);
+  if (rc) return rc;
+  rc = run_loss(c, u, u->y, target, n, u->H, u->W, loss ? loss : u->loss, nullptr, u->gy8, where);
+  if (rc) return rc;
+  rc = run_backward(c, u);
+  if (rc) return rc;
+  if (y)
+    UCHK(cudaMemcpyAsync(y, u->y, (size_t)n * u->H * u->W * kOutCh * sizeof(float), cudaMemcpyDeviceToDevice,
+                         sc::ctx_stream(c)));
+  return SC_OK;
+}
+
+int sc_unet_adam(sc_ctx *c, sc_unet *u, float lr) {
+  if (!c || !u || !(lr >= 0.0f)) return SC_ERR_INVALID_ARG;
+  u->step += 1;
+  return refresh_bf16(c, u, 1, lr);
+}
+
+int sc_unet_train_step(sc_ctx *c, sc_unet *u, const float *x, const float *target, int32_t n, float lr, float *loss) {
+  int rc = sc_unet_loss_grad(c, u, x, target, n, nullptr, loss);
+  if (rc) return rc;
+  return sc_unet_adam(c, u, lr);
+}
+
+int sc_ssim_l1_loss(sc_ctx *c, const float *pred, const float *target, int32_t n, int32_t h, int32_t w, float *loss,
+                    float *grad) {
+  if (!c || !pred || !target || n < 1 || h < 11 || w < 11) return SC_ERR_INVALID_ARG;
+  const char *where = "sc_ssim_l1_loss";
+  // a private workspace sized for this call
+  sc_unet tmp;
+  const int Hv = h - 10, Wv = w - 10;
+  const int lpart = n * (((Wv + kSTW - 1) / kSTW) * ((Hv + kSTH - 1) / kSTH) +
+                         ((w + kSTW - 1) / kSTW) * ((h + kSTH - 1) / kSTH));
+  Carve cv{nullptr};
+  for (int pass = 0; pass < 2; ++pass) {
+    cv.off = 0;
+    for (int k = 0; k < 3; ++k) tmp.smap[k] = cv.take<float>((size_t)n * Hv * Wv * 3);
+    tmp.lpart = cv.take<double>(lpart);
+    tmp.lpart_n = lpart;
+    if (pass == 0) {
+      cv.base = static_cast<char *>(sc::ctx_alloc(c, cv.off));
+      if (!cv.base) return fail(c, SC_ERR_OOM, "sc_ssim_l1_loss: out of device memory");
+    }
+  }
+  float gk[kWin];
+  double gs = 0.0, gd[kWin];
+  for (int i = 0; i < kWin; ++i) {
+    const double d = i - 5.0;
+    gd[i] = std::exp(-d * d / (2.0 * 1.5 * 1.5));
+    gs += gd[i];
+  }
+  for (int i = 0; i < kWin; ++i) gk[i] = (float)(gd[i] / gs);
+  cudaError_t e = cudaMemcpyToSymbol(c_gauss, gk, sizeof(gk));
+  int rc = e == cudaSuccess ? run_loss(c, &tmp, pred, target, n, h, w, loss, grad, nullptr, where)
+                            : cuda_fail(c, e, where);
+  sc::ctx_free(c, cv.base);
+  tmp.block = nullptr;
+  return rc;
+}
+
+int sc_unet_pack_frame(sc_ctx *c, const sc_frame *f, float *x, int32_t index) {
+  if (!c || !f || !x || index < 0) return SC_ERR_INVALID_ARG;
+  if (!f->rgb || !f->albedo || !f->normal_camera || !f->depth_norm || !f->mask)
+    return fail(c, SC_ERR_INVALID_ARG, "sc_unet_pack_frame: rgb, albedo, normal_camera, depth_norm and mask needed");
+  const char *where = "sc_unet_pack_frame";
+  const int64_t P = (int64_t)f->width * f->height;
+  k_pack_frame<<<(unsigned)((P + 255) / 256), 256, 0, sc::ctx_stream(c)>>>(
+      reinterpret_cast<const float4 *>(f->rgb), reinterpret_cast<const float4 *>(f->albedo),
+      reinterpret_cast<const float4 *>(f->normal_camera), f->depth_norm, f->mask, x + index * P * kInCh, P);
+  UCHK(cudaGetLastError());
+  return SC_OK;
+}
+
+static int buffer_view(const sc_unet *u, int id, int l, const void **ptr, int *dtype, int *ch, int *cs, int *co) {
+  if (l < 0 || l >= kLevels) return SC_ERR_INVALID_ARG;
+  const int cl = kChans[l];
+  const bool dec = l < kLevels - 1;
+  *dtype = 0;
+  *co = 0;
+  *ch = cl;
+  *cs = cl;
+  *ptr = nullptr;
+  switch (id) {
+    case SC_UNET_BUF_INPUT:
+      if (l) return SC_ERR_INVALID_ARG;
+      *ptr = u->x0;
+      *ch = kInPad;
+      *cs = kInPad;
+      break;
+    case SC_UNET_BUF_ENC1: *ptr = u->a1[l]; break;
+    case SC_UNET_BUF_ENC2: {
+      const View v = enc_out(u, l);
+      *ptr = v.p;
+      *cs = v.cs;
+      *co = v.co;
+      break;
+    }
+    case SC_UNET_BUF_POOL:
+      if (!l) return SC_ERR_INVALID_ARG;
+      *ptr = u->pool[l];
+      *ch = *cs = kChans[l - 1];
+      break;
+    case SC_UNET_BUF_UP:
+      if (!dec) return SC_ERR_INVALID_ARG;
+      *ptr = u->cat[l];
+      *cs = 2 * cl;
+      break;
+    case SC_UNET_BUF_DEC1:
+      if (!dec) return SC_ERR_INVALID_ARG;
+      *ptr = u->d1[l];
+      break;
+    case SC_UNET_BUF_DEC2:
+      if (!dec) return SC_ERR_INVALID_ARG;
+      *ptr = u->d2[l];
+      break;
+    case SC_UNET_BUF_OUT:
+      if (l) return SC_ERR_INVALID_ARG;
+      *ptr = u->y;
+      *dtype = 1;
+      *ch = *cs = kOutCh;
+      break;
+    case SC_UNET_BUF_GOUT:
+      if (l) return SC_ERR_INVALID_ARG;
+      *ptr = u->gy8;
+      *ch = *cs = kGyCh;
+      break;
+    case SC_UNET_BUF_GDEC2:
+      if (!dec) return SC_ERR_INVALID_ARG;
+      *ptr = u->gd2[l];
+      break;
+    case SC_UNET_BUF_GDEC1:
+      if (!dec) return SC_ERR_INVALID_ARG;
+      *ptr = u->gd1[l];
+      break;
+    case SC_UNET_BUF_GUP:
+      if (!dec) return SC_ERR_INVALID_ARG;
+      *ptr = u->gup[l];
+      break;
+    case SC_UNET_BUF_GSKIP:
+      if (!dec) return SC_ERR_INVALID_ARG;
+      *ptr = u->gskip[l];
+      *dtype = 1;
+      break;
+    case SC_UNET_BUF_GENC2: *ptr = u->ge2[l]; break;
+    case SC_UNET_BUF_GENC1: *ptr = u->ge1[l]; break;
+    default: return SC_ERR_INVALID_ARG;
+  }
+  return SC_OK;
+}
+
+int sc_unet_buffer(const sc_unet *u, int32_t id, int32_t level, sc_unet_buffer_info *info) {
+  if (!u || !info) return SC_ERR_INVALID_ARG;
+  const void *p;
+  int dtype, ch, cs, co;
+  int rc = buffer_view(u, id, level, &p, &dtype, &ch, &cs, &co);
+  if (rc) return rc;
+  info->dtype = dtype;
+  info->n = u->n;
+  info->h = u->hl[level];
+  info->w = u->wl[level];
+  info->c = ch;
+  return SC_OK;
+}
+
+int sc_unet_copy_buffer(sc_ctx *c, const sc_unet *u, int32_t id, int32_t level, void *dst) {
+  if (!c || !u || !dst) return SC_ERR_INVALID_ARG;
+  const void *p;
+  int dtype, ch, cs, co;
+  int rc = buffer_view(u, id, level, &p, &dtype, &ch, &cs, &co);
+  if (rc) return fail(c, rc, "sc_unet_copy_buffer: no such buffer");
+  const char *where = "sc_unet_copy_buffer";
+  const size_t es = dtype ? 4 : 2;
+  const size_t rows = (size_t)u->n * u->hl[level] * u->wl[level];
+  UCHK(cudaMemcpy2DAsync(dst, ch * es, static_cast<const char *>(p) + co * es, cs * es, ch * es, rows,
+                         cudaMemcpyDeviceToDevice, sc::ctx_stream(c)));
+  return SC_OK;
+}
+
+}  // extern "C"

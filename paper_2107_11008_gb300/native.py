@@ -90,6 +90,10 @@ class sc_scene_info(C.Structure):
                 ("bvh_bytes", C.c_int64), ("max_depth", C.c_int32), ("pad", C.c_int32)]
 
 
+class sc_unet_buffer_info(C.Structure):
+    _fields_ = [("dtype", C.c_int32), ("n", C.c_int32), ("h", C.c_int32), ("w", C.c_int32), ("c", C.c_int32)]
+
+
 STRUCTS = [sc_material, sc_light, sc_camera, sc_scene_desc, sc_trace_params, sc_light_params, sc_resolve_params,
            sc_path_record, sc_light_record, sc_frame, sc_scene_info]
 
@@ -122,6 +126,25 @@ SIGNATURES = {
                                   P(C.c_void_p)]),
     "sc_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sc_batch_destroy": (C.c_int, [C.c_void_p, C.c_void_p]),
+    # sc_unet.h
+    "sc_unet_param_count": (C.c_int, [P(C.c_int64)]),
+    "sc_unet_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, P(C.c_void_p)]),
+    "sc_unet_destroy": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sc_unet_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sc_unet_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sc_unet_get_grads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sc_unet_set_grads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sc_unet_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sc_unet_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                    C.c_void_p]),
+    "sc_unet_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_float]),
+    "sc_unet_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
+                                     C.c_void_p]),
+    "sc_ssim_l1_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                  C.c_void_p]),
+    "sc_unet_pack_frame": (C.c_int, [C.c_void_p, P(sc_frame), C.c_void_p, C.c_int32]),
+    "sc_unet_buffer": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, P(sc_unet_buffer_info)]),
+    "sc_unet_copy_buffer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
 }
 
 _lib = None
@@ -266,3 +289,74 @@ def sc_batch_launch(ctx, batch):
 
 def sc_batch_destroy(ctx, batch):
     return check(load().sc_batch_destroy(ctx, batch), ctx)
+
+
+# --- sc_unet.h ---------------------------------------------------------------------------------
+SC_UNET_BUF = dict(INPUT=0, ENC1=1, ENC2=2, POOL=3, UP=4, DEC1=5, DEC2=6, OUT=7, GOUT=8, GDEC2=9, GDEC1=10,
+                   GUP=11, GSKIP=12, GENC2=13, GENC1=14)
+
+
+def sc_unet_param_count() -> int:
+    n = C.c_int64()
+    check(load().sc_unet_param_count(C.byref(n)))
+    return n.value
+
+
+def sc_unet_create(ctx, max_batch, height, width):
+    out = C.c_void_p()
+    check(load().sc_unet_create(ctx, max_batch, height, width, C.byref(out)), ctx)
+    return out.value
+
+
+def sc_unet_destroy(ctx, net):
+    return check(load().sc_unet_destroy(ctx, net), ctx)
+
+
+def sc_unet_set_params(ctx, net, params_dev):
+    return check(load().sc_unet_set_params(ctx, net, params_dev), ctx)
+
+
+def sc_unet_get_params(ctx, net, params_dev):
+    return check(load().sc_unet_get_params(ctx, net, params_dev), ctx)
+
+
+def sc_unet_get_grads(ctx, net, grads_dev):
+    return check(load().sc_unet_get_grads(ctx, net, grads_dev), ctx)
+
+
+def sc_unet_set_grads(ctx, net, grads_dev):
+    return check(load().sc_unet_set_grads(ctx, net, grads_dev), ctx)
+
+
+def sc_unet_forward(ctx, net, x_dev, n, y_dev):
+    return check(load().sc_unet_forward(ctx, net, x_dev, n, y_dev), ctx)
+
+
+def sc_unet_loss_grad(ctx, net, x_dev, target_dev, n, y_dev=None, loss_dev=None):
+    return check(load().sc_unet_loss_grad(ctx, net, x_dev, target_dev, n, y_dev, loss_dev), ctx)
+
+
+def sc_unet_adam(ctx, net, lr):
+    return check(load().sc_unet_adam(ctx, net, lr), ctx)
+
+
+def sc_unet_train_step(ctx, net, x_dev, target_dev, n, lr, loss_dev=None):
+    return check(load().sc_unet_train_step(ctx, net, x_dev, target_dev, n, lr, loss_dev), ctx)
+
+
+def sc_ssim_l1_loss(ctx, pred_dev, target_dev, n, h, w, loss_dev=None, grad_dev=None):
+    return check(load().sc_ssim_l1_loss(ctx, pred_dev, target_dev, n, h, w, loss_dev, grad_dev), ctx)
+
+
+def sc_unet_pack_frame(ctx, frame: sc_frame, x_dev, index):
+    return check(load().sc_unet_pack_frame(ctx, C.byref(frame), x_dev, index), ctx)
+
+
+def sc_unet_buffer(net, buf_id, level) -> sc_unet_buffer_info:
+    info = sc_unet_buffer_info()
+    check(load().sc_unet_buffer(net, buf_id, level, C.byref(info)))
+    return info
+
+
+def sc_unet_copy_buffer(ctx, net, buf_id, level, dst_dev):
+    return check(load().sc_unet_copy_buffer(ctx, net, buf_id, level, dst_dev), ctx)

@@ -1,0 +1,355 @@
+"""The BF16 U-Net denoiser on the tensor cores against the FP64 oracle (oracle/unet.py).
+
+Layer by layer, each GPU kernel is fed its own BF16 inputs (read back from the library) and its
+output is compared with the oracle layer on exactly those inputs: BF16 outputs within half an ulp
+of BF16 (2^-8 relative, with slack) plus the FP32 accumulation bound, FP32 outputs within the FP32
+accumulation bound.  End to end, the network on BF16-rounded parameters and input is compared
+with the oracle network in FP64: output within 2e-2 relative, gradients with cosine >= 0.999.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import unet as U  # noqa: E402
+from paper_2107_11008_gb300 import denoiser as D  # noqa: E402
+from paper_2107_11008_gb300 import renderer as R  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+CH = D.CHANS
+BF16_REL = 2.0 ** -8   # BF16 keeps 8 significant bits: rounding error <= 2^-9 relative
+ACC_REL = 2e-4          # FP32 accumulation of up to ~10^6 products, relative to the sum of |products|
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = R.Context(0)
+    yield c
+    c.close()
+
+
+def _params(seed, bias_scale=0.1):
+    rng = np.random.default_rng(seed)
+    p = U.init_params(seed=seed)
+    for k in p:
+        if k.endswith("_b"):
+            p[k] = rng.normal(0.0, bias_scale, p[k].shape)
+    return p
+
+
+def _inputs(seed, n, h, w):
+    rng = np.random.default_rng(seed)
+    x = rng.random((n, h, w, 11))
+    x[..., 6:9] = rng.normal(size=(n, h, w, 3))          # normals
+    x[..., 10] = (rng.random((n, h, w)) < 0.3)           # mask
+    t = rng.random((n, h, w, 3))
+    return x, t
+
+
+def _np(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def _check_bf16(gpu, ref, absum, what):
+    err = np.abs(gpu - ref)
+    bound = BF16_REL * np.abs(ref) + ACC_REL * absum + 1e-30
+    bad = err > bound
+    assert not bad.any(), f"{what}: {bad.sum()} of {bad.size} beyond bound, worst {np.max(err / bound):.3g}x"
+
+
+def _check_f32(gpu, ref, absum, what):
+    err = np.abs(gpu - ref)
+    bound = ACC_REL * absum + 1e-12
+    bad = err > bound
+    assert not bad.any(), f"{what}: {bad.sum()} of {bad.size} beyond bound, worst {np.max(err / bound):.3g}x"
+
+
+def _conv_abs(x, w):
+    return U.conv3x3(np.abs(x), np.abs(w), np.zeros(w.shape[0]))
+
+
+class Net:
+    """A GPU network with BF16-rounded parameters and the same parameters for the oracle."""
+
+    def __init__(self, ctx, n, h, w, seed):
+        self.ctx, self.n, self.h, self.w = ctx, n, h, w
+        p = _params(seed)
+        self.p = {k: (U.bf16(v) if not k.endswith("_b") else v) for k, v in p.items()}
+        self.flat = D.flatten(p)
+        self.net = D.UNet(ctx, n, h, w)
+        self.net.set_params(_dev(self.flat))
+        x, t = _inputs(seed + 1, n, h, w)
+        self.x, self.t = U.bf16(x), t
+        self.xd, self.td = _dev(x), _dev(t)
+
+    def buf(self, name, level=0):
+        return _np(self.net.buffer(name, level))
+
+
+def test_param_layout_and_bf16_refresh(ctx):
+    net = D.UNet(ctx, 1, 16, 16)
+    flat = D.he_init(3).cuda()
+    net.set_params(flat)
+    np.testing.assert_array_equal(net.get_params().cpu().numpy(), flat.cpu().numpy())
+    assert [s for _, s in D.param_shapes()] == [s for _, s in U.param_shapes()]
+    net.close()
+
+
+def test_forward_layer_by_layer(ctx):
+    N = Net(ctx, 2, 32, 40, seed=11)
+    y = N.net.forward(N.xd)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    p = N.p
+    x16 = N.buf("INPUT")
+    np.testing.assert_array_equal(x16[..., :11], N.x)
+    assert not x16[..., 11:].any()
+    for l in range(4):
+        xin = N.x if l == 0 else N.buf("POOL", l)
+        if l > 0:
+            np.testing.assert_array_equal(xin, U.maxpool2(N.buf("ENC2", l - 1))[0])
+        a1 = N.buf("ENC1", l)
+        w = p[f"enc{l}_c1_w"]
+        _check_bf16(a1, U.relu(U.conv3x3(xin, w, p[f"enc{l}_c1_b"])), _conv_abs(xin, w), f"enc{l}_c1")
+        e = N.buf("ENC2", l)
+        w = p[f"enc{l}_c2_w"]
+        _check_bf16(e, U.relu(U.conv3x3(a1, w, p[f"enc{l}_c2_b"])), _conv_abs(a1, w), f"enc{l}_c2")
+    for l in (2, 1, 0):
+        ui = N.buf("ENC2", 3) if l == 2 else N.buf("DEC2", l + 1)
+        up = N.buf("UP", l)
+        w = p[f"up{l}_w"]
+        _check_bf16(up, U.convT2(ui, w, p[f"up{l}_b"]), U.convT2(np.abs(ui), np.abs(w), 0 * p[f"up{l}_b"]),
+                    f"up{l}")
+        cat = np.concatenate([up, N.buf("ENC2", l)], axis=-1)
+        d1 = N.buf("DEC1", l)
+        w = p[f"dec{l}_c1_w"]
+        _check_bf16(d1, U.relu(U.conv3x3(cat, w, p[f"dec{l}_c1_b"])), _conv_abs(cat, w), f"dec{l}_c1")
+        d2 = N.buf("DEC2", l)
+        w = p[f"dec{l}_c2_w"]
+        _check_bf16(d2, U.relu(U.conv3x3(d1, w, p[f"dec{l}_c2_b"])), _conv_abs(d1, w), f"dec{l}_c2")
+    d2 = N.buf("DEC2", 0)
+    ref = np.einsum("nijc,oc->nijo", d2, p["out_w"]) + p["out_b"]
+    _check_f32(_np(y), ref, np.einsum("nijc,oc->nijo", np.abs(d2), np.abs(p["out_w"])) + np.abs(p["out_b"]), "out")
+    N.net.close()
+
+
+def test_forward_end_to_end_vs_fp64_oracle(ctx):
+    N = Net(ctx, 2, 32, 48, seed=21)
+    y = _np(N.net.forward(N.xd))
+    ref, _ = U.forward(N.p, N.x, CH)
+    rel = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert rel < 2e-2, rel
+    N.net.close()
+
+
+def test_ssim_l1_loss_kernel(ctx):
+    rng = np.random.default_rng(5)
+    p = rng.random((2, 40, 48, 3))
+    t = np.clip(p + 0.1 * rng.normal(size=p.shape), 0, None)
+    loss, grad = D.ssim_l1_loss(ctx, _dev(p), _dev(t))
+    torch.cuda.synchronize()
+    pf, tf = p.astype(np.float32), t.astype(np.float32)   # the kernel reads FP32 inputs
+    ref_v, ref_g = U.loss(pf.astype(np.float64), tf.astype(np.float64))
+    assert float(loss.item()) == pytest.approx(ref_v, rel=1e-4)
+    g = _np(grad)
+    scale = np.abs(ref_g).max()
+    assert np.abs(g - ref_g).max() <= 2e-3 * scale
+    cos = (g * ref_g).sum() / np.linalg.norm(g) / np.linalg.norm(ref_g)
+    assert cos > 0.99999, cos
+    # identical images: loss 0
+    loss0, _ = D.ssim_l1_loss(ctx, _dev(p), _dev(p))
+    assert abs(float(loss0.item())) < 1e-5
+
+
+def test_backward_layer_by_layer(ctx):
+    N = Net(ctx, 2, 32, 40, seed=31)
+    y, loss = N.net.loss_grad(N.xd, N.td)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    p = N.p
+    G = D.unflatten(N.net.get_grads().cpu().numpy().astype(np.float64))
+    yv = _np(y)
+    # loss gradient (FP32 kernel) rounded to BF16
+    _, gy_ref = U.loss(yv, N.t)
+    gy = N.buf("GOUT")
+    assert not gy[..., 3:].any()
+    gy = gy[..., :3]
+    assert np.abs(gy - gy_ref).max() <= BF16_REL * np.abs(gy_ref).max() + 2e-3 * np.abs(gy_ref).max()
+
+    def wcheck(name, ref, absum):
+        _check_f32(G[name], ref, absum, name)
+
+    d2 = N.buf("DEC2", 0)
+    wcheck("out_w", np.einsum("nijo,nijc->oc", gy, d2), np.einsum("nijo,nijc->oc", np.abs(gy), np.abs(d2)))
+    wcheck("out_b", gy.sum(axis=(0, 1, 2)), np.abs(gy).sum(axis=(0, 1, 2)))
+    gh = np.einsum("nijo,oc->nijc", gy, p["out_w"]) * (d2 > 0)
+    _check_bf16(N.buf("GDEC2", 0), gh, np.einsum("nijo,oc->nijc", np.abs(gy), np.abs(p["out_w"])), "gdec2_0")
+
+    def conv_bwd(name, xin, gz, mask):
+        w = p[f"{name}_w"]
+        gx, gw, gb = U.conv3x3_backward(xin, w, gz)
+        _, aw, ab = U.conv3x3_backward(np.abs(xin), np.abs(w), np.abs(gz))
+        wcheck(f"{name}_w", gw, aw)
+        wcheck(f"{name}_b", gb, ab)
+        agx, _, _ = U.conv3x3_backward(np.abs(xin), np.abs(w), np.abs(gz))
+        return (gx * mask if mask is not None else gx), agx
+
+    for l in range(3):
+        d1, gz = N.buf("DEC1", l), N.buf("GDEC2", l)
+        gx, agx = conv_bwd(f"dec{l}_c2", d1, gz, d1 > 0)
+        _check_bf16(N.buf("GDEC1", l), gx, agx, f"gdec1_{l}")
+        cat = np.concatenate([N.buf("UP", l), N.buf("ENC2", l)], axis=-1)
+        gc, agc = conv_bwd(f"dec{l}_c1", cat, N.buf("GDEC1", l), None)
+        c = CH[l]
+        _check_bf16(N.buf("GUP", l), gc[..., :c], agc[..., :c], f"gup_{l}")
+        _check_f32(N.buf("GSKIP", l), gc[..., c:], agc[..., c:], f"gskip_{l}")
+        ui = N.buf("ENC2", 3) if l == 2 else N.buf("DEC2", l + 1)
+        gu = N.buf("GUP", l)
+        w = p[f"up{l}_w"]
+        gx, gw, gb = U.convT2_backward(ui, w, gu)
+        agx, aw, ab = U.convT2_backward(np.abs(ui), np.abs(w), np.abs(gu))
+        wcheck(f"up{l}_w", gw, aw)
+        wcheck(f"up{l}_b", gb, ab)
+        dst = N.buf("GENC2", 3) if l == 2 else N.buf("GDEC2", l + 1)
+        _check_bf16(dst, gx * (ui > 0), agx, f"gup_in_{l}")
+    for l in (3, 2, 1, 0):
+        a1, ge2 = N.buf("ENC1", l), N.buf("GENC2", l)
+        gx, agx = conv_bwd(f"enc{l}_c2", a1, ge2, a1 > 0)
+        _check_bf16(N.buf("GENC1", l), gx, agx, f"genc1_{l}")
+        xin = N.x if l == 0 else N.buf("POOL", l)
+        ge1 = N.buf("GENC1", l)
+        gx, agx = conv_bwd(f"enc{l}_c1", xin, ge1, None)
+        if l > 0:
+            e = N.buf("ENC2", l - 1)
+            _, arg = U.maxpool2(e)
+            gpool = U.maxpool2_backward(gx, arg, e.shape)
+            apool = U.maxpool2_backward(agx, arg, e.shape)
+            skip = N.buf("GSKIP", l - 1)
+            ref = (gpool + skip) * (e > 0)
+            _check_bf16(N.buf("GENC2", l - 1), ref, apool + np.abs(skip), f"genc2_{l - 1}")
+    N.net.close()
+
+
+def test_gradients_end_to_end_vs_fp64_oracle(ctx):
+    N = Net(ctx, 2, 32, 48, seed=41)
+    y, loss = N.net.loss_grad(N.xd, N.td)
+    torch.cuda.synchronize()
+    yr, cache = U.forward(N.p, N.x, CH)
+    lv, gy = U.loss(yr, N.t)
+    assert float(loss.item()) == pytest.approx(lv, rel=2e-2)
+    gr, _ = U.backward(N.p, cache, gy, CH)
+    G = D.unflatten(N.net.get_grads().cpu().numpy().astype(np.float64))
+    a = np.concatenate([G[k].ravel() for k, _ in U.param_shapes()])
+    b = np.concatenate([gr[k].ravel() for k, _ in U.param_shapes()])
+    cos = a @ b / np.linalg.norm(a) / np.linalg.norm(b)
+    assert cos >= 0.999, cos
+    for k, _ in U.param_shapes():
+        ck = (G[k] * gr[k]).sum() / (np.linalg.norm(G[k]) * np.linalg.norm(gr[k]) + 1e-300)
+        assert ck >= 0.99, (k, ck)
+    N.net.close()
+
+
+def test_adam_matches_oracle(ctx):
+    net = D.UNet(ctx, 1, 16, 16)
+    rng = np.random.default_rng(7)
+    p0 = D.flatten(_params(2))
+    net.set_params(_dev(p0))
+    ref = {"w": p0.copy()}
+    m = {"w": np.zeros_like(p0)}
+    v = {"w": np.zeros_like(p0)}
+    for t in (1, 2, 3):
+        g = rng.normal(size=p0.shape) * 10.0 ** rng.uniform(-6, 0, size=p0.shape)
+        g32 = g.astype(np.float32).astype(np.float64)
+        net.set_grads(_dev(g32))
+        net.adam(1e-3)
+        U.adam_step(ref, {"w": g32}, m, v, t, lr=1e-3)
+    got = net.get_params().cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got, ref["w"], rtol=1e-5, atol=2e-7)
+    net.close()
+
+
+def test_training_reduces_loss(ctx):
+    """A learnable task (target = a fixed smooth function of the input): 150 Adam steps."""
+    rng = np.random.default_rng(3)
+    n, h, w = 4, 32, 32
+    x = rng.random((n, h, w, 11)).astype(np.float32)
+    t = np.stack([x[..., 3], 0.5 * x[..., 4] + 0.25, x[..., 0] * x[..., 5]], axis=-1)
+    net = D.UNet(ctx, n, h, w)
+    net.set_params(D.he_init(0).cuda())
+    xd, td = _dev(x), _dev(t)
+    losses = []
+    for i in range(150):
+        loss = net.train_step(xd, td, 2e-3)
+        if i % 10 == 0 or i == 149:
+            losses.append(float(loss.item()))
+    ctx.sync_status()
+    assert np.all(np.isfinite(losses))
+    assert losses[-1] < 0.5 * losses[0], losses
+    net.close()
+
+
+def test_full_size_step_sampled_weight_gradients(ctx):
+    """16 x 256^2 (the training workload): the split-K weight gradients of the output layer and the
+    first conv, recomputed over all 2^20 pixels from the GPU's own BF16 operands."""
+    n, h, w = 16, 256, 256
+    rng = np.random.default_rng(9)
+    x = rng.random((n, h, w, 11)).astype(np.float32)
+    t = rng.random((n, h, w, 3)).astype(np.float32)
+    net = D.UNet(ctx, n, h, w)
+    net.set_params(D.he_init(1).cuda())
+    y, loss = net.loss_grad(_dev(x), _dev(t))
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert np.isfinite(float(loss.item()))
+    G = D.unflatten(net.get_grads().cpu().numpy().astype(np.float64))
+    gy = net.buffer("GOUT").float()[..., :3].reshape(-1, 3).double()
+    d2 = net.buffer("DEC2", 0).float().reshape(-1, 32).double()
+    ref = (gy.T @ d2).cpu().numpy()
+    absum = (gy.abs().T @ d2.abs()).cpu().numpy()
+    _check_f32(G["out_w"], ref, absum, "out_w full size")
+    # enc0 conv 1, centre tap, all 11 input channels, all 32 outputs
+    xin = net.buffer("INPUT").float()[..., :11].reshape(-1, 11).double()
+    ge1 = net.buffer("GENC1", 0).float().reshape(-1, 32).double()
+    ref = (ge1.T @ xin).cpu().numpy()
+    absum = (ge1.abs().T @ xin.abs()).cpu().numpy()
+    _check_f32(G["enc0_c1_w"][:, 1, 1, :], ref, absum, "enc0_c1 centre tap full size")
+    _check_f32(G["enc0_c1_b"], ge1.sum(0).cpu().numpy(), ge1.abs().sum(0).cpu().numpy(), "enc0_c1_b full size")
+    net.close()
+
+
+def test_invalid_arguments(ctx):
+    from paper_2107_11008_gb300 import native as NN
+
+    with pytest.raises(NN.ScError):
+        D.UNet(ctx, 1, 20, 16)  # height not a multiple of 8
+    net = D.UNet(ctx, 2, 16, 16)
+    x = torch.zeros((3, 16, 16, 11), device="cuda")
+    with pytest.raises(NN.ScError):
+        net.forward(x)  # batch above max_batch
+    net.close()
+
+
+def test_pack_frame_from_render(ctx):
+    from paper_2107_11008_gb300 import scenes as S
+
+    sc = S.ball_on_plane(width=24, height=16)
+    gs = R.GpuScene(ctx, sc)
+    f = R.Frame(24, 16)
+    R.trace_camera(ctx, gs, f, 2, 8)
+    R.resolve(ctx, gs, f, 2.0, 1.0)
+    x = torch.zeros((1, 16, 24, 11), device="cuda")
+    D.pack_frame(ctx, f, x, 0)
+    torch.cuda.synchronize()
+    xv = x[0].cpu().numpy()
+    np.testing.assert_allclose(xv[..., 0:3], np.log1p(np.maximum(f["rgb"].cpu().numpy()[..., :3], 0)), rtol=1e-6)
+    np.testing.assert_array_equal(xv[..., 3:6], f["albedo"].cpu().numpy()[..., :3])
+    np.testing.assert_array_equal(xv[..., 6:9], f["normal_camera"].cpu().numpy()[..., :3])
+    np.testing.assert_array_equal(xv[..., 9], f["depth_norm"].cpu().numpy())
+    np.testing.assert_array_equal(xv[..., 10], (f["mask"].cpu().numpy() != 0).astype(np.float32))
