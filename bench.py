@@ -53,9 +53,11 @@ def parse():
     ap.add_argument("--res", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="glass512", choices=["glass512", "batch64"],
+    ap.add_argument("--den-ratio", type=int, default=64, help="denoise workload: light paths per camera sample")
+    ap.add_argument("--workload", default="glass512", choices=["glass512", "batch64", "unet_train", "denoise"],
                     help="batch64: 64 randomised scenes (1k-200k tris, 128^2..1024^2, 64 spp) in one graph-captured "
-                         "persistent launch vs 64 sequential launches")
+                         "persistent launch vs 64 sequential launches; unet_train: U-Net training steps on batches "
+                         "of 16 x 256^2 render pairs; denoise: 4-spp render + U-Net vs the plain tracer at matched MSE")
     return ap.parse_args()
 
 
@@ -116,6 +118,292 @@ def run_batch(args):
                 "sequential_launches": {"ms_per_step": seq_ms, "value": world * paths / (seq_ms * 1e-3) / 1e6},
                 "batch_over_sequential": seq_ms / batch_ms, "scene_generation_s": gen_s, "lbvh_build_s": build_s,
                 "gpu_launches": args.steps, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# U-Net denoiser workloads
+# ---------------------------------------------------------------------------------------------
+UNET_CHANS = (32, 48, 64, 128)
+# our kernels per training step: input pack, 8 encoder convs, 3 pools, 3 x (up, 2 convs), output
+# conv (22); loss (3); output layer wgrad+reduce+dgrad (3); decoder 3 x 3 layers x 3 (27); encoder
+# 8 convs x (wgrad+reduce+dgrad) minus the first layer's dgrad (23); Adam (1)
+UNET_TRAIN_LAUNCHES = 22 + 3 + 3 + 27 + 23 + 1
+UNET_FWD_LAUNCHES = 22
+
+
+def unet_macs(h, w, in_ch=11, out_ch=3):
+    """Multiply-adds of one forward pass over an h x w image (algorithmic: unpadded channels)."""
+    c = UNET_CHANS
+    px = [(h >> l) * (w >> l) for l in range(4)]
+    m, cin = 0, in_ch
+    for l in range(4):
+        m += px[l] * 9 * cin * c[l] + px[l] * 9 * c[l] * c[l]
+        cin = c[l]
+    for l in range(3):
+        m += px[l + 1] * c[l + 1] * 4 * c[l] + px[l] * 9 * 2 * c[l] * c[l] + px[l] * 9 * c[l] * c[l]
+    return m + px[0] * c[0] * out_ch
+
+
+def unet_train_macs(h, w, in_ch=11):
+    """Forward + data gradients (all layers but the first) + weight gradients."""
+    first = h * w * 9 * in_ch * UNET_CHANS[0]
+    return 3 * unet_macs(h, w, in_ch) - first
+
+
+def unet_cpu_baseline(seconds, h=64, w=64):
+    """The FP64 NumPy oracle, as it stands: forward + loss + backward of one 64 x 64 image, repeated
+    for about `seconds`; reported as 256^2 images/s by pixel count."""
+    import numpy as np
+
+    from oracle import unet as U
+
+    rng = np.random.default_rng(0)
+    p = U.init_params(seed=0)
+    x, t = rng.random((1, h, w, 11)), rng.random((1, h, w, 3))
+    n, t0 = 0, time.perf_counter()
+    while True:
+        y, cache = U.forward(p, x, UNET_CHANS)
+        _, gy = U.loss(y, t)
+        U.backward(p, cache, gy, UNET_CHANS)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > seconds or n >= 50:
+            break
+    scale = (h * w) / (256 * 256)
+    return {"value": n / el * scale, "unit": "images/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} forward+loss+backward passes of one {h}x{w} image in FP64 NumPy ({el:.1f} s; numpy may use "
+                      f"up to {os.cpu_count()} BLAS threads), scaled to 256^2 images by pixel count"}
+
+
+def run_unet_train(args):
+    """Training steps of the BF16 U-Net on batches of 16 render pairs at 256^2 (config-1-type scenes:
+    4 spp + AOV input, 256 spp target; the step's work does not depend on the pixel values)."""
+    import torch
+
+    from paper_2107_11008_gb300 import denoiser as D
+    from paper_2107_11008_gb300 import renderer as R
+    from paper_2107_11008_gb300 import scenes as S
+    from paper_2107_11008_gb300 import training as T
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, hw = 16, 256
+    stream = torch.cuda.current_stream(dev)
+    ctx = R.Context(local, stream)
+    pairs = T.make_pairs(ctx, [S.denoise_scene(100 * rank + i, hw, hw) for i in range(n)], T.RenderSpec(4, 4),
+                         T.RenderSpec(256, 256), seed=rank)
+    net = D.UNet(ctx, n, hw, hw)
+    net.set_params(D.he_init(0).to(dev))
+    x, t = pairs.x.contiguous(), pairs.target.contiguous()
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    lr = 1e-4
+    for _ in range(max(3, args.warmup)):
+        net.train_step(x, t, lr, loss)
+    torch.cuda.synchronize(dev)
+    ctx.sync_status()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    sampler = ClockSampler(local)
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        net.train_step(x, t, lr, loss)
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ctx.sync_status()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    # forward alone (inference throughput of the same batch)
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        net.forward(x)
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    fwd_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    # end to end: the batch from pinned host memory each step, the loss read back
+    xh, th = x.cpu().pin_memory(), t.cpu().pin_memory()
+    lh = torch.empty(1, dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x.copy_(xh, non_blocking=True)
+        t.copy_(th, non_blocking=True)
+        net.train_step(x, t, lr, loss)
+        lh.copy_(loss, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    value = world * n / (ms * 1e-3)
+    flops = 2.0 * unet_train_macs(hw, hw) * n
+    pk = peaks()
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    achieved = flops / (ms * 1e-3) / 1e12
+    if rank == 0:
+        cb = None if args.no_cpu_baseline or world > 1 else unet_cpu_baseline(min(args.cpu_seconds, 15.0))
+        line = {"metric": "U-Net training images/s (16 x 256^2 per step)", "value": value, "unit": "images/s",
+                "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                "data": "synthetic (render pairs of scenes.denoise_scene)",
+                "config": {"workload": "unet_train: U-Net 11->3, widths 32/48/64/128 (585,363 params), batch 16 of "
+                                       "256^2, loss 0.16 L1 + 0.84 (1 - SSIM 11x11), Adam",
+                           "l2": "working set ~1.5 GB > L2 (no flush)", "parallelism": f"replicas x{world}"},
+                "forward_ms": fwd_ms, "forward_images_s": world * n / (fwd_ms * 1e-3),
+                "roofline": {"kernel": "all U-Net GEMMs of the step (tcgen05 BF16, FP32 accumulate)", "bound": "tensor",
+                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                             "traffic": None, "flops_per_step": flops,
+                             "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"},
+                "e2e": {"value": world * n / e2e_s, "unit": "images/s",
+                        "h2d_bytes_per_step": (xh.numel() + th.numel()) * 4, "d2h_bytes_per_step": 4},
+                "gpu_launches": UNET_TRAIN_LAUNCHES * args.steps, "clocks": clocks, "cpu_baseline": cb}
+        print(json.dumps(line), flush=True)
+
+
+def run_denoise(args):
+    """Denoised frames vs the plain tracer at matched MSE on held-out config-1-type scenes at 256^2.
+
+    Both pipelines spend the same ratio of light paths to camera samples (``--den-ratio``, 64):
+    the denoised frame is 4 camera spp + 4 x ratio light paths per pixel, the U-Net removing the
+    camera estimate's noise (it is trained on 64 pairs: that estimate at 4 spp -> 1024 spp) and
+    the light-traced caustic buffer added back; the plain frame is N spp + N x ratio light paths.
+    MSEs are against a reference of two independent halves (2048 spp + 8192 light paths / px
+    each), with the reference's own variance, MSE(half_a, half_b) / 4, subtracted."""
+    import numpy as np
+    import torch
+
+    from paper_2107_11008_gb300 import denoiser as D
+    from paper_2107_11008_gb300 import renderer as R
+    from paper_2107_11008_gb300 import scenes as S
+    from paper_2107_11008_gb300 import training as T
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hw, n_train, n_test, ratio = 256, 64, 8, args.den_ratio
+    lo = T.RenderSpec(4, 4 * ratio)
+    stream = torch.cuda.current_stream(dev)
+    ctx = R.Context(local, stream)
+    t0 = time.perf_counter()
+    train = T.make_pairs(ctx, [S.denoise_scene(i, hw, hw) for i in range(n_train)], lo, T.RenderSpec(1024, 0),
+                         seed=1, source="direct")
+    test_scenes = [S.denoise_scene(10_000 + i, hw, hw) for i in range(n_test)]
+    test = T.make_pairs(ctx, test_scenes, lo, T.RenderSpec(0, 0), seed=2, source="direct")
+    gss = [R.GpuScene(ctx, s) for s in test_scenes]
+    f = R.Frame(hw, hw, device=dev)
+    half = T.RenderSpec(2048, 8192)
+    ref_a = torch.empty_like(test.rgb_lo)
+    ref_b = torch.empty_like(test.rgb_lo)
+    for i, g in enumerate(gss):
+        for k, dst in enumerate((ref_a, ref_b)):
+            T.render(ctx, g, f, half, seed=3, sample_offset=(1 << 24) + k * half.spp,
+                     path_offset=(1 << 42) + k * 8192 * hw * hw, scene_index=i)
+            dst[i].copy_(f["rgb"])
+    ref = 0.5 * (ref_a + ref_b)
+    var_ref = T.mse(ref_a, ref_b) / 4.0
+    gen_s = time.perf_counter() - t0
+    net = D.UNet(ctx, 8, hw, hw)
+    net.set_params(D.he_init(0).to(dev))
+    t0 = time.perf_counter()
+    T.train(net, train, steps=1500, batch=8, lr=2e-3, lr_final=5e-5, seed=0)
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    ctx.sync_status()
+    den = T.denoise(net, test.x, test.add())
+    m_den = T.mse(den, ref) - var_ref
+    m_in = T.mse(test.rgb_lo, ref) - var_ref
+    # plain tracer at increasing budgets, same light/camera ratio, samples disjoint from the reference's
+    sweep = {}
+    for spp in (4, 8, 16, 32, 64, 128):
+        out = torch.empty_like(ref)
+        for i, g in enumerate(gss):
+            T.render(ctx, g, f, T.RenderSpec(spp, spp * ratio), seed=7, scene_index=i)
+            out[i].copy_(f["rgb"])
+        sweep[spp] = T.mse(out, ref) - var_ref
+    ctx.sync_status()
+    budgets = sorted(sweep)
+    above = [s for s in budgets if sweep[s] > m_den]
+    below = [s for s in budgets if sweep[s] <= m_den]
+    if below and above:  # log-log interpolation between the bracketing budgets
+        s_lo, s_hi = max(above), min(below)
+        a, b = np.log(sweep[s_lo]), np.log(sweep[s_hi])
+        spp_match = float(np.exp(np.log(s_lo) + (np.log(m_den) - a) / (b - a) * (np.log(s_hi) - np.log(s_lo))))
+    elif below:
+        spp_match = float(budgets[0])
+    else:  # beyond the sweep: MSE ~ 1/spp from the largest budget
+        spp_match = budgets[-1] * sweep[budgets[-1]] / m_den
+    # timed frames on test scene 0: (a) 4 spp + caustics + denoise, (b) plain at the matched budget
+    g0 = gss[0]
+    x1 = torch.empty((1, hw, hw, 11), dtype=torch.float32, device=dev)
+    y1 = torch.empty((1, hw, hw, 3), dtype=torch.float32, device=dev)
+    rgb1 = torch.empty((1, hw, hw, 4), dtype=torch.float32, device=dev)
+    net1 = D.UNet(ctx, 1, hw, hw)
+    net1.set_params(net.get_params())
+
+    def denoised_frame():
+        T.render(ctx, g0, f, lo, seed=11)
+        D.pack_frame(ctx, f, x1, 0, source="direct")
+        net1.forward(x1, y1)
+        D.output_rgb(ctx, y1, f["caustic"], out=rgb1)
+
+    spp_int = max(1, int(np.ceil(spp_match)))
+    plain_spec = T.RenderSpec(spp_int, spp_int * ratio)
+
+    def plain_frame():
+        T.render(ctx, g0, f, plain_spec, seed=11)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for fn in (denoised_frame, plain_frame):
+        for _ in range(max(3, args.warmup)):
+            fn()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        denoised_frame()
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    den_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        plain_frame()
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    # the network alone
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        net1.forward(x1, y1)
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    net_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    clocks = sampler.stop()
+    ctx.sync_status()
+    # end to end: the denoised RGB read back to pinned host memory every frame
+    out_h = torch.empty((hw, hw, 4), dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        denoised_frame()
+        out_h.copy_(rgb1[0], non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if rank == 0:
+        line = {"metric": "denoised fps at the plain tracer's matched MSE (256^2 ball-on-plane scenes)",
+                "value": world * 1e3 / den_ms, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": den_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic (scenes.denoise_scene)",
+                "config": {"workload": "denoise: 256^2 config-1-type scenes; U-Net on the camera estimate trained "
+                                       "1500 steps on 64 pairs (4 -> 1024 spp), light-traced caustics added back; "
+                                       "8 held-out scenes; reference 2 x (2048 spp + 8192 light paths/px)",
+                           "input": f"{lo.spp} camera spp + {lo.lights_per_pixel} light paths/px",
+                           "light_paths_per_camera_sample": ratio},
+                "mse": {"denoised": m_den, "input": m_in, "reference_variance": var_ref, "plain_sweep": sweep},
+                "matched_spp": spp_match, "plain_frame": {"spp": spp_int, "light_paths_per_px": spp_int * ratio,
+                                                          "ms": plain_ms, "fps": world * 1e3 / plain_ms},
+                "fps_ratio_denoised_over_plain": plain_ms / den_ms, "unet_forward_ms": net_ms,
+                "setup_s": {"pairs_and_reference": gen_s, "training": train_s},
+                "e2e": {"value": world * 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": hw * hw * 16},
+                "gpu_launches": args.steps * ((3 + 1 + UNET_FWD_LAUNCHES + 1) + 3 + UNET_FWD_LAUNCHES),
+                "clocks": clocks, "cpu_baseline": None}
         print(json.dumps(line), flush=True)
 
 
@@ -255,6 +543,12 @@ def main():
         return
     if args.workload == "batch64":
         run_batch(args)
+        return
+    if args.workload == "unet_train":
+        run_unet_train(args)
+        return
+    if args.workload == "denoise":
+        run_denoise(args)
         return
     import torch
     import torch.distributed as dist

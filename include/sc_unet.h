@@ -89,10 +89,23 @@ int sc_unet_train_step(sc_ctx *ctx, sc_unet *net, const float *x, const float *t
 int sc_ssim_l1_loss(sc_ctx *ctx, const float *pred, const float *target, int32_t n, int32_t h, int32_t w,
                     float *loss, float *grad);
 
+/* Which radiance estimate a network input / target is built from: the full image (camera paths
+ * + light-traced caustics, sc_frame.rgb) or the camera estimator alone (sc_frame.direct), in
+ * which case the caustic buffer is added back after denoising (sc_unet_output_rgb's `add`). */
+enum { SC_UNET_SRC_RGB = 0, SC_UNET_SRC_DIRECT = 1 };
+
 /* Builds the 11-channel network input from a rendered frame's buffers (supercaustics.h
- * sc_frame: rgb, albedo, normal, depth_norm, mask) for image `index` of a batch:
- * x + index * H * W * 11 receives [log1p(max(rgb, 0)), albedo, normal, depth_norm, mask != 0]. */
-int sc_unet_pack_frame(sc_ctx *ctx, const sc_frame *frame, float *x, int32_t index);
+ * sc_frame: rgb or direct, albedo, normal_camera, depth_norm, mask) for image `index` of a
+ * batch: x + index * H * W * 11 receives [log1p(max(L, 0)), albedo, normal, depth_norm,
+ * mask != 0], L the estimate selected by `source`. */
+int sc_unet_pack_frame(sc_ctx *ctx, const sc_frame *frame, int32_t source, float *x, int32_t index);
+
+/* Training target of a rendered frame: t + index * H * W * 3 receives log1p(max(L, 0)). */
+int sc_unet_pack_target(sc_ctx *ctx, const sc_frame *frame, int32_t source, float *t, int32_t index);
+/* Denoised linear RGB from network outputs: rgb[p] = (expm1(y[p][0..2]) clamped at 0, plus
+ * add[p].xyz when add is given, 1) for n_px pixels; y FP32 [n_px][3], add float4 [n_px] or NULL,
+ * rgb float4 [n_px] (all device). */
+int sc_unet_output_rgb(sc_ctx *ctx, const float *y, int64_t n_px, const float *add, float *rgb);
 
 /* Internal tensors, for inspection by tests: id below, level 0..3. */
 enum {

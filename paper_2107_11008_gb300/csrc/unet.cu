@@ -2,14 +2,18 @@
 // Adam, all on the GPU.  Every convolution (forward, data gradient, weight gradient), the
 // transposed convolutions and the 1x1 output layer run through the tcgen05 GEMM of
 // unet_gemm.cuh; pooling, the loss, the weight-gradient reduction and Adam are plain CUDA.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "internal.h"
 #include "sc_unet.h"
+#include "unet_conv.cuh"
 #include "unet_gemm.cuh"
 
 namespace sc {
@@ -66,6 +70,29 @@ __global__ void k_pack_frame(const float4 *rgb, const float4 *albedo, const floa
   o[10] = mask[p] ? 1.0f : 0.0f;
 }
 
+__global__ void k_pack_target(const float4 *rgb, float *t, int64_t P) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float4 c = rgb[p];
+  t[p * 3 + 0] = log1pf(fmaxf(c.x, 0.0f));
+  t[p * 3 + 1] = log1pf(fmaxf(c.y, 0.0f));
+  t[p * 3 + 2] = log1pf(fmaxf(c.z, 0.0f));
+}
+
+__global__ void k_output_rgb(const float *y, int64_t P, const float4 *add, float4 *rgb) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float4 o = make_float4(fmaxf(expm1f(y[p * 3]), 0.0f), fmaxf(expm1f(y[p * 3 + 1]), 0.0f),
+                         fmaxf(expm1f(y[p * 3 + 2]), 0.0f), 1.0f);
+  if (add) {
+    const float4 a = add[p];
+    o.x += a.x;
+    o.y += a.y;
+    o.z += a.z;
+  }
+  rgb[p] = o;
+}
+
 // 2x2 stride-2 max pool of a channel slice: src (h x w, stride cs, offset co) -> dst [P/4][C]
 __global__ void k_pool(const bf16 *src, int cs, int co, int C, int n, int h, int w, bf16 *dst) {
   const int groups = C / 8;
@@ -92,48 +119,68 @@ enum { KIND_BIAS = 0, KIND_CONV = 1, KIND_UP = 2, KIND_OUT = 3 };
 
 // Sum of the K-split partial products in a fixed order, scattered to the flat FP32 gradient.
 // part[(s * Mpad + r) * np + n]; rows r: conv (tap * cin_p + c) | ones; up: c | ones;
-// out: c | ones.
-__global__ void k_wgrad_reduce(const float *part, int splits, int Mpad, int np, int rows, int kind, int cout, int cin,
-                               int cin_p, float *gw, float *gb) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= (int64_t)(rows + 1) * np) return;
+// out: c | ones.  Block = 32 consecutive entries (r, n) x 8 split groups; group g sums splits
+// g, g + 8, ... (coalesced 128-byte reads), then the 8 group sums are added in order.
+constexpr int kRedEntries = 32, kRedGroups = 8;
+
+__device__ __forceinline__ float split_sum(const float *part, int splits, int Mpad, int np, int r, int n, int g) {
+  float s = 0.0f;
+  for (int k = g; k < splits; k += kRedGroups) s += part[((int64_t)k * Mpad + r) * np + n];
+  return s;
+}
+
+__global__ void __launch_bounds__(kRedEntries *kRedGroups) k_wgrad_reduce(const float *part, int splits, int Mpad,
+                                                                           int np, int rows, int kind, int cout,
+                                                                           int cin, int cin_p, float *gw, float *gb) {
+  __shared__ float sh[kRedGroups][kRedEntries];
+  const int e = threadIdx.x % kRedEntries, g = threadIdx.x / kRedEntries;
+  const int64_t i = (int64_t)blockIdx.x * kRedEntries + e;
+  const int64_t total = (int64_t)(rows + 1) * np;
   const int r = (int)(i / np), n = (int)(i % np);
-  auto sum = [&](int rr, int nn) {
-    float s = 0.0f;
-    for (int k = 0; k < splits; ++k) s += part[((int64_t)k * Mpad + rr) * np + nn];
-    return s;
-  };
+  const bool valid = i < total;
+  // the bias of a transposed conv sums its four (a, e) column blocks of the ones row
+  float v = 0.0f;
+  if (valid) {
+    if (kind == KIND_UP && r == rows) {
+      if (n < cout)
+        for (int ae = 0; ae < 4; ++ae) v += split_sum(part, splits, Mpad, np, r, ae * cout + n, g);
+    } else {
+      v = split_sum(part, splits, Mpad, np, r, n, g);
+    }
+  }
+  sh[g][e] = v;
+  __syncthreads();
+  if (g != 0 || !valid) return;
+  float t = 0.0f;
+  for (int k = 0; k < kRedGroups; ++k) t += sh[k][e];
   if (kind == KIND_CONV) {
     if (n >= cout) return;
     if (r == rows) {
-      gb[n] = sum(r, n);
+      gb[n] = t;
       return;
     }
     const int tap = r / cin_p, c = r - tap * cin_p;
-    if (c < cin) gw[((int64_t)n * 9 + tap) * cin + c] = sum(r, n);
+    if (c < cin) gw[((int64_t)n * 9 + tap) * cin + c] = t;
   } else if (kind == KIND_UP) {
-    if (n >= 4 * cout) return;
     if (r == rows) {
-      if (n < cout) {
-        float s = 0.0f;
-        for (int ae = 0; ae < 4; ++ae) s += sum(r, ae * cout + n);
-        gb[n] = s;
-      }
+      if (n < cout) gb[n] = t;
       return;
     }
+    if (n >= 4 * cout) return;
     const int ae = n / cout, o = n - ae * cout;
-    gw[((int64_t)r * 4 + ae) * cout + o] = sum(r, n);
+    gw[((int64_t)r * 4 + ae) * cout + o] = t;
   } else {  // KIND_OUT
     if (n >= cout) return;
-    if (r == rows) gb[n] = sum(r, n);
-    else gw[(int64_t)n * cin + r] = sum(r, n);
+    if (r == rows) gb[n] = t;
+    else gw[(int64_t)n * cin + r] = t;
   }
 }
 
 struct Seg {
   int64_t off;
   int32_t count, kind, cout, cin, cin_p, first_block;
-  bf16 *wf, *wd;
+  bf16 *wf, *wd;    // B layouts of the gathering GEMM (forward, data gradient)
+  bf16 *wtf, *wtd;  // B layouts of the TMA convolution: [tap][k-group][n][8]
 };
 
 // One bias-corrected Adam step over every parameter (update != 0), then the BF16 copies:
@@ -164,7 +211,11 @@ __global__ void k_adam(const Seg *segs, int nseg, float *p, const float *g, floa
   if (S.kind == KIND_CONV) {
     const int o = i / (9 * S.cin), rem = i - o * 9 * S.cin, tap = rem / S.cin, c = rem - tap * S.cin;
     S.wf[((int64_t)o * 9 + tap) * S.cin_p + c] = b;
-    if (S.wd) S.wd[((int64_t)c * 9 + tap) * S.cout + o] = b;
+    S.wtf[(((int64_t)tap * (S.cin_p / 8) + c / 8) * S.cout + o) * 8 + (c & 7)] = b;
+    if (S.wd) {
+      S.wd[((int64_t)c * 9 + tap) * S.cout + o] = b;
+      S.wtd[(((int64_t)tap * (S.cout / 8) + o / 8) * S.cin + c) * 8 + (o & 7)] = b;
+    }
   } else if (S.kind == KIND_UP) {
     const int c = i / (4 * S.cout), rem = i - c * 4 * S.cout;
     S.wf[(int64_t)rem * S.cin + c] = b;
@@ -397,7 +448,7 @@ namespace {
 struct Layer {
   int kind = 0, cout = 0, cin = 0, cin_p = 0;
   int64_t w_off = 0, b_off = 0, w_count = 0;
-  bf16 *wf = nullptr, *wd = nullptr;
+  bf16 *wf = nullptr, *wd = nullptr, *wtf = nullptr, *wtd = nullptr;
   int64_t wf_elems = 0, wd_elems = 0;
 };
 
@@ -624,6 +675,72 @@ View up_in(const sc_unet *u, int l) {  // input of the transposed conv that prod
   return {u->d2[l + 1], kChans[l + 1], 0};
 }
 
+// ---- 3x3 convolution: TMA halo-tile kernel where the row width allows, gathering GEMM otherwise
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+bool conv_tma_ok(int cin, int N, int w) {
+  return w % 128 == 0 && cin % 16 == 0 && N % 16 == 0 && N <= 128 && conv_smem_bytes(cin, N) <= 227 * 1024 &&
+         tensor_map_encoder() != nullptr;
+}
+
+// src: NHWC BF16 slice (stride cs, offset co) with `cin` channels per tap; N output channels;
+// wdense: [N][9][cin] (gathering GEMM), wtma: [tap][cin/8][N][8] (TMA kernel); sign -1 = data gradient
+template <class EP>
+cudaError_t conv3x3(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h, int w, int n, int N,
+                    const bf16 *wdense, const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s) {
+  const int M = n * h * w;
+  if (!conv_tma_ok(cin, N, w))
+    return gemm(nbr(src, cs, co, h, w, cin, 9, sign, M), dense(wdense, 9 * cin, N), e, M, N, 9 * cin, 1, 9 * cin, st,
+                s);
+  CUtensorMap map;
+  const cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
+  const cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)w * cs * 2, (cuuint64_t)h * w * cs * 2};
+  const cuuint32_t box[4] = {8, (cuuint32_t)kHaloW, (cuuint32_t)kHaloH, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = tensor_map_encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(src + co), dims,
+                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  auto kern = k_conv_tma<EP>;
+  const int smem = (int)conv_smem_bytes(cin, N);
+  static std::mutex mu;
+  static bool attr_set[kMaxDev] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!attr_set[dev]) {
+      cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      if (err != cudaSuccess) return err;
+      attr_set[dev] = true;
+    }
+  }
+  int occ = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kConvThreads, smem);
+  if (err != cudaSuccess) return err;
+  const int cols = 2 * (int)conv_acc_cols(N);
+  if (occ * cols > 512) occ = 512 / cols;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const int ntiles = n * h * (w / 128);
+  const int grid = std::min(ntiles, u->num_sms * occ);
+  kern<<<grid, kConvThreads, smem, s>>>(map, wtma, cin, N, n, h, w, sign, e, st);
+  return cudaGetLastError();
+}
+
 int run_forward(sc_ctx *c, sc_unet *u, const float *x, int n) {
   const char *where = "sc_unet_forward";
   cudaStream_t s = sc::ctx_stream(c);
@@ -639,12 +756,11 @@ int run_forward(sc_ctx *c, sc_unet *u, const float *x, int n) {
     const Layer &c1 = u->L[enc_layer(l, 0)], &c2 = u->L[enc_layer(l, 1)];
     const bf16 *src = l == 0 ? u->x0 : u->pool[l];
     const int scs = l == 0 ? kInPad : kChans[l - 1];
-    UCHK(gemm(nbr(src, scs, 0, h, w, c1.cin_p, 9, 1, (int)P[l]), dense(c1.wf, 9 * c1.cin_p, cl),
-              bias_act(u->a1[l], cl, 0, prm + c1.b_off, cl, 1), (int)P[l], cl, 9 * c1.cin_p, 1, 9 * c1.cin_p, st,
-              s));
+    UCHK(conv3x3(u, src, scs, 0, c1.cin_p, h, w, n, cl, c1.wf, c1.wtf, 1,
+                 bias_act(u->a1[l], cl, 0, prm + c1.b_off, cl, 1), st, s));
     const View e = enc_out(u, l);
-    UCHK(gemm(nbr(u->a1[l], cl, 0, h, w, cl, 9, 1, (int)P[l]), dense(c2.wf, 9 * cl, cl),
-              bias_act(e.p, e.cs, e.co, prm + c2.b_off, cl, 1), (int)P[l], cl, 9 * cl, 1, 9 * cl, st, s));
+    UCHK(conv3x3(u, u->a1[l], cl, 0, cl, h, w, n, cl, c2.wf, c2.wtf, 1,
+                 bias_act(e.p, e.cs, e.co, prm + c2.b_off, cl, 1), st, s));
     if (l + 1 < kLevels) {
       const int64_t tot = P[l + 1] * (cl / 8);
       k_pool<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(e.p, e.cs, e.co, cl, n, h, w, u->pool[l + 1]);
@@ -665,10 +781,10 @@ int run_forward(sc_ctx *c, sc_unet *u, const float *x, int n) {
     eu.w = u->wl[l + 1];
     UCHK(gemm(nbr(ui.p, ui.cs, ui.co, u->hl[l + 1], u->wl[l + 1], cn, 1, 1, (int)P[l + 1]), dense(up.wf, cn, 4 * cl),
               eu, (int)P[l + 1], 4 * cl, cn, 1, cn, st, s));
-    UCHK(gemm(nbr(u->cat[l], 2 * cl, 0, h, w, 2 * cl, 9, 1, (int)P[l]), dense(c1.wf, 18 * cl, cl),
-              bias_act(u->d1[l], cl, 0, prm + c1.b_off, cl, 1), (int)P[l], cl, 18 * cl, 1, 18 * cl, st, s));
-    UCHK(gemm(nbr(u->d1[l], cl, 0, h, w, cl, 9, 1, (int)P[l]), dense(c2.wf, 9 * cl, cl),
-              bias_act(u->d2[l], cl, 0, prm + c2.b_off, cl, 1), (int)P[l], cl, 9 * cl, 1, 9 * cl, st, s));
+    UCHK(conv3x3(u, u->cat[l], 2 * cl, 0, 2 * cl, h, w, n, cl, c1.wf, c1.wtf, 1,
+                 bias_act(u->d1[l], cl, 0, prm + c1.b_off, cl, 1), st, s));
+    UCHK(conv3x3(u, u->d1[l], cl, 0, cl, h, w, n, cl, c2.wf, c2.wtf, 1,
+                 bias_act(u->d2[l], cl, 0, prm + c2.b_off, cl, 1), st, s));
   }
   const Layer &o = u->L[kOutLayer];
   EOut eo;
@@ -717,7 +833,8 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
   const int N = ly.kind == KIND_UP ? 4 * ly.cout : ly.cout;
   UCHK(gemm(A, B, ep, g.rows + 1, N, (int)K, splits, ks, sc::ctx_status(c), sc::ctx_stream(c)));
   const int64_t tot = (int64_t)(g.rows + 1) * g.np;
-  k_wgrad_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, sc::ctx_stream(c)>>>(
+  k_wgrad_reduce<<<(unsigned)((tot + kRedEntries - 1) / kRedEntries), kRedEntries * kRedGroups, 0,
+                   sc::ctx_stream(c)>>>(
       u->wpart, splits, Mpad, g.np, g.rows, ly.kind, ly.cout, ly.cin, ly.cin_p, u->grads + ly.w_off,
       u->grads + ly.b_off);
   UCHK(cudaGetLastError());
@@ -750,8 +867,8 @@ int run_backward(sc_ctx *c, sc_unet *u) {
     rc = wgrad(c, u, c2, tpix(u->d1[l], cl, 0, h, w, cl, 9, 0, 9 * cl, 1, kTM),
                tpix(u->gd2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
     if (rc) return rc;
-    UCHK(gemm(nbr(u->gd2[l], cl, 0, h, w, cl, 9, -1, (int)P[l]), dense(c2.wd, 9 * cl, cl),
-              egrad(u->gd1[l], cl, u->d1[l], cl, 0, cl), (int)P[l], cl, 9 * cl, 1, 9 * cl, st, s));
+    UCHK(conv3x3(u, u->gd2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, -1, egrad(u->gd1[l], cl, u->d1[l], cl, 0, cl),
+                 st, s));
     // dec conv 1: input cat = [up, skip], output gradient gd1 -> gup (BF16) | gskip (FP32)
     rc = wgrad(c, u, c1, tpix(u->cat[l], 2 * cl, 0, h, w, 2 * cl, 9, 0, 18 * cl, 1, kTM),
                tpix(u->gd1[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
@@ -760,8 +877,7 @@ int run_backward(sc_ctx *c, sc_unet *u) {
     es.split = cl;
     es.out2 = u->gskip[l];
     es.o2cs = cl;
-    UCHK(gemm(nbr(u->gd1[l], cl, 0, h, w, cl, 9, -1, (int)P[l]), dense(c1.wd, 9 * cl, 2 * cl), es, (int)P[l],
-              2 * cl, 9 * cl, 1, 9 * cl, st, s));
+    UCHK(conv3x3(u, u->gd1[l], cl, 0, cl, h, w, n, 2 * cl, c1.wd, c1.wtd, -1, es, st, s));
     // transposed conv: input up_in (level l+1), output gradient gup (level l)
     const View ui = up_in(u, l);
     const int hn = u->hl[l + 1], wn = u->wl[l + 1];
@@ -788,8 +904,8 @@ int run_backward(sc_ctx *c, sc_unet *u) {
     rc = wgrad(c, u, c2, tpix(u->a1[l], cl, 0, h, w, cl, 9, 0, 9 * cl, 1, kTM),
                tpix(u->ge2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
     if (rc) return rc;
-    UCHK(gemm(nbr(u->ge2[l], cl, 0, h, w, cl, 9, -1, (int)P[l]), dense(c2.wd, 9 * cl, cl),
-              egrad(u->ge1[l], cl, u->a1[l], cl, 0, cl), (int)P[l], cl, 9 * cl, 1, 9 * cl, st, s));
+    UCHK(conv3x3(u, u->ge2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, -1, egrad(u->ge1[l], cl, u->a1[l], cl, 0, cl),
+                 st, s));
     const bf16 *src = l == 0 ? u->x0 : u->pool[l];
     const int scs = l == 0 ? kInPad : kChans[l - 1];
     rc = wgrad(c, u, c1, tpix(src, scs, 0, h, w, c1.cin_p, 9, 0, 9 * c1.cin_p, 1, kTM),
@@ -810,8 +926,7 @@ int run_backward(sc_ctx *c, sc_unet *u) {
       pb.h = h;
       pb.w = w;
       pb.N = cp;
-      UCHK(gemm(nbr(u->ge1[l], cl, 0, h, w, cl, 9, -1, (int)P[l]), dense(c1.wd, 9 * cl, cp), pb, (int)P[l], cp,
-                9 * cl, 1, 9 * cl, st, s));
+      UCHK(conv3x3(u, u->ge1[l], cl, 0, cl, h, w, n, cp, c1.wd, c1.wtd, -1, pb, st, s));
     }
   }
   return SC_OK;
@@ -919,6 +1034,10 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
     for (int i = 0; i < kNumLayers; ++i) {
       u->L[i].wf = cv.take<bf16>(u->L[i].wf_elems);
       u->L[i].wd = u->L[i].wd_elems ? cv.take<bf16>(u->L[i].wd_elems) : nullptr;
+      if (u->L[i].kind == KIND_CONV) {
+        u->L[i].wtf = cv.take<bf16>(u->L[i].wf_elems);
+        u->L[i].wtd = u->L[i].wd_elems ? cv.take<bf16>(u->L[i].wd_elems) : nullptr;
+      }
     }
     u->x0 = cv.take<bf16>(P[0] * kInPad);
     for (int l = 0; l < kLevels; ++l) {
@@ -964,6 +1083,8 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
   for (size_t i = 0, j = 0; i < (size_t)kNumLayers; ++i, j += 2) {
     segs[j].wf = u->L[i].wf;
     segs[j].wd = u->L[i].wd;
+    segs[j].wtf = u->L[i].wtf;
+    segs[j].wtd = u->L[i].wtd;
   }
   u->nseg = (int)segs.size();
   u->adam_blocks = blocks;
@@ -1112,15 +1233,45 @@ int sc_ssim_l1_loss(sc_ctx *c, const float *pred, const float *target, int32_t n
   return rc;
 }
 
-int sc_unet_pack_frame(sc_ctx *c, const sc_frame *f, float *x, int32_t index) {
+static const float *frame_source(const sc_frame *f, int source) {
+  switch (source) {
+    case SC_UNET_SRC_RGB: return f->rgb;
+    case SC_UNET_SRC_DIRECT: return f->direct;
+    default: return nullptr;
+  }
+}
+
+int sc_unet_pack_frame(sc_ctx *c, const sc_frame *f, int32_t source, float *x, int32_t index) {
   if (!c || !f || !x || index < 0) return SC_ERR_INVALID_ARG;
-  if (!f->rgb || !f->albedo || !f->normal_camera || !f->depth_norm || !f->mask)
-    return fail(c, SC_ERR_INVALID_ARG, "sc_unet_pack_frame: rgb, albedo, normal_camera, depth_norm and mask needed");
+  if (!frame_source(f, source) || !f->albedo || !f->normal_camera || !f->depth_norm || !f->mask)
+    return fail(c, SC_ERR_INVALID_ARG,
+                "sc_unet_pack_frame: the source estimate, albedo, normal_camera, depth_norm and mask needed");
   const char *where = "sc_unet_pack_frame";
   const int64_t P = (int64_t)f->width * f->height;
   k_pack_frame<<<(unsigned)((P + 255) / 256), 256, 0, sc::ctx_stream(c)>>>(
-      reinterpret_cast<const float4 *>(f->rgb), reinterpret_cast<const float4 *>(f->albedo),
+      reinterpret_cast<const float4 *>(frame_source(f, source)), reinterpret_cast<const float4 *>(f->albedo),
       reinterpret_cast<const float4 *>(f->normal_camera), f->depth_norm, f->mask, x + index * P * kInCh, P);
+  UCHK(cudaGetLastError());
+  return SC_OK;
+}
+
+
+int sc_unet_pack_target(sc_ctx *c, const sc_frame *f, int32_t source, float *t, int32_t index) {
+  if (!c || !f || !t || index < 0 || !frame_source(f, source)) return SC_ERR_INVALID_ARG;
+  const char *where = "sc_unet_pack_target";
+  const int64_t P = (int64_t)f->width * f->height;
+  k_pack_target<<<(unsigned)((P + 255) / 256), 256, 0, sc::ctx_stream(c)>>>(
+      reinterpret_cast<const float4 *>(frame_source(f, source)), t + index * P * kOutCh, P);
+  UCHK(cudaGetLastError());
+  return SC_OK;
+}
+
+int sc_unet_output_rgb(sc_ctx *c, const float *y, int64_t n_px, const float *add, float *rgb) {
+  if (!c || !y || !rgb || n_px < 0) return SC_ERR_INVALID_ARG;
+  if (n_px == 0) return SC_OK;
+  const char *where = "sc_unet_output_rgb";
+  k_output_rgb<<<(unsigned)((n_px + 255) / 256), 256, 0, sc::ctx_stream(c)>>>(
+      y, n_px, reinterpret_cast<const float4 *>(add), reinterpret_cast<float4 *>(rgb));
   UCHK(cudaGetLastError());
   return SC_OK;
 }

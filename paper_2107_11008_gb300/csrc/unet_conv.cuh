@@ -1,0 +1,164 @@
+// unet_conv.cuh -- persistent, warp-specialised 3x3 convolution (forward or data gradient) on
+// tcgen05 with TMA halo tiles, for rows whose width is a multiple of 128 pixels.
+//
+// A tile is 128 consecutive output pixels of one image row.  For each group of 8 input channels
+// the producer warp loads, with one TMA tensor copy, the 3 x 130 pixel neighbourhood of the tile
+// (rows y-1..y+1, columns x0-1..x0+128; outside the image the hardware fills zeros) into a
+// "slab": pixel-major rows of 16 bytes.  In that slab, the 128 input pixels that tap (dy, dx)
+// multiplies are consecutive 16-byte rows, so the MMA operand of every tap is the same slab
+// seen from a shifted start address (8-row core matrices 128 bytes apart, k-groups one slab
+// apart): nine taps, one load.  The weights of the whole layer stay resident in shared memory
+// (one bulk copy per CTA, laid out in global memory exactly as the MMA reads them).
+//
+// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = MMA issuer (one thread each), warps
+// 2..5 = epilogue (TMEM -> registers -> epilogue functor).  Two shared-memory A stages and two
+// TMEM accumulators let the loads of tile i+1 and the epilogue of tile i-1 overlap the MMAs of
+// tile i.  Every wait is bounded; a timeout latches SC_STATUS_WATCHDOG and the CTA winds down.
+#pragma once
+#include "unet_gemm.cuh"
+
+namespace sc {
+namespace unet {
+
+constexpr int kHaloW = 130, kHaloH = 3;
+constexpr uint32_t kSlabBytes = 6272;  // 8 channels x 3 x 130 pixels x 2 bytes = 6240, rounded up to 128
+constexpr uint32_t kSlabTx = 6240;
+constexpr int kConvThreads = 192;
+
+__host__ __device__ constexpr uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+__host__ __device__ constexpr uint32_t conv_w_bytes(int cin_p, int N) { return 9u * (uint32_t)cin_p * N * 2u; }
+__host__ __device__ constexpr uint32_t conv_a_bytes(int cin_p) { return (uint32_t)(cin_p / 8) * kSlabBytes; }
+__host__ __device__ constexpr uint32_t conv_acc_cols(int N) { return N <= 32 ? 32u : (N <= 64 ? 64u : 128u); }
+__host__ __device__ constexpr size_t conv_smem_bytes(int cin_p, int N) {
+  return align_up(conv_w_bytes(cin_p, N), 1024) + 2 * align_up(conv_a_bytes(cin_p), 1024) + 128;
+}
+
+// Resident weights: wt[tap][kg][n][8] BF16 (kg = group of 8 reduction channels), i.e. for each
+// (tap, kg) the N rows of 16 bytes the B operand needs.  amap: 4-D tensor map of the input
+// (channels of the slice, width, height, images), box (8, 130, 3, 1).
+template <class EP>
+__global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_constant__ CUtensorMap amap,
+                                                              const bf16 *__restrict__ wt, int cin_p, int N,
+                                                              int n_img, int h, int w, int sign, EP E,
+                                                              unsigned *status) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ng = cin_p / 8;
+  const uint32_t wbytes = conv_w_bytes(cin_p, N);
+  const uint32_t astride = align_up(conv_a_bytes(cin_p), 1024);
+  uint8_t *sW = sm;
+  uint8_t *sA = sm + align_up(wbytes, 1024);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sA + 2 * astride);
+  // bar[0] weights full, [1,2] A full, [3,4] A empty, [5,6] accumulator full, [7,8] accumulator empty
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 9);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(slot + 1);
+  const int tiles_x = w / 128;
+  const int ntiles = n_img * h * tiles_x;
+  const uint32_t half = conv_acc_cols(N);  // column offset of accumulator 1
+  const uint32_t cols = 2 * half;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_addr(&bar[0]), 1);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(tc::smem_addr(&bar[1 + i]), 1);
+      tc::mbar_init(tc::smem_addr(&bar[3 + i]), 1);
+      tc::mbar_init(tc::smem_addr(&bar[5 + i]), 1);
+      tc::mbar_init(tc::smem_addr(&bar[7 + i]), 4);
+    }
+    *abort_flag = 0;
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tc::smem_addr(slot), cols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = *slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer ------------------------------------------------------------------------
+      tc::mbar_expect_tx(tc::smem_addr(&bar[0]), wbytes);
+      tc::bulk_load(tc::smem_addr(sW), wt, wbytes, tc::smem_addr(&bar[0]));
+      int issued = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++issued) {
+        const int s = issued & 1, u = issued >> 1;
+        if (u > 0 && !tc::mbar_wait(tc::smem_addr(&bar[3 + s]), (u - 1) & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        if (*abort_flag) break;
+        const int xt = t % tiles_x, r = t / tiles_x, y = r % h, img = r / h;
+        const uint32_t full = tc::smem_addr(&bar[1 + s]);
+        tc::mbar_expect_tx(full, (uint32_t)ng * kSlabTx);
+        const uint32_t dst = tc::smem_addr(sA + s * astride);
+        for (int g = 0; g < ng; ++g)
+          tc::tma_load_4d(dst + g * kSlabBytes, &amap, 8 * g, xt * 128 - 1, y - 1, img, full);
+      }
+      // wait (bounded) for the copies still in flight before leaving
+      for (int k = issued - 2; k < issued; ++k)
+        if (k >= 0) tc::mbar_wait(tc::smem_addr(&bar[1 + (k & 1)]), (k >> 1) & 1);
+      tc::mbar_wait(tc::smem_addr(&bar[0]), 0);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer -----------------------------------------------------------------------
+      const uint32_t idesc = tc::idesc_bf16_f32(kTM, N);
+      bool ok = tc::mbar_wait(tc::smem_addr(&bar[0]), 0);
+      int i = 0;
+      for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
+        const int s = i & 1, u = i >> 1;
+        if (!tc::mbar_wait(tc::smem_addr(&bar[1 + s]), u & 1)) ok = false;
+        if (ok && u > 0 && !tc::mbar_wait(tc::smem_addr(&bar[7 + s]), (u - 1) & 1)) ok = false;
+        if (!ok || *abort_flag) break;
+        tc::fence_after();
+        const uint32_t d = taddr + (uint32_t)s * half;
+        const uint32_t a0 = tc::smem_addr(sA + s * astride), w0 = tc::smem_addr(sW);
+        for (int tap = 0; tap < 9; ++tap) {
+          const int ty = tap / 3, tx = tap - 3 * ty;
+          const int off = (sign * (ty - 1) + 1) * kHaloW + sign * (tx - 1) + 1;  // slab pixel of output 0
+          for (int ks = 0; ks < ng / 2; ++ks) {
+            const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(2 * ks) * kSlabBytes + (uint32_t)off * 16u, kSlabBytes,
+                                              128u);
+            const uint64_t bd = tc::smem_desc(w0 + (uint32_t)((tap * ng + 2 * ks) * N * 16), (uint32_t)N * 16u, 128u);
+            tc::mma_bf16(d, ad, bd, idesc, (tap > 0 || ks > 0) ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(tc::smem_addr(&bar[3 + s]));  // A stage free
+        tc::mma_commit(tc::smem_addr(&bar[5 + s]));  // accumulator full
+      }
+      if (!ok) *abort_flag = 1;
+    }
+  } else {
+    // ---- epilogue (warps 2..5; warp w reads TMEM lanes 32 * (w % 4) ..) -------------------------
+    const int q = warp & 3;
+    const int r = 32 * q + lane;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int s = i & 1, u = i >> 1;
+      if (!tc::mbar_wait(tc::smem_addr(&bar[5 + s]), u & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc::fence_after();
+      const int xt = t % tiles_x, rr = t / tiles_x;
+      const int row = rr * w + xt * 128 + r;  // rr = img * h + y
+      for (int n0 = 0; n0 < N; n0 += 16) {
+        float v[16];
+        tc::tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)s * half + (uint32_t)n0, v);
+        E.store(row, n0, v, 0);
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(tc::smem_addr(&bar[7 + s]));
+      if (*abort_flag) break;
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(taddr, cols);
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(status, SC_STATUS_WATCHDOG);
+}
+
+}  // namespace unet
+}  // namespace sc

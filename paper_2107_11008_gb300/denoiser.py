@@ -157,7 +157,26 @@ def ssim_l1_loss(ctx: Context, pred: torch.Tensor, target: torch.Tensor, want_gr
     return loss, grad
 
 
-def pack_frame(ctx: Context, frame: Frame, x: torch.Tensor, index: int = 0):
-    """Writes the 11-channel network input of ``frame`` into image ``index`` of x [n, H, W, 11]."""
-    N.sc_unet_pack_frame(ctx.handle, frame.struct(), _ptr(x), index)
+SOURCES = {"rgb": N.SC_UNET_SRC_RGB, "direct": N.SC_UNET_SRC_DIRECT}
+
+
+def pack_frame(ctx: Context, frame: Frame, x: torch.Tensor, index: int = 0, source: str = "rgb"):
+    """Writes the 11-channel network input of ``frame`` into image ``index`` of x [n, H, W, 11];
+    ``source`` picks the radiance estimate: the full image or the camera estimator alone."""
+    N.sc_unet_pack_frame(ctx.handle, frame.struct(), SOURCES[source], _ptr(x), index)
     return x
+
+
+def pack_target(ctx: Context, frame: Frame, t: torch.Tensor, index: int = 0, source: str = "rgb"):
+    """Writes log1p of the frame's selected estimate into image ``index`` of t [n, H, W, 3]."""
+    N.sc_unet_pack_target(ctx.handle, frame.struct(), SOURCES[source], _ptr(t), index)
+    return t
+
+
+def output_rgb(ctx: Context, y: torch.Tensor, add: torch.Tensor | None = None,
+               out: torch.Tensor | None = None) -> torch.Tensor:
+    """Linear RGB (float4 per pixel, w = 1) of network outputs y [..., 3], plus ``add`` (float4
+    per pixel, e.g. the light-traced caustic buffer) when given."""
+    rgb = out if out is not None else torch.empty(y.shape[:-1] + (4,), dtype=torch.float32, device=y.device)
+    N.sc_unet_output_rgb(ctx.handle, _ptr(y), y.numel() // 3, _ptr(add), _ptr(rgb))
+    return rgb

@@ -142,7 +142,9 @@ SIGNATURES = {
                                      C.c_void_p]),
     "sc_ssim_l1_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
                                   C.c_void_p]),
-    "sc_unet_pack_frame": (C.c_int, [C.c_void_p, P(sc_frame), C.c_void_p, C.c_int32]),
+    "sc_unet_pack_frame": (C.c_int, [C.c_void_p, P(sc_frame), C.c_int32, C.c_void_p, C.c_int32]),
+    "sc_unet_pack_target": (C.c_int, [C.c_void_p, P(sc_frame), C.c_int32, C.c_void_p, C.c_int32]),
+    "sc_unet_output_rgb": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "sc_unet_buffer": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, P(sc_unet_buffer_info)]),
     "sc_unet_copy_buffer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
 }
@@ -348,8 +350,11 @@ def sc_ssim_l1_loss(ctx, pred_dev, target_dev, n, h, w, loss_dev=None, grad_dev=
     return check(load().sc_ssim_l1_loss(ctx, pred_dev, target_dev, n, h, w, loss_dev, grad_dev), ctx)
 
 
-def sc_unet_pack_frame(ctx, frame: sc_frame, x_dev, index):
-    return check(load().sc_unet_pack_frame(ctx, C.byref(frame), x_dev, index), ctx)
+SC_UNET_SRC_RGB, SC_UNET_SRC_DIRECT = 0, 1
+
+
+def sc_unet_pack_frame(ctx, frame: sc_frame, source, x_dev, index):
+    return check(load().sc_unet_pack_frame(ctx, C.byref(frame), source, x_dev, index), ctx)
 
 
 def sc_unet_buffer(net, buf_id, level) -> sc_unet_buffer_info:
@@ -360,3 +365,11 @@ def sc_unet_buffer(net, buf_id, level) -> sc_unet_buffer_info:
 
 def sc_unet_copy_buffer(ctx, net, buf_id, level, dst_dev):
     return check(load().sc_unet_copy_buffer(ctx, net, buf_id, level, dst_dev), ctx)
+
+
+def sc_unet_pack_target(ctx, frame: sc_frame, source, t_dev, index):
+    return check(load().sc_unet_pack_target(ctx, C.byref(frame), source, t_dev, index), ctx)
+
+
+def sc_unet_output_rgb(ctx, y_dev, n_px, add_dev, rgb_dev):
+    return check(load().sc_unet_output_rgb(ctx, y_dev, n_px, add_dev, rgb_dev), ctx)

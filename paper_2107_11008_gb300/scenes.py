@@ -473,6 +473,35 @@ def ball_on_plane(width=64, height=64, subdiv=3, ior=1.5, light_pos=(2.0, 4.0, 2
     return b.build(cam, name=f"ball_on_plane_{width}x{height}")
 
 
+def denoise_scene(seed: int, width=64, height=64) -> Scene:
+    """A ball-on-plane scene with randomised parameters, for denoiser training pairs: glass
+    icosphere (1280 tris) of radius 0.6-1.2 resting on the plane y = -1 near the origin, IOR
+    uniform in [1.33, 1.9], plane albedo 0.3-0.8 (checkered half the time), point light at a
+    random position 3-5 m up, camera jittered around (0, 1, 4)."""
+    rng = np.random.default_rng(20_000 + seed)
+    b = SceneBuilder()
+    ior = float(rng.uniform(1.33, 1.9))
+    glass = b.material(Material(MAT_DIELECTRIC, cauchy_a=ior, cauchy_b=0.0))
+    a = float(rng.uniform(0.3, 0.8))
+    if rng.random() < 0.5:
+        a2 = float(rng.uniform(0.1, 0.9))
+        floor = b.material(Material(MAT_DIFFUSE, albedo=(a, a, a), albedo2=(a2, a2, a2),
+                                    checker_scale=float(rng.uniform(1.0, 4.0))))
+    else:
+        floor = b.material(Material(MAT_DIFFUSE, albedo=(a, a, a)))
+    r = float(rng.uniform(0.6, 1.2))
+    centre = (float(rng.uniform(-0.6, 0.6)), r - 1.0, float(rng.uniform(-0.6, 0.6)))
+    b.add(icosphere(3).transformed(np.eye(3), r, centre), glass)
+    b.add(quad((-10, -1, -10), (0, 0, 20), (20, 0, 0)), floor)
+    lp = (float(rng.uniform(-3, 3)), float(rng.uniform(3, 5)), float(rng.uniform(-3, 3)))
+    power = 20.0 * (lp[0] ** 2 + (lp[1] + 1) ** 2 + lp[2] ** 2) / 29.0  # about the same irradiance at the origin
+    b.lights.append(Light(LIGHT_POINT, lp, power=(power,) * 3))
+    eye = (float(rng.normal(0, 0.3)), 1.0 + float(rng.normal(0, 0.2)), 4.0 + float(rng.normal(0, 0.3)))
+    look = (float(rng.normal(0, 0.15)), float(rng.normal(-0.2, 0.1)), 0.0)
+    cam = Camera(eye, look, (0.0, 1.0, 0.0), 40.0, width, height)
+    return b.build(cam, name=f"denoise_scene_s{seed}_{width}x{height}")
+
+
 def glass_scene(seed=0, width=512, height=512, n_objects=4, tris_per_object=20480, families=FAMILIES,
                 cauchy=(1.5, 0.004), light_size=1.0, light_radiance=20.0) -> Scene:
     """Several transparent meshes (sphere, hollow cylinder glass, torus, superellipsoid) with random pose

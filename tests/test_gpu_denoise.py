@@ -1,0 +1,61 @@
+"""What the learned part gains: the U-Net trained on the tracer's own low/high-sample pairs,
+evaluated on held-out scenes against the plain low-sample render (both vs a high-sample target)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2107_11008_gb300 import denoiser as D  # noqa: E402
+from paper_2107_11008_gb300 import renderer as R  # noqa: E402
+from paper_2107_11008_gb300 import scenes as S  # noqa: E402
+from paper_2107_11008_gb300 import training as T  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = R.Context(0)
+    yield c
+    c.close()
+
+
+def test_pairs_use_disjoint_samples_and_same_estimator(ctx):
+    sc = [S.denoise_scene(7, 32, 32)]
+    lo, hi = T.RenderSpec(16, 16), T.RenderSpec(16, 16)
+    p = T.make_pairs(ctx, sc, lo, hi, seed=3)
+    # equal budgets, disjoint samples: different noise, same expectation
+    a, b = p.rgb_lo[..., :3], p.rgb_hi[..., :3]
+    assert not torch.equal(a, b)
+    assert abs(float(a.mean()) - float(b.mean())) < 0.25 * float(b.mean())
+    np.testing.assert_allclose(p.target.cpu().numpy(), np.log1p(np.maximum(b.cpu().numpy(), 0)), rtol=1e-6)
+    np.testing.assert_allclose(p.x[..., :3].cpu().numpy(), np.log1p(np.maximum(a.cpu().numpy(), 0)), rtol=1e-6)
+
+
+@pytest.mark.parametrize("source,lights", [("rgb", 4), ("direct", 1024)])
+def test_trained_denoiser_beats_the_noisy_input(ctx, source, lights):
+    """rgb: the network denoises the whole 4-spp image (4 light paths / px); direct: it denoises
+    the 4-spp camera estimate and the caustic buffer of 1024 light paths / px is added back."""
+    lo, hi = T.RenderSpec(spp=4, lights_per_pixel=lights), T.RenderSpec(spp=512, lights_per_pixel=4096)
+    train = T.make_pairs(ctx, [S.denoise_scene(i, 64, 64) for i in range(48)], lo, hi, seed=1, source=source)
+    test = T.make_pairs(ctx, [S.denoise_scene(1000 + i, 64, 64) for i in range(8)], lo, hi, seed=2, source=source)
+    net = D.UNet(ctx, 8, 64, 64)
+    net.set_params(D.he_init(0).cuda())
+    log = T.train(net, train, steps=800, batch=8, lr=2e-3, lr_final=1e-4, log_every=100)
+    ctx.sync_status()
+    assert log[-1][1] < log[0][1]
+    den = T.denoise(net, test.x, test.add())
+    m_noisy = T.mse(test.rgb_lo, test.rgb_hi)
+    m_den = T.mse(den, test.rgb_hi)
+    # log-space error, which the network is trained in
+    lt = torch.log1p(test.rgb_hi[..., :3].clamp_min(0))
+    l_noisy = float(((torch.log1p(test.rgb_lo[..., :3].clamp_min(0)) - lt) ** 2).mean())
+    l_den = float(((torch.log1p(den[..., :3]) - lt) ** 2).mean())
+    print(f"[{source}, {lights} light paths/px] held-out MSE: noisy {m_noisy:.4g}, denoised {m_den:.4g} "
+          f"(log space {l_noisy:.4g} -> {l_den:.4g}); losses {log}")
+    assert m_den < (0.75 if source == "rgb" else 0.5) * m_noisy
+    assert l_den < 0.5 * l_noisy
+    net.close()
+

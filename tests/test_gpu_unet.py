@@ -102,8 +102,14 @@ def test_param_layout_and_bf16_refresh(ctx):
     net.close()
 
 
-def test_forward_layer_by_layer(ctx):
-    N = Net(ctx, 2, 32, 40, seed=11)
+# (n, h, w): w = 40 runs every convolution through the gathering GEMM; w = 256 runs levels 0 and 1
+# (rows of 256 and 128 pixels) through the TMA halo-tile kernel
+GEOMS = [(2, 32, 40), (1, 16, 256)]
+
+
+@pytest.mark.parametrize("geom", GEOMS, ids=["gather", "tma"])
+def test_forward_layer_by_layer(ctx, geom):
+    N = Net(ctx, *geom, seed=11)
     y = N.net.forward(N.xd)
     torch.cuda.synchronize()
     ctx.sync_status()
@@ -168,8 +174,9 @@ def test_ssim_l1_loss_kernel(ctx):
     assert abs(float(loss0.item())) < 1e-5
 
 
-def test_backward_layer_by_layer(ctx):
-    N = Net(ctx, 2, 32, 40, seed=31)
+@pytest.mark.parametrize("geom", GEOMS, ids=["gather", "tma"])
+def test_backward_layer_by_layer(ctx, geom):
+    N = Net(ctx, *geom, seed=31)
     y, loss = N.net.loss_grad(N.xd, N.td)
     torch.cuda.synchronize()
     ctx.sync_status()
@@ -344,9 +351,19 @@ def test_pack_frame_from_render(ctx):
     f = R.Frame(24, 16)
     R.trace_camera(ctx, gs, f, 2, 8)
     R.resolve(ctx, gs, f, 2.0, 1.0)
-    x = torch.zeros((1, 16, 24, 11), device="cuda")
+    x = torch.zeros((2, 16, 24, 11), device="cuda")
     D.pack_frame(ctx, f, x, 0)
+    D.pack_frame(ctx, f, x, 1, source="direct")
+    t = torch.zeros((1, 16, 24, 3), device="cuda")
+    D.pack_target(ctx, f, t, 0, source="direct")
+    y = torch.log1p(torch.rand((16, 24, 3), device="cuda"))
+    out = D.output_rgb(ctx, y, f["caustic"])
     torch.cuda.synchronize()
+    np.testing.assert_allclose(x[1, ..., 0:3].cpu().numpy(), np.log1p(np.maximum(f["direct"].cpu().numpy()[..., :3], 0)),
+                               rtol=1e-6)
+    np.testing.assert_allclose(t[0].cpu().numpy(), x[1, ..., 0:3].cpu().numpy(), rtol=1e-6)
+    np.testing.assert_allclose(out[..., :3].cpu().numpy(),
+                               np.expm1(y.cpu().numpy()) + f["caustic"].cpu().numpy()[..., :3], rtol=1e-5, atol=1e-6)
     xv = x[0].cpu().numpy()
     np.testing.assert_allclose(xv[..., 0:3], np.log1p(np.maximum(f["rgb"].cpu().numpy()[..., :3], 0)), rtol=1e-6)
     np.testing.assert_array_equal(xv[..., 3:6], f["albedo"].cpu().numpy()[..., :3])
