@@ -691,8 +691,17 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+// groups of 8 input channels per A stage: the largest even divisor of cin / 8 for which the
+// resident weights and two stages fit in 227 KB (0: the layer does not fit)
+int conv_stage_groups(int cin, int N) {
+  const int ng = cin / 8;
+  for (int gs = ng; gs >= 2; gs -= 2)
+    if (ng % gs == 0 && conv_smem_bytes(cin, N, gs) <= 227 * 1024) return gs;
+  return 0;
+}
+
 bool conv_tma_ok(int cin, int N, int w) {
-  return w % 128 == 0 && cin % 16 == 0 && N % 16 == 0 && N <= 128 && conv_smem_bytes(cin, N) <= 227 * 1024 &&
+  return w % 128 == 0 && cin % 16 == 0 && N % 16 == 0 && N <= 128 && conv_stage_groups(cin, N) > 0 &&
          tensor_map_encoder() != nullptr;
 }
 
@@ -715,7 +724,8 @@ cudaError_t conv3x3(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h,
                                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   auto kern = k_conv_tma<EP>;
-  const int smem = (int)conv_smem_bytes(cin, N);
+  const int gs = conv_stage_groups(cin, N);
+  const int smem = (int)conv_smem_bytes(cin, N, gs);
   static std::mutex mu;
   static bool attr_set[kMaxDev] = {};
   int dev = 0;
@@ -737,7 +747,7 @@ cudaError_t conv3x3(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h,
   if (occ < 1) return cudaErrorInvalidConfiguration;
   const int ntiles = n * h * (w / 128);
   const int grid = std::min(ntiles, u->num_sms * occ);
-  kern<<<grid, kConvThreads, smem, s>>>(map, wtma, cin, N, n, h, w, sign, e, st);
+  kern<<<grid, kConvThreads, smem, s>>>(map, wtma, cin, N, gs, n, h, w, sign, e, st);
   return cudaGetLastError();
 }
 

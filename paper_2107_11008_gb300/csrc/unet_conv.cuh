@@ -8,7 +8,9 @@
 // multiplies are consecutive 16-byte rows, so the MMA operand of every tap is the same slab
 // seen from a shifted start address (8-row core matrices 128 bytes apart, k-groups one slab
 // apart): nine taps, one load.  The weights of the whole layer stay resident in shared memory
-// (one bulk copy per CTA, laid out in global memory exactly as the MMA reads them).
+// (one bulk copy per CTA, laid out in global memory exactly as the MMA reads them).  When the
+// input has more channels than two A stages can hold next to the weights, a tile's channels are
+// streamed in chunks of `gs` groups of 8, accumulating into the same TMEM columns.
 //
 // Warp roles (192 threads): warp 0 = TMA producer, warp 1 = MMA issuer (one thread each), warps
 // 2..5 = epilogue (TMEM -> registers -> epilogue functor).  Two shared-memory A stages and two
@@ -27,10 +29,11 @@ constexpr int kConvThreads = 192;
 
 __host__ __device__ constexpr uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 __host__ __device__ constexpr uint32_t conv_w_bytes(int cin_p, int N) { return 9u * (uint32_t)cin_p * N * 2u; }
-__host__ __device__ constexpr uint32_t conv_a_bytes(int cin_p) { return (uint32_t)(cin_p / 8) * kSlabBytes; }
+__host__ __device__ constexpr uint32_t conv_a_bytes(int gs) { return (uint32_t)gs * kSlabBytes; }
 __host__ __device__ constexpr uint32_t conv_acc_cols(int N) { return N <= 32 ? 32u : (N <= 64 ? 64u : 128u); }
-__host__ __device__ constexpr size_t conv_smem_bytes(int cin_p, int N) {
-  return align_up(conv_w_bytes(cin_p, N), 1024) + 2 * align_up(conv_a_bytes(cin_p), 1024) + 128;
+// gs: groups of 8 input channels per A stage
+__host__ __device__ constexpr size_t conv_smem_bytes(int cin_p, int N, int gs) {
+  return align_up(conv_w_bytes(cin_p, N), 1024) + 2 * align_up(conv_a_bytes(gs), 1024) + 128;
 }
 
 // Resident weights: wt[tap][kg][n][8] BF16 (kg = group of 8 reduction channels), i.e. for each
@@ -38,14 +41,15 @@ __host__ __device__ constexpr size_t conv_smem_bytes(int cin_p, int N) {
 // (channels of the slice, width, height, images), box (8, 130, 3, 1).
 template <class EP>
 __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_constant__ CUtensorMap amap,
-                                                              const bf16 *__restrict__ wt, int cin_p, int N,
+                                                              const bf16 *__restrict__ wt, int cin_p, int N, int gs,
                                                               int n_img, int h, int w, int sign, EP E,
                                                               unsigned *status) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ng = cin_p / 8;
+  const int nchunk = ng / gs;
   const uint32_t wbytes = conv_w_bytes(cin_p, N);
-  const uint32_t astride = align_up(conv_a_bytes(cin_p), 1024);
+  const uint32_t astride = align_up(conv_a_bytes(gs), 1024);
   uint8_t *sW = sm;
   uint8_t *sA = sm + align_up(wbytes, 1024);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sA + 2 * astride);
@@ -81,19 +85,21 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
       tc::mbar_expect_tx(tc::smem_addr(&bar[0]), wbytes);
       tc::bulk_load(tc::smem_addr(sW), wt, wbytes, tc::smem_addr(&bar[0]));
       int issued = 0;
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++issued) {
-        const int s = issued & 1, u = issued >> 1;
-        if (u > 0 && !tc::mbar_wait(tc::smem_addr(&bar[3 + s]), (u - 1) & 1)) {
-          *abort_flag = 1;
-          break;
-        }
-        if (*abort_flag) break;
+      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
         const int xt = t % tiles_x, r = t / tiles_x, y = r % h, img = r / h;
-        const uint32_t full = tc::smem_addr(&bar[1 + s]);
-        tc::mbar_expect_tx(full, (uint32_t)ng * kSlabTx);
-        const uint32_t dst = tc::smem_addr(sA + s * astride);
-        for (int g = 0; g < ng; ++g)
-          tc::tma_load_4d(dst + g * kSlabBytes, &amap, 8 * g, xt * 128 - 1, y - 1, img, full);
+        for (int ch = 0; ch < nchunk; ++ch, ++issued) {
+          const int s = issued & 1, u = issued >> 1;
+          if (u > 0 && !tc::mbar_wait(tc::smem_addr(&bar[3 + s]), (u - 1) & 1)) {
+            *abort_flag = 1;
+            break;
+          }
+          if (*abort_flag) break;
+          const uint32_t full = tc::smem_addr(&bar[1 + s]);
+          tc::mbar_expect_tx(full, (uint32_t)gs * kSlabTx);
+          const uint32_t dst = tc::smem_addr(sA + s * astride);
+          for (int g = 0; g < gs; ++g)
+            tc::tma_load_4d(dst + g * kSlabBytes, &amap, 8 * (ch * gs + g), xt * 128 - 1, y - 1, img, full);
+        }
       }
       // wait (bounded) for the copies still in flight before leaving
       for (int k = issued - 2; k < issued; ++k)
@@ -105,27 +111,35 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
       // ---- MMA issuer -----------------------------------------------------------------------
       const uint32_t idesc = tc::idesc_bf16_f32(kTM, N);
       bool ok = tc::mbar_wait(tc::smem_addr(&bar[0]), 0);
-      int i = 0;
+      int i = 0, staged = 0;
+      const uint32_t w0 = tc::smem_addr(sW);
       for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
-        const int s = i & 1, u = i >> 1;
-        if (!tc::mbar_wait(tc::smem_addr(&bar[1 + s]), u & 1)) ok = false;
-        if (ok && u > 0 && !tc::mbar_wait(tc::smem_addr(&bar[7 + s]), (u - 1) & 1)) ok = false;
-        if (!ok || *abort_flag) break;
-        tc::fence_after();
-        const uint32_t d = taddr + (uint32_t)s * half;
-        const uint32_t a0 = tc::smem_addr(sA + s * astride), w0 = tc::smem_addr(sW);
-        for (int tap = 0; tap < 9; ++tap) {
-          const int ty = tap / 3, tx = tap - 3 * ty;
-          const int off = (sign * (ty - 1) + 1) * kHaloW + sign * (tx - 1) + 1;  // slab pixel of output 0
-          for (int ks = 0; ks < ng / 2; ++ks) {
-            const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(2 * ks) * kSlabBytes + (uint32_t)off * 16u, kSlabBytes,
-                                              128u);
-            const uint64_t bd = tc::smem_desc(w0 + (uint32_t)((tap * ng + 2 * ks) * N * 16), (uint32_t)N * 16u, 128u);
-            tc::mma_bf16(d, ad, bd, idesc, (tap > 0 || ks > 0) ? 1u : 0u);
+        const int a = i & 1, ua = i >> 1;  // accumulator and its use count
+        if (ua > 0 && !tc::mbar_wait(tc::smem_addr(&bar[7 + a]), (ua - 1) & 1)) ok = false;
+        const uint32_t d = taddr + (uint32_t)a * half;
+        for (int ch = 0; ok && ch < nchunk; ++ch, ++staged) {
+          const int s = staged & 1, u = staged >> 1;
+          if (!tc::mbar_wait(tc::smem_addr(&bar[1 + s]), u & 1)) ok = false;
+          if (!ok || *abort_flag) {
+            ok = false;
+            break;
           }
+          tc::fence_after();
+          const uint32_t a0 = tc::smem_addr(sA + s * astride);
+          for (int tap = 0; tap < 9; ++tap) {
+            const int ty = tap / 3, tx = tap - 3 * ty;
+            const int off = (sign * (ty - 1) + 1) * kHaloW + sign * (tx - 1) + 1;  // slab pixel of output 0
+            for (int ks = 0; ks < gs / 2; ++ks) {
+              const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(2 * ks) * kSlabBytes + (uint32_t)off * 16u,
+                                                kSlabBytes, 128u);
+              const uint64_t bd = tc::smem_desc(w0 + (uint32_t)((tap * ng + ch * gs + 2 * ks) * N * 16),
+                                                (uint32_t)N * 16u, 128u);
+              tc::mma_bf16(d, ad, bd, idesc, (ch > 0 || tap > 0 || ks > 0) ? 1u : 0u);
+            }
+          }
+          tc::mma_commit(tc::smem_addr(&bar[3 + s]));  // A stage free
         }
-        tc::mma_commit(tc::smem_addr(&bar[3 + s]));  // A stage free
-        tc::mma_commit(tc::smem_addr(&bar[5 + s]));  // accumulator full
+        if (ok) tc::mma_commit(tc::smem_addr(&bar[5 + a]));  // accumulator full
       }
       if (!ok) *abort_flag = 1;
     }
