@@ -119,6 +119,20 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
                : "memory");
 }
 
+// four 8x8 BF16 matrices from shared memory, transposed: lane L supplies the address of row L % 8
+// of matrix L / 8 (16 bytes); register i of lane L receives elements (2 (L % 4), 2 (L % 4) + 1) of
+// row L / 4 of the transpose of matrix i
+// (no memory clobber: the caller orders it against writes of the source with its own barriers,
+// which lets several of these be in flight at once)
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void st_shared_b32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
 // make generic-proxy shared-memory writes visible to the tensor cores (async proxy)
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 

@@ -15,6 +15,7 @@
 #include "sc_unet.h"
 #include "unet_conv.cuh"
 #include "unet_gemm.cuh"
+#include "unet_wgrad.cuh"
 
 namespace sc {
 int ctx_device(const sc_ctx *c);
@@ -826,22 +827,73 @@ int run_loss(sc_ctx *c, sc_unet *u, const float *pred, const float *target, int 
   return SC_OK;
 }
 
+// raw stages of the TMA weight-gradient kernel that fit (0: it does not fit)
+int wgrad_tma_stages(int cin, int cout, int mtiles) {
+  if ((uint32_t)mtiles * wg_cstride(cout) > 512u) return 0;
+  if (wg_smem_bytes(cin, cout, 2) <= 227 * 1024) return 2;
+  if (wg_smem_bytes(cin, cout, 1) <= 227 * 1024) return 1;
+  return 0;
+}
+
+bool encode_map(CUtensorMap *map, const bf16 *base, int channels, int cs, int w, int h, int n, int box_w, int box_h) {
+  const cuuint64_t dims[4] = {(cuuint64_t)channels, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
+  const cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)w * cs * 2, (cuuint64_t)h * w * cs * 2};
+  const cuuint32_t box[4] = {8, (cuuint32_t)box_w, (cuuint32_t)box_h, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return tensor_map_encoder()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(base), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // weight gradient of one layer: A (rows = (tap, c) | c, + ones row), B (rows = output channels),
-// contracted over the pixels, reduced deterministically into the flat gradient
+// contracted over the pixels, reduced deterministically into the flat gradient.  3x3 layers on
+// rows of 128k pixels take the TMA kernel (x: the layer input, gz: its output gradient).
 int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, int64_t K) {
   const char *where = "sc_unet wgrad";
   const Wgrad g = wgrad_shape(ly);
-  int splits, ks;
-  split_k(g.Mtiles, K, u->num_sms, &splits, &ks);
   const int Mpad = g.Mtiles * kTM;
-  if ((size_t)splits * Mpad * g.np > u->wpart_floats)
-    return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
-  EPartial ep;
-  ep.part = u->wpart;
-  ep.ld = g.np;
-  ep.Mpad = Mpad;
-  const int N = ly.kind == KIND_UP ? 4 * ly.cout : ly.cout;
-  UCHK(gemm(A, B, ep, g.rows + 1, N, (int)K, splits, ks, sc::ctx_status(c), sc::ctx_stream(c)));
+  const int rst = ly.kind == KIND_CONV && A.mode == 0 && A.ntaps == 9 && A.w % 128 == 0 && B.co == 0 &&
+                          B.cs == ly.cout && tensor_map_encoder() != nullptr
+                      ? wgrad_tma_stages(A.cin, ly.cout, g.Mtiles)
+                      : 0;
+  int splits;
+  if (rst > 0) {
+    const int n_img = (int)(K / ((int64_t)A.h * A.w));
+    const int ntiles = n_img * A.h * (A.w / 128);
+    splits = std::min(ntiles, u->num_sms);
+    if ((size_t)splits * Mpad * g.np > u->wpart_floats)
+      return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
+    CUtensorMap xm, gm;
+    if (!encode_map(&xm, A.src + A.co, A.cin, A.cs, A.w, A.h, n_img, kHaloW, kHaloH) ||
+        !encode_map(&gm, B.src, ly.cout, ly.cout, A.w, A.h, n_img, 128, 1))
+      return fail(c, SC_ERR_CUDA, "sc_unet wgrad: tensor map encoding failed");
+    const int smem = (int)wg_smem_bytes(A.cin, ly.cout, rst);
+    static bool attr[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (dev >= 0 && dev < kMaxDev && !attr[dev]) {
+        UCHK(cudaFuncSetAttribute(k_wgrad_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr[dev] = true;
+      }
+    }
+    k_wgrad_tma<<<splits, kWgThreads, smem, sc::ctx_stream(c)>>>(xm, gm, A.cin, ly.cout, g.Mtiles, rst, n_img, A.h,
+                                                                    A.w, u->wpart, sc::ctx_status(c));
+    UCHK(cudaGetLastError());
+  } else {
+    int ks;
+    split_k(g.Mtiles, K, u->num_sms, &splits, &ks);
+    if ((size_t)splits * Mpad * g.np > u->wpart_floats)
+      return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
+    EPartial ep;
+    ep.part = u->wpart;
+    ep.ld = g.np;
+    ep.Mpad = Mpad;
+    const int N = ly.kind == KIND_UP ? 4 * ly.cout : ly.cout;
+    UCHK(gemm(A, B, ep, g.rows + 1, N, (int)K, splits, ks, sc::ctx_status(c), sc::ctx_stream(c)));
+  }
   const int64_t tot = (int64_t)(g.rows + 1) * g.np;
   k_wgrad_reduce<<<(unsigned)((tot + kRedEntries - 1) / kRedEntries), kRedEntries * kRedGroups, 0,
                    sc::ctx_stream(c)>>>(
@@ -1007,6 +1059,7 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
     }
     int splits, ks;
     split_k(g.Mtiles, P[lvl], u->num_sms, &splits, &ks);
+    splits = std::max(splits, u->num_sms);  // the TMA weight-gradient kernel: one split per SM
     const size_t need = (size_t)splits * g.Mtiles * kTM * g.np;
     if (need > wpart) wpart = need;
   }

@@ -1,0 +1,238 @@
+// unet_wgrad.cuh -- weight gradient of a 3x3 convolution on tcgen05 with TMA tiles, for rows
+// whose width is a multiple of 128 pixels.
+//
+//   gw[o][tap][c] = sum_p gz[p][o] * x[p + offset(tap)][c],   gb[o] = sum_p gz[p][o]
+//
+// as D[(tap, c) | ones][o] = sum over pixels.  The contraction runs over pixels, so both operands
+// must have 8 consecutive pixels in each 16-byte row (K-major), while activations and gradients
+// are stored with 8 consecutive channels per 16 bytes.  Per tile of 128 pixels of one row, the
+// producer warp brings with TMA the 3 x 130 pixel neighbourhood of x (as the forward kernel does)
+// and the 128 pixels of gz; four transposer warps build each 128-row block of the A operand (rows
+// (tap, c): the slab read at the tap's pixel offset) and the B operand (rows o) with
+// ldmatrix.trans (8 x 8 transposes from shared memory) into the padded canonical layout; one
+// thread issues the MMAs.  The accumulators of all row blocks (rows 9 cin + 1, 128 per block,
+// cout columns each, 32/64/128 apart) stay in TMEM across the CTA's whole range of tiles; at the end the
+// epilogue warps write them as this CTA's partial sums, reduced in a fixed order by
+// k_wgrad_reduce.  Every wait is bounded.
+#pragma once
+#include "unet_conv.cuh"
+
+namespace sc {
+namespace unet {
+
+constexpr uint32_t kGzTileBytes = 128 * 16;           // one group of 8 gz channels of a tile
+constexpr uint32_t kTLBO = 144;                         // padded K-direction core stride
+constexpr uint32_t kTSBO = 16 * kTLBO;                  // 16 pixel groups per 8-row group
+constexpr uint32_t kTBlockBytes = 16 * kTSBO;           // one 128-row operand block
+constexpr int kWgWarps = 10;                            // producer, MMA, 8 transposers
+constexpr int kWgThreads = 32 * kWgWarps;
+constexpr int kWgTrans = kWgWarps - 2;
+
+__host__ __device__ constexpr uint32_t wg_raw_bytes(int cin, int cout) {
+  return align_up((uint32_t)(cin / 8) * kSlabBytes + (uint32_t)(cout / 8) * kGzTileBytes, 1024);
+}
+__host__ __device__ constexpr uint32_t wg_b_bytes(int cout) { return align_up((uint32_t)(cout / 8) * kTSBO, 1024); }
+__host__ __device__ constexpr uint32_t wg_cstride(int cout) { return cout <= 32 ? 32u : (cout <= 64 ? 64u : 128u); }
+__host__ __device__ constexpr size_t wg_smem_bytes(int cin, int cout, int rstages) {
+  return (size_t)rstages * wg_raw_bytes(cin, cout) + 2 * kTBlockBytes + 2 * wg_b_bytes(cout) + 256;
+}
+
+__global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_constant__ CUtensorMap xmap,
+                                                               const __grid_constant__ CUtensorMap gmap, int cin,
+                                                               int cout, int mtiles, int rstages, int n_img, int h,
+                                                               int w, float *part, unsigned *status) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ngx = cin / 8, ngz = cout / 8;
+  const int rows = 9 * cin;  // data rows; row `rows` is the ones row
+  const uint32_t rawb = wg_raw_bytes(cin, cout), bb = wg_b_bytes(cout);
+  uint8_t *sRaw = sm;
+  uint8_t *sA = sm + rstages * rawb;
+  uint8_t *sB = sA + 2 * kTBlockBytes;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sB + 2 * bb);
+  // [0,1] raw full, [2,3] raw empty, [4,5] A full, [6,7] A empty, [8,9] B full, [10,11] B empty, [12] done
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 13);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(slot + 1);
+  const int tiles_x = w / 128;
+  const int ntiles = n_img * h * tiles_x;
+  const int t0 = (int)((int64_t)blockIdx.x * ntiles / gridDim.x);
+  const int t1 = (int)((int64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
+  const int mine = t1 - t0;
+  const uint32_t cstride = wg_cstride(cout);
+  uint32_t cols = 32;
+  while (cols < (uint32_t)mtiles * cstride) cols <<= 1;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(tc::smem_addr(&bar[0 + i]), 1);
+      tc::mbar_init(tc::smem_addr(&bar[2 + i]), kWgTrans);
+      tc::mbar_init(tc::smem_addr(&bar[4 + i]), kWgTrans);
+      tc::mbar_init(tc::smem_addr(&bar[6 + i]), 1);
+      tc::mbar_init(tc::smem_addr(&bar[8 + i]), kWgTrans);
+      tc::mbar_init(tc::smem_addr(&bar[10 + i]), 1);
+    }
+    tc::mbar_init(tc::smem_addr(&bar[12]), 1);
+    *abort_flag = 0;
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tc::smem_addr(slot), cols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = *slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer: x neighbourhood and gz tile per pixel tile ------------------------------
+      int i = 0;
+      for (; i < mine && !*abort_flag; ++i) {
+        const int rs = i % rstages, u = i / rstages;
+        if (u > 0 && !tc::mbar_wait(tc::smem_addr(&bar[2 + rs]), (u - 1) & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        const int t = t0 + i;
+        const int xt = t % tiles_x, r = t / tiles_x, y = r % h, img = r / h;
+        const uint32_t full = tc::smem_addr(&bar[0 + rs]);
+        tc::mbar_expect_tx(full, (uint32_t)ngx * kSlabTx + (uint32_t)ngz * kGzTileBytes);
+        const uint32_t dst = tc::smem_addr(sRaw + rs * rawb);
+        for (int g = 0; g < ngx; ++g) tc::tma_load_4d(dst + g * kSlabBytes, &xmap, 8 * g, xt * 128 - 1, y - 1, img, full);
+        const uint32_t gdst = dst + ngx * kSlabBytes;
+        for (int g = 0; g < ngz; ++g) tc::tma_load_4d(gdst + g * kGzTileBytes, &gmap, 8 * g, xt * 128, y, img, full);
+      }
+      for (int k = i - rstages; k < i; ++k)
+        if (k >= 0) tc::mbar_wait(tc::smem_addr(&bar[0 + k % rstages]), (k / rstages) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ---------------------------------------------------------------------------
+      const uint32_t idesc = tc::idesc_bf16_f32(kTM, cout);
+      bool ok = true;
+      int m = 0;  // operand blocks consumed
+      for (int i = 0; ok && i < mine; ++i) {
+        const int bs = i & 1;
+        if (!tc::mbar_wait(tc::smem_addr(&bar[8 + bs]), (i >> 1) & 1)) ok = false;
+        const uint32_t b0 = tc::smem_addr(sB + bs * bb);
+        for (int k = 0; ok && k < mtiles; ++k, ++m) {
+          const int ab = m & 1;
+          if (!tc::mbar_wait(tc::smem_addr(&bar[4 + ab]), (m >> 1) & 1) || *abort_flag) {
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+          const uint32_t a0 = tc::smem_addr(sA + ab * kTBlockBytes);
+          for (int ks = 0; ks < 8; ++ks)
+            tc::mma_bf16(taddr + (uint32_t)k * cstride, tc::smem_desc(a0 + (uint32_t)ks * 2u * kTLBO, kTLBO, kTSBO),
+                         tc::smem_desc(b0 + (uint32_t)ks * 2u * kTLBO, kTLBO, kTSBO), idesc,
+                         (i > 0 || ks > 0) ? 1u : 0u);
+          tc::mma_commit(tc::smem_addr(&bar[6 + ab]));  // A block free
+        }
+        if (ok) tc::mma_commit(tc::smem_addr(&bar[10 + bs]));  // B block free
+      }
+      if (!ok) *abort_flag = 1;
+      tc::mma_commit(tc::smem_addr(&bar[12]));  // all MMAs issued by this thread complete
+    }
+  } else {
+    // ---- transposers (warps 2..9), then the epilogue (warps 2..5) -----------------------------
+    const int tw = warp - 2;
+    const int mrow = lane & 7, mat = lane >> 3;  // ldmatrix: this lane's row and matrix
+    const uint32_t wofs = (uint32_t)(lane >> 2) * 16u + (uint32_t)(lane & 3) * 4u;  // store offset in a core
+    int m = 0;
+    bool ok = true;
+    for (int i = 0; ok && i < mine; ++i) {
+      const int rs = i % rstages;
+      if (!tc::mbar_wait(tc::smem_addr(&bar[0 + rs]), (i / rstages) & 1)) {
+        ok = false;
+        break;
+      }
+      const uint32_t raw = tc::smem_addr(sRaw + rs * rawb);
+      const uint32_t gz = raw + ngx * kSlabBytes;
+      // B block: rows o (cout), 128 pixels; unit q = (og, quad of pixel groups), one ldmatrix.x4 each
+      const int bs = i & 1;
+      if (i >= 2 && !tc::mbar_wait(tc::smem_addr(&bar[10 + bs]), ((i >> 1) - 1) & 1)) {
+        ok = false;
+        break;
+      }
+      uint8_t *bdst = sB + bs * bb;
+      for (int q = tw; q < ngz * 4; q += kWgTrans) {
+        const int og = q >> 2, pg = (q & 3) * 4 + mat;
+        uint32_t r[4];
+        tc::ldsm_x4_trans(gz + og * kGzTileBytes + (uint32_t)(8 * pg + mrow) * 16u, r[0], r[1], r[2], r[3]);
+        uint8_t *c0 = bdst + og * kTSBO + (uint32_t)((q & 3) * 4) * kTLBO + wofs;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) *reinterpret_cast<uint32_t *>(c0 + j * kTLBO) = r[j];
+      }
+      tc::fence_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(tc::smem_addr(&bar[8 + bs]));
+      // A blocks: rows 128k .. 128k+127 of (tap, c) | ones | zero; 64 units (16 core rows x 4
+      // quads of pixel groups) per block, 8 per warp, transposed 4 at a time
+      for (int k = 0; k < mtiles; ++k, ++m) {
+        const int ab = m & 1;
+        if (m >= 2 && !tc::mbar_wait(tc::smem_addr(&bar[6 + ab]), ((m >> 1) - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        uint8_t *adst = sA + ab * kTBlockBytes;
+#pragma unroll
+        for (int b4 = 0; b4 < 64 / kWgTrans; b4 += 4) {
+          uint32_t r[4][4];
+          int r0w[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int q = tw + kWgTrans * (b4 + e);
+            const int rg = q >> 2, quad = q & 3;
+            r0w[e] = 128 * k + 8 * rg;  // first operand row of this core row
+            if (r0w[e] < rows) {
+              const int tap = r0w[e] / cin, cg = (r0w[e] - tap * cin) >> 3;
+              const int dy = tap / 3, dx = tap - 3 * dy;  // slab row and column offset (0..2)
+              const int pg = quad * 4 + mat;
+              tc::ldsm_x4_trans(raw + cg * kSlabBytes + (uint32_t)(dy * kHaloW + 8 * pg + mrow + dx) * 16u, r[e][0],
+                                r[e][1], r[e][2], r[e][3]);
+            } else {
+              // the ones row (bias gradient) heads the first core row after the data; the rest is zero
+              const uint32_t v = (r0w[e] == rows && (lane >> 2) == 0) ? 0x3F803F80u : 0u;
+              r[e][0] = r[e][1] = r[e][2] = r[e][3] = v;
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int q = tw + kWgTrans * (b4 + e);
+            uint8_t *c0 = adst + (q >> 2) * kTSBO + (uint32_t)((q & 3) * 4) * kTLBO + wofs;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) *reinterpret_cast<uint32_t *>(c0 + j * kTLBO) = r[e][j];
+          }
+        }
+        tc::fence_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(tc::smem_addr(&bar[4 + ab]));
+      }
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(tc::smem_addr(&bar[2 + rs]));  // raw stage read
+    }
+    if (!ok) *abort_flag = 1;
+    // epilogue (warps 2..5: TMEM lane quarters 2, 3, 0, 1): this CTA's partial sums of every row block
+    const int qd = warp & 3;
+    const bool done = tc::mbar_wait(tc::smem_addr(&bar[12]), 0);
+    tc::fence_after();
+    const int Mpad = mtiles * kTM;
+    for (int k = 0; warp < 6 && k < mtiles; ++k)
+      for (int n0 = 0; n0 < cout; n0 += 16) {
+        float v[16];
+        tc::tmem_ld16(taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)k * cstride + (uint32_t)n0, v);
+        if (done && !*abort_flag && mine > 0) {
+          float4 *p = reinterpret_cast<float4 *>(part + ((int64_t)blockIdx.x * Mpad + 128 * k + 32 * qd + lane) * cout + n0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) p[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+      }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(taddr, cols);
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(status, SC_STATUS_WATCHDOG);
+}
+
+}  // namespace unet
+}  // namespace sc
