@@ -736,19 +736,31 @@ cudaError_t conv3x3(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h,
     std::lock_guard<std::mutex> lk(mu);
     if (!attr_set[dev]) {
       cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
       if (err != cudaSuccess) return err;
       attr_set[dev] = true;
     }
   }
-  int occ = 0;
-  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kConvThreads, smem);
+  // CTAs resident per SM: shared memory, registers and threads, capped by TMEM (the dynamic
+  // shared memory is padded so that no more than the TMEM cap can ever be co-resident)
+  cudaFuncAttributes fa;
+  cudaError_t err = cudaFuncGetAttributes(&fa, kern);
   if (err != cudaSuccess) return err;
   const int cols = 2 * (int)conv_acc_cols(N);
-  if (occ * cols > 512) occ = 512 / cols;
-  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const int by_tmem = 512 / cols;
+  const int regs = ((fa.numRegs + 7) / 8) * 8 * kConvThreads;
+  const int by_regs = regs > 0 ? 65536 / regs : 1;
+  const int kSmemPerSM = 228 * 1024, kSmemPerBlockReserve = 1024;
+  int smem_launch = smem;
+  if (kSmemPerSM / (smem_launch + kSmemPerBlockReserve) > by_tmem)
+    smem_launch = kSmemPerSM / (by_tmem + 1) - kSmemPerBlockReserve + 16;
+  const int by_smem = kSmemPerSM / (smem_launch + kSmemPerBlockReserve);
+  int occ = std::min(std::min(by_smem, by_regs), std::min(by_tmem, 2048 / kConvThreads));
+  if (occ < 1) occ = 1;
   const int ntiles = n * h * (w / 128);
   const int grid = std::min(ntiles, u->num_sms * occ);
-  kern<<<grid, kConvThreads, smem, s>>>(map, wtma, cin, N, gs, n, h, w, sign, e, st);
+  kern<<<grid, kConvThreads, smem_launch, s>>>(map, wtma, cin, N, gs, n, h, w, sign, e, st);
   return cudaGetLastError();
 }
 
