@@ -31,15 +31,16 @@ UNIT = "Mpaths/s"
 WORKLOAD = ("glass_scene_512: 4 glass meshes x ~20k tris (sphere, hollow cylinder, torus, superellipsoid; seed 0) "
             "over checkered floor+wall, 1x1 m rect light, Cauchy A=1.5 B=0.004, 8 bins, depth 12, "
             "256 spp + 4M light paths, LBVH build + resolve per frame")
-# FP32 work per traversal step: a node visit tests two child boxes, each slab
-# test being 3 axes x 2 planes x (sub + mul); a watertight triangle test is ~43 flops.
-FLOPS_PER_NODE = 24
+# FP32 work per traversal step: a 4-wide node visit tests four child boxes, each slab test being
+# 3 axes x 2 planes x (sub + mul), and loads 7 float4 (boxes + child references); a watertight
+# triangle test is ~43 flops on 48 bytes.
+FLOPS_PER_NODE = 48
 FLOPS_PER_TRI = 43
-BYTES_PER_NODE = 64
+BYTES_PER_NODE = 112
 BYTES_PER_TRI = 48
 # our kernels per step: LBVH build (bounds init, gather, morton, 8 x (hist, scan, scatter),
-# reorder, karras, refit, depth) + camera + lights + resolve
-LAUNCHES_PER_STEP = 30 + 3
+# reorder, karras, refit, depth, 4-wide collapse) + camera + lights + resolve
+LAUNCHES_PER_STEP = 31 + 3
 
 
 def parse():

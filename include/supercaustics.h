@@ -198,9 +198,10 @@ typedef struct {
 /* Read-only summary of a built scene. */
 typedef struct {
   int32_t n_tris, n_nodes, n_materials, n_lights;
-  int64_t bvh_bytes;   /* nodes + reordered triangles + shading attributes */
-  int32_t max_depth;   /* deepest leaf of the BVH */
-  int32_t pad;
+  int64_t bvh_bytes;   /* binary + 4-wide nodes + reordered triangles + shading attributes */
+  int32_t max_depth;   /* deepest leaf of the binary BVH */
+  int32_t bvh_width;   /* children per node of the camera kernel's traversal (4: nodes collapsed
+                          from the binary LBVH, which the other kernels traverse) */
 } sc_scene_info;
 
 /* --- context ------------------------------------------------------------------------- */
@@ -218,7 +219,8 @@ const char *sc_last_error(const sc_ctx *ctx);
 int sc_sync_status(sc_ctx *ctx);
 /* Optional traversal work counters: a device uint64[3] that sc_trace_camera and
  * sc_trace_lights add to while set: [0] traversal queries (closest + any hit), [1] BVH
- * nodes visited (each = two child-box tests), [2] triangle tests.  NULL switches counting
+ * nodes visited (sc_trace_camera: 4-wide nodes, four child-box tests each;
+ * sc_trace_lights: binary nodes, two each), [2] triangle tests.  NULL switches counting
  * off.  The caller owns the buffer and zeroes it. */
 int sc_set_counters(sc_ctx *ctx, uint64_t *counters);
 

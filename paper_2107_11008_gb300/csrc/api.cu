@@ -22,7 +22,7 @@ struct sc_ctx {
 
 struct sc_scene {
   sc::DevScene dev{};
-  void *persist = nullptr;  // one allocation: nodes | tris | shade | shade2 | tri_obj | mats | lights | depth
+  void *persist = nullptr;  // one allocation: nodes | nodes4 | tris | shade | shade2 | tri_obj | mats | lights | depth
   size_t persist_bytes = 0;
   int32_t *d_depth = nullptr;
   int n_tris = 0, n_nodes = 0;
@@ -224,6 +224,7 @@ int sc_build_scene(sc_ctx *c, const sc_scene_desc *d, sc_scene **out) {
   // persistent block
   Carver P{nullptr};
   P.take<float4>(sizeof(float4) * 4 * nn);
+  P.take<float4>(sizeof(float4) * 8 * nn);
   P.take<float4>(sizeof(float4) * 3 * nt);
   P.take<float4>(sizeof(float4) * 3 * nt);
   P.take<float4>(sizeof(float4) * nt);
@@ -240,6 +241,7 @@ int sc_build_scene(sc_ctx *c, const sc_scene_desc *d, sc_scene **out) {
   Carver Q{static_cast<char *>(s->persist)};
   sc::BuildBuffers b{};
   b.nodes = Q.take<float4>(sizeof(float4) * 4 * nn);
+  b.nodes4 = Q.take<float4>(sizeof(float4) * 8 * nn);
   b.tris = Q.take<float4>(sizeof(float4) * 3 * nt);
   b.shade = Q.take<float4>(sizeof(float4) * 3 * nt);
   b.shade2 = Q.take<float4>(sizeof(float4) * nt);
@@ -334,6 +336,7 @@ int sc_build_scene(sc_ctx *c, const sc_scene_desc *d, sc_scene **out) {
   s->n_tris = n;
   s->n_nodes = nn;
   s->dev.nodes = b.nodes;
+  s->dev.nodes4 = b.nodes4;
   s->dev.tris = b.tris;
   s->dev.shade = b.shade;
   s->dev.shade2 = b.shade2;
@@ -364,7 +367,8 @@ int sc_scene_get_info(const sc_scene *s, sc_scene_info *info) {
   info->n_nodes = s->n_nodes;
   info->n_materials = s->dev.n_mats;
   info->n_lights = s->dev.n_lights;
-  info->bvh_bytes = (int64_t)s->n_nodes * 64 + (int64_t)s->n_tris * (48 + 48 + 16 + 4);
+  info->bvh_bytes = (int64_t)s->n_nodes * (64 + 128) + (int64_t)s->n_tris * (48 + 48 + 16 + 4);
+  info->bvh_width = s->dev.nodes4 ? 4 : 2;
   int32_t depth = -1;
   if (cudaMemcpy(&depth, s->d_depth, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
     cudaGetLastError();

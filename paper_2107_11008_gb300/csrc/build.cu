@@ -16,6 +16,8 @@
 //      (ordering through __threadfence + an atomic counter per node).
 #include <cfloat>
 
+#include <algorithm>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -347,6 +349,60 @@ __global__ void k_depth(BuildBuffers b) {
   atomicMax(b.depth, d);
 }
 
+// Collapse the binary LBVH into 4-wide nodes: every binary node at even depth becomes a 4-wide
+// node whose children are its children, an internal child being replaced by that child's two
+// children (so a 4-wide node's internal children are again at even depth).  The 4-wide node is
+// stored at the binary node's index; nodes at odd depth leave their slot unused.
+__global__ void k_collapse4(BuildBuffers b) {
+  const int n = b.n_tris;
+  const int n_int = n > 1 ? n - 1 : 1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_int) return;
+  int depth = 0;
+  for (int node = i; node != 0 && depth <= 4 * 64;) {
+    node = b.parents[node] >> 1;
+    ++depth;
+  }
+  if (depth & 1) return;
+  float lo[3][4], hi[3][4];
+  int ref[4];
+  int cnt = 0;
+  auto take = [&](int m, int slot) {  // child `slot` of binary node m
+    const float4 *nd = b.nodes + 4 * m;
+    const float4 xy = nd[slot], z = nd[2], r = nd[3];
+    lo[0][cnt] = xy.x;
+    hi[0][cnt] = xy.y;
+    lo[1][cnt] = xy.z;
+    hi[1][cnt] = xy.w;
+    lo[2][cnt] = slot ? z.z : z.x;
+    hi[2][cnt] = slot ? z.w : z.y;
+    ref[cnt] = __float_as_int(slot ? r.y : r.x);
+    ++cnt;
+  };
+  const float4 r = b.nodes[4 * i + 3];
+  for (int slot = 0; slot < 2; ++slot) {
+    const int c = __float_as_int(slot ? r.y : r.x);
+    if (c < 0) {
+      take(i, slot);
+    } else {
+      take(c, 0);
+      take(c, 1);
+    }
+  }
+  for (int k = cnt; k < 4; ++k) {
+    lo[0][k] = lo[1][k] = lo[2][k] = 0.0f;
+    hi[0][k] = hi[1][k] = hi[2][k] = 0.0f;
+    ref[k] = kEmptyRef;
+  }
+  float4 *o = b.nodes4 + 8 * i;
+  for (int a = 0; a < 3; ++a) {
+    o[2 * a] = make_float4(lo[a][0], lo[a][1], lo[a][2], lo[a][3]);
+    o[2 * a + 1] = make_float4(hi[a][0], hi[a][1], hi[a][2], hi[a][3]);
+  }
+  o[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]), __int_as_float(ref[3]));
+  o[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
 #define SC_TRY(x)                              \
   do {                                         \
     cudaError_t e_ = (x);                      \
@@ -381,6 +437,10 @@ cudaError_t launch_build(const BuildBuffers &b, cudaStream_t s) {
   }
   k_refit<<<G, T, 0, s>>>(b);
   k_depth<<<G, T, 0, s>>>(b);
+  if (b.nodes4) {
+    const int Gi = (std::max(n - 1, 1) + T - 1) / T;
+    k_collapse4<<<Gi, T, 0, s>>>(b);
+  }
   return cudaGetLastError();
 }
 

@@ -18,7 +18,8 @@
 namespace sc {
 
 constexpr float kPi = 3.14159265358979323846f;
-constexpr int kStack = 64;
+constexpr int kStack = 96;   // 4-wide traversal (camera kernel) pushes up to 3 entries per visit
+constexpr int kStack2 = 64;  // binary traversal (trace())
 constexpr uint32_t kMiss = 0xFFFFFFFFu;
 constexpr int kMaxBins = 64;
 // traversal watchdog: node visits per query before the query is abandoned
@@ -166,6 +167,7 @@ __device__ __forceinline__ float3 cam_dir(const Cam &c, float sx, float sy) {
 
 struct DevScene {
   const float4 *nodes;
+  const float4 *nodes4;  // 4-wide nodes collapsed from the binary LBVH (NULL: traverse `nodes`)
   const float4 *tris;
   const float4 *shade;
   const float4 *shade2;
@@ -274,13 +276,36 @@ struct Hit {
   uint32_t id;  // input triangle id
 };
 
-// Work done by traversal queries (node visits = internal nodes loaded, each with two box tests).
+// Work done by traversal queries (node visits = 4-wide nodes loaded, each with four box tests).
 struct TravCount {
   unsigned nodes = 0, tris = 0, queries = 0;
 };
 
+// Resumable form of trace(): the query's state lives with the caller and each call visits at
+// most `budget` nodes, so a persistent kernel can interleave other lanes' shading with long
+// traversals.  Results are identical to trace() (same visit order, same tie-break).
+struct TravState {
+  Hit h;
+  int node, sp, visits;
+  bool anyhit;
+};
+__device__ __forceinline__ void trav_begin(TravState &ts, float tmax, bool anyhit) {
+  ts.h.t = tmax;
+  ts.h.prim = -1;
+  ts.h.id = kMiss;
+  ts.h.b1 = ts.h.b2 = 0.0f;
+  ts.node = 0;
+  ts.sp = 0;
+  ts.visits = 0;
+  ts.anyhit = anyhit;
+}
+__device__ __forceinline__ bool trav_step4(const DevScene &S, const WRay &w, float tmax, TravState &ts, int *stack,
+                                           int budget, unsigned *status, TravCount &tc);
+
 // Closest hit (anyhit = false; ties on equal t go to the lowest input id) or any hit with
-// 0 < t < tmax (anyhit = true; returns the first one found).  One traversal loop serves both so
+// 0 < t < tmax (anyhit = true; returns the first one found), over the binary LBVH: the kernels
+// that trace whole paths per thread (light tracer, resolve, queries) run faster on it than on the
+// 4-wide nodes the camera kernel's state machine uses.  One traversal loop serves both so
 // that lanes of a warp tracing shadow rays and extension rays stay in the same loop.  Stack
 // overflow and the visit watchdog latch a status bit and abandon the query (reported as a miss).
 static __device__ __forceinline__ Hit trace(const DevScene &S, float3 o, float3 d, float tmax, bool anyhit,
@@ -293,7 +318,7 @@ static __device__ __forceinline__ Hit trace(const DevScene &S, float3 o, float3 
   h.b1 = h.b2 = 0.0f;
   if (S.n_tris <= 0) return h;
   const WRay w = make_wray(o, d);
-  int stack[kStack];
+  int stack[kStack2];
   int sp = 0;
   int node = 0;
   int visits = 0;
@@ -337,7 +362,7 @@ static __device__ __forceinline__ Hit trace(const DevScene &S, float3 o, float3 
     }
     if (ha && hb) {
       const bool a_first = ta <= tb;
-      if (sp >= kStack) {
+      if (sp >= kStack2) {
         atomicOr(status, SC_STATUS_STACK_OVERFLOW);
         h.prim = -1;
         h.id = kMiss;
@@ -359,28 +384,40 @@ static __device__ __forceinline__ Hit trace(const DevScene &S, float3 o, float3 
   return h;
 }
 
-// Resumable form of trace(): the query's state lives with the caller and each call visits at
-// most `budget` nodes, so a persistent kernel can interleave other lanes' shading with long
-// traversals.  Results are identical to trace() (same visit order, same tie-break).
-struct TravState {
-  Hit h;
-  int node, sp, visits;
-  bool anyhit;
-};
-__device__ __forceinline__ void trav_begin(TravState &ts, float tmax, bool anyhit) {
-  ts.h.t = tmax;
-  ts.h.prim = -1;
-  ts.h.id = kMiss;
-  ts.h.b1 = ts.h.b2 = 0.0f;
-  ts.node = 0;
-  ts.sp = 0;
-  ts.visits = 0;
-  ts.anyhit = anyhit;
-}
 // Returns true when the query is complete (ts.h holds the answer; prim < 0 = miss).
 __device__ __forceinline__ bool trav_step(const DevScene &S, const WRay &w, float tmax, TravState &ts, int *stack,
                                           int budget, unsigned *status, TravCount &tc) {
   if (S.n_tris <= 0) return true;
+  return trav_step4(S, w, tmax, ts, stack, budget, status, tc);
+}
+
+// ------------------------------------------------------------------------------------------
+// 4-wide traversal.  Node j of nodes4 (8 float4, j = the index of the binary node it was
+// collapsed from) holds, structure-of-arrays, the boxes of up to four children: x lo, x hi,
+// y lo, y hi, z lo, z hi, then the four child references (>= 0: a 4-wide node, < 0: leaf ~k,
+// kEmptyRef: no child).  One visit tests the four boxes, tests the hit leaves' triangles at
+// once, and continues with the nearest hit internal child, pushing the others farthest first.
+// The closest hit (with its tie-break on the input id) does not depend on the visit order.
+// ------------------------------------------------------------------------------------------
+constexpr int kEmptyRef = 0x7FFFFFFF;
+
+__device__ __forceinline__ float comp4(const float4 &v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void sort_pair(float &ka, int &ra, float &kb, int &rb) {
+  if (kb < ka) {
+    const float tk = ka;
+    ka = kb;
+    kb = tk;
+    const int tr = ra;
+    ra = rb;
+    rb = tr;
+  }
+}
+
+__device__ __forceinline__ bool trav_step4(const DevScene &S, const WRay &w, float tmax, TravState &ts, int *stack,
+                                           int budget, unsigned *status, TravCount &tc) {
+  const float kInf = __int_as_float(0x7f800000);
   for (int it = 0; it < budget; ++it) {
     ++tc.nodes;
     if (++ts.visits > kMaxVisits) {
@@ -397,20 +434,33 @@ __device__ __forceinline__ bool trav_step(const DevScene &S, const WRay &w, floa
       ts.h.t = tmax;
       return true;
     }
-    const float4 n0 = __ldg(&S.nodes[4 * node + 0]);
-    const float4 n1 = __ldg(&S.nodes[4 * node + 1]);
-    const float4 n2 = __ldg(&S.nodes[4 * node + 2]);
-    const float4 n3 = __ldg(&S.nodes[4 * node + 3]);
-    const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-    float ta, tb;
-    bool ha = box_test(w, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, ts.h.t, ta);
-    bool hb = box_test(w, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, ts.h.t, tb);
+    const float4 *nd = S.nodes4 + 8 * node;
+    const float4 xl = __ldg(nd), xh = __ldg(nd + 1), yl = __ldg(nd + 2), yh = __ldg(nd + 3);
+    const float4 zl = __ldg(nd + 4), zh = __ldg(nd + 5), rr = __ldg(nd + 6);
+    int ref[4] = {__float_as_int(rr.x), __float_as_int(rr.y), __float_as_int(rr.z), __float_as_int(rr.w)};
+    float key[4];
 #pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const bool hit_box = side == 0 ? ha : hb;
-      const int c = side == 0 ? c0 : c1;
-      if (hit_box && c < 0) {
-        const int k = ~c;
+    for (int i = 0; i < 4; ++i) {
+      float tn;
+      const bool hb = ref[i] != kEmptyRef &&
+                      box_test(w, comp4(xl, i), comp4(xh, i), comp4(yl, i), comp4(yh, i), comp4(zl, i), comp4(zh, i),
+                               ts.h.t, tn);
+      key[i] = hb ? tn : kInf;
+    }
+    // leaves (one triangle each) are tested right away, the hit ones of this lane in one compact
+    // loop (a warp runs as many triangle tests as its busiest lane, not one per child slot)
+    unsigned leaves = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (key[i] < kInf && ref[i] < 0) {
+        leaves |= 1u << i;
+        key[i] = kInf;
+      }
+    while (leaves) {
+      const int i = __ffs(leaves) - 1;
+      leaves &= leaves - 1;
+      {
+        const int k = ~(i == 0 ? ref[0] : (i == 1 ? ref[1] : (i == 2 ? ref[2] : ref[3])));
         if (!SC_IN_RANGE(status, 2, k, S.n_tris)) {
           ts.h.prim = -1;
           ts.h.id = kMiss;
@@ -427,32 +477,34 @@ __device__ __forceinline__ bool trav_step(const DevScene &S, const WRay &w, floa
             if (ts.anyhit) return true;
           }
         }
-        if (side == 0) ha = false;
-        else hb = false;
       }
     }
-    if (ha && hb) {
-      const bool a_first = ta <= tb;
-      if (ts.sp >= kStack) {
-        atomicOr(status, SC_STATUS_STACK_OVERFLOW);
-        ts.h.prim = -1;
-        ts.h.id = kMiss;
-        ts.h.t = tmax;
-        return true;
-      }
-      stack[ts.sp++] = a_first ? c1 : c0;
-      ts.node = a_first ? c0 : c1;
-    } else if (ha) {
-      ts.node = c0;
-    } else if (hb) {
-      ts.node = c1;
-    } else {
+    // internal children by entry distance (misses sort last)
+    sort_pair(key[0], ref[0], key[1], ref[1]);
+    sort_pair(key[2], ref[2], key[3], ref[3]);
+    sort_pair(key[0], ref[0], key[2], ref[2]);
+    sort_pair(key[1], ref[1], key[3], ref[3]);
+    sort_pair(key[1], ref[1], key[2], ref[2]);
+    const int cnt = (key[0] < kInf) + (key[1] < kInf) + (key[2] < kInf) + (key[3] < kInf);
+    if (cnt == 0) {
       if (ts.sp == 0) {
         if (ts.h.prim < 0) ts.h.t = tmax;
         return true;
       }
       ts.node = stack[--ts.sp];
+      continue;
     }
+    if (ts.sp + cnt - 1 > kStack) {
+      atomicOr(status, SC_STATUS_STACK_OVERFLOW);
+      ts.h.prim = -1;
+      ts.h.id = kMiss;
+      ts.h.t = tmax;
+      return true;
+    }
+    if (cnt > 3) stack[ts.sp++] = ref[3];
+    if (cnt > 2) stack[ts.sp++] = ref[2];
+    if (cnt > 1) stack[ts.sp++] = ref[1];
+    ts.node = ref[0];
   }
   return false;
 }

@@ -18,6 +18,8 @@ struct BuildBuffers {
   int32_t n_tris, n_objects;
   // outputs (device, owned by the scene)
   float4 *nodes;   // 4 * max(n_tris - 1, 1)
+  float4 *nodes4;  // 8 * max(n_tris - 1, 1): 4-wide nodes at the indices of the binary nodes they
+                   // were collapsed from (NULL: not built)
   float4 *tris;    // 3 * n_tris (leaf order)
   float4 *shade;   // 3 * n_tris (input order)
   float4 *shade2;  // n_tris

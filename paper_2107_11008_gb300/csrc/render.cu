@@ -17,7 +17,7 @@ namespace sc {
 constexpr int kBlock = 128;
 // resident blocks per SM the camera kernel is compiled for (register budget = 64K / (128 * this))
 #ifndef SC_CAM_MIN_BLOCKS
-#define SC_CAM_MIN_BLOCKS 1
+#define SC_CAM_MIN_BLOCKS 4
 #endif
 // node visits per traversal chunk in the camera kernel
 #ifndef SC_TRAV_CHUNK

@@ -87,7 +87,7 @@ class sc_frame(C.Structure):
 
 class sc_scene_info(C.Structure):
     _fields_ = [("n_tris", C.c_int32), ("n_nodes", C.c_int32), ("n_materials", C.c_int32), ("n_lights", C.c_int32),
-                ("bvh_bytes", C.c_int64), ("max_depth", C.c_int32), ("pad", C.c_int32)]
+                ("bvh_bytes", C.c_int64), ("max_depth", C.c_int32), ("bvh_width", C.c_int32)]
 
 
 class sc_unet_buffer_info(C.Structure):
