@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--res", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--den-ratio", type=int, default=64, help="denoise workload: light paths per camera sample")
+    ap.add_argument("--den-ratio", type=int, default=16, help="denoise workload: light paths per camera sample")
     ap.add_argument("--workload", default="glass512", choices=["glass512", "batch64", "unet_train", "denoise"],
                     help="batch64: 64 randomised scenes (1k-200k tris, 128^2..1024^2, 64 spp) in one graph-captured "
                          "persistent launch vs 64 sequential launches; unet_train: U-Net training steps on batches "
@@ -261,10 +261,12 @@ def run_unet_train(args):
 def run_denoise(args):
     """Denoised frames vs the plain tracer at matched MSE on held-out config-1-type scenes at 256^2.
 
-    Both pipelines spend the same ratio of light paths to camera samples (``--den-ratio``, 64):
-    the denoised frame is 4 camera spp + 4 x ratio light paths per pixel, the U-Net removing the
-    camera estimate's noise (it is trained on 64 pairs: that estimate at 4 spp -> 1024 spp) and
-    the light-traced caustic buffer added back; the plain frame is N spp + N x ratio light paths.
+    Both pipelines spend the same ratio of light paths to camera samples (``--den-ratio``, 16),
+    light paths aimed into the sphere around the glass (guided emission): the denoised frame is
+    4 camera spp + 4 x ratio light paths per pixel, the U-Net removing the camera estimate's noise
+    (trained 6000 steps on 16 random 128^2 crops of 64 pairs: that estimate at 4 spp -> 1024 spp)
+    and the light-traced caustic buffer added back; the plain frame is N spp + N x ratio light
+    paths.
     MSEs are against a reference of two independent halves (2048 spp + 8192 light paths / px
     each), with the reference's own variance, MSE(half_a, half_b) / 4, subtracted."""
     import numpy as np
@@ -288,6 +290,7 @@ def run_denoise(args):
     test_scenes = [S.denoise_scene(10_000 + i, hw, hw) for i in range(n_test)]
     test = T.make_pairs(ctx, test_scenes, lo, T.RenderSpec(0, 0), seed=2, source="direct")
     gss = [R.GpuScene(ctx, s) for s in test_scenes]
+    guides = [S.guide_sphere(s) for s in test_scenes]
     f = R.Frame(hw, hw, device=dev)
     half = T.RenderSpec(2048, 8192)
     ref_a = torch.empty_like(test.rgb_lo)
@@ -295,18 +298,20 @@ def run_denoise(args):
     for i, g in enumerate(gss):
         for k, dst in enumerate((ref_a, ref_b)):
             T.render(ctx, g, f, half, seed=3, sample_offset=(1 << 24) + k * half.spp,
-                     path_offset=(1 << 42) + k * 8192 * hw * hw, scene_index=i)
+                     path_offset=(1 << 42) + k * 8192 * hw * hw, scene_index=i, guide=guides[i])
             dst[i].copy_(f["rgb"])
     ref = 0.5 * (ref_a + ref_b)
     var_ref = T.mse(ref_a, ref_b) / 4.0
     gen_s = time.perf_counter() - t0
-    net = D.UNet(ctx, 8, hw, hw)
-    net.set_params(D.he_init(0).to(dev))
+    trainer = D.UNet(ctx, 16, 128, 128)  # 128^2 random crops of the 256^2 pairs, 16 per step
+    trainer.set_params(D.he_init(0).to(dev))
     t0 = time.perf_counter()
-    T.train(net, train, steps=1500, batch=8, lr=2e-3, lr_final=5e-5, seed=0)
+    T.train(trainer, train, steps=6000, batch=16, crop=128, lr=2e-3, lr_final=5e-5, seed=0)
     torch.cuda.synchronize(dev)
     train_s = time.perf_counter() - t0
     ctx.sync_status()
+    net = D.UNet(ctx, 8, hw, hw)
+    net.set_params(trainer.get_params())
     den = T.denoise(net, test.x, test.add())
     m_den = T.mse(den, ref) - var_ref
     m_in = T.mse(test.rgb_lo, ref) - var_ref
@@ -315,7 +320,7 @@ def run_denoise(args):
     for spp in (4, 8, 16, 32, 64, 128):
         out = torch.empty_like(ref)
         for i, g in enumerate(gss):
-            T.render(ctx, g, f, T.RenderSpec(spp, spp * ratio), seed=7, scene_index=i)
+            T.render(ctx, g, f, T.RenderSpec(spp, spp * ratio), seed=7, scene_index=i, guide=guides[i])
             out[i].copy_(f["rgb"])
         sweep[spp] = T.mse(out, ref) - var_ref
     ctx.sync_status()
@@ -339,7 +344,7 @@ def run_denoise(args):
     net1.set_params(net.get_params())
 
     def denoised_frame():
-        T.render(ctx, g0, f, lo, seed=11)
+        T.render(ctx, g0, f, lo, seed=11, guide=guides[0])
         D.pack_frame(ctx, f, x1, 0, source="direct")
         net1.forward(x1, y1)
         D.output_rgb(ctx, y1, f["caustic"], out=rgb1)
@@ -348,7 +353,7 @@ def run_denoise(args):
     plain_spec = T.RenderSpec(spp_int, spp_int * ratio)
 
     def plain_frame():
-        T.render(ctx, g0, f, plain_spec, seed=11)
+        T.render(ctx, g0, f, plain_spec, seed=11, guide=guides[0])
 
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     for fn in (denoised_frame, plain_frame):
@@ -392,8 +397,9 @@ def run_denoise(args):
                 "warmup": max(3, args.warmup), "ms_per_step": den_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic (scenes.denoise_scene)",
                 "config": {"workload": "denoise: 256^2 config-1-type scenes; U-Net on the camera estimate trained "
-                                       "1500 steps on 64 pairs (4 -> 1024 spp), light-traced caustics added back; "
-                                       "8 held-out scenes; reference 2 x (2048 spp + 8192 light paths/px)",
+                                       "6000 steps x 16 crops of 128^2 from 64 pairs (4 -> 1024 spp), guided "
+                                       "light-traced caustics added back; 8 held-out scenes; reference 2 x (2048 spp "
+                                       "+ 8192 guided light paths/px)",
                            "input": f"{lo.spp} camera spp + {lo.lights_per_pixel} light paths/px",
                            "light_paths_per_camera_sample": ratio},
                 "mse": {"denoised": m_den, "input": m_in, "reference_variance": var_ref, "plain_sweep": sweep},

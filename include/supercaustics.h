@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define SC_ABI_VERSION 1
+#define SC_ABI_VERSION 2
 
 #define SC_OK 0
 #define SC_ERR_INVALID_ARG (-1)
@@ -135,12 +135,21 @@ typedef struct {
   int32_t scene_index, flags;
 } sc_trace_params;
 
-/* Light tracer parameters: paths path_offset .. path_offset + n_paths - 1. */
+/* Light tracer parameters: paths path_offset .. path_offset + n_paths - 1.
+ * guide: a sphere (centre xyz, radius) enclosing every dielectric triangle, or radius <= 0 for
+ * none.  With a guide, point and rect lights emit only into the cone that subtends the sphere
+ * from the emission point (uniform within the cone; the path's throughput carries the cone's
+ * solid angle, and for a rect light the cosine to its normal, directions behind the light
+ * contributing nothing).  A caustic path L S+ D E meets glass first, so its first direction lies
+ * in that cone: the splat estimate keeps its expectation while no path is spent on directions
+ * that cannot make a caustic.  Disk lights (collimated) ignore the guide.  A guide together with
+ * SC_FLAG_SPLAT_DIRECT is rejected (direct splats start outside the cone). */
 typedef struct {
   int64_t n_paths, path_offset;
   int32_t max_depth, n_bins;
   uint64_t seed;
   int32_t scene_index, flags;
+  float guide[4];
 } sc_light_params;
 
 /* Resolve: divide accumulators by their totals and derive the ground-truth buffers. */

@@ -73,7 +73,7 @@ class PathRec(C.Structure):
 class LightParams(C.Structure):
     _fields_ = [("n_paths", C.c_int64), ("path_offset", C.c_int64), ("max_depth", C.c_int32), ("nbins", C.c_int32),
                 ("seed", C.c_uint64), ("scene_index", C.c_int32), ("flags", C.c_int32),
-                ("n_threads", C.c_int32), ("brute", C.c_int32), ("tol", Tolerances)]
+                ("n_threads", C.c_int32), ("brute", C.c_int32), ("tol", Tolerances), ("guide", C.c_double * 4)]
 
 
 class LightRec(C.Structure):
@@ -204,11 +204,13 @@ class OracleScene:
         return accum, (records_to_numpy(recs, PathRec) if records else None)
 
     def trace_lights(self, n_paths, max_depth, nbins=1, seed=0, path_offset=0, scene_index=0, flags=0,
-                     records=True, accum=None, n_threads=0, brute=False, tol=None):
+                     records=True, accum=None, n_threads=0, brute=False, tol=None, guide=None):
+        """guide: (cx, cy, cz, r) sphere around the dielectric triangles for guided emission, or None."""
         tol = tol or default_tol()
         if not records:
             tol.sens_delta = 0.0
-        P = LightParams(n_paths, path_offset, max_depth, nbins, seed, scene_index, flags, n_threads, int(brute), tol)
+        g = (C.c_double * 4)(*(guide if guide is not None else (0.0, 0.0, 0.0, 0.0)))
+        P = LightParams(n_paths, path_offset, max_depth, nbins, seed, scene_index, flags, n_threads, int(brute), tol, g)
         if accum is None:
             accum = np.zeros((self.H, self.W, 3))
         recs = (LightRec * n_paths)() if records else None

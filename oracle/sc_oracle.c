@@ -738,6 +738,7 @@ typedef struct {
   int32_t scene_index, flags;
   int32_t n_threads, brute;
   tolerances tol;
+  double guide[4]; /* sphere enclosing the dielectric triangles (centre, radius); radius <= 0: none */
 } light_params;
 
 typedef struct {
@@ -934,6 +935,25 @@ static void camera_path(const scene *s, const cam_params *P, const double *wts, 
 /* ------------------------------------------------------------------------------------------ */
 /* light path (caustics)                                                                       */
 /* ------------------------------------------------------------------------------------------ */
+
+/* Guided emission: a direction uniform in the cone that subtends the guide sphere (centre g[0..2],
+ * radius g[3]) from x, drawn from (u0, u1) as cos(theta) = 1 - u0 (1 - cos(theta_max)),
+ * phi = 2 pi u1 about the axis x -> centre.  Returns the cone's solid angle 2 pi (1 - cos
+ * theta_max), or 0 (no direction drawn) when there is no guide or x lies inside the sphere. */
+static double guided_dir(const double *g, v3 x, double u0, double u1, v3 *dir) {
+  if (!(g[3] > 0)) return 0.0;
+  v3 v = sub(V(g[0], g[1], g[2]), x);
+  double dist = len(v);
+  if (!(dist > g[3])) return 0.0;
+  v3 w = mul(v, 1.0 / dist), t1, t2;
+  double sin2 = (g[3] / dist) * (g[3] / dist);
+  double cmax = sqrt(fmax(0.0, 1.0 - sin2));
+  double omc = sin2 / (1.0 + cmax); /* 1 - cos(theta_max) */
+  double ct = 1.0 - u0 * omc, st = sqrt(fmax(0.0, 1.0 - ct * ct)), phi = 2.0 * PI * u1;
+  onb(w, &t1, &t2);
+  *dir = normalize(add(add(mul(t1, st * cos(phi)), mul(t2, st * sin(phi))), mul(w, ct)));
+  return 2.0 * PI * omc;
+}
 static void light_path_impl(const scene *s, const light_params *P, const double *wts, int64_t idx, double delta,
                             double *accum, light_rec *rec) {
   actx a;
@@ -954,20 +974,34 @@ static void light_path_impl(const scene *s, const light_params *P, const double 
     const light *L = &s->lights[j];
     ray r;
     v3 beta;
+    int emitted = 1;
     if (L->kind == LIGHT_POINT) {
       double z = 1.0 - 2.0 * u01(xd[0]), phi = 2.0 * PI * u01(xd[1]);
       double rr = sqrt(fmax(0.0, 1.0 - z * z));
       r.o = L->p;
-      r.d = normalize(V(rr * cos(phi), rr * sin(phi), z));
-      beta = mul(L->power, 4.0 * PI * s->nlights);
+      double omega = guided_dir(P->guide, r.o, u01(xd[0]), u01(xd[1]), &r.d);
+      if (omega > 0) {
+        beta = mul(L->power, omega * s->nlights);
+      } else {
+        r.d = normalize(V(rr * cos(phi), rr * sin(phi), z));
+        beta = mul(L->power, 4.0 * PI * s->nlights);
+      }
     } else if (L->kind == LIGHT_RECT) {
       v3 c = cross(L->u, L->v);
       double area = len(c);
       v3 nl = mul(c, 1.0 / area);
       v3 x = add(add(L->p, mul(L->u, u01(xe[1]))), mul(L->v, u01(xe[2])));
-      r.d = cosine_dir(nl, u01(xd[0]), u01(xd[1]));
+      double omega = guided_dir(P->guide, x, u01(xd[0]), u01(xd[1]), &r.d);
+      if (omega > 0) {
+        double cl = dot(r.d, nl);
+        note(&a, fabs(cl), P->tol.cosg, AMB_GRAZE);
+        emitted = cl > 0; /* one-sided emitter */
+        beta = mul(L->power, area * s->nlights * cl * omega);
+      } else {
+        r.d = cosine_dir(nl, u01(xd[0]), u01(xd[1]));
+        beta = mul(L->power, PI * area * s->nlights);
+      }
       r.o = add(x, mul(nl, eps_of(x)));
-      beta = mul(L->power, PI * area * s->nlights);
     } else {
       v3 dir = normalize(L->u), t1, t2;
       onb(dir, &t1, &t2);
@@ -978,7 +1012,7 @@ static void light_path_impl(const scene *s, const light_params *P, const double 
     }
     int had_spec = 0;
     nudge(&r, delta, P->seed ^ 0x5A5A5A5Aull, lo, hi, 0);
-    for (int k = 0; k < P->max_depth; ++k) {
+    for (int k = 0; emitted && k < P->max_depth; ++k) {
       hit h = closest_noted(s, r, P->brute, &a);
       sig = fnv(sig, h.tri < 0 ? EV_MISS : (uint32_t)h.tri);
       if (h.tri < 0) break;

@@ -1,4 +1,5 @@
 // api.cu -- the C ABI (include/supercaustics.h): contexts, scenes, launches, status.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -443,6 +444,10 @@ int sc_trace_lights(sc_ctx *c, const sc_scene *s, const sc_light_params *p, cons
   if (r) return r;
   if (!p || p->n_paths < 0 || p->path_offset < 0 || p->max_depth < 0 || p->n_bins < 1 || p->n_bins > sc::kMaxBins)
     return fail(c, SC_ERR_INVALID_ARG, "sc_trace_lights: bad parameters (n_bins must be 1..64)");
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(p->guide[k])) return fail(c, SC_ERR_INVALID_ARG, "sc_trace_lights: guide sphere not finite");
+  if (p->guide[3] > 0.0f && (p->flags & SC_FLAG_SPLAT_DIRECT))
+    return fail(c, SC_ERR_INVALID_ARG, "sc_trace_lights: a guide sphere cannot be combined with SC_FLAG_SPLAT_DIRECT");
   if (p->n_paths == 0) return SC_OK;
   const int grid = persistent_grid(c, sc::light_kernel_ptr(), &c->light_blocks_per_sm);
   cudaError_t e = sc::launch_trace_lights(s->dev, *p, *f, c->d_words,

@@ -331,27 +331,62 @@ __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_pa
     int pixel = -1;
     float3 C = f3(0.f, 0.f, 0.f), X = f3(__int_as_float(0x7FC00000), __int_as_float(0x7FC00000),
                                          __int_as_float(0x7FC00000));
+    bool emitted = true;
     if (S.n_lights > 0) {
       const int j = choose(xe.x, S.n_lights);
       const sc_light Lg = S.lights[j];
       float3 o, d, beta;
+      const float3 gc = f3(P.guide[0], P.guide[1], P.guide[2]);
+      const float gr = P.guide[3];
+      // guided emission: direction uniform in the cone subtending the guide sphere from x;
+      // returns the cone's solid angle, or 0 when x lies inside the sphere (then unguided)
+      auto guided = [&](float3 x, float3 &dir) -> float {
+        if (!(gr > 0.0f)) return 0.0f;
+        const float3 v = gc - x;
+        const float dist = length(v);
+        if (!(dist > gr)) return 0.0f;
+        const float3 wz = v * (1.0f / dist);
+        const float sin2 = (gr / dist) * (gr / dist);
+        const float cmax = sqrtf(fmaxf(0.0f, 1.0f - sin2));
+        const float omc = sin2 / (1.0f + cmax);  // 1 - cos(theta_max) without cancellation
+        const float ct = 1.0f - u01(xd.x) * omc;
+        const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+        float sp, cp;
+        sincospif(2.0f * u01(xd.y), &sp, &cp);
+        float3 t1, t2;
+        onb(wz, t1, t2);
+        dir = normalize(t1 * (st * cp) + t2 * (st * sp) + wz * ct);
+        return 2.0f * kPi * omc;
+      };
       if (Lg.kind == SC_LIGHT_POINT) {
         const float z = 1.0f - 2.0f * u01(xd.x);
         float s, c;
         sincospif(2.0f * u01(xd.y), &s, &c);
         const float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
         o = f3(Lg.p);
-        d = normalize(f3(rr * c, rr * s, z));
-        beta = f3(Lg.power) * (4.0f * kPi * S.n_lights);
+        const float omega = guided(o, d);
+        if (omega > 0.0f) {
+          beta = f3(Lg.power) * (omega * S.n_lights);
+        } else {
+          d = normalize(f3(rr * c, rr * s, z));
+          beta = f3(Lg.power) * (4.0f * kPi * S.n_lights);
+        }
       } else if (Lg.kind == SC_LIGHT_RECT) {
         const float3 eu = f3(Lg.u), ev = f3(Lg.v);
         const float3 c = cross(eu, ev);
         const float area = length(c);
         const float3 nlt = c * (1.0f / area);
         const float3 x = f3(Lg.p) + eu * u01(xe.y) + ev * u01(xe.z);
-        d = cosine_dir(nlt, u01(xd.x), u01(xd.y));
+        const float omega = guided(x, d);
+        if (omega > 0.0f) {
+          const float cl = dot(d, nlt);
+          emitted = cl > 0.0f;  // one-sided emitter
+          beta = f3(Lg.power) * (area * S.n_lights * cl * omega);
+        } else {
+          d = cosine_dir(nlt, u01(xd.x), u01(xd.y));
+          beta = f3(Lg.power) * (kPi * area * S.n_lights);
+        }
         o = x + nlt * eps_of(x);
-        beta = f3(Lg.power) * (kPi * area * S.n_lights);
       } else {
         const float3 dir = normalize(f3(Lg.u));
         float3 t1, t2;
@@ -364,7 +399,7 @@ __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_pa
         beta = f3(Lg.power) * (kPi * Lg.radius * Lg.radius * S.n_lights);
       }
       bool had_spec = false;
-      for (int k = 0; k < P.max_depth; ++k) {
+      for (int k = 0; emitted && k < P.max_depth; ++k) {
         const Hit h = closest_hit(S, o, d, 3.0e38f, status, tc);
         sig = fnv(sig, h.id);
         if (h.prim < 0) break;

@@ -58,7 +58,7 @@ class sc_trace_params(C.Structure):
 
 class sc_light_params(C.Structure):
     _fields_ = [("n_paths", C.c_int64), ("path_offset", C.c_int64), ("max_depth", C.c_int32), ("n_bins", C.c_int32),
-                ("seed", C.c_uint64), ("scene_index", C.c_int32), ("flags", C.c_int32)]
+                ("seed", C.c_uint64), ("scene_index", C.c_int32), ("flags", C.c_int32), ("guide", C.c_float * 4)]
 
 
 class sc_resolve_params(C.Structure):

@@ -238,8 +238,10 @@ def trace_camera(ctx: Context, gs: GpuScene, frame: Frame, spp: int, max_depth: 
 
 
 def trace_lights(ctx: Context, gs: GpuScene, frame: Frame, n_paths: int, max_depth: int, n_bins: int = 1,
-                 seed: int = 0, path_offset: int = 0, scene_index: int = 0, flags: int = 0):
-    p = N.sc_light_params(n_paths, path_offset, max_depth, n_bins, seed, scene_index, flags)
+                 seed: int = 0, path_offset: int = 0, scene_index: int = 0, flags: int = 0, guide=None):
+    """guide: (cx, cy, cz, r) from scenes.guide_sphere for guided emission, or None."""
+    g = (C.c_float * 4)(*(guide if guide is not None else (0.0, 0.0, 0.0, 0.0)))
+    p = N.sc_light_params(n_paths, path_offset, max_depth, n_bins, seed, scene_index, flags, g)
     N.sc_trace_lights(ctx.handle, gs.handle, p, frame.struct())
 
 

@@ -473,6 +473,23 @@ def ball_on_plane(width=64, height=64, subdiv=3, ior=1.5, light_pos=(2.0, 4.0, 2
     return b.build(cam, name=f"ball_on_plane_{width}x{height}")
 
 
+def guide_sphere(scene: Scene) -> tuple:
+    """(cx, cy, cz, r): a sphere enclosing every dielectric triangle, as float32 values (the
+    radius rounded up so that the rounded sphere still encloses them), or a zero radius when the
+    scene has no glass.  The light tracer's guided emission aims into this sphere."""
+    kinds = np.array([m.kind for m in scene.materials])
+    tri_mat = np.asarray(scene.object_material)[np.asarray(scene.tri_object)]
+    sel = kinds[tri_mat] == MAT_DIELECTRIC
+    if not sel.any():
+        return (0.0, 0.0, 0.0, 0.0)
+    v = np.asarray(scene.positions, np.float64)[np.asarray(scene.indices)[sel].ravel()]
+    c = (v.min(axis=0) + v.max(axis=0)) * 0.5
+    c32 = c.astype(np.float32).astype(np.float64)
+    r = np.sqrt(((v - c32) ** 2).sum(axis=1)).max() * (1.0 + 1e-5) + 1e-6
+    r32 = np.nextafter(np.float32(r), np.float32(np.inf))
+    return (float(c32[0]), float(c32[1]), float(c32[2]), float(r32))
+
+
 def denoise_scene(seed: int, width=64, height=64) -> Scene:
     """A ball-on-plane scene with randomised parameters, for denoiser training pairs: glass
     icosphere (1280 tris) of radius 0.6-1.2 resting on the plane y = -1 near the origin, IOR

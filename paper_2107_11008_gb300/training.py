@@ -19,7 +19,7 @@ import torch
 
 from . import denoiser as D
 from . import renderer as R
-from .scenes import Scene
+from .scenes import Scene, guide_sphere
 
 
 @dataclass
@@ -28,17 +28,20 @@ class RenderSpec:
     lights_per_pixel: float
     max_depth: int = 8
     n_bins: int = 1
+    guided: bool = True  # light paths aimed into the sphere around the glass (scenes.guide_sphere)
 
 
 def render(ctx: R.Context, gs: R.GpuScene, frame: R.Frame, spec: RenderSpec, seed: int, sample_offset: int = 0,
-           path_offset: int = 0, scene_index: int = 0):
-    """Camera paths + light paths + resolve into ``frame`` (accumulators cleared first)."""
+           path_offset: int = 0, scene_index: int = 0, guide=None):
+    """Camera paths + light paths + resolve into ``frame`` (accumulators cleared first); ``guide``
+    is the scene's guide sphere, used when ``spec.guided``."""
     frame.zero_accumulators()
     n_light = int(round(spec.lights_per_pixel * frame.width * frame.height))
     if spec.spp > 0:
         R.trace_camera(ctx, gs, frame, spec.spp, spec.max_depth, spec.n_bins, seed, sample_offset, scene_index)
     if n_light > 0:
-        R.trace_lights(ctx, gs, frame, n_light, spec.max_depth, spec.n_bins, seed, path_offset, scene_index)
+        R.trace_lights(ctx, gs, frame, n_light, spec.max_depth, spec.n_bins, seed, path_offset, scene_index,
+                       guide=guide if spec.guided else None)
     R.resolve(ctx, gs, frame, max(spec.spp, 1), max(n_light, 1))
 
 
@@ -72,12 +75,13 @@ def make_pairs(ctx: R.Context, scenes: list[Scene], lo: RenderSpec, hi: RenderSp
         if (sc.camera.width, sc.camera.height) != (w, h):
             raise ValueError("all scenes of a pair set share one resolution")
         gs = R.GpuScene(ctx, sc)
-        render(ctx, gs, f, lo, seed, 0, 0, scene_index=i)
+        guide = guide_sphere(sc)
+        render(ctx, gs, f, lo, seed, 0, 0, scene_index=i, guide=guide)
         D.pack_frame(ctx, f, x, i, source)
         rgb_lo[i].copy_(f["rgb"])
         caustic_lo[i].copy_(f["caustic"])
         # the target uses the samples after the input's: independent noise, same estimator
-        render(ctx, gs, f, hi, seed, lo.spp, n_light_lo, scene_index=i)
+        render(ctx, gs, f, hi, seed, lo.spp, n_light_lo, scene_index=i, guide=guide)
         D.pack_target(ctx, f, t, i, source)
         rgb_hi[i].copy_(f["rgb"])
         ctx.stream.synchronize()

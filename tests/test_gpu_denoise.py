@@ -38,7 +38,11 @@ def test_pairs_use_disjoint_samples_and_same_estimator(ctx):
 def test_trained_denoiser_beats_the_noisy_input(ctx, source, lights):
     """rgb: the network denoises the whole 4-spp image (4 light paths / px); direct: it denoises
     the 4-spp camera estimate and the caustic buffer of 1024 light paths / px is added back."""
-    lo, hi = T.RenderSpec(spp=4, lights_per_pixel=lights), T.RenderSpec(spp=512, lights_per_pixel=4096)
+    # rgb: uniform light emission, so that the network's input carries the noisy caustics it is
+    # asked to remove; direct: guided emission (the production setting)
+    guided = source == "direct"
+    lo = T.RenderSpec(spp=4, lights_per_pixel=lights, guided=guided)
+    hi = T.RenderSpec(spp=512, lights_per_pixel=4096, guided=guided)
     train = T.make_pairs(ctx, [S.denoise_scene(i, 64, 64) for i in range(48)], lo, hi, seed=1, source=source)
     test = T.make_pairs(ctx, [S.denoise_scene(1000 + i, 64, 64) for i in range(8)], lo, hi, seed=2, source=source)
     net = D.UNet(ctx, 8, 64, 64)

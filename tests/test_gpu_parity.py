@@ -210,7 +210,7 @@ def test_occluded_matches_oracle(ctx):
 # Estimators
 # ------------------------------------------------------------------------------------------
 
-def _render(ctx, sc, spp, depth, n_bins=1, n_light=0, seed=0, flags=0, lflags=0, records=True):
+def _render(ctx, sc, spp, depth, n_bins=1, n_light=0, seed=0, flags=0, lflags=0, records=True, guide=None):
     gs = R.GpuScene(ctx, sc)
     fr = R.Frame(sc.camera.width, sc.camera.height)
     if records:
@@ -220,7 +220,7 @@ def _render(ctx, sc, spp, depth, n_bins=1, n_light=0, seed=0, flags=0, lflags=0,
     if spp:
         R.trace_camera(ctx, gs, fr, spp, depth, n_bins, seed, flags=flags)
     if n_light:
-        R.trace_lights(ctx, gs, fr, n_light, depth, n_bins, seed, flags=lflags)
+        R.trace_lights(ctx, gs, fr, n_light, depth, n_bins, seed, flags=lflags, guide=guide)
     R.resolve(ctx, gs, fr, spp, n_light)
     ctx.sync_status()
     return gs, fr
@@ -275,6 +275,28 @@ def test_light_parity_rect_light_dispersion(ctx):
     assert st["splatted"] > 0.002
     img = fr["accum_caustic"][..., :3].cpu().numpy() / n
     assert np.mean((img - acc / n) ** 2) <= MSE
+
+
+@pytest.mark.parametrize("which", ["point", "rect"])
+def test_light_parity_guided_emission(ctx, which):
+    """Guided emission (directions in the cone subtending the glass's bounding sphere): records
+    and caustic image vs the oracle given the same float32 sphere."""
+    sc = S.ball_on_plane() if which == "point" else _small_glass(40, 40)
+    guide = S.guide_sphere(sc)
+    n, depth, nb = (1 << 17, 8, 1) if which == "point" else (1 << 16, 12, 8)
+    _, fr = _render(ctx, sc, 0, depth, n_bins=nb, n_light=n, seed=5, guide=guide)
+    g = R.light_records_numpy(fr.light_records)
+    acc, rec = O.OracleScene(sc).trace_lights(n, depth, nbins=nb, seed=5, guide=guide)
+    st = compare_lights(g, rec, max_ambiguous=MAX_AMBIGUOUS_GLASS)
+    assert st["splatted"] > 0.005  # the ball hides most of its own caustic from this camera
+    img = fr["accum_caustic"][..., :3].cpu().numpy() / n
+    assert np.mean((img - acc / n) ** 2) <= MSE
+
+
+def test_guided_emission_rejected_with_direct_splats(ctx):
+    sc = S.ball_on_plane(16, 16)
+    with pytest.raises(R.N.ScError):
+        _render(ctx, sc, 0, 8, n_light=64, lflags=R.N.SC_FLAG_SPLAT_DIRECT, guide=S.guide_sphere(sc), records=False)
 
 
 def test_resolve_ground_truth_parity(ctx):

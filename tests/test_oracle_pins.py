@@ -491,3 +491,44 @@ def test_ground_truth_buffers_on_ball_and_plane():
     # albedo of glass is 1, of the plane its albedo
     np.testing.assert_allclose(g["albedo"][inside], 1.0)
     np.testing.assert_allclose(g["albedo"][outside], 0.5)
+
+
+@pytest.mark.parametrize("which", ["point", "rect"])
+def test_guided_emission_keeps_the_caustic_expectation(which):
+    """Emission aimed into the sphere around the glass (with the cone's solid angle, and the
+    emitter cosine for a rect light, in the throughput) estimates the same L S+ D E splat image as
+    uniform emission, with a much smaller variance: total splatted power per path over 10
+    independent batches agrees within 4 standard errors, and the guided batches spread less."""
+    if which == "point":
+        sc = S.ball_on_plane(width=32, height=32)
+        depth, nb = 8, 1
+    else:
+        sc = S.glass_scene(0, width=32, height=32, n_objects=1, tris_per_object=320)
+        depth, nb = 12, 1
+    guide = S.guide_sphere(sc)
+    orc = O.OracleScene(sc)
+    n = 20000
+
+    def batches(g):
+        v = [orc.trace_lights(n, depth, nbins=nb, seed=100 + b, records=False, guide=g)[0].sum() / n for b in range(10)]
+        return np.mean(v), np.std(v, ddof=1) / np.sqrt(len(v))
+
+    mu, su = batches(None)
+    mg, sg = batches(guide)
+    assert mu > 0 and mg > 0
+    assert abs(mu - mg) < 4.0 * np.hypot(su, sg), (mu, su, mg, sg)
+    assert sg < su
+
+
+def test_guide_sphere_encloses_the_glass():
+    sc = S.glass_scene(1, width=16, height=16, n_objects=3, tris_per_object=320)
+    cx, cy, cz, r = S.guide_sphere(sc)
+    kinds = np.array([m.kind for m in sc.materials])
+    sel = kinds[sc.object_material[sc.tri_object]] == S.MAT_DIELECTRIC
+    v = sc.positions[sc.indices[sel].ravel()].astype(np.float64)
+    assert np.sqrt(((v - [cx, cy, cz]) ** 2).sum(axis=1)).max() <= r
+    assert all(float(np.float32(x)) == x for x in (cx, cy, cz, r))
+    b = S.SceneBuilder()
+    b.add(S.quad((-1, 0, -1), (0, 0, 2), (2, 0, 0)), b.material(S.Material(S.MAT_DIFFUSE)))
+    no_glass = b.build(S.Camera((0, 1, 3), (0, 0, 0), (0, 1, 0), 40.0, 8, 8))
+    assert S.guide_sphere(no_glass)[3] == 0.0
