@@ -344,7 +344,7 @@ def run_denoise(args):
     net1.set_params(net.get_params())
 
     def denoised_frame():
-        T.render(ctx, g0, f, lo, seed=11, guide=guides[0])
+        T.render(ctx, g0, f, lo, seed=11, guide=guides[0], chunked=False)
         D.pack_frame(ctx, f, x1, 0, source="direct")
         net1.forward(x1, y1)
         D.output_rgb(ctx, y1, f["caustic"], out=rgb1)
@@ -353,7 +353,7 @@ def run_denoise(args):
     plain_spec = T.RenderSpec(spp_int, spp_int * ratio)
 
     def plain_frame():
-        T.render(ctx, g0, f, plain_spec, seed=11, guide=guides[0])
+        T.render(ctx, g0, f, plain_spec, seed=11, guide=guides[0], chunked=False)
 
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     for fn in (denoised_frame, plain_frame):

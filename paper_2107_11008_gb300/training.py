@@ -31,18 +31,53 @@ class RenderSpec:
     guided: bool = True  # light paths aimed into the sphere around the glass (scenes.guide_sphere)
 
 
+CHUNK = 256  # samples (and light paths) per pixel accumulated in one float32 pass
+
+
 def render(ctx: R.Context, gs: R.GpuScene, frame: R.Frame, spec: RenderSpec, seed: int, sample_offset: int = 0,
-           path_offset: int = 0, scene_index: int = 0, guide=None):
+           path_offset: int = 0, scene_index: int = 0, guide=None, chunked: bool = True):
     """Camera paths + light paths + resolve into ``frame`` (accumulators cleared first); ``guide``
-    is the scene's guide sphere, used when ``spec.guided``."""
-    frame.zero_accumulators()
-    n_light = int(round(spec.lights_per_pixel * frame.width * frame.height))
+    is the scene's guide sphere, used when ``spec.guided``.  Budgets above CHUNK per pixel run as
+    passes of consecutive sample / path ranges whose resolved estimates are averaged in float64
+    (a bright caustic pixel collecting millions of splats in one float32 sum would lose the small
+    ones), so the result is the same estimator as one pass.  ``chunked=False`` always runs one pass
+    (timing a frame as a user would render it)."""
+    w, h = frame.width, frame.height
+    n_light = int(round(spec.lights_per_pixel * w * h))
+    g = guide if spec.guided else None
+
+    def one(spp, soff, nl, poff):
+        frame.zero_accumulators()
+        if spp > 0:
+            R.trace_camera(ctx, gs, frame, spp, spec.max_depth, spec.n_bins, seed, soff, scene_index)
+        if nl > 0:
+            R.trace_lights(ctx, gs, frame, nl, spec.max_depth, spec.n_bins, seed, poff, scene_index, guide=g)
+        R.resolve(ctx, gs, frame, max(spp, 1), max(nl, 1))
+
+    if not chunked or (spec.spp <= CHUNK and spec.lights_per_pixel <= CHUNK):
+        one(spec.spp, sample_offset, n_light, path_offset)
+        return
+    direct = torch.zeros((h, w, 3), dtype=torch.float64, device=frame["rgb"].device)
+    caustic = torch.zeros_like(direct)
+    done = 0
+    while done < spec.spp:
+        k = min(CHUNK, spec.spp - done)
+        one(k, sample_offset + done, 0, 0)
+        direct += frame["direct"][..., :3].double() * k
+        done += k
+    done, step = 0, CHUNK * w * h
+    while done < n_light:
+        k = min(step, n_light - done)
+        one(0, 0, k, path_offset + done)
+        caustic += frame["caustic"][..., :3].double() * k
+        done += k
     if spec.spp > 0:
-        R.trace_camera(ctx, gs, frame, spec.spp, spec.max_depth, spec.n_bins, seed, sample_offset, scene_index)
+        direct /= spec.spp
     if n_light > 0:
-        R.trace_lights(ctx, gs, frame, n_light, spec.max_depth, spec.n_bins, seed, path_offset, scene_index,
-                       guide=guide if spec.guided else None)
-    R.resolve(ctx, gs, frame, max(spec.spp, 1), max(n_light, 1))
+        caustic /= n_light
+    frame["direct"][..., :3] = direct.float()
+    frame["caustic"][..., :3] = caustic.float()
+    frame["rgb"][..., :3] = (direct + caustic).float()
 
 
 @dataclass
