@@ -264,7 +264,7 @@ def run_denoise(args):
     Both pipelines spend the same ratio of light paths to camera samples (``--den-ratio``, 16),
     light paths aimed into the sphere around the glass (guided emission): the denoised frame is
     4 camera spp + 4 x ratio light paths per pixel, the U-Net removing the camera estimate's noise
-    (trained 6000 steps on 16 random 128^2 crops of 64 pairs: that estimate at 4 spp -> 1024 spp)
+    (trained 12000 steps on 16 random 128^2 crops of 256 pairs: that estimate at 4 -> 1024 spp)
     and the light-traced caustic buffer added back; the plain frame is N spp + N x ratio light
     paths.
     MSEs are against a reference of two independent halves (2048 spp + 8192 light paths / px
@@ -280,7 +280,7 @@ def run_denoise(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    hw, n_train, n_test, ratio = 256, 64, 8, args.den_ratio
+    hw, n_train, n_test, ratio = 256, 256, 8, args.den_ratio
     lo = T.RenderSpec(4, 4 * ratio)
     stream = torch.cuda.current_stream(dev)
     ctx = R.Context(local, stream)
@@ -306,7 +306,7 @@ def run_denoise(args):
     trainer = D.UNet(ctx, 16, 128, 128)  # 128^2 random crops of the 256^2 pairs, 16 per step
     trainer.set_params(D.he_init(0).to(dev))
     t0 = time.perf_counter()
-    T.train(trainer, train, steps=6000, batch=16, crop=128, lr=2e-3, lr_final=5e-5, seed=0)
+    T.train(trainer, train, steps=12000, batch=16, crop=128, lr=1.5e-3, lr_final=5e-5, seed=0)
     torch.cuda.synchronize(dev)
     train_s = time.perf_counter() - t0
     ctx.sync_status()
@@ -397,7 +397,7 @@ def run_denoise(args):
                 "warmup": max(3, args.warmup), "ms_per_step": den_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic (scenes.denoise_scene)",
                 "config": {"workload": "denoise: 256^2 config-1-type scenes; U-Net on the camera estimate trained "
-                                       "6000 steps x 16 crops of 128^2 from 64 pairs (4 -> 1024 spp), guided "
+                                       "12000 steps x 16 crops of 128^2 from 256 pairs (4 -> 1024 spp), guided "
                                        "light-traced caustics added back; 8 held-out scenes; reference 2 x (2048 spp "
                                        "+ 8192 guided light paths/px)",
                            "input": f"{lo.spp} camera spp + {lo.lights_per_pixel} light paths/px",
