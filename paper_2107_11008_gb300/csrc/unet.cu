@@ -694,16 +694,21 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // groups of 8 input channels per A stage: the largest even divisor of cin / 8 for which the
 // resident weights and two stages fit in 227 KB (0: the layer does not fit)
-int conv_stage_groups(int cin, int N) {
+int conv_stage_groups(int cin, int N, uint32_t gstride) {
   const int ng = cin / 8;
   for (int gs = ng; gs >= 2; gs -= 2)
-    if (ng % gs == 0 && conv_smem_bytes(cin, N, gs) <= 227 * 1024) return gs;
+    if (ng % gs == 0 && conv_smem_bytes(cin, N, gs, gstride) <= 227 * 1024) return gs;
   return 0;
 }
 
-bool conv_tma_ok(int cin, int N, int w) {
-  return w % 128 == 0 && cin % 16 == 0 && N % 16 == 0 && N <= 128 && conv_stage_groups(cin, N) > 0 &&
-         tensor_map_encoder() != nullptr;
+bool conv_rows_ok(int w, int h) {
+  if (w % 128 == 0) return true;
+  return w >= 16 && w < 128 && 128 % w == 0 && h % (128 / w) == 0;
+}
+
+bool conv_tma_ok(int cin, int N, int w, int h) {
+  return conv_rows_ok(w, h) && cin % 16 == 0 && N % 16 == 0 && N <= 128 &&
+         conv_stage_groups(cin, N, conv_geo(1, h, w).gstride) > 0 && tensor_map_encoder() != nullptr;
 }
 
 // src: NHWC BF16 slice (stride cs, offset co) with `cin` channels per tap; N output channels;
@@ -712,21 +717,22 @@ template <class EP>
 cudaError_t conv3x3(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h, int w, int n, int N,
                     const bf16 *wdense, const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s) {
   const int M = n * h * w;
-  if (!conv_tma_ok(cin, N, w))
+  if (!conv_tma_ok(cin, N, w, h))
     return gemm(nbr(src, cs, co, h, w, cin, 9, sign, M), dense(wdense, 9 * cin, N), e, M, N, 9 * cin, 1, 9 * cin, st,
                 s);
   CUtensorMap map;
   const cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
   const cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)w * cs * 2, (cuuint64_t)h * w * cs * 2};
-  const cuuint32_t box[4] = {8, (cuuint32_t)kHaloW, (cuuint32_t)kHaloH, 1};
+  const ConvGeo G = conv_geo(n, h, w);
+  const cuuint32_t box[4] = {8, (cuuint32_t)(G.narrow ? w : kHaloW), (cuuint32_t)(G.narrow ? G.th + 2 : kHaloH), 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = tensor_map_encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(src + co), dims,
                                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   auto kern = k_conv_tma<EP>;
-  const int gs = conv_stage_groups(cin, N);
-  const int smem = (int)conv_smem_bytes(cin, N, gs);
+  const int gs = conv_stage_groups(cin, N, G.gstride);
+  const int smem = (int)conv_smem_bytes(cin, N, gs, G.gstride);
   static std::mutex mu;
   static bool attr_set[kMaxDev] = {};
   int dev = 0;
@@ -758,9 +764,9 @@ cudaError_t conv3x3(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h,
   const int by_smem = kSmemPerSM / (smem_launch + kSmemPerBlockReserve);
   int occ = std::min(std::min(by_smem, by_regs), std::min(by_tmem, 2048 / kConvThreads));
   if (occ < 1) occ = 1;
-  const int ntiles = n * h * (w / 128);
+  const int ntiles = G.narrow ? n * (h / G.th) : n * h * (w / 128);
   const int grid = std::min(ntiles, u->num_sms * occ);
-  kern<<<grid, kConvThreads, smem_launch, s>>>(map, wtma, cin, N, gs, n, h, w, sign, e, st);
+  kern<<<grid, kConvThreads, smem_launch, s>>>(map, wtma, cin, N, gs, G, sign, e, st);
   return cudaGetLastError();
 }
 

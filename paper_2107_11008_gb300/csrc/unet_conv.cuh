@@ -12,6 +12,11 @@
 // input has more channels than two A stages can hold next to the weights, a tile's channels are
 // streamed in chunks of `gs` groups of 8, accumulating into the same TMEM columns.
 //
+// Rows narrower than 128 pixels (w = 64, 32, 16): a tile is 128 / w whole rows, and per group of
+// 8 channels three TMA copies bring the (rows + 2) x w neighbourhood shifted by dx = -1, 0, +1
+// (zero-filled outside the image) into three slabs whose rows are exactly w pixels long, so that
+// tap (dy, dx) is again 128 consecutive 16-byte rows: slab dx read from row dy.
+//
 // Warp roles (192 threads): warp 0 = TMA producer, warp 1 = MMA issuer (one thread each), warps
 // 2..5 = epilogue (TMEM -> registers -> epilogue functor).  Two shared-memory A stages and two
 // TMEM accumulators let the loads of tile i+1 and the epilogue of tile i-1 overlap the MMAs of
@@ -31,9 +36,32 @@ __host__ __device__ constexpr uint32_t align_up(uint32_t x, uint32_t a) { return
 __host__ __device__ constexpr uint32_t conv_w_bytes(int cin_p, int N) { return 9u * (uint32_t)cin_p * N * 2u; }
 __host__ __device__ constexpr uint32_t conv_a_bytes(int gs) { return (uint32_t)gs * kSlabBytes; }
 __host__ __device__ constexpr uint32_t conv_acc_cols(int N) { return N <= 32 ? 32u : (N <= 64 ? 64u : 128u); }
-// gs: groups of 8 input channels per A stage
-__host__ __device__ constexpr size_t conv_smem_bytes(int cin_p, int N, int gs) {
-  return align_up(conv_w_bytes(cin_p, N), 1024) + 2 * align_up(conv_a_bytes(gs), 1024) + 128;
+// gs: groups of 8 input channels per A stage, gstride: bytes per group in a stage
+__host__ __device__ constexpr size_t conv_smem_bytes(int cin_p, int N, int gs, uint32_t gstride = kSlabBytes) {
+  return align_up(conv_w_bytes(cin_p, N), 1024) + 2 * align_up((uint32_t)gs * gstride, 1024) + 128;
+}
+
+// Tiling of one launch: wide rows (w a multiple of 128: tiles of 128 pixels of a row, one 3 x 130
+// slab per channel group) or narrow rows (128 / w rows per tile, three dx-shifted slabs).
+struct ConvGeo {
+  int n_img, h, w;
+  int narrow;        // 0 wide, 1 narrow
+  int th;            // rows per tile (narrow)
+  uint32_t slab;     // bytes of one dx slab (narrow)
+  uint32_t gstride;  // bytes of one channel group in a stage
+  uint32_t tx;       // bytes the TMA copies of one channel group deliver
+};
+__host__ __device__ inline ConvGeo conv_geo(int n_img, int h, int w) {
+  ConvGeo g;
+  g.n_img = n_img;
+  g.h = h;
+  g.w = w;
+  g.narrow = w < 128;
+  g.th = g.narrow ? 128 / w : 1;
+  g.slab = g.narrow ? align_up((uint32_t)(g.th + 2) * w * 16u, 128) : 0u;
+  g.gstride = g.narrow ? 3u * g.slab : kSlabBytes;
+  g.tx = g.narrow ? 3u * (uint32_t)(g.th + 2) * w * 16u : kSlabTx;
+  return g;
 }
 
 // Resident weights: wt[tap][kg][n][8] BF16 (kg = group of 8 reduction channels), i.e. for each
@@ -42,22 +70,23 @@ __host__ __device__ constexpr size_t conv_smem_bytes(int cin_p, int N, int gs) {
 template <class EP>
 __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_constant__ CUtensorMap amap,
                                                               const bf16 *__restrict__ wt, int cin_p, int N, int gs,
-                                                              int n_img, int h, int w, int sign, EP E,
-                                                              unsigned *status) {
+                                                              ConvGeo G, int sign, EP E, unsigned *status) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ng = cin_p / 8;
   const int nchunk = ng / gs;
   const uint32_t wbytes = conv_w_bytes(cin_p, N);
-  const uint32_t astride = align_up(conv_a_bytes(gs), 1024);
+  const uint32_t astride = align_up((uint32_t)gs * G.gstride, 1024);
+  const int h = G.h, w = G.w;
   uint8_t *sW = sm;
   uint8_t *sA = sm + align_up(wbytes, 1024);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sA + 2 * astride);
   // bar[0] weights full, [1,2] A full, [3,4] A empty, [5,6] accumulator full, [7,8] accumulator empty
   uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 9);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(slot + 1);
-  const int tiles_x = w / 128;
-  const int ntiles = n_img * h * tiles_x;
+  const int tiles_x = G.narrow ? 1 : w / 128;
+  const int tiles_y = G.narrow ? h / G.th : h;
+  const int ntiles = G.n_img * tiles_y * tiles_x;
   const uint32_t half = conv_acc_cols(N);  // column offset of accumulator 1
   const uint32_t cols = 2 * half;
   if (threadIdx.x == 0) {
@@ -86,7 +115,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
       tc::bulk_load(tc::smem_addr(sW), wt, wbytes, tc::smem_addr(&bar[0]));
       int issued = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
-        const int xt = t % tiles_x, r = t / tiles_x, y = r % h, img = r / h;
+        const int xt = t % tiles_x, r = t / tiles_x, y = (r % tiles_y) * G.th, img = r / tiles_y;
         for (int ch = 0; ch < nchunk; ++ch, ++issued) {
           const int s = issued & 1, u = issued >> 1;
           if (u > 0 && !tc::mbar_wait(tc::smem_addr(&bar[3 + s]), (u - 1) & 1)) {
@@ -95,10 +124,16 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
           }
           if (*abort_flag) break;
           const uint32_t full = tc::smem_addr(&bar[1 + s]);
-          tc::mbar_expect_tx(full, (uint32_t)gs * kSlabTx);
+          tc::mbar_expect_tx(full, (uint32_t)gs * G.tx);
           const uint32_t dst = tc::smem_addr(sA + s * astride);
-          for (int g = 0; g < gs; ++g)
-            tc::tma_load_4d(dst + g * kSlabBytes, &amap, 8 * (ch * gs + g), xt * 128 - 1, y - 1, img, full);
+          for (int g = 0; g < gs; ++g) {
+            if (G.narrow) {
+              for (int dx = 0; dx < 3; ++dx)
+                tc::tma_load_4d(dst + g * G.gstride + dx * G.slab, &amap, 8 * (ch * gs + g), dx - 1, y - 1, img, full);
+            } else {
+              tc::tma_load_4d(dst + g * G.gstride, &amap, 8 * (ch * gs + g), xt * 128 - 1, y - 1, img, full);
+            }
+          }
         }
       }
       // wait (bounded) for the copies still in flight before leaving
@@ -128,10 +163,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
           const uint32_t a0 = tc::smem_addr(sA + s * astride);
           for (int tap = 0; tap < 9; ++tap) {
             const int ty = tap / 3, tx = tap - 3 * ty;
-            const int off = (sign * (ty - 1) + 1) * kHaloW + sign * (tx - 1) + 1;  // slab pixel of output 0
+            const int sy = sign * (ty - 1) + 1, sx = sign * (tx - 1) + 1;  // neighbourhood row / column (0..2)
+            // start of the 128 rows output pixel 0 multiplies at this tap
+            const uint32_t off = G.narrow ? (uint32_t)sx * G.slab + (uint32_t)(sy * w) * 16u
+                                          : (uint32_t)(sy * kHaloW + sx) * 16u;
             for (int ks = 0; ks < gs / 2; ++ks) {
-              const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(2 * ks) * kSlabBytes + (uint32_t)off * 16u,
-                                                kSlabBytes, 128u);
+              const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(2 * ks) * G.gstride + off, G.gstride, 128u);
               const uint64_t bd = tc::smem_desc(w0 + (uint32_t)((tap * ng + ch * gs + 2 * ks) * N * 16),
                                                 (uint32_t)N * 16u, 128u);
               tc::mma_bf16(d, ad, bd, idesc, (ch > 0 || tap > 0 || ks > 0) ? 1u : 0u);
@@ -156,7 +193,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
       }
       tc::fence_after();
       const int xt = t % tiles_x, rr = t / tiles_x;
-      const int row = rr * w + xt * 128 + r;  // rr = img * h + y
+      // rr = img * tiles_y + tile row; the tile starts at pixel (img * h + y0) * w + xt * 128
+      const int row = ((rr / tiles_y) * h + (rr % tiles_y) * G.th) * w + xt * 128 + r;
       for (int n0 = 0; n0 < N; n0 += 16) {
         float v[16];
         tc::tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)s * half + (uint32_t)n0, v);

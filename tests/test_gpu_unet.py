@@ -102,12 +102,14 @@ def test_param_layout_and_bf16_refresh(ctx):
     net.close()
 
 
-# (n, h, w): w = 40 runs every convolution through the gathering GEMM; w = 256 runs levels 0 and 1
-# (rows of 256 and 128 pixels) through the TMA halo-tile kernel
-GEOMS = [(2, 32, 40), (1, 16, 256)]
+# (n, h, w): w = 40 runs every convolution through the gathering GEMM; 1 x 16 x 256 runs levels 0
+# and 1 (rows of 256 and 128 pixels) through the TMA kernel's wide tiles and level 2 (64) through
+# its narrow tiles; 1 x 64 x 128 runs rows of 128, 64, 32 and 16 pixels through the TMA kernel
+GEOMS = [(2, 32, 40), (1, 16, 256), (1, 64, 128)]
+GEOM_IDS = ["gather", "tma", "tma_narrow"]
 
 
-@pytest.mark.parametrize("geom", GEOMS, ids=["gather", "tma"])
+@pytest.mark.parametrize("geom", GEOMS, ids=GEOM_IDS)
 def test_forward_layer_by_layer(ctx, geom):
     N = Net(ctx, *geom, seed=11)
     y = N.net.forward(N.xd)
@@ -174,7 +176,7 @@ def test_ssim_l1_loss_kernel(ctx):
     assert abs(float(loss0.item())) < 1e-5
 
 
-@pytest.mark.parametrize("geom", GEOMS, ids=["gather", "tma"])
+@pytest.mark.parametrize("geom", GEOMS, ids=GEOM_IDS)
 def test_backward_layer_by_layer(ctx, geom):
     N = Net(ctx, *geom, seed=31)
     y, loss = N.net.loss_grad(N.xd, N.td)
