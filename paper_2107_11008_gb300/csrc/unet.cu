@@ -846,10 +846,10 @@ int run_loss(sc_ctx *c, sc_unet *u, const float *pred, const float *target, int 
 }
 
 // raw stages of the TMA weight-gradient kernel that fit (0: it does not fit)
-int wgrad_tma_stages(int cin, int cout, int mtiles) {
+int wgrad_tma_stages(int cin, int cout, int mtiles, uint32_t gstride) {
   if ((uint32_t)mtiles * wg_cstride(cout) > 512u) return 0;
-  if (wg_smem_bytes(cin, cout, 2) <= 227 * 1024) return 2;
-  if (wg_smem_bytes(cin, cout, 1) <= 227 * 1024) return 1;
+  if (wg_smem_bytes(cin, cout, 2, gstride) <= 227 * 1024) return 2;
+  if (wg_smem_bytes(cin, cout, 1, gstride) <= 227 * 1024) return 1;
   return 0;
 }
 
@@ -870,22 +870,26 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
   const char *where = "sc_unet wgrad";
   const Wgrad g = wgrad_shape(ly);
   const int Mpad = g.Mtiles * kTM;
-  const int rst = ly.kind == KIND_CONV && A.mode == 0 && A.ntaps == 9 && A.w % 128 == 0 && B.co == 0 &&
-                          B.cs == ly.cout && tensor_map_encoder() != nullptr
-                      ? wgrad_tma_stages(A.cin, ly.cout, g.Mtiles)
+  const ConvGeo G = conv_geo((int)(K / ((int64_t)A.h * A.w)), A.h, A.w);
+  // the persistent TMA kernel pays a pipeline fill per CTA: worth it with >= 8 tiles per CTA
+  const int64_t tiles = K / 128;
+  const int rst = ly.kind == KIND_CONV && A.mode == 0 && A.ntaps == 9 && conv_rows_ok(A.w, A.h) && B.co == 0 &&
+                          B.cs == ly.cout && tiles >= 8LL * u->num_sms && tensor_map_encoder() != nullptr
+                      ? wgrad_tma_stages(A.cin, ly.cout, g.Mtiles, G.gstride)
                       : 0;
   int splits;
   if (rst > 0) {
-    const int n_img = (int)(K / ((int64_t)A.h * A.w));
-    const int ntiles = n_img * A.h * (A.w / 128);
+    const int n_img = G.n_img;
+    const int ntiles = G.narrow ? n_img * (A.h / G.th) : n_img * A.h * (A.w / 128);
     splits = std::min(ntiles, u->num_sms);
     if ((size_t)splits * Mpad * g.np > u->wpart_floats)
       return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
     CUtensorMap xm, gm;
-    if (!encode_map(&xm, A.src + A.co, A.cin, A.cs, A.w, A.h, n_img, kHaloW, kHaloH) ||
-        !encode_map(&gm, B.src, ly.cout, ly.cout, A.w, A.h, n_img, 128, 1))
+    if (!encode_map(&xm, A.src + A.co, A.cin, A.cs, A.w, A.h, n_img, G.narrow ? A.w : kHaloW,
+                    G.narrow ? G.th + 2 : kHaloH) ||
+        !encode_map(&gm, B.src, ly.cout, ly.cout, A.w, A.h, n_img, G.narrow ? A.w : 128, G.narrow ? G.th : 1))
       return fail(c, SC_ERR_CUDA, "sc_unet wgrad: tensor map encoding failed");
-    const int smem = (int)wg_smem_bytes(A.cin, ly.cout, rst);
+    const int smem = (int)wg_smem_bytes(A.cin, ly.cout, rst, G.gstride);
     static bool attr[kMaxDev] = {};
     static std::mutex mu;
     int dev = 0;
@@ -893,12 +897,14 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
     {
       std::lock_guard<std::mutex> lk(mu);
       if (dev >= 0 && dev < kMaxDev && !attr[dev]) {
-        UCHK(cudaFuncSetAttribute(k_wgrad_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        UCHK(cudaFuncSetAttribute(k_wgrad_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        UCHK(cudaFuncSetAttribute(k_wgrad_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr[dev] = true;
       }
     }
-    k_wgrad_tma<<<splits, kWgThreads, smem, sc::ctx_stream(c)>>>(xm, gm, A.cin, ly.cout, g.Mtiles, rst, n_img, A.h,
-                                                                    A.w, u->wpart, sc::ctx_status(c));
+    auto kern = G.narrow ? k_wgrad_tma<true> : k_wgrad_tma<false>;
+    kern<<<splits, kWgThreads, smem, sc::ctx_stream(c)>>>(xm, gm, A.cin, ly.cout, g.Mtiles, rst, G, u->wpart,
+                                                           sc::ctx_status(c));
     UCHK(cudaGetLastError());
   } else {
     int ks;

@@ -1,5 +1,5 @@
-// unet_wgrad.cuh -- weight gradient of a 3x3 convolution on tcgen05 with TMA tiles, for rows
-// whose width is a multiple of 128 pixels.
+// unet_wgrad.cuh -- weight gradient of a 3x3 convolution on tcgen05 with TMA tiles (tiles of 128
+// pixels: part of a row of 128k pixels, or 128 / w whole narrower rows, as in unet_conv.cuh).
 //
 //   gw[o][tap][c] = sum_p gz[p][o] * x[p + offset(tap)][c],   gb[o] = sum_p gz[p][o]
 //
@@ -28,24 +28,26 @@ constexpr int kWgWarps = 10;                            // producer, MMA, 8 tran
 constexpr int kWgThreads = 32 * kWgWarps;
 constexpr int kWgTrans = kWgWarps - 2;
 
-__host__ __device__ constexpr uint32_t wg_raw_bytes(int cin, int cout) {
-  return align_up((uint32_t)(cin / 8) * kSlabBytes + (uint32_t)(cout / 8) * kGzTileBytes, 1024);
+__host__ __device__ constexpr uint32_t wg_raw_bytes(int cin, int cout, uint32_t gstride = kSlabBytes) {
+  return align_up((uint32_t)(cin / 8) * gstride + (uint32_t)(cout / 8) * kGzTileBytes, 1024);
 }
 __host__ __device__ constexpr uint32_t wg_b_bytes(int cout) { return align_up((uint32_t)(cout / 8) * kTSBO, 1024); }
 __host__ __device__ constexpr uint32_t wg_cstride(int cout) { return cout <= 32 ? 32u : (cout <= 64 ? 64u : 128u); }
-__host__ __device__ constexpr size_t wg_smem_bytes(int cin, int cout, int rstages) {
-  return (size_t)rstages * wg_raw_bytes(cin, cout) + 2 * kTBlockBytes + 2 * wg_b_bytes(cout) + 256;
+__host__ __device__ constexpr size_t wg_smem_bytes(int cin, int cout, int rstages, uint32_t gstride = kSlabBytes) {
+  return (size_t)rstages * wg_raw_bytes(cin, cout, gstride) + 2 * kTBlockBytes + 2 * wg_b_bytes(cout) + 256;
 }
 
+template <bool NARROW>
 __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_constant__ CUtensorMap xmap,
                                                                const __grid_constant__ CUtensorMap gmap, int cin,
-                                                               int cout, int mtiles, int rstages, int n_img, int h,
-                                                               int w, float *part, unsigned *status) {
+                                                               int cout, int mtiles, int rstages, ConvGeo G,
+                                                               float *part, unsigned *status) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ngx = cin / 8, ngz = cout / 8;
   const int rows = 9 * cin;  // data rows; row `rows` is the ones row
-  const uint32_t rawb = wg_raw_bytes(cin, cout), bb = wg_b_bytes(cout);
+  const uint32_t rawb = wg_raw_bytes(cin, cout, G.gstride), bb = wg_b_bytes(cout);
+  const int h = G.h, w = G.w;
   uint8_t *sRaw = sm;
   uint8_t *sA = sm + rstages * rawb;
   uint8_t *sB = sA + 2 * kTBlockBytes;
@@ -53,8 +55,9 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_consta
   // [0,1] raw full, [2,3] raw empty, [4,5] A full, [6,7] A empty, [8,9] B full, [10,11] B empty, [12] done
   uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 13);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(slot + 1);
-  const int tiles_x = w / 128;
-  const int ntiles = n_img * h * tiles_x;
+  const int tiles_x = NARROW ? 1 : w / 128;
+  const int tiles_y = NARROW ? h / G.th : h;
+  const int ntiles = G.n_img * tiles_y * tiles_x;
   const int t0 = (int)((int64_t)blockIdx.x * ntiles / gridDim.x);
   const int t1 = (int)((int64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
   const int mine = t1 - t0;
@@ -93,12 +96,19 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_consta
           break;
         }
         const int t = t0 + i;
-        const int xt = t % tiles_x, r = t / tiles_x, y = r % h, img = r / h;
+        const int xt = t % tiles_x, r = t / tiles_x, y = (r % tiles_y) * G.th, img = r / tiles_y;
         const uint32_t full = tc::smem_addr(&bar[0 + rs]);
-        tc::mbar_expect_tx(full, (uint32_t)ngx * kSlabTx + (uint32_t)ngz * kGzTileBytes);
+        tc::mbar_expect_tx(full, (uint32_t)ngx * G.tx + (uint32_t)ngz * kGzTileBytes);
         const uint32_t dst = tc::smem_addr(sRaw + rs * rawb);
-        for (int g = 0; g < ngx; ++g) tc::tma_load_4d(dst + g * kSlabBytes, &xmap, 8 * g, xt * 128 - 1, y - 1, img, full);
-        const uint32_t gdst = dst + ngx * kSlabBytes;
+        for (int g = 0; g < ngx; ++g) {
+          if (NARROW) {
+            for (int dx = 0; dx < 3; ++dx)
+              tc::tma_load_4d(dst + g * G.gstride + dx * G.slab, &xmap, 8 * g, dx - 1, y - 1, img, full);
+          } else {
+            tc::tma_load_4d(dst + g * G.gstride, &xmap, 8 * g, xt * 128 - 1, y - 1, img, full);
+          }
+        }
+        const uint32_t gdst = dst + ngx * G.gstride;
         for (int g = 0; g < ngz; ++g) tc::tma_load_4d(gdst + g * kGzTileBytes, &gmap, 8 * g, xt * 128, y, img, full);
       }
       for (int k = i - rstages; k < i; ++k)
@@ -147,7 +157,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_consta
         break;
       }
       const uint32_t raw = tc::smem_addr(sRaw + rs * rawb);
-      const uint32_t gz = raw + ngx * kSlabBytes;
+      const uint32_t gz = raw + ngx * G.gstride;
       // B block: rows o (cout), 128 pixels; unit q = (og, quad of pixel groups), one ldmatrix.x4 each
       const int bs = i & 1;
       if (i >= 2 && !tc::mbar_wait(tc::smem_addr(&bar[10 + bs]), ((i >> 1) - 1) & 1)) {
@@ -186,10 +196,11 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_consta
             r0w[e] = 128 * k + 8 * rg;  // first operand row of this core row
             if (r0w[e] < rows) {
               const int tap = r0w[e] / cin, cg = (r0w[e] - tap * cin) >> 3;
-              const int dy = tap / 3, dx = tap - 3 * dy;  // slab row and column offset (0..2)
-              const int pg = quad * 4 + mat;
-              tc::ldsm_x4_trans(raw + cg * kSlabBytes + (uint32_t)(dy * kHaloW + 8 * pg + mrow + dx) * 16u, r[e][0],
-                                r[e][1], r[e][2], r[e][3]);
+              const int dy = tap / 3, dx = tap - 3 * dy;  // neighbourhood row and column offset (0..2)
+              const int p = 8 * (quad * 4 + mat) + mrow;   // tile pixel of this ldmatrix row
+              const uint32_t src = NARROW ? raw + cg * G.gstride + dx * G.slab + (uint32_t)(dy * w + p) * 16u
+                                          : raw + cg * kSlabBytes + (uint32_t)(dy * kHaloW + p + dx) * 16u;
+              tc::ldsm_x4_trans(src, r[e][0], r[e][1], r[e][2], r[e][3]);
             } else {
               // the ones row (bias gradient) heads the first core row after the data; the rest is zero
               const uint32_t v = (r0w[e] == rows && (lane >> 2) == 0) ? 0x3F803F80u : 0u;
