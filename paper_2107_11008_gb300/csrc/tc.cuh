@@ -103,13 +103,13 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 }
 
 // ---- TMA ------------------------------------------------------------------------------------
-// 4-D tiled tensor load (coordinates innermost first) into shared memory, completing on mbar
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *tmap, int c0, int c1, int c2, int c3,
+// 5-D tiled tensor load (coordinates innermost first) into shared memory, completing on mbar
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const void *tmap, int c0, int c1, int c2, int c3, int c4,
                                             uint32_t mbar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(dst),
-      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+      "[%7];" ::"r"(dst),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mbar)
       : "memory");
 }
 // contiguous global -> shared copy (16-byte aligned addresses, size a multiple of 16)

@@ -39,16 +39,26 @@ constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 // small kernels
 // ---------------------------------------------------------------------------------------------
 
-// x [P][11] FP32 -> [P][16] BF16 (channels 11..15 zero)
-__global__ void k_pack_input(const float *x, bf16 *out, int64_t P) {
+// x [P][11] FP32 -> 16 BF16 channels (11..15 zero), row-blocked with rows of w pixels
+__global__ void k_pack_input(const float *x, bf16 *out, int64_t P, int w) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= P) return;
   float v[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = i < kInCh ? x[p * kInCh + i] : 0.0f;
-  uint4 *o = reinterpret_cast<uint4 *>(out + p * kInPad);
-  o[0] = pack8(v);
-  o[1] = pack8(v + 8);
+  const int64_t r = p / w;
+  bf16 *o = out + rb_off(r, (int)(p - r * w), 0, kInPad, w);
+  *reinterpret_cast<uint4 *>(o) = pack8(v);
+  *reinterpret_cast<uint4 *>(o + 8 * w) = pack8(v + 8);
+}
+
+// a channel slice of a row-blocked BF16 tensor -> dense [rows * w][ch] (test inspection)
+__global__ void k_rb_to_dense(const bf16 *src, int cs, int co, int ch, int64_t rows, int w, bf16 *dst) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= rows * w * ch) return;
+  const int c = (int)(i % ch);
+  const int64_t p = i / ch, r = p / w;
+  dst[i] = src[rb_off(r, (int)(p - r * w), co + c, cs, w)];
 }
 
 // 11-channel network input from a frame's buffers
@@ -94,26 +104,29 @@ __global__ void k_output_rgb(const float *y, int64_t P, const float4 *add, float
   rgb[p] = o;
 }
 
-// 2x2 stride-2 max pool of a channel slice: src (h x w, stride cs, offset co) -> dst [P/4][C]
+// 2x2 stride-2 max pool of a channel slice: src (row-blocked, h x w, cs channels, slice at co)
+// -> dst (row-blocked, h/2 x w/2, C channels).  Thread order: pixel fastest, then channel group,
+// then output row, so that a warp reads and writes contiguous runs.
 __global__ void k_pool(const bf16 *src, int cs, int co, int C, int n, int h, int w, bf16 *dst) {
   const int groups = C / 8;
-  const int64_t total = (int64_t)n * (h / 2) * (w / 2) * groups;
+  const int ho = h / 2, wo = w / 2;
+  const int64_t total = (int64_t)n * ho * wo * groups;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= total) return;
-  const int g = (int)(i % groups);
-  const int64_t q = i / groups;
-  const int ho = h / 2, wo = w / 2;
-  const int x = (int)(q % wo), y = (int)((q / wo) % ho), img = (int)(q / ((int64_t)wo * ho));
+  const int x = (int)(i % wo);
+  const int64_t t = i / wo;
+  const int g = (int)(t % groups);
+  const int64_t ro = t / groups;  // img * ho + y
+  const int64_t ri = ro / ho * h + 2 * (ro % ho);
   float best[8];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const int64_t pix = (int64_t)(img * h + 2 * y + (k >> 1)) * w + 2 * x + (k & 1);
     float v[8];
-    unpack8(ldg16(src + pix * cs + co + g * 8), v);
+    unpack8(ldg16(src + rb_off(ri + (k >> 1), 2 * x + (k & 1), co + g * 8, cs, w)), v);
 #pragma unroll
     for (int j = 0; j < 8; ++j) best[j] = k == 0 ? v[j] : fmaxf(best[j], v[j]);
   }
-  *reinterpret_cast<uint4 *>(dst + q * C + g * 8) = pack8(best);
+  *reinterpret_cast<uint4 *>(dst + rb_off(ro, x, g * 8, C, wo)) = pack8(best);
 }
 
 enum { KIND_BIAS = 0, KIND_CONV = 1, KIND_UP = 2, KIND_OUT = 3 };
@@ -621,7 +634,7 @@ BDense dense(const bf16 *W, int ldk, int N) {
   b.N = N;
   return b;
 }
-EBiasAct bias_act(bf16 *out, int cs, int co, const float *bias, int N, int relu) {
+EBiasAct bias_act(bf16 *out, int cs, int co, const float *bias, int N, int relu, int w) {
   EBiasAct e;
   e.out = out;
   e.cs = cs;
@@ -629,10 +642,12 @@ EBiasAct bias_act(bf16 *out, int cs, int co, const float *bias, int N, int relu)
   e.bias = bias;
   e.N = N;
   e.relu = relu;
+  e.w = w;
   return e;
 }
-EGrad egrad(bf16 *out, int ocs, const bf16 *mask, int mcs, int mco, int N) {
+EGrad egrad(bf16 *out, int ocs, const bf16 *mask, int mcs, int mco, int N, int w) {
   EGrad e;
+  e.w = w;
   e.out = out;
   e.ocs = ocs;
   e.oco = 0;
@@ -692,6 +707,26 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+// 5-D tensor map of the channel slice [co, co + channels) of a row-blocked BF16 tensor (cs
+// channels, rows of w pixels, h rows, n images).  blocked: dims (64, w / 8, groups, h, n) -- the
+// innermost 128 bytes are 8 pixels x 8 channels, so a box row of whole 8-pixel blocks is one
+// contiguous run -- with box (64, box_w / 8, 1, box_h, 1); otherwise dims (8, w, groups, h, n)
+// and box (8, box_w, 1, box_h, 1) for boxes that start at any pixel.
+bool encode_rb_map(CUtensorMap *map, const bf16 *src, int co, int channels, int cs, int w, int h, int n, bool blocked,
+                   int box_w, int box_h) {
+  const cuuint64_t e0 = blocked ? 64 : 8;
+  const cuuint64_t row = (cuuint64_t)cs * w * 2;  // bytes of one image row, all channel groups
+  const cuuint64_t dims[5] = {e0, (cuuint64_t)(blocked ? w / 8 : w), (cuuint64_t)(channels / 8), (cuuint64_t)h,
+                              (cuuint64_t)n};
+  const cuuint64_t strides[4] = {e0 * 2, (cuuint64_t)w * 16, row, row * h};
+  const cuuint32_t box[5] = {(cuuint32_t)e0, (cuuint32_t)(blocked ? box_w / 8 : box_w), 1, (cuuint32_t)box_h, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  auto enc = tensor_map_encoder();
+  return enc && enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(src + (int64_t)co * w), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // groups of 8 input channels per A stage: the largest even divisor of cin / 8 for which the
 // resident weights and two stages fit in 227 KB (0: the layer does not fit)
 int conv_stage_groups(int cin, int N, uint32_t gstride) {
@@ -711,8 +746,9 @@ bool conv_tma_ok(int cin, int N, int w, int h) {
          conv_stage_groups(cin, N, conv_geo(1, h, w).gstride) > 0 && tensor_map_encoder() != nullptr;
 }
 
-// src: NHWC BF16 slice (stride cs, offset co) with `cin` channels per tap; N output channels;
-// wdense: [N][9][cin] (gathering GEMM), wtma: [tap][cin/8][N][8] (TMA kernel); sign -1 = data gradient
+// src: row-blocked BF16 slice (cs channels, slice at co) with `cin` channels per tap; N output
+// channels; wdense: [N][9][cin] (gathering GEMM), wtma: [tap][cin/8][N][8] (TMA kernel); sign -1 =
+// data gradient
 template <class EP>
 cudaError_t conv3x3(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h, int w, int n, int N,
                     const bf16 *wdense, const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s) {
@@ -721,15 +757,10 @@ cudaError_t conv3x3(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h,
     return gemm(nbr(src, cs, co, h, w, cin, 9, sign, M), dense(wdense, 9 * cin, N), e, M, N, 9 * cin, 1, 9 * cin, st,
                 s);
   CUtensorMap map;
-  const cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
-  const cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)w * cs * 2, (cuuint64_t)h * w * cs * 2};
   const ConvGeo G = conv_geo(n, h, w);
-  const cuuint32_t box[4] = {8, (cuuint32_t)(G.narrow ? w : kHaloW), (cuuint32_t)(G.narrow ? G.th + 2 : kHaloH), 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = tensor_map_encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(src + co), dims,
-                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  if (!(G.narrow ? encode_rb_map(&map, src, co, cin, cs, w, h, n, false, w, G.th + 2)
+                 : encode_rb_map(&map, src, co, cin, cs, w, h, n, true, kHaloW, kHaloH)))
+    return cudaErrorInvalidValue;
   auto kern = k_conv_tma<EP>;
   const int gs = conv_stage_groups(cin, N, G.gstride);
   const int smem = (int)conv_smem_bytes(cin, N, gs, G.gstride);
@@ -777,7 +808,7 @@ int run_forward(sc_ctx *c, sc_unet *u, const float *x, int n) {
   u->n = n;
   int64_t P[kLevels];
   for (int l = 0; l < kLevels; ++l) P[l] = (int64_t)n * u->hl[l] * u->wl[l];
-  k_pack_input<<<(unsigned)((P[0] + 255) / 256), 256, 0, s>>>(x, u->x0, P[0]);
+  k_pack_input<<<(unsigned)((P[0] + 255) / 256), 256, 0, s>>>(x, u->x0, P[0], u->wl[0]);
   UCHK(cudaGetLastError());
   const float *prm = u->params;
   for (int l = 0; l < kLevels; ++l) {
@@ -786,10 +817,10 @@ int run_forward(sc_ctx *c, sc_unet *u, const float *x, int n) {
     const bf16 *src = l == 0 ? u->x0 : u->pool[l];
     const int scs = l == 0 ? kInPad : kChans[l - 1];
     UCHK(conv3x3(u, src, scs, 0, c1.cin_p, h, w, n, cl, c1.wf, c1.wtf, 1,
-                 bias_act(u->a1[l], cl, 0, prm + c1.b_off, cl, 1), st, s));
+                 bias_act(u->a1[l], cl, 0, prm + c1.b_off, cl, 1, w), st, s));
     const View e = enc_out(u, l);
     UCHK(conv3x3(u, u->a1[l], cl, 0, cl, h, w, n, cl, c2.wf, c2.wtf, 1,
-                 bias_act(e.p, e.cs, e.co, prm + c2.b_off, cl, 1), st, s));
+                 bias_act(e.p, e.cs, e.co, prm + c2.b_off, cl, 1, w), st, s));
     if (l + 1 < kLevels) {
       const int64_t tot = P[l + 1] * (cl / 8);
       k_pool<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(e.p, e.cs, e.co, cl, n, h, w, u->pool[l + 1]);
@@ -811,9 +842,9 @@ int run_forward(sc_ctx *c, sc_unet *u, const float *x, int n) {
     UCHK(gemm(nbr(ui.p, ui.cs, ui.co, u->hl[l + 1], u->wl[l + 1], cn, 1, 1, (int)P[l + 1]), dense(up.wf, cn, 4 * cl),
               eu, (int)P[l + 1], 4 * cl, cn, 1, cn, st, s));
     UCHK(conv3x3(u, u->cat[l], 2 * cl, 0, 2 * cl, h, w, n, cl, c1.wf, c1.wtf, 1,
-                 bias_act(u->d1[l], cl, 0, prm + c1.b_off, cl, 1), st, s));
+                 bias_act(u->d1[l], cl, 0, prm + c1.b_off, cl, 1, w), st, s));
     UCHK(conv3x3(u, u->d1[l], cl, 0, cl, h, w, n, cl, c2.wf, c2.wtf, 1,
-                 bias_act(u->d2[l], cl, 0, prm + c2.b_off, cl, 1), st, s));
+                 bias_act(u->d2[l], cl, 0, prm + c2.b_off, cl, 1, w), st, s));
   }
   const Layer &o = u->L[kOutLayer];
   EOut eo;
@@ -853,16 +884,6 @@ int wgrad_tma_stages(int cin, int cout, int mtiles, uint32_t gstride) {
   return 0;
 }
 
-bool encode_map(CUtensorMap *map, const bf16 *base, int channels, int cs, int w, int h, int n, int box_w, int box_h) {
-  const cuuint64_t dims[4] = {(cuuint64_t)channels, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
-  const cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)w * cs * 2, (cuuint64_t)h * w * cs * 2};
-  const cuuint32_t box[4] = {8, (cuuint32_t)box_w, (cuuint32_t)box_h, 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  return tensor_map_encoder()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(base), dims, strides, box,
-                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 // weight gradient of one layer: A (rows = (tap, c) | c, + ones row), B (rows = output channels),
 // contracted over the pixels, reduced deterministically into the flat gradient.  3x3 layers on
 // rows of 128k pixels take the TMA kernel (x: the layer input, gz: its output gradient).
@@ -885,9 +906,10 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
     if ((size_t)splits * Mpad * g.np > u->wpart_floats)
       return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
     CUtensorMap xm, gm;
-    if (!encode_map(&xm, A.src + A.co, A.cin, A.cs, A.w, A.h, n_img, G.narrow ? A.w : kHaloW,
-                    G.narrow ? G.th + 2 : kHaloH) ||
-        !encode_map(&gm, B.src, ly.cout, ly.cout, A.w, A.h, n_img, G.narrow ? A.w : 128, G.narrow ? G.th : 1))
+    const bool xok = G.narrow ? encode_rb_map(&xm, A.src, A.co, A.cin, A.cs, A.w, A.h, n_img, false, A.w, G.th + 2)
+                              : encode_rb_map(&xm, A.src, A.co, A.cin, A.cs, A.w, A.h, n_img, true, kHaloW, kHaloH);
+    if (!xok ||
+        !encode_rb_map(&gm, B.src, 0, ly.cout, ly.cout, A.w, A.h, n_img, true, G.narrow ? A.w : 128, G.narrow ? G.th : 1))
       return fail(c, SC_ERR_CUDA, "sc_unet wgrad: tensor map encoding failed");
     const int smem = (int)wg_smem_bytes(A.cin, ly.cout, rst, G.gstride);
     static bool attr[kMaxDev] = {};
@@ -943,7 +965,7 @@ int run_backward(sc_ctx *c, sc_unet *u) {
                tpix(u->gy8, kGyCh, 0, u->hl[0], u->wl[0], kGyCh, 1, 0, kOutCh, 0, pad16(kOutCh)), P[0]);
     if (rc) return rc;
     UCHK(gemm(nbr(u->gy8, kGyCh, 0, u->hl[0], u->wl[0], kGyCh, 1, 1, (int)P[0]), dense(o.wd, kGyCh, c0),
-              egrad(u->gd2[0], c0, u->d2[0], c0, 0, c0), (int)P[0], c0, kGyCh, 1, kGyCh, st, s));
+              egrad(u->gd2[0], c0, u->d2[0], c0, 0, c0, u->wl[0]), (int)P[0], c0, kGyCh, 1, kGyCh, st, s));
   }
   // decoder, shallow to deep
   for (int l = 0; l < kLevels - 1; ++l) {
@@ -953,13 +975,13 @@ int run_backward(sc_ctx *c, sc_unet *u) {
     rc = wgrad(c, u, c2, tpix(u->d1[l], cl, 0, h, w, cl, 9, 0, 9 * cl, 1, kTM),
                tpix(u->gd2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
     if (rc) return rc;
-    UCHK(conv3x3(u, u->gd2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, -1, egrad(u->gd1[l], cl, u->d1[l], cl, 0, cl),
+    UCHK(conv3x3(u, u->gd2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, -1, egrad(u->gd1[l], cl, u->d1[l], cl, 0, cl, w),
                  st, s));
     // dec conv 1: input cat = [up, skip], output gradient gd1 -> gup (BF16) | gskip (FP32)
     rc = wgrad(c, u, c1, tpix(u->cat[l], 2 * cl, 0, h, w, 2 * cl, 9, 0, 18 * cl, 1, kTM),
                tpix(u->gd1[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
     if (rc) return rc;
-    EGrad es = egrad(u->gup[l], cl, nullptr, 0, 0, 2 * cl);
+    EGrad es = egrad(u->gup[l], cl, nullptr, 0, 0, 2 * cl, w);
     es.split = cl;
     es.out2 = u->gskip[l];
     es.o2cs = cl;
@@ -980,7 +1002,7 @@ int run_backward(sc_ctx *c, sc_unet *u) {
     // gradient w.r.t. up_in, masked by its ReLU: the next decoder conv 2's output gradient,
     // or at the deepest level the encoder's last conv output gradient
     bf16 *dst = l + 1 == kLevels - 1 ? u->ge2[l + 1] : u->gd2[l + 1];
-    UCHK(gemm(ag, dense(up.wd, 4 * cl, cn), egrad(dst, cn, ui.p, ui.cs, ui.co, cn), (int)P[l + 1], cn, 4 * cl, 1,
+    UCHK(gemm(ag, dense(up.wd, 4 * cl, cn), egrad(dst, cn, ui.p, ui.cs, ui.co, cn, wn), (int)P[l + 1], cn, 4 * cl, 1,
               4 * cl, st, s));
   }
   // encoder, deep to shallow; ge2[l] holds d loss / d (pre-ReLU) encoder conv 2 output
@@ -990,7 +1012,7 @@ int run_backward(sc_ctx *c, sc_unet *u) {
     rc = wgrad(c, u, c2, tpix(u->a1[l], cl, 0, h, w, cl, 9, 0, 9 * cl, 1, kTM),
                tpix(u->ge2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
     if (rc) return rc;
-    UCHK(conv3x3(u, u->ge2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, -1, egrad(u->ge1[l], cl, u->a1[l], cl, 0, cl),
+    UCHK(conv3x3(u, u->ge2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, -1, egrad(u->ge1[l], cl, u->a1[l], cl, 0, cl, w),
                  st, s));
     const bf16 *src = l == 0 ? u->x0 : u->pool[l];
     const int scs = l == 0 ? kInPad : kChans[l - 1];
@@ -1463,8 +1485,15 @@ int sc_unet_copy_buffer(sc_ctx *c, const sc_unet *u, int32_t id, int32_t level, 
   const char *where = "sc_unet_copy_buffer";
   const size_t es = dtype ? 4 : 2;
   const size_t rows = (size_t)u->n * u->hl[level] * u->wl[level];
-  UCHK(cudaMemcpy2DAsync(dst, ch * es, static_cast<const char *>(p) + co * es, cs * es, ch * es, rows,
-                         cudaMemcpyDeviceToDevice, sc::ctx_stream(c)));
+  if (dtype) {  // FP32 tensors are [pixel][cs]
+    UCHK(cudaMemcpy2DAsync(dst, ch * es, static_cast<const char *>(p) + co * es, cs * es, ch * es, rows,
+                           cudaMemcpyDeviceToDevice, sc::ctx_stream(c)));
+  } else {  // BF16 tensors are row-blocked
+    const int64_t total = (int64_t)rows * ch;
+    k_rb_to_dense<<<(unsigned)((total + 255) / 256), 256, 0, sc::ctx_stream(c)>>>(
+        static_cast<const bf16 *>(p), cs, co, ch, (int64_t)u->n * u->hl[level], u->wl[level], static_cast<bf16 *>(dst));
+    UCHK(cudaGetLastError());
+  }
   return SC_OK;
 }
 

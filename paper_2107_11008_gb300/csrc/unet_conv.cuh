@@ -2,11 +2,12 @@
 // tcgen05 with TMA halo tiles, for rows whose width is a multiple of 128 pixels.
 //
 // A tile is 128 consecutive output pixels of one image row.  For each group of 8 input channels
-// the producer warp loads, with one TMA tensor copy, the 3 x 130 pixel neighbourhood of the tile
-// (rows y-1..y+1, columns x0-1..x0+128; outside the image the hardware fills zeros) into a
-// "slab": pixel-major rows of 16 bytes.  In that slab, the 128 input pixels that tap (dy, dx)
-// multiplies are consecutive 16-byte rows, so the MMA operand of every tap is the same slab
-// seen from a shifted start address (8-row core matrices 128 bytes apart, k-groups one slab
+// the producer warp loads, with one TMA tensor copy, the 3 x 144 pixel neighbourhood of the tile
+// (rows y-1..y+1, columns x0-8..x0+135: whole 8-pixel blocks of the row-blocked tensor, so each
+// row of the box is one contiguous 2304-byte run; outside the image the hardware fills zeros)
+// into a "slab": pixel-major rows of 16 bytes.  In that slab, the 128 input pixels that tap
+// (dy, dx) multiplies are consecutive 16-byte rows, so the MMA operand of every tap is the same
+// slab seen from a shifted start address (8-row core matrices 128 bytes apart, k-groups one slab
 // apart): nine taps, one load.  The weights of the whole layer stay resident in shared memory
 // (one bulk copy per CTA, laid out in global memory exactly as the MMA reads them).  When the
 // input has more channels than two A stages can hold next to the weights, a tile's channels are
@@ -27,9 +28,10 @@
 namespace sc {
 namespace unet {
 
-constexpr int kHaloW = 130, kHaloH = 3;
-constexpr uint32_t kSlabBytes = 6272;  // 8 channels x 3 x 130 pixels x 2 bytes = 6240, rounded up to 128
-constexpr uint32_t kSlabTx = 6240;
+// wide-row slab: 3 rows of 144 pixels starting kHaloLead pixels left of the tile (18 blocks of 8)
+constexpr int kHaloW = 144, kHaloH = 3, kHaloLead = 8;
+constexpr uint32_t kSlabBytes = 6912;  // 8 channels x 3 x 144 pixels x 2 bytes (54 x 128)
+constexpr uint32_t kSlabTx = 6912;
 constexpr int kConvThreads = 192;
 
 __host__ __device__ constexpr uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -41,7 +43,7 @@ __host__ __device__ constexpr size_t conv_smem_bytes(int cin_p, int N, int gs, u
   return align_up(conv_w_bytes(cin_p, N), 1024) + 2 * align_up((uint32_t)gs * gstride, 1024) + 128;
 }
 
-// Tiling of one launch: wide rows (w a multiple of 128: tiles of 128 pixels of a row, one 3 x 130
+// Tiling of one launch: wide rows (w a multiple of 128: tiles of 128 pixels of a row, one 3 x 144
 // slab per channel group) or narrow rows (128 / w rows per tile, three dx-shifted slabs).
 struct ConvGeo {
   int n_img, h, w;
@@ -65,8 +67,10 @@ __host__ __device__ inline ConvGeo conv_geo(int n_img, int h, int w) {
 }
 
 // Resident weights: wt[tap][kg][n][8] BF16 (kg = group of 8 reduction channels), i.e. for each
-// (tap, kg) the N rows of 16 bytes the B operand needs.  amap: 4-D tensor map of the input
-// (channels of the slice, width, height, images), box (8, 130, 3, 1).
+// (tap, kg) the N rows of 16 bytes the B operand needs.  amap: 5-D tensor map of the row-blocked
+// input slice: wide rows (64 = 8 pixels x 8 channels, w / 8 pixel blocks, channel groups,
+// height, images), box (64, 18, 1, 3, 1); narrow rows (8 channels, w, channel groups, height,
+// images), box (8, w, 1, th + 2, 1).
 template <class EP>
 __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_constant__ CUtensorMap amap,
                                                               const bf16 *__restrict__ wt, int cin_p, int N, int gs,
@@ -129,9 +133,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
           for (int g = 0; g < gs; ++g) {
             if (G.narrow) {
               for (int dx = 0; dx < 3; ++dx)
-                tc::tma_load_4d(dst + g * G.gstride + dx * G.slab, &amap, 8 * (ch * gs + g), dx - 1, y - 1, img, full);
+                tc::tma_load_5d(dst + g * G.gstride + dx * G.slab, &amap, 0, dx - 1, ch * gs + g, y - 1, img, full);
             } else {
-              tc::tma_load_4d(dst + g * G.gstride, &amap, 8 * (ch * gs + g), xt * 128 - 1, y - 1, img, full);
+              tc::tma_load_5d(dst + g * G.gstride, &amap, 0, xt * (128 / 8) - kHaloLead / 8, ch * gs + g, y - 1, img,
+                              full);
             }
           }
         }
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
             const int sy = sign * (ty - 1) + 1, sx = sign * (tx - 1) + 1;  // neighbourhood row / column (0..2)
             // start of the 128 rows output pixel 0 multiplies at this tap
             const uint32_t off = G.narrow ? (uint32_t)sx * G.slab + (uint32_t)(sy * w) * 16u
-                                          : (uint32_t)(sy * kHaloW + sx) * 16u;
+                                          : (uint32_t)(sy * kHaloW + sx + kHaloLead - 1) * 16u;
             for (int ks = 0; ks < gs / 2; ++ks) {
               const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(2 * ks) * G.gstride + off, G.gstride, 128u);
               const uint64_t bd = tc::smem_desc(w0 + (uint32_t)((tap * ng + ch * gs + 2 * ks) * N * 16),

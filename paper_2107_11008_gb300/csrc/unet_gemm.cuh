@@ -15,6 +15,13 @@
 // Layout: core matrices along K are kLBO = 144 bytes apart (128 bytes of data + 16 of padding),
 // so the 8 threads that each store one 16-byte row of 8 different core matrices hit 8
 // different bank groups; 8-row groups are kSBO = 8 * kLBO apart.
+//
+// BF16 activations and gradients live in HBM "row-blocked": an image row stores its groups of 8
+// channels one after another, and within a group the row's pixels are consecutive 16-byte
+// vectors (element (img, y, x, c) of a tensor of cs channels at
+// ((img * h + y) * cs / 8 + c / 8) * w * 8 + x * 8 + c % 8).  A warp whose lanes own consecutive
+// pixels then reads or writes 512 contiguous bytes per 16-byte access, and a TMA box of a
+// channel group's pixels is one contiguous run instead of one 16-byte piece per pixel.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -42,6 +49,11 @@ __host__ __device__ constexpr size_t gemm_smem_bytes(int np) {
 }
 
 __device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
+// element offset of channel c of pixel x in image row `row` (= img * h + y) of a row-blocked
+// tensor with cs channels and rows of w pixels; c, cs multiples of 8 where 16 bytes are moved
+__host__ __device__ __forceinline__ int64_t rb_off(int64_t row, int x, int c, int cs, int w) {
+  return ((row * (cs >> 3) + (c >> 3)) * w + x) * 8 + (c & 7);
+}
 __device__ __forceinline__ uint4 ldg16(const bf16 *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -170,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm(AL A, BL B, EP E, int M, int 
 // ---------------------------------------------------------------------------------------------
 
 // A operand, one pixel per row (thread t owns row t of the tile): the 3x3 neighbourhood (or the
-// pixel itself, ntaps == 1) of an NHWC BF16 tensor, k = tap * cin + channel.  sign = +1 is the
+// pixel itself, ntaps == 1) of a row-blocked BF16 tensor, k = tap * cin + channel.  sign = +1 is the
 // forward correlation; sign = -1 flips the taps, which is the data gradient of a 3x3 conv.
 struct ANbr {
   const bf16 *src;
@@ -206,7 +218,7 @@ struct ANbr {
           xx += sign * (tap - 3 * ty - 1);
         }
         if (ok && yy >= 0 && yy < h && xx >= 0 && xx < w)
-          v = ldg16(src + ((int64_t)(img * h + yy) * w + xx) * cs + co + c);
+          v = ldg16(src + rb_off((int64_t)img * h + yy, xx, co + c, cs, w));
         c += 8;
         if (c == cin) {
           c = 0;
@@ -248,7 +260,7 @@ struct AUpGrad {
       if (gi * 8 < kc) {
         if (ok) {
           const int yy = 2 * y + (ae >> 1), xx = 2 * x + (ae & 1);
-          v = ldg16(g + ((int64_t)(img * 2 * h + yy) * (2 * w) + xx) * gcs + o);
+          v = ldg16(g + rb_off((int64_t)img * 2 * h + yy, xx, o, gcs, 2 * w));
         }
         o += 8;
         if (o == cu) {
@@ -331,7 +343,7 @@ struct TPix {
             px = 2 * xx + (tap & 1);
           }
           pix[j] = (py >= 0 && py < sh && px >= 0 && px < sw)
-                       ? ldg16(src + ((int64_t)(im * sh + py) * sw + px) * cs + co + c)
+                       ? ldg16(src + rb_off((int64_t)im * sh + py, px, co + c, cs, sw))
                        : zero4();
           if (++xx == w) {
             xx = 0;
@@ -372,12 +384,13 @@ struct TPix {
 // Epilogues (v[16] = columns n0 .. n0+15 of one row)
 // ---------------------------------------------------------------------------------------------
 
-// out = act(v + bias) in BF16 at pixel `row` (act: ReLU or identity); N multiple of 16
+// out = act(v + bias) in BF16 at pixel `row` (act: ReLU or identity) of a row-blocked tensor
+// with rows of w pixels; N multiple of 16
 struct EBiasAct {
   bf16 *out;
   int cs, co;
   const float *bias;
-  int N, relu;
+  int N, relu, w;
   __device__ __forceinline__ void store(int row, int n0, const float *v, int) const {
     if (n0 >= N) return;
     float t[16];
@@ -386,9 +399,10 @@ struct EBiasAct {
       t[i] = v[i] + __ldg(bias + n0 + i);
       if (relu) t[i] = fmaxf(t[i], 0.0f);
     }
-    uint4 *p = reinterpret_cast<uint4 *>(out + (int64_t)row * cs + co + n0);
-    p[0] = pack8(t);
-    p[1] = pack8(t + 8);
+    const int r = row / w;
+    bf16 *p = out + rb_off(r, row - r * w, co + n0, cs, w);
+    *reinterpret_cast<uint4 *>(p) = pack8(t);
+    *reinterpret_cast<uint4 *>(p + 8 * w) = pack8(t + 8);
   }
 };
 
@@ -407,9 +421,9 @@ struct EUpFwd {
     float u[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) u[i] = v[i] + __ldg(bias + o0 + i);
-    uint4 *p = reinterpret_cast<uint4 *>(out + ((int64_t)(img * 2 * h + yy) * (2 * w) + xx) * cs + co + o0);
-    p[0] = pack8(u);
-    p[1] = pack8(u + 8);
+    bf16 *p = out + rb_off((int64_t)img * 2 * h + yy, xx, co + o0, cs, 2 * w);
+    *reinterpret_cast<uint4 *>(p) = pack8(u);
+    *reinterpret_cast<uint4 *>(p + 16 * w) = pack8(u + 8);
   }
 };
 
@@ -423,8 +437,9 @@ struct EOut {
   }
 };
 
-// data gradient: columns n < split -> BF16 out, times (mask > 0) when a mask is given;
-// columns n >= split -> FP32 out2 (unmasked).  N and split multiples of 16.
+// data gradient: columns n < split -> BF16 out (row-blocked, rows of w pixels), times
+// (mask > 0) when a mask is given (row-blocked); columns n >= split -> FP32 out2 ([pixel][o2cs],
+// unmasked).  N and split multiples of 16.
 struct EGrad {
   bf16 *out;
   int ocs, oco;
@@ -432,7 +447,7 @@ struct EGrad {
   int mcs, mco;
   int N, split;
   float *out2;
-  int o2cs;
+  int o2cs, w;
   __device__ __forceinline__ void store(int row, int n0, const float *v, int) const {
     if (n0 >= N) return;
     if (n0 >= split) {
@@ -444,24 +459,26 @@ struct EGrad {
     float t[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) t[i] = v[i];
+    const int r = row / w, x = row - r * w;
     if (mask) {
       float mv[16];
-      const bf16 *mp = mask + (int64_t)row * mcs + mco + n0;
+      const bf16 *mp = mask + rb_off(r, x, mco + n0, mcs, w);
       unpack8(ldg16(mp), mv);
-      unpack8(ldg16(mp + 8), mv + 8);
+      unpack8(ldg16(mp + 8 * w), mv + 8);
 #pragma unroll
       for (int i = 0; i < 16; ++i)
         if (!(mv[i] > 0.0f)) t[i] = 0.0f;
     }
-    uint4 *p = reinterpret_cast<uint4 *>(out + (int64_t)row * ocs + oco + n0);
-    p[0] = pack8(t);
-    p[1] = pack8(t + 8);
+    bf16 *p = out + rb_off(r, x, oco + n0, ocs, w);
+    *reinterpret_cast<uint4 *>(p) = pack8(t);
+    *reinterpret_cast<uint4 *>(p + 8 * w) = pack8(t + 8);
   }
 };
 
 // data gradient w.r.t. the output of a 2x2 max pool (row = pooled pixel, h x w), routed to the
-// first maximum of its window in row-major order, plus the skip gradient of the pool input,
-// times the ReLU mask of the pool input; written in BF16 at the pool input's resolution.
+// first maximum of its window in row-major order, plus the skip gradient of the pool input
+// (FP32, [pixel][scs]), times the ReLU mask of the pool input; written in BF16 at the pool
+// input's resolution.  e and out are row-blocked at that resolution (rows of 2w pixels).
 struct EPoolBack {
   bf16 *out;
   int ocs;
@@ -477,10 +494,11 @@ struct EPoolBack {
     int64_t pix[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      pix[q] = (int64_t)(img * 2 * h + 2 * y + (q >> 1)) * (2 * w) + 2 * x + (q & 1);
-      const bf16 *ep = e + pix[q] * ecs + eco + n0;
+      const int64_t r2 = (int64_t)img * 2 * h + 2 * y + (q >> 1);
+      pix[q] = r2 * (2 * w) + 2 * x + (q & 1);
+      const bf16 *ep = e + rb_off(r2, 2 * x + (q & 1), eco + n0, ecs, 2 * w);
       unpack8(ldg16(ep), ev[q]);
-      unpack8(ldg16(ep + 8), ev[q] + 8);
+      unpack8(ldg16(ep + 16 * w), ev[q] + 8);
     }
     int win[16];
 #pragma unroll
@@ -517,9 +535,9 @@ struct EPoolBack {
         if (win[i] == q) o[i] += v[i];
         if (!(ev[q][i] > 0.0f)) o[i] = 0.0f;
       }
-      uint4 *p = reinterpret_cast<uint4 *>(out + pix[q] * ocs + n0);
-      p[0] = pack8(o);
-      p[1] = pack8(o + 8);
+      bf16 *p = out + rb_off((int64_t)img * 2 * h + 2 * y + (q >> 1), 2 * x + (q & 1), n0, ocs, 2 * w);
+      *reinterpret_cast<uint4 *>(p) = pack8(o);
+      *reinterpret_cast<uint4 *>(p + 16 * w) = pack8(o + 8);
     }
   }
 };

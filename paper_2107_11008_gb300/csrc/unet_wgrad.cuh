@@ -6,8 +6,8 @@
 // as D[(tap, c) | ones][o] = sum over pixels.  The contraction runs over pixels, so both operands
 // must have 8 consecutive pixels in each 16-byte row (K-major), while activations and gradients
 // are stored with 8 consecutive channels per 16 bytes.  Per tile of 128 pixels of one row, the
-// producer warp brings with TMA the 3 x 130 pixel neighbourhood of x (as the forward kernel does)
-// and the 128 pixels of gz; four transposer warps build each 128-row block of the A operand (rows
+// producer warp brings with TMA the 3 x 144 pixel neighbourhood of x (as the forward kernel does)
+// and the 128 pixels of gz; sixteen transposer warps build each 128-row block of the A operand (rows
 // (tap, c): the slab read at the tap's pixel offset) and the B operand (rows o) with
 // ldmatrix.trans (8 x 8 transposes from shared memory) into the padded canonical layout; one
 // thread issues the MMAs.  The accumulators of all row blocks (rows 9 cin + 1, 128 per block,
@@ -24,9 +24,15 @@ constexpr uint32_t kGzTileBytes = 128 * 16;           // one group of 8 gz chann
 constexpr uint32_t kTLBO = 144;                         // padded K-direction core stride
 constexpr uint32_t kTSBO = 16 * kTLBO;                  // 16 pixel groups per 8-row group
 constexpr uint32_t kTBlockBytes = 16 * kTSBO;           // one 128-row operand block
-constexpr int kWgWarps = 10;                            // producer, MMA, 8 transposers
+#ifndef SC_WG_TRANS
+#define SC_WG_TRANS 16
+#endif
+constexpr int kWgTrans = SC_WG_TRANS;                   // transposer warps (a divisor of 16)
+constexpr int kWgWarps = kWgTrans + 2;                  // + producer, MMA
 constexpr int kWgThreads = 32 * kWgWarps;
-constexpr int kWgTrans = kWgWarps - 2;
+constexpr int kWgMaxBlocks = 16;                        // 128-row operand blocks (512 TMEM columns / 32)
+constexpr uint32_t kWgTabBytes = kWgMaxBlocks * 64 * 4;  // per (block, unit): slab offset of the unit
+constexpr uint32_t kWgOnes = 0x80000001u, kWgZero = 0x80000000u;
 
 __host__ __device__ constexpr uint32_t wg_raw_bytes(int cin, int cout, uint32_t gstride = kSlabBytes) {
   return align_up((uint32_t)(cin / 8) * gstride + (uint32_t)(cout / 8) * kGzTileBytes, 1024);
@@ -34,7 +40,8 @@ __host__ __device__ constexpr uint32_t wg_raw_bytes(int cin, int cout, uint32_t 
 __host__ __device__ constexpr uint32_t wg_b_bytes(int cout) { return align_up((uint32_t)(cout / 8) * kTSBO, 1024); }
 __host__ __device__ constexpr uint32_t wg_cstride(int cout) { return cout <= 32 ? 32u : (cout <= 64 ? 64u : 128u); }
 __host__ __device__ constexpr size_t wg_smem_bytes(int cin, int cout, int rstages, uint32_t gstride = kSlabBytes) {
-  return (size_t)rstages * wg_raw_bytes(cin, cout, gstride) + 2 * kTBlockBytes + 2 * wg_b_bytes(cout) + 256;
+  return (size_t)rstages * wg_raw_bytes(cin, cout, gstride) + 2 * kTBlockBytes + 2 * wg_b_bytes(cout) + 256 +
+         kWgTabBytes;
 }
 
 template <bool NARROW>
@@ -55,6 +62,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_consta
   // [0,1] raw full, [2,3] raw empty, [4,5] A full, [6,7] A empty, [8,9] B full, [10,11] B empty, [12] done
   uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 13);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(slot + 1);
+  uint32_t *tab = reinterpret_cast<uint32_t *>(sB + 2 * bb + 256);
   const int tiles_x = NARROW ? 1 : w / 128;
   const int tiles_y = NARROW ? h / G.th : h;
   const int ntiles = G.n_img * tiles_y * tiles_x;
@@ -75,6 +83,21 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_consta
     }
     tc::mbar_init(tc::smem_addr(&bar[12]), 1);
     *abort_flag = 0;
+  }
+  // A-operand unit table (the same for every tile): unit q of 128-row block k covers operand rows
+  // 128k + 8 (q / 4) .. + 7 (tap, channel group) and pixel groups 4 (q % 4) .. + 3; its entry is
+  // the slab byte offset of its first ldmatrix row, or kWgOnes / kWgZero past the data rows
+  for (int i = threadIdx.x; i < mtiles * 64; i += kWgThreads) {
+    const int k = i >> 6, q = i & 63;
+    const int r0 = 128 * k + 8 * (q >> 2), quad = q & 3;
+    uint32_t e = r0 == rows ? kWgOnes : kWgZero;
+    if (r0 < rows) {
+      const int tap = r0 / cin, cg = (r0 - tap * cin) >> 3;
+      const int dy = tap / 3, dx = tap - 3 * dy;
+      e = NARROW ? (uint32_t)cg * G.gstride + (uint32_t)dx * G.slab + (uint32_t)(dy * w + 32 * quad) * 16u
+                 : (uint32_t)cg * kSlabBytes + (uint32_t)(dy * kHaloW + 32 * quad + dx + kHaloLead - 1) * 16u;
+    }
+    tab[i] = e;
   }
   if (warp == 1) {
     tc::tmem_alloc(tc::smem_addr(slot), cols);
@@ -103,13 +126,15 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_consta
         for (int g = 0; g < ngx; ++g) {
           if (NARROW) {
             for (int dx = 0; dx < 3; ++dx)
-              tc::tma_load_4d(dst + g * G.gstride + dx * G.slab, &xmap, 8 * g, dx - 1, y - 1, img, full);
+              tc::tma_load_5d(dst + g * G.gstride + dx * G.slab, &xmap, 0, dx - 1, g, y - 1, img, full);
           } else {
-            tc::tma_load_4d(dst + g * G.gstride, &xmap, 8 * g, xt * 128 - 1, y - 1, img, full);
+            tc::tma_load_5d(dst + g * G.gstride, &xmap, 0, xt * (128 / 8) - kHaloLead / 8, g, y - 1, img, full);
           }
         }
+        // gz: whole 8-pixel blocks (box (64, 128 / 8 or w / 8, 1, 1 or th, 1))
         const uint32_t gdst = dst + ngx * G.gstride;
-        for (int g = 0; g < ngz; ++g) tc::tma_load_4d(gdst + g * kGzTileBytes, &gmap, 8 * g, xt * 128, y, img, full);
+        for (int g = 0; g < ngz; ++g)
+          tc::tma_load_5d(gdst + g * kGzTileBytes, &gmap, 0, xt * (128 / 8), g, y, img, full);
       }
       for (int k = i - rstages; k < i; ++k)
         if (k >= 0) tc::mbar_wait(tc::smem_addr(&bar[0 + k % rstages]), (k / rstages) & 1);
@@ -148,6 +173,8 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_consta
     const int tw = warp - 2;
     const int mrow = lane & 7, mat = lane >> 3;  // ldmatrix: this lane's row and matrix
     const uint32_t wofs = (uint32_t)(lane >> 2) * 16u + (uint32_t)(lane & 3) * 4u;  // store offset in a core
+    const uint32_t lofs = (uint32_t)(8 * mat + mrow) * 16u;  // this lane's ldmatrix row within a unit
+    const uint32_t ones = (lane >> 2) == 0 ? 0x3F803F80u : 0u;  // the ones row: row 0 of its core
     int m = 0;
     bool ok = true;
     for (int i = 0; ok && i < mine; ++i) {
@@ -185,25 +212,18 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_consta
           break;
         }
         uint8_t *adst = sA + ab * kTBlockBytes;
+        const uint32_t *tk = tab + 64 * k;
 #pragma unroll
         for (int b4 = 0; b4 < 64 / kWgTrans; b4 += 4) {
           uint32_t r[4][4];
-          int r0w[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const int q = tw + kWgTrans * (b4 + e);
-            const int rg = q >> 2, quad = q & 3;
-            r0w[e] = 128 * k + 8 * rg;  // first operand row of this core row
-            if (r0w[e] < rows) {
-              const int tap = r0w[e] / cin, cg = (r0w[e] - tap * cin) >> 3;
-              const int dy = tap / 3, dx = tap - 3 * dy;  // neighbourhood row and column offset (0..2)
-              const int p = 8 * (quad * 4 + mat) + mrow;   // tile pixel of this ldmatrix row
-              const uint32_t src = NARROW ? raw + cg * G.gstride + dx * G.slab + (uint32_t)(dy * w + p) * 16u
-                                          : raw + cg * kSlabBytes + (uint32_t)(dy * kHaloW + p + dx) * 16u;
-              tc::ldsm_x4_trans(src, r[e][0], r[e][1], r[e][2], r[e][3]);
+            const uint32_t te = tk[tw + kWgTrans * (b4 + e)];
+            if (!(te >> 31)) {
+              tc::ldsm_x4_trans(raw + te + lofs, r[e][0], r[e][1], r[e][2], r[e][3]);
             } else {
               // the ones row (bias gradient) heads the first core row after the data; the rest is zero
-              const uint32_t v = (r0w[e] == rows && (lane >> 2) == 0) ? 0x3F803F80u : 0u;
+              const uint32_t v = te == kWgOnes ? ones : 0u;
               r[e][0] = r[e][1] = r[e][2] = r[e][3] = v;
             }
           }
