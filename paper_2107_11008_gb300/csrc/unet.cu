@@ -1,7 +1,8 @@
 // unet.cu -- the BF16 U-Net denoiser (include/sc_unet.h): forward, L1 + SSIM loss, backward,
-// Adam, all on the GPU.  Every convolution (forward, data gradient, weight gradient), the
-// transposed convolutions and the 1x1 output layer run through the tcgen05 GEMM of
-// unet_gemm.cuh; pooling, the loss, the weight-gradient reduction and Adam are plain CUDA.
+// Adam, all on the GPU.  Every 3x3 convolution (forward, data gradient, weight gradient) and the
+// transposed convolutions run on the tensor cores (tcgen05: the TMA kernels of unet_conv.cuh and
+// unet_wgrad.cuh, else the gathering GEMM of unet_gemm.cuh); the 1x1 output layer (HBM-bound),
+// pooling, the loss, the weight-gradient reduction and Adam are plain CUDA.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -131,14 +132,133 @@ __global__ void k_pool(const bf16 *src, int cs, int co, int C, int n, int h, int
 
 enum { KIND_BIAS = 0, KIND_CONV = 1, KIND_UP = 2, KIND_OUT = 3 };
 
+// ---- the 1x1 output layer (32 -> 3): HBM-bound, so plain CUDA-core kernels ------------------
+// Weights are the BF16 copy the rest of the network uses, W[o][c] (o < 3, c < 32); products and
+// sums in FP32.  x, the layer input, is row-blocked with 32 channels and rows of w pixels.
+constexpr int kOutBlock = 256;
+
+__device__ __forceinline__ void load_out_w(const bf16 *W, float *sw) {
+  for (int i = threadIdx.x; i < kOutCh * 32; i += blockDim.x) sw[i] = __bfloat162float(W[i]);
+}
+
+// y[p][o] = sum_c W[o][c] x[p][c] + b[o]
+__global__ void __launch_bounds__(kOutBlock) k_out_fwd(const bf16 *x, int w, int64_t P, const bf16 *W,
+                                                        const float *b, float *y) {
+  __shared__ float sw[kOutCh * 32];
+  load_out_w(W, sw);
+  __syncthreads();
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int64_t r = p / w;
+  const int xx = (int)(p - r * w);
+  float a[kOutCh] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    float v[8];
+    unpack8(ldg16(x + rb_off(r, xx, 8 * g, 32, w)), v);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int o = 0; o < kOutCh; ++o) a[o] = fmaf(sw[o * 32 + 8 * g + j], v[j], a[o]);
+  }
+#pragma unroll
+  for (int o = 0; o < kOutCh; ++o) y[p * kOutCh + o] = a[o] + __ldg(b + o);
+}
+
+// gx[p][c] = (sum_o W[o][c] gy[p][o]) * (x[p][c] > 0): the data gradient through the layer and
+// the ReLU of its input.  gy: [p][8] BF16 (3 used); gx row-blocked like x.
+__global__ void __launch_bounds__(kOutBlock) k_out_dgrad(const bf16 *gy8, const bf16 *x, int w, int64_t P,
+                                                          const bf16 *W, bf16 *gx) {
+  __shared__ float sw[kOutCh * 32];
+  load_out_w(W, sw);
+  __syncthreads();
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int64_t r = p / w;
+  const int xx = (int)(p - r * w);
+  float gy[8];
+  unpack8(ldg16(gy8 + p * kGyCh), gy);
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    float m[8], t[8];
+    const int64_t off = rb_off(r, xx, 8 * g, 32, w);
+    unpack8(ldg16(x + off), m);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = 8 * g + j;
+      const float v = fmaf(sw[64 + c], gy[2], fmaf(sw[32 + c], gy[1], sw[c] * gy[0]));
+      t[j] = m[j] > 0.0f ? v : 0.0f;
+    }
+    *reinterpret_cast<uint4 *>(gx + off) = pack8(t);
+  }
+}
+
+// Weight and bias gradient, stage 1: block b sums gy[p][o] x[p][c] and gy[p][o] over its pixel
+// range [b * span, (b + 1) * span) in a fixed order (thread (lane, group) takes every 64th pixel,
+// then a fixed shared-memory tree over the 64 lanes) -> part[b][99] (96 weights o * 32 + c, then
+// 3 biases; thread group g < 3 also sums the bias of output g).
+constexpr int kOutParts = kOutCh * 32 + kOutCh;
+__global__ void __launch_bounds__(kOutBlock) k_out_wgrad(const bf16 *gy8, const bf16 *x, int w, int64_t P,
+                                                          int64_t span, float *part) {
+  __shared__ float red[kOutBlock][kOutCh * 8 + 1];
+  const int pl = threadIdx.x & 63, g = threadIdx.x >> 6;  // pixel lane, channel group
+  float acc[kOutCh * 8 + 1];
+#pragma unroll
+  for (int i = 0; i < kOutCh * 8 + 1; ++i) acc[i] = 0.0f;
+  const int64_t p0 = blockIdx.x * span, p1 = min(P, p0 + span);
+  for (int64_t p = p0 + pl; p < p1; p += 64) {
+    const int64_t r = p / w;
+    const int xx = (int)(p - r * w);
+    float gy[8], v[8];
+    unpack8(ldg16(gy8 + p * kGyCh), gy);
+    unpack8(ldg16(x + rb_off(r, xx, 8 * g, 32, w)), v);
+#pragma unroll
+    for (int o = 0; o < kOutCh; ++o)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[o * 8 + j] = fmaf(gy[o], v[j], acc[o * 8 + j]);
+    acc[kOutCh * 8] += g == 0 ? gy[0] : (g == 1 ? gy[1] : (g == 2 ? gy[2] : 0.0f));
+  }
+#pragma unroll
+  for (int i = 0; i < kOutCh * 8 + 1; ++i) red[threadIdx.x][i] = acc[i];
+  __syncthreads();
+  for (int s = 32; s > 0; s >>= 1) {
+    if (pl < s)
+#pragma unroll
+      for (int i = 0; i < kOutCh * 8 + 1; ++i) red[threadIdx.x][i] += red[threadIdx.x + s][i];
+    __syncthreads();
+  }
+  if (pl == 0) {
+    float *o = part + (int64_t)blockIdx.x * kOutParts;
+#pragma unroll
+    for (int oo = 0; oo < kOutCh; ++oo)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) o[oo * 32 + 8 * g + j] = red[threadIdx.x][oo * 8 + j];
+    if (g < kOutCh) o[kOutCh * 32 + g] = red[threadIdx.x][kOutCh * 8];
+  }
+}
+
+// stage 2: the block partials summed in block order -> gw[o * 32 + c], gb[o]
+__global__ void k_out_wgrad_final(const float *part, int nblk, float *gw, float *gb) {
+  const int i = threadIdx.x;
+  if (i >= kOutParts) return;
+  float t = 0.0f;
+#pragma unroll 8
+  for (int b = 0; b < nblk; ++b) t += part[(int64_t)b * kOutParts + i];
+  if (i < kOutCh * 32) gw[i] = t;
+  else gb[i - kOutCh * 32] = t;
+}
+
+
+
 // Sum of the K-split partial products in a fixed order, scattered to the flat FP32 gradient.
-// part[(s * Mpad + r) * np + n]; rows r: conv (tap * cin_p + c) | ones; up: c | ones;
-// out: c | ones.  Block = 32 consecutive entries (r, n) x 8 split groups; group g sums splits
+// part[(s * Mpad + r) * np + n]; rows r: conv (tap * cin_p + c) | ones; up: c | ones.
+// Block = 32 consecutive entries (r, n) x 8 split groups; group g sums splits
 // g, g + 8, ... (coalesced 128-byte reads), then the 8 group sums are added in order.
 constexpr int kRedEntries = 32, kRedGroups = 8;
 
 __device__ __forceinline__ float split_sum(const float *part, int splits, int Mpad, int np, int r, int n, int g) {
   float s = 0.0f;
+#pragma unroll 8
   for (int k = g; k < splits; k += kRedGroups) s += part[((int64_t)k * Mpad + r) * np + n];
   return s;
 }
@@ -175,7 +295,7 @@ __global__ void __launch_bounds__(kRedEntries *kRedGroups) k_wgrad_reduce(const 
     }
     const int tap = r / cin_p, c = r - tap * cin_p;
     if (c < cin) gw[((int64_t)n * 9 + tap) * cin + c] = t;
-  } else if (kind == KIND_UP) {
+  } else {  // KIND_UP
     if (r == rows) {
       if (n < cout) gb[n] = t;
       return;
@@ -183,10 +303,6 @@ __global__ void __launch_bounds__(kRedEntries *kRedGroups) k_wgrad_reduce(const 
     if (n >= 4 * cout) return;
     const int ae = n / cout, o = n - ae * cout;
     gw[((int64_t)r * 4 + ae) * cout + o] = t;
-  } else {  // KIND_OUT
-    if (n >= cout) return;
-    if (r == rows) gb[n] = t;
-    else gw[(int64_t)n * cin + r] = t;
   }
 }
 
@@ -235,9 +351,7 @@ __global__ void k_adam(const Seg *segs, int nseg, float *p, const float *g, floa
     S.wf[(int64_t)rem * S.cin + c] = b;
     S.wd[i] = b;
   } else if (S.kind == KIND_OUT) {
-    const int o = i / S.cin, c = i - o * S.cin;
     S.wf[i] = b;
-    S.wd[(int64_t)c * kGyCh + o] = b;
   }
 }
 
@@ -566,7 +680,7 @@ int64_t layout_params(Layer *L) {
       ly.wf_elems = ly.wd_elems = (int64_t)ly.cin * 4 * ly.cout;
     } else {
       ly.wf_elems = (int64_t)ly.cout * ly.cin;
-      ly.wd_elems = (int64_t)ly.cin * kGyCh;
+      ly.wd_elems = 0;
     }
   }
   return off;
@@ -727,13 +841,28 @@ bool encode_rb_map(CUtensorMap *map, const bf16 *src, int co, int channels, int 
                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// groups of 8 input channels per A stage: the largest even divisor of cin / 8 for which the
-// resident weights and two stages fit in 227 KB (0: the layer does not fit)
+// groups of 8 input channels per A stage (0: the layer does not fit in 227 KB next to its
+// resident weights).  Among the even divisors of cin / 8 that fit, the one that lets the most CTAs
+// share an SM (shared memory, TMEM, at most 4 by registers) when SC_CONV_MAXOCC, else the largest;
+// ties go to the larger (fewer chunks per tile).  More co-resident CTAs overlap one CTA's loads
+// with another's MMAs and epilogue, which pays more than fewer chunks per tile.
+#ifndef SC_CONV_MAXOCC
+#define SC_CONV_MAXOCC 1
+#endif
 int conv_stage_groups(int cin, int N, uint32_t gstride) {
   const int ng = cin / 8;
-  for (int gs = ng; gs >= 2; gs -= 2)
-    if (ng % gs == 0 && conv_smem_bytes(cin, N, gs, gstride) <= 227 * 1024) return gs;
-  return 0;
+  int best = 0, best_occ = 0;
+  for (int gs = ng; gs >= 2; gs -= 2) {
+    const int bytes = (int)conv_smem_bytes(cin, N, gs, gstride);
+    if (ng % gs != 0 || bytes > 227 * 1024) continue;
+    if (!SC_CONV_MAXOCC) return gs;
+    const int occ = std::min(std::min(228 * 1024 / (bytes + 1024), 512 / (2 * (int)conv_acc_cols(N))), 4);
+    if (occ > best_occ) {
+      best = gs;
+      best_occ = occ;
+    }
+  }
+  return best;
 }
 
 bool conv_rows_ok(int w, int h) {
@@ -847,12 +976,9 @@ int run_forward(sc_ctx *c, sc_unet *u, const float *x, int n) {
                  bias_act(u->d2[l], cl, 0, prm + c2.b_off, cl, 1, w), st, s));
   }
   const Layer &o = u->L[kOutLayer];
-  EOut eo;
-  eo.y = u->y;
-  eo.bias = prm + o.b_off;
-  eo.N = kOutCh;
-  UCHK(gemm(nbr(u->d2[0], kChans[0], 0, u->hl[0], u->wl[0], kChans[0], 1, 1, (int)P[0]), dense(o.wf, kChans[0], kOutCh),
-            eo, (int)P[0], kOutCh, kChans[0], 1, kChans[0], st, s));
+  k_out_fwd<<<(unsigned)((P[0] + kOutBlock - 1) / kOutBlock), kOutBlock, 0, s>>>(u->d2[0], u->wl[0], P[0], o.wf,
+                                                                                 prm + o.b_off, u->y);
+  UCHK(cudaGetLastError());
   return SC_OK;
 }
 
@@ -957,15 +1083,21 @@ int run_backward(sc_ctx *c, sc_unet *u) {
   int64_t P[kLevels];
   for (int l = 0; l < kLevels; ++l) P[l] = (int64_t)n * u->hl[l] * u->wl[l];
   int rc;
-  // output layer
+  // output layer: weight and bias gradient (two fixed-order stages), data gradient into gd2[0]
   {
     const Layer &o = u->L[kOutLayer];
-    const int c0 = kChans[0];
-    rc = wgrad(c, u, o, tpix(u->d2[0], c0, 0, u->hl[0], u->wl[0], c0, 1, 0, c0, 1, kTM),
-               tpix(u->gy8, kGyCh, 0, u->hl[0], u->wl[0], kGyCh, 1, 0, kOutCh, 0, pad16(kOutCh)), P[0]);
-    if (rc) return rc;
-    UCHK(gemm(nbr(u->gy8, kGyCh, 0, u->hl[0], u->wl[0], kGyCh, 1, 1, (int)P[0]), dense(o.wd, kGyCh, c0),
-              egrad(u->gd2[0], c0, u->d2[0], c0, 0, c0, u->wl[0]), (int)P[0], c0, kGyCh, 1, kGyCh, st, s));
+    const int w0 = u->wl[0];
+    const int nblk = 2 * u->num_sms;
+    if ((size_t)nblk * kOutParts > u->wpart_floats)
+      return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
+    const int64_t span = (P[0] + nblk - 1) / nblk;
+    k_out_wgrad<<<nblk, kOutBlock, 0, s>>>(u->gy8, u->d2[0], w0, P[0], span, u->wpart);
+    UCHK(cudaGetLastError());
+    k_out_wgrad_final<<<1, 128, 0, s>>>(u->wpart, nblk, u->grads + o.w_off, u->grads + o.b_off);
+    UCHK(cudaGetLastError());
+    k_out_dgrad<<<(unsigned)((P[0] + kOutBlock - 1) / kOutBlock), kOutBlock, 0, s>>>(u->gy8, u->d2[0], w0, P[0],
+                                                                                   o.wf, u->gd2[0]);
+    UCHK(cudaGetLastError());
   }
   // decoder, shallow to deep
   for (int l = 0; l < kLevels - 1; ++l) {

@@ -427,16 +427,6 @@ struct EUpFwd {
   }
 };
 
-// 1x1 output conv: y[row][n] = v[n] + bias[n] (FP32, n < N)
-struct EOut {
-  float *y;
-  const float *bias;
-  int N;
-  __device__ __forceinline__ void store(int row, int n0, const float *v, int) const {
-    for (int i = 0; i < 16 && n0 + i < N; ++i) y[(int64_t)row * N + n0 + i] = v[i] + __ldg(bias + n0 + i);
-  }
-};
-
 // data gradient: columns n < split -> BF16 out (row-blocked, rows of w pixels), times
 // (mask > 0) when a mask is given (row-blocked); columns n >= split -> FP32 out2 ([pixel][o2cs],
 // unmasked).  N and split multiples of 16.
