@@ -206,9 +206,9 @@ __global__ void __launch_bounds__(kOutBlock) k_out_wgrad(const bf16 *gy8, const 
 #pragma unroll
   for (int i = 0; i < kOutCh * 8 + 1; ++i) acc[i] = 0.0f;
   const int64_t p0 = blockIdx.x * span, p1 = min(P, p0 + span);
+  int64_t r = (p0 + pl) / w;
+  int xx = (int)(p0 + pl - r * w);
   for (int64_t p = p0 + pl; p < p1; p += 64) {
-    const int64_t r = p / w;
-    const int xx = (int)(p - r * w);
     float gy[8], v[8];
     unpack8(ldg16(gy8 + p * kGyCh), gy);
     unpack8(ldg16(x + rb_off(r, xx, 8 * g, 32, w)), v);
@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(kOutBlock) k_out_wgrad(const bf16 *gy8, const 
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[o * 8 + j] = fmaf(gy[o], v[j], acc[o * 8 + j]);
     acc[kOutCh * 8] += g == 0 ? gy[0] : (g == 1 ? gy[1] : (g == 2 ? gy[2] : 0.0f));
+    for (xx += 64; xx >= w; xx -= w) ++r;  // next pixel of this lane: p + 64
   }
 #pragma unroll
   for (int i = 0; i < kOutCh * 8 + 1; ++i) red[threadIdx.x][i] = acc[i];
@@ -237,15 +238,23 @@ __global__ void __launch_bounds__(kOutBlock) k_out_wgrad(const bf16 *gy8, const 
   }
 }
 
-// stage 2: the block partials summed in block order -> gw[o * 32 + c], gb[o]
-__global__ void k_out_wgrad_final(const float *part, int nblk, float *gw, float *gb) {
-  const int i = threadIdx.x;
-  if (i >= kOutParts) return;
-  float t = 0.0f;
-#pragma unroll 8
-  for (int b = 0; b < nblk; ++b) t += part[(int64_t)b * kOutParts + i];
-  if (i < kOutCh * 32) gw[i] = t;
-  else gb[i - kOutCh * 32] = t;
+// stage 2: block i of kOutParts sums entry i of the block partials in a fixed order (thread t
+// takes partials t, t + 128, ..., then a fixed shared-memory tree) -> gw[o * 32 + c], gb[o]
+__global__ void __launch_bounds__(128) k_out_wgrad_final(const float *part, int nblk, float *gw, float *gb) {
+  __shared__ float red[128];
+  const int i = blockIdx.x, t = threadIdx.x;
+  float v = 0.0f;
+  for (int b = t; b < nblk; b += 128) v += part[(int64_t)b * kOutParts + i];
+  red[t] = v;
+  __syncthreads();
+  for (int s = 64; s > 0; s >>= 1) {
+    if (t < s) red[t] += red[t + s];
+    __syncthreads();
+  }
+  if (t == 0) {
+    if (i < kOutCh * 32) gw[i] = red[0];
+    else gb[i - kOutCh * 32] = red[0];
+  }
 }
 
 
@@ -1002,6 +1011,9 @@ int run_loss(sc_ctx *c, sc_unet *u, const float *pred, const float *target, int 
   return SC_OK;
 }
 
+#ifndef SC_WG_MIN_TILES
+#define SC_WG_MIN_TILES 2
+#endif
 // raw stages of the TMA weight-gradient kernel that fit (0: it does not fit)
 int wgrad_tma_stages(int cin, int cout, int mtiles, uint32_t gstride) {
   if ((uint32_t)mtiles * wg_cstride(cout) > 512u) return 0;
@@ -1018,10 +1030,12 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
   const Wgrad g = wgrad_shape(ly);
   const int Mpad = g.Mtiles * kTM;
   const ConvGeo G = conv_geo((int)(K / ((int64_t)A.h * A.w)), A.h, A.w);
-  // the persistent TMA kernel pays a pipeline fill per CTA: worth it with >= 8 tiles per CTA
+  // the persistent TMA kernel pays a pipeline fill per CTA: worth it with >= SC_WG_MIN_TILES
+  // tiles per CTA
   const int64_t tiles = K / 128;
   const int rst = ly.kind == KIND_CONV && A.mode == 0 && A.ntaps == 9 && conv_rows_ok(A.w, A.h) && B.co == 0 &&
-                          B.cs == ly.cout && tiles >= 8LL * u->num_sms && tensor_map_encoder() != nullptr
+                          B.cs == ly.cout && tiles >= (int64_t)SC_WG_MIN_TILES * u->num_sms &&
+                          tensor_map_encoder() != nullptr
                       ? wgrad_tma_stages(A.cin, ly.cout, g.Mtiles, G.gstride)
                       : 0;
   int splits;
@@ -1093,7 +1107,7 @@ int run_backward(sc_ctx *c, sc_unet *u) {
     const int64_t span = (P[0] + nblk - 1) / nblk;
     k_out_wgrad<<<nblk, kOutBlock, 0, s>>>(u->gy8, u->d2[0], w0, P[0], span, u->wpart);
     UCHK(cudaGetLastError());
-    k_out_wgrad_final<<<1, 128, 0, s>>>(u->wpart, nblk, u->grads + o.w_off, u->grads + o.b_off);
+    k_out_wgrad_final<<<kOutParts, 128, 0, s>>>(u->wpart, nblk, u->grads + o.w_off, u->grads + o.b_off);
     UCHK(cudaGetLastError());
     k_out_dgrad<<<(unsigned)((P[0] + kOutBlock - 1) / kOutBlock), kOutBlock, 0, s>>>(u->gy8, u->d2[0], w0, P[0],
                                                                                    o.wf, u->gd2[0]);
