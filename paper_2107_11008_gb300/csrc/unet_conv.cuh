@@ -152,7 +152,22 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
       const uint32_t idesc = tc::idesc_bf16_f32(kTM, N);
       bool ok = tc::mbar_wait(tc::smem_addr(&bar[0]), 0);
       int i = 0, staged = 0;
-      const uint32_t w0 = tc::smem_addr(sW);
+      // Descriptors are built once and advanced by adding byte offsets / 16 to their start
+      // field (every start is a multiple of 16 below 2^18, so the 14-bit field never carries):
+      // A: stage base + the tap's shift in the slab + 2 groups per K step of 16;
+      // B: weights of (tap, channel group) at (tap * ng + group) * N rows of 16 bytes.
+      const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(sA), G.gstride, 128u);
+      const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(sW), (uint32_t)N * 16u, 128u);
+      uint32_t toff[9];
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int ty = tap / 3, tx = tap - 3 * ty;
+        const int sy = sign * (ty - 1) + 1, sx = sign * (tx - 1) + 1;  // neighbourhood row / column (0..2)
+        // start of the 128 rows output pixel 0 multiplies at this tap
+        toff[tap] = (G.narrow ? (uint32_t)sx * G.slab + (uint32_t)(sy * w) * 16u
+                              : (uint32_t)(sy * kHaloW + sx + kHaloLead - 1) * 16u) >> 4;
+      }
+      const uint32_t kstep = (2u * G.gstride) >> 4, sstep = astride >> 4;
       for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
         const int a = i & 1, ua = i >> 1;  // accumulator and its use count
         if (ua > 0 && !tc::mbar_wait(tc::smem_addr(&bar[7 + a]), (ua - 1) & 1)) ok = false;
@@ -165,19 +180,15 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
             break;
           }
           tc::fence_after();
-          const uint32_t a0 = tc::smem_addr(sA + s * astride);
+          const uint64_t as = adesc0 + (uint64_t)((uint32_t)s * sstep);
+          const uint64_t bs = bdesc0 + (uint64_t)((uint32_t)(ch * gs) * (uint32_t)N);
+#pragma unroll
           for (int tap = 0; tap < 9; ++tap) {
-            const int ty = tap / 3, tx = tap - 3 * ty;
-            const int sy = sign * (ty - 1) + 1, sx = sign * (tx - 1) + 1;  // neighbourhood row / column (0..2)
-            // start of the 128 rows output pixel 0 multiplies at this tap
-            const uint32_t off = G.narrow ? (uint32_t)sx * G.slab + (uint32_t)(sy * w) * 16u
-                                          : (uint32_t)(sy * kHaloW + sx + kHaloLead - 1) * 16u;
-            for (int ks = 0; ks < gs / 2; ++ks) {
-              const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(2 * ks) * G.gstride + off, G.gstride, 128u);
-              const uint64_t bd = tc::smem_desc(w0 + (uint32_t)((tap * ng + ch * gs + 2 * ks) * N * 16),
-                                                (uint32_t)N * 16u, 128u);
-              tc::mma_bf16(d, ad, bd, idesc, (ch > 0 || tap > 0 || ks > 0) ? 1u : 0u);
-            }
+            const uint64_t at = as + toff[tap];
+            const uint64_t bt = bs + (uint64_t)((uint32_t)(tap * ng) * (uint32_t)N);
+            for (int ks = 0; ks < gs / 2; ++ks)
+              tc::mma_bf16(d, at + (uint64_t)(ks * kstep), bt + (uint64_t)(2u * ks * (uint32_t)N), idesc,
+                           (ch > 0 || tap > 0 || ks > 0) ? 1u : 0u);
           }
           tc::mma_commit(tc::smem_addr(&bar[3 + s]));  // A stage free
         }

@@ -143,12 +143,16 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_consta
     if (lane == 0) {
       // ---- MMA issuer ---------------------------------------------------------------------------
       const uint32_t idesc = tc::idesc_bf16_f32(kTM, cout);
+      // descriptors advanced by start-field adds (byte offsets / 16; no carry below 2^18)
+      const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(sA), kTLBO, kTSBO);
+      const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(sB), kTLBO, kTSBO);
+      const uint32_t kstep = (2u * kTLBO) >> 4;
       bool ok = true;
       int m = 0;  // operand blocks consumed
       for (int i = 0; ok && i < mine; ++i) {
         const int bs = i & 1;
         if (!tc::mbar_wait(tc::smem_addr(&bar[8 + bs]), (i >> 1) & 1)) ok = false;
-        const uint32_t b0 = tc::smem_addr(sB + bs * bb);
+        const uint64_t bd = bdesc0 + (uint64_t)(((uint32_t)bs * bb) >> 4);
         for (int k = 0; ok && k < mtiles; ++k, ++m) {
           const int ab = m & 1;
           if (!tc::mbar_wait(tc::smem_addr(&bar[4 + ab]), (m >> 1) & 1) || *abort_flag) {
@@ -156,10 +160,10 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_consta
             break;
           }
           tc::fence_after();
-          const uint32_t a0 = tc::smem_addr(sA + ab * kTBlockBytes);
+          const uint64_t ad = adesc0 + (uint64_t)(((uint32_t)ab * kTBlockBytes) >> 4);
+#pragma unroll
           for (int ks = 0; ks < 8; ++ks)
-            tc::mma_bf16(taddr + (uint32_t)k * cstride, tc::smem_desc(a0 + (uint32_t)ks * 2u * kTLBO, kTLBO, kTSBO),
-                         tc::smem_desc(b0 + (uint32_t)ks * 2u * kTLBO, kTLBO, kTSBO), idesc,
+            tc::mma_bf16(taddr + (uint32_t)k * cstride, ad + (uint64_t)(ks * kstep), bd + (uint64_t)(ks * kstep), idesc,
                          (i > 0 || ks > 0) ? 1u : 0u);
           tc::mma_commit(tc::smem_addr(&bar[6 + ab]));  // A block free
         }
