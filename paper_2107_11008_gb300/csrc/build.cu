@@ -349,46 +349,68 @@ __global__ void k_depth(BuildBuffers b) {
   atomicMax(b.depth, d);
 }
 
-// Collapse the binary LBVH into 4-wide nodes: every binary node at even depth becomes a 4-wide
-// node whose children are its children, an internal child being replaced by that child's two
-// children (so a 4-wide node's internal children are again at even depth).  The 4-wide node is
-// stored at the binary node's index; nodes at odd depth leave their slot unused.
+// Collapse the binary LBVH into 4-wide nodes, one per binary internal node (stored at its
+// index).  SC_COLLAPSE_GREEDY: starting from the node's two children, the internal child with the
+// largest surface area is replaced by its two children until there are four (or only leaves):
+// wide nodes then split space where the binary tree's big boxes are, wherever that is in depth.
+// Otherwise the children of the node's children (every binary node at even depth becomes a wide
+// node).  A record depends on its binary subtree alone, so all are built at once; traversal from
+// the root reaches only the records its references name.
+#ifndef SC_COLLAPSE_GREEDY
+#define SC_COLLAPSE_GREEDY 1
+#endif
 __global__ void k_collapse4(BuildBuffers b) {
   const int n = b.n_tris;
   const int n_int = n > 1 ? n - 1 : 1;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_int) return;
-  int depth = 0;
-  for (int node = i; node != 0 && depth <= 4 * 64;) {
-    node = b.parents[node] >> 1;
-    ++depth;
-  }
-  if (depth & 1) return;
   float lo[3][4], hi[3][4];
   int ref[4];
-  int cnt = 0;
-  auto take = [&](int m, int slot) {  // child `slot` of binary node m
+  // entry k <- child `slot` of binary node m
+  auto put = [&](int m, int slot, int k) {
     const float4 *nd = b.nodes + 4 * m;
     const float4 xy = nd[slot], z = nd[2], r = nd[3];
-    lo[0][cnt] = xy.x;
-    hi[0][cnt] = xy.y;
-    lo[1][cnt] = xy.z;
-    hi[1][cnt] = xy.w;
-    lo[2][cnt] = slot ? z.z : z.x;
-    hi[2][cnt] = slot ? z.w : z.y;
-    ref[cnt] = __float_as_int(slot ? r.y : r.x);
-    ++cnt;
+    lo[0][k] = xy.x;
+    hi[0][k] = xy.y;
+    lo[1][k] = xy.z;
+    hi[1][k] = xy.w;
+    lo[2][k] = slot ? z.z : z.x;
+    hi[2][k] = slot ? z.w : z.y;
+    ref[k] = __float_as_int(slot ? r.y : r.x);
   };
+  int cnt = 0;
+#if SC_COLLAPSE_GREEDY
+  put(i, 0, cnt++);
+  put(i, 1, cnt++);
+  while (cnt < 4) {
+    int best = -1;
+    float best_area = -1.0f;
+    for (int k = 0; k < cnt; ++k) {
+      if (ref[k] < 0) continue;
+      const float dx = hi[0][k] - lo[0][k], dy = hi[1][k] - lo[1][k], dz = hi[2][k] - lo[2][k];
+      const float area = dx * dy + dy * dz + dz * dx;
+      if (area > best_area) {
+        best_area = area;
+        best = k;
+      }
+    }
+    if (best < 0) break;
+    const int m = ref[best];
+    put(m, 1, cnt++);
+    put(m, 0, best);
+  }
+#else
   const float4 r = b.nodes[4 * i + 3];
   for (int slot = 0; slot < 2; ++slot) {
     const int c = __float_as_int(slot ? r.y : r.x);
     if (c < 0) {
-      take(i, slot);
+      put(i, slot, cnt++);
     } else {
-      take(c, 0);
-      take(c, 1);
+      put(c, 0, cnt++);
+      put(c, 1, cnt++);
     }
   }
+#endif
   for (int k = cnt; k < 4; ++k) {
     lo[0][k] = lo[1][k] = lo[2][k] = 0.0f;
     hi[0][k] = hi[1][k] = hi[2][k] = 0.0f;
