@@ -41,6 +41,12 @@ BYTES_PER_TRI = 48
 # our kernels per step: LBVH build (bounds init, gather, morton, 8 x (hist, scan, scatter),
 # reorder, karras, refit, depth, 4-wide collapse) + camera + lights + resolve
 LAUNCHES_PER_STEP = 31 + 3
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size camera launch, from
+# one ncu capture of this kernel version:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
+#       -k regex:k_trace_camera -s 4 -c 1 python bench.py --steps 1 --warmup 3 --no-cpu-baseline
+# (the scene stays in L2, so DRAM sees little more than the accumulators and first touches)
+CAMERA_DRAM_BYTES = 24.2e6
 
 
 def parse():
@@ -131,6 +137,12 @@ UNET_CHANS = (32, 48, 64, 128)
 # 8 convs x (wgrad+reduce+dgrad) minus the first layer's dgrad (23); Adam (1)
 UNET_TRAIN_LAUNCHES = 22 + 3 + 3 + 27 + 23 + 1
 UNET_FWD_LAUNCHES = 22
+# DRAM bytes of one training step (all its kernels, dram__bytes_read.sum + dram__bytes_write.sum
+# summed over the step's launches), from one ncu capture of these kernel versions:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
+#       -k regex:"k_(gemm|conv_tma|wgrad_tma|ssim|pool|adam|wgrad_reduce|loss_final|pack_input|out_)" -c 80 \
+#       python bench.py --workload unet_train --steps 1 --warmup 3 --no-cpu-baseline
+UNET_STEP_DRAM_BYTES = 3.62e9
 
 
 def unet_macs(h, w, in_ch=11, out_ch=3):
@@ -250,7 +262,8 @@ def run_unet_train(args):
                 "forward_ms": fwd_ms, "forward_images_s": world * n / (fwd_ms * 1e-3),
                 "roofline": {"kernel": "all U-Net GEMMs of the step (tcgen05 BF16, FP32 accumulate)", "bound": "tensor",
                              "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                             "traffic": None, "flops_per_step": flops,
+                             "traffic": UNET_STEP_DRAM_BYTES, "traffic_unit": "bytes per step (ncu)",
+                             "flops_per_step": flops,
                              "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"},
                 "e2e": {"value": world * n / e2e_s, "unit": "images/s",
                         "h2d_bytes_per_step": (xh.numel() + th.numel()) * 4, "d2h_bytes_per_step": 4},
@@ -696,7 +709,8 @@ def main():
                           "camera_grays_s": cam_counts[0] / cam_s / 1e9,
                           "camera_l2_side_gbs": cam_bytes / cam_s / 1e9},
             "roofline": {"kernel": "k_trace_camera", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": CAMERA_DRAM_BYTES,
+                         "traffic_unit": "bytes per launch (ncu)",
                          "peak_source": f"FP32: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (MEASURED_PEAKS sm_max)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,
