@@ -320,6 +320,7 @@ struct Seg {
   int32_t count, kind, cout, cin, cin_p, first_block;
   bf16 *wf, *wd;    // B layouts of the gathering GEMM (forward, data gradient)
   bf16 *wtf, *wtd;  // B layouts of the TMA convolution: [tap][k-group][n][8]
+  bf16 *wtf2, *wtd2;  // the same split in two halves of n, [half][tap][k-group][n/2][8] (or null)
 };
 
 // One bias-corrected Adam step over every parameter (update != 0), then the BF16 copies:
@@ -354,6 +355,14 @@ __global__ void k_adam(const Seg *segs, int nseg, float *p, const float *g, floa
     if (S.wd) {
       S.wd[((int64_t)c * 9 + tap) * S.cout + o] = b;
       S.wtd[(((int64_t)tap * (S.cout / 8) + o / 8) * S.cin + c) * 8 + (o & 7)] = b;
+    }
+    if (S.wtf2) {
+      const int hn = S.cout / 2, hf = o / hn, oo = o - hf * hn;
+      S.wtf2[((((int64_t)hf * 9 + tap) * (S.cin_p / 8) + c / 8) * hn + oo) * 8 + (c & 7)] = b;
+    }
+    if (S.wtd2) {
+      const int hc = S.cin / 2, hf = c / hc, cc = c - hf * hc;
+      S.wtd2[((((int64_t)hf * 9 + tap) * (S.cout / 8) + o / 8) * hc + cc) * 8 + (o & 7)] = b;
     }
   } else if (S.kind == KIND_UP) {
     const int c = i / (4 * S.cout), rem = i - c * 4 * S.cout;
@@ -586,6 +595,7 @@ struct Layer {
   int kind = 0, cout = 0, cin = 0, cin_p = 0;
   int64_t w_off = 0, b_off = 0, w_count = 0;
   bf16 *wf = nullptr, *wd = nullptr, *wtf = nullptr, *wtd = nullptr;
+  bf16 *wtf2 = nullptr, *wtd2 = nullptr;  // n-split TMA layouts, for layers whose weights do not fit whole
   int64_t wf_elems = 0, wd_elems = 0;
 };
 
@@ -593,6 +603,8 @@ int enc_layer(int l, int j) { return 2 * l + j; }
 int up_layer(int l) { return 8 + (2 - l) * 3; }
 int dec_layer(int l, int j) { return up_layer(l) + 1 + j; }
 constexpr int kOutLayer = 17, kNumLayers = 18;
+// 3x3 layers whose TMA weight image is larger than this also get an n-split copy
+constexpr uint32_t kConvSplitBytes = 200u * 1024u;
 
 struct Wgrad {
   int rows = 0, Mtiles = 0, np = 0;
@@ -884,16 +896,66 @@ bool conv_tma_ok(int cin, int N, int w, int h) {
          conv_stage_groups(cin, N, conv_geo(1, h, w).gstride) > 0 && tensor_map_encoder() != nullptr;
 }
 
+// Output columns [off, off + n) of a convolution's epilogue (the n-split TMA path).
+template <class EP>
+struct ColSplit {
+  static constexpr bool ok = false;
+  static EP shift(const EP &e, int, int) { return e; }
+};
+template <>
+struct ColSplit<EBiasAct> {
+  static constexpr bool ok = true;
+  static EBiasAct shift(EBiasAct e, int off, int n) {
+    e.co += off;
+    e.bias += off;
+    e.N = n;
+    return e;
+  }
+};
+template <>
+struct ColSplit<EGrad> {  // BF16 columns only (split == N)
+  static constexpr bool ok = true;
+  static EGrad shift(EGrad e, int off, int n) {
+    e.oco += off;
+    e.mco += off;
+    e.N = n;
+    e.split = n;
+    return e;
+  }
+};
+bool col_splittable(const EBiasAct &, int) { return true; }
+bool col_splittable(const EGrad &e, int N) { return e.split == N && !e.out2; }
+bool col_splittable(const EPoolBack &, int) { return false; }
+
+template <class EP>
+cudaError_t conv3x3_tma(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h, int w, int n, int N,
+                        const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s);
+
 // src: row-blocked BF16 slice (cs channels, slice at co) with `cin` channels per tap; N output
-// channels; wdense: [N][9][cin] (gathering GEMM), wtma: [tap][cin/8][N][8] (TMA kernel); sign -1 =
-// data gradient
+// channels; wdense: [N][9][cin] (gathering GEMM), wtma: [tap][cin/8][N][8] (TMA kernel), wtma2:
+// the same in two halves of N (or null), used when the whole weights do not fit next to the
+// stages but half of them do; sign -1 = data gradient
 template <class EP>
 cudaError_t conv3x3(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h, int w, int n, int N,
-                    const bf16 *wdense, const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s) {
+                    const bf16 *wdense, const bf16 *wtma, const bf16 *wtma2, int sign, const EP &e, unsigned *st,
+                    cudaStream_t s) {
   const int M = n * h * w;
-  if (!conv_tma_ok(cin, N, w, h))
-    return gemm(nbr(src, cs, co, h, w, cin, 9, sign, M), dense(wdense, 9 * cin, N), e, M, N, 9 * cin, 1, 9 * cin, st,
-                s);
+  if (conv_tma_ok(cin, N, w, h)) return conv3x3_tma(u, src, cs, co, cin, h, w, n, N, wtma, sign, e, st, s);
+  if (ColSplit<EP>::ok && wtma2 && N % 32 == 0 && col_splittable(e, N) && conv_tma_ok(cin, N / 2, w, h)) {
+    for (int hf = 0; hf < 2; ++hf) {
+      const cudaError_t err = conv3x3_tma(u, src, cs, co, cin, h, w, n, N / 2, wtma2 + (size_t)hf * 9 * cin * (N / 2),
+                                          sign, ColSplit<EP>::shift(e, hf * (N / 2), N / 2), st, s);
+      if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+  }
+  return gemm(nbr(src, cs, co, h, w, cin, 9, sign, M), dense(wdense, 9 * cin, N), e, M, N, 9 * cin, 1, 9 * cin, st,
+              s);
+}
+
+template <class EP>
+cudaError_t conv3x3_tma(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h, int w, int n, int N,
+                        const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s) {
   CUtensorMap map;
   const ConvGeo G = conv_geo(n, h, w);
   if (!(G.narrow ? encode_rb_map(&map, src, co, cin, cs, w, h, n, false, w, G.th + 2)
@@ -954,10 +1016,10 @@ int run_forward(sc_ctx *c, sc_unet *u, const float *x, int n) {
     const Layer &c1 = u->L[enc_layer(l, 0)], &c2 = u->L[enc_layer(l, 1)];
     const bf16 *src = l == 0 ? u->x0 : u->pool[l];
     const int scs = l == 0 ? kInPad : kChans[l - 1];
-    UCHK(conv3x3(u, src, scs, 0, c1.cin_p, h, w, n, cl, c1.wf, c1.wtf, 1,
+    UCHK(conv3x3(u, src, scs, 0, c1.cin_p, h, w, n, cl, c1.wf, c1.wtf, c1.wtf2, 1,
                  bias_act(u->a1[l], cl, 0, prm + c1.b_off, cl, 1, w), st, s));
     const View e = enc_out(u, l);
-    UCHK(conv3x3(u, u->a1[l], cl, 0, cl, h, w, n, cl, c2.wf, c2.wtf, 1,
+    UCHK(conv3x3(u, u->a1[l], cl, 0, cl, h, w, n, cl, c2.wf, c2.wtf, c2.wtf2, 1,
                  bias_act(e.p, e.cs, e.co, prm + c2.b_off, cl, 1, w), st, s));
     if (l + 1 < kLevels) {
       const int64_t tot = P[l + 1] * (cl / 8);
@@ -979,9 +1041,9 @@ int run_forward(sc_ctx *c, sc_unet *u, const float *x, int n) {
     eu.w = u->wl[l + 1];
     UCHK(gemm(nbr(ui.p, ui.cs, ui.co, u->hl[l + 1], u->wl[l + 1], cn, 1, 1, (int)P[l + 1]), dense(up.wf, cn, 4 * cl),
               eu, (int)P[l + 1], 4 * cl, cn, 1, cn, st, s));
-    UCHK(conv3x3(u, u->cat[l], 2 * cl, 0, 2 * cl, h, w, n, cl, c1.wf, c1.wtf, 1,
+    UCHK(conv3x3(u, u->cat[l], 2 * cl, 0, 2 * cl, h, w, n, cl, c1.wf, c1.wtf, c1.wtf2, 1,
                  bias_act(u->d1[l], cl, 0, prm + c1.b_off, cl, 1, w), st, s));
-    UCHK(conv3x3(u, u->d1[l], cl, 0, cl, h, w, n, cl, c2.wf, c2.wtf, 1,
+    UCHK(conv3x3(u, u->d1[l], cl, 0, cl, h, w, n, cl, c2.wf, c2.wtf, c2.wtf2, 1,
                  bias_act(u->d2[l], cl, 0, prm + c2.b_off, cl, 1, w), st, s));
   }
   const Layer &o = u->L[kOutLayer];
@@ -1121,7 +1183,7 @@ int run_backward(sc_ctx *c, sc_unet *u) {
     rc = wgrad(c, u, c2, tpix(u->d1[l], cl, 0, h, w, cl, 9, 0, 9 * cl, 1, kTM),
                tpix(u->gd2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
     if (rc) return rc;
-    UCHK(conv3x3(u, u->gd2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, -1, egrad(u->gd1[l], cl, u->d1[l], cl, 0, cl, w),
+    UCHK(conv3x3(u, u->gd2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, c2.wtd2, -1, egrad(u->gd1[l], cl, u->d1[l], cl, 0, cl, w),
                  st, s));
     // dec conv 1: input cat = [up, skip], output gradient gd1 -> gup (BF16) | gskip (FP32)
     rc = wgrad(c, u, c1, tpix(u->cat[l], 2 * cl, 0, h, w, 2 * cl, 9, 0, 18 * cl, 1, kTM),
@@ -1131,7 +1193,7 @@ int run_backward(sc_ctx *c, sc_unet *u) {
     es.split = cl;
     es.out2 = u->gskip[l];
     es.o2cs = cl;
-    UCHK(conv3x3(u, u->gd1[l], cl, 0, cl, h, w, n, 2 * cl, c1.wd, c1.wtd, -1, es, st, s));
+    UCHK(conv3x3(u, u->gd1[l], cl, 0, cl, h, w, n, 2 * cl, c1.wd, c1.wtd, c1.wtd2, -1, es, st, s));
     // transposed conv: input up_in (level l+1), output gradient gup (level l)
     const View ui = up_in(u, l);
     const int hn = u->hl[l + 1], wn = u->wl[l + 1];
@@ -1158,7 +1220,7 @@ int run_backward(sc_ctx *c, sc_unet *u) {
     rc = wgrad(c, u, c2, tpix(u->a1[l], cl, 0, h, w, cl, 9, 0, 9 * cl, 1, kTM),
                tpix(u->ge2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
     if (rc) return rc;
-    UCHK(conv3x3(u, u->ge2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, -1, egrad(u->ge1[l], cl, u->a1[l], cl, 0, cl, w),
+    UCHK(conv3x3(u, u->ge2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, c2.wtd2, -1, egrad(u->ge1[l], cl, u->a1[l], cl, 0, cl, w),
                  st, s));
     const bf16 *src = l == 0 ? u->x0 : u->pool[l];
     const int scs = l == 0 ? kInPad : kChans[l - 1];
@@ -1180,7 +1242,7 @@ int run_backward(sc_ctx *c, sc_unet *u) {
       pb.h = h;
       pb.w = w;
       pb.N = cp;
-      UCHK(conv3x3(u, u->ge1[l], cl, 0, cl, h, w, n, cp, c1.wd, c1.wtd, -1, pb, st, s));
+      UCHK(conv3x3(u, u->ge1[l], cl, 0, cl, h, w, n, cp, c1.wd, c1.wtd, c1.wtd2, -1, pb, st, s));
     }
   }
   return SC_OK;
@@ -1292,6 +1354,10 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
       if (u->L[i].kind == KIND_CONV) {
         u->L[i].wtf = cv.take<bf16>(u->L[i].wf_elems);
         u->L[i].wtd = u->L[i].wd_elems ? cv.take<bf16>(u->L[i].wd_elems) : nullptr;
+        if (conv_w_bytes(u->L[i].cin_p, u->L[i].cout) > kConvSplitBytes) {
+          u->L[i].wtf2 = cv.take<bf16>(u->L[i].wf_elems);
+          u->L[i].wtd2 = u->L[i].wd_elems ? cv.take<bf16>(u->L[i].wd_elems) : nullptr;
+        }
       }
     }
     u->x0 = cv.take<bf16>(P[0] * kInPad);
@@ -1340,6 +1406,8 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
     segs[j].wd = u->L[i].wd;
     segs[j].wtf = u->L[i].wtf;
     segs[j].wtd = u->L[i].wtd;
+    segs[j].wtf2 = u->L[i].wtf2;
+    segs[j].wtd2 = u->L[i].wtd2;
   }
   u->nseg = (int)segs.size();
   u->adam_blocks = blocks;
