@@ -368,6 +368,7 @@ __global__ void k_adam(const Seg *segs, int nseg, float *p, const float *g, floa
     const int c = i / (4 * S.cout), rem = i - c * 4 * S.cout;
     S.wf[(int64_t)rem * S.cin + c] = b;
     S.wd[i] = b;
+    S.wtf[((int64_t)(c / 8) * (4 * S.cout) + rem) * 8 + (c & 7)] = b;
   } else if (S.kind == KIND_OUT) {
     S.wf[i] = b;
   }
@@ -870,11 +871,11 @@ bool encode_rb_map(CUtensorMap *map, const bf16 *src, int co, int channels, int 
 #ifndef SC_CONV_MAXOCC
 #define SC_CONV_MAXOCC 1
 #endif
-int conv_stage_groups(int cin, int N, uint32_t gstride) {
+int conv_stage_groups(int cin, int N, uint32_t gstride, int taps = 9) {
   const int ng = cin / 8;
   int best = 0, best_occ = 0;
   for (int gs = ng; gs >= 2; gs -= 2) {
-    const int bytes = (int)conv_smem_bytes(cin, N, gs, gstride);
+    const int bytes = (int)conv_smem_bytes(cin, N, gs, gstride, taps);
     if (ng % gs != 0 || bytes > 227 * 1024) continue;
     if (!SC_CONV_MAXOCC) return gs;
     const int occ = std::min(std::min(228 * 1024 / (bytes + 1024), 512 / (2 * (int)conv_acc_cols(N))), 4);
@@ -891,9 +892,10 @@ bool conv_rows_ok(int w, int h) {
   return w >= 16 && w < 128 && 128 % w == 0 && h % (128 / w) == 0;
 }
 
-bool conv_tma_ok(int cin, int N, int w, int h) {
-  return conv_rows_ok(w, h) && cin % 16 == 0 && N % 16 == 0 && N <= 128 &&
-         conv_stage_groups(cin, N, conv_geo(1, h, w).gstride) > 0 && tensor_map_encoder() != nullptr;
+// taps 9: 3x3 convolution (N <= 128); taps 1: pointwise (N <= 256, two 256-column accumulators)
+bool conv_tma_ok(int cin, int N, int w, int h, int taps = 9) {
+  return conv_rows_ok(w, h) && cin % 16 == 0 && N % 16 == 0 && N <= (taps == 1 ? 256 : 128) &&
+         conv_stage_groups(cin, N, conv_geo(1, h, w, taps).gstride, taps) > 0 && tensor_map_encoder() != nullptr;
 }
 
 // Output columns [off, off + n) of a convolution's epilogue (the n-split TMA path).
@@ -929,7 +931,7 @@ bool col_splittable(const EPoolBack &, int) { return false; }
 
 template <class EP>
 cudaError_t conv3x3_tma(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h, int w, int n, int N,
-                        const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s);
+                        const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s, int taps = 9);
 
 // src: row-blocked BF16 slice (cs channels, slice at co) with `cin` channels per tap; N output
 // channels; wdense: [N][9][cin] (gathering GEMM), wtma: [tap][cin/8][N][8] (TMA kernel), wtma2:
@@ -953,17 +955,20 @@ cudaError_t conv3x3(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h,
               s);
 }
 
+// The TMA kernel for a 3x3 convolution (taps 9) or a pointwise contraction of each pixel's
+// channels (taps 1; wtma [cin/8][N][8]).
 template <class EP>
 cudaError_t conv3x3_tma(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h, int w, int n, int N,
-                        const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s) {
+                        const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s, int taps) {
   CUtensorMap map;
-  const ConvGeo G = conv_geo(n, h, w);
-  if (!(G.narrow ? encode_rb_map(&map, src, co, cin, cs, w, h, n, false, w, G.th + 2)
-                 : encode_rb_map(&map, src, co, cin, cs, w, h, n, true, kHaloW, kHaloH)))
-    return cudaErrorInvalidValue;
+  const ConvGeo G = conv_geo(n, h, w, taps);
+  const bool mapped = taps == 1 ? encode_rb_map(&map, src, co, cin, cs, w, h, n, true, G.narrow ? w : 128, G.th)
+                      : G.narrow ? encode_rb_map(&map, src, co, cin, cs, w, h, n, false, w, G.th + 2)
+                                 : encode_rb_map(&map, src, co, cin, cs, w, h, n, true, kHaloW, kHaloH);
+  if (!mapped) return cudaErrorInvalidValue;
   auto kern = k_conv_tma<EP>;
-  const int gs = conv_stage_groups(cin, N, G.gstride);
-  const int smem = (int)conv_smem_bytes(cin, N, gs, G.gstride);
+  const int gs = conv_stage_groups(cin, N, G.gstride, taps);
+  const int smem = (int)conv_smem_bytes(cin, N, gs, G.gstride, taps);
   static std::mutex mu;
   static bool attr_set[kMaxDev] = {};
   int dev = 0;
@@ -1039,8 +1044,11 @@ int run_forward(sc_ctx *c, sc_unet *u, const float *x, int n) {
     eu.cu = cl;
     eu.h = u->hl[l + 1];
     eu.w = u->wl[l + 1];
-    UCHK(gemm(nbr(ui.p, ui.cs, ui.co, u->hl[l + 1], u->wl[l + 1], cn, 1, 1, (int)P[l + 1]), dense(up.wf, cn, 4 * cl),
-              eu, (int)P[l + 1], 4 * cl, cn, 1, cn, st, s));
+    if (conv_tma_ok(cn, 4 * cl, u->wl[l + 1], u->hl[l + 1], 1))
+      UCHK(conv3x3_tma(u, ui.p, ui.cs, ui.co, cn, u->hl[l + 1], u->wl[l + 1], n, 4 * cl, up.wtf, 1, eu, st, s, 1));
+    else
+      UCHK(gemm(nbr(ui.p, ui.cs, ui.co, u->hl[l + 1], u->wl[l + 1], cn, 1, 1, (int)P[l + 1]),
+                dense(up.wf, cn, 4 * cl), eu, (int)P[l + 1], 4 * cl, cn, 1, cn, st, s));
     UCHK(conv3x3(u, u->cat[l], 2 * cl, 0, 2 * cl, h, w, n, cl, c1.wf, c1.wtf, c1.wtf2, 1,
                  bias_act(u->d1[l], cl, 0, prm + c1.b_off, cl, 1, w), st, s));
     UCHK(conv3x3(u, u->d1[l], cl, 0, cl, h, w, n, cl, c2.wf, c2.wtf, c2.wtf2, 1,
@@ -1351,6 +1359,7 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
     for (int i = 0; i < kNumLayers; ++i) {
       u->L[i].wf = cv.take<bf16>(u->L[i].wf_elems);
       u->L[i].wd = u->L[i].wd_elems ? cv.take<bf16>(u->L[i].wd_elems) : nullptr;
+      if (u->L[i].kind == KIND_UP) u->L[i].wtf = cv.take<bf16>(u->L[i].wf_elems);
       if (u->L[i].kind == KIND_CONV) {
         u->L[i].wtf = cv.take<bf16>(u->L[i].wf_elems);
         u->L[i].wtd = u->L[i].wd_elems ? cv.take<bf16>(u->L[i].wd_elems) : nullptr;

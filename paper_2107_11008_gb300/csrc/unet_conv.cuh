@@ -35,31 +35,43 @@ constexpr uint32_t kSlabTx = 6912;
 constexpr int kConvThreads = 192;
 
 __host__ __device__ constexpr uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
-__host__ __device__ constexpr uint32_t conv_w_bytes(int cin_p, int N) { return 9u * (uint32_t)cin_p * N * 2u; }
+__host__ __device__ constexpr uint32_t conv_w_bytes(int cin_p, int N, int taps = 9) {
+  return (uint32_t)taps * (uint32_t)cin_p * N * 2u;
+}
 __host__ __device__ constexpr uint32_t conv_a_bytes(int gs) { return (uint32_t)gs * kSlabBytes; }
-__host__ __device__ constexpr uint32_t conv_acc_cols(int N) { return N <= 32 ? 32u : (N <= 64 ? 64u : 128u); }
+__host__ __device__ constexpr uint32_t conv_acc_cols(int N) {
+  return N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u));
+}
 // gs: groups of 8 input channels per A stage, gstride: bytes per group in a stage
-__host__ __device__ constexpr size_t conv_smem_bytes(int cin_p, int N, int gs, uint32_t gstride = kSlabBytes) {
-  return align_up(conv_w_bytes(cin_p, N), 1024) + 2 * align_up((uint32_t)gs * gstride, 1024) + 128;
+__host__ __device__ constexpr size_t conv_smem_bytes(int cin_p, int N, int gs, uint32_t gstride = kSlabBytes,
+                                                     int taps = 9) {
+  return align_up(conv_w_bytes(cin_p, N, taps), 1024) + 2 * align_up((uint32_t)gs * gstride, 1024) + 128;
 }
 
 // Tiling of one launch: wide rows (w a multiple of 128: tiles of 128 pixels of a row, one 3 x 144
 // slab per channel group) or narrow rows (128 / w rows per tile, three dx-shifted slabs).
 struct ConvGeo {
   int n_img, h, w;
+  int taps;          // 9 (3x3) or 1 (pointwise: the tile's own pixels, no halo)
   int narrow;        // 0 wide, 1 narrow
   int th;            // rows per tile (narrow)
   uint32_t slab;     // bytes of one dx slab (narrow)
   uint32_t gstride;  // bytes of one channel group in a stage
   uint32_t tx;       // bytes the TMA copies of one channel group deliver
 };
-__host__ __device__ inline ConvGeo conv_geo(int n_img, int h, int w) {
+__host__ __device__ inline ConvGeo conv_geo(int n_img, int h, int w, int taps = 9) {
   ConvGeo g;
   g.n_img = n_img;
   g.h = h;
   g.w = w;
+  g.taps = taps;
   g.narrow = w < 128;
   g.th = g.narrow ? 128 / w : 1;
+  if (taps == 1) {  // 128 pixels x 16 bytes per channel group, whole 8-pixel blocks
+    g.slab = 0u;
+    g.gstride = g.tx = 128u * 16u;
+    return g;
+  }
   g.slab = g.narrow ? align_up((uint32_t)(g.th + 2) * w * 16u, 128) : 0u;
   g.gstride = g.narrow ? 3u * g.slab : kSlabBytes;
   g.tx = g.narrow ? 3u * (uint32_t)(g.th + 2) * w * 16u : kSlabTx;
@@ -70,7 +82,9 @@ __host__ __device__ inline ConvGeo conv_geo(int n_img, int h, int w) {
 // (tap, kg) the N rows of 16 bytes the B operand needs.  amap: 5-D tensor map of the row-blocked
 // input slice: wide rows (64 = 8 pixels x 8 channels, w / 8 pixel blocks, channel groups,
 // height, images), box (64, 18, 1, 3, 1); narrow rows (8 channels, w, channel groups, height,
-// images), box (8, w, 1, th + 2, 1).
+// images), box (8, w, 1, th + 2, 1).  Pointwise (G.taps == 1, e.g. a 2x2 stride-2 transposed
+// conv, whose N columns are the four output pixels' channels): the blocked map with box
+// (64, 16 or w / 8, 1, 1 or th, 1) and wt[kg][n][8].
 template <class EP>
 __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_constant__ CUtensorMap amap,
                                                               const bf16 *__restrict__ wt, int cin_p, int N, int gs,
@@ -79,7 +93,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ng = cin_p / 8;
   const int nchunk = ng / gs;
-  const uint32_t wbytes = conv_w_bytes(cin_p, N);
+  const uint32_t wbytes = conv_w_bytes(cin_p, N, G.taps);
   const uint32_t astride = align_up((uint32_t)gs * G.gstride, 1024);
   const int h = G.h, w = G.w;
   uint8_t *sW = sm;
@@ -131,7 +145,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
           tc::mbar_expect_tx(full, (uint32_t)gs * G.tx);
           const uint32_t dst = tc::smem_addr(sA + s * astride);
           for (int g = 0; g < gs; ++g) {
-            if (G.narrow) {
+            if (G.taps == 1) {
+              tc::tma_load_5d(dst + g * G.gstride, &amap, 0, G.narrow ? 0 : xt * (128 / 8), ch * gs + g, y, img, full);
+            } else if (G.narrow) {
               for (int dx = 0; dx < 3; ++dx)
                 tc::tma_load_5d(dst + g * G.gstride + dx * G.slab, &amap, 0, dx - 1, ch * gs + g, y - 1, img, full);
             } else {
@@ -161,6 +177,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
       uint32_t toff[9];
 #pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
+        if (G.taps == 1) {
+          toff[tap] = 0u;
+          continue;
+        }
         const int ty = tap / 3, tx = tap - 3 * ty;
         const int sy = sign * (ty - 1) + 1, sx = sign * (tx - 1) + 1;  // neighbourhood row / column (0..2)
         // start of the 128 rows output pixel 0 multiplies at this tap
@@ -184,6 +204,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
           const uint64_t bs = bdesc0 + (uint64_t)((uint32_t)(ch * gs) * (uint32_t)N);
 #pragma unroll
           for (int tap = 0; tap < 9; ++tap) {
+            if (tap >= G.taps) break;
             const uint64_t at = as + toff[tap];
             const uint64_t bt = bs + (uint64_t)((uint32_t)(tap * ng) * (uint32_t)N);
             for (int ks = 0; ks < gs / 2; ++ks)
