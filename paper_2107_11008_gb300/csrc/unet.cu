@@ -641,6 +641,12 @@ struct sc_unet {
   float *wpart = nullptr;
   size_t wpart_floats = 0;
   int num_sms = 0;
+  // the backward pass runs the weight gradients (and their reductions, which share `wpart`) in
+  // order on a second stream, forked from the context stream once each layer's output gradient
+  // is enqueued and joined before it returns: they are needed only by Adam
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork[24] = {};
+  cudaEvent_t join = nullptr;
 };
 
 namespace {
@@ -655,6 +661,27 @@ int cuda_fail(sc_ctx *c, cudaError_t e, const char *where) {
 }
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// the weight-gradient stream and its events, created on device `dev` (the caller's current device
+// is restored); release_streams undoes whatever was created
+cudaError_t create_streams(sc_unet *u, int dev) {
+  int prev = -1;
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e != cudaSuccess) return e;
+  if (prev != dev && (e = cudaSetDevice(dev)) != cudaSuccess) return e;
+  e = cudaStreamCreateWithFlags(&u->side, cudaStreamNonBlocking);
+  for (cudaEvent_t &ev : u->fork)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&u->join, cudaEventDisableTiming);
+  if (prev != dev) cudaSetDevice(prev);
+  return e;
+}
+void release_streams(sc_unet *u) {
+  for (cudaEvent_t &ev : u->fork)
+    if (ev) cudaEventDestroy(ev);
+  if (u->join) cudaEventDestroy(u->join);
+  if (u->side) cudaStreamDestroy(u->side);
+}
 
 struct Carve {
   char *base;
@@ -1095,7 +1122,7 @@ int wgrad_tma_stages(int cin, int cout, int mtiles, uint32_t gstride) {
 // weight gradient of one layer: A (rows = (tap, c) | c, + ones row), B (rows = output channels),
 // contracted over the pixels, reduced deterministically into the flat gradient.  3x3 layers on
 // rows of 128k pixels take the TMA kernel (x: the layer input, gz: its output gradient).
-int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, int64_t K) {
+int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, int64_t K, cudaStream_t ws) {
   const char *where = "sc_unet wgrad";
   const Wgrad g = wgrad_shape(ly);
   const int Mpad = g.Mtiles * kTM;
@@ -1135,7 +1162,7 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
       }
     }
     auto kern = G.narrow ? k_wgrad_tma<true> : k_wgrad_tma<false>;
-    kern<<<splits, kWgThreads, smem, sc::ctx_stream(c)>>>(xm, gm, A.cin, ly.cout, g.Mtiles, rst, G, u->wpart,
+    kern<<<splits, kWgThreads, smem, ws>>>(xm, gm, A.cin, ly.cout, g.Mtiles, rst, G, u->wpart,
                                                            sc::ctx_status(c));
     UCHK(cudaGetLastError());
   } else {
@@ -1148,25 +1175,35 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
     ep.ld = g.np;
     ep.Mpad = Mpad;
     const int N = ly.kind == KIND_UP ? 4 * ly.cout : ly.cout;
-    UCHK(gemm(A, B, ep, g.rows + 1, N, (int)K, splits, ks, sc::ctx_status(c), sc::ctx_stream(c)));
+    UCHK(gemm(A, B, ep, g.rows + 1, N, (int)K, splits, ks, sc::ctx_status(c), ws));
   }
   const int64_t tot = (int64_t)(g.rows + 1) * g.np;
   k_wgrad_reduce<<<(unsigned)((tot + kRedEntries - 1) / kRedEntries), kRedEntries * kRedGroups, 0,
-                   sc::ctx_stream(c)>>>(
+                   ws>>>(
       u->wpart, splits, Mpad, g.np, g.rows, ly.kind, ly.cout, ly.cin, ly.cin_p, u->grads + ly.w_off,
       u->grads + ly.b_off);
   UCHK(cudaGetLastError());
   return SC_OK;
 }
 
-int run_backward(sc_ctx *c, sc_unet *u) {
+int backward_body(sc_ctx *c, sc_unet *u) {
   const char *where = "sc_unet backward";
   cudaStream_t s = sc::ctx_stream(c);
+  cudaStream_t ws = u->side;
   unsigned *st = sc::ctx_status(c);
   const int n = u->n;
   int64_t P[kLevels];
   for (int l = 0; l < kLevels; ++l) P[l] = (int64_t)n * u->hl[l] * u->wl[l];
   int rc;
+  // the side stream waits for everything enqueued on the context stream so far
+  int nfork = 0;
+  auto fork = [&]() -> cudaError_t {
+    if (nfork >= (int)(sizeof(u->fork) / sizeof(u->fork[0]))) return cudaErrorInvalidValue;
+    cudaError_t e = cudaEventRecord(u->fork[nfork], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ws, u->fork[nfork], 0);
+    ++nfork;
+    return e;
+  };
   // output layer: weight and bias gradient (two fixed-order stages), data gradient into gd2[0]
   {
     const Layer &o = u->L[kOutLayer];
@@ -1175,9 +1212,10 @@ int run_backward(sc_ctx *c, sc_unet *u) {
     if ((size_t)nblk * kOutParts > u->wpart_floats)
       return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
     const int64_t span = (P[0] + nblk - 1) / nblk;
-    k_out_wgrad<<<nblk, kOutBlock, 0, s>>>(u->gy8, u->d2[0], w0, P[0], span, u->wpart);
+    UCHK(fork());
+    k_out_wgrad<<<nblk, kOutBlock, 0, ws>>>(u->gy8, u->d2[0], w0, P[0], span, u->wpart);
     UCHK(cudaGetLastError());
-    k_out_wgrad_final<<<kOutParts, 128, 0, s>>>(u->wpart, nblk, u->grads + o.w_off, u->grads + o.b_off);
+    k_out_wgrad_final<<<kOutParts, 128, 0, ws>>>(u->wpart, nblk, u->grads + o.w_off, u->grads + o.b_off);
     UCHK(cudaGetLastError());
     k_out_dgrad<<<(unsigned)((P[0] + kOutBlock - 1) / kOutBlock), kOutBlock, 0, s>>>(u->gy8, u->d2[0], w0, P[0],
                                                                                    o.wf, u->gd2[0]);
@@ -1188,14 +1226,16 @@ int run_backward(sc_ctx *c, sc_unet *u) {
     const int h = u->hl[l], w = u->wl[l], cl = kChans[l], cn = kChans[l + 1];
     const Layer &c2 = u->L[dec_layer(l, 1)], &c1 = u->L[dec_layer(l, 0)], &up = u->L[up_layer(l)];
     // dec conv 2: input d1, output gradient gd2
+    UCHK(fork());
     rc = wgrad(c, u, c2, tpix(u->d1[l], cl, 0, h, w, cl, 9, 0, 9 * cl, 1, kTM),
-               tpix(u->gd2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
+               tpix(u->gd2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws);
     if (rc) return rc;
     UCHK(conv3x3(u, u->gd2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, c2.wtd2, -1, egrad(u->gd1[l], cl, u->d1[l], cl, 0, cl, w),
                  st, s));
     // dec conv 1: input cat = [up, skip], output gradient gd1 -> gup (BF16) | gskip (FP32)
+    UCHK(fork());
     rc = wgrad(c, u, c1, tpix(u->cat[l], 2 * cl, 0, h, w, 2 * cl, 9, 0, 18 * cl, 1, kTM),
-               tpix(u->gd1[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
+               tpix(u->gd1[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws);
     if (rc) return rc;
     EGrad es = egrad(u->gup[l], cl, nullptr, 0, 0, 2 * cl, w);
     es.split = cl;
@@ -1205,8 +1245,9 @@ int run_backward(sc_ctx *c, sc_unet *u) {
     // transposed conv: input up_in (level l+1), output gradient gup (level l)
     const View ui = up_in(u, l);
     const int hn = u->hl[l + 1], wn = u->wl[l + 1];
+    UCHK(fork());
     rc = wgrad(c, u, up, tpix(ui.p, ui.cs, ui.co, hn, wn, cn, 1, 0, cn, 1, kTM),
-               tpix(u->gup[l], cl, 0, hn, wn, cl, 4, 1, 4 * cl, 0, pad16(4 * cl)), P[l + 1]);
+               tpix(u->gup[l], cl, 0, hn, wn, cl, 4, 1, 4 * cl, 0, pad16(4 * cl)), P[l + 1], ws);
     if (rc) return rc;
     AUpGrad ag;
     ag.g = u->gup[l];
@@ -1225,15 +1266,17 @@ int run_backward(sc_ctx *c, sc_unet *u) {
   for (int l = kLevels - 1; l >= 0; --l) {
     const int h = u->hl[l], w = u->wl[l], cl = kChans[l];
     const Layer &c2 = u->L[enc_layer(l, 1)], &c1 = u->L[enc_layer(l, 0)];
+    UCHK(fork());
     rc = wgrad(c, u, c2, tpix(u->a1[l], cl, 0, h, w, cl, 9, 0, 9 * cl, 1, kTM),
-               tpix(u->ge2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
+               tpix(u->ge2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws);
     if (rc) return rc;
     UCHK(conv3x3(u, u->ge2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, c2.wtd2, -1, egrad(u->ge1[l], cl, u->a1[l], cl, 0, cl, w),
                  st, s));
     const bf16 *src = l == 0 ? u->x0 : u->pool[l];
     const int scs = l == 0 ? kInPad : kChans[l - 1];
+    UCHK(fork());
     rc = wgrad(c, u, c1, tpix(src, scs, 0, h, w, c1.cin_p, 9, 0, 9 * c1.cin_p, 1, kTM),
-               tpix(u->ge1[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l]);
+               tpix(u->ge1[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws);
     if (rc) return rc;
     if (l > 0) {
       // through the pool into the level above, plus its skip gradient, times its ReLU mask
@@ -1253,6 +1296,18 @@ int run_backward(sc_ctx *c, sc_unet *u) {
       UCHK(conv3x3(u, u->ge1[l], cl, 0, cl, h, w, n, cp, c1.wd, c1.wtd, c1.wtd2, -1, pb, st, s));
     }
   }
+  return SC_OK;
+}
+
+// the backward pass, then the context stream waits for the weight-gradient stream (also after
+// an error, so that no work of this call is left unordered with the next one)
+int run_backward(sc_ctx *c, sc_unet *u) {
+  const char *where = "sc_unet backward";
+  const int rc = backward_body(c, u);
+  cudaError_t e = cudaEventRecord(u->join, u->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sc::ctx_stream(c), u->join, 0);
+  if (rc) return rc;
+  UCHK(e);
   return SC_OK;
 }
 
@@ -1438,7 +1493,9 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
   }
   for (int i = 0; i < kWin; ++i) gk[i] = (float)(gd[i] / gs);
   e = cudaMemcpyToSymbol(c_gauss, gk, sizeof(gk));
+  if (e == cudaSuccess) e = create_streams(u, dev);
   if (e != cudaSuccess) {
+    release_streams(u);
     sc::ctx_free(c, u->block);
     delete u;
     return cuda_fail(c, e, where);
@@ -1449,6 +1506,7 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
 
 int sc_unet_destroy(sc_ctx *c, sc_unet *u) {
   if (!c || !u) return SC_ERR_INVALID_ARG;
+  release_streams(u);
   sc::ctx_free(c, u->block);
   delete u;
   return SC_OK;
