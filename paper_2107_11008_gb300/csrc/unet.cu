@@ -272,12 +272,34 @@ __device__ __forceinline__ float split_sum(const float *part, int splits, int Mp
   return s;
 }
 
-__global__ void __launch_bounds__(kRedEntries *kRedGroups) k_wgrad_reduce(const float *part, int splits, int Mpad,
-                                                                           int np, int rows, int kind, int cout,
-                                                                           int cin, int cin_p, float *gw, float *gb) {
+// One launch reduces the split-K partials of every layer of a backward pass: segment t covers
+// blocks [first_block, next first_block) and its own partial region of the workspace.
+struct RedSeg {
+  int64_t part_off, w_off, b_off;  // floats into the workspace / into the flat gradient
+  int splits, Mpad, np, rows, kind, cout, cin, cin_p, first_block;
+};
+constexpr int kMaxRedSegs = 20;
+struct RedTable {
+  int n;
+  RedSeg s[kMaxRedSegs];
+};
+
+__global__ void __launch_bounds__(kRedEntries *kRedGroups) k_wgrad_reduce(const __grid_constant__ RedTable T,
+                                                                           const float *wpart, float *grads) {
   __shared__ float sh[kRedGroups][kRedEntries];
+  int lo = 0, hi = T.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (T.s[mid].first_block <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const RedSeg &S = T.s[lo];
+  const float *part = wpart + S.part_off;
+  float *gw = grads + S.w_off, *gb = grads + S.b_off;
+  const int splits = S.splits, Mpad = S.Mpad, np = S.np, rows = S.rows, kind = S.kind, cout = S.cout, cin = S.cin,
+            cin_p = S.cin_p;
   const int e = threadIdx.x % kRedEntries, g = threadIdx.x / kRedEntries;
-  const int64_t i = (int64_t)blockIdx.x * kRedEntries + e;
+  const int64_t i = (int64_t)((int)blockIdx.x - S.first_block) * kRedEntries + e;
   const int64_t total = (int64_t)(rows + 1) * np;
   const int r = (int)(i / np), n = (int)(i % np);
   const bool valid = i < total;
@@ -597,6 +619,7 @@ struct Layer {
   int64_t w_off = 0, b_off = 0, w_count = 0;
   bf16 *wf = nullptr, *wd = nullptr, *wtf = nullptr, *wtd = nullptr;
   bf16 *wtf2 = nullptr, *wtd2 = nullptr;  // n-split TMA layouts, for layers whose weights do not fit whole
+  size_t part_off = 0, part_floats = 0;   // this layer's region of the weight-gradient partials
   int64_t wf_elems = 0, wd_elems = 0;
 };
 
@@ -1122,8 +1145,10 @@ int wgrad_tma_stages(int cin, int cout, int mtiles, uint32_t gstride) {
 // weight gradient of one layer: A (rows = (tap, c) | c, + ones row), B (rows = output channels),
 // contracted over the pixels, reduced deterministically into the flat gradient.  3x3 layers on
 // rows of 128k pixels take the TMA kernel (x: the layer input, gz: its output gradient).
-int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, int64_t K, cudaStream_t ws) {
+int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, int64_t K, cudaStream_t ws,
+          RedTable &red, int &red_blocks) {
   const char *where = "sc_unet wgrad";
+  float *part = u->wpart + ly.part_off;
   const Wgrad g = wgrad_shape(ly);
   const int Mpad = g.Mtiles * kTM;
   const ConvGeo G = conv_geo((int)(K / ((int64_t)A.h * A.w)), A.h, A.w);
@@ -1140,7 +1165,7 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
     const int n_img = G.n_img;
     const int ntiles = G.narrow ? n_img * (A.h / G.th) : n_img * A.h * (A.w / 128);
     splits = std::min(ntiles, u->num_sms);
-    if ((size_t)splits * Mpad * g.np > u->wpart_floats)
+    if ((size_t)splits * Mpad * g.np > ly.part_floats)
       return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
     CUtensorMap xm, gm;
     const bool xok = G.narrow ? encode_rb_map(&xm, A.src, A.co, A.cin, A.cs, A.w, A.h, n_img, false, A.w, G.th + 2)
@@ -1162,26 +1187,37 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
       }
     }
     auto kern = G.narrow ? k_wgrad_tma<true> : k_wgrad_tma<false>;
-    kern<<<splits, kWgThreads, smem, ws>>>(xm, gm, A.cin, ly.cout, g.Mtiles, rst, G, u->wpart,
+    kern<<<splits, kWgThreads, smem, ws>>>(xm, gm, A.cin, ly.cout, g.Mtiles, rst, G, part,
                                                            sc::ctx_status(c));
     UCHK(cudaGetLastError());
   } else {
     int ks;
     split_k(g.Mtiles, K, u->num_sms, &splits, &ks);
-    if ((size_t)splits * Mpad * g.np > u->wpart_floats)
+    if ((size_t)splits * Mpad * g.np > ly.part_floats)
       return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
     EPartial ep;
-    ep.part = u->wpart;
+    ep.part = part;
     ep.ld = g.np;
     ep.Mpad = Mpad;
     const int N = ly.kind == KIND_UP ? 4 * ly.cout : ly.cout;
     UCHK(gemm(A, B, ep, g.rows + 1, N, (int)K, splits, ks, sc::ctx_status(c), ws));
   }
-  const int64_t tot = (int64_t)(g.rows + 1) * g.np;
-  k_wgrad_reduce<<<(unsigned)((tot + kRedEntries - 1) / kRedEntries), kRedEntries * kRedGroups, 0,
-                   ws>>>(
-      u->wpart, splits, Mpad, g.np, g.rows, ly.kind, ly.cout, ly.cin, ly.cin_p, u->grads + ly.w_off,
-      u->grads + ly.b_off);
+  // the reduction of this layer's partials joins the pass's single reduce launch
+  if (red.n >= kMaxRedSegs) return fail(c, SC_ERR_INVALID_ARG, "sc_unet: too many weight-gradient segments");
+  RedSeg &sg = red.s[red.n++];
+  sg.part_off = (int64_t)ly.part_off;
+  sg.w_off = ly.w_off;
+  sg.b_off = ly.b_off;
+  sg.splits = splits;
+  sg.Mpad = Mpad;
+  sg.np = g.np;
+  sg.rows = g.rows;
+  sg.kind = ly.kind;
+  sg.cout = ly.cout;
+  sg.cin = ly.cin;
+  sg.cin_p = ly.cin_p;
+  sg.first_block = red_blocks;
+  red_blocks += (int)(((int64_t)(g.rows + 1) * g.np + kRedEntries - 1) / kRedEntries);
   UCHK(cudaGetLastError());
   return SC_OK;
 }
@@ -1195,6 +1231,9 @@ int backward_body(sc_ctx *c, sc_unet *u) {
   int64_t P[kLevels];
   for (int l = 0; l < kLevels; ++l) P[l] = (int64_t)n * u->hl[l] * u->wl[l];
   int rc;
+  RedTable red;
+  red.n = 0;
+  int red_blocks = 0;
   // the side stream waits for everything enqueued on the context stream so far
   int nfork = 0;
   auto fork = [&]() -> cudaError_t {
@@ -1209,13 +1248,14 @@ int backward_body(sc_ctx *c, sc_unet *u) {
     const Layer &o = u->L[kOutLayer];
     const int w0 = u->wl[0];
     const int nblk = 2 * u->num_sms;
-    if ((size_t)nblk * kOutParts > u->wpart_floats)
+    if ((size_t)nblk * kOutParts > o.part_floats)
       return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
     const int64_t span = (P[0] + nblk - 1) / nblk;
     UCHK(fork());
-    k_out_wgrad<<<nblk, kOutBlock, 0, ws>>>(u->gy8, u->d2[0], w0, P[0], span, u->wpart);
+    float *opart = u->wpart + o.part_off;
+    k_out_wgrad<<<nblk, kOutBlock, 0, ws>>>(u->gy8, u->d2[0], w0, P[0], span, opart);
     UCHK(cudaGetLastError());
-    k_out_wgrad_final<<<kOutParts, 128, 0, ws>>>(u->wpart, nblk, u->grads + o.w_off, u->grads + o.b_off);
+    k_out_wgrad_final<<<kOutParts, 128, 0, ws>>>(opart, nblk, u->grads + o.w_off, u->grads + o.b_off);
     UCHK(cudaGetLastError());
     k_out_dgrad<<<(unsigned)((P[0] + kOutBlock - 1) / kOutBlock), kOutBlock, 0, s>>>(u->gy8, u->d2[0], w0, P[0],
                                                                                    o.wf, u->gd2[0]);
@@ -1228,14 +1268,14 @@ int backward_body(sc_ctx *c, sc_unet *u) {
     // dec conv 2: input d1, output gradient gd2
     UCHK(fork());
     rc = wgrad(c, u, c2, tpix(u->d1[l], cl, 0, h, w, cl, 9, 0, 9 * cl, 1, kTM),
-               tpix(u->gd2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws);
+               tpix(u->gd2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws, red, red_blocks);
     if (rc) return rc;
     UCHK(conv3x3(u, u->gd2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, c2.wtd2, -1, egrad(u->gd1[l], cl, u->d1[l], cl, 0, cl, w),
                  st, s));
     // dec conv 1: input cat = [up, skip], output gradient gd1 -> gup (BF16) | gskip (FP32)
     UCHK(fork());
     rc = wgrad(c, u, c1, tpix(u->cat[l], 2 * cl, 0, h, w, 2 * cl, 9, 0, 18 * cl, 1, kTM),
-               tpix(u->gd1[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws);
+               tpix(u->gd1[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws, red, red_blocks);
     if (rc) return rc;
     EGrad es = egrad(u->gup[l], cl, nullptr, 0, 0, 2 * cl, w);
     es.split = cl;
@@ -1247,7 +1287,7 @@ int backward_body(sc_ctx *c, sc_unet *u) {
     const int hn = u->hl[l + 1], wn = u->wl[l + 1];
     UCHK(fork());
     rc = wgrad(c, u, up, tpix(ui.p, ui.cs, ui.co, hn, wn, cn, 1, 0, cn, 1, kTM),
-               tpix(u->gup[l], cl, 0, hn, wn, cl, 4, 1, 4 * cl, 0, pad16(4 * cl)), P[l + 1], ws);
+               tpix(u->gup[l], cl, 0, hn, wn, cl, 4, 1, 4 * cl, 0, pad16(4 * cl)), P[l + 1], ws, red, red_blocks);
     if (rc) return rc;
     AUpGrad ag;
     ag.g = u->gup[l];
@@ -1268,7 +1308,7 @@ int backward_body(sc_ctx *c, sc_unet *u) {
     const Layer &c2 = u->L[enc_layer(l, 1)], &c1 = u->L[enc_layer(l, 0)];
     UCHK(fork());
     rc = wgrad(c, u, c2, tpix(u->a1[l], cl, 0, h, w, cl, 9, 0, 9 * cl, 1, kTM),
-               tpix(u->ge2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws);
+               tpix(u->ge2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws, red, red_blocks);
     if (rc) return rc;
     UCHK(conv3x3(u, u->ge2[l], cl, 0, cl, h, w, n, cl, c2.wd, c2.wtd, c2.wtd2, -1, egrad(u->ge1[l], cl, u->a1[l], cl, 0, cl, w),
                  st, s));
@@ -1276,7 +1316,7 @@ int backward_body(sc_ctx *c, sc_unet *u) {
     const int scs = l == 0 ? kInPad : kChans[l - 1];
     UCHK(fork());
     rc = wgrad(c, u, c1, tpix(src, scs, 0, h, w, c1.cin_p, 9, 0, 9 * c1.cin_p, 1, kTM),
-               tpix(u->ge1[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws);
+               tpix(u->ge1[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws, red, red_blocks);
     if (rc) return rc;
     if (l > 0) {
       // through the pool into the level above, plus its skip gradient, times its ReLU mask
@@ -1295,6 +1335,11 @@ int backward_body(sc_ctx *c, sc_unet *u) {
       pb.N = cp;
       UCHK(conv3x3(u, u->ge1[l], cl, 0, cl, h, w, n, cp, c1.wd, c1.wtd, c1.wtd2, -1, pb, st, s));
     }
+  }
+  // every layer's split-K partials, reduced in one launch on the weight-gradient stream
+  if (red.n > 0) {
+    k_wgrad_reduce<<<(unsigned)red_blocks, kRedEntries * kRedGroups, 0, ws>>>(red, u->wpart, u->grads);
+    UCHK(cudaGetLastError());
   }
   return SC_OK;
 }
@@ -1362,10 +1407,11 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
   }
   int64_t P[kLevels];
   for (int l = 0; l < kLevels; ++l) P[l] = (int64_t)max_batch * u->hl[l] * u->wl[l];
-  // weight-gradient workspace: the largest split layout over the layers
+  // weight-gradient workspace: one region per layer (the largest split layout it can take), so
+  // that all split-K reductions of a backward pass run in one launch at its end
   size_t wpart = 0;
   for (int i = 0; i < kNumLayers; ++i) {
-    const Layer &ly = u->L[i];
+    Layer &ly = u->L[i];
     const Wgrad g = wgrad_shape(ly);
     int lvl = 0;
     if (i < 8) lvl = i / 2;
@@ -1377,8 +1423,11 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
     int splits, ks;
     split_k(g.Mtiles, P[lvl], u->num_sms, &splits, &ks);
     splits = std::max(splits, u->num_sms);  // the TMA weight-gradient kernel: one split per SM
-    const size_t need = (size_t)splits * g.Mtiles * kTM * g.np;
-    if (need > wpart) wpart = need;
+    size_t need = (size_t)splits * g.Mtiles * kTM * g.np;
+    if (i == kOutLayer) need = (size_t)2 * u->num_sms * kOutParts;  // k_out_wgrad's block partials
+    ly.part_off = wpart;
+    ly.part_floats = need;
+    wpart += (need + 63) & ~size_t(63);
   }
   const int Hv = height - 10, Wv = width - 10;
   const int lpart = max_batch * (((Wv + kSTW - 1) / kSTW) * ((Hv + kSTH - 1) / kSTH) +
