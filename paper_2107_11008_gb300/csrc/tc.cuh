@@ -94,6 +94,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32
     if (mbar_try_wait(mbar, parity)) return true;
   return false;
 }
+// the same, also giving up (false) once *abort is set, which it reads only every 256 polls so
+// that a phase that has already completed costs a single try_wait
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity, const volatile int *abort,
+                                                   uint32_t limit = 1u << 24) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    if ((i & 255u) == 255u && *abort) return false;
+  }
+  return false;
+}
 // arrive once and add `bytes` to the transaction count the current phase waits for
 __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");

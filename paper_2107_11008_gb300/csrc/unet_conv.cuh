@@ -187,29 +187,42 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
         toff[tap] = (G.narrow ? (uint32_t)sx * G.slab + (uint32_t)(sy * w) * 16u
                               : (uint32_t)(sy * kHaloW + sx + kHaloLead - 1) * 16u) >> 4;
       }
-      const uint32_t kstep = (2u * G.gstride) >> 4, sstep = astride >> 4;
+      const uint32_t kstep = (2u * G.gstride) >> 4, sstep = astride >> 4, tstep = (uint32_t)(ng * N);
+      // only the low word (start field) of a descriptor moves: 32-bit adds, then the fixed high word
+      const uint32_t alo0 = (uint32_t)adesc0, ahi = (uint32_t)(adesc0 >> 32);
+      const uint32_t blo0 = (uint32_t)bdesc0, bhi = (uint32_t)(bdesc0 >> 32);
+      auto desc = [](uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | lo; };
+      // the issue loop is the kernel's critical path: it checks the abort flag only inside waits
+      // that have not completed yet
       for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
         const int a = i & 1, ua = i >> 1;  // accumulator and its use count
-        if (ua > 0 && !tc::mbar_wait(tc::smem_addr(&bar[7 + a]), (ua - 1) & 1)) ok = false;
+        if (ua > 0 && !tc::mbar_wait_or_abort(tc::smem_addr(&bar[7 + a]), (ua - 1) & 1, abort_flag)) ok = false;
         const uint32_t d = taddr + (uint32_t)a * half;
         for (int ch = 0; ok && ch < nchunk; ++ch, ++staged) {
           const int s = staged & 1, u = staged >> 1;
-          if (!tc::mbar_wait(tc::smem_addr(&bar[1 + s]), u & 1)) ok = false;
-          if (!ok || *abort_flag) {
+          if (!tc::mbar_wait_or_abort(tc::smem_addr(&bar[1 + s]), u & 1, abort_flag)) {
             ok = false;
             break;
           }
           tc::fence_after();
-          const uint64_t as = adesc0 + (uint64_t)((uint32_t)s * sstep);
-          const uint64_t bs = bdesc0 + (uint64_t)((uint32_t)(ch * gs) * (uint32_t)N);
+          const uint32_t as = alo0 + (uint32_t)s * sstep;
+          const uint32_t bs = blo0 + (uint32_t)(ch * gs) * (uint32_t)N;
+          if (gs == 2) {  // one K step of 16 per tap
 #pragma unroll
-          for (int tap = 0; tap < 9; ++tap) {
-            if (tap >= G.taps) break;
-            const uint64_t at = as + toff[tap];
-            const uint64_t bt = bs + (uint64_t)((uint32_t)(tap * ng) * (uint32_t)N);
-            for (int ks = 0; ks < gs / 2; ++ks)
-              tc::mma_bf16(d, at + (uint64_t)(ks * kstep), bt + (uint64_t)(2u * ks * (uint32_t)N), idesc,
-                           (ch > 0 || tap > 0 || ks > 0) ? 1u : 0u);
+            for (int tap = 0; tap < 9; ++tap) {
+              if (tap >= G.taps) break;
+              tc::mma_bf16(d, desc(as + toff[tap], ahi), desc(bs + (uint32_t)tap * tstep, bhi), idesc,
+                           (ch > 0 || tap > 0) ? 1u : 0u);
+            }
+          } else {
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+              if (tap >= G.taps) break;
+              const uint32_t at = as + toff[tap], bt = bs + (uint32_t)tap * tstep;
+              for (int ks = 0; ks < gs / 2; ++ks)
+                tc::mma_bf16(d, desc(at + (uint32_t)ks * kstep, ahi), desc(bt + 2u * (uint32_t)ks * (uint32_t)N, bhi),
+                             idesc, (ch > 0 || tap > 0 || ks > 0) ? 1u : 0u);
+            }
           }
           tc::mma_commit(tc::smem_addr(&bar[3 + s]));  // A stage free
         }
