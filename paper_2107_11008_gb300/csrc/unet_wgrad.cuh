@@ -147,24 +147,28 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tma(const __grid_consta
       const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(sA), kTLBO, kTSBO);
       const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(sB), kTLBO, kTSBO);
       const uint32_t kstep = (2u * kTLBO) >> 4;
+      // low words only (start fields); the abort flag is read only inside pending waits
+      const uint32_t alo0 = (uint32_t)adesc0, ahi = (uint32_t)(adesc0 >> 32);
+      const uint32_t blo0 = (uint32_t)bdesc0, bhi = (uint32_t)(bdesc0 >> 32);
+      auto desc = [](uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | lo; };
       bool ok = true;
       int m = 0;  // operand blocks consumed
       for (int i = 0; ok && i < mine; ++i) {
         const int bs = i & 1;
-        if (!tc::mbar_wait(tc::smem_addr(&bar[8 + bs]), (i >> 1) & 1)) ok = false;
-        const uint64_t bd = bdesc0 + (uint64_t)(((uint32_t)bs * bb) >> 4);
+        if (!tc::mbar_wait_or_abort(tc::smem_addr(&bar[8 + bs]), (i >> 1) & 1, abort_flag)) ok = false;
+        const uint32_t bd = blo0 + (((uint32_t)bs * bb) >> 4);
         for (int k = 0; ok && k < mtiles; ++k, ++m) {
           const int ab = m & 1;
-          if (!tc::mbar_wait(tc::smem_addr(&bar[4 + ab]), (m >> 1) & 1) || *abort_flag) {
+          if (!tc::mbar_wait_or_abort(tc::smem_addr(&bar[4 + ab]), (m >> 1) & 1, abort_flag)) {
             ok = false;
             break;
           }
           tc::fence_after();
-          const uint64_t ad = adesc0 + (uint64_t)(((uint32_t)ab * kTBlockBytes) >> 4);
+          const uint32_t ad = alo0 + (((uint32_t)ab * kTBlockBytes) >> 4);
 #pragma unroll
           for (int ks = 0; ks < 8; ++ks)
-            tc::mma_bf16(taddr + (uint32_t)k * cstride, ad + (uint64_t)(ks * kstep), bd + (uint64_t)(ks * kstep), idesc,
-                         (i > 0 || ks > 0) ? 1u : 0u);
+            tc::mma_bf16(taddr + (uint32_t)k * cstride, desc(ad + (uint32_t)ks * kstep, ahi),
+                         desc(bd + (uint32_t)ks * kstep, bhi), idesc, (i > 0 || ks > 0) ? 1u : 0u);
           tc::mma_commit(tc::smem_addr(&bar[6 + ab]));  // A block free
         }
         if (ok) tc::mma_commit(tc::smem_addr(&bar[10 + bs]));  // B block free
