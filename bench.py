@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--den-ratio", type=int, default=16, help="denoise workload: light paths per camera sample")
+    ap.add_argument("--den-steps", type=int, default=48000, help="denoise workload: training steps")
     ap.add_argument("--workload", default="glass512", choices=["glass512", "batch64", "unet_train", "denoise"],
                     help="batch64: 64 randomised scenes (1k-200k tris, 128^2..1024^2, 64 spp) in one graph-captured "
                          "persistent launch vs 64 sequential launches; unet_train: U-Net training steps on batches "
@@ -277,7 +278,7 @@ def run_denoise(args):
     Both pipelines spend the same ratio of light paths to camera samples (``--den-ratio``, 16),
     light paths aimed into the sphere around the glass (guided emission): the denoised frame is
     4 camera spp + 4 x ratio light paths per pixel, the U-Net removing the camera estimate's noise
-    (trained 12000 steps on 16 random 128^2 crops of 256 pairs: that estimate at 4 -> 1024 spp)
+    (trained --den-steps (48000) steps on 16 random 128^2 crops of 256 pairs: that estimate at 4 -> 1024 spp)
     and the light-traced caustic buffer added back; the plain frame is N spp + N x ratio light
     paths.
     MSEs are against a reference of two independent halves (2048 spp + 8192 light paths / px
@@ -319,7 +320,7 @@ def run_denoise(args):
     trainer = D.UNet(ctx, 16, 128, 128)  # 128^2 random crops of the 256^2 pairs, 16 per step
     trainer.set_params(D.he_init(0).to(dev))
     t0 = time.perf_counter()
-    T.train(trainer, train, steps=12000, batch=16, crop=128, lr=1.5e-3, lr_final=5e-5, seed=0)
+    T.train(trainer, train, steps=args.den_steps, batch=16, crop=128, lr=1.5e-3, lr_final=5e-5, seed=0)
     torch.cuda.synchronize(dev)
     train_s = time.perf_counter() - t0
     ctx.sync_status()
@@ -410,7 +411,7 @@ def run_denoise(args):
                 "warmup": max(3, args.warmup), "ms_per_step": den_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic (scenes.denoise_scene)",
                 "config": {"workload": "denoise: 256^2 config-1-type scenes; U-Net on the camera estimate trained "
-                                       "12000 steps x 16 crops of 128^2 from 256 pairs (4 -> 1024 spp), guided "
+                                       f"{args.den_steps} steps x 16 crops of 128^2 from 256 pairs (4 -> 1024 spp), guided "
                                        "light-traced caustics added back; 8 held-out scenes; reference 2 x (2048 spp "
                                        "+ 8192 guided light paths/px)",
                            "input": f"{lo.spp} camera spp + {lo.lights_per_pixel} light paths/px",
