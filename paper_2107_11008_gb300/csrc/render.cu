@@ -21,7 +21,7 @@ constexpr int kBlock = 128;
 #endif
 // node visits per traversal chunk in the camera kernel
 #ifndef SC_TRAV_CHUNK
-#define SC_TRAV_CHUNK 16
+#define SC_TRAV_CHUNK 12
 #endif
 
 // Camera paths as a per-lane state machine.  Every loop iteration each live lane traces exactly
