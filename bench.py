@@ -46,7 +46,7 @@ LAUNCHES_PER_STEP = 31 + 3
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
 #       -k regex:k_trace_camera -s 4 -c 1 python bench.py --steps 1 --warmup 3 --no-cpu-baseline
 # (the scene stays in L2, so DRAM sees little more than the accumulators and first touches)
-CAMERA_DRAM_BYTES = 23.4e6
+CAMERA_DRAM_BYTES = 24.4e6
 
 
 def parse():
@@ -133,13 +133,15 @@ def run_batch(args):
 # U-Net denoiser workloads
 # ---------------------------------------------------------------------------------------------
 UNET_CHANS = (32, 48, 64, 128)
-# our kernels per training step: input pack, 8 encoder convs, 3 pools, 3 x (up, 2 convs), output
-# conv (22); loss (3); output layer wgrad+reduce+dgrad (3); decoder 3 x 3 layers x 3 (27); encoder
-# 8 convs x (wgrad+reduce+dgrad) minus the first layer's dgrad (23); Adam (1)
-UNET_TRAIN_LAUNCHES = 22 + 3 + 3 + 27 + 23 + 1
-UNET_FWD_LAUNCHES = 22
+# our kernels per training step (counted from an ncu launch list of one step): forward 23 (input
+# pack, 9 encoder conv launches -- the 128 -> 128 conv runs as two halves --, 3 pools, 3 x
+# (transposed conv, 2 convs), output layer); loss 3; backward 38 (output layer 3, decoder 3 x 6,
+# encoder 16, one split-K reduce); Adam 1
+UNET_TRAIN_LAUNCHES = 23 + 3 + 38 + 1
+UNET_FWD_LAUNCHES = 23
 # DRAM bytes of one training step (all its kernels, dram__bytes_read.sum + dram__bytes_write.sum
-# summed over the step's launches), from one ncu capture of these kernel versions:
+# summed over launches 1-65 = the first step; launch 0 is the parameter refresh), from one ncu
+# capture of these kernel versions:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
 #       -k regex:"k_(gemm|conv_tma|wgrad_tma|ssim|pool|adam|wgrad_reduce|loss_final|pack_input|out_)" -c 80 \
 #       python bench.py --workload unet_train --steps 1 --warmup 3 --no-cpu-baseline
