@@ -242,6 +242,12 @@ int sc_scene_get_info(const sc_scene *scene, sc_scene_info *info);
  * < 0 is leaf ~k), tris_host n_tris * 48 bytes (three float4 vertices in leaf order, .w
  * of the first holding the input triangle index as int bits).  Synchronises. */
 int sc_scene_export_bvh(sc_ctx *ctx, const sc_scene *scene, void *nodes_host, void *tris_host);
+/* Copy the 4-wide BVH the camera kernel traverses to host memory: n_nodes * 128 bytes, record j
+ * collapsed from binary node j (only records reachable from record 0 through child references
+ * are traversed): float4 x lo, x hi, y lo, y hi, z lo, z hi of the four children (structure of
+ * arrays), int4 child references (>= 0: record of that binary node, < 0: leaf ~k, 0x7FFFFFFF:
+ * empty), float4 padding.  SC_ERR_UNSUPPORTED if the scene has no 4-wide nodes.  Synchronises. */
+int sc_scene_export_bvh4(sc_ctx *ctx, const sc_scene *scene, void *nodes4_host);
 
 /* --- LBVH build without device allocation --------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot allocate

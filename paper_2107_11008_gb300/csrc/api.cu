@@ -389,6 +389,14 @@ int sc_scene_export_bvh(sc_ctx *c, const sc_scene *s, void *nodes_host, void *tr
   return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_scene_export_bvh");
 }
 
+int sc_scene_export_bvh4(sc_ctx *c, const sc_scene *s, void *nodes4_host) {
+  if (!c || !valid_scene(s) || !nodes4_host) return fail(c, SC_ERR_INVALID_ARG, "sc_scene_export_bvh4: null argument");
+  if (!s->dev.nodes4) return fail(c, SC_ERR_UNSUPPORTED, "sc_scene_export_bvh4: the scene has no 4-wide nodes");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(nodes4_host, s->dev.nodes4, (size_t)s->n_nodes * 128, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_scene_export_bvh4");
+}
+
 int sc_intersect(sc_ctx *c, const sc_scene *s, const float *rays, int64_t n, float *hits) {
   if (!c || !valid_scene(s) || n < 0 || (n > 0 && (!rays || !hits)))
     return fail(c, SC_ERR_INVALID_ARG, "sc_intersect: bad argument");

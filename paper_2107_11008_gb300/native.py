@@ -114,6 +114,7 @@ SIGNATURES = {
     "sc_free_scene": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sc_scene_get_info": (C.c_int, [C.c_void_p, P(sc_scene_info)]),
     "sc_scene_export_bvh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sc_scene_export_bvh4": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sc_build_bvh_noalloc": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.c_int32, C.c_int32] + [C.c_void_p] * 5),
     "sc_intersect": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "sc_occluded": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
@@ -238,6 +239,10 @@ def sc_scene_get_info(scene) -> sc_scene_info:
 
 def sc_scene_export_bvh(ctx, scene, nodes_host, tris_host):
     return check(load().sc_scene_export_bvh(ctx, scene, nodes_host, tris_host), ctx)
+
+
+def sc_scene_export_bvh4(ctx, scene, nodes4_host):
+    return check(load().sc_scene_export_bvh4(ctx, scene, nodes4_host), ctx)
 
 
 def sc_intersect(ctx, scene, rays_dev, n, hits_dev):

@@ -154,6 +154,14 @@ class GpuScene:
         N.sc_scene_export_bvh(self.ctx.handle, self.handle, nodes.ctypes.data, tris.ctypes.data)
         return nodes, tris[: info.n_tris]
 
+    def export_bvh4(self):
+        """The 4-wide records [n_nodes, 32] float32 (children boxes SoA, int32 child references in
+        columns 24..27; see sc_scene_export_bvh4)."""
+        info = self.info()
+        nodes4 = np.empty((max(info.n_nodes, 1), 32), np.float32)
+        N.sc_scene_export_bvh4(self.ctx.handle, self.handle, nodes4.ctypes.data)
+        return nodes4[: info.n_nodes]
+
     def free(self):
         if getattr(self, "handle", None):
             N.sc_free_scene(self.ctx.handle, self.handle)

@@ -98,6 +98,71 @@ def _check_bvh(gs, sc):
                 np.testing.assert_array_equal(lo, np.minimum(lo0, lo1))
                 np.testing.assert_array_equal(hi, np.maximum(hi0, hi1))
     assert 1 <= info.max_depth <= 64
+    if info.bvh_width == 4:
+        _check_bvh4(gs, nodes, tris, ch, slot_box, n)
+
+
+def _check_bvh4(gs, nodes, tris, ch, slot_box, n):
+    """The 4-wide records the camera kernel traverses: from record 0 every leaf is reached exactly
+    once; each record's children are a cut of its binary subtree (their leaves are exactly the
+    subtree's); boxes are the binary tree's own (triangle bounds for leaves); fewer than four
+    children only when all of them are leaves; empty slots last."""
+    n4 = gs.export_bvh4()
+    assert n4.shape == (n - 1, 32)
+    refs4 = n4[:, 24:28].copy().view(np.int32)
+    empty = 0x7FFFFFFF
+    box_of = {}
+    for i in range(n - 1):
+        for s in range(2):
+            if ch[i, s] >= 0:
+                box_of[int(ch[i, s])] = slot_box(i, s)
+    under = {}
+
+    def leaves_under(j):  # binary internal node j
+        if j in under:
+            return under[j]
+        out, stack = [], [j]
+        while stack:
+            m = stack.pop()
+            for s in range(2):
+                c = int(ch[m, s])
+                if c < 0:
+                    out.append(~c)
+                else:
+                    stack.append(c)
+        under[j] = sorted(out)
+        return under[j]
+
+    seen, visited, stack = [], set(), [0]
+    while stack:
+        j = stack.pop()
+        assert j not in visited
+        visited.add(j)
+        refs = refs4[j]
+        valid = refs != empty
+        k = int(valid.sum())
+        assert 2 <= k <= 4 and valid[:k].all()
+        kids = [int(c) for c in refs[:k]]
+        if k < 4:
+            assert all(c < 0 for c in kids)
+        cut = []
+        for s, c in enumerate(kids):
+            lo = n4[j, [s, 8 + s, 16 + s]]
+            hi = n4[j, [4 + s, 12 + s, 20 + s]]
+            if c < 0:
+                v = tris[~c].reshape(3, 4)[:, :3]
+                np.testing.assert_array_equal(lo, v.min(0))
+                np.testing.assert_array_equal(hi, v.max(0))
+                cut.append(~c)
+                seen.append(~c)
+            else:
+                blo, bhi = box_of[c]
+                np.testing.assert_array_equal(lo, blo)
+                np.testing.assert_array_equal(hi, bhi)
+                cut.extend(leaves_under(c))
+                stack.append(c)
+        assert sorted(cut) == leaves_under(j)
+    assert sorted(seen) == list(range(n))
 
 
 @pytest.mark.parametrize("n_tris", [1, 2, 3, 7, 200, 2049, 5000])
