@@ -480,54 +480,55 @@ struct EPoolBack {
   __device__ __forceinline__ void store(int row, int n0, const float *v, int) const {
     if (n0 >= N) return;
     const int x = row % w, t = row / w, y = t % h, img = t / h;
-    float ev[4][16];
-    int64_t pix[4];
+    // two halves of 8 channels, one after the other, so that few values are live at once
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t r2 = (int64_t)img * 2 * h + 2 * y + (q >> 1);
-      pix[q] = r2 * (2 * w) + 2 * x + (q & 1);
-      const bf16 *ep = e + rb_off(r2, 2 * x + (q & 1), eco + n0, ecs, 2 * w);
-      unpack8(ldg16(ep), ev[q]);
-      unpack8(ldg16(ep + 16 * w), ev[q] + 8);
-    }
-    int win[16];
+    for (int hh = 0; hh < 2; ++hh) {
+      const int c = n0 + 8 * hh;
+      float ev[4][8];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      int b = 0;
-      float best = ev[0][i];
+      for (int q = 0; q < 4; ++q)
+        unpack8(ldg16(e + rb_off((int64_t)img * 2 * h + 2 * y + (q >> 1), 2 * x + (q & 1), eco + c, ecs, 2 * w)),
+                ev[q]);
+      int win[8];
 #pragma unroll
-      for (int q = 1; q < 4; ++q)
-        if (ev[q][i] > best) {
-          best = ev[q][i];
-          b = q;
-        }
-      win[i] = b;
-    }
+      for (int i = 0; i < 8; ++i) {
+        int b = 0;
+        float best = ev[0][i];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float o[16];
-      if (skip) {
-        const float4 *sp = reinterpret_cast<const float4 *>(skip + pix[q] * scs + n0);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float4 f = __ldg(sp + i);
-          o[4 * i] = f.x;
-          o[4 * i + 1] = f.y;
-          o[4 * i + 2] = f.z;
-          o[4 * i + 3] = f.w;
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) o[i] = 0.0f;
+        for (int q = 1; q < 4; ++q)
+          if (ev[q][i] > best) {
+            best = ev[q][i];
+            b = q;
+          }
+        win[i] = b;
       }
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        if (win[i] == q) o[i] += v[i];
-        if (!(ev[q][i] > 0.0f)) o[i] = 0.0f;
+      for (int q = 0; q < 4; ++q) {
+        const int64_t r2 = (int64_t)img * 2 * h + 2 * y + (q >> 1);
+        const int x2 = 2 * x + (q & 1);
+        float o[8];
+        if (skip) {
+          const float4 *sp = reinterpret_cast<const float4 *>(skip + (r2 * (2 * w) + x2) * scs + c);
+          const float4 f0 = __ldg(sp), f1 = __ldg(sp + 1);
+          o[0] = f0.x;
+          o[1] = f0.y;
+          o[2] = f0.z;
+          o[3] = f0.w;
+          o[4] = f1.x;
+          o[5] = f1.y;
+          o[6] = f1.z;
+          o[7] = f1.w;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) o[i] = 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (win[i] == q) o[i] += v[8 * hh + i];
+          if (!(ev[q][i] > 0.0f)) o[i] = 0.0f;
+        }
+        *reinterpret_cast<uint4 *>(out + rb_off(r2, x2, c, ocs, 2 * w)) = pack8(o);
       }
-      bf16 *p = out + rb_off((int64_t)img * 2 * h + 2 * y + (q >> 1), 2 * x + (q & 1), n0, ocs, 2 * w);
-      *reinterpret_cast<uint4 *>(p) = pack8(o);
-      *reinterpret_cast<uint4 *>(p + 16 * w) = pack8(o + 8);
     }
   }
 };
