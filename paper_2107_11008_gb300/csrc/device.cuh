@@ -270,6 +270,21 @@ __device__ __forceinline__ bool box_test(const WRay &w, float lx, float hx, floa
   return t0 <= t1;
 }
 
+// The same slab test with each axis's entry and exit planes already chosen by the sign of the
+// ray's reciprocal direction (n* entry, f* exit): with inv >= 0, (lo - o) * inv <= (hi - o) * inv
+// holds after rounding too, so the min / max that box_test takes per axis are exactly these, and
+// the result is bit for bit box_test's.
+__device__ __forceinline__ bool box_test_nf(const WRay &w, float nx, float fx, float ny, float fy, float nz, float fz,
+                                            float tmax, float &tnear) {
+  const float tnx = (nx - w.o.x) * w.inv.x, tfx = (fx - w.o.x) * w.inv.x;
+  const float tny = (ny - w.o.y) * w.inv.y, tfy = (fy - w.o.y) * w.inv.y;
+  const float tnz = (nz - w.o.z) * w.inv.z, tfz = (fz - w.o.z) * w.inv.z;
+  const float t0 = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, 0.0f));
+  const float t1 = fminf(fminf(tfx, tfy), fminf(tfz, tmax)) * 1.0000004f;
+  tnear = t0;
+  return t0 <= t1;
+}
+
 struct Hit {
   float t, b1, b2;
   int prim;     // leaf order, -1 = miss
@@ -435,16 +450,17 @@ __device__ __forceinline__ bool trav_step4(const DevScene &S, const WRay &w, flo
       return true;
     }
     const float4 *nd = S.nodes4 + 8 * node;
-    const float4 xl = __ldg(nd), xh = __ldg(nd + 1), yl = __ldg(nd + 2), yh = __ldg(nd + 3);
-    const float4 zl = __ldg(nd + 4), zh = __ldg(nd + 5), rr = __ldg(nd + 6);
+    // entry / exit bounds of each axis, picked by the sign of the reciprocal direction
+    const int sx = w.inv.x < 0.0f, sy = w.inv.y < 0.0f, sz = w.inv.z < 0.0f;
+    const float4 nx = __ldg(nd + sx), fx = __ldg(nd + 1 - sx), ny = __ldg(nd + 2 + sy), fy = __ldg(nd + 3 - sy);
+    const float4 nz = __ldg(nd + 4 + sz), fz = __ldg(nd + 5 - sz), rr = __ldg(nd + 6);
     int ref[4] = {__float_as_int(rr.x), __float_as_int(rr.y), __float_as_int(rr.z), __float_as_int(rr.w)};
     float key[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       float tn;
-      const bool hb = ref[i] != kEmptyRef &&
-                      box_test(w, comp4(xl, i), comp4(xh, i), comp4(yl, i), comp4(yh, i), comp4(zl, i), comp4(zh, i),
-                               ts.h.t, tn);
+      const bool hb = ref[i] != kEmptyRef && box_test_nf(w, comp4(nx, i), comp4(fx, i), comp4(ny, i), comp4(fy, i),
+                                                         comp4(nz, i), comp4(fz, i), ts.h.t, tn);
       key[i] = hb ? tn : kInf;
     }
     // leaves (one triangle each) are tested right away, the hit ones of this lane in one compact
