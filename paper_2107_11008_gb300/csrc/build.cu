@@ -411,9 +411,11 @@ __global__ void k_collapse4(BuildBuffers b) {
     }
   }
 #endif
+  // empty slots: an inverted box (lo > hi on every axis), which no ray enters whatever the signs
+  // of its direction, so traversal needs no test of the reference
   for (int k = cnt; k < 4; ++k) {
-    lo[0][k] = lo[1][k] = lo[2][k] = 0.0f;
-    hi[0][k] = hi[1][k] = hi[2][k] = 0.0f;
+    lo[0][k] = lo[1][k] = lo[2][k] = 3.0e38f;
+    hi[0][k] = hi[1][k] = hi[2][k] = -3.0e38f;
     ref[k] = kEmptyRef;
   }
   float4 *o = b.nodes4 + 8 * i;

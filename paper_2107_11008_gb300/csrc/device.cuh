@@ -410,7 +410,7 @@ __device__ __forceinline__ bool trav_step(const DevScene &S, const WRay &w, floa
 // 4-wide traversal.  Node j of nodes4 (8 float4, j = the index of the binary node it was
 // collapsed from) holds, structure-of-arrays, the boxes of up to four children: x lo, x hi,
 // y lo, y hi, z lo, z hi, then the four child references (>= 0: a 4-wide node, < 0: leaf ~k,
-// kEmptyRef: no child).  One visit tests the four boxes, tests the hit leaves' triangles at
+// kEmptyRef: no child, whose box is inverted so that it is never entered).  One visit tests the four boxes, tests the hit leaves' triangles at
 // once, and continues with the nearest hit internal child, pushing the others farthest first.
 // The closest hit (with its tie-break on the input id) does not depend on the visit order.
 // ------------------------------------------------------------------------------------------
@@ -459,8 +459,9 @@ __device__ __forceinline__ bool trav_step4(const DevScene &S, const WRay &w, flo
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       float tn;
-      const bool hb = ref[i] != kEmptyRef && box_test_nf(w, comp4(nx, i), comp4(fx, i), comp4(ny, i), comp4(fy, i),
-                                                         comp4(nz, i), comp4(fz, i), ts.h.t, tn);
+      // empty slots hold inverted boxes and never pass
+      const bool hb = box_test_nf(w, comp4(nx, i), comp4(fx, i), comp4(ny, i), comp4(fy, i), comp4(nz, i), comp4(fz, i),
+                                  ts.h.t, tn);
       key[i] = hb ? tn : kInf;
     }
     // leaves (one triangle each) are tested right away, the hit ones of this lane in one compact
