@@ -410,8 +410,9 @@ __device__ __forceinline__ bool trav_step(const DevScene &S, const WRay &w, floa
 // 4-wide traversal.  Node j of nodes4 (8 float4, j = the index of the binary node it was
 // collapsed from) holds, structure-of-arrays, the boxes of up to four children: x lo, x hi,
 // y lo, y hi, z lo, z hi, then the four child references (>= 0: a 4-wide node, < 0: leaf ~k,
-// kEmptyRef: no child, whose box is inverted so that it is never entered).  One visit tests the four boxes, tests the hit leaves' triangles at
-// once, and continues with the nearest hit internal child, pushing the others farthest first.
+// kEmptyRef: no child, whose box is inverted so that it is never entered).  One visit tests the
+// four boxes, tests the hit leaves' triangles at once, and continues with the nearest hit
+// internal child, pushing the others farthest first.
 // The closest hit (with its tie-break on the input id) does not depend on the visit order.
 // ------------------------------------------------------------------------------------------
 constexpr int kEmptyRef = 0x7FFFFFFF;
