@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on seeded inputs.
 
-Bar (the benchmark spec): bit-exact hit-triangle ids / mask / id buffers away from grazing cases,
+Bar: bit-exact hit-triangle ids / mask / id buffers away from grazing cases,
 per-path radiance within 1e-4 relative, image MSE within 1e-5 at equal spp and seed.
 """
 import math
