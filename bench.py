@@ -143,7 +143,7 @@ UNET_FWD_LAUNCHES = 23
 # summed over launches 1-65 = the first step; launch 0 is the parameter refresh), from one ncu
 # capture of these kernel versions:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
-#       -k regex:"k_(gemm|conv_tma|wgrad_tma|ssim|pool|adam|wgrad_reduce|loss_final|pack_input|out_)" -c 80 \
+#       -k regex:"k_(gemm|conv_tma|wgrad_tma|ssim|pool|adam|wgrad_reduce|loss_final|pack_input|out_)" -c 66 \
 #       python bench.py --workload unet_train --steps 1 --warmup 3 --no-cpu-baseline
 UNET_STEP_DRAM_BYTES = 3.62e9
 

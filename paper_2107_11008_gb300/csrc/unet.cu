@@ -411,189 +411,143 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 }
 
 // SSIM of each valid 11x11 window and d SSIM / d (mu_x, E[x^2], E[xy]) of that window.
-// Grid: (ceil(Wv / 32), ceil(Hv / 8), n), 256 threads; Wv = w - 10, Hv = h - 10.  The block loads
-// its (8 + 10) x (32 + 10) pixel tile of all three channels once (coalesced: a tile row is 126
-// consecutive floats); per channel the horizontal blur runs as 144 tasks of 4 outputs (14 pixels
-// of a row in registers) and the vertical one as 128 tasks of 2 windows (12 rows in registers).
+// Grid: (ceil(Wv / 32), ceil(Hv / 8), n), 256 threads; Wv = w - 10, Hv = h - 10.
 __global__ void __launch_bounds__(256) k_ssim_fwd(const float *p, const float *t, int h, int w, float *dmx,
                                                   float *dexx, float *dexy, double *part) {
-  constexpr int TW = kSTW + 10, TH = kSTH + 10;
-  __shared__ float sp[3][TH][TW], st[3][TH][TW];
-  __shared__ float hz[5][TH][kSTW];
+  __shared__ float sp[kSTH + 10][kSTW + 10], st[kSTH + 10][kSTW + 10];
+  __shared__ float hz[5][kSTH + 10][kSTW];
   __shared__ double red[256];
   const int Hv = h - 10, Wv = w - 10;
   const int x0 = blockIdx.x * kSTW, y0 = blockIdx.y * kSTH, img = blockIdx.z;
-  for (int i = threadIdx.x; i < TH * TW * 3; i += 256) {
-    const int r = i / (TW * 3), rem = i - r * (TW * 3), cc = rem / 3, ch = rem - cc * 3;
-    const int yy = y0 + r, xx = x0 + cc;
-    const bool in = yy < h && xx < w;
-    const int64_t idx = ((int64_t)(img * h + yy) * w + xx) * 3 + ch;
-    sp[ch][r][cc] = in ? p[idx] : 0.0f;
-    st[ch][r][cc] = in ? t[idx] : 0.0f;
-  }
-  __syncthreads();
+  const int tx = threadIdx.x % kSTW, ty = threadIdx.x / kSTW;
+  const int wx = x0 + tx, wy = y0 + ty;
   double acc = 0.0;
   for (int ch = 0; ch < 3; ++ch) {
-    if (threadIdx.x < TH * (kSTW / 4)) {  // horizontal: row r, columns c0 .. c0 + 3
-      const int r = threadIdx.x / (kSTW / 4), c0 = (threadIdx.x % (kSTW / 4)) * 4;
-      float u[14], q[14];
-#pragma unroll
-      for (int j = 0; j < 14; ++j) {
-        u[j] = sp[ch][r][c0 + j];
-        q[j] = st[ch][r][c0 + j];
-      }
-#pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        float a = 0, b = 0, aa = 0, bb = 0, ab = 0;
-#pragma unroll
-        for (int k = 0; k < kWin; ++k) {
-          const float g = c_gauss[k], uu = u[o + k], qq = q[o + k];
-          a += g * uu;
-          b += g * qq;
-          aa += g * uu * uu;
-          bb += g * qq * qq;
-          ab += g * uu * qq;
-        }
-        hz[0][r][c0 + o] = a;
-        hz[1][r][c0 + o] = b;
-        hz[2][r][c0 + o] = aa;
-        hz[3][r][c0 + o] = bb;
-        hz[4][r][c0 + o] = ab;
-      }
+    for (int i = threadIdx.x; i < (kSTH + 10) * (kSTW + 10); i += 256) {
+      const int r = i / (kSTW + 10), cc = i % (kSTW + 10);
+      const int yy = y0 + r, xx = x0 + cc;
+      const bool in = yy < h && xx < w;
+      const int64_t idx = ((int64_t)(img * h + yy) * w + xx) * 3 + ch;
+      sp[r][cc] = in ? p[idx] : 0.0f;
+      st[r][cc] = in ? t[idx] : 0.0f;
     }
     __syncthreads();
-    if (threadIdx.x < kSTW * (kSTH / 2)) {  // vertical: column tx, window rows ty, ty + 1
-      const int tx = threadIdx.x % kSTW, ty = (threadIdx.x / kSTW) * 2;
-      float m[5][2];
+    for (int i = threadIdx.x; i < (kSTH + 10) * kSTW; i += 256) {
+      const int r = i / kSTW, cc = i % kSTW;
+      float a = 0, b = 0, aa = 0, bb = 0, ab = 0;
 #pragma unroll
-      for (int qi = 0; qi < 5; ++qi) {
-        float col[12];
-#pragma unroll
-        for (int j = 0; j < 12; ++j) col[j] = hz[qi][ty + j][tx];
-#pragma unroll
-        for (int o = 0; o < 2; ++o) {
-          float v = 0;
-#pragma unroll
-          for (int k = 0; k < kWin; ++k) v += c_gauss[k] * col[o + k];
-          m[qi][o] = v;
-        }
+      for (int k = 0; k < kWin; ++k) {
+        const float g = c_gauss[k], u = sp[r][cc + k], q = st[r][cc + k];
+        a += g * u;
+        b += g * q;
+        aa += g * u * u;
+        bb += g * q * q;
+        ab += g * u * q;
       }
+      hz[0][r][cc] = a;
+      hz[1][r][cc] = b;
+      hz[2][r][cc] = aa;
+      hz[3][r][cc] = bb;
+      hz[4][r][cc] = ab;
+    }
+    __syncthreads();
+    float mx = 0, my = 0, exx = 0, eyy = 0, exy = 0;
 #pragma unroll
-      for (int o = 0; o < 2; ++o) {
-        const int wx = x0 + tx, wy = y0 + ty + o;
-        if (wx < Wv && wy < Hv) {
-          const float mx = m[0][o], my = m[1][o], exx = m[2][o], eyy = m[3][o], exy = m[4][o];
-          const float a1 = 2.0f * mx * my + kC1;
-          const float a2 = 2.0f * (exy - mx * my) + kC2;
-          const float b1 = mx * mx + my * my + kC1;
-          const float b2 = (exx - mx * mx) + (eyy - my * my) + kC2;
-          const float S = a1 * a2 / (b1 * b2);
-          const int64_t oi = ((int64_t)(img * Hv + wy) * Wv + wx) * 3 + ch;
-          dmx[oi] = (2.0f * my * a2 - 2.0f * my * a1) / (b1 * b2) - S * (2.0f * mx / b1 - 2.0f * mx / b2);
-          dexx[oi] = -S / b2;
-          dexy[oi] = 2.0f * a1 / (b1 * b2);
-          acc += S;
-        }
-      }
+    for (int k = 0; k < kWin; ++k) {
+      const float g = c_gauss[k];
+      mx += g * hz[0][ty + k][tx];
+      my += g * hz[1][ty + k][tx];
+      exx += g * hz[2][ty + k][tx];
+      eyy += g * hz[3][ty + k][tx];
+      exy += g * hz[4][ty + k][tx];
+    }
+    if (wx < Wv && wy < Hv) {
+      const float a1 = 2.0f * mx * my + kC1;
+      const float a2 = 2.0f * (exy - mx * my) + kC2;
+      const float b1 = mx * mx + my * my + kC1;
+      const float b2 = (exx - mx * mx) + (eyy - my * my) + kC2;
+      const float S = a1 * a2 / (b1 * b2);
+      const int64_t o = ((int64_t)(img * Hv + wy) * Wv + wx) * 3 + ch;
+      dmx[o] = (2.0f * my * a2 - 2.0f * my * a1) / (b1 * b2) - S * (2.0f * mx / b1 - 2.0f * mx / b2);
+      dexx[o] = -S / b2;
+      dexy[o] = 2.0f * a1 / (b1 * b2);
+      acc += S;
     }
     __syncthreads();
   }
-  const double sum = block_sum(acc, red);
-  if (threadIdx.x == 0) part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = sum;
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
 }
 
 // d loss / d pred per pixel: the adjoint of the window blurs applied to the three coefficient
-// maps plus the L1 term.  Grid: (ceil(w / 32), ceil(h / 8), n), 256 threads.  The window maps of
-// rows y0 - 10 .. y0 + 7 and columns x0 - 10 .. x0 + 31 are loaded once for all channels; the
-// blurs are register-blocked as in k_ssim_fwd.
+// maps plus the L1 term.  Grid: (ceil(w / 32), ceil(h / 8), n), 256 threads.
 __global__ void __launch_bounds__(256) k_ssim_bwd(const float *p, const float *t, int h, int w, const float *dmx,
                                                   const float *dexx, const float *dexy, float inv_px, float inv_win,
                                                   float *grad, bf16 *gy8, double *part) {
-  constexpr int TW = kSTW + 10, TH = kSTH + 10;
-  __shared__ float wm[3][3][TH][TW];
-  __shared__ float hz[3][TH][kSTW];
+  __shared__ float wm[3][kSTH + 10][kSTW + 10];
+  __shared__ float hz[3][kSTH + 10][kSTW];
   __shared__ double red[256];
   const int Hv = h - 10, Wv = w - 10;
   const int x0 = blockIdx.x * kSTW, y0 = blockIdx.y * kSTH, img = blockIdx.z;
-  for (int i = threadIdx.x; i < TH * TW * 3; i += 256) {
-    const int r = i / (TW * 3), rem = i - r * (TW * 3), cc = rem / 3, ch = rem - cc * 3;
-    const int wy = y0 - 10 + r, wx = x0 - 10 + cc;
-    const bool ok = wy >= 0 && wy < Hv && wx >= 0 && wx < Wv;
-    const int64_t o = ((int64_t)(img * Hv + wy) * Wv + wx) * 3 + ch;
-    wm[ch][0][r][cc] = ok ? dmx[o] : 0.0f;
-    wm[ch][1][r][cc] = ok ? dexx[o] : 0.0f;
-    wm[ch][2][r][cc] = ok ? dexy[o] : 0.0f;
-  }
-  __syncthreads();
-  // this thread's pixels for the per-pixel part: column tx, rows ty, ty + 1
-  const int tx = threadIdx.x % kSTW, ty = (threadIdx.x / kSTW) * 2;
-  float gout[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+  const int tx = threadIdx.x % kSTW, ty = threadIdx.x / kSTW;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool in = x < w && y < h;
+  const int64_t pix = ((int64_t)(img * h + y) * w + x);
+  float gout[3] = {0.0f, 0.0f, 0.0f};
   double acc = 0.0;
-#pragma unroll
   for (int ch = 0; ch < 3; ++ch) {
-    if (threadIdx.x < TH * (kSTW / 4)) {  // horizontal adjoint: row r, columns c0 .. c0 + 3
-      const int r = threadIdx.x / (kSTW / 4), c0 = (threadIdx.x % (kSTW / 4)) * 4;
-#pragma unroll
-      for (int qi = 0; qi < 3; ++qi) {
-        float v[14];
-#pragma unroll
-        for (int j = 0; j < 14; ++j) v[j] = wm[ch][qi][r][c0 + j];
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          float a = 0;
-#pragma unroll
-          for (int k = 0; k < kWin; ++k) a += c_gauss[k] * v[o + 10 - k];
-          hz[qi][r][c0 + o] = a;
-        }
-      }
+    // window maps over rows y0-10 .. y0+7, cols x0-10 .. x0+31
+    for (int i = threadIdx.x; i < (kSTH + 10) * (kSTW + 10); i += 256) {
+      const int r = i / (kSTW + 10), cc = i % (kSTW + 10);
+      const int wy = y0 - 10 + r, wx = x0 - 10 + cc;
+      const bool ok = wy >= 0 && wy < Hv && wx >= 0 && wx < Wv;
+      const int64_t o = ((int64_t)(img * Hv + wy) * Wv + wx) * 3 + ch;
+      wm[0][r][cc] = ok ? dmx[o] : 0.0f;
+      wm[1][r][cc] = ok ? dexx[o] : 0.0f;
+      wm[2][r][cc] = ok ? dexy[o] : 0.0f;
     }
     __syncthreads();
-    if (threadIdx.x < kSTW * (kSTH / 2)) {
-      float G[3][2];
+    for (int i = threadIdx.x; i < (kSTH + 10) * kSTW; i += 256) {
+      const int r = i / kSTW, cc = i % kSTW;
+      float a = 0, b = 0, c = 0;
 #pragma unroll
-      for (int qi = 0; qi < 3; ++qi) {
-        float col[12];
-#pragma unroll
-        for (int j = 0; j < 12; ++j) col[j] = hz[qi][ty + j][tx];
-#pragma unroll
-        for (int o = 0; o < 2; ++o) {
-          float v = 0;
-#pragma unroll
-          for (int k = 0; k < kWin; ++k) v += c_gauss[k] * col[o + 10 - k];
-          G[qi][o] = v;
-        }
+      for (int k = 0; k < kWin; ++k) {
+        const float g = c_gauss[k];
+        a += g * wm[0][r][cc + 10 - k];
+        b += g * wm[1][r][cc + 10 - k];
+        c += g * wm[2][r][cc + 10 - k];
       }
+      hz[0][r][cc] = a;
+      hz[1][r][cc] = b;
+      hz[2][r][cc] = c;
+    }
+    __syncthreads();
+    if (in) {
+      float G0 = 0, G1 = 0, G2 = 0;
 #pragma unroll
-      for (int o = 0; o < 2; ++o) {
-        const int x = x0 + tx, y = y0 + ty + o;
-        if (x < w && y < h) {
-          const int64_t pix = (int64_t)(img * h + y) * w + x;
-          const float pv = p[pix * 3 + ch], tv = t[pix * 3 + ch];
-          const float d = pv - tv;
-          const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
-          const float gs = G[0][o] + 2.0f * pv * G[1][o] + tv * G[2][o];
-          const float gr = (float)kL1W * sgn * inv_px - (float)kSsimW * gs * inv_win;
-          gout[o][ch] = gr;
-          if (grad) grad[pix * 3 + ch] = gr;
-          acc += fabs((double)d);
-        }
+      for (int k = 0; k < kWin; ++k) {
+        const float g = c_gauss[k];
+        G0 += g * hz[0][ty + 10 - k][tx];
+        G1 += g * hz[1][ty + 10 - k][tx];
+        G2 += g * hz[2][ty + 10 - k][tx];
       }
+      const float pv = p[pix * 3 + ch], tv = t[pix * 3 + ch];
+      const float d = pv - tv;
+      const float sgn = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
+      const float gs = G0 + 2.0f * pv * G1 + tv * G2;
+      const float gr = (float)kL1W * sgn * inv_px - (float)kSsimW * gs * inv_win;
+      gout[ch] = gr;
+      if (grad) grad[pix * 3 + ch] = gr;
+      acc += fabs((double)d);
     }
     __syncthreads();
   }
-  if (threadIdx.x < kSTW * (kSTH / 2) && gy8) {
-#pragma unroll
-    for (int o = 0; o < 2; ++o) {
-      const int x = x0 + tx, y = y0 + ty + o;
-      if (x < w && y < h) {
-        const int64_t pix = (int64_t)(img * h + y) * w + x;
-        float v[8] = {gout[o][0], gout[o][1], gout[o][2], 0, 0, 0, 0, 0};
-        *reinterpret_cast<uint4 *>(gy8 + pix * kGyCh) = pack8(v);
-      }
-    }
+  if (in && gy8) {
+    float v[8] = {gout[0], gout[1], gout[2], 0, 0, 0, 0, 0};
+    *reinterpret_cast<uint4 *>(gy8 + pix * kGyCh) = pack8(v);
   }
-  const double sum = block_sum(acc, red);
-  if (threadIdx.x == 0) part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = sum;
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
 }
 
 __global__ void k_loss_final(const double *ps, int nps, const double *pl, int npl, double n_px, double n_win,
