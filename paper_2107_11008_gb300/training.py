@@ -11,7 +11,6 @@ orders the calls and picks crops and batches.
 """
 from __future__ import annotations
 
-import time
 from dataclasses import dataclass
 
 import numpy as np
@@ -171,15 +170,3 @@ def denoise(net: D.UNet, x: torch.Tensor, add: torch.Tensor | None = None, batch
 def mse(a: torch.Tensor, b: torch.Tensor) -> float:
     """Mean squared error over the RGB channels (float64 on the device)."""
     return float(((a[..., :3].double() - b[..., :3].double()) ** 2).mean())
-
-
-def time_call(fn, reps: int = 3) -> float:
-    """Median wall time in seconds of fn() with a device synchronise on both sides."""
-    ts = []
-    for _ in range(reps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        fn()
-        torch.cuda.synchronize()
-        ts.append(time.perf_counter() - t0)
-    return float(np.median(ts))
