@@ -1,5 +1,6 @@
 // unet_conv.cuh -- persistent, warp-specialised 3x3 convolution (forward or data gradient) on
-// tcgen05 with TMA halo tiles, for rows whose width is a multiple of 128 pixels.
+// tcgen05 with TMA halo tiles, for rows whose width is a multiple of 128 pixels or divides 128,
+// and the same kernel in a pointwise mode (one tap: a contraction of each pixel's channels).
 //
 // A tile is 128 consecutive output pixels of one image row.  For each group of 8 input channels
 // the producer warp loads, with one TMA tensor copy, the 3 x 144 pixel neighbourhood of the tile
@@ -18,10 +19,17 @@
 // (zero-filled outside the image) into three slabs whose rows are exactly w pixels long, so that
 // tap (dy, dx) is again 128 consecutive 16-byte rows: slab dx read from row dy.
 //
+// Pointwise mode (ConvGeo.taps == 1): per group of 8 channels one TMA copy of the tile's own 128
+// pixels (whole 8-pixel blocks, no halo) and a single tap; with N <= 256 output columns it serves
+// the 2x2 stride-2 transposed convolution, whose columns are the four output pixels' channels.
+//
 // Warp roles (192 threads): warp 0 = TMA producer, warp 1 = MMA issuer (one thread each), warps
 // 2..5 = epilogue (TMEM -> registers -> epilogue functor).  Two shared-memory A stages and two
 // TMEM accumulators let the loads of tile i+1 and the epilogue of tile i-1 overlap the MMAs of
-// tile i.  Every wait is bounded; a timeout latches SC_STATUS_WATCHDOG and the CTA winds down.
+// tile i.  The single issuing thread is the kernel's critical path, so its loop does little
+// besides the MMAs: descriptors built once and advanced by 32-bit adds on their start field, the
+// abort flag read only inside waits that have not completed.  Every wait is bounded; a timeout
+// latches SC_STATUS_WATCHDOG and the CTA winds down.
 #pragma once
 #include "unet_gemm.cuh"
 

@@ -7,13 +7,14 @@
 // must have 8 consecutive pixels in each 16-byte row (K-major), while activations and gradients
 // are stored with 8 consecutive channels per 16 bytes.  Per tile of 128 pixels of one row, the
 // producer warp brings with TMA the 3 x 144 pixel neighbourhood of x (as the forward kernel does)
-// and the 128 pixels of gz; sixteen transposer warps build each 128-row block of the A operand (rows
-// (tap, c): the slab read at the tap's pixel offset) and the B operand (rows o) with
-// ldmatrix.trans (8 x 8 transposes from shared memory) into the padded canonical layout; one
-// thread issues the MMAs.  The accumulators of all row blocks (rows 9 cin + 1, 128 per block,
-// cout columns each, 32/64/128 apart) stay in TMEM across the CTA's whole range of tiles; at the end the
-// epilogue warps write them as this CTA's partial sums, reduced in a fixed order by
-// k_wgrad_reduce.  Every wait is bounded.
+// and the 128 pixels of gz; sixteen transposer warps build each 128-row block of the A operand
+// (rows (tap, c): the slab read at the tap's pixel offset, looked up in a per-CTA table of 8 x 8
+// units) and the B operand (rows o) with ldmatrix.trans (8 x 8 transposes from shared memory)
+// into the padded canonical layout; one thread issues the MMAs.  The accumulators of all row
+// blocks (rows 9 cin + 1, 128 per block, cout columns each, 32/64/128 apart) stay in TMEM across
+// the CTA's whole range of tiles; at the end the epilogue warps write them as this CTA's partial
+// sums into the layer's region of the workspace, reduced in a fixed order by k_wgrad_reduce.
+// Every wait is bounded.
 #pragma once
 #include "unet_conv.cuh"
 
