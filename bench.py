@@ -538,7 +538,8 @@ def run_reference(args):
 
     sc = S.glass_scene(0, width=args.res, height=args.res)
     # each step: a bounded sample of the frame; sized so that warmup + steps stay within minutes
-    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    # (and at most --cpu-seconds)
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup), args.cpu_seconds))
     vals, secs = [], []
     cb = None
     for i in range(args.warmup + args.steps):
