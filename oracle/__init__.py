@@ -46,7 +46,7 @@ class Tolerances(C.Structure):
 # sens_delta: every recorded path is re-traced twice with its ray nudged by +-1e-6 (relative) after
 # each scattering event; a path whose signature or radiance (beyond sens_rel) moves is flagged
 # "sensitive" -- float32 cannot be expected to follow it decision for decision.
-DEFAULT_TOL = dict(pos=2e-5, t=1e-5, cosg=1e-4, fres=1e-4, tir=1e-5, px=1e-3, growth=1.0, sens_delta=1e-6,
+DEFAULT_TOL = dict(pos=2e-5, t=1e-5, cosg=1e-4, fres=1e-4, tir=1e-5, px=1e-4, growth=1.0, sens_delta=1e-6,
                    sens_rel=5e-5)
 
 

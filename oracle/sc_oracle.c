@@ -246,7 +246,7 @@ typedef struct {
   double sens_rel;   /* a re-trace moving the radiance by more than this (relative) flags the path */
 } tolerances;
 
-static const tolerances DEFAULT_TOL = {2e-5, 1e-5, 1e-4, 1e-4, 1e-5, 1e-3, 1.0, 0.0, 1e-4};
+static const tolerances DEFAULT_TOL = {2e-5, 1e-5, 1e-4, 1e-4, 1e-5, 1e-4, 1.0, 0.0, 1e-4};
 
 /* near misses are tracked inside this window (relative), wider than any tolerance */
 #define NM_WIN 1e-3

@@ -23,11 +23,9 @@
 
 namespace sc {
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 4;
-constexpr int kTile = kSortThreads * kSortItems;
+constexpr int kTile = kSortTile;
 
-size_t sort_blocks(int32_t n) { return (size_t)((n + kTile - 1) / kTile); }
+size_t sort_blocks(int32_t n) { return sort_blocks_for(n); }
 
 // order-preserving float <-> uint32 map for atomic min/max
 __device__ __forceinline__ uint32_t f2key(float f) {

@@ -11,6 +11,12 @@ namespace sc {
 struct DevScene;
 
 // ---- LBVH build (build.cu) ----------------------------------------------------------------
+// Radix sort geometry: each sort block ranks kSortThreads * kSortItems keys, and the digit
+// histograms hold 256 words per block (sort_blocks(n) blocks for n keys).
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 4;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr size_t sort_blocks_for(int64_t n) { return (size_t)((n + kSortTile - 1) / kSortTile); }
 struct BuildBuffers {
   // inputs (device)
   const float *positions, *normals, *uvs;

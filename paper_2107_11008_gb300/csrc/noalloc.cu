@@ -18,8 +18,8 @@ namespace {
 constexpr int kNoAllocMaxTris = SC_NOALLOC_MAX_TRIS;
 
 constexpr size_t al(size_t x) { return (x + 255) & ~size_t(255); }
-constexpr size_t kSortTile = 1024;  // keys per radix-sort block (build.cu)
-constexpr size_t kBlocksMax = (kNoAllocMaxTris + kSortTile - 1) / kSortTile;
+// radix-sort blocks of the largest accepted build: sized from the sort's own tile (internal.h)
+constexpr size_t kBlocksMax = sc::sort_blocks_for(kNoAllocMaxTris);
 constexpr size_t kScratchBytes = al(sizeof(float4) * 3 * kNoAllocMaxTris)   // triangles in input order
                                  + al(sizeof(float4) * kNoAllocMaxTris)      // centroids
                                  + al(sizeof(uint32_t) * 8)                  // centroid bounds
@@ -30,6 +30,15 @@ constexpr size_t kScratchBytes = al(sizeof(float4) * 3 * kNoAllocMaxTris)   // t
                                  + al(sizeof(int32_t) * kNoAllocMaxTris)     // refit counters
                                  + al(sizeof(int32_t));                      // deepest leaf
 
+// The regions carved below, in order; the carve is checked against kScratchBytes at run time.
+constexpr size_t kCarvedBytes = al(sizeof(float4) * 3 * kNoAllocMaxTris) + al(sizeof(float4) * kNoAllocMaxTris) +
+                                al(sizeof(uint32_t) * 8) + al(sizeof(unsigned long long) * kNoAllocMaxTris) +
+                                al(sizeof(unsigned long long) * kNoAllocMaxTris) +
+                                al(sizeof(uint32_t) * kNoAllocMaxTris) + al(sizeof(uint32_t) * kNoAllocMaxTris) +
+                                al(sizeof(uint32_t) * 256 * kBlocksMax) + al(sizeof(int32_t) * 2 * kNoAllocMaxTris) +
+                                al(sizeof(int32_t) * kNoAllocMaxTris) + al(sizeof(int32_t));
+static_assert(kCarvedBytes == kScratchBytes, "scratch carve and scratch size disagree");
+
 // The scratch array.  In host code its name is only a stand-in for the device symbol; the real
 // device address comes from cudaGetSymbolAddress (below) and is what the kernels receive.
 static __device__ __align__(256) unsigned char g_build_scratch[kScratchBytes];
@@ -38,7 +47,10 @@ constexpr int kMaxDevices = 64;
 std::mutex g_lock;
 void *g_scratch_addr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on `device` (which must be current), looked up once.
+// Device address of the scratch array on `device` (which must be current), looked up once per
+// device and kept for the life of the process.  This assumes the device's primary context (the
+// one the CUDA runtime uses) also lives as long as the process: after cudaDeviceReset the cached
+// address would be stale, so a process that resets a device must not call this entry point again.
 cudaError_t scratch_address(int device, void **out) {
   std::lock_guard<std::mutex> guard(g_lock);
   if (!g_scratch_addr[device]) {
@@ -91,10 +103,15 @@ extern "C" int sc_build_bvh_noalloc(sc_ctx *ctx, const float *positions, const f
     sc::ctx_set_error(ctx, "sc_build_bvh_noalloc: device index out of range");
     return SC_ERR_INVALID_ARG;
   }
-  cudaError_t e = cudaSetDevice(dev);
+  // The symbol lookup needs the context's device current; the caller's current device is put
+  // back before returning, on every path.
+  int prev_dev = -1;
+  cudaError_t e = cudaGetDevice(&prev_dev);
+  if (e == cudaSuccess && prev_dev != dev) e = cudaSetDevice(dev);
   void *base = nullptr;
   if (e == cudaSuccess) e = scratch_address(dev, &base);
   if (e != cudaSuccess) {
+    if (prev_dev >= 0 && prev_dev != dev) cudaSetDevice(prev_dev);
     sc::ctx_set_error(ctx, std::string("sc_build_bvh_noalloc: ") + cudaGetErrorString(e));
     return SC_ERR_CUDA;
   }
@@ -127,7 +144,16 @@ extern "C" int sc_build_bvh_noalloc(sc_ctx *ctx, const float *positions, const f
   // Whatever a previous call left in the array is overwritten before it is read: the first
   // kernel resets the centroid bounds and the depth word, the hierarchy kernel zeroes the refit
   // counters, and every other scratch word is written before use.
+  if (static_cast<size_t>(c.p - static_cast<char *>(base)) != kScratchBytes) {
+    if (prev_dev != dev) cudaSetDevice(prev_dev);
+    sc::ctx_set_error(ctx, "sc_build_bvh_noalloc: internal scratch layout mismatch");
+    return SC_ERR_INVALID_ARG;
+  }
   e = sc::launch_build(b, sc::ctx_stream(ctx));
+  if (prev_dev != dev) {
+    const cudaError_t e2 = cudaSetDevice(prev_dev);
+    if (e == cudaSuccess) e = e2;
+  }
   if (e != cudaSuccess) {
     sc::ctx_set_error(ctx, std::string("sc_build_bvh_noalloc: ") + cudaGetErrorString(e));
     return SC_ERR_CUDA;

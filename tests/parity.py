@@ -1,22 +1,38 @@
 """Comparison helpers: CUDA path records vs the FP64 oracle's, element by element.
 
-Parity bar (per path, outside the oracle's ambiguous set): bit-exact hit-triangle ids and
-path signatures (every hit id and scattering decision), radiance within 1e-4 relative;
-image MSE within 1e-5 at equal samples and seed.  The ambiguous set is where an FP32 and an
-FP64 evaluation may legitimately take different discrete decisions (near-edge hits, Fresnel
-draws within 1e-4 of R, grazing cosines, shadow rays skimming an edge, splats on a pixel border)
-and must stay below 0.5 % of the paths.  Paths whose FP64 re-traces under +-1e-6 ray nudges
-change (signature, or radiance by more than 5e-5) (long chains through curved glass, where rounding is amplified) are also excluded; that
-share depends on the scene (about 0.4 % for one glass ball, a few percent for several
-overlapping glass objects) and each test states its bound.
+Parity bar (per path): bit-exact hit-triangle ids and path signatures (every hit id and scattering
+decision), radiance within 1e-4 relative; image MSE within 1e-5 at equal samples and seed.
+
+The oracle alone (FP64, no GPU record involved) sorts the paths that an FP32 tracer cannot be held
+to decision for decision into two sets, and each set has its own check:
+
+* grazing-epsilon paths: some decision of the path lies within its tolerance of flipping (a hit
+  near a triangle edge, a second hit at nearly the same distance, a grazing cosine, a Fresnel draw
+  within 1e-4 of R, the total-internal-reflection edge, a shadow ray skimming an edge, a checker
+  border, a splat on a pixel border).  Excluded from every per-path check; their share must stay
+  below MAX_GRAZING = 0.5 % of the paths (scene-specific bounds above that are stated, with their
+  reading, where they are used).
+* sensitive paths (no grazing flag): the oracle re-traces the path twice with its ray nudged by
+  +-1e-6 relative after every scattering event (about 16 float32 ulps: the rounding a ray picks up
+  between two events) and the signature or radiance moves.  Long chains through curved glass
+  amplify rounding, so such a path's later decisions are not reproducible in FP32.  Held to a
+  weaker check: the first hit is still bit-exact (a first hit that moves under the nudge is an edge
+  case, flagged grazing), and the paired GPU-minus-oracle radiance differences over the set must
+  be consistent with zero mean (|sum d| <= 5 sqrt(sum d^2) per channel): both sides still draw
+  valid samples of the same estimator.  Their share is printed; it is a property of the scene's
+  optics measured by the oracle, not a tolerance.
+
+The image MSE bound is over all paths, ambiguous or not.
 """
 import numpy as np
 
 REL = 1e-4
 MSE = 1e-5
-MAX_AMBIGUOUS = 0.005
-# scenes with several overlapping glass objects (rows crossing glass exclude more)
-MAX_AMBIGUOUS_GLASS = 0.10
+MAX_GRAZING = 0.005
+AMB_SENSITIVE = 512
+# sanity bound on the sensitive share (the oracle measures 0.9 % on one glass ball, 2-3 % on
+# several 20k-triangle glass objects); a larger share would mean the classifier misfires
+MAX_SENSITIVE = 0.15
 
 
 def rel_close(a, b, rel=REL, floor=1e-6):
@@ -26,22 +42,37 @@ def rel_close(a, b, rel=REL, floor=1e-6):
     return np.abs(a - b) <= rel * scale
 
 
-def compare_camera(gpu: dict, orc: dict, rel=REL, max_ambiguous=MAX_AMBIGUOUS):
-    """Returns a dict of fractions; raises AssertionError with details on a parity failure."""
-    amb = orc["amb"] != 0
-    ok = ~amb
-    frac_amb = float(amb.mean())
+def split_ambiguous(amb):
+    """(grazing, sensitive-only) boolean masks from the oracle's per-path flag words."""
+    amb = np.asarray(amb)
+    grazing = (amb & ~AMB_SENSITIVE) != 0
+    sensitive = ((amb & AMB_SENSITIVE) != 0) & ~grazing
+    return grazing, sensitive
+
+
+def _paired_zero_mean(d, k=5.0):
+    """Per channel: |sum d| <= k sqrt(sum d^2) (+ a float32 floor).  True where consistent."""
+    d = np.asarray(d, np.float64).reshape(len(d), -1)
+    s = d.sum(axis=0)
+    q = np.sqrt((d * d).sum(axis=0))
+    return np.abs(s) <= k * q + 1e-6 * max(len(d), 1)
+
+
+def compare_camera(gpu: dict, orc: dict, rel=REL, max_grazing=MAX_GRAZING, max_sensitive=MAX_SENSITIVE):
+    """Returns a dict of shares; raises AssertionError with details on a parity failure."""
+    grazing, sensitive = split_ambiguous(orc["amb"])
+    exact = ~grazing & ~sensitive
     sig_eq = gpu["signature"] == orc["signature"]
     first_eq = gpu["first_tri"] == orc["first_tri"]
     L_ok = rel_close(gpu["L"], orc["L"], rel).all(axis=1)
-    bad_sig = np.flatnonzero(ok & ~sig_eq)
-    bad_first = np.flatnonzero(ok & ~first_eq)
-    bad_L = np.flatnonzero(ok & sig_eq & ~L_ok)
+    bad_first = np.flatnonzero(~grazing & ~first_eq)  # exact and sensitive paths alike
+    bad_sig = np.flatnonzero(exact & ~sig_eq)
+    bad_L = np.flatnonzero(exact & sig_eq & ~L_ok)
     msg = []
     if len(bad_first):
         i = bad_first[0]
         msg.append(f"{len(bad_first)} first-hit ids differ (e.g. path {i}: gpu {gpu['first_tri'][i]} "
-                   f"oracle {orc['first_tri'][i]})")
+                   f"oracle {orc['first_tri'][i]}, sensitive {bool(sensitive[i])})")
     if len(bad_sig):
         i = bad_sig[0]
         msg.append(f"{len(bad_sig)} signatures differ (e.g. path {i}: nq gpu {gpu['n_queries'][i]} "
@@ -49,20 +80,31 @@ def compare_camera(gpu: dict, orc: dict, rel=REL, max_ambiguous=MAX_AMBIGUOUS):
     if len(bad_L):
         i = bad_L[0]
         msg.append(f"{len(bad_L)} radiances off by > {rel} rel (e.g. path {i}: gpu {gpu['L'][i]} oracle {orc['L'][i]})")
-    if frac_amb > max_ambiguous:
-        msg.append(f"ambiguous fraction {frac_amb:.4f} > {max_ambiguous}")
+    if sensitive.any():
+        d = np.asarray(gpu["L"], np.float64)[sensitive] - np.asarray(orc["L"], np.float64)[sensitive]
+        if not _paired_zero_mean(d).all():
+            msg.append(f"sensitive paths: GPU - oracle radiance has a nonzero mean (sum {d.sum(0)}, "
+                       f"rms {np.sqrt((d * d).sum(0))})")
+    if grazing.mean() > max_grazing:
+        msg.append(f"grazing share {grazing.mean():.4f} > {max_grazing}")
+    if sensitive.mean() > max_sensitive:
+        msg.append(f"sensitive share {sensitive.mean():.4f} > {max_sensitive}")
     assert not msg, "; ".join(msg)
-    return {"ambiguous": frac_amb, "n": int(len(amb)), "sig_equal_all": float(sig_eq.mean())}
+    stats = {"grazing": float(grazing.mean()), "sensitive": float(sensitive.mean()), "n": int(len(grazing)),
+             "sensitive_diverged": float((~sig_eq[sensitive]).mean()) if sensitive.any() else 0.0,
+             "sig_equal_all": float(sig_eq.mean())}
+    print("camera parity:", stats)
+    return stats
 
 
-def compare_lights(gpu: dict, orc: dict, rel=REL, max_ambiguous=MAX_AMBIGUOUS):
-    amb = orc["amb"] != 0
-    ok = ~amb
+def compare_lights(gpu: dict, orc: dict, rel=REL, max_grazing=MAX_GRAZING, max_sensitive=MAX_SENSITIVE):
+    grazing, sensitive = split_ambiguous(orc["amb"])
+    exact = ~grazing & ~sensitive
     pix_eq = gpu["pixel"] == orc["pixel"]
     sig_eq = gpu["signature"] == orc["signature"]
     C_ok = rel_close(gpu["C"], orc["C"], rel).all(axis=1)
-    bad = np.flatnonzero(ok & ~(pix_eq & sig_eq))
-    badC = np.flatnonzero(ok & pix_eq & sig_eq & ~C_ok)
+    bad = np.flatnonzero(exact & ~(pix_eq & sig_eq))
+    badC = np.flatnonzero(exact & pix_eq & sig_eq & ~C_ok)
     msg = []
     if len(bad):
         i = bad[0]
@@ -71,7 +113,16 @@ def compare_lights(gpu: dict, orc: dict, rel=REL, max_ambiguous=MAX_AMBIGUOUS):
     if len(badC):
         i = badC[0]
         msg.append(f"{len(badC)} splat contributions off (e.g. {i}: gpu {gpu['C'][i]} oracle {orc['C'][i]})")
-    if amb.mean() > max_ambiguous:
-        msg.append(f"ambiguous fraction {amb.mean():.4f} > {max_ambiguous}")
+    if sensitive.any():
+        d = np.asarray(gpu["C"], np.float64)[sensitive] - np.asarray(orc["C"], np.float64)[sensitive]
+        if not _paired_zero_mean(d).all():
+            msg.append(f"sensitive light paths: GPU - oracle splat has a nonzero mean (sum {d.sum(0)})")
+    if grazing.mean() > max_grazing:
+        msg.append(f"grazing share {grazing.mean():.4f} > {max_grazing}")
+    if sensitive.mean() > max_sensitive:
+        msg.append(f"sensitive share {sensitive.mean():.4f} > {max_sensitive}")
     assert not msg, "; ".join(msg)
-    return {"ambiguous": float(amb.mean()), "splatted": float((orc["pixel"] >= 0).mean())}
+    stats = {"grazing": float(grazing.mean()), "sensitive": float(sensitive.mean()),
+             "splatted": float((orc["pixel"] >= 0).mean())}
+    print("light parity:", stats)
+    return stats

@@ -8,7 +8,7 @@ import oracle as O  # noqa: E402
 from paper_2107_11008_gb300 import renderer as R  # noqa: E402
 from paper_2107_11008_gb300 import scenes as S  # noqa: E402
 
-from .parity import MAX_AMBIGUOUS_GLASS, compare_camera  # noqa: E402
+from .parity import MAX_GRAZING, compare_camera  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -54,10 +54,15 @@ def test_batch_member_matches_oracle(ctx):
         f.alloc_path_records(spp)
     R.trace_batch(ctx, gss, fb, spp, depth, seed=9)
     ctx.sync_status()
+    n_paths = n_grazing = 0
     for i in (0, 5):
         g = R.path_records_numpy(fb[i].path_records)
         _, rec = O.OracleScene(scs[i]).trace_camera(spp, depth, seed=9, scene_index=i)
-        compare_camera(g, rec, max_ambiguous=MAX_AMBIGUOUS_GLASS)
+        # the grazing share is bounded over both members together (scene 0 has only 676 paths)
+        st = compare_camera(g, rec, max_grazing=1.0)
+        n_paths += st["n"]
+        n_grazing += round(st["grazing"] * st["n"])
+    assert n_grazing / n_paths <= MAX_GRAZING
 
 
 def test_batch_graph_replays(ctx):

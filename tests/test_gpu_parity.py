@@ -15,7 +15,13 @@ from paper_2107_11008_gb300 import native as N  # noqa: E402
 from paper_2107_11008_gb300 import renderer as R  # noqa: E402
 from paper_2107_11008_gb300 import scenes as S  # noqa: E402
 
-from .parity import MAX_AMBIGUOUS_GLASS, MSE, compare_camera, compare_lights, rel_close  # noqa: E402
+from .parity import MSE, compare_camera, compare_lights, rel_close  # noqa: E402
+
+# The 512^2 scene's meshes have ~20k triangles each: the tolerance band around triangle edges
+# (2e-5 max(1, |p|)) covers a larger share of their surface, and a path through glass meets several
+# of them.  The oracle alone measures 0.76 % grazing paths on the sampled rows below (1.25 % over
+# the frame, tests/test_oracle_pins.py); this scene's bound is 2 %.
+MAX_GRAZING_DENSE_MESH = 0.02
 
 pytestmark = pytest.mark.gpu
 
@@ -298,7 +304,7 @@ def test_camera_parity_ball_on_plane(ctx):
     _, fr = _render(ctx, sc, spp, depth)
     g = R.path_records_numpy(fr.path_records)
     acc, rec = O.OracleScene(sc).trace_camera(spp, depth)
-    stats = compare_camera(g, rec, max_ambiguous=0.02)
+    compare_camera(g, rec)
     img = fr["direct"][..., :3].cpu().numpy()
     assert np.mean((img - acc / spp) ** 2) <= MSE
     # the glass is actually exercised
@@ -313,7 +319,7 @@ def test_camera_parity_dispersive_glass_scene_ragged(ctx):
     _, fr = _render(ctx, sc, spp, depth, n_bins=nb, seed=11)
     g = R.path_records_numpy(fr.path_records)
     acc, rec = O.OracleScene(sc).trace_camera(spp, depth, nbins=nb, seed=11)
-    compare_camera(g, rec, max_ambiguous=MAX_AMBIGUOUS_GLASS)
+    compare_camera(g, rec)
     img = fr["direct"][..., :3].cpu().numpy()
     assert np.mean((img - acc / spp) ** 2) <= MSE
     assert len(np.unique(rec["bin"])) == nb
@@ -336,7 +342,7 @@ def test_light_parity_rect_light_dispersion(ctx):
     _, fr = _render(ctx, sc, 0, 12, n_bins=8, n_light=n, seed=3)
     g = R.light_records_numpy(fr.light_records)
     acc, rec = O.OracleScene(sc).trace_lights(n, 12, nbins=8, seed=3)
-    st = compare_lights(g, rec, max_ambiguous=MAX_AMBIGUOUS_GLASS)
+    st = compare_lights(g, rec)
     assert st["splatted"] > 0.002
     img = fr["accum_caustic"][..., :3].cpu().numpy() / n
     assert np.mean((img - acc / n) ** 2) <= MSE
@@ -352,7 +358,7 @@ def test_light_parity_guided_emission(ctx, which):
     _, fr = _render(ctx, sc, 0, depth, n_bins=nb, n_light=n, seed=5, guide=guide)
     g = R.light_records_numpy(fr.light_records)
     acc, rec = O.OracleScene(sc).trace_lights(n, depth, nbins=nb, seed=5, guide=guide)
-    st = compare_lights(g, rec, max_ambiguous=MAX_AMBIGUOUS_GLASS)
+    st = compare_lights(g, rec)
     assert st["splatted"] > 0.005  # the ball hides most of its own caustic from this camera
     img = fr["accum_caustic"][..., :3].cpu().numpy() / n
     assert np.mean((img - acc / n) ** 2) <= MSE
@@ -506,4 +512,4 @@ def test_full_size_glass_scene_sampled_rows(ctx):
     for y in rows:
         _, rec = orc.trace_camera(spp, depth, nbins=nb, window=(0, 512, y, y + 1))
         sel = slice(y * 512 * spp, (y + 1) * 512 * spp)
-        compare_camera({k: v[sel] for k, v in g.items()}, rec, max_ambiguous=MAX_AMBIGUOUS_GLASS)
+        compare_camera({k: v[sel] for k, v in g.items()}, rec, max_grazing=MAX_GRAZING_DENSE_MESH)
