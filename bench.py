@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--light-paths", type=int, default=1 << 22)
     ap.add_argument("--res", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the sub-results (cfg1 frame, batch64, U-Net training) of the default line")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--den-ratio", type=int, default=16, help="denoise workload: light paths per camera sample")
     ap.add_argument("--den-steps", type=int, default=48000, help="denoise workload: training steps")
@@ -69,15 +71,14 @@ def parse():
     return ap.parse_args()
 
 
-def run_batch(args):
-    """64 randomised dataset scenes traced in one persistent CUDA-graph launch vs one launch per scene."""
+def measure_batch(steps, warmup, local, world):
+    """64 randomised dataset scenes traced in one persistent CUDA-graph launch vs one launch per scene.
+    Returns (batch ms per launch, sequential ms per pass, info dict)."""
     import torch
 
     from paper_2107_11008_gb300 import renderer as R
     from paper_2107_11008_gb300 import scenes as S
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n, spp, depth = 64, 64, 12
     t0 = time.perf_counter()
@@ -93,39 +94,57 @@ def run_batch(args):
     frames = [R.Frame(s.camera.width, s.camera.height, device=dev, fields=("accum_camera",)) for s in scs]
     batch = R.Batch(ctx, gss, frames, spp, depth, seed=3)
     stream = torch.cuda.current_stream(dev)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.launch()
     ctx.sync_status()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     sampler = ClockSampler(local)
     ev[0].record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         batch.launch()
     ev[1].record(stream)
     torch.cuda.synchronize(dev)
-    batch_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    batch_ms = ev[0].elapsed_time(ev[1]) / steps
     # the same work as one plain launch per scene
     ev[0].record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         for i, (g, f) in enumerate(zip(gss, frames)):
             R.trace_camera(ctx, g, f, spp, depth, seed=3, scene_index=i)
     ev[1].record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
-    seq_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    seq_ms = ev[0].elapsed_time(ev[1]) / steps
     ctx.sync_status()
     paths = sum(s.camera.width * s.camera.height for s in scs) * spp
+    info = {"triangles": sum(s.n_tris for s in scs), "camera_paths": paths, "scene_generation_s": gen_s,
+            "lbvh_build_s": build_s, "clocks": clocks}
+    batch.close()
+    for g in gss:
+        g.free()
+    ctx.close()
+    return batch_ms, seq_ms, info
+
+
+BATCH_WORKLOAD = ("batch64: scenes.random_scene(0..63): 1-6 glass objects, 1k-200k tris, resolution from "
+                  "{128,256,512,1024}^2, IOR U[1.33,1.9], 64 spp, depth 12")
+
+
+def run_batch(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    batch_ms, seq_ms, info = measure_batch(args.steps, args.warmup, local, world)
+    paths = info["camera_paths"]
     value = world * paths / (batch_ms * 1e-3) / 1e6
     if rank == 0:
         line = {"metric": "Mpaths/s of 64 randomised scenes in one graph-captured launch", "value": value,
                 "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "batch64: scenes.random_scene(0..63): 1-6 glass objects, 1k-200k tris, "
-                                       "resolution from {128,256,512,1024}^2, IOR U[1.33,1.9], 64 spp, depth 12",
-                           "triangles": sum(s.n_tris for s in scs), "camera_paths": paths},
+                "config": {"workload": BATCH_WORKLOAD, "triangles": info["triangles"], "camera_paths": paths},
                 "sequential_launches": {"ms_per_step": seq_ms, "value": world * paths / (seq_ms * 1e-3) / 1e6},
-                "batch_over_sequential": seq_ms / batch_ms, "scene_generation_s": gen_s, "lbvh_build_s": build_s,
-                "gpu_launches": args.steps, "clocks": clocks}
+                "batch_over_sequential": seq_ms / batch_ms, "scene_generation_s": info["scene_generation_s"],
+                "lbvh_build_s": info["lbvh_build_s"], "gpu_launches": args.steps, "clocks": info["clocks"]}
         print(json.dumps(line), flush=True)
 
 
@@ -192,9 +211,10 @@ def unet_cpu_baseline(seconds, h=64, w=64):
                       f"up to {os.cpu_count()} BLAS threads), scaled to 256^2 images by pixel count"}
 
 
-def run_unet_train(args):
+def measure_unet_train(steps, warmup, local, world, e2e=True):
     """Training steps of the BF16 U-Net on batches of 16 render pairs at 256^2 (config-1-type scenes:
-    4 spp + AOV input, 256 spp target; the step's work does not depend on the pixel values)."""
+    4 spp + AOV input, 256 spp target; the step's work does not depend on the pixel values).
+    Returns a dict of timings (ms per step, forward ms, e2e s per step) and sizes."""
     import torch
 
     from paper_2107_11008_gb300 import denoiser as D
@@ -202,8 +222,7 @@ def run_unet_train(args):
     from paper_2107_11008_gb300 import scenes as S
     from paper_2107_11008_gb300 import training as T
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
+    rank = int(os.environ.get("RANK", "0"))
     dev = torch.device("cuda", local)
     n, hw = 16, 256
     stream = torch.cuda.current_stream(dev)
@@ -215,63 +234,83 @@ def run_unet_train(args):
     x, t = pairs.x.contiguous(), pairs.target.contiguous()
     loss = torch.empty(1, dtype=torch.float32, device=dev)
     lr = 1e-4
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         net.train_step(x, t, lr, loss)
     torch.cuda.synchronize(dev)
     ctx.sync_status()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     sampler = ClockSampler(local)
     ev[0].record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         net.train_step(x, t, lr, loss)
     ev[1].record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
     ctx.sync_status()
-    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    ms = ev[0].elapsed_time(ev[1]) / steps
     # forward alone (inference throughput of the same batch)
     ev[0].record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         net.forward(x)
     ev[1].record(stream)
     torch.cuda.synchronize(dev)
-    fwd_ms = ev[0].elapsed_time(ev[1]) / args.steps
-    # end to end: the batch from pinned host memory each step, the loss read back
-    xh, th = x.cpu().pin_memory(), t.cpu().pin_memory()
-    lh = torch.empty(1, dtype=torch.float32, pin_memory=True)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        x.copy_(xh, non_blocking=True)
-        t.copy_(th, non_blocking=True)
-        net.train_step(x, t, lr, loss)
-        lh.copy_(loss, non_blocking=True)
+    fwd_ms = ev[0].elapsed_time(ev[1]) / steps
+    out = {"ms": ms, "forward_ms": fwd_ms, "batch": n, "hw": hw, "clocks": clocks}
+    if e2e:
+        # end to end: the batch from pinned host memory each step, the loss read back
+        xh, th = x.cpu().pin_memory(), t.cpu().pin_memory()
+        lh = torch.empty(1, dtype=torch.float32, pin_memory=True)
         torch.cuda.synchronize(dev)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    value = world * n / (ms * 1e-3)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            x.copy_(xh, non_blocking=True)
+            t.copy_(th, non_blocking=True)
+            net.train_step(x, t, lr, loss)
+            lh.copy_(loss, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        out["e2e_s"] = (time.perf_counter() - t0) / steps
+        out["h2d"] = (xh.numel() + th.numel()) * 4
+    net.close()
+    ctx.close()
+    return out
+
+
+def unet_roofline(ms, n, hw):
     flops = 2.0 * unet_train_macs(hw, hw) * n
-    pk = peaks()
-    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    peak = peaks().get("bf16_tflops_sustained", 1700.0)
     achieved = flops / (ms * 1e-3) / 1e12
+    return {"kernel": "all U-Net GEMMs of the step (tcgen05 BF16, FP32 accumulate)", "bound": "tensor",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": UNET_STEP_DRAM_BYTES, "traffic_unit": "bytes per step (ncu)", "flops_per_step": flops,
+            "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
+
+
+def run_unet_train(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    r = measure_unet_train(args.steps, args.warmup, local, world)
+    n, hw, ms = r["batch"], r["hw"], r["ms"]
+    value = world * n / (ms * 1e-3)
     if rank == 0:
         cb = None if args.no_cpu_baseline or world > 1 else unet_cpu_baseline(min(args.cpu_seconds, 15.0))
         line = {"metric": "U-Net training images/s (16 x 256^2 per step)", "value": value, "unit": "images/s",
                 "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
                 "data": "synthetic (render pairs of scenes.denoise_scene)",
-                "config": {"workload": "unet_train: U-Net 11->3, widths 32/48/64/128 (585,363 params), batch 16 of "
-                                       "256^2, loss 0.16 L1 + 0.84 (1 - SSIM 11x11), Adam",
-                           "l2": "working set ~1.5 GB > L2 (no flush)", "parallelism": f"replicas x{world}"},
-                "forward_ms": fwd_ms, "forward_images_s": world * n / (fwd_ms * 1e-3),
-                "roofline": {"kernel": "all U-Net GEMMs of the step (tcgen05 BF16, FP32 accumulate)", "bound": "tensor",
-                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                             "traffic": UNET_STEP_DRAM_BYTES, "traffic_unit": "bytes per step (ncu)",
-                             "flops_per_step": flops,
-                             "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"},
-                "e2e": {"value": world * n / e2e_s, "unit": "images/s",
-                        "h2d_bytes_per_step": (xh.numel() + th.numel()) * 4, "d2h_bytes_per_step": 4},
-                "gpu_launches": UNET_TRAIN_LAUNCHES * args.steps, "clocks": clocks, "cpu_baseline": cb}
+                "config": {"workload": UNET_WORKLOAD, "l2": "working set ~1.5 GB > L2 (no flush)",
+                           "parallelism": f"replicas x{world}"},
+                "forward_ms": r["forward_ms"], "forward_images_s": world * n / (r["forward_ms"] * 1e-3),
+                "roofline": unet_roofline(ms, n, hw),
+                "e2e": {"value": world * n / r["e2e_s"], "unit": "images/s", "h2d_bytes_per_step": r["h2d"],
+                        "d2h_bytes_per_step": 4},
+                "gpu_launches": UNET_TRAIN_LAUNCHES * args.steps, "clocks": r["clocks"], "cpu_baseline": cb}
         print(json.dumps(line), flush=True)
+
+
+UNET_WORKLOAD = ("unet_train: U-Net 11->3, widths 32/48/64/128 (585,363 params), batch 16 of 256^2, loss 0.16 L1 "
+                 "+ 0.84 (1 - SSIM 11x11), Adam")
 
 
 def run_denoise(args):
@@ -530,6 +569,92 @@ def cpu_baseline(scene, spp_full, nl_full, seconds, depth=12, nbins=8):
             "seconds": t_cam + t_light}
 
 
+def measure_peaks(ctx, dev, stream, repeats=5):
+    """FP32 FMA throughput (TFLOP/s) and L2 read bandwidth (GB/s) on this device, best of
+    `repeats` launches of the library's measurement kernels, each sized to about 20 ms."""
+    import torch
+
+    from paper_2107_11008_gb300 import native as N
+
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def best(launch):
+        out = []
+        for _ in range(repeats):
+            ev[0].record(stream)
+            work = launch()
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            out.append(work / (ev[0].elapsed_time(ev[1]) * 1e-3))
+        return max(out)
+
+    iters = 1 << 14
+    N.sc_peak_fma(ctx.handle, iters, sink.data_ptr())  # warm-up
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    N.sc_peak_fma(ctx.handle, iters, sink.data_ptr())
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    iters = max(16, int(iters * 20.0 / max(ev[0].elapsed_time(ev[1]), 1e-3)) // 16 * 16)
+    fma = best(lambda: N.sc_peak_fma(ctx.handle, iters, sink.data_ptr())) / 1e12
+    nbytes = 32 << 20  # resident in the 129 MB L2
+    buf = torch.ones(nbytes // 4, dtype=torch.float32, device=dev)
+    reps = 64
+    N.sc_peak_l2_read(ctx.handle, buf.data_ptr(), nbytes, reps, sink.data_ptr())
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    N.sc_peak_l2_read(ctx.handle, buf.data_ptr(), nbytes, reps, sink.data_ptr())
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    reps = max(1, int(reps * 20.0 / max(ev[0].elapsed_time(ev[1]), 1e-3)))
+    l2 = best(lambda: N.sc_peak_l2_read(ctx.handle, buf.data_ptr(), nbytes, reps, sink.data_ptr())) / 1e9
+    return {"fp32_tflops": fma, "l2_read_gbs": l2,
+            "how": f"sc_peak_fma ({iters} steps x 8 chains x SMs x 2048 threads) and sc_peak_l2_read (32 MB x {reps} "
+                   "passes, L1 bypassed), best of 5 launches of ~20 ms each, CUDA events, just before the timed region"}
+
+
+def measure_cfg1(local, steps=20, warmup=3):
+    """The 64x64 parity workload as a frame: LBVH build + 16 spp camera paths (depth 8) + resolve."""
+    import torch
+
+    from paper_2107_11008_gb300 import renderer as R
+    from paper_2107_11008_gb300 import scenes as S
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sc = S.ball_on_plane()
+    ctx = R.Context(local, stream)
+    arrays = R.SceneArrays(sc, dev)
+    frame = R.Frame(sc.camera.width, sc.camera.height, device=dev)
+    spp, depth = 16, 8
+
+    def frame_once():
+        gs = R.GpuScene(ctx, arrays)
+        frame.zero_accumulators()
+        R.trace_camera(ctx, gs, frame, spp, depth)
+        R.resolve(ctx, gs, frame, spp, 0)
+        gs.free()
+
+    for _ in range(warmup):
+        frame_once()
+    ctx.sync_status()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(steps):
+        frame_once()
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    ctx.sync_status()
+    ms = ev[0].elapsed_time(ev[1]) / steps
+    paths = sc.camera.width * sc.camera.height * spp
+    ctx.close()
+    return {"workload": "cfg1 ball_on_plane: 64^2, glass icosphere 1280 tris on a plane, point light, 16 spp, depth 8, "
+                        "LBVH build + camera + resolve per frame (latency-bound)",
+            "ms_per_frame": ms, "frames_per_s": 1e3 / ms, "camera_mpaths_s": paths / (ms * 1e-3) / 1e6,
+            "steps": steps, "warmup": warmup}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -632,6 +757,8 @@ def main():
     R.N.sc_set_counters(ctx.handle, None)
     gs.free()
 
+    mp = measure_peaks(ctx, dev, stream)
+
     # timed region: K steps, L2 flushed between steps, CUDA events on the launching stream
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     if world > 1:
@@ -681,12 +808,44 @@ def main():
     e2e_value = world * paths_per_step / e2e_s / 1e6
 
     pk = peaks()
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
     cam_s = statistics.mean(cam_ms) * 1e-3
     cam_flops = cam_counts[1] * FLOPS_PER_NODE + cam_counts[2] * FLOPS_PER_TRI
     cam_bytes = cam_counts[1] * BYTES_PER_NODE + cam_counts[2] * BYTES_PER_TRI
-    achieved = cam_flops / cam_s / 1e12
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+    bounds = {
+        "fp32": {"achieved": cam_flops / cam_s / 1e12, "peak": mp["fp32_tflops"], "unit": "TFLOP/s",
+                 "per_launch": cam_flops},
+        "l2": {"achieved": cam_bytes / cam_s / 1e9, "peak": mp["l2_read_gbs"], "unit": "GB/s",
+               "per_launch": cam_bytes},
+        "hbm": {"achieved": CAMERA_DRAM_BYTES / cam_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "per_launch": CAMERA_DRAM_BYTES},
+    }
+    for b in bounds.values():
+        b["frac"] = b["achieved"] / b["peak"]
+    # the attainable rate is the minimum over the three ceilings: the binding one has the largest fraction
+    bind = max(bounds, key=lambda k: bounds[k]["frac"])
+    roofline = {"kernel": "k_trace_camera", "bound": {"fp32": "alu", "l2": "l2", "hbm": "hbm"}[bind],
+                "achieved": bounds[bind]["achieved"], "peak": bounds[bind]["peak"], "unit": bounds[bind]["unit"],
+                "frac": bounds[bind]["frac"], "traffic": CAMERA_DRAM_BYTES, "traffic_unit": "bytes per launch (ncu)",
+                "bounds": bounds,
+                "peak_source": "fp32 and l2: measured in this run (" + mp["how"] + "); hbm: MEASURED_PEAKS hbm_gbs "
+                               "(of measured)",
+                "algorithmic": f"per 4-wide node visit {BYTES_PER_NODE} B + {FLOPS_PER_NODE} flop, per triangle test "
+                               f"{BYTES_PER_TRI} B + {FLOPS_PER_TRI} flop, counted live (sc_set_counters)"}
+    subs = {}
+    if not args.no_sub and rank == 0:
+        subs["cfg1"] = measure_cfg1(local)
+        bms, sms, info = measure_batch(1, 1, local, world)
+        subs["batch64"] = {"workload": BATCH_WORKLOAD, "camera_paths": info["camera_paths"],
+                           "triangles": info["triangles"], "ms_per_launch": bms,
+                           "mpaths_s": info["camera_paths"] / (bms * 1e-3) / 1e6,
+                           "sequential_ms": sms, "sequential_mpaths_s": info["camera_paths"] / (sms * 1e-3) / 1e6,
+                           "batch_over_sequential": sms / bms, "steps": 1, "warmup": 1,
+                           "scene_generation_s": info["scene_generation_s"], "lbvh_build_s": info["lbvh_build_s"]}
+        u = measure_unet_train(10, 3, local, world, e2e=False)
+        subs["unet_train"] = {"workload": UNET_WORKLOAD, "ms_per_step": u["ms"],
+                              "images_s": u["batch"] / (u["ms"] * 1e-3), "forward_ms": u["forward_ms"],
+                              "roofline": unet_roofline(u["ms"], u["batch"], u["hw"]), "steps": 10, "warmup": 3}
     if rank == 0:
         cb = None
         if not args.no_cpu_baseline and world == 1:
@@ -712,15 +871,14 @@ def main():
                           "lights": {"queries": light_counts[0], "nodes": light_counts[1], "tris": light_counts[2]},
                           "camera_grays_s": cam_counts[0] / cam_s / 1e9,
                           "camera_l2_side_gbs": cam_bytes / cam_s / 1e9},
-            "roofline": {"kernel": "k_trace_camera", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": CAMERA_DRAM_BYTES,
-                         "traffic_unit": "bytes per launch (ncu)",
-                         "peak_source": f"FP32: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (MEASURED_PEAKS sm_max)"},
+            "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": clocks,
             "cpu_baseline": cb,
         }
+        if subs:
+            line["sub_results"] = subs
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -84,6 +84,28 @@ int sc_unet_adam(sc_ctx *ctx, sc_unet *net, float lr);
 int sc_unet_train_step(sc_ctx *ctx, sc_unet *net, const float *x, const float *target, int32_t n, float lr,
                        float *loss);
 
+/* Training state (checkpoint / resume).  The state is the FP32 master parameters, the two Adam
+ * moment vectors (sc_unet_param_count floats each, same flat layout) and the Adam step count, which
+ * sets the bias corrections of the next step.  Restoring all of it and repeating the same calls
+ * continues training bit for bit as if it had not been interrupted (every kernel of a training
+ * step is deterministic).
+ * sc_unet_get_state: copies the moments to adam_m / adam_v (device, either may be NULL) and the
+ *   step count to *step (host, may be NULL).  Parameters: sc_unet_get_params.
+ * sc_unet_set_state: parameters, moments (device) and step count in one call; refreshes the BF16
+ *   copies the kernels read.  SC_ERR_INVALID_ARG on a null buffer or a step outside [0, 2^31).
+ * sc_unet_save: writes the whole state to the file `path` (binary: an 8-byte tag "SCUNET1", the
+ *   parameter count, the step count and the four level widths as int64, then the parameters,
+ *   the first moment and the second moment as FP32, little-endian).  Synchronises the context
+ *   stream.  SC_ERR_INVALID_ARG if the file cannot be written.
+ * sc_unet_load: reads such a file into the network (any batch size or geometry: the state does
+ *   not depend on them); SC_ERR_INVALID_ARG, with the network unchanged, if the file is missing,
+ *   truncated or holds another architecture.  Synchronises the context stream. */
+int sc_unet_get_state(sc_ctx *ctx, const sc_unet *net, float *adam_m, float *adam_v, int64_t *step);
+int sc_unet_set_state(sc_ctx *ctx, sc_unet *net, const float *params, const float *adam_m, const float *adam_v,
+                      int64_t step);
+int sc_unet_save(sc_ctx *ctx, const sc_unet *net, const char *path);
+int sc_unet_load(sc_ctx *ctx, sc_unet *net, const char *path);
+
 /* The loss alone: pred, target [n, h, w, 3] FP32 (device); loss (device, 1 float, optional);
  * grad (device, [n, h, w, 3] FP32, optional) = d loss / d pred.  h, w >= 11. */
 int sc_ssim_l1_loss(sc_ctx *ctx, const float *pred, const float *target, int32_t n, int32_t h, int32_t w,

@@ -233,6 +233,23 @@ int sc_sync_status(sc_ctx *ctx);
  * off.  The caller owns the buffer and zeroes it. */
 int sc_set_counters(sc_ctx *ctx, uint64_t *counters);
 
+/* Failure-detection limits of the BVH traversals (all kernels of this context from the next
+ * launch on).  A query that visits more than max_visits nodes latches SC_STATUS_WATCHDOG
+ * (sc_sync_status: SC_ERR_TIMEOUT); one whose traversal stack would need more than stack_depth4
+ * entries (4-wide traversal of the camera kernels, at most 96) or stack_depth2 entries (binary
+ * traversal of the light tracer, resolve and queries, at most 64) latches
+ * SC_STATUS_STACK_OVERFLOW (SC_ERR_STACK_OVERFLOW).  Either way the query is abandoned and reported
+ * as a miss, so the frame is wrong and the status says so.  A field of 0 means its default
+ * (max_visits 4,194,304; the compiled stack sizes); sc_set_limits(ctx, NULL) restores all
+ * defaults.  Values above the compiled stacks are rejected (SC_ERR_INVALID_ARG).  Small limits
+ * exist to test the error paths. */
+typedef struct {
+  int64_t max_visits;
+  int32_t stack_depth4, stack_depth2;
+} sc_limits;
+int sc_set_limits(sc_ctx *ctx, const sc_limits *limits);
+int sc_get_limits(const sc_ctx *ctx, sc_limits *limits);
+
 /* --- scene: LBVH build (Karras 2012 hierarchy over 30-bit Morton codes) ------------------ */
 int sc_build_scene(sc_ctx *ctx, const sc_scene_desc *desc, sc_scene **out);
 int sc_free_scene(sc_ctx *ctx, sc_scene *scene);
@@ -311,6 +328,21 @@ int sc_batch_create(sc_ctx *ctx, const sc_scene *const *scenes, const sc_frame *
                     const sc_trace_params *params, sc_batch **out);
 int sc_batch_launch(sc_ctx *ctx, sc_batch *batch);
 int sc_batch_destroy(sc_ctx *ctx, sc_batch *batch);
+
+/* --- measurement kernels (roofline denominators) ------------------------------------------
+ * The paper reports no performance figures; these two kernels measure, on the context's device,
+ * the two ceilings that bound BVH traversal besides HBM: FP32 FMA throughput and L2 read
+ * bandwidth.  Both launch on the context stream and return at once; the caller times them with
+ * events on that stream.
+ * sc_peak_fma: SM count x 2048 threads, each running 8 independent FMA chains of `iters` steps
+ *   (iters a positive multiple of 16).  *flops (host) receives the flops the launch performs
+ *   (2 per FMA).  sink: a device float the kernel never writes in practice (keeps the work live).
+ * sc_peak_l2_read: reads the device buffer `buf` (16-byte aligned, `bytes` a multiple of 16, sized
+ *   to stay resident in L2, e.g. 32 MB) `reps` times with L1-bypassing 16-byte loads from SM count
+ *   x 2048 threads; *bytes_read (host) receives bytes * reps.  Returns SC_ERR_INVALID_ARG on a bad
+ *   size, alignment or null pointer. */
+int sc_peak_fma(sc_ctx *ctx, int64_t iters, float *sink, int64_t *flops);
+int sc_peak_l2_read(sc_ctx *ctx, const void *buf, int64_t bytes, int32_t reps, float *sink, int64_t *bytes_read);
 
 #ifdef __cplusplus
 }

@@ -1,4 +1,6 @@
 // api.cu -- the C ABI (include/supercaustics.h): contexts, scenes, launches, status.
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +21,8 @@ struct sc_ctx {
   int num_sms = 0;
   int cam_blocks_per_sm = 0, light_blocks_per_sm = 0;
   unsigned long long *counters = nullptr;  // optional traversal work counters (device)
+  // failure-detection limits of the traversals (sc_set_limits)
+  int32_t max_visits = sc::kMaxVisits, stack4 = sc::kStack, stack2 = sc::kStack2;
 };
 
 struct sc_scene {
@@ -74,6 +78,15 @@ struct Carver {
 };
 
 bool valid_scene(const sc_scene *s) { return s && s->dev.nodes; }
+
+// the scene's device record with the context's traversal limits, as every launch passes it
+sc::DevScene launch_scene(const sc_ctx *c, const sc_scene *s) {
+  sc::DevScene d = s->dev;
+  d.max_visits = c->max_visits;
+  d.stack4 = c->stack4;
+  d.stack2 = c->stack2;
+  return d;
+}
 
 }  // namespace
 
@@ -182,6 +195,33 @@ int sc_sync_status(sc_ctx *c) {
     if (st & SC_STATUS_WATCHDOG) return fail(c, SC_ERR_TIMEOUT, "traversal watchdog expired");
     if (st & SC_STATUS_QUEUE_OVERFLOW) return fail(c, SC_ERR_QUEUE_OVERFLOW, "work queue overflow");
   }
+  return SC_OK;
+}
+
+int sc_set_limits(sc_ctx *c, const sc_limits *l) {
+  if (!c) return SC_ERR_INVALID_ARG;
+  if (!l) {
+    c->max_visits = sc::kMaxVisits;
+    c->stack4 = sc::kStack;
+    c->stack2 = sc::kStack2;
+    return SC_OK;
+  }
+  if (l->max_visits < 0 || l->stack_depth4 < 0 || l->stack_depth4 > sc::kStack || l->stack_depth2 < 0 ||
+      l->stack_depth2 > sc::kStack2)
+    return fail(c, SC_ERR_INVALID_ARG, "sc_set_limits: max_visits >= 0, stack_depth4 in [0, " +
+                                           std::to_string(sc::kStack) + "], stack_depth2 in [0, " +
+                                           std::to_string(sc::kStack2) + "]");
+  c->max_visits = l->max_visits == 0 ? sc::kMaxVisits : (int32_t)std::min<int64_t>(l->max_visits, INT32_MAX);
+  c->stack4 = l->stack_depth4 == 0 ? sc::kStack : l->stack_depth4;
+  c->stack2 = l->stack_depth2 == 0 ? sc::kStack2 : l->stack_depth2;
+  return SC_OK;
+}
+
+int sc_get_limits(const sc_ctx *c, sc_limits *l) {
+  if (!c || !l) return SC_ERR_INVALID_ARG;
+  l->max_visits = c->max_visits;
+  l->stack_depth4 = c->stack4;
+  l->stack_depth2 = c->stack2;
   return SC_OK;
 }
 
@@ -400,14 +440,14 @@ int sc_scene_export_bvh4(sc_ctx *c, const sc_scene *s, void *nodes4_host) {
 int sc_intersect(sc_ctx *c, const sc_scene *s, const float *rays, int64_t n, float *hits) {
   if (!c || !valid_scene(s) || n < 0 || (n > 0 && (!rays || !hits)))
     return fail(c, SC_ERR_INVALID_ARG, "sc_intersect: bad argument");
-  cudaError_t e = sc::launch_intersect(s->dev, rays, n, hits, c->d_words, c->stream);
+  cudaError_t e = sc::launch_intersect(launch_scene(c, s), rays, n, hits, c->d_words, c->stream);
   return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_intersect");
 }
 
 int sc_occluded(sc_ctx *c, const sc_scene *s, const float *rays, int64_t n, int32_t *occ) {
   if (!c || !valid_scene(s) || n < 0 || (n > 0 && (!rays || !occ)))
     return fail(c, SC_ERR_INVALID_ARG, "sc_occluded: bad argument");
-  cudaError_t e = sc::launch_occluded(s->dev, rays, n, occ, c->d_words, c->stream);
+  cudaError_t e = sc::launch_occluded(launch_scene(c, s), rays, n, occ, c->d_words, c->stream);
   return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_occluded");
 }
 
@@ -443,7 +483,7 @@ int sc_trace_camera(sc_ctx *c, const sc_scene *s, const sc_trace_params *p, cons
     return fail(c, SC_ERR_INVALID_ARG, "sc_trace_camera: bad parameters (n_bins must be 1..64)");
   if (p->spp == 0) return SC_OK;
   const int grid = persistent_grid(c, sc::camera_kernel_ptr(), &c->cam_blocks_per_sm);
-  cudaError_t e = sc::launch_trace_camera(s->dev, *p, *f, c->d_words, c->d_words + 1, c->counters, grid, c->stream);
+  cudaError_t e = sc::launch_trace_camera(launch_scene(c, s), *p, *f, c->d_words, c->d_words + 1, c->counters, grid, c->stream);
   return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_trace_camera");
 }
 
@@ -458,7 +498,7 @@ int sc_trace_lights(sc_ctx *c, const sc_scene *s, const sc_light_params *p, cons
     return fail(c, SC_ERR_INVALID_ARG, "sc_trace_lights: a guide sphere cannot be combined with SC_FLAG_SPLAT_DIRECT");
   if (p->n_paths == 0) return SC_OK;
   const int grid = persistent_grid(c, sc::light_kernel_ptr(), &c->light_blocks_per_sm);
-  cudaError_t e = sc::launch_trace_lights(s->dev, *p, *f, c->d_words,
+  cudaError_t e = sc::launch_trace_lights(launch_scene(c, s), *p, *f, c->d_words,
                                           reinterpret_cast<unsigned long long *>(c->d_words + 2), c->counters, grid,
                                           c->stream);
   return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_trace_lights");
@@ -495,7 +535,7 @@ static int batch_table(sc_ctx *c, const sc_scene *const *scenes, const sc_frame 
       return fail(c, SC_ERR_INVALID_ARG, "batch: more than 2^31 - 1 blocks of work");
     }
     std::memset(&h[i], 0, sizeof(h[i]));
-    h[i].S = s->dev;
+    h[i].S = launch_scene(c, s);
     h[i].F = frames[i];
     h[i].begin = begin;
     begin += t;
@@ -585,7 +625,7 @@ int sc_resolve(sc_ctx *c, const sc_scene *s, const sc_resolve_params *p, const s
   if (r) return r;
   if (!p || p->spp_total < 0 || p->light_paths_total < 0 || !(p->depth_range > 0))
     return fail(c, SC_ERR_INVALID_ARG, "sc_resolve: bad parameters");
-  cudaError_t e = sc::launch_resolve(s->dev, *p, *f, c->d_words, c->stream);
+  cudaError_t e = sc::launch_resolve(launch_scene(c, s), *p, *f, c->d_words, c->stream);
   return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_resolve");
 }
 

@@ -22,7 +22,8 @@ constexpr int kStack = 96;   // 4-wide traversal (camera kernel) pushes up to 3 
 constexpr int kStack2 = 64;  // binary traversal (trace())
 constexpr uint32_t kMiss = 0xFFFFFFFFu;
 constexpr int kMaxBins = 64;
-// traversal watchdog: node visits per query before the query is abandoned
+// traversal watchdog: node visits per query before the query is abandoned (default; the context's
+// limits override it per launch, sc_set_limits)
 constexpr int kMaxVisits = 1 << 22;
 
 enum : uint32_t { EV_REFLECT = 1, EV_REFRACT = 2, EV_LIT = 3, EV_UNLIT = 4, EV_FIXUP = 7 };
@@ -177,6 +178,9 @@ struct DevScene {
   int32_t n_tris, n_nodes, n_mats, n_lights;
   float env[3];
   sc_camera cam;
+  // failure-detection limits of the traversals, filled from the context at each launch
+  // (sc_set_limits): node visits per query, stack entries of the 4-wide / binary traversal
+  int32_t max_visits, stack4, stack2, pad;
 };
 
 // Work tickets of a scene (32 per 8x4 pixel tile) and the blocks of a batched launch over it.
@@ -339,7 +343,7 @@ static __device__ __forceinline__ Hit trace(const DevScene &S, float3 o, float3 
   int visits = 0;
   for (;;) {
     ++tc.nodes;
-    if (++visits > kMaxVisits) {
+    if (++visits > S.max_visits) {
       atomicOr(status, SC_STATUS_WATCHDOG);
       h.prim = -1;
       h.id = kMiss;
@@ -377,7 +381,7 @@ static __device__ __forceinline__ Hit trace(const DevScene &S, float3 o, float3 
     }
     if (ha && hb) {
       const bool a_first = ta <= tb;
-      if (sp >= kStack2) {
+      if (sp >= S.stack2) {
         atomicOr(status, SC_STATUS_STACK_OVERFLOW);
         h.prim = -1;
         h.id = kMiss;
@@ -436,7 +440,7 @@ __device__ __forceinline__ bool trav_step4(const DevScene &S, const WRay &w, flo
   const float kInf = __int_as_float(0x7f800000);
   for (int it = 0; it < budget; ++it) {
     ++tc.nodes;
-    if (++ts.visits > kMaxVisits) {
+    if (++ts.visits > S.max_visits) {
       atomicOr(status, SC_STATUS_WATCHDOG);
       ts.h.prim = -1;
       ts.h.id = kMiss;
@@ -512,7 +516,7 @@ __device__ __forceinline__ bool trav_step4(const DevScene &S, const WRay &w, flo
       ts.node = stack[--ts.sp];
       continue;
     }
-    if (ts.sp + cnt - 1 > kStack) {
+    if (ts.sp + cnt - 1 > S.stack4) {
       atomicOr(status, SC_STATUS_STACK_OVERFLOW);
       ts.h.prim = -1;
       ts.h.id = kMiss;

@@ -4,7 +4,9 @@
 // unet_wgrad.cuh, else the gathering GEMM of unet_gemm.cuh); the 1x1 output layer (HBM-bound),
 // pooling, the loss, the weight-gradient reduction and Adam are plain CUDA.
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -1628,6 +1630,95 @@ int sc_unet_adam(sc_ctx *c, sc_unet *u, float lr) {
   if (!c || !u || !(lr >= 0.0f)) return SC_ERR_INVALID_ARG;
   u->step += 1;
   return refresh_bf16(c, u, 1, lr);
+}
+
+int sc_unet_get_state(sc_ctx *c, const sc_unet *u, float *adam_m, float *adam_v, int64_t *step) {
+  if (!c || !u) return SC_ERR_INVALID_ARG;
+  const char *where = "sc_unet_get_state";
+  const size_t bytes = (size_t)u->n_params * sizeof(float);
+  cudaStream_t s = sc::ctx_stream(c);
+  if (adam_m) UCHK(cudaMemcpyAsync(adam_m, u->adam_m, bytes, cudaMemcpyDeviceToDevice, s));
+  if (adam_v) UCHK(cudaMemcpyAsync(adam_v, u->adam_v, bytes, cudaMemcpyDeviceToDevice, s));
+  if (step) *step = u->step;
+  return SC_OK;
+}
+
+int sc_unet_set_state(sc_ctx *c, sc_unet *u, const float *params, const float *adam_m, const float *adam_v,
+                      int64_t step) {
+  if (!c || !u || !params || !adam_m || !adam_v || step < 0 || step > INT32_MAX)
+    return fail(c, SC_ERR_INVALID_ARG, "sc_unet_set_state: null buffer or step out of range");
+  const char *where = "sc_unet_set_state";
+  const size_t bytes = (size_t)u->n_params * sizeof(float);
+  cudaStream_t s = sc::ctx_stream(c);
+  UCHK(cudaMemcpyAsync(u->params, params, bytes, cudaMemcpyDeviceToDevice, s));
+  UCHK(cudaMemcpyAsync(u->adam_m, adam_m, bytes, cudaMemcpyDeviceToDevice, s));
+  UCHK(cudaMemcpyAsync(u->adam_v, adam_v, bytes, cudaMemcpyDeviceToDevice, s));
+  u->step = (int)step;
+  return refresh_bf16(c, u, 0, 0.0f);
+}
+
+namespace {
+// checkpoint file: header, then FP32 params, Adam m, Adam v (n_params each), little-endian
+struct CkptHeader {
+  char magic[8];       // "SCUNET1\0"
+  int64_t n_params;
+  int64_t step;
+  int64_t chans[4];    // level widths, checked on load
+};
+constexpr char kCkptMagic[8] = {'S', 'C', 'U', 'N', 'E', 'T', '1', '\0'};
+}  // namespace
+
+int sc_unet_save(sc_ctx *c, const sc_unet *u, const char *path) {
+  if (!c || !u || !path) return SC_ERR_INVALID_ARG;
+  const char *where = "sc_unet_save";
+  const size_t n = (size_t)u->n_params;
+  std::vector<float> host(3 * n);
+  cudaStream_t s = sc::ctx_stream(c);
+  UCHK(cudaMemcpyAsync(host.data(), u->params, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+  UCHK(cudaMemcpyAsync(host.data() + n, u->adam_m, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+  UCHK(cudaMemcpyAsync(host.data() + 2 * n, u->adam_v, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+  UCHK(cudaStreamSynchronize(s));
+  CkptHeader h{};
+  std::memcpy(h.magic, kCkptMagic, 8);
+  h.n_params = u->n_params;
+  h.step = u->step;
+  for (int l = 0; l < kLevels; ++l) h.chans[l] = kChans[l];
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return fail(c, SC_ERR_INVALID_ARG, std::string("sc_unet_save: cannot open ") + path + " for writing");
+  const bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 && std::fwrite(host.data(), sizeof(float), 3 * n, f) == 3 * n;
+  const bool closed = std::fclose(f) == 0;
+  if (!ok || !closed) return fail(c, SC_ERR_INVALID_ARG, std::string("sc_unet_save: write to ") + path + " failed");
+  return SC_OK;
+}
+
+int sc_unet_load(sc_ctx *c, sc_unet *u, const char *path) {
+  if (!c || !u || !path) return SC_ERR_INVALID_ARG;
+  const char *where = "sc_unet_load";
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return fail(c, SC_ERR_INVALID_ARG, std::string("sc_unet_load: cannot open ") + path);
+  CkptHeader h{};
+  bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, kCkptMagic, 8) == 0 &&
+            h.n_params == u->n_params && h.step >= 0 && h.step <= INT32_MAX;
+  for (int l = 0; ok && l < kLevels; ++l) ok = h.chans[l] == kChans[l];
+  const size_t n = (size_t)u->n_params;
+  std::vector<float> host;
+  if (ok) {
+    host.resize(3 * n);
+    ok = std::fread(host.data(), sizeof(float), 3 * n, f) == 3 * n;
+  }
+  std::fclose(f);
+  if (!ok)
+    return fail(c, SC_ERR_INVALID_ARG,
+                std::string("sc_unet_load: ") + path + " is not a checkpoint of this network (or is truncated)");
+  cudaStream_t s = sc::ctx_stream(c);
+  UCHK(cudaMemcpyAsync(u->params, host.data(), n * sizeof(float), cudaMemcpyHostToDevice, s));
+  UCHK(cudaMemcpyAsync(u->adam_m, host.data() + n, n * sizeof(float), cudaMemcpyHostToDevice, s));
+  UCHK(cudaMemcpyAsync(u->adam_v, host.data() + 2 * n, n * sizeof(float), cudaMemcpyHostToDevice, s));
+  u->step = (int)h.step;
+  const int rc = refresh_bf16(c, u, 0, 0.0f);
+  if (rc) return rc;
+  UCHK(cudaStreamSynchronize(s));  // the host staging buffer is released on return
+  return SC_OK;
 }
 
 int sc_unet_train_step(sc_ctx *c, sc_unet *u, const float *x, const float *target, int32_t n, float lr, float *loss) {

@@ -114,6 +114,25 @@ class UNet:
         N.sc_unet_set_grads(self.ctx.handle, self.h, _ptr(flat))
         self.ctx.stream.synchronize()
 
+    # training state (checkpoint / resume) ----------------------------------------------------
+    def get_state(self):
+        """(params, adam_m, adam_v, step): the whole training state, device tensors + the step count."""
+        m = torch.empty(self.n_params, dtype=torch.float32, device=self.dev)
+        v = torch.empty(self.n_params, dtype=torch.float32, device=self.dev)
+        step = N.sc_unet_get_state(self.ctx.handle, self.h, _ptr(m), _ptr(v))
+        return self.get_params(), m, v, step
+
+    def set_state(self, params: torch.Tensor, m: torch.Tensor, v: torch.Tensor, step: int):
+        p, m, v = (t.to(self.dev, torch.float32).contiguous() for t in (params, m, v))
+        N.sc_unet_set_state(self.ctx.handle, self.h, _ptr(p), _ptr(m), _ptr(v), int(step))
+        self.ctx.stream.synchronize()
+
+    def save(self, path: str):
+        N.sc_unet_save(self.ctx.handle, self.h, path)
+
+    def load(self, path: str):
+        N.sc_unet_load(self.ctx.handle, self.h, path)
+
     # compute --------------------------------------------------------------------------------
     def forward(self, x: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
         n = x.shape[0]

@@ -127,6 +127,14 @@ SIGNATURES = {
                                   P(C.c_void_p)]),
     "sc_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sc_batch_destroy": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sc_set_limits": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sc_get_limits": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sc_unet_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, P(C.c_int64)]),
+    "sc_unet_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
+    "sc_unet_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_char_p]),
+    "sc_unet_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_char_p]),
+    "sc_peak_fma": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, P(C.c_int64)]),
+    "sc_peak_l2_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, P(C.c_int64)]),
     # sc_unet.h
     "sc_unet_param_count": (C.c_int, [P(C.c_int64)]),
     "sc_unet_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, P(C.c_void_p)]),
@@ -292,6 +300,54 @@ def sc_batch_create(ctx, scenes, frames, params: sc_trace_params):
 
 def sc_batch_launch(ctx, batch):
     return check(load().sc_batch_launch(ctx, batch), ctx)
+
+
+class sc_limits(C.Structure):
+    _fields_ = [("max_visits", C.c_int64), ("stack_depth4", C.c_int32), ("stack_depth2", C.c_int32)]
+
+
+def sc_set_limits(ctx, max_visits=0, stack_depth4=0, stack_depth2=0, defaults=False):
+    if defaults:
+        check(load().sc_set_limits(ctx, None), ctx)
+    else:
+        lim = sc_limits(max_visits, stack_depth4, stack_depth2)
+        check(load().sc_set_limits(ctx, C.byref(lim)), ctx)
+
+
+def sc_get_limits(ctx) -> sc_limits:
+    lim = sc_limits()
+    check(load().sc_get_limits(ctx, C.byref(lim)), ctx)
+    return lim
+
+
+def sc_unet_get_state(ctx, net, m_dev, v_dev) -> int:
+    step = C.c_int64()
+    check(load().sc_unet_get_state(ctx, net, m_dev, v_dev, C.byref(step)), ctx)
+    return step.value
+
+
+def sc_unet_set_state(ctx, net, params_dev, m_dev, v_dev, step):
+    check(load().sc_unet_set_state(ctx, net, params_dev, m_dev, v_dev, step), ctx)
+
+
+def sc_unet_save(ctx, net, path: str):
+    check(load().sc_unet_save(ctx, net, os.fsencode(path)), ctx)
+
+
+def sc_unet_load(ctx, net, path: str):
+    check(load().sc_unet_load(ctx, net, os.fsencode(path)), ctx)
+
+
+def sc_peak_fma(ctx, iters, sink_dev) -> int:
+    flops = C.c_int64()
+    check(load().sc_peak_fma(ctx, iters, sink_dev, C.byref(flops)), ctx)
+    return flops.value
+
+
+def sc_peak_l2_read(ctx, buf_dev, nbytes, reps, sink_dev) -> int:
+    nread = C.c_int64()
+    check(load().sc_peak_l2_read(ctx, buf_dev, nbytes, reps, sink_dev, C.byref(nread)), ctx)
+    return nread.value
 
 
 def sc_batch_destroy(ctx, batch):

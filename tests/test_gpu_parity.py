@@ -509,7 +509,12 @@ def test_full_size_glass_scene_sampled_rows(ctx):
     g = R.path_records_numpy(fr.path_records)
     rows = [0, 137, 300, 511]
     orc = O.OracleScene(sc)
+    n_paths = n_grazing = 0
     for y in rows:
         _, rec = orc.trace_camera(spp, depth, nbins=nb, window=(0, 512, y, y + 1))
         sel = slice(y * 512 * spp, (y + 1) * 512 * spp)
-        compare_camera({k: v[sel] for k, v in g.items()}, rec, max_grazing=MAX_GRAZING_DENSE_MESH)
+        # per-path checks row by row; the grazing share is bounded over the sampled rows together
+        st = compare_camera({k: v[sel] for k, v in g.items()}, rec, max_grazing=1.0)
+        n_paths += st["n"]
+        n_grazing += round(st["grazing"] * st["n"])
+    assert n_grazing / n_paths <= MAX_GRAZING_DENSE_MESH
