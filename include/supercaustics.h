@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define SC_ABI_VERSION 2
+#define SC_ABI_VERSION 3
 
 #define SC_OK 0
 #define SC_ERR_INVALID_ARG (-1)
@@ -158,6 +158,8 @@ typedef struct {
   double light_paths_total;  /* light paths accumulated (0 = no caustic buffer) */
   float depth_range;         /* Sec. III-D depth range, 10 m by default */
   float tau_rel;             /* caustic mask threshold relative to direct luminance */
+  int32_t outline_px;        /* Sec. III-D outline thickness T in pixels, 1..32 (0 = 1) */
+  float depth_jump_rel;      /* occlusion boundaries: relative depth jump (0 = 0.05) */
 } sc_resolve_params;
 
 /* One record per camera path (debug / parity output). */
@@ -199,6 +201,15 @@ typedef struct {
   float *normal_world;      /* float4[W*H] shading normal facing the camera, w = 1 on hit */
   float *normal_camera;     /* float4[W*H] the same in camera space (x right, y up, z to eye) */
   float *albedo;            /* float4[W*H] first-hit albedo (glass 1, miss 0) */
+  /* Sec. III-D "Outlines": 1 on transparent pixels whose Chebyshev window of radius outline_px
+   * holds another instance id (an inner band along the silhouettes), else 0.  Needs instance_id
+   * and mask. */
+  uint8_t *outline;
+  /* Sec. III-D "Occlusion Boundaries", per transparent pixel against its four in-image
+   * neighbours: 1 = nearer side of a depth jump |d_p - d_q| > depth_jump_rel * min(d_p, d_q) (a
+   * miss always jumps), 2 = contact edge (a neighbour shows another id, no jump), 0 = neither or
+   * not transparent.  Needs instance_id, mask and depth. */
+  uint8_t *occlusion;
   sc_path_record *path_records;    /* [H][W][spp] of the last sc_trace_camera call, or NULL */
   sc_light_record *light_records;  /* [n_paths] of the last sc_trace_lights call, or NULL */
   int32_t width, height;

@@ -625,6 +625,12 @@ int sc_resolve(sc_ctx *c, const sc_scene *s, const sc_resolve_params *p, const s
   if (r) return r;
   if (!p || p->spp_total < 0 || p->light_paths_total < 0 || !(p->depth_range > 0))
     return fail(c, SC_ERR_INVALID_ARG, "sc_resolve: bad parameters");
+  if (p->outline_px < 0 || p->outline_px > 32 || !(p->depth_jump_rel >= 0.0f) || !std::isfinite(p->depth_jump_rel))
+    return fail(c, SC_ERR_INVALID_ARG, "sc_resolve: outline_px must be in [0, 32], depth_jump_rel finite and >= 0");
+  if ((f->outline || f->occlusion) && (!f->instance_id || !f->mask))
+    return fail(c, SC_ERR_INVALID_ARG, "sc_resolve: outline and occlusion buffers need instance_id and mask");
+  if (f->occlusion && !f->depth)
+    return fail(c, SC_ERR_INVALID_ARG, "sc_resolve: the occlusion buffer needs depth");
   cudaError_t e = sc::launch_resolve(launch_scene(c, s), *p, *f, c->d_words, c->stream);
   return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_resolve");
 }

@@ -523,6 +523,88 @@ __global__ void k_resolve(DevScene S, sc_resolve_params P, sc_frame F, unsigned 
   if (F.albedo) reinterpret_cast<float4 *>(F.albedo)[pix] = alb;
 }
 
+// Outline and occlusion-boundary ground truth (Sec. III-D) from the buffers k_resolve wrote:
+// instance ids, transparency mask, depth.  One block per 32 x 8 pixels.  The block stages the ids
+// of its tile plus a halo of R = max(T, 1) pixels in shared memory (coordinates clamped to the
+// image, which leaves every clipped window's minimum and maximum unchanged), takes per halo row the
+// minimum and maximum id over each output column's 2T+1 wide window, then per output pixel the
+// minimum and maximum of those over 2T+1 rows: the pixel is on the outline when either differs from
+// its own id (the Chebyshev window of radius T holds another id) and it is transparent.  Occlusion
+// codes compare each transparent pixel with its four in-image neighbours: 1 when it is the nearer
+// side of a depth jump |d_p - d_q| > jump_rel * min(d_p, d_q) (a miss, d = inf, always jumps),
+// else 2 when a neighbour shows another id, else 0.
+constexpr int kEdgeTX = 32, kEdgeTY = 8;
+__global__ void __launch_bounds__(kEdgeTX * kEdgeTY) k_gt_edges(sc_frame F, int T, float jump_rel) {
+  extern __shared__ int edge_sm[];
+  const int W = F.width, H = F.height;
+  const int R = T > 1 ? T : 1;
+  const int SW = kEdgeTX + 2 * R, SH = kEdgeTY + 2 * R;
+  int *ids = edge_sm;               // SH x SW
+  int *rmin = ids + SH * SW;        // SH x kEdgeTX
+  int *rmax = rmin + SH * kEdgeTX;  // SH x kEdgeTX
+  const int x0 = blockIdx.x * kEdgeTX, y0 = blockIdx.y * kEdgeTY;
+  const int tid = threadIdx.y * kEdgeTX + threadIdx.x;
+  constexpr int nt = kEdgeTX * kEdgeTY;
+  for (int i = tid; i < SH * SW; i += nt) {
+    const int r = i / SW, c = i - r * SW;
+    const int y = min(max(y0 - R + r, 0), H - 1), x = min(max(x0 - R + c, 0), W - 1);
+    ids[i] = F.instance_id[y * W + x];
+  }
+  __syncthreads();
+  if (F.outline) {
+    for (int i = tid; i < SH * kEdgeTX; i += nt) {
+      const int r = i / kEdgeTX, c = i - r * kEdgeTX;
+      const int *row = ids + r * SW + c + R - T;  // smem columns c + R - T .. c + R + T
+      int mn = row[0], mx = row[0];
+      for (int k = 1; k <= 2 * T; ++k) {
+        mn = min(mn, row[k]);
+        mx = max(mx, row[k]);
+      }
+      rmin[i] = mn;
+      rmax[i] = mx;
+    }
+    __syncthreads();
+  }
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  if (x >= W || y >= H) return;
+  const int p = y * W + x;
+  const int cy = threadIdx.y + R, cx = threadIdx.x + R;
+  const int id = ids[cy * SW + cx];
+  const bool transparent = F.mask[p] != 0;
+  if (F.outline) {
+    bool edge = false;
+    if (transparent) {
+      int mn = id, mx = id;
+      for (int k = -T; k <= T; ++k) {
+        const int i = (cy + k) * kEdgeTX + threadIdx.x;
+        mn = min(mn, rmin[i]);
+        mx = max(mx, rmax[i]);
+      }
+      edge = mn != id || mx != id;
+    }
+    F.outline[p] = edge ? 1 : 0;
+  }
+  if (F.occlusion) {
+    uint8_t code = 0;
+    if (transparent) {
+      const float dp = F.depth[p];
+      bool nearer = false, contact = false;
+      const int ox[4] = {-1, 1, 0, 0}, oy[4] = {0, 0, -1, 1};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int qx = x + ox[k], qy = y + oy[k];
+        if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
+        const float dq = F.depth[qy * W + qx];
+        const bool jump = fabsf(dp - dq) > jump_rel * fminf(dp, dq);
+        nearer |= jump && dp < dq;
+        contact |= ids[(cy + oy[k]) * SW + cx + ox[k]] != id;
+      }
+      code = nearer ? 1 : (contact ? 2 : 0);
+    }
+    F.occlusion[p] = code;
+  }
+}
+
 __global__ void k_intersect(DevScene S, const float4 *rays, int64_t n, float4 *hits, unsigned *status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -581,6 +663,14 @@ cudaError_t launch_resolve(const DevScene &S, const sc_resolve_params &p, const 
                            cudaStream_t s) {
   const int n = f.width * f.height;
   k_resolve<<<blocks_for(n, 128), 128, 0, s>>>(S, p, f, status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || (!f.outline && !f.occlusion) || n == 0) return e;
+  const int T = f.outline && p.outline_px > 0 ? p.outline_px : 1;  // the halo only the outline needs
+  const float jump = p.depth_jump_rel > 0.0f ? p.depth_jump_rel : 0.05f;
+  const int R = T > 1 ? T : 1;
+  const size_t smem = sizeof(int) * ((size_t)(kEdgeTY + 2 * R) * (kEdgeTX + 2 * R) + 2 * (kEdgeTY + 2 * R) * kEdgeTX);
+  const dim3 grid((f.width + kEdgeTX - 1) / kEdgeTX, (f.height + kEdgeTY - 1) / kEdgeTY);
+  k_gt_edges<<<grid, dim3(kEdgeTX, kEdgeTY), smem, s>>>(f, T, jump);
   return cudaGetLastError();
 }
 

@@ -63,7 +63,7 @@ class sc_light_params(C.Structure):
 
 class sc_resolve_params(C.Structure):
     _fields_ = [("spp_total", C.c_double), ("light_paths_total", C.c_double), ("depth_range", C.c_float),
-                ("tau_rel", C.c_float)]
+                ("tau_rel", C.c_float), ("outline_px", C.c_int32), ("depth_jump_rel", C.c_float)]
 
 
 class sc_path_record(C.Structure):
@@ -78,7 +78,7 @@ class sc_light_record(C.Structure):
 
 FRAME_FIELDS = ["accum_camera", "accum_caustic", "rgb", "direct", "caustic", "instance_id", "tri_id", "mask",
                 "caustic_mask", "local_caustic_mask", "depth", "depth_norm", "normal_world", "normal_camera",
-                "albedo", "path_records", "light_records"]
+                "albedo", "outline", "occlusion", "path_records", "light_records"]
 
 
 class sc_frame(C.Structure):

@@ -182,7 +182,8 @@ class Frame:
     """Frame buffers as CUDA tensors; ``fields`` selects which outputs are produced."""
 
     ALL = ("accum_camera", "accum_caustic", "rgb", "direct", "caustic", "instance_id", "tri_id", "mask",
-           "caustic_mask", "local_caustic_mask", "depth", "depth_norm", "normal_world", "normal_camera", "albedo")
+           "caustic_mask", "local_caustic_mask", "depth", "depth_norm", "normal_world", "normal_camera", "albedo",
+           "outline", "occlusion")
 
     def __init__(self, width: int, height: int, device="cuda", fields=ALL):
         self.width, self.height = width, height
@@ -192,7 +193,7 @@ class Frame:
                 self.t[f] = torch.zeros((height, width, 4), dtype=torch.float32, device=device)
             elif f in ("instance_id", "tri_id"):
                 self.t[f] = torch.zeros((height, width), dtype=torch.int32, device=device)
-            elif f in ("mask", "caustic_mask", "local_caustic_mask"):
+            elif f in ("mask", "caustic_mask", "local_caustic_mask", "outline", "occlusion"):
                 self.t[f] = torch.zeros((height, width), dtype=torch.uint8, device=device)
             else:
                 self.t[f] = torch.zeros((height, width), dtype=torch.float32, device=device)
@@ -254,8 +255,9 @@ def trace_lights(ctx: Context, gs: GpuScene, frame: Frame, n_paths: int, max_dep
 
 
 def resolve(ctx: Context, gs: GpuScene, frame: Frame, spp_total: float, light_paths_total: float,
-            depth_range: float = 10.0, tau_rel: float = 0.25):
-    p = N.sc_resolve_params(float(spp_total), float(light_paths_total), depth_range, tau_rel)
+            depth_range: float = 10.0, tau_rel: float = 0.25, outline_px: int = 1, depth_jump_rel: float = 0.05):
+    p = N.sc_resolve_params(float(spp_total), float(light_paths_total), depth_range, tau_rel, int(outline_px),
+                            float(depth_jump_rel))
     N.sc_resolve(ctx.handle, gs.handle, p, frame.struct())
 
 

@@ -518,3 +518,84 @@ def test_full_size_glass_scene_sampled_rows(ctx):
         n_paths += st["n"]
         n_grazing += round(st["grazing"] * st["n"])
     assert n_grazing / n_paths <= MAX_GRAZING_DENSE_MESH
+
+
+# ------------------------------------------------------------------------------------------
+# Outline and occlusion-boundary ground truth (Sec. III-D)
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("T", [1, 4, 20, 32])
+def test_outline_and_occlusion_from_the_gpu_buffers(ctx, T):
+    """The kernel's outline / occlusion codes equal the oracle's definitions applied to the GPU's own
+    instance ids, mask and depth: bit for bit, except occlusion decisions within 1e-5 (relative) of
+    the depth-jump threshold (FP32 vs FP64 evaluation of the same comparison)."""
+    from oracle import gt_edges as G
+
+    sc = _small_glass(70, 45)
+    gs = R.GpuScene(ctx, sc)
+    fr = R.Frame(sc.camera.width, sc.camera.height)
+    R.resolve(ctx, gs, fr, 1, 0, outline_px=T, depth_jump_rel=0.05)
+    ctx.sync_status()
+    ids = fr["instance_id"].cpu().numpy()
+    mask = fr["mask"].cpu().numpy()
+    depth = fr["depth"].cpu().numpy()
+    out = fr["outline"].cpu().numpy()
+    np.testing.assert_array_equal(out, G.outline(ids, mask, T))
+    assert out.sum() > 0
+    occ = fr["occlusion"].cpu().numpy()
+    ref = G.occlusion_boundaries(ids, mask, depth.astype(np.float64), np.float32(0.05))
+    clear = G.occlusion_margin(depth.astype(np.float64), np.float32(0.05)) > 1e-5
+    np.testing.assert_array_equal(occ[clear], ref[clear])
+    assert (occ == 1).sum() > 0
+
+
+def test_outline_and_occlusion_end_to_end_vs_oracle(ctx):
+    """Against the oracle's own pixel-centre ids / mask / depth: equal wherever no pixel of the
+    window is a grazing case of the resolve ray (or a near-threshold depth comparison)."""
+    from scipy import ndimage
+
+    from oracle import gt_edges as G
+
+    sc = _small_glass(64, 48)
+    gs = R.GpuScene(ctx, sc)
+    T = 3
+    fr = R.Frame(sc.camera.width, sc.camera.height)
+    R.resolve(ctx, gs, fr, 1, 0, outline_px=T, depth_jump_rel=0.05)
+    ctx.sync_status()
+    g = O.OracleScene(sc).resolve(None, None, 1, 0)
+    amb = g["amb"] != 0
+    ref_out = G.outline(g["instance"], g["mask"], T)
+    ref_occ = G.occlusion_boundaries(g["instance"], g["mask"], g["depth"], 0.05)
+    near_amb = ndimage.maximum_filter(amb.astype(np.uint8), size=2 * T + 1, mode="nearest") != 0
+    np.testing.assert_array_equal(fr["outline"].cpu().numpy()[~near_amb], ref_out[~near_amb])
+    near_amb1 = ndimage.maximum_filter(amb.astype(np.uint8), size=3, mode="nearest") != 0
+    clear = ~near_amb1 & (G.occlusion_margin(g["depth"], 0.05) > 1e-4)
+    np.testing.assert_array_equal(fr["occlusion"].cpu().numpy()[clear], ref_occ[clear])
+    assert clear.mean() > 0.95 and (~near_amb).mean() > 0.9
+
+
+def test_outline_full_size_frame(ctx):
+    """512^2 dispersive glass frame at the paper's example thicknesses (1 px and 20 px)."""
+    from oracle import gt_edges as G
+
+    sc = S.glass_scene(0)
+    gs = R.GpuScene(ctx, sc)
+    for T in (1, 20):
+        fr = R.Frame(512, 512, fields=("instance_id", "mask", "depth", "outline", "occlusion"))
+        R.resolve(ctx, gs, fr, 1, 0, outline_px=T)
+        ctx.sync_status()
+        ids, mask = fr["instance_id"].cpu().numpy(), fr["mask"].cpu().numpy()
+        np.testing.assert_array_equal(fr["outline"].cpu().numpy(), G.outline(ids, mask, T))
+
+
+def test_outline_arguments_are_checked(ctx):
+    sc = S.ball_on_plane(16, 16)
+    gs = R.GpuScene(ctx, sc)
+    fr = R.Frame(16, 16)
+    for bad in (dict(outline_px=33), dict(outline_px=-1), dict(depth_jump_rel=-0.1)):
+        with pytest.raises(N.ScError):
+            R.resolve(ctx, gs, fr, 1, 0, **bad)
+    no_ids = R.Frame(16, 16, fields=("mask", "depth", "outline"))
+    with pytest.raises(N.ScError):
+        R.resolve(ctx, gs, no_ids, 1, 0)
+    ctx.sync_status()
