@@ -67,14 +67,25 @@ enum { SC_LIGHT_POINT = 0, SC_LIGHT_RECT = 1, SC_LIGHT_DISK = 2 };
 enum {
   SC_FLAG_FORCE_TRANSMIT = 1,   /* dielectrics refract unless totally internally reflecting */
   SC_FLAG_SPLAT_DIRECT = 2,     /* light tracer also splats paths with no specular event */
-  SC_FLAG_EMITTER_AFTER_DS = 4  /* camera paths count emitters reached as E D S+ L */
+  SC_FLAG_EMITTER_AFTER_DS = 4, /* camera paths count emitters reached as E D S+ L */
+  /* Sub-bin wavelength jitter (camera and light tracer): a path's wavelength is 400 + 300 u nm
+   * for its bin draw u (so its bin is still floor(u B)), its index of refraction n(lambda) at that
+   * wavelength and its RGB weight the CIE fit's linear sRGB there divided by the fit's mean over
+   * 400-700 nm.  No effect with one bin. */
+  SC_FLAG_WAVELENGTH_JITTER = 8
 };
 
 /* Surface description (Sec. III-C lists the glass and backdrop properties the paper varies).
  * DIFFUSE: Lambert albedo; if checker_scale > 0, albedo alternates with albedo2 on a
  * checkerboard of checker_scale squares per unit of the surface uv.  DIELECTRIC: glass with
- * Cauchy index n(lambda) = cauchy_a + cauchy_b / lambda_um^2.  EMISSIVE: one-sided emitter
- * of radiance `emission` along the triangle winding normal. */
+ * Cauchy index n(lambda) = cauchy_a + cauchy_b / lambda_um^2; its colour is a Beer-Lambert
+ * absorption coefficient per metre (RGB): a segment of length t that ends on the glass's inner
+ * side multiplies the path throughput by exp(-absorption * t); roughness > 0 makes it a rough
+ * dielectric (Walter, Marschner, Li, Torrance, EGSR 2007, GGX of width alpha = roughness):
+ * a microfacet normal drawn with density D(m)|m.n| from the path's bounce draws, Fresnel-chosen
+ * reflection or refraction about it, throughput times |i.m| G1(i) G1(o) / (|i.n| |m.n|); a
+ * facet turned away or a direction leaving on the wrong side ends the path.  EMISSIVE:
+ * one-sided emitter of radiance `emission` along the triangle winding normal. */
 typedef struct {
   int32_t kind;
   float albedo[3];
@@ -82,6 +93,8 @@ typedef struct {
   float checker_scale;
   float cauchy_a, cauchy_b;
   float emission[3];
+  float absorption[3];
+  float roughness;
 } sc_material;
 
 /* Light sources (Sec. III-C "lighting"; Fig. 4: softness follows the source size).

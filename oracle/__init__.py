@@ -20,6 +20,7 @@ _LIB = os.path.join(_HERE, "libsc_oracle.so")
 FLAG_FORCE_TRANSMIT = 1
 FLAG_SPLAT_DIRECT = 2
 FLAG_EMITTER_AFTER_DS = 4
+FLAG_WAVELENGTH_JITTER = 8
 
 AMB_NAMES = {1: "edge", 2: "tgap", 4: "graze", 8: "fresnel", 16: "tir", 32: "shadow", 64: "splat",
              128: "checker", 256: "fixup", 512: "sensitive"}
@@ -111,6 +112,11 @@ def lib():
         L.orc_fresnel.argtypes = [C.c_double, C.c_double, C.c_double]
         L.orc_fresnel.restype = C.c_double
         L.orc_refract.argtypes = [P(C.c_double), P(C.c_double), C.c_double, P(C.c_double)]
+        L.orc_jitter_mean.argtypes = [P(C.c_double)]
+        L.orc_rough_scatter.argtypes = [P(C.c_double), P(C.c_double), P(C.c_double), C.c_double, C.c_double,
+                                        C.c_double, C.c_double, C.c_double, C.c_int, P(C.c_double), P(C.c_double),
+                                        P(C.c_int)]
+        L.orc_rough_scatter.restype = C.c_int
         L.orc_scene_create.argtypes = [C.c_int, P(C.c_float), P(C.c_float), P(C.c_float), C.c_int, P(C.c_int),
                                        P(C.c_int), C.c_int, P(C.c_int), C.c_int, P(C.c_double), C.c_int,
                                        P(C.c_double), P(C.c_double), C.c_int, C.c_int, P(C.c_double)]
@@ -270,6 +276,24 @@ def xyz_to_rgb(xyz) -> np.ndarray:
     out = np.empty(3)
     lib().orc_xyz_to_rgb(_p(a, C.c_double), _p(out, C.c_double))
     return out
+
+
+def jitter_mean() -> np.ndarray:
+    """Mean linear sRGB of the CIE fit over 400-700 nm (the weight normaliser of wavelength jitter)."""
+    out = np.empty(3)
+    lib().orc_jitter_mean(_p(out, C.c_double))
+    return out
+
+
+def rough_scatter(d, ns, ng, n_lambda, alpha, u0, u1, u2, flags=0):
+    """One rough-dielectric scatter: (ok, new direction, weight, reflected)."""
+    d, ns, ng = (np.ascontiguousarray(v, np.float64) for v in (d, ns, ng))
+    out = np.empty(3)
+    w = C.c_double()
+    refl = C.c_int()
+    ok = lib().orc_rough_scatter(_p(d, C.c_double), _p(ns, C.c_double), _p(ng, C.c_double), n_lambda, alpha, u0, u1,
+                                 u2, flags, _p(out, C.c_double), C.byref(w), C.byref(refl))
+    return bool(ok), out, w.value, bool(refl.value)
 
 
 def fresnel(cos_i: float, n_i: float, n_t: float) -> float:

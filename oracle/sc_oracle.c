@@ -23,7 +23,10 @@
  *              Shirley (JCGT 2013, multi-lobe), normalised per channel to mean 1 over bins;
  *              B = 1 means no dispersion (n = A, weight 1).
  *   dielectric exact unpolarised Fresnel, Snell refraction, total internal reflection,
- *              reflect iff u < R, throughput unchanged.
+ *              reflect iff u < R, throughput unchanged.  Glass variants of Sec. III-C (colour,
+ *              roughness): Beer-Lambert absorption over each segment inside the glass, and a
+ *              rough dielectric (Walter et al. 2007, GGX) when the material's roughness > 0.
+ *   wavelength jitter  optionally lambda = 400 + 300 u from the bin draw (continuous spectrum).
  *   diffuse    Lambert; next-event estimation to one uniformly chosen light (glass blocks
  *              shadow rays); cosine-weighted bounce in the Duff et al. (JCGT 2017) frame.
  *   camera path  emitter radiance is counted only along purely specular prefixes.
@@ -46,12 +49,12 @@
 
 enum { MAT_DIFFUSE = 0, MAT_DIELECTRIC = 1, MAT_EMISSIVE = 2 };
 enum { LIGHT_POINT = 0, LIGHT_RECT = 1, LIGHT_DISK = 2 };
-enum { FLAG_FORCE_TRANSMIT = 1, FLAG_SPLAT_DIRECT = 2, FLAG_EMITTER_AFTER_DS = 4 };
+enum { FLAG_FORCE_TRANSMIT = 1, FLAG_SPLAT_DIRECT = 2, FLAG_EMITTER_AFTER_DS = 4, FLAG_WAVELENGTH_JITTER = 8 };
 enum {
   AMB_EDGE = 1, AMB_TGAP = 2, AMB_GRAZE = 4, AMB_FRESNEL = 8, AMB_TIR = 16,
   AMB_SHADOW = 32, AMB_SPLAT = 64, AMB_CHECKER = 128, AMB_FIXUP = 256, AMB_SENSITIVE = 512
 };
-enum { EV_MISS = 0xFFFFFFFFu, EV_REFLECT = 1, EV_REFRACT = 2, EV_LIT = 3, EV_UNLIT = 4, EV_FIXUP = 7 };
+enum { EV_MISS = 0xFFFFFFFFu, EV_REFLECT = 1, EV_REFRACT = 2, EV_LIT = 3, EV_UNLIT = 4, EV_FIXUP = 7, EV_KILL = 9 };
 
 static const double PI = 3.14159265358979323846;
 
@@ -146,10 +149,51 @@ ORC_API void orc_spectral_weights(int nbins, double *w /* nbins*3 */, double *la
   for (int b = 0; b < nbins; ++b) { w[3 * b] /= mean.x; w[3 * b + 1] /= mean.y; w[3 * b + 2] /= mean.z; }
 }
 
-static double cauchy(double A, double B, int bin, int nbins) {
+/* Cauchy index at wavelength lam (nm); one bin means no dispersion */
+static double cauchy_at(double A, double B, double lam, int nbins) {
   if (nbins <= 1) return A;
-  double lum = bin_lambda(bin, nbins) * 1e-3;
+  double lum = lam * 1e-3;
   return A + B / (lum * lum);
+}
+
+/* Sub-bin wavelength jitter (Sec. III-C varies the glass; a reading of how a renderer samples the
+ * spectrum continuously): the bin draw u gives lam = 400 + 300 u, uniform over 400-700 nm, whose
+ * bin is still floor(u B).  Its RGB weight is the CIE fit's linear sRGB at lam divided per channel
+ * by the fit's mean over 400-700 nm, so that a flat spectrum stays white in expectation.  The mean
+ * is the composite Simpson rule with 6000 intervals. */
+static v3 g_jitter_mean;
+static pthread_once_t g_jitter_once = PTHREAD_ONCE_INIT;
+static void jitter_mean_init(void) {
+  const int n = 6000;
+  const double h = 300.0 / n;
+  v3 acc = add(xyz_to_rgb(cie_xyz(400.0)), xyz_to_rgb(cie_xyz(700.0)));
+  for (int i = 1; i < n; ++i) acc = add(acc, mul(xyz_to_rgb(cie_xyz(400.0 + i * h)), (i & 1) ? 4.0 : 2.0));
+  g_jitter_mean = mul(acc, h / 3.0 / 300.0);
+}
+static v3 jitter_mean(void) {
+  pthread_once(&g_jitter_once, jitter_mean_init);
+  return g_jitter_mean;
+}
+ORC_API void orc_jitter_mean(double *out) {
+  v3 m = jitter_mean();
+  out[0] = m.x; out[1] = m.y; out[2] = m.z;
+}
+
+/* the wavelength of a path and its RGB weight, from the bin draw x */
+typedef struct { int bin; double lam; v3 w; } spec_sample;
+static spec_sample spectral_sample(uint32_t x, int nbins, int flags, const double *wts) {
+  spec_sample sp;
+  sp.bin = choose(x, nbins > 0 ? nbins : 1);
+  if (nbins <= 1) { sp.lam = 550.0; sp.w = V(1, 1, 1); return sp; }
+  if (flags & FLAG_WAVELENGTH_JITTER) {
+    sp.lam = 400.0 + 300.0 * u01(x);
+    v3 c = xyz_to_rgb(cie_xyz(sp.lam)), m = jitter_mean();
+    sp.w = V(c.x / m.x, c.y / m.y, c.z / m.z);
+  } else {
+    sp.lam = bin_lambda(sp.bin, nbins);
+    sp.w = V(wts[3 * sp.bin], wts[3 * sp.bin + 1], wts[3 * sp.bin + 2]);
+  }
+  return sp;
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -204,6 +248,8 @@ static v3 cosine_dir(v3 n, double u1, double u2) {
 /* ------------------------------------------------------------------------------------------ */
 typedef struct {
   int kind; v3 a1, a2; double checker, A, B; v3 emission;
+  v3 absorb;     /* dielectric: Beer-Lambert absorption coefficient per metre (RGB) */
+  double alpha;  /* dielectric: GGX roughness (0 = smooth) */
 } material;
 typedef struct {
   int kind; v3 p, u, v, power; double radius;
@@ -338,11 +384,13 @@ ORC_API void *orc_scene_create(int nv, const float *pos, const float *nrm, const
   s->nmat = nmat;
   s->mats = calloc((size_t)(nmat > 0 ? nmat : 1), sizeof(material));
   for (int m = 0; m < nmat; ++m) {
-    const double *q = mats + 13 * m;
+    const double *q = mats + 17 * m;
     s->mats[m].kind = (int)q[0];
     s->mats[m].a1 = V(q[1], q[2], q[3]); s->mats[m].a2 = V(q[4], q[5], q[6]);
     s->mats[m].checker = q[7]; s->mats[m].A = q[8]; s->mats[m].B = q[9];
     s->mats[m].emission = V(q[10], q[11], q[12]);
+    s->mats[m].absorb = V(q[13], q[14], q[15]);
+    s->mats[m].alpha = q[16];
   }
   s->nlights = nlights;
   s->lights = calloc((size_t)(nlights > 0 ? nlights : 1), sizeof(light));
@@ -707,6 +755,96 @@ static v3 dielectric(const surf *f, v3 d, double n_lambda, double u0, int flags,
   return out;
 }
 
+/* Smith masking term of GGX for a direction at cosine cos_v to the macro normal (Walter et al.
+ * 2007, eq. 34; the sign condition on v.m is checked by the caller) */
+static double ggx_g1(double cos_v, double alpha) {
+  double c2 = cos_v * cos_v;
+  double tan2 = (1.0 - c2) / c2;
+  return 2.0 / (1.0 + sqrt(1.0 + alpha * alpha * tan2));
+}
+
+/* Rough dielectric (Walter, Marschner, Li, Torrance, "Microfacet Models for Refraction through
+ * Rough Surfaces", EGSR 2007), GGX distribution of width alpha.  Macro normal n = the shading
+ * normal facing the ray (the geometric one if the shading normal faces away).  A microfacet normal
+ * m is drawn with density D(m) |m.n|: tan^2(theta_m) = alpha^2 u1 / (1 - u1), phi_m = 2 pi u2 in the
+ * Duff et al. frame of n.  Reflection or refraction about m is chosen as for a smooth surface with
+ * the Fresnel reflectance at m (u0 < F), and the throughput is multiplied by the estimator weight
+ * of that sampling, |i.m| G1(i) G1(o) / (|i.n| |m.n|) (Walter et al. eq. 41; i = -d the direction
+ * back to the ray's origin, o the new direction).  Returns 0 (the path ends) when m faces away
+ * from i or o leaves on the wrong side of the macro or the geometric surface. */
+static int rough_dielectric(const surf *f, v3 d, double n_lambda, double alpha, double u0, double u1, double u2,
+                            int flags, v3 *out, double *weight, int *reflected, int *fixup, actx *a) {
+  int entering = f->cosg < 0;
+  double n_i = entering ? 1.0 : n_lambda, n_t = entering ? n_lambda : 1.0;
+  double eta = n_i / n_t;
+  v3 n = f->nsf;
+  double cn = -dot(d, n);
+  note(a, fabs(cn), a->tol->cosg, AMB_FIXUP);
+  *fixup = 0;
+  *reflected = 0;
+  *weight = 0.0;
+  if (!(cn > 0)) {
+    n = f->ngf;
+    cn = -dot(d, n);
+    *fixup = 1;
+  }
+  v3 t1, t2;
+  onb(n, &t1, &t2);
+  double tan2 = alpha * alpha * u1 / (1.0 - u1);
+  double cm = 1.0 / sqrt(1.0 + tan2), sm = sqrt(fmax(0.0, 1.0 - cm * cm)), phi = 2.0 * PI * u2;
+  v3 m = normalize(add(add(mul(t1, sm * cos(phi)), mul(t2, sm * sin(phi))), mul(n, cm)));
+  double c = -dot(d, m);
+  note(a, fabs(c), a->tol->cosg, AMB_GRAZE);
+  if (!(c > 0)) return 0;
+  double k = 1.0 - eta * eta * (1.0 - c * c);
+  note(a, fabs(k), a->tol->tir, AMB_TIR);
+  double R = 1.0;
+  if (k >= 0) {
+    R = fresnel(c, sqrt(k), n_i, n_t);
+    if (!(flags & FLAG_FORCE_TRANSMIT)) note(a, fabs(u0 - R), a->tol->fres, AMB_FRESNEL);
+  }
+  int refl = (k < 0) || (!(flags & FLAG_FORCE_TRANSMIT) && u0 < R);
+  v3 o = refl ? normalize(add(d, mul(m, 2.0 * c))) : normalize(add(mul(d, eta), mul(m, eta * c - sqrt(k))));
+  *reflected = refl;
+  double sg = dot(o, f->ngf), sn = dot(o, n), om = dot(o, m);
+  note(a, fabs(sg), a->tol->cosg, AMB_FIXUP);
+  note(a, fabs(sn), a->tol->cosg, AMB_FIXUP);
+  if (refl ? !(sg > 0 && sn > 0) : !(sg < 0 && sn < 0)) return 0;
+  if (!(om * sn > 0)) return 0;
+  *weight = c * ggx_g1(cn, alpha) * ggx_g1(fabs(sn), alpha) / (cn * cm);
+  *out = o;
+  return 1;
+}
+
+/* one rough scatter for the pins: d, ns, ng unit; the surface faces d's origin as for a hit with
+ * dot(d, ng) = cosg.  Returns 1 with out_dir and weight, or 0 when the path would end. */
+ORC_API int orc_rough_scatter(const double *d, const double *ns, const double *ng, double n_lambda, double alpha,
+                              double u0, double u1, double u2, int flags, double *out_dir, double *weight,
+                              int *reflected) {
+  surf f;
+  memset(&f, 0, sizeof(f));
+  v3 dv = V(d[0], d[1], d[2]);
+  f.ng = V(ng[0], ng[1], ng[2]);
+  f.ns = V(ns[0], ns[1], ns[2]);
+  f.cosg = dot(dv, f.ng);
+  double side = f.cosg < 0 ? 1.0 : -1.0;
+  f.ngf = mul(f.ng, side);
+  f.nsf = mul(f.ns, side);
+  tolerances tol = DEFAULT_TOL;
+  actx a;
+  actx_init(&a, &tol);
+  v3 o = V(0, 0, 0);
+  int fix;
+  int ok = rough_dielectric(&f, dv, n_lambda, alpha, u0, u1, u2, flags, &o, weight, reflected, &fix, &a);
+  out_dir[0] = o.x; out_dir[1] = o.y; out_dir[2] = o.z;
+  return ok;
+}
+
+/* Beer-Lambert attenuation of a segment of length t inside a dielectric */
+static v3 absorb_over(const material *m, double t) {
+  return V(exp(-m->absorb.x * t), exp(-m->absorb.y * t), exp(-m->absorb.z * t));
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* parameters and records (layouts mirrored in oracle/__init__.py)                             */
 /* ------------------------------------------------------------------------------------------ */
@@ -841,7 +979,8 @@ static void camera_path_impl(const scene *s, const cam_params *P, const double *
   uint32_t pix = (uint32_t)(py * s->W + px);
   uint32_t x[4];
   draw(P->seed, pix, (uint32_t)sample, 0, 0, (uint32_t)P->scene_index, x);
-  int bin = choose(x[2], P->nbins > 0 ? P->nbins : 1);
+  spec_sample sp = spectral_sample(x[2], P->nbins, P->flags, wts);
+  int bin = sp.bin;
   ray r = camera_ray(s, (px + u01(x[0])) / s->W, (py + u01(x[1])) / s->H);
   nudge(&r, delta, P->seed ^ 0xA5A5A5A5ull, pix, (uint32_t)sample, 0);
   v3 beta = V(1, 1, 1), L = V(0, 0, 0);
@@ -860,6 +999,8 @@ static void camera_path_impl(const scene *s, const cam_params *P, const double *
     if (k == 0) { rec->p0[0] = f.p.x; rec->p0[1] = f.p.y; rec->p0[2] = f.p.z; }
     note(&a, fabs(f.cosg), P->tol.cosg, AMB_GRAZE);
     const material *m = &s->mats[f.mat];
+    /* a segment that ends on a dielectric's inner side ran through that glass */
+    if (m->kind == MAT_DIELECTRIC && f.cosg > 0) beta = hadamard(beta, absorb_over(m, h.t));
     if (m->kind == MAT_EMISSIVE) {
       int count = spec_only || ((P->flags & FLAG_EMITTER_AFTER_DS) && diffuse_first && n_diffuse == 1 &&
                                 last_specular);
@@ -870,8 +1011,17 @@ static void camera_path_impl(const scene *s, const cam_params *P, const double *
     draw(P->seed, pix, (uint32_t)sample, (uint32_t)(k + 1), 1, (uint32_t)P->scene_index, xs);
     if (m->kind == MAT_DIELECTRIC) {
       int refl, fix;
-      double n_l = cauchy(m->A, m->B, bin, P->nbins);
-      v3 d = dielectric(&f, r.d, n_l, u01(xs[0]), P->flags, &refl, &fix, &a);
+      double n_l = cauchy_at(m->A, m->B, sp.lam, P->nbins);
+      v3 d;
+      if (m->alpha > 0) {
+        double wgt;
+        int ok = rough_dielectric(&f, r.d, n_l, m->alpha, u01(xs[0]), u01(xs[1]), u01(xs[2]), P->flags, &d, &wgt,
+                                  &refl, &fix, &a);
+        if (!ok) { sig = fnv(sig, EV_KILL); ++a.nspec; break; }
+        beta = mul(beta, wgt);
+      } else {
+        d = dielectric(&f, r.d, n_l, u01(xs[0]), P->flags, &refl, &fix, &a);
+      }
       sig = fnv(sig, refl ? EV_REFLECT : EV_REFRACT);
       if (fix) sig = fnv(sig, EV_FIXUP);
       ++a.nspec;
@@ -906,8 +1056,7 @@ static void camera_path_impl(const scene *s, const cam_params *P, const double *
     r.d = d;
     nudge(&r, delta, P->seed ^ 0xA5A5A5A5ull, pix, (uint32_t)sample, k + 1);
   }
-  v3 w = V(wts[3 * bin], wts[3 * bin + 1], wts[3 * bin + 2]);
-  L = hadamard(L, w);
+  L = hadamard(L, sp.w);
   rec->L[0] = L.x; rec->L[1] = L.y; rec->L[2] = L.z;
   rec->n_queries = q;
   rec->signature = sig;
@@ -962,7 +1111,8 @@ static void light_path_impl(const scene *s, const light_params *P, const double 
   uint32_t xe[4], xd[4];
   draw(P->seed, lo, hi, 0, 4, (uint32_t)P->scene_index, xe);
   draw(P->seed, lo, hi, 0, 3, (uint32_t)P->scene_index, xd);
-  int bin = choose(xe[3], P->nbins > 0 ? P->nbins : 1);
+  spec_sample sp = spectral_sample(xe[3], P->nbins, P->flags, wts);
+  int bin = sp.bin;
   uint32_t sig = 2166136261u;
   rec->pixel = -1;
   rec->C[0] = rec->C[1] = rec->C[2] = 0;
@@ -1019,13 +1169,23 @@ static void light_path_impl(const scene *s, const light_params *P, const double 
       surf f = interact(s, r, h);
       note(&a, fabs(f.cosg), P->tol.cosg, AMB_GRAZE);
       const material *m = &s->mats[f.mat];
+      if (m->kind == MAT_DIELECTRIC && f.cosg > 0) beta = hadamard(beta, absorb_over(m, h.t));
       if (m->kind == MAT_EMISSIVE) break;
       if (m->kind == MAT_DIELECTRIC) {
         uint32_t xs[4];
         draw(P->seed, lo, hi, (uint32_t)(k + 1), 3, (uint32_t)P->scene_index, xs);
         int refl, fix;
-        double n_l = cauchy(m->A, m->B, bin, P->nbins);
-        v3 d = dielectric(&f, r.d, n_l, u01(xs[0]), P->flags, &refl, &fix, &a);
+        double n_l = cauchy_at(m->A, m->B, sp.lam, P->nbins);
+        v3 d;
+        if (m->alpha > 0) {
+          double wgt;
+          int ok = rough_dielectric(&f, r.d, n_l, m->alpha, u01(xs[0]), u01(xs[1]), u01(xs[2]), P->flags, &d,
+                                    &wgt, &refl, &fix, &a);
+          if (!ok) { sig = fnv(sig, EV_KILL); ++a.nspec; break; }
+          beta = mul(beta, wgt);
+        } else {
+          d = dielectric(&f, r.d, n_l, u01(xs[0]), P->flags, &refl, &fix, &a);
+        }
         sig = fnv(sig, refl ? EV_REFLECT : EV_REFRACT);
         if (fix) sig = fnv(sig, EV_FIXUP);
         ++a.nspec;
@@ -1067,8 +1227,7 @@ static void light_path_impl(const scene *s, const light_params *P, const double 
       sig = fnv(sig, EV_LIT);
       double apix = (2.0 * s->th * s->aspect / s->W) * (2.0 * s->th / s->H);
       double g = cs / (dc * dc * apix * cc * cc * cc) / PI;
-      v3 wb = V(wts[3 * bin], wts[3 * bin + 1], wts[3 * bin + 2]);
-      v3 C = hadamard(hadamard(mul(beta, g), alb), wb);
+      v3 C = hadamard(hadamard(mul(beta, g), alb), sp.w);
       rec->pixel = iy * s->W + ix;
       rec->C[0] = C.x; rec->C[1] = C.y; rec->C[2] = C.z;
       if (accum) {

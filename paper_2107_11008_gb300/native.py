@@ -30,7 +30,7 @@ class ScError(RuntimeError):
 class sc_material(C.Structure):
     _fields_ = [("kind", C.c_int32), ("albedo", C.c_float * 3), ("albedo2", C.c_float * 3),
                 ("checker_scale", C.c_float), ("cauchy_a", C.c_float), ("cauchy_b", C.c_float),
-                ("emission", C.c_float * 3)]
+                ("emission", C.c_float * 3), ("absorption", C.c_float * 3), ("roughness", C.c_float)]
 
 
 class sc_light(C.Structure):

@@ -66,6 +66,8 @@ def _materials(scene: Scene):
         a.checker_scale = m.checker_scale
         a.cauchy_a, a.cauchy_b = m.cauchy_a, m.cauchy_b
         a.emission[:] = [float(x) for x in m.emission]
+        a.absorption[:] = [float(x) for x in getattr(m, "absorption", (0.0, 0.0, 0.0))]
+        a.roughness = float(getattr(m, "roughness", 0.0))
     return arr
 
 

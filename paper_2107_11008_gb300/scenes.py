@@ -51,12 +51,15 @@ class Material:
     cauchy_a: float = 1.5
     cauchy_b: float = 0.0  # um^2
     emission: tuple = (0.0, 0.0, 0.0)
+    absorption: tuple = (0.0, 0.0, 0.0)  # dielectric: Beer-Lambert coefficient per metre (glass colour)
+    roughness: float = 0.0  # dielectric: GGX width alpha (0 = smooth glass)
 
     def flat(self) -> list:
-        """13 numbers: kind, albedo[3], albedo2[3], checker_scale, A, B, emission[3]."""
+        """17 numbers: kind, albedo[3], albedo2[3], checker_scale, A, B, emission[3], absorption[3],
+        roughness."""
         return [float(self.kind), *map(float, self.albedo), *map(float, self.albedo2),
                 float(self.checker_scale), float(self.cauchy_a), float(self.cauchy_b),
-                *map(float, self.emission)]
+                *map(float, self.emission), *map(float, self.absorption), float(self.roughness)]
 
 
 @dataclass
@@ -128,7 +131,7 @@ class Scene:
         return int(self.object_material.shape[0])
 
     def materials_flat(self) -> np.ndarray:
-        return np.asarray([m.flat() for m in self.materials], dtype=np.float64).reshape(-1, 13)
+        return np.asarray([m.flat() for m in self.materials], dtype=np.float64).reshape(-1, 17)
 
     def lights_flat(self) -> np.ndarray:
         return np.asarray([l.flat() for l in self.lights], dtype=np.float64).reshape(-1, 14)
