@@ -26,7 +26,7 @@ constexpr int kMaxBins = 64;
 // limits override it per launch, sc_set_limits)
 constexpr int kMaxVisits = 1 << 22;
 
-enum : uint32_t { EV_REFLECT = 1, EV_REFRACT = 2, EV_LIT = 3, EV_UNLIT = 4, EV_FIXUP = 7 };
+enum : uint32_t { EV_REFLECT = 1, EV_REFRACT = 2, EV_LIT = 3, EV_UNLIT = 4, EV_FIXUP = 7, EV_KILL = 9 };
 
 // Checked builds (-DSC_CHECKED): SC_IN_RANGE(status, site, v, n) is false when v is outside
 // [0, n); the first failure stores (site, v, thread) in status[8..10] and sets
@@ -100,19 +100,21 @@ __device__ __forceinline__ uint32_t fnv(uint32_t h, uint32_t w) { return (h ^ w)
 // ------------------------------------------------------------------------------------------
 // The table is tiny (one entry per bin, built once per block), so it is evaluated in FP64: the
 // XYZ -> RGB rows cancel strongly for some bins and FP32 would leave ~1e-4 relative error there.
-__device__ __forceinline__ double lobe(double lam, double mu, double s1, double s2) {
+__host__ __device__ inline double lobe_hd(double lam, double mu, double s1, double s2) {
   const double t = (lam - mu) / (lam < mu ? s1 : s2);
   return exp(-0.5 * t * t);
 }
-__device__ __forceinline__ void bin_rgb(int b, int nbins, double out[3]) {
-  const double lam = 400.0 + (b + 0.5) * 300.0 / nbins;
-  const double X = 1.056 * lobe(lam, 599.8, 37.9, 31.0) + 0.362 * lobe(lam, 442.0, 16.0, 26.7) -
-                   0.065 * lobe(lam, 501.1, 20.4, 26.2);
-  const double Y = 0.821 * lobe(lam, 568.8, 46.9, 40.5) + 0.286 * lobe(lam, 530.9, 16.3, 31.1);
-  const double Z = 1.217 * lobe(lam, 437.0, 11.8, 36.0) + 0.681 * lobe(lam, 459.0, 26.0, 13.8);
+__host__ __device__ inline void lambda_rgb(double lam, double out[3]) {
+  const double X = 1.056 * lobe_hd(lam, 599.8, 37.9, 31.0) + 0.362 * lobe_hd(lam, 442.0, 16.0, 26.7) -
+                   0.065 * lobe_hd(lam, 501.1, 20.4, 26.2);
+  const double Y = 0.821 * lobe_hd(lam, 568.8, 46.9, 40.5) + 0.286 * lobe_hd(lam, 530.9, 16.3, 31.1);
+  const double Z = 1.217 * lobe_hd(lam, 437.0, 11.8, 36.0) + 0.681 * lobe_hd(lam, 459.0, 26.0, 13.8);
   out[0] = 3.2404542 * X - 1.5371385 * Y - 0.4985314 * Z;
   out[1] = -0.9692660 * X + 1.8760108 * Y + 0.0415560 * Z;
   out[2] = 0.0556434 * X - 0.2040259 * Y + 1.0572252 * Z;
+}
+__device__ __forceinline__ void bin_rgb(int b, int nbins, double out[3]) {
+  lambda_rgb(400.0 + (b + 0.5) * 300.0 / nbins, out);
 }
 // Fills w[0..nbins) (shared memory); call from every thread of the block.
 __device__ __forceinline__ void spectral_table(float3 *w, int nbins) {
@@ -136,10 +138,43 @@ __device__ __forceinline__ void spectral_table(float3 *w, int nbins) {
   }
   __syncthreads();
 }
-__device__ __forceinline__ float cauchy(float A, float B, int bin, int nbins) {
+// A path keeps the uniform u of its bin draw (exact in FP32: u = (x >> 8) 2^-24); its bin is the
+// exact integer floor(u B) and its wavelength the bin centre, or with SC_FLAG_WAVELENGTH_JITTER
+// 400 + 300 u nm (continuous).
+__device__ __forceinline__ int bin_of(float u, int nbins) {
+  return (int)(((unsigned long long)(uint32_t)(u * 16777216.0f) * (unsigned)nbins) >> 24);
+}
+__device__ __forceinline__ float path_lambda(float u, int nbins, bool jitter) {
+  return jitter ? 400.0f + 300.0f * u : 400.0f + (bin_of(u, nbins) + 0.5f) * 300.0f / nbins;
+}
+__device__ __forceinline__ float cauchy_at(float A, float B, float lam, int nbins) {
   if (nbins <= 1) return A;
-  const float lum = (400.0f + (bin + 0.5f) * 300.0f / nbins) * 1e-3f;
+  const float lum = lam * 1e-3f;
   return A + B / (lum * lum);
+}
+// Jitter: RGB weight at 400 + 300 u nm, the fit's sRGB there over its 400-700 nm mean (inv_mean
+// = 1 / mean per channel, computed on the host), evaluated in FP64 like the bin table.
+struct JitterNorm {
+  double inv_mean[3];
+};
+static __device__ __noinline__ float3 jitter_weight(float u, const JitterNorm &jn) {
+  double c[3];
+  lambda_rgb(400.0 + 300.0 * (double)u, c);
+  return make_float3((float)(c[0] * jn.inv_mean[0]), (float)(c[1] * jn.inv_mean[1]), (float)(c[2] * jn.inv_mean[2]));
+}
+// the normaliser, on the host: composite Simpson rule over 400-700 nm, 3000 intervals
+inline JitterNorm jitter_norm_host() {
+  const int n = 3000;
+  const double h = 300.0 / n;
+  double acc[3] = {0.0, 0.0, 0.0}, c[3];
+  for (int i = 0; i <= n; ++i) {
+    lambda_rgb(400.0 + i * h, c);
+    const double w = (i == 0 || i == n) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+    for (int k = 0; k < 3; ++k) acc[k] += w * c[k];
+  }
+  JitterNorm jn;
+  for (int k = 0; k < 3; ++k) jn.inv_mean[k] = 300.0 / (acc[k] * h / 3.0);
+  return jn;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -637,6 +672,14 @@ __device__ __forceinline__ float3 dielectric(const Surf &f, float3 d, float n_la
   return out;
 }
 
+// Beer-Lambert attenuation of a segment of length t inside a dielectric (per RGB channel)
+__device__ __forceinline__ float3 absorb_over(const sc_material &m, float t) {
+  return f3(expf(-m.absorption[0] * t), expf(-m.absorption[1] * t), expf(-m.absorption[2] * t));
+}
+__device__ __forceinline__ bool absorbs(const sc_material &m) {
+  return m.absorption[0] != 0.0f || m.absorption[1] != 0.0f || m.absorption[2] != 0.0f;
+}
+
 // orthonormal basis around unit n (Duff et al., "Building an Orthonormal Basis, Revisited",
 // JCGT 2017) and a cosine-weighted direction about n
 __device__ __forceinline__ void onb(float3 n, float3 &t1, float3 &t2) {
@@ -653,6 +696,58 @@ __device__ __forceinline__ float3 cosine_dir(float3 n, float u1, float u2) {
   float s, c;
   sincospif(2.0f * u2, &s, &c);
   return normalize(t1 * (r * c) + t2 * (r * s) + n * sqrtf(fmaxf(0.0f, 1.0f - u1)));
+}
+
+// Smith masking of GGX at cosine cos_v to the macro normal (Walter et al. 2007, eq. 34)
+__device__ __forceinline__ float ggx_g1(float cos_v, float alpha) {
+  const float c2 = cos_v * cos_v;
+  return 2.0f / (1.0f + sqrtf(1.0f + alpha * alpha * ((1.0f - c2) / c2)));
+}
+
+// Rough dielectric (Walter, Marschner, Li, Torrance, EGSR 2007, GGX of width alpha): macro normal
+// n = shading normal facing the ray (geometric if it faces away); microfacet normal m drawn with
+// density D(m)|m.n| (tan^2 theta_m = alpha^2 u1 / (1 - u1), phi = 2 pi u2 in the Duff frame of n);
+// Fresnel choice at m as for smooth glass; weight = |i.m| G1(i) G1(o) / (|i.n| |m.n|) (eq. 41).
+// Returns false (the path ends) for a facet turned away from the ray or an outgoing direction on
+// the wrong side of the macro or the geometric surface.
+static __device__ __noinline__ bool rough_dielectric(const Surf &f, float3 d, float n_lambda, float alpha, float u0,
+                                                 float u1, float u2, int flags, float3 &out, float &weight,
+                                                 bool &reflected, bool &fixup) {
+  const bool entering = f.cosg < 0.0f;
+  const float n_i = entering ? 1.0f : n_lambda, n_t = entering ? n_lambda : 1.0f;
+  const float eta = n_i / n_t;
+  float3 n = f.nsf;
+  float cn = -dot(d, n);
+  fixup = false;
+  reflected = false;
+  weight = 0.0f;
+  if (!(cn > 0.0f)) {
+    n = f.ngf;
+    cn = -dot(d, n);
+    fixup = true;
+  }
+  float3 t1, t2;
+  onb(n, t1, t2);
+  const float tan2 = alpha * alpha * u1 / (1.0f - u1);
+  const float cm = 1.0f / sqrtf(1.0f + tan2);
+  const float sm = sqrtf(tan2) * cm;  // sin theta_m without the cancellation of sqrt(1 - cm^2)
+  float sp, cp;
+  sincospif(2.0f * u2, &sp, &cp);
+  const float3 m = normalize(t1 * (sm * cp) + t2 * (sm * sp) + n * cm);
+  const float c = -dot(d, m);
+  if (!(c > 0.0f)) return false;
+  const float k = 1.0f - eta * eta * (1.0f - c * c);
+  float R = 1.0f;
+  if (k >= 0.0f) R = fresnel(c, sqrtf(k), n_i, n_t);
+  const bool refl = (k < 0.0f) || (!(flags & SC_FLAG_FORCE_TRANSMIT) && u0 < R);
+  const float3 o = refl ? normalize(d + m * (2.0f * c)) : normalize(d * eta + m * (eta * c - sqrtf(k)));
+  reflected = refl;
+  const float sg = dot(o, f.ngf), sn = dot(o, n), om = dot(o, m);
+  if (refl ? !(sg > 0.0f && sn > 0.0f) : !(sg < 0.0f && sn < 0.0f)) return false;
+  if (!(om * sn > 0.0f)) return false;
+  weight = c * ggx_g1(cn, alpha) * ggx_g1(fabsf(sn), alpha) / (cn * cm);
+  out = o;
+  return true;
 }
 
 }  // namespace sc

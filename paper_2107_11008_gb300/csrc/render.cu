@@ -46,7 +46,8 @@ enum : uint32_t {
 template <bool BATCH>
 __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS)
     k_trace_camera_t(DevScene S0, sc_trace_params P, sc_frame F0, const BatchEntry *tab, int n_tab,
-                     unsigned total_tickets, unsigned *status, unsigned *ticket, unsigned long long *counters) {
+                     unsigned total_tickets, unsigned *status, unsigned *ticket, unsigned long long *counters,
+                     JitterNorm jn) {
   TravCount tc;
   __shared__ float3 wts[kMaxBins];
   __shared__ BatchEntry blk;
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS)
   const int lane = threadIdx.x & 31;
   const float3 env = f3(S.env);
   const int nb = P.n_bins > 0 ? P.n_bins : 1;
+  const bool jitter = (P.flags & SC_FLAG_WAVELENGTH_JITTER) && nb > 1;
   const int scene_index = BATCH ? P.scene_index + (int)blk_scene : P.scene_index;
 
   // pixel state
@@ -81,7 +83,8 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS)
   bool done = false;
   float3 acc = f3(0.f, 0.f, 0.f);
   // path state
-  int mode = M_IDLE, k = 0, bin = 0, n_diffuse = 0;
+  int mode = M_IDLE, k = 0, n_diffuse = 0;
+  float ul = 0.0f;  // the path's bin draw u: bin floor(u B), wavelength (path_lambda)
   uint32_t fl = 0, sig = 0, first = kMiss, nq = 0, nspec = 0;
   float3 o = f3(0.f, 0.f, 0.f), d = o, beta = o, L = o, nee = o, o2 = o, d2 = o;
   float tmax = 3.0e38f;
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS)
     if (mode == M_IDLE && pix >= 0 && s < P.spp) {
       // start sample s: primary ray (tag 0: jitter x, jitter y, wavelength bin)
       const uint4 x0 = draw(P.seed, (uint32_t)pix, (uint32_t)(P.sample_offset + s), 0u, 0u, (uint32_t)scene_index);
-      bin = choose(x0.z, nb);
+      ul = u01(x0.z);
       o = cam.eye;
       d = cam_dir(cam, (px + u01(x0.x)) / cam.W, (py + u01(x0.y)) / cam.H);
       tmax = 3.0e38f;
@@ -184,6 +187,8 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS)
       } else {
         const Surf f = interact(S, d, h);
         const sc_material m = S.mats[SC_IN_RANGE(status, 7, f.mat, S.n_mats) ? f.mat : 0];
+        // a segment that ends on a dielectric's inner side ran through that glass (Beer-Lambert)
+        if (m.kind == SC_MAT_DIELECTRIC && f.cosg > 0.0f && absorbs(m)) beta = beta * absorb_over(m, h.t);
         if (m.kind == SC_MAT_EMISSIVE) {
           const bool count = (fl & F_SPEC_ONLY) || ((P.flags & SC_FLAG_EMITTER_AFTER_DS) && (fl & F_DIFFUSE_FIRST) &&
                                                     n_diffuse == 1 && (fl & F_LAST_SPECULAR));
@@ -193,17 +198,30 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS)
           const uint32_t pixu = (uint32_t)pix, smp = (uint32_t)(P.sample_offset + s);
           const uint4 xs = draw(P.seed, pixu, smp, (uint32_t)(k + 1), 1u, (uint32_t)scene_index);
           if (m.kind == SC_MAT_DIELECTRIC) {
-            bool refl, fix;
-            const float nl = cauchy(m.cauchy_a, m.cauchy_b, bin, P.n_bins);
-            const float3 nd = dielectric(f, d, nl, u01(xs.x), P.flags, refl, fix);
-            sig = fnv(sig, refl ? EV_REFLECT : EV_REFRACT);
-            if (fix) sig = fnv(sig, EV_FIXUP);
+            bool refl, fix, alive = true;
+            const float nl = cauchy_at(m.cauchy_a, m.cauchy_b, path_lambda(ul, nb, jitter), P.n_bins);
+            float3 nd;
+            if (m.roughness > 0.0f) {
+              float w;
+              alive = rough_dielectric(f, d, nl, m.roughness, u01(xs.x), u01(xs.y), u01(xs.z), P.flags, nd, w, refl,
+                                       fix);
+              beta = beta * w;
+            } else {
+              nd = dielectric(f, d, nl, u01(xs.x), P.flags, refl, fix);
+            }
             ++nspec;
-            fl |= F_LAST_SPECULAR;
-            o = offset_along(f.p, f.ng, nd);
-            d = nd;
-            ++k;
-            if (k >= P.max_depth) finish = true;
+            if (!alive) {
+              sig = fnv(sig, EV_KILL);
+              finish = true;
+            } else {
+              sig = fnv(sig, refl ? EV_REFLECT : EV_REFRACT);
+              if (fix) sig = fnv(sig, EV_FIXUP);
+              fl |= F_LAST_SPECULAR;
+              o = offset_along(f.p, f.ng, nd);
+              d = nd;
+              ++k;
+              if (k >= P.max_depth) finish = true;
+            }
           } else {
             // diffuse: next-event estimate (shadow ray traced next iteration), then the bounce
             const float3 alb = albedo_at(S, m, f);
@@ -282,7 +300,8 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS)
       }
     }
     if (finish) {
-      const float3 Lw = L * wts[bin];
+      const int bin = bin_of(ul, nb);
+      const float3 Lw = L * (jitter ? jitter_weight(ul, jn) : wts[bin]);
       acc = acc + Lw;
       if (F.path_records && SC_IN_RANGE(status, 9, (int64_t)pix * P.spp + s, (int64_t)cam.W * cam.H * P.spp)) {
         sc_path_record r;
@@ -308,7 +327,7 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS)
 // One light path: emission, specular chain, splat at the first diffuse vertex after glass.
 __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_params P, sc_frame F,
                                                          unsigned *status, unsigned long long *ticket,
-                                                         unsigned long long *counters) {
+                                                         unsigned long long *counters, JitterNorm jn) {
   TravCount tc;
   __shared__ float3 wts[kMaxBins];
   spectral_table(wts, P.n_bins);
@@ -326,7 +345,10 @@ __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_pa
     const uint32_t lo = (uint32_t)idx, hi = (uint32_t)((uint64_t)idx >> 32);
     const uint4 xe = draw(P.seed, lo, hi, 0u, 4u, (uint32_t)P.scene_index);
     const uint4 xd = draw(P.seed, lo, hi, 0u, 3u, (uint32_t)P.scene_index);
-    const int bin = choose(xe.w, P.n_bins > 0 ? P.n_bins : 1);
+    const int nbl = P.n_bins > 0 ? P.n_bins : 1;
+    const bool jitter = (P.flags & SC_FLAG_WAVELENGTH_JITTER) && nbl > 1;
+    const float ul = u01(xe.w);
+    const int bin = bin_of(ul, nbl);
     uint32_t sig = 2166136261u, nspec = 0;
     int pixel = -1;
     float3 C = f3(0.f, 0.f, 0.f), X = f3(__int_as_float(0x7FC00000), __int_as_float(0x7FC00000),
@@ -405,12 +427,26 @@ __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_pa
         if (h.prim < 0) break;
         const Surf f = interact(S, d, h);
         const sc_material m = S.mats[f.mat];
+        if (m.kind == SC_MAT_DIELECTRIC && f.cosg > 0.0f && absorbs(m)) beta = beta * absorb_over(m, h.t);
         if (m.kind == SC_MAT_EMISSIVE) break;
         if (m.kind == SC_MAT_DIELECTRIC) {
           const uint4 xs = draw(P.seed, lo, hi, (uint32_t)(k + 1), 3u, (uint32_t)P.scene_index);
           bool refl, fix;
-          const float nl = cauchy(m.cauchy_a, m.cauchy_b, bin, P.n_bins);
-          const float3 nd = dielectric(f, d, nl, u01(xs.x), P.flags, refl, fix);
+          const float nl = cauchy_at(m.cauchy_a, m.cauchy_b, path_lambda(ul, nbl, jitter), P.n_bins);
+          float3 nd;
+          if (m.roughness > 0.0f) {
+            float w;
+            const bool alive = rough_dielectric(f, d, nl, m.roughness, u01(xs.x), u01(xs.y), u01(xs.z), P.flags, nd,
+                                                w, refl, fix);
+            if (!alive) {
+              sig = fnv(sig, EV_KILL);
+              ++nspec;
+              break;
+            }
+            beta = beta * w;
+          } else {
+            nd = dielectric(f, d, nl, u01(xs.x), P.flags, refl, fix);
+          }
           sig = fnv(sig, refl ? EV_REFLECT : EV_REFRACT);
           if (fix) sig = fnv(sig, EV_FIXUP);
           ++nspec;
@@ -443,7 +479,7 @@ __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_pa
         }
         sig = fnv(sig, EV_LIT);
         const float g = cs / (dc * dc * apix * cc * cc * cc) / kPi;
-        C = beta * g * alb * wts[bin];
+        C = beta * g * alb * (jitter ? jitter_weight(ul, jn) : wts[bin]);
         pixel = iy * cam.W + ix;
         if (F.accum_caustic) {
           float *a = F.accum_caustic + 4 * (int64_t)pixel;
@@ -637,7 +673,8 @@ cudaError_t launch_trace_camera(const DevScene &S, const sc_trace_params &p, con
                                 unsigned *ticket, unsigned long long *counters, int grid, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  k_trace_camera_t<false><<<grid, kBlock, 0, s>>>(S, p, f, nullptr, 0, 0u, status, ticket, counters);
+  static const JitterNorm jn = jitter_norm_host();
+  k_trace_camera_t<false><<<grid, kBlock, 0, s>>>(S, p, f, nullptr, 0, 0u, status, ticket, counters, jn);
   return cudaGetLastError();
 }
 
@@ -646,7 +683,8 @@ cudaError_t launch_trace_batch(const BatchEntry *tab, int n, unsigned total_bloc
   if (total_blocks == 0) return cudaSuccess;
   DevScene none{};
   sc_frame nof{};
-  k_trace_camera_t<true><<<total_blocks, kBlock, 0, s>>>(none, p, nof, tab, n, 0u, status, nullptr, counters);
+  static const JitterNorm jn = jitter_norm_host();
+  k_trace_camera_t<true><<<total_blocks, kBlock, 0, s>>>(none, p, nof, tab, n, 0u, status, nullptr, counters, jn);
   return cudaGetLastError();
 }
 
@@ -655,7 +693,8 @@ cudaError_t launch_trace_lights(const DevScene &S, const sc_light_params &p, con
                                 cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_trace_lights<<<grid, kBlock, 0, s>>>(S, p, f, status, ticket, counters);
+  static const JitterNorm jn = jitter_norm_host();
+  k_trace_lights<<<grid, kBlock, 0, s>>>(S, p, f, status, ticket, counters, jn);
   return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@ ERRORS = {-1: "SC_ERR_INVALID_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_OOM", -4: "SC
 SC_FLAG_FORCE_TRANSMIT = 1
 SC_FLAG_SPLAT_DIRECT = 2
 SC_FLAG_EMITTER_AFTER_DS = 4
+SC_FLAG_WAVELENGTH_JITTER = 8
 
 
 class ScError(RuntimeError):

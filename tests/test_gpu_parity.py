@@ -599,3 +599,47 @@ def test_outline_arguments_are_checked(ctx):
     with pytest.raises(N.ScError):
         R.resolve(ctx, gs, no_ids, 1, 0)
     ctx.sync_status()
+
+
+# ------------------------------------------------------------------------------------------
+# Glass variants (Sec. III-C): colour (Beer-Lambert), roughness (GGX), wavelength jitter
+# ------------------------------------------------------------------------------------------
+
+def _variant_glass(width=48, height=36, roughness=0.0, absorption=(0.0, 0.0, 0.0)):
+    import dataclasses
+
+    sc = _small_glass(width, height)
+    sc.materials = [dataclasses.replace(m, roughness=roughness, absorption=absorption)
+                    if m.kind == S.MAT_DIELECTRIC else m for m in sc.materials]
+    return sc
+
+
+@pytest.mark.parametrize("variant", ["absorbing", "rough", "rough_absorbing_jitter"])
+def test_camera_parity_glass_variants(ctx, variant):
+    rough = 0.0 if variant == "absorbing" else 0.15
+    sc = _variant_glass(roughness=rough, absorption=(0.6, 1.5, 3.0) if "absorbing" in variant else (0, 0, 0))
+    flags = N.SC_FLAG_WAVELENGTH_JITTER if "jitter" in variant else 0
+    spp, depth, nb = 4, 12, 8
+    _, fr = _render(ctx, sc, spp, depth, n_bins=nb, seed=13, flags=flags)
+    g = R.path_records_numpy(fr.path_records)
+    acc, rec = O.OracleScene(sc).trace_camera(spp, depth, nbins=nb, seed=13, flags=flags)
+    compare_camera(g, rec)
+    img = fr["direct"][..., :3].cpu().numpy()
+    assert np.mean((img - acc / spp) ** 2) <= MSE
+    if rough:  # the rough glass really scatters, and some paths end on it
+        assert (rec["n_specular"] >= 1).mean() > 0.05
+
+
+@pytest.mark.parametrize("variant", ["absorbing_rough", "jitter"])
+def test_light_parity_glass_variants(ctx, variant):
+    sc = _variant_glass(40, 40, roughness=0.15 if "rough" in variant else 0.0,
+                        absorption=(0.6, 1.5, 3.0) if "absorbing" in variant else (0, 0, 0))
+    flags = N.SC_FLAG_WAVELENGTH_JITTER if variant == "jitter" else 0
+    n = 1 << 16
+    _, fr = _render(ctx, sc, 0, 12, n_bins=8, n_light=n, seed=17, lflags=flags, guide=S.guide_sphere(sc))
+    g = R.light_records_numpy(fr.light_records)
+    acc, rec = O.OracleScene(sc).trace_lights(n, 12, nbins=8, seed=17, flags=flags, guide=S.guide_sphere(sc))
+    st = compare_lights(g, rec)
+    assert st["splatted"] > 0.002
+    img = fr["accum_caustic"][..., :3].cpu().numpy() / n
+    assert np.mean((img - acc / n) ** 2) <= MSE
