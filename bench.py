@@ -38,15 +38,30 @@ FLOPS_PER_NODE = 48
 FLOPS_PER_TRI = 43
 BYTES_PER_NODE = 112
 BYTES_PER_TRI = 48
-# our kernels per step: LBVH build (bounds init, gather, morton, 8 x (hist, scan, scatter),
-# reorder, karras, refit, depth, 4-wide collapse) + camera + lights + resolve
-LAUNCHES_PER_STEP = 31 + 3
+# our kernels per step besides the camera estimator: LBVH build (bounds init, gather, morton,
+# 8 x (hist, scan, scatter), reorder, karras, refit, depth, 4-wide collapse) + lights + resolve +
+# outline/occlusion pass
+LAUNCHES_PER_STEP_BASE = 31 + 3
+
+
+def camera_launches(engine, width, height, spp, depth):
+    """Kernel launches of one sc_trace_camera call: one persistent kernel, or per wave of whole
+    pixels (at most 2^24 paths) generate + depth x (extend, dielectric, diffuse, shadow, rotate) +
+    reduce."""
+    if engine == "persistent":
+        return 1
+    tiles = ((width + 7) // 8) * ((height + 3) // 4)
+    one_tile = 32 * spp
+    max_paths = max(one_tile, min(tiles * one_tile, 1 << 24))
+    wave_tiles = max(1, max_paths // one_tile)
+    waves = -(-tiles // wave_tiles)
+    return waves * (2 + 5 * depth)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size camera launch, from
 # one ncu capture of this kernel version:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
 #       -k regex:k_trace_camera -s 4 -c 1 python bench.py --steps 1 --warmup 3 --no-cpu-baseline
 # (the scene stays in L2, so DRAM sees little more than the accumulators and first touches)
-CAMERA_DRAM_BYTES = 24.5e6
+CAMERA_DRAM_BYTES = {"persistent": 24.5e6, "wavefront": None}
 
 
 def parse():
@@ -59,6 +74,8 @@ def parse():
     ap.add_argument("--light-paths", type=int, default=1 << 22)
     ap.add_argument("--res", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--camera-engine", default="wavefront", choices=["wavefront", "persistent"],
+                    help="sc_trace_camera engine: event-regrouped wavefront kernels or the persistent state machine")
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the sub-results (cfg1 frame, batch64, U-Net training) of the default line")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -716,6 +733,8 @@ def main():
     dev_arrays = R.SceneArrays(scene, dev)
     stream = torch.cuda.current_stream(dev)
     ctx = R.Context(local, stream)
+    R.N.sc_set_camera_engine(ctx.handle, {"wavefront": R.N.SC_CAMERA_WAVEFRONT,
+                                          "persistent": R.N.SC_CAMERA_PERSISTENT}[args.camera_engine])
     frame = R.Frame(res, res, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     sample_offset = rank * spp  # disjoint sample ranges per rank
@@ -812,21 +831,24 @@ def main():
     cam_flops = cam_counts[1] * FLOPS_PER_NODE + cam_counts[2] * FLOPS_PER_TRI
     cam_bytes = cam_counts[1] * BYTES_PER_NODE + cam_counts[2] * BYTES_PER_TRI
     hbm_peak = pk.get("hbm_gbs", 6800.0)
+    dram = CAMERA_DRAM_BYTES[args.camera_engine]
     bounds = {
         "fp32": {"achieved": cam_flops / cam_s / 1e12, "peak": mp["fp32_tflops"], "unit": "TFLOP/s",
                  "per_launch": cam_flops},
         "l2": {"achieved": cam_bytes / cam_s / 1e9, "peak": mp["l2_read_gbs"], "unit": "GB/s",
                "per_launch": cam_bytes},
-        "hbm": {"achieved": CAMERA_DRAM_BYTES / cam_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                "per_launch": CAMERA_DRAM_BYTES},
     }
+    if dram is not None:
+        bounds["hbm"] = {"achieved": dram / cam_s / 1e9, "peak": hbm_peak, "unit": "GB/s", "per_launch": dram}
     for b in bounds.values():
         b["frac"] = b["achieved"] / b["peak"]
     # the attainable rate is the minimum over the three ceilings: the binding one has the largest fraction
     bind = max(bounds, key=lambda k: bounds[k]["frac"])
-    roofline = {"kernel": "k_trace_camera", "bound": {"fp32": "alu", "l2": "l2", "hbm": "hbm"}[bind],
+    cam_kernel = ("camera traversal: k_wf_extend + k_wf_shadow, timed over the whole camera phase (all its kernels)"
+                  if args.camera_engine == "wavefront" else "k_trace_camera_t")
+    roofline = {"kernel": cam_kernel, "bound": {"fp32": "alu", "l2": "l2", "hbm": "hbm"}[bind],
                 "achieved": bounds[bind]["achieved"], "peak": bounds[bind]["peak"], "unit": bounds[bind]["unit"],
-                "frac": bounds[bind]["frac"], "traffic": CAMERA_DRAM_BYTES, "traffic_unit": "bytes per launch (ncu)",
+                "frac": bounds[bind]["frac"], "traffic": dram, "traffic_unit": "bytes per camera phase (ncu)",
                 "bounds": bounds,
                 "peak_source": "fp32 and l2: measured in this run (" + mp["how"] + "); hbm: MEASURED_PEAKS hbm_gbs "
                                "(of measured)",
@@ -861,6 +883,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "resolution": res, "spp": spp, "light_paths": nl, "max_depth": depth,
                        "wavelength_bins": nbins, "triangles": scene.n_tris, "parallelism": f"replicas x{world}",
+                       "camera_engine": args.camera_engine,
                        "l2": "flushed between steps (256 MB write)"},
             "frames_per_s": world * 1e3 / ms_per_step,
             "camera_mpaths_s": world * res * res * spp / (statistics.mean(cam_ms) * 1e-3) / 1e6,
@@ -873,7 +896,8 @@ def main():
                           "camera_l2_side_gbs": cam_bytes / cam_s / 1e9},
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "gpu_launches": (LAUNCHES_PER_STEP_BASE + camera_launches(args.camera_engine, res, res, spp, depth)) *
+                            args.steps,
             "clocks": clocks,
             "cpu_baseline": cb,
         }

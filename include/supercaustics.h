@@ -274,6 +274,19 @@ typedef struct {
 int sc_set_limits(sc_ctx *ctx, const sc_limits *limits);
 int sc_get_limits(const sc_ctx *ctx, sc_limits *limits);
 
+/* How sc_trace_camera runs the camera estimator (sc_trace_batch always uses the persistent
+ * state machine).  Both give the same path records and accumulators bit for bit.
+ *   SC_CAMERA_WAVEFRONT (default): waves of whole pixels (at most 2^24 paths each, all samples of
+ *     every pixel of the wave) advance one event at a time through separate kernels -- closest-hit
+ *     traversal, dielectric events, diffuse events with next-event estimation, shadow rays --
+ *     each over a queue of the paths at that event; path state in device memory allocated per
+ *     call (about 230 bytes per path of a wave) through the context's allocator.
+ *   SC_CAMERA_PERSISTENT: one persistent kernel whose lanes each run a path as a state machine,
+ *     interleaving traversal chunks and shading; no workspace. */
+enum { SC_CAMERA_WAVEFRONT = 0, SC_CAMERA_PERSISTENT = 1 };
+int sc_set_camera_engine(sc_ctx *ctx, int32_t engine);
+int sc_get_camera_engine(const sc_ctx *ctx, int32_t *engine);
+
 /* --- scene: LBVH build (Karras 2012 hierarchy over 30-bit Morton codes) ------------------ */
 int sc_build_scene(sc_ctx *ctx, const sc_scene_desc *desc, sc_scene **out);
 int sc_free_scene(sc_ctx *ctx, sc_scene *scene);

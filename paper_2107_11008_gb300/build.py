@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libsupercaustics.so")
-SOURCES = ["api.cu", "build.cu", "render.cu", "noalloc.cu", "peaks.cu", "unet.cu"]
+SOURCES = ["api.cu", "build.cu", "render.cu", "wavefront.cu", "noalloc.cu", "peaks.cu", "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -23,6 +23,7 @@ struct sc_ctx {
   unsigned long long *counters = nullptr;  // optional traversal work counters (device)
   // failure-detection limits of the traversals (sc_set_limits)
   int32_t max_visits = sc::kMaxVisits, stack4 = sc::kStack, stack2 = sc::kStack2;
+  int32_t camera_engine = SC_CAMERA_WAVEFRONT;  // sc_set_camera_engine
 };
 
 struct sc_scene {
@@ -214,6 +215,20 @@ int sc_set_limits(sc_ctx *c, const sc_limits *l) {
   c->max_visits = l->max_visits == 0 ? sc::kMaxVisits : (int32_t)std::min<int64_t>(l->max_visits, INT32_MAX);
   c->stack4 = l->stack_depth4 == 0 ? sc::kStack : l->stack_depth4;
   c->stack2 = l->stack_depth2 == 0 ? sc::kStack2 : l->stack_depth2;
+  return SC_OK;
+}
+
+int sc_set_camera_engine(sc_ctx *c, int32_t engine) {
+  if (!c) return SC_ERR_INVALID_ARG;
+  if (engine != SC_CAMERA_WAVEFRONT && engine != SC_CAMERA_PERSISTENT)
+    return fail(c, SC_ERR_INVALID_ARG, "sc_set_camera_engine: unknown engine");
+  c->camera_engine = engine;
+  return SC_OK;
+}
+
+int sc_get_camera_engine(const sc_ctx *c, int32_t *engine) {
+  if (!c || !engine) return SC_ERR_INVALID_ARG;
+  *engine = c->camera_engine;
   return SC_OK;
 }
 
@@ -482,6 +497,19 @@ int sc_trace_camera(sc_ctx *c, const sc_scene *s, const sc_trace_params *p, cons
   if (!p || p->spp < 0 || p->sample_offset < 0 || p->max_depth < 0 || p->n_bins < 1 || p->n_bins > sc::kMaxBins)
     return fail(c, SC_ERR_INVALID_ARG, "sc_trace_camera: bad parameters (n_bins must be 1..64)");
   if (p->spp == 0) return SC_OK;
+  if (c->camera_engine == SC_CAMERA_WAVEFRONT) {
+    // waves of whole pixels of up to 2^24 paths (at least one 8x4 tile with all its samples)
+    const int64_t tiles = (int64_t)((f->width + 7) / 8) * ((f->height + 3) / 4);
+    const int64_t one_tile = 32 * (int64_t)p->spp;
+    const int64_t max_paths = std::max<int64_t>(one_tile, std::min<int64_t>(tiles * one_tile, int64_t(1) << 24));
+    if (max_paths > INT32_MAX / 2) return fail(c, SC_ERR_INVALID_ARG, "sc_trace_camera: spp too large");
+    void *ws = dalloc(c, sc::wavefront_workspace_bytes(max_paths));
+    if (!ws) return fail(c, SC_ERR_OOM, "sc_trace_camera: no device memory for the path wavefront");
+    cudaError_t e = sc::launch_trace_camera_wavefront(launch_scene(c, s), *p, *f, c->d_words, c->counters, ws,
+                                                      max_paths, c->num_sms, c->stream);
+    dfree(c, ws);
+    return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_trace_camera");
+  }
   const int grid = persistent_grid(c, sc::camera_kernel_ptr(), &c->cam_blocks_per_sm);
   cudaError_t e = sc::launch_trace_camera(launch_scene(c, s), *p, *f, c->d_words, c->d_words + 1, c->counters, grid, c->stream);
   return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_trace_camera");

@@ -56,6 +56,12 @@ cudaError_t launch_intersect(const DevScene &S, const float *rays, int64_t n, fl
                              cudaStream_t s);
 cudaError_t launch_occluded(const DevScene &S, const float *rays, int64_t n, int32_t *occ, unsigned *status,
                             cudaStream_t s);
+// the camera estimator as a wavefront (wavefront.cu): waves of whole pixels of at most max_paths
+// paths, path state and queues in `workspace` (wavefront_workspace_bytes(max_paths) bytes)
+size_t wavefront_workspace_bytes(int64_t max_paths);
+cudaError_t launch_trace_camera_wavefront(const DevScene &S, const sc_trace_params &p, const sc_frame &f,
+                                          unsigned *status, unsigned long long *counters, void *workspace,
+                                          int64_t max_paths, int num_sms, cudaStream_t s);
 const void *camera_kernel_ptr();
 const void *light_kernel_ptr();
 struct BatchEntry;

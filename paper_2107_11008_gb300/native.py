@@ -129,6 +129,8 @@ SIGNATURES = {
     "sc_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sc_batch_destroy": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sc_set_limits": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sc_set_camera_engine": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sc_get_camera_engine": (C.c_int, [C.c_void_p, P(C.c_int32)]),
     "sc_get_limits": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sc_unet_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, P(C.c_int64)]),
     "sc_unet_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
@@ -313,6 +315,20 @@ def sc_set_limits(ctx, max_visits=0, stack_depth4=0, stack_depth2=0, defaults=Fa
     else:
         lim = sc_limits(max_visits, stack_depth4, stack_depth2)
         check(load().sc_set_limits(ctx, C.byref(lim)), ctx)
+
+
+SC_CAMERA_WAVEFRONT = 0
+SC_CAMERA_PERSISTENT = 1
+
+
+def sc_set_camera_engine(ctx, engine: int):
+    check(load().sc_set_camera_engine(ctx, engine), ctx)
+
+
+def sc_get_camera_engine(ctx) -> int:
+    e = C.c_int32()
+    check(load().sc_get_camera_engine(ctx, C.byref(e)), ctx)
+    return e.value
 
 
 def sc_get_limits(ctx) -> sc_limits:
