@@ -8,6 +8,7 @@ arrays produced by ``paper_2107_11008_gb300.scenes``.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 
@@ -81,7 +82,14 @@ class LightRec(C.Structure):
     _fields_ = [("C", C.c_double * 3), ("x", C.c_double * 3), ("pixel", C.c_int32), ("amb", C.c_int32),
                 ("signature", C.c_uint32), ("n_specular", C.c_int32), ("bin", C.c_int32), ("pad", C.c_int32),
                 ("min_ratio", C.c_double), ("ratio_nspec", C.c_int32), ("ratio_kind", C.c_int32),
-                ("kmin", C.c_double * 9), ("knspec", C.c_int32 * 9), ("pad2", C.c_int32)]
+                ("kmin", C.c_double * 9), ("knspec", C.c_int32 * 9), ("pad2", C.c_int32),
+                ("beta", C.c_double * 3), ("n", C.c_double * 3), ("photon", C.c_int32), ("pad3", C.c_int32)]
+
+
+class GatherRec(C.Structure):
+    _fields_ = [("x", C.c_double * 3), ("n", C.c_double * 3), ("w", C.c_double * 3), ("valid", C.c_int32),
+                ("bin", C.c_int32), ("amb", C.c_int32), ("n_specular", C.c_int32), ("signature", C.c_uint32),
+                ("pad", C.c_uint32)]
 
 
 class ResolveParams(C.Structure):
@@ -94,7 +102,7 @@ class PixelOut(C.Structure):
                 ("depth", C.c_double), ("depth_norm", C.c_double), ("n_world", C.c_double * 3),
                 ("n_cam", C.c_double * 3), ("albedo", C.c_double * 3), ("instance", C.c_int32), ("tri", C.c_int32),
                 ("mask", C.c_int32), ("caustic_mask", C.c_int32), ("local_caustic_mask", C.c_int32),
-                ("amb", C.c_int32)]
+                ("amb", C.c_int32), ("local_caustic", C.c_double * 3)]
 
 
 _lib = None
@@ -128,13 +136,16 @@ def lib():
                                    P(C.c_int)]
         L.orc_trace_camera.argtypes = [C.c_void_p, P(CamParams), P(C.c_double), P(PathRec)]
         L.orc_trace_lights.argtypes = [C.c_void_p, P(LightParams), P(C.c_double), P(LightRec)]
-        L.orc_resolve.argtypes = [C.c_void_p, P(ResolveParams), P(C.c_double), P(C.c_double), P(PixelOut)]
+        L.orc_resolve.argtypes = [C.c_void_p, P(ResolveParams), P(C.c_double), P(C.c_double), P(C.c_double),
+                                  P(PixelOut)]
         L.orc_sizes.argtypes = [P(C.c_int)]
         sizes = (C.c_int * 8)()
         L.orc_sizes(sizes)
-        want = [C.sizeof(t) for t in (CamParams, PathRec, LightParams, LightRec, ResolveParams, PixelOut, Tolerances)]
-        if list(sizes[:7]) != want:
-            raise RuntimeError(f"oracle struct layout mismatch: C {list(sizes[:7])} vs Python {want}")
+        want = [C.sizeof(t) for t in (CamParams, PathRec, LightParams, LightRec, ResolveParams, PixelOut, Tolerances,
+                                      GatherRec)]
+        if list(sizes[:8]) != want:
+            raise RuntimeError(f"oracle struct layout mismatch: C {list(sizes[:8])} vs Python {want}")
+        L.orc_trace_gather.argtypes = [C.c_void_p, P(CamParams), P(GatherRec)]
         _lib = L
     return _lib
 
@@ -223,12 +234,27 @@ class OracleScene:
         lib().orc_trace_lights(self.h, C.byref(P), _p(accum, C.c_double), recs)
         return accum, (records_to_numpy(recs, LightRec) if records else None)
 
-    def resolve(self, acc_cam, acc_caus, spp_total, light_paths_total, depth_range=10.0, tau_rel=0.25, brute=False):
+    def trace_gather(self, spp, max_depth, nbins=1, seed=0, sample_offset=0, scene_index=0, flags=0, window=None,
+                     brute=False):
+        """Gather points of the local-caustic estimate: per (pixel, sample) of the window, the first
+        diffuse vertex of the camera path's prefix if reached through glass (valid), its normal, bin
+        and camera-side weight beta * albedo / pi * W(lambda)."""
+        x0, x1, y0, y1 = window if window is not None else (0, self.W, 0, self.H)
+        tol = default_tol()
+        tol.sens_delta = 0.0
+        P = CamParams(spp, sample_offset, max_depth, nbins, seed, scene_index, flags, x0, x1, y0, y1, 1, int(brute), tol)
+        recs = (GatherRec * ((y1 - y0) * (x1 - x0) * spp))()
+        lib().orc_trace_gather(self.h, C.byref(P), recs)
+        return records_to_numpy(recs, GatherRec)
+
+    def resolve(self, acc_cam, acc_caus, spp_total, light_paths_total, depth_range=10.0, tau_rel=0.25, brute=False,
+                acc_local=None):
         P = ResolveParams(float(spp_total), float(light_paths_total), depth_range, tau_rel, int(brute), 0)
         out = (PixelOut * (self.W * self.H))()
         a = None if acc_cam is None else np.ascontiguousarray(acc_cam, np.float64)
         b = None if acc_caus is None else np.ascontiguousarray(acc_caus, np.float64)
-        lib().orc_resolve(self.h, C.byref(P), _p(a, C.c_double), _p(b, C.c_double), out)
+        c = None if acc_local is None else np.ascontiguousarray(acc_local, np.float64)
+        lib().orc_resolve(self.h, C.byref(P), _p(a, C.c_double), _p(b, C.c_double), _p(c, C.c_double), out)
         r = records_to_numpy(out, PixelOut)
         return {k: v.reshape((self.H, self.W) + v.shape[1:]) for k, v in r.items()}
 
@@ -249,6 +275,38 @@ def _np_fmt(t):
         return (_np_fmt(t._type_), (t._length_,))
     return {C.c_double: np.float64, C.c_float: np.float32, C.c_int32: np.int32, C.c_uint32: np.uint32,
             C.c_int64: np.int64, C.c_uint64: np.uint64}[t]
+
+
+def local_caustic_gather(gather: dict, photons: dict, radius: float, n_light_paths: int, nbins: int):
+    """Photon density estimate at the gather points (Jensen's photon map with a constant kernel):
+    L = w * B * sum(beta_i) / (N_L * pi * r^2) over the photons i of the gather point's bin within
+    distance r whose normal faces the same side (n_i . n > 0); B = bins (each photon's bin has
+    probability 1/B), N_L = light paths traced.  gather: trace_gather records; photons: trace_lights
+    records.  Returns (L [n, 3], margin [n]): margin = the smallest | |x_i - x| - r | / r over the
+    candidate photons, small where an FP32 evaluation may count a photon differently."""
+    from scipy.spatial import cKDTree
+
+    have = photons["photon"] != 0
+    px, pn, pb, pbin = photons["x"][have], photons["n"][have], photons["beta"][have], photons["bin"][have]
+    n = len(gather["valid"])
+    L = np.zeros((n, 3))
+    margin = np.full(n, np.inf)
+    if len(px) == 0:
+        return L, margin
+    tree = cKDTree(px)
+    valid = np.flatnonzero(gather["valid"] != 0)
+    lists = tree.query_ball_point(gather["x"][valid], r=radius * (1.0 + 1e-3))
+    norm = max(nbins, 1) / (n_light_paths * math.pi * radius * radius)
+    for i, cand in zip(valid, lists):
+        if not cand:
+            continue
+        cand = np.asarray(cand)
+        dist = np.linalg.norm(px[cand] - gather["x"][i], axis=1)
+        margin[i] = float(np.min(np.abs(dist - radius)) / radius)
+        sel = cand[(dist < radius) & (pbin[cand] == gather["bin"][i]) & (pn[cand] @ gather["n"][i] > 0)]
+        if len(sel):
+            L[i] = gather["w"][i] * pb[sel].sum(axis=0) * norm
+    return L, margin
 
 
 def philox(counters: np.ndarray, key: int) -> np.ndarray:

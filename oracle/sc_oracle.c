@@ -889,6 +889,12 @@ typedef struct {
   int32_t ratio_nspec, ratio_kind;
   double kmin[9];
   int32_t knspec[9], pad2;
+  /* photon of the local-caustic estimate: deposited at the first diffuse vertex after at least
+   * one specular event (photon = 1), with the path throughput there (no spectral weight) and the
+   * shading normal on the side the light came from */
+  double beta[3];
+  double n[3];
+  int32_t photon, pad3;
 } light_rec;
 
 static uint32_t fnv(uint32_t h, uint32_t w) { return (h ^ w) * 16777619u; }
@@ -949,10 +955,12 @@ static v3 nee(const scene *s, const surf *f, v3 albedo, const uint32_t x[4], int
   return mul(hadamard(albedo, le), geo * (double)s->nlights / PI);
 }
 
-/* Sensitivity re-trace: the same path with its ray nudged after every scattering event by a
+/* Sensitivity re-traces: the same path with its ray nudged after every scattering event by a
  * deterministic pseudo-random offset of relative size delta (a few float32 ulps or more).  A path
  * whose decisions or radiance move under such nudges cannot be reproduced by a float32 tracer
  * decision for decision, whatever its local margins. */
+/* the re-traces: two perturbation directions (stream salts) times both signs */
+static const uint64_t NUDGE_SALT[2] = {0xA5A5A5A5ull, 0x3C3C3C3C5A5A5A5Aull};
 static void nudge(ray *r, double delta, uint64_t seed, uint32_t c0, uint32_t c1, int k) {
   if (delta == 0.0) return;
   uint32_t x[4], y[4];
@@ -973,7 +981,7 @@ static int sensitive3(const double *a, const double *b, double rel) {
 }
 
 static void camera_path_impl(const scene *s, const cam_params *P, const double *wts, int px, int py,
-                             int sample, double delta, path_rec *rec) {
+                             int sample, double delta, uint64_t salt, path_rec *rec) {
   actx a;
   actx_init(&a, &P->tol);
   uint32_t pix = (uint32_t)(py * s->W + px);
@@ -982,7 +990,7 @@ static void camera_path_impl(const scene *s, const cam_params *P, const double *
   spec_sample sp = spectral_sample(x[2], P->nbins, P->flags, wts);
   int bin = sp.bin;
   ray r = camera_ray(s, (px + u01(x[0])) / s->W, (py + u01(x[1])) / s->H);
-  nudge(&r, delta, P->seed ^ 0xA5A5A5A5ull, pix, (uint32_t)sample, 0);
+  nudge(&r, delta, P->seed ^ salt, pix, (uint32_t)sample, 0);
   v3 beta = V(1, 1, 1), L = V(0, 0, 0);
   int spec_only = 1, diffuse_first = 0, n_diffuse = 0, q = 0;
   uint32_t sig = 2166136261u;
@@ -1028,7 +1036,7 @@ static void camera_path_impl(const scene *s, const cam_params *P, const double *
       last_specular = 1;
       r.o = offset_along(f.p, f.ng, d);
       r.d = d;
-      nudge(&r, delta, P->seed ^ 0xA5A5A5A5ull, pix, (uint32_t)sample, k + 1);
+      nudge(&r, delta, P->seed ^ salt, pix, (uint32_t)sample, k + 1);
       continue;
     }
     /* diffuse */
@@ -1054,7 +1062,7 @@ static void camera_path_impl(const scene *s, const cam_params *P, const double *
     beta = hadamard(beta, alb);
     r.o = add(f.p, mul(f.ngf, eps_of(f.p)));
     r.d = d;
-    nudge(&r, delta, P->seed ^ 0xA5A5A5A5ull, pix, (uint32_t)sample, k + 1);
+    nudge(&r, delta, P->seed ^ salt, pix, (uint32_t)sample, k + 1);
   }
   L = hadamard(L, sp.w);
   rec->L[0] = L.x; rec->L[1] = L.y; rec->L[2] = L.z;
@@ -1071,14 +1079,100 @@ static void camera_path_impl(const scene *s, const cam_params *P, const double *
 
 static void camera_path(const scene *s, const cam_params *P, const double *wts, int px, int py, int sample,
                         path_rec *rec) {
-  camera_path_impl(s, P, wts, px, py, sample, 0.0, rec);
+  camera_path_impl(s, P, wts, px, py, sample, 0.0, 0, rec);
   if (P->tol.sens_delta > 0) {
-    for (int sgn = -1; sgn <= 1; sgn += 2) {
-      path_rec alt;
-      camera_path_impl(s, P, wts, px, py, sample, sgn * P->tol.sens_delta, &alt);
-      if (alt.signature != rec->signature || sensitive3(alt.L, rec->L, P->tol.sens_rel)) rec->amb |= AMB_SENSITIVE;
-    }
+    for (int v = 0; v < 2 && !(rec->amb & AMB_SENSITIVE); ++v)
+      for (int sgn = -1; sgn <= 1; sgn += 2) {
+        path_rec alt;
+        camera_path_impl(s, P, wts, px, py, sample, sgn * P->tol.sens_delta, NUDGE_SALT[v], &alt);
+        if (alt.signature != rec->signature || sensitive3(alt.L, rec->L, P->tol.sens_rel)) rec->amb |= AMB_SENSITIVE;
+      }
   }
+}
+
+/* Local caustics (caustics seen through glass, E S+ D S+ L; Sec. III-D "Local & Non-local
+ * Caustics Mask"): a camera path's prefix, traced exactly as the camera estimator traces it (same
+ * draws, same dielectric events), up to its first non-dielectric hit.  If that is a diffuse
+ * surface reached after at least one dielectric event, the path gathers photons there; the
+ * record holds the gather point, its shading normal on the camera's side, the bin, and the
+ * camera-side weight w = beta * albedo / pi * W(lambda) (RGB).  Photon density estimation itself
+ * (photons of the same bin within the radius, normals on the same side) is done by the caller. */
+typedef struct {
+  double x[3], n[3], w[3];
+  int32_t valid, bin, amb, n_specular;
+  uint32_t signature, pad;
+} gather_rec;
+
+static void gather_path(const scene *s, const cam_params *P, const double *wts, int px, int py, int sample,
+                        gather_rec *rec) {
+  actx a;
+  actx_init(&a, &P->tol);
+  memset(rec, 0, sizeof(*rec));
+  uint32_t pix = (uint32_t)(py * s->W + px);
+  uint32_t x[4];
+  draw(P->seed, pix, (uint32_t)sample, 0, 0, (uint32_t)P->scene_index, x);
+  spec_sample sp = spectral_sample(x[2], P->nbins, P->flags, wts);
+  rec->bin = sp.bin;
+  ray r = camera_ray(s, (px + u01(x[0])) / s->W, (py + u01(x[1])) / s->H);
+  v3 beta = V(1, 1, 1);
+  uint32_t sig = 2166136261u;
+  for (int k = 0; k < P->max_depth; ++k) {
+    hit h = closest_noted(s, r, P->brute, &a);
+    sig = fnv(sig, h.tri < 0 ? EV_MISS : (uint32_t)h.tri);
+    if (h.tri < 0) break;
+    surf f = interact(s, r, h);
+    note(&a, fabs(f.cosg), P->tol.cosg, AMB_GRAZE);
+    const material *m = &s->mats[f.mat];
+    if (m->kind == MAT_DIELECTRIC && f.cosg > 0) beta = hadamard(beta, absorb_over(m, h.t));
+    if (m->kind == MAT_EMISSIVE) break;
+    if (m->kind == MAT_DIELECTRIC) {
+      uint32_t xs[4];
+      draw(P->seed, pix, (uint32_t)sample, (uint32_t)(k + 1), 1, (uint32_t)P->scene_index, xs);
+      int refl, fix;
+      double n_l = cauchy_at(m->A, m->B, sp.lam, P->nbins);
+      v3 d;
+      if (m->alpha > 0) {
+        double wgt;
+        int ok = rough_dielectric(&f, r.d, n_l, m->alpha, u01(xs[0]), u01(xs[1]), u01(xs[2]), P->flags, &d, &wgt,
+                                  &refl, &fix, &a);
+        if (!ok) { sig = fnv(sig, EV_KILL); ++a.nspec; break; }
+        beta = mul(beta, wgt);
+      } else {
+        d = dielectric(&f, r.d, n_l, u01(xs[0]), P->flags, &refl, &fix, &a);
+      }
+      sig = fnv(sig, refl ? EV_REFLECT : EV_REFRACT);
+      if (fix) sig = fnv(sig, EV_FIXUP);
+      ++a.nspec;
+      r.o = offset_along(f.p, f.ng, d);
+      r.d = d;
+      continue;
+    }
+    /* diffuse: the gather vertex when reached through glass */
+    if (a.nspec > 0) {
+      v3 alb = albedo_at(s, h.tri, &f, &a);
+      v3 w = hadamard(hadamard(beta, alb), sp.w);
+      rec->valid = 1;
+      rec->x[0] = f.p.x; rec->x[1] = f.p.y; rec->x[2] = f.p.z;
+      rec->n[0] = f.nsf.x; rec->n[1] = f.nsf.y; rec->n[2] = f.nsf.z;
+      rec->w[0] = w.x / PI; rec->w[1] = w.y / PI; rec->w[2] = w.z / PI;
+    }
+    break;
+  }
+  rec->amb = a.amb;
+  rec->n_specular = a.nspec;
+  rec->signature = sig;
+}
+
+/* one gather record per (pixel, sample) of the window, row-major, samples innermost */
+ORC_API void orc_trace_gather(void *sp, const cam_params *P, gather_rec *recs) {
+  const scene *s = sp;
+  double *wts = malloc(sizeof(double) * 3 * (size_t)(P->nbins > 1 ? P->nbins : 1));
+  orc_spectral_weights(P->nbins, wts, NULL);
+  int64_t i = 0;
+  for (int py = P->y0; py < P->y1; ++py)
+    for (int px = P->x0; px < P->x1; ++px)
+      for (int smp = 0; smp < P->spp; ++smp) gather_path(s, P, wts, px, py, P->sample_offset + smp, &recs[i++]);
+  free(wts);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -1104,6 +1198,7 @@ static double guided_dir(const double *g, v3 x, double u0, double u1, v3 *dir) {
   return 2.0 * PI * omc;
 }
 static void light_path_impl(const scene *s, const light_params *P, const double *wts, int64_t idx, double delta,
+                            uint64_t salt,
                             double *accum, light_rec *rec) {
   actx a;
   actx_init(&a, &P->tol);
@@ -1118,6 +1213,9 @@ static void light_path_impl(const scene *s, const light_params *P, const double 
   rec->C[0] = rec->C[1] = rec->C[2] = 0;
   rec->x[0] = rec->x[1] = rec->x[2] = NAN;
   rec->bin = bin;
+  rec->photon = 0;
+  rec->beta[0] = rec->beta[1] = rec->beta[2] = 0;
+  rec->n[0] = rec->n[1] = rec->n[2] = 0;
   if (s->nlights == 0) goto done;
   {
     int j = choose(xe[0], s->nlights);
@@ -1161,7 +1259,7 @@ static void light_path_impl(const scene *s, const light_params *P, const double 
       beta = mul(L->power, PI * L->radius * L->radius * s->nlights);
     }
     int had_spec = 0;
-    nudge(&r, delta, P->seed ^ 0x5A5A5A5Aull, lo, hi, 0);
+    nudge(&r, delta, P->seed ^ salt, lo, hi, 0);
     for (int k = 0; emitted && k < P->max_depth; ++k) {
       hit h = closest_noted(s, r, P->brute, &a);
       sig = fnv(sig, h.tri < 0 ? EV_MISS : (uint32_t)h.tri);
@@ -1192,12 +1290,17 @@ static void light_path_impl(const scene *s, const light_params *P, const double 
         had_spec = 1;
         r.o = offset_along(f.p, f.ng, d);
         r.d = d;
-        nudge(&r, delta, P->seed ^ 0x5A5A5A5Aull, lo, hi, k + 1);
+        nudge(&r, delta, P->seed ^ salt, lo, hi, k + 1);
         continue;
       }
       /* diffuse receiver */
       if (!had_spec && !(P->flags & FLAG_SPLAT_DIRECT)) break;
       rec->x[0] = f.p.x; rec->x[1] = f.p.y; rec->x[2] = f.p.z;
+      if (had_spec) {
+        rec->photon = 1;
+        rec->beta[0] = beta.x; rec->beta[1] = beta.y; rec->beta[2] = beta.z;
+        rec->n[0] = f.nsf.x; rec->n[1] = f.nsf.y; rec->n[2] = f.nsf.z;
+      }
       v3 alb = albedo_at(s, h.tri, &f, &a);
       v3 wc = sub(s->eye, f.p);
       double dc = len(wc);
@@ -1249,14 +1352,15 @@ done:
 
 static void light_path(const scene *s, const light_params *P, const double *wts, int64_t idx, double *accum,
                        light_rec *rec) {
-  light_path_impl(s, P, wts, idx, 0.0, accum, rec);
+  light_path_impl(s, P, wts, idx, 0.0, 0, accum, rec);
   if (P->tol.sens_delta > 0) {
-    for (int sgn = -1; sgn <= 1; sgn += 2) {
-      light_rec alt;
-      light_path_impl(s, P, wts, idx, sgn * P->tol.sens_delta, NULL, &alt);
-      if (alt.signature != rec->signature || alt.pixel != rec->pixel || sensitive3(alt.C, rec->C, P->tol.sens_rel))
-        rec->amb |= AMB_SENSITIVE;
-    }
+    for (int v = 0; v < 2 && !(rec->amb & AMB_SENSITIVE); ++v)
+      for (int sgn = -1; sgn <= 1; sgn += 2) {
+        light_rec alt;
+        light_path_impl(s, P, wts, idx, sgn * P->tol.sens_delta, NUDGE_SALT[v] ^ 0xFFull, NULL, &alt);
+        if (alt.signature != rec->signature || alt.pixel != rec->pixel || sensitive3(alt.C, rec->C, P->tol.sens_rel))
+          rec->amb |= AMB_SENSITIVE;
+      }
   }
 }
 
@@ -1391,12 +1495,14 @@ typedef struct {
   double depth, depth_norm;
   double n_world[3], n_cam[3], albedo[3];
   int32_t instance, tri, mask, caustic_mask, local_caustic_mask, amb;
+  double local_caustic[3];
 } pixel_out;
 
 static double luminance(const double *c) { return 0.2126 * c[0] + 0.7152 * c[1] + 0.0722 * c[2]; }
 
+/* acc_local (may be NULL): sums over the spp_total camera samples of the local-caustic gather */
 ORC_API void orc_resolve(void *sp, const resolve_params *P, const double *acc_cam, const double *acc_caus,
-                         pixel_out *out) {
+                         const double *acc_local, pixel_out *out) {
   const scene *s = sp;
   for (int py = 0; py < s->H; ++py)
     for (int px = 0; px < s->W; ++px) {
@@ -1406,7 +1512,8 @@ ORC_API void orc_resolve(void *sp, const resolve_params *P, const double *acc_ca
       for (int c = 0; c < 3; ++c) {
         o->direct[c] = acc_cam ? acc_cam[3 * i + c] / P->spp_total : 0.0;
         o->caustic[c] = (acc_caus && P->light_paths_total > 0) ? acc_caus[3 * i + c] / P->light_paths_total : 0.0;
-        o->rgb[c] = o->direct[c] + o->caustic[c];
+        o->local_caustic[c] = (acc_local && P->spp_total > 0) ? acc_local[3 * i + c] / P->spp_total : 0.0;
+        o->rgb[c] = o->direct[c] + o->caustic[c] + o->local_caustic[c];
       }
       actx a;
       actx_init(&a, &DEFAULT_TOL);
@@ -1432,7 +1539,9 @@ ORC_API void orc_resolve(void *sp, const resolve_params *P, const double *acc_ca
       o->albedo[0] = alb.x; o->albedo[1] = alb.y; o->albedo[2] = alb.z;
       double yc = luminance(o->caustic), yd = luminance(o->direct);
       o->caustic_mask = (m->kind != MAT_DIELECTRIC) && (yc > P->tau_rel * fmax(yd, 1e-3));
-      o->local_caustic_mask = 0;
+      /* local caustics: seen through the glass of this pixel (the with / without difference is the
+       * local-caustic buffer) */
+      o->local_caustic_mask = (m->kind == MAT_DIELECTRIC) && (luminance(o->local_caustic) > P->tau_rel * fmax(yd, 1e-3));
     }
 }
 
@@ -1444,5 +1553,6 @@ ORC_API int orc_sizes(int *out) {
   out[4] = (int)sizeof(resolve_params);
   out[5] = (int)sizeof(pixel_out);
   out[6] = (int)sizeof(tolerances);
-  return 7;
+  out[7] = (int)sizeof(gather_rec);
+  return 8;
 }

@@ -19,6 +19,10 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libsupercaustics.so")
 SOURCES = ["api.cu", "build.cu", "render.cu", "wavefront.cu", "noalloc.cu", "peaks.cu", "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The camera estimator exists twice (persistent state machine in render.cu, wavefront kernels in
+# wavefront.cu) built from the same device functions; without multiply-add contraction both
+# round every operation the same way, so the two give identical results bit for bit.
+PER_SOURCE_FLAGS = {"render.cu": ["-fmad=false"], "wavefront.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -51,7 +55,7 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags=()) ->
 
     def compile_one(src):
         obj = os.path.join(objdir, src.replace(".cu", ".o"))
-        cmd = [cc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc] + flags + PER_SOURCE_FLAGS.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
