@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define SC_ABI_VERSION 3
+#define SC_ABI_VERSION 4
 
 #define SC_OK 0
 #define SC_ERR_INVALID_ARG (-1)
@@ -201,14 +201,15 @@ typedef struct {
 typedef struct {
   float *accum_camera;      /* float4[W*H], radiance sums added by sc_trace_camera */
   float *accum_caustic;     /* float4[W*H], splat sums added by sc_trace_lights */
-  float *rgb;               /* float4[W*H] direct + caustic */
+  float *rgb;               /* float4[W*H] direct + caustic + local caustic */
   float *direct;            /* float4[W*H] camera estimator / spp_total */
   float *caustic;           /* float4[W*H] splats / light_paths_total */
   int32_t *instance_id;     /* int32[W*H] object id of the pixel-centre hit, -1 = miss */
   int32_t *tri_id;          /* int32[W*H] triangle id (input order), -1 = miss */
   uint8_t *mask;            /* uint8[W*H] 1 = transparent object */
   uint8_t *caustic_mask;    /* uint8[W*H] non-local caustic (on a non-glass surface) */
-  uint8_t *local_caustic_mask; /* uint8[W*H] caustic seen through glass (always 0) */
+  uint8_t *local_caustic_mask; /* uint8[W*H] local caustic: a glass pixel whose local-caustic
+                                  luminance exceeds tau_rel * max(direct luminance, 1e-3) */
   float *depth;             /* float[W*H] Euclidean distance, +inf = miss */
   float *depth_norm;        /* float[W*H] min(depth / depth_range, 1) */
   float *normal_world;      /* float4[W*H] shading normal facing the camera, w = 1 on hit */
@@ -223,6 +224,8 @@ typedef struct {
    * miss always jumps), 2 = contact edge (a neighbour shows another id, no jump), 0 = neither or
    * not transparent.  Needs instance_id, mask and depth. */
   uint8_t *occlusion;
+  float *accum_local_caustic; /* float4[W*H], photon-gather sums added by sc_gather_local_caustics */
+  float *local_caustic;     /* float4[W*H] accum_local_caustic / spp_total (added into rgb) */
   sc_path_record *path_records;    /* [H][W][spp] of the last sc_trace_camera call, or NULL */
   sc_light_record *light_records;  /* [n_paths] of the last sc_trace_lights call, or NULL */
   int32_t width, height;
@@ -344,6 +347,37 @@ int sc_trace_camera(sc_ctx *ctx, const sc_scene *scene, const sc_trace_params *p
 int sc_trace_lights(sc_ctx *ctx, const sc_scene *scene, const sc_light_params *params, const sc_frame *frame);
 /* Resolve: rgb/direct/caustic from the accumulators, plus the pixel-centre ground truth. */
 int sc_resolve(sc_ctx *ctx, const sc_scene *scene, const sc_resolve_params *params, const sc_frame *frame);
+
+/* --- local caustics: caustics seen through glass (photon map) ----------------------------------
+ * Sec. III-D separates caustics projected onto other surfaces (non-local: the splats of
+ * sc_trace_lights) from caustics seen inside the transparent objects (local).  A local caustic is a
+ * light path L S+ D seen along E S+: neither the splat (a straight unoccluded line to the pinhole)
+ * nor the camera estimator (its next-event rays are blocked by glass) reaches it, so it is estimated
+ * from a photon map.
+ * sc_photon_map_create: traces the light paths of `params` (the sc_trace_lights estimator: same
+ *   random numbers, guide, bins, flags) and keeps, per path reaching a diffuse surface after at least
+ *   one glass event, a photon: position, shading normal on the lit side, throughput, wavelength bin.
+ *   Photons are hashed into cells of 2 * radius and sorted by bucket (light-path order within a
+ *   bucket).  Device memory through the context's allocator: ~70 bytes per light path kept, ~130
+ *   during the build.  radius > 0 (scene units); n_paths in [1, 2^30].
+ * sc_gather_local_caustics: camera paths of `params` (the camera estimator's own random numbers and
+ *   decisions) follow their dielectric events to their first diffuse vertex; one reached through
+ *   glass adds beta * albedo / pi * W(lambda) * B * sum(throughput of the photons of its bin within
+ *   radius whose normal faces the same side) / (N_L * pi * radius^2) to frame->accum_local_caustic
+ *   (B bins, N_L light paths of the map).  params->n_bins must equal the map's.  Path records, if
+ *   requested, hold each sample's contribution (signature and counts of its prefix).  The estimate
+ *   is the constant-kernel density estimate of photon mapping: biased by the kernel's width, which
+ *   shrinks with the radius.
+ * sc_photon_map_export: host copies of the photons (n_paths x 12 floats, bucket order: position +
+ *   bin as int bits, normal + deposited flag, throughput + 0) and of order (n_paths uint32: the
+ *   light path of each slot).  Synchronises. */
+typedef struct sc_photon_map sc_photon_map;
+int sc_photon_map_create(sc_ctx *ctx, const sc_scene *scene, const sc_light_params *params, float radius,
+                         sc_photon_map **out);
+int sc_photon_map_destroy(sc_ctx *ctx, sc_photon_map *map);
+int sc_photon_map_export(sc_ctx *ctx, const sc_photon_map *map, float *photons_host, uint32_t *order_host);
+int sc_gather_local_caustics(sc_ctx *ctx, const sc_scene *scene, const sc_photon_map *map,
+                             const sc_trace_params *params, const sc_frame *frame);
 
 /* --- batched camera tracing ----------------------------------------------------------------
  * A dataset generator renders many randomised scenes (Sec. III-A, Sec. IV-A: thousands of

@@ -17,12 +17,13 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libsupercaustics.so")
-SOURCES = ["api.cu", "build.cu", "render.cu", "wavefront.cu", "noalloc.cu", "peaks.cu", "unet.cu"]
+SOURCES = ["api.cu", "build.cu", "render.cu", "wavefront.cu", "photons.cu", "noalloc.cu", "peaks.cu", "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The camera estimator exists twice (persistent state machine in render.cu, wavefront kernels in
-# wavefront.cu) built from the same device functions; without multiply-add contraction both
-# round every operation the same way, so the two give identical results bit for bit.
-PER_SOURCE_FLAGS = {"render.cu": ["-fmad=false"], "wavefront.cu": ["-fmad=false"]}
+# wavefront.cu) and its prefix a third time (photon gather in photons.cu), all built from the same
+# device functions; without multiply-add contraction each rounds every operation the same way, so
+# they take the same decisions and the two engines give identical results bit for bit.
+PER_SOURCE_FLAGS = {"render.cu": ["-fmad=false"], "wavefront.cu": ["-fmad=false"], "photons.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:

@@ -99,6 +99,12 @@ void ctx_set_error(sc_ctx *c, const std::string &msg) { c->err = msg; }
 void *ctx_alloc(sc_ctx *c, size_t bytes) { return dalloc(c, bytes); }
 void ctx_free(sc_ctx *c, void *p) { dfree(c, p); }
 unsigned *ctx_status(sc_ctx *c) { return c->d_words; }
+unsigned long long *ctx_counters(sc_ctx *c) { return c->counters; }
+int ctx_num_sms(const sc_ctx *c) { return c->num_sms; }
+bool scene_valid(const sc_scene *s) { return valid_scene(s); }
+DevScene scene_launch_view(const sc_ctx *c, const sc_scene *s) { return launch_scene(c, s); }
+// the light tracer for the photon map: no frame outputs, photons written to `photons`
+int trace_light_photons(sc_ctx *c, const sc_scene *s, const sc_light_params *p, float4 *photons);
 }  // namespace sc
 
 extern "C" {
@@ -532,6 +538,7 @@ int sc_trace_lights(sc_ctx *c, const sc_scene *s, const sc_light_params *p, cons
   return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_trace_lights");
 }
 
+
 // ---- batched camera tracing -----------------------------------------------------------------
 struct sc_batch {
   sc::BatchEntry *table = nullptr;  // device
@@ -664,3 +671,22 @@ int sc_resolve(sc_ctx *c, const sc_scene *s, const sc_resolve_params *p, const s
 }
 
 }  // extern "C"
+
+namespace sc {
+int trace_light_photons(sc_ctx *c, const sc_scene *s, const sc_light_params *p, float4 *photons) {
+  if (!p || p->n_paths <= 0 || p->path_offset < 0 || p->max_depth < 0 || p->n_bins < 1 || p->n_bins > kMaxBins)
+    return fail(c, SC_ERR_INVALID_ARG, "photon map: bad light parameters (n_paths >= 1, n_bins 1..64)");
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(p->guide[k])) return fail(c, SC_ERR_INVALID_ARG, "photon map: guide sphere not finite");
+  if (p->guide[3] > 0.0f && (p->flags & SC_FLAG_SPLAT_DIRECT))
+    return fail(c, SC_ERR_INVALID_ARG, "photon map: a guide sphere cannot be combined with SC_FLAG_SPLAT_DIRECT");
+  sc_frame f{};
+  f.width = s->dev.cam.width;
+  f.height = s->dev.cam.height;
+  const int grid = persistent_grid(c, light_kernel_ptr(), &c->light_blocks_per_sm);
+  cudaError_t e = launch_trace_lights(launch_scene(c, s), *p, f, c->d_words,
+                                      reinterpret_cast<unsigned long long *>(c->d_words + 2), c->counters, grid,
+                                      c->stream, photons);
+  return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "photon map: light tracing");
+}
+}  // namespace sc

@@ -431,6 +431,26 @@ __global__ void k_collapse4(BuildBuffers b) {
     if (e_ != cudaSuccess) return e_;          \
   } while (0)
 
+// Stable LSD radix sort of n (key, value) pairs on the byte digits first_byte .. first_byte +
+// passes - 1 of the keys (an even number of passes leaves the result in keys / vals).
+cudaError_t radix_sort_pairs(unsigned long long *keys, uint32_t *vals, unsigned long long *keys_alt,
+                             uint32_t *vals_alt, uint32_t *hist, int32_t n, int first_byte, int passes,
+                             cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = (int)sort_blocks(n);
+  unsigned long long *ka = keys, *kb = keys_alt;
+  uint32_t *va = vals, *vb = vals_alt;
+  for (int pass = 0; pass < passes; ++pass) {
+    const int shift = 8 * (first_byte + pass);
+    k_sort_hist<<<nb, kSortThreads, 0, s>>>(ka, n, shift, hist, nb);
+    k_scan<<<1, 1024, 0, s>>>(hist, 256 * nb);
+    k_sort_scatter<<<nb, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, hist, nb);
+    unsigned long long *tk = ka; ka = kb; kb = tk;
+    uint32_t *tv = va; va = vb; vb = tv;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_build(const BuildBuffers &b, cudaStream_t s) {
   const int n = b.n_tris;
   if (n <= 0) return cudaSuccess;

@@ -43,13 +43,18 @@ struct BuildBuffers {
 };
 size_t sort_blocks(int32_t n);
 cudaError_t launch_build(const BuildBuffers &b, cudaStream_t s);
+// stable LSD radix sort on key bytes first_byte .. first_byte + passes - 1 (hist: 256 *
+// sort_blocks(n) words); with an even number of passes the result is back in keys / vals
+cudaError_t radix_sort_pairs(unsigned long long *keys, uint32_t *vals, unsigned long long *keys_alt,
+                             uint32_t *vals_alt, uint32_t *hist, int32_t n, int first_byte, int passes,
+                             cudaStream_t s);
 
 // ---- renderer (render.cu) -----------------------------------------------------------------
 cudaError_t launch_trace_camera(const DevScene &S, const sc_trace_params &p, const sc_frame &f, unsigned *status,
                                 unsigned *ticket, unsigned long long *counters, int grid, cudaStream_t s);
 cudaError_t launch_trace_lights(const DevScene &S, const sc_light_params &p, const sc_frame &f, unsigned *status,
                                 unsigned long long *ticket, unsigned long long *counters, int grid,
-                                cudaStream_t s);
+                                cudaStream_t s, float4 *photons = nullptr);
 cudaError_t launch_resolve(const DevScene &S, const sc_resolve_params &p, const sc_frame &f, unsigned *status,
                            cudaStream_t s);
 cudaError_t launch_intersect(const DevScene &S, const float *rays, int64_t n, float *hits, unsigned *status,

@@ -325,9 +325,12 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS)
 }
 
 // One light path: emission, specular chain, splat at the first diffuse vertex after glass.
+// photons (optional): three float4 per path -- (position, bin as int bits), (shading normal on the
+// side the light arrived from, 1 if deposited), (throughput, 0) -- at that same vertex.
 __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_params P, sc_frame F,
                                                          unsigned *status, unsigned long long *ticket,
-                                                         unsigned long long *counters, JitterNorm jn) {
+                                                         unsigned long long *counters, JitterNorm jn,
+                                                         float4 *photons) {
   TravCount tc;
   __shared__ float3 wts[kMaxBins];
   spectral_table(wts, P.n_bins);
@@ -354,6 +357,8 @@ __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_pa
     float3 C = f3(0.f, 0.f, 0.f), X = f3(__int_as_float(0x7FC00000), __int_as_float(0x7FC00000),
                                          __int_as_float(0x7FC00000));
     bool emitted = true;
+    bool ph = false;
+    float3 phn = f3(0.f, 0.f, 0.f), phb = phn;
     if (S.n_lights > 0) {
       const int j = choose(xe.x, S.n_lights);
       const sc_light Lg = S.lights[j];
@@ -457,6 +462,11 @@ __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_pa
         }
         if (!had_spec && !(P.flags & SC_FLAG_SPLAT_DIRECT)) break;
         X = f.p;
+        if (had_spec) {
+          ph = true;
+          phn = f.nsf;
+          phb = beta;
+        }
         const float3 alb = albedo_at(S, m, f);
         float3 wc = cam.eye - f.p;
         const float dc = length(wc);
@@ -490,6 +500,12 @@ __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_pa
         break;
       }
     }
+    if (photons) {
+      float4 *q = photons + 3 * li;
+      q[0] = make_float4(X.x, X.y, X.z, __int_as_float(bin));
+      q[1] = make_float4(phn.x, phn.y, phn.z, ph ? 1.0f : 0.0f);
+      q[2] = make_float4(phb.x, phb.y, phb.z, 0.0f);
+    }
     if (F.light_records) {
       sc_light_record r;
       r.C[0] = C.x; r.C[1] = C.y; r.C[2] = C.z;
@@ -520,14 +536,18 @@ __global__ void k_resolve(DevScene S, sc_resolve_params P, sc_frame F, unsigned 
   float3 D = f3(0.f, 0.f, 0.f), C = f3(0.f, 0.f, 0.f);
   if (F.accum_camera) D = xyz(reinterpret_cast<const float4 *>(F.accum_camera)[pix]) * inv_spp;
   if (F.accum_caustic) C = xyz(reinterpret_cast<const float4 *>(F.accum_caustic)[pix]) * inv_nl;
+  float3 Lc = f3(0.f, 0.f, 0.f);
+  if (F.accum_local_caustic) Lc = xyz(reinterpret_cast<const float4 *>(F.accum_local_caustic)[pix]) * inv_spp;
   if (F.direct) reinterpret_cast<float4 *>(F.direct)[pix] = make_float4(D.x, D.y, D.z, 1.0f);
   if (F.caustic) reinterpret_cast<float4 *>(F.caustic)[pix] = make_float4(C.x, C.y, C.z, 1.0f);
-  if (F.rgb) reinterpret_cast<float4 *>(F.rgb)[pix] = make_float4(D.x + C.x, D.y + C.y, D.z + C.z, 1.0f);
+  if (F.local_caustic) reinterpret_cast<float4 *>(F.local_caustic)[pix] = make_float4(Lc.x, Lc.y, Lc.z, 1.0f);
+  if (F.rgb)
+    reinterpret_cast<float4 *>(F.rgb)[pix] = make_float4(D.x + C.x + Lc.x, D.y + C.y + Lc.y, D.z + C.z + Lc.z, 1.0f);
   const float3 d = cam_dir(cam, (px + 0.5f) / cam.W, (py + 0.5f) / cam.H);
   TravCount tc;
   const Hit h = closest_hit(S, cam.eye, d, 3.0e38f, status, tc);
   int inst = -1, tri = -1;
-  uint8_t mask = 0, cmask = 0;
+  uint8_t mask = 0, cmask = 0, lmask = 0;
   float depth = __int_as_float(0x7F800000), dn = 1.0f;
   float4 nw = make_float4(0.f, 0.f, 0.f, 0.f), nc = nw, alb = nw;
   if (h.prim >= 0) {
@@ -546,12 +566,14 @@ __global__ void k_resolve(DevScene S, sc_resolve_params P, sc_frame F, unsigned 
     const float yc = 0.2126f * C.x + 0.7152f * C.y + 0.0722f * C.z;
     const float yd = 0.2126f * D.x + 0.7152f * D.y + 0.0722f * D.z;
     cmask = (m.kind != SC_MAT_DIELECTRIC) && (yc > P.tau_rel * fmaxf(yd, 1e-3f));
+    const float yl = 0.2126f * Lc.x + 0.7152f * Lc.y + 0.0722f * Lc.z;
+    lmask = (m.kind == SC_MAT_DIELECTRIC) && (yl > P.tau_rel * fmaxf(yd, 1e-3f));
   }
   if (F.instance_id) F.instance_id[pix] = inst;
   if (F.tri_id) F.tri_id[pix] = tri;
   if (F.mask) F.mask[pix] = mask;
   if (F.caustic_mask) F.caustic_mask[pix] = cmask;
-  if (F.local_caustic_mask) F.local_caustic_mask[pix] = 0;
+  if (F.local_caustic_mask) F.local_caustic_mask[pix] = lmask;
   if (F.depth) F.depth[pix] = depth;
   if (F.depth_norm) F.depth_norm[pix] = dn;
   if (F.normal_world) reinterpret_cast<float4 *>(F.normal_world)[pix] = nw;
@@ -690,11 +712,11 @@ cudaError_t launch_trace_batch(const BatchEntry *tab, int n, unsigned total_bloc
 
 cudaError_t launch_trace_lights(const DevScene &S, const sc_light_params &p, const sc_frame &f, unsigned *status,
                                 unsigned long long *ticket, unsigned long long *counters, int grid,
-                                cudaStream_t s) {
+                                cudaStream_t s, float4 *photons) {
   cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   static const JitterNorm jn = jitter_norm_host();
-  k_trace_lights<<<grid, kBlock, 0, s>>>(S, p, f, status, ticket, counters, jn);
+  k_trace_lights<<<grid, kBlock, 0, s>>>(S, p, f, status, ticket, counters, jn, photons);
   return cudaGetLastError();
 }
 

@@ -79,7 +79,8 @@ class sc_light_record(C.Structure):
 
 FRAME_FIELDS = ["accum_camera", "accum_caustic", "rgb", "direct", "caustic", "instance_id", "tri_id", "mask",
                 "caustic_mask", "local_caustic_mask", "depth", "depth_norm", "normal_world", "normal_camera",
-                "albedo", "outline", "occlusion", "path_records", "light_records"]
+                "albedo", "outline", "occlusion", "accum_local_caustic", "local_caustic", "path_records",
+                "light_records"]
 
 
 class sc_frame(C.Structure):
@@ -136,6 +137,10 @@ SIGNATURES = {
     "sc_unet_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "sc_unet_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_char_p]),
     "sc_unet_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_char_p]),
+    "sc_photon_map_create": (C.c_int, [C.c_void_p, C.c_void_p, P(sc_light_params), C.c_float, P(C.c_void_p)]),
+    "sc_photon_map_destroy": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sc_photon_map_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sc_gather_local_caustics": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, P(sc_trace_params), P(sc_frame)]),
     "sc_peak_fma": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, P(C.c_int64)]),
     "sc_peak_l2_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, P(C.c_int64)]),
     # sc_unet.h
@@ -353,6 +358,24 @@ def sc_unet_save(ctx, net, path: str):
 
 def sc_unet_load(ctx, net, path: str):
     check(load().sc_unet_load(ctx, net, os.fsencode(path)), ctx)
+
+
+def sc_photon_map_create(ctx, scene, params: sc_light_params, radius: float):
+    out = C.c_void_p()
+    check(load().sc_photon_map_create(ctx, scene, C.byref(params), radius, C.byref(out)), ctx)
+    return out.value
+
+
+def sc_photon_map_destroy(ctx, pm):
+    check(load().sc_photon_map_destroy(ctx, pm), ctx)
+
+
+def sc_photon_map_export(ctx, pm, photons_host, order_host):
+    check(load().sc_photon_map_export(ctx, pm, photons_host, order_host), ctx)
+
+
+def sc_gather_local_caustics(ctx, scene, pm, params: sc_trace_params, frame: sc_frame):
+    check(load().sc_gather_local_caustics(ctx, scene, pm, C.byref(params), C.byref(frame)), ctx)
 
 
 def sc_peak_fma(ctx, iters, sink_dev) -> int:

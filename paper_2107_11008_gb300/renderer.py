@@ -177,7 +177,7 @@ class GpuScene:
 
 
 FLOAT4_FIELDS = ("accum_camera", "accum_caustic", "rgb", "direct", "caustic", "normal_world", "normal_camera",
-                 "albedo")
+                 "albedo", "accum_local_caustic", "local_caustic")
 
 
 class Frame:
@@ -185,7 +185,7 @@ class Frame:
 
     ALL = ("accum_camera", "accum_caustic", "rgb", "direct", "caustic", "instance_id", "tri_id", "mask",
            "caustic_mask", "local_caustic_mask", "depth", "depth_norm", "normal_world", "normal_camera", "albedo",
-           "outline", "occlusion")
+           "outline", "occlusion", "accum_local_caustic", "local_caustic")
 
     def __init__(self, width: int, height: int, device="cuda", fields=ALL):
         self.width, self.height = width, height
@@ -206,7 +206,7 @@ class Frame:
         return self.t[k]
 
     def zero_accumulators(self):
-        for k in ("accum_camera", "accum_caustic"):
+        for k in ("accum_camera", "accum_caustic", "accum_local_caustic"):
             if k in self.t:
                 self.t[k].zero_()
 
@@ -261,6 +261,45 @@ def resolve(ctx: Context, gs: GpuScene, frame: Frame, spp_total: float, light_pa
     p = N.sc_resolve_params(float(spp_total), float(light_paths_total), depth_range, tau_rel, int(outline_px),
                             float(depth_jump_rel))
     N.sc_resolve(ctx.handle, gs.handle, p, frame.struct())
+
+
+class PhotonMap:
+    """Photons of the light paths that reach a diffuse surface through glass, hashed for gathering
+    (sc_photon_map_create); ``gather`` adds the local caustics of camera paths to a frame."""
+
+    def __init__(self, ctx: Context, gs: GpuScene, n_paths: int, radius: float, max_depth: int, n_bins: int = 1,
+                 seed: int = 0, path_offset: int = 0, scene_index: int = 0, flags: int = 0, guide=None):
+        g = (0.0, 0.0, 0.0, 0.0) if guide is None else tuple(float(x) for x in guide)
+        p = N.sc_light_params(int(n_paths), int(path_offset), max_depth, n_bins, seed, scene_index, flags, g)
+        self.ctx, self.n_paths, self.radius = ctx, int(n_paths), float(radius)
+        self.handle = N.sc_photon_map_create(ctx.handle, gs.handle, p, float(radius))
+
+    def export(self):
+        """Photons in light-path order: dict of position (n,3), bin (n,), normal (n,3), deposited (n,),
+        throughput (n,3)."""
+        ph = np.empty((self.n_paths, 12), np.float32)
+        order = np.empty(self.n_paths, np.uint32)
+        N.sc_photon_map_export(self.ctx.handle, self.handle, ph.ctypes.data, order.ctypes.data)
+        out = np.empty_like(ph)
+        out[order] = ph
+        return {"x": out[:, 0:3], "bin": out[:, 3].view(np.int32), "n": out[:, 4:7], "photon": out[:, 7] != 0,
+                "beta": out[:, 8:11]}
+
+    def gather(self, gs: GpuScene, frame: Frame, spp: int, max_depth: int, n_bins: int = 1, seed: int = 0,
+               sample_offset: int = 0, scene_index: int = 0, flags: int = 0):
+        p = N.sc_trace_params(spp, sample_offset, max_depth, n_bins, seed, scene_index, flags)
+        N.sc_gather_local_caustics(self.ctx.handle, gs.handle, self.handle, p, frame.struct())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.sc_photon_map_destroy(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
 
 
 def intersect(ctx: Context, gs: GpuScene, origins: torch.Tensor, dirs: torch.Tensor, tmax: float = 3.0e38):

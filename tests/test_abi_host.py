@@ -40,7 +40,7 @@ def test_struct_layouts_and_version():
     from paper_2107_11008_gb300 import native as N
 
     lib = N.load()
-    assert N.sc_abi_version() == 3
+    assert N.sc_abi_version() == 4
     sizes = (C.c_int32 * 16)()
     k = lib.sc_struct_sizes(sizes, 16)
     assert k == len(N.STRUCTS)
