@@ -61,7 +61,11 @@ def camera_launches(engine, width, height, spp, depth):
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
 #       -k regex:k_trace_camera -s 4 -c 1 python bench.py --steps 1 --warmup 3 --no-cpu-baseline
 # (the scene stays in L2, so DRAM sees little more than the accumulators and first touches)
-CAMERA_DRAM_BYTES = {"persistent": 24.5e6, "wavefront": None}
+# wavefront: all kernels of one 256-spp camera phase, scaled by the path count (x16) from one ncu capture
+# of the 16-spp frame (the traffic is path state and queues, proportional to the paths):
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
+#       -k regex:k_wf_ -s 248 -c 62 python bench.py --steps 1 --warmup 3 --spp 16 --no-cpu-baseline --no-sub
+CAMERA_DRAM_BYTES = {"persistent": 24.5e6, "wavefront": 16 * 10.465e9}
 
 
 def parse():
