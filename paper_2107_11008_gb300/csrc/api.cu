@@ -543,7 +543,11 @@ int sc_trace_lights(sc_ctx *c, const sc_scene *s, const sc_light_params *p, cons
 struct sc_batch {
   sc::BatchEntry *table = nullptr;  // device
   int n = 0;
-  unsigned total = 0;
+  unsigned total = 0;         // blocks of the persistent engine
+  int64_t total_slots = 0;    // pixel slots of the wavefront engine
+  int engine = SC_CAMERA_WAVEFRONT;
+  void *workspace = nullptr;  // wavefront path state, kept for the graph's lifetime
+  int64_t max_paths = 0;
   sc_trace_params params{};
   cudaStream_t capture = nullptr;
   cudaGraph_t graph = nullptr;
@@ -551,13 +555,14 @@ struct sc_batch {
 };
 
 static int batch_table(sc_ctx *c, const sc_scene *const *scenes, const sc_frame *frames, int32_t n,
-                       const sc_trace_params *p, sc::BatchEntry **out, unsigned *total) {
+                       const sc_trace_params *p, sc::BatchEntry **out, unsigned *total, int64_t *total_slots) {
   if (!c || !scenes || !frames || n < 1 || !p) return fail(c, SC_ERR_INVALID_ARG, "batch: null argument or n < 1");
   if (p->spp < 0 || p->sample_offset < 0 || p->max_depth < 0 || p->n_bins < 1 || p->n_bins > sc::kMaxBins)
     return fail(c, SC_ERR_INVALID_ARG, "batch: bad parameters (n_bins must be 1..64)");
   sc::BatchEntry *h = new (std::nothrow) sc::BatchEntry[n];
   if (!h) return fail(c, SC_ERR_OOM, "batch: host table");
   unsigned begin = 0;
+  int64_t slots = 0;
   for (int i = 0; i < n; ++i) {
     const sc_scene *s = scenes[i];
     if (!valid_scene(s) || frames[i].width != s->dev.cam.width || frames[i].height != s->dev.cam.height) {
@@ -573,7 +578,13 @@ static int batch_table(sc_ctx *c, const sc_scene *const *scenes, const sc_frame 
     h[i].S = launch_scene(c, s);
     h[i].F = frames[i];
     h[i].begin = begin;
+    h[i].slot_begin = (unsigned)slots;
     begin += t;
+    slots += sc::scene_tickets(s->dev.cam);
+    if (slots > 0x7FFFFFFF) {
+      delete[] h;
+      return fail(c, SC_ERR_INVALID_ARG, "batch: more than 2^31 - 1 pixel slots");
+    }
   }
   sc::BatchEntry *d = static_cast<sc::BatchEntry *>(dalloc(c, sizeof(sc::BatchEntry) * n));
   if (!d) {
@@ -589,17 +600,37 @@ static int batch_table(sc_ctx *c, const sc_scene *const *scenes, const sc_frame 
   }
   *out = d;
   *total = begin;
+  *total_slots = slots;
   return SC_OK;
+}
+
+// wavefront workspace of a batch: waves of up to 2^24 paths, at least one 32-slot tile of all samples
+static int64_t batch_wave_paths(const sc_trace_params *p, int64_t total_slots) {
+  const int64_t one_tile = 32 * (int64_t)std::max(p->spp, 1);
+  return std::max<int64_t>(one_tile, std::min<int64_t>(total_slots * (int64_t)std::max(p->spp, 1), int64_t(1) << 24));
 }
 
 int sc_trace_batch(sc_ctx *c, const sc_scene *const *scenes, const sc_frame *frames, int32_t n,
                    const sc_trace_params *p) {
   sc::BatchEntry *tab = nullptr;
   unsigned total = 0;
-  int r = batch_table(c, scenes, frames, n, p, &tab, &total);
+  int64_t slots = 0;
+  int r = batch_table(c, scenes, frames, n, p, &tab, &total, &slots);
   if (r) return r;
-  cudaError_t e = p->spp > 0 ? sc::launch_trace_batch(tab, n, total, *p, c->d_words, c->counters, c->stream)
-                             : cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  if (p->spp > 0 && c->camera_engine == SC_CAMERA_WAVEFRONT) {
+    const int64_t max_paths = batch_wave_paths(p, slots);
+    void *ws = dalloc(c, sc::wavefront_workspace_bytes(max_paths));
+    if (!ws) {
+      dfree(c, tab);
+      return fail(c, SC_ERR_OOM, "sc_trace_batch: no device memory for the path wavefront");
+    }
+    e = sc::launch_trace_batch_wavefront(tab, n, slots, *p, c->d_words, c->counters, ws, max_paths, c->num_sms,
+                                         c->stream);
+    dfree(c, ws);
+  } else if (p->spp > 0) {
+    e = sc::launch_trace_batch(tab, n, total, *p, c->d_words, c->counters, c->stream);
+  }
   dfree(c, tab);
   return e == cudaSuccess ? SC_OK : cuda_fail(c, e, "sc_trace_batch");
 }
@@ -610,19 +641,34 @@ int sc_batch_create(sc_ctx *c, const sc_scene *const *scenes, const sc_frame *fr
   *out = nullptr;
   sc_batch *b = new (std::nothrow) sc_batch;
   if (!b) return fail(c, SC_ERR_OOM, "sc_batch_create: host allocation");
-  int r = batch_table(c, scenes, frames, n, p, &b->table, &b->total);
+  int r = batch_table(c, scenes, frames, n, p, &b->table, &b->total, &b->total_slots);
   if (r) {
     delete b;
     return r;
   }
   b->n = n;
   b->params = *p;
+  b->engine = c->camera_engine;
+  if (b->engine == SC_CAMERA_WAVEFRONT && p->spp > 0) {
+    b->max_paths = batch_wave_paths(p, b->total_slots);
+    b->workspace = dalloc(c, sc::wavefront_workspace_bytes(b->max_paths));
+    cudaError_t es = b->workspace ? cudaStreamSynchronize(c->stream) : cudaErrorMemoryAllocation;
+    if (es != cudaSuccess) {
+      if (b->workspace) dfree(c, b->workspace);
+      dfree(c, b->table);
+      delete b;
+      return cuda_fail(c, es, "sc_batch_create: path wavefront");
+    }
+  }
   cudaError_t e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t el = b->params.spp > 0 ? sc::launch_trace_batch(b->table, n, b->total, b->params, c->d_words,
-                                                                c->counters, b->capture)
-                                       : cudaSuccess;
+    cudaError_t el = cudaSuccess;
+    if (b->params.spp > 0 && b->engine == SC_CAMERA_WAVEFRONT)
+      el = sc::launch_trace_batch_wavefront(b->table, n, b->total_slots, b->params, c->d_words, c->counters,
+                                            b->workspace, b->max_paths, c->num_sms, b->capture);
+    else if (b->params.spp > 0)
+      el = sc::launch_trace_batch(b->table, n, b->total, b->params, c->d_words, c->counters, b->capture);
     e = cudaStreamEndCapture(b->capture, &b->graph);
     if (el != cudaSuccess) e = el;
   }
@@ -630,6 +676,7 @@ int sc_batch_create(sc_ctx *c, const sc_scene *const *scenes, const sc_frame *fr
   if (e != cudaSuccess) {
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->capture) cudaStreamDestroy(b->capture);
+    if (b->workspace) dfree(c, b->workspace);
     dfree(c, b->table);
     delete b;
     return cuda_fail(c, e, "sc_batch_create");
@@ -650,6 +697,7 @@ int sc_batch_destroy(sc_ctx *c, sc_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->capture) cudaStreamDestroy(b->capture);
+  if (b->workspace) dfree(c, b->workspace);
   dfree(c, b->table);
   delete b;
   return SC_OK;

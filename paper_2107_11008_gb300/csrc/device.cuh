@@ -227,12 +227,14 @@ __host__ __device__ __forceinline__ unsigned scene_blocks(const sc_camera &c) {
   return (scene_tickets(c) + kBatchChunk - 1) / kBatchChunk;
 }
 
-// One scene of a batched launch: its tables, its frame buffers and its first block.
+// One scene of a batched launch: its tables, its frame buffers, its first block (persistent
+// engine) and its first pixel slot in the concatenation of all scenes' tile-order slots (wavefront).
 struct BatchEntry {
   DevScene S;
   sc_frame F;
   unsigned begin;
-  unsigned pad[3];
+  unsigned slot_begin;
+  unsigned pad[2];
 };
 
 // ------------------------------------------------------------------------------------------

@@ -9,6 +9,7 @@
 namespace sc {
 
 struct DevScene;
+struct BatchEntry;
 
 // ---- LBVH build (build.cu) ----------------------------------------------------------------
 // Radix sort geometry: each sort block ranks kSortThreads * kSortItems keys, and the digit
@@ -67,6 +68,11 @@ size_t wavefront_workspace_bytes(int64_t max_paths);
 cudaError_t launch_trace_camera_wavefront(const DevScene &S, const sc_trace_params &p, const sc_frame &f,
                                           unsigned *status, unsigned long long *counters, void *workspace,
                                           int64_t max_paths, int num_sms, cudaStream_t s);
+// the batched launch on the wavefront engine: tab[i].slot_begin = first tile-order pixel slot of
+// scene i, total_slots = their sum
+cudaError_t launch_trace_batch_wavefront(const BatchEntry *tab, int n, int64_t total_slots, const sc_trace_params &p,
+                                         unsigned *status, unsigned long long *counters, void *workspace,
+                                         int64_t max_paths, int num_sms, cudaStream_t s);
 const void *camera_kernel_ptr();
 const void *light_kernel_ptr();
 struct BatchEntry;

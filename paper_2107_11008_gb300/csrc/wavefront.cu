@@ -20,6 +20,7 @@
 // functions), so path records and accumulators are bit for bit the same.  Path state lives in
 // HBM as structure of arrays; queues are compacted with warp-aggregated atomics.
 #include <algorithm>
+#include <cstring>
 
 #include "device.cuh"
 #include "internal.h"
@@ -55,21 +56,57 @@ struct Wave {
   int n;          // paths = wave_px * spp
 };
 
+// One scene (S, F) or, for a batch, the scene table: tab[i].slot_begin is the first tile-order
+// pixel slot of scene i in the batch's concatenation of all scenes' slots.
 struct WfArgs {
   DevScene S;
   sc_trace_params P;
   sc_frame F;
+  const BatchEntry *tab;
+  int n_tab;
   unsigned *status;
   unsigned long long *counters;
   JitterNorm jn;
-  int nb, tiles_x;
+  int nb;
   int jitter;
 };
 
-__device__ __forceinline__ void pixel_of(const WfArgs &a, int tslot, int &px, int &py) {
+// the scene, frame and random-stream scene index of scene sc (always the one scene without a batch)
+template <bool B>
+__device__ __forceinline__ const DevScene &scene_of(const WfArgs &a, int sc) {
+  return B ? a.tab[sc].S : a.S;
+}
+template <bool B>
+__device__ __forceinline__ const sc_frame &frame_of(const WfArgs &a, int sc) {
+  return B ? a.tab[sc].F : a.F;
+}
+template <bool B>
+__device__ __forceinline__ uint32_t stream_of(const WfArgs &a, int sc) {
+  return (uint32_t)(a.P.scene_index + (B ? sc : 0));
+}
+
+// global tile-order slot -> scene and local slot (binary search over the slot starts)
+template <bool B>
+__device__ __forceinline__ int slot_scene(const WfArgs &a, int g, int &local) {
+  if (!B) {
+    local = g;
+    return 0;
+  }
+  int lo = 0, hi = a.n_tab - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int)a.tab[mid].slot_begin <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  local = g - (int)a.tab[lo].slot_begin;
+  return lo;
+}
+
+__device__ __forceinline__ void pixel_of(const DevScene &S, int tslot, int &px, int &py) {
+  const unsigned tiles_x = (unsigned)((S.cam.width + 7) / 8);
   const unsigned tile = (unsigned)tslot >> 5, in = (unsigned)tslot & 31u;
-  px = (int)(tile % (unsigned)a.tiles_x) * 8 + (int)(in & 7u);
-  py = (int)(tile / (unsigned)a.tiles_x) * 4 + (int)(in >> 3);
+  px = (int)(tile % tiles_x) * 8 + (int)(in & 7u);
+  py = (int)(tile / tiles_x) * 4 + (int)(in >> 3);
 }
 
 // Appends v for every lane with pred set; the whole warp must call it together.
@@ -97,28 +134,32 @@ __device__ __forceinline__ void flush_counts(const WfArgs &a, const TravCount &t
 }
 
 // ---- generate: one path per (sample, pixel slot) of the wave -----------------------------------
+template <bool B>
 __global__ void __launch_bounds__(kWfBlock) k_wf_generate(WfArgs a, Wave w) {
-  const Cam cam = make_cam(a.S.cam);
   const int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < w.n; base += stride) {
     const int p = base + (threadIdx.x & 31);
     bool live = false;
     if (p < w.n) {
       const int s = p / w.wave_px, t = p - s * w.wave_px;
+      int local;
+      const int sc = slot_scene<B>(a, w.t0 + t, local);
+      const DevScene &S = scene_of<B>(a, sc);
+      const Cam cam = make_cam(S.cam);
       int px, py;
-      pixel_of(a, w.t0 + t, px, py);
+      pixel_of(S, local, px, py);
       live = px < cam.W && py < cam.H;
       w.L[p] = make_float4(0.f, 0.f, 0.f, live ? 0.0f : 1.0f);
       if (live) {
         const uint32_t pix = (uint32_t)(py * cam.W + px);
-        const uint4 x0 = draw(a.P.seed, pix, (uint32_t)(a.P.sample_offset + s), 0u, 0u, (uint32_t)a.P.scene_index);
+        const uint4 x0 = draw(a.P.seed, pix, (uint32_t)(a.P.sample_offset + s), 0u, 0u, stream_of<B>(a, sc));
         const float ul = u01(x0.z);
         const float3 d = cam_dir(cam, (px + u01(x0.x)) / cam.W, (py + u01(x0.y)) / cam.H);
         w.o[p] = make_float4(cam.eye.x, cam.eye.y, cam.eye.z, ul);
         w.d[p] = make_float4(d.x, d.y, d.z, 0.0f);
         w.beta[p] = make_float4(1.f, 1.f, 1.f, 0.f);
         w.m0[p] = make_uint4(2166136261u, kMiss, 0u, 0u);
-        w.m1[p] = make_uint4(0u, 0u, W_SPEC_ONLY, 0u);
+        w.m1[p] = make_uint4(0u, 0u, W_SPEC_ONLY, (uint32_t)sc);
       }
     }
     warp_push(w.q_ext[0], w.cnt + C_EXT0, live, (uint32_t)p);
@@ -126,17 +167,16 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_generate(WfArgs a, Wave w) {
 }
 
 // ---- extend: closest hits of the extend queue, classified by material ----------------------------
+template <bool B>
 __global__ void __launch_bounds__(kWfBlock) k_wf_extend(WfArgs a, Wave w, int cur) {
-  const DevScene &S = a.S;
   const uint32_t *q = w.q_ext[cur];
   const unsigned nq_total = w.cnt[cur ? C_EXT1 : C_EXT0];
   unsigned *ticket = w.cnt + C_TICKET_EXT;
   const int lane = threadIdx.x & 31;
-  const float3 env = f3(S.env);
   TravCount tc;
   TravState ts;
   int stack[kStack];
-  int p = -1;
+  int p = -1, sc = 0;
   bool tracing = false, exhausted = false;
   float3 o = f3(0.f, 0.f, 0.f), d = o;
   for (;;) {
@@ -152,6 +192,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_extend(WfArgs a, Wave w, int cu
         const unsigned t = base + (unsigned)__popc(wmask & ((1u << lane) - 1u));
         if (t < nq_total) {
           p = (int)q[t];
+          if (B) sc = (int)w.m1[p].w;
           const float4 o4 = w.o[p], d4 = w.d[p];
           o = f3(o4.x, o4.y, o4.z);
           d = f3(d4.x, d4.y, d4.z);
@@ -165,12 +206,14 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_extend(WfArgs a, Wave w, int cu
     if (__all_sync(0xFFFFFFFFu, !tracing && exhausted)) break;
     bool done = false;
     if (tracing) {
-      done = trav_step(S, make_wray(o, d), 3.0e38f, ts, stack, kWfChunk, a.status, tc);
+      done = trav_step(scene_of<B>(a, sc), make_wray(o, d), 3.0e38f, ts, stack, kWfChunk, a.status, tc);
       if (done) tracing = false;
     }
     // a finished query: record the hit, end the path or queue it for its material
     bool to_diel = false, to_diff = false;
     if (done) {
+      const DevScene &S = scene_of<B>(a, sc);
+      const float3 env = f3(S.env);
       ++tc.queries;
       const Hit h = ts.h;
       uint4 m0 = w.m0[p];
@@ -213,11 +256,15 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_extend(WfArgs a, Wave w, int cu
 }
 
 // pixel index and sample number of path slot p (for its random numbers)
+template <bool B>
 __device__ __forceinline__ void path_pixel(const WfArgs &a, const Wave &w, int p, uint32_t &pix, uint32_t &smp) {
   const int s = p / w.wave_px, t = p - s * w.wave_px;
+  int local;
+  const int sc = slot_scene<B>(a, w.t0 + t, local);
+  const DevScene &S = scene_of<B>(a, sc);
   int px, py;
-  pixel_of(a, w.t0 + t, px, py);
-  pix = (uint32_t)(py * a.S.cam.width + px);
+  pixel_of(S, local, px, py);
+  pix = (uint32_t)(py * S.cam.width + px);
   smp = (uint32_t)(a.P.sample_offset + s);
 }
 
@@ -233,8 +280,8 @@ __device__ __forceinline__ Hit load_hit(const Wave &w, int p) {
 }
 
 // ---- dielectric events -----------------------------------------------------------------------
+template <bool B>
 __global__ void __launch_bounds__(kWfBlock) k_wf_dielectric(WfArgs a, Wave w, int next) {
-  const DevScene &S = a.S;
   const unsigned n = w.cnt[C_DIEL];
   const int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < (int)n; base += stride) {
@@ -243,6 +290,9 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_dielectric(WfArgs a, Wave w, in
     int p = 0;
     if (i < (int)n) {
       p = (int)w.q_diel[i];
+      uint4 m0 = w.m0[p], m1 = w.m1[p];
+      const int sc = (int)m1.w;
+      const DevScene &S = scene_of<B>(a, sc);
       const float4 o4 = w.o[p], d4 = w.d[p], b4 = w.beta[p];
       const float ul = o4.w;
       const float3 d = f3(d4.x, d4.y, d4.z);
@@ -252,10 +302,9 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_dielectric(WfArgs a, Wave w, in
       const sc_material m = S.mats[SC_IN_RANGE(a.status, 7, f.mat, S.n_mats) ? f.mat : 0];
       // the segment ended on the glass's inner side: it ran through the glass (Beer-Lambert)
       if (f.cosg > 0.0f && absorbs(m)) beta = beta * absorb_over(m, h.t);
-      uint4 m0 = w.m0[p], m1 = w.m1[p];
       uint32_t pix, smp;
-      path_pixel(a, w, p, pix, smp);
-      const uint4 xs = draw(a.P.seed, pix, smp, m1.x + 1u, 1u, (uint32_t)a.P.scene_index);
+      path_pixel<B>(a, w, p, pix, smp);
+      const uint4 xs = draw(a.P.seed, pix, smp, m1.x + 1u, 1u, stream_of<B>(a, sc));
       bool refl, fix, alive = true;
       const float nl = cauchy_at(m.cauchy_a, m.cauchy_b, path_lambda(ul, a.nb, a.jitter), a.P.n_bins);
       float3 nd;
@@ -296,8 +345,8 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_dielectric(WfArgs a, Wave w, in
 }
 
 // ---- diffuse events: next-event estimate and cosine bounce -----------------------------------
+template <bool B>
 __global__ void __launch_bounds__(kWfBlock) k_wf_diffuse(WfArgs a, Wave w, int next) {
-  const DevScene &S = a.S;
   const unsigned n = w.cnt[C_DIFF];
   const int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < (int)n; base += stride) {
@@ -306,6 +355,9 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_diffuse(WfArgs a, Wave w, int n
     int p = 0;
     if (i < (int)n) {
       p = (int)w.q_diff[i];
+      uint4 m0 = w.m0[p], m1 = w.m1[p];
+      const int sc = (int)m1.w;
+      const DevScene &S = scene_of<B>(a, sc);
       const float4 o4 = w.o[p], d4 = w.d[p], b4 = w.beta[p];
       const float ul = o4.w;
       const float3 d = f3(d4.x, d4.y, d4.z);
@@ -313,16 +365,15 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_diffuse(WfArgs a, Wave w, int n
       const Hit h = load_hit(w, p);
       const Surf f = interact(S, d, h);
       const sc_material m = S.mats[SC_IN_RANGE(a.status, 7, f.mat, S.n_mats) ? f.mat : 0];
-      uint4 m0 = w.m0[p], m1 = w.m1[p];
       uint32_t pix, smp;
-      path_pixel(a, w, p, pix, smp);
+      path_pixel<B>(a, w, p, pix, smp);
       const uint32_t k = m1.x;
-      const uint4 xs = draw(a.P.seed, pix, smp, k + 1u, 1u, (uint32_t)a.P.scene_index);
+      const uint4 xs = draw(a.P.seed, pix, smp, k + 1u, 1u, stream_of<B>(a, sc));
       const float3 alb = albedo_at(S, m, f);
       float3 so = f3(0.f, 0.f, 0.f), sd = so, nee = so;
       float sdist = 0.0f;
       if (S.n_lights > 0) {
-        const uint4 xn = draw(a.P.seed, pix, smp, k + 1u, 2u, (uint32_t)a.P.scene_index);
+        const uint4 xn = draw(a.P.seed, pix, smp, k + 1u, 2u, stream_of<B>(a, sc));
         const sc_light Lg = S.lights[choose(xn.x, S.n_lights)];
         float3 lp = f3(0.f, 0.f, 0.f);
         float geo = 0.0f;
@@ -399,15 +450,15 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_diffuse(WfArgs a, Wave w, int n
 }
 
 // ---- shadow rays of the next-event estimates -----------------------------------------------------
+template <bool B>
 __global__ void __launch_bounds__(kWfBlock) k_wf_shadow(WfArgs a, Wave w, int next) {
-  const DevScene &S = a.S;
   const unsigned nq_total = w.cnt[C_SHADOW];
   unsigned *ticket = w.cnt + C_TICKET_SHADOW;
   const int lane = threadIdx.x & 31;
   TravCount tc;
   TravState ts;
   int stack[kStack];
-  int p = -1;
+  int p = -1, sc = 0;
   bool tracing = false, exhausted = false;
   float3 o = f3(0.f, 0.f, 0.f), d = o;
   float tmax = 0.0f;
@@ -423,6 +474,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_shadow(WfArgs a, Wave w, int ne
         const unsigned t = base + (unsigned)__popc(wmask & ((1u << lane) - 1u));
         if (t < nq_total) {
           p = (int)w.q_shadow[t];
+          if (B) sc = (int)w.m1[p].w;
           const float4 o4 = w.so[p], d4 = w.sd[p];
           o = f3(o4.x, o4.y, o4.z);
           d = f3(d4.x, d4.y, d4.z);
@@ -437,7 +489,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_shadow(WfArgs a, Wave w, int ne
     if (__all_sync(0xFFFFFFFFu, !tracing && exhausted)) break;
     bool done = false;
     if (tracing) {
-      done = trav_step(S, make_wray(o, d), tmax, ts, stack, kWfChunk, a.status, tc);
+      done = trav_step(scene_of<B>(a, sc), make_wray(o, d), tmax, ts, stack, kWfChunk, a.status, tc);
       if (done) tracing = false;
     }
     bool cont = false;
@@ -481,15 +533,20 @@ __global__ void k_wf_rotate(Wave w, int cur) {
 
 // Per pixel slot of the wave: its samples in order, each weighted by its wavelength (bin table or
 // jitter), summed and added to the accumulator; records of every path.
+template <bool B>
 __global__ void __launch_bounds__(kWfBlock) k_wf_reduce(WfArgs a, Wave w) {
   __shared__ float3 wts[kMaxBins];
   spectral_table(wts, a.P.n_bins);  // ends with __syncthreads
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= w.wave_px) return;
+  int local;
+  const int sc = slot_scene<B>(a, w.t0 + t, local);
+  const DevScene &S = scene_of<B>(a, sc);
+  const sc_frame &F = frame_of<B>(a, sc);
   int px, py;
-  pixel_of(a, w.t0 + t, px, py);
-  if (px >= a.S.cam.width || py >= a.S.cam.height) return;
-  const int pix = py * a.S.cam.width + px;
+  pixel_of(S, local, px, py);
+  if (px >= S.cam.width || py >= S.cam.height) return;
+  const int pix = py * S.cam.width + px;
   const int spp = a.P.spp;
   float3 acc = f3(0.f, 0.f, 0.f);
   for (int s = 0; s < spp; ++s) {
@@ -499,7 +556,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_reduce(WfArgs a, Wave w) {
     const int bin = bin_of(ul, a.nb);
     const float3 Lw = f3(L4.x, L4.y, L4.z) * (a.jitter ? jitter_weight(ul, a.jn) : wts[bin]);
     acc = acc + Lw;
-    if (a.F.path_records && SC_IN_RANGE(a.status, 9, (int64_t)pix * spp + s, (int64_t)a.S.cam.width * a.S.cam.height * spp)) {
+    if (F.path_records && SC_IN_RANGE(a.status, 9, (int64_t)pix * spp + s, (int64_t)S.cam.width * S.cam.height * spp)) {
       const uint4 m0 = w.m0[p];
       sc_path_record r;
       r.L[0] = Lw.x; r.L[1] = Lw.y; r.L[2] = Lw.z;
@@ -508,11 +565,11 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_reduce(WfArgs a, Wave w) {
       r.n_queries = m0.z;
       r.bin = (uint32_t)bin;
       r.n_specular = m0.w;
-      a.F.path_records[(int64_t)pix * spp + s] = r;
+      F.path_records[(int64_t)pix * spp + s] = r;
     }
   }
-  if (a.F.accum_camera && SC_IN_RANGE(a.status, 4, pix, a.S.cam.width * a.S.cam.height)) {
-    float4 *acp = reinterpret_cast<float4 *>(a.F.accum_camera) + pix;
+  if (F.accum_camera && SC_IN_RANGE(a.status, 4, pix, S.cam.width * S.cam.height)) {
+    float4 *acp = reinterpret_cast<float4 *>(F.accum_camera) + pix;
     float4 v = *acp;
     v.x += acc.x; v.y += acc.y; v.z += acc.z;
     *acp = v;
@@ -536,22 +593,10 @@ int64_t wavefront_wave_pixels(int width, int height, int spp, int64_t max_paths)
   return wave_tiles * 32;
 }
 
-cudaError_t launch_trace_camera_wavefront(const DevScene &S, const sc_trace_params &p, const sc_frame &f,
-                                          unsigned *status, unsigned long long *counters, void *workspace,
-                                          int64_t max_paths, int num_sms, cudaStream_t s) {
-  static const JitterNorm jn = jitter_norm_host();
-  WfArgs a;
-  a.S = S;
-  a.P = p;
-  a.F = f;
-  a.status = status;
-  a.counters = counters;
-  a.jn = jn;
-  a.nb = p.n_bins > 0 ? p.n_bins : 1;
-  a.jitter = (p.flags & SC_FLAG_WAVELENGTH_JITTER) && a.nb > 1;
-  a.tiles_x = (S.cam.width + 7) / 8;
-  const int64_t total_px = (int64_t)a.tiles_x * ((S.cam.height + 3) / 4) * 32;
-  const int64_t wave_px = wavefront_wave_pixels(S.cam.width, S.cam.height, p.spp, max_paths);
+namespace {
+
+// Carves the wave's arrays out of the workspace (the layout wavefront_workspace_bytes sizes).
+bool carve_wave(void *workspace, int64_t max_paths, Wave &w) {
   const size_t n = (size_t)max_paths;
   char *base = static_cast<char *>(workspace);
   size_t off = 0;
@@ -560,7 +605,6 @@ cudaError_t launch_trace_camera_wavefront(const DevScene &S, const sc_trace_para
     off += a256(bytes);
     return r;
   };
-  Wave w;
   w.o = reinterpret_cast<float4 *>(take(16 * n));
   w.d = reinterpret_cast<float4 *>(take(16 * n));
   w.beta = reinterpret_cast<float4 *>(take(16 * n));
@@ -579,32 +623,80 @@ cudaError_t launch_trace_camera_wavefront(const DevScene &S, const sc_trace_para
   w.q_diff = reinterpret_cast<uint32_t *>(take(4 * n));
   w.q_shadow = reinterpret_cast<uint32_t *>(take(4 * n));
   w.cnt = reinterpret_cast<unsigned *>(take(4 * C_WORDS));
-  if (off > wavefront_workspace_bytes(max_paths)) return cudaErrorInvalidValue;
+  return off <= wavefront_workspace_bytes(max_paths);
+}
+
+// Waves of whole pixel slots over [0, total_slots): each wave's kernels, bounce by bounce.
+template <bool B>
+cudaError_t run_waves(const WfArgs &a, Wave w, int64_t total_slots, int64_t wave_px, int num_sms, cudaStream_t s) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wf_extend, kWfBlock, 0);
-  if (e != cudaSuccess || per_sm <= 0) per_sm = 4;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wf_extend<B>, kWfBlock, 0);
+  if (e != cudaSuccess || per_sm <= 0) {
+    cudaGetLastError();
+    per_sm = 4;
+  }
   const int persistent = num_sms * per_sm;
   const int wide = num_sms * 16;
-  for (int64_t t0 = 0; t0 < total_px; t0 += wave_px) {
+  for (int64_t t0 = 0; t0 < total_slots; t0 += wave_px) {
     w.t0 = (int)t0;
-    w.wave_px = (int)std::min<int64_t>(wave_px, total_px - t0);
-    w.n = w.wave_px * p.spp;
+    w.wave_px = (int)std::min<int64_t>(wave_px, total_slots - t0);
+    w.n = w.wave_px * a.P.spp;
     e = cudaMemsetAsync(w.cnt, 0, 4 * C_WORDS, s);
     if (e != cudaSuccess) return e;
-    k_wf_generate<<<std::max(1, std::min(wide, (w.n + kWfBlock - 1) / kWfBlock)), kWfBlock, 0, s>>>(a, w);
-    for (int b = 0; b < p.max_depth; ++b) {
+    k_wf_generate<B><<<std::max(1, std::min(wide, (w.n + kWfBlock - 1) / kWfBlock)), kWfBlock, 0, s>>>(a, w);
+    for (int b = 0; b < a.P.max_depth; ++b) {
       const int cur = b & 1, next = cur ^ 1;
-      k_wf_extend<<<persistent, kWfBlock, 0, s>>>(a, w, cur);
-      k_wf_dielectric<<<wide, kWfBlock, 0, s>>>(a, w, next);
-      k_wf_diffuse<<<wide, kWfBlock, 0, s>>>(a, w, next);
-      k_wf_shadow<<<persistent, kWfBlock, 0, s>>>(a, w, next);
+      k_wf_extend<B><<<persistent, kWfBlock, 0, s>>>(a, w, cur);
+      k_wf_dielectric<B><<<wide, kWfBlock, 0, s>>>(a, w, next);
+      k_wf_diffuse<B><<<wide, kWfBlock, 0, s>>>(a, w, next);
+      k_wf_shadow<B><<<persistent, kWfBlock, 0, s>>>(a, w, next);
       k_wf_rotate<<<1, 32, 0, s>>>(w, cur);
     }
-    k_wf_reduce<<<(w.wave_px + kWfBlock - 1) / kWfBlock, kWfBlock, 0, s>>>(a, w);
+    k_wf_reduce<B><<<(w.wave_px + kWfBlock - 1) / kWfBlock, kWfBlock, 0, s>>>(a, w);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+WfArgs make_args(const sc_trace_params &p, unsigned *status, unsigned long long *counters) {
+  static const JitterNorm jn = jitter_norm_host();
+  WfArgs a;
+  memset(&a, 0, sizeof(a));
+  a.P = p;
+  a.status = status;
+  a.counters = counters;
+  a.jn = jn;
+  a.nb = p.n_bins > 0 ? p.n_bins : 1;
+  a.jitter = (p.flags & SC_FLAG_WAVELENGTH_JITTER) && a.nb > 1;
+  return a;
+}
+
+}  // namespace
+
+cudaError_t launch_trace_camera_wavefront(const DevScene &S, const sc_trace_params &p, const sc_frame &f,
+                                          unsigned *status, unsigned long long *counters, void *workspace,
+                                          int64_t max_paths, int num_sms, cudaStream_t s) {
+  WfArgs a = make_args(p, status, counters);
+  a.S = S;
+  a.F = f;
+  Wave w;
+  if (!carve_wave(workspace, max_paths, w)) return cudaErrorInvalidValue;
+  const int64_t total_slots = (int64_t)scene_tickets(S.cam);
+  const int64_t wave_px = wavefront_wave_pixels(S.cam.width, S.cam.height, p.spp, max_paths);
+  return run_waves<false>(a, w, total_slots, wave_px, num_sms, s);
+}
+
+cudaError_t launch_trace_batch_wavefront(const BatchEntry *tab, int n, int64_t total_slots, const sc_trace_params &p,
+                                         unsigned *status, unsigned long long *counters, void *workspace,
+                                         int64_t max_paths, int num_sms, cudaStream_t s) {
+  WfArgs a = make_args(p, status, counters);
+  a.tab = tab;
+  a.n_tab = n;
+  Wave w;
+  if (!carve_wave(workspace, max_paths, w)) return cudaErrorInvalidValue;
+  const int64_t wave_px = std::max<int64_t>(32, max_paths / (32 * (int64_t)std::max(p.spp, 1)) * 32);
+  return run_waves<true>(a, w, total_slots, wave_px, num_sms, s);
 }
 
 }  // namespace sc
