@@ -85,7 +85,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--den-ratio", type=int, default=16, help="denoise workload: light paths per camera sample")
     ap.add_argument("--den-steps", type=int, default=48000, help="denoise workload: training steps")
-    ap.add_argument("--workload", default="glass512", choices=["glass512", "batch64", "unet_train", "denoise"],
+    ap.add_argument("--seg-steps", type=int, default=4000, help="caustic_seg workload: training steps")
+    ap.add_argument("--workload", default="glass512",
+                    choices=["glass512", "batch64", "unet_train", "denoise", "caustic_seg"],
                     help="batch64: 64 randomised scenes (1k-200k tris, 128^2..1024^2, 64 spp) in one graph-captured "
                          "persistent launch vs 64 sequential launches; unet_train: U-Net training steps on batches "
                          "of 16 x 256^2 render pairs; denoise: 4-spp render + U-Net vs the plain tracer at matched MSE")
@@ -490,6 +492,76 @@ def run_denoise(args):
         print(json.dumps(line), flush=True)
 
 
+def run_caustic_seg(args):
+    """The paper's caustic-segmentation experiment (Sec. IV-B, Table II), synthetic -> synthetic: the
+    BF16 U-Net trained with the segmentation loss on rendered 128^2 glass scenes labelled by their
+    caustic masks, evaluated by IoU on held-out scenes of the training object families and on scenes
+    of a family it never saw; against a brightness-threshold baseline."""
+    import torch
+
+    from paper_2107_11008_gb300 import denoiser as D
+    from paper_2107_11008_gb300 import native as N
+    from paper_2107_11008_gb300 import renderer as R
+    from paper_2107_11008_gb300 import scenes as S
+    from paper_2107_11008_gb300 import training as T
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hw, n_train, n_test = 128, 256, 48
+    known, novel = ("sphere", "cylinder", "torus"), ("superellipsoid",)
+    spec = T.RenderSpec(16, 128, max_depth=8)
+    stream = torch.cuda.current_stream(dev)
+    ctx = R.Context(local, stream)
+    t0 = time.perf_counter()
+
+    def scenes(seed0, n, fams):
+        return [S.glass_scene(seed0 + i, hw, hw, n_objects=3, tris_per_object=2000, families=fams) for i in range(n)]
+
+    train = T.seg_data(ctx, scenes(20_000 + 1000 * rank, n_train, known), spec, seed=1)
+    test_known = T.seg_data(ctx, scenes(30_000, n_test, known), spec, seed=2)
+    test_novel = T.seg_data(ctx, scenes(40_000, n_test, novel), spec, seed=3)
+    data_s = time.perf_counter() - t0
+    net = D.UNet(ctx, 16, hw, hw)
+    net.set_params(D.he_init(0).to(dev))
+    net.set_loss(N.SC_UNET_LOSS_BCE)
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    sampler = ClockSampler(local)
+    ev[0].record(stream)
+    logged = T.train(net, train, steps=args.seg_steps, batch=16, lr=2e-3, lr_final=1e-4, seed=0, log_every=500)
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ctx.sync_status()
+    train_ms = ev[0].elapsed_time(ev[1])
+    lab = lambda d: d.target[..., 0] > 0.5  # noqa: E731
+    iou_known = T.iou(T.predict_masks(net, test_known.x), lab(test_known))
+    iou_novel = T.iou(T.predict_masks(net, test_novel.x), lab(test_novel))
+    iou_train = T.iou(T.predict_masks(net, train.x), lab(train))
+    thr, (b_known, b_novel) = T.brightness_baseline(train, [test_known, test_novel])
+    if rank == 0:
+        line = {"metric": "caustic segmentation IoU, held-out scenes of the training object families", "value": iou_known,
+                "unit": "IoU", "n_gpus": world, "steps": args.seg_steps, "warmup": 0,
+                "ms_per_step": train_ms / args.seg_steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16", "data": "synthetic (scenes.glass_scene)",
+                "config": {"workload": f"caustic_seg: {n_train} training scenes of 128^2 ({'/'.join(known)}, 3 glass "
+                                       f"objects each), labels = non-local caustic masks, input = rendered RGB "
+                                       f"(16 spp + 128 guided light paths/px); tests: {n_test} scenes of the same "
+                                       f"families, {n_test} of an unseen family ({novel[0]})",
+                           "loss": "binary cross-entropy with logits (sc_unet_set_loss)", "batch": 16,
+                           "steps": args.seg_steps},
+                "iou": {"known_objects": iou_known, "novel_objects": iou_novel, "training_images": iou_train},
+                "brightness_threshold_baseline": {"threshold_log1p_luminance": thr, "known_objects": b_known,
+                                                  "novel_objects": b_novel},
+                "caustic_pixel_fraction": {"train": float(lab(train).float().mean()),
+                                           "known": float(lab(test_known).float().mean()),
+                                           "novel": float(lab(test_novel).float().mean())},
+                "loss_log": logged, "data_generation_s": data_s, "train_images_s": 16e3 * args.seg_steps / train_ms,
+                "gpu_launches": None, "clocks": clocks, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -719,6 +791,9 @@ def main():
         return
     if args.workload == "denoise":
         run_denoise(args)
+        return
+    if args.workload == "caustic_seg":
+        run_caustic_seg(args)
         return
     import torch
     import torch.distributed as dist

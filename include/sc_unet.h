@@ -84,6 +84,15 @@ int sc_unet_adam(sc_ctx *ctx, sc_unet *net, float lr);
 int sc_unet_train_step(sc_ctx *ctx, sc_unet *net, const float *x, const float *target, int32_t n, float lr,
                        float *loss);
 
+/* Training loss of sc_unet_loss_grad / sc_unet_train_step (default SC_UNET_LOSS_L1_SSIM, above).
+ * SC_UNET_LOSS_BCE trains a segmentation network (the paper's Sec. IV trains its U-Net to segment
+ * transparent objects and caustics): output channel 0 is a logit, target channel 0 a label in
+ * [0, 1], loss = mean over pixels of softplus(y) - t y (binary cross-entropy with logits, FP64
+ * partial sums in a fixed order); output channels 1 and 2 and target channels 1 and 2 take no part
+ * (zero gradient).  The loss stays set until changed. */
+enum { SC_UNET_LOSS_L1_SSIM = 0, SC_UNET_LOSS_BCE = 1 };
+int sc_unet_set_loss(sc_ctx *ctx, sc_unet *net, int32_t kind);
+
 /* Training state (checkpoint / resume).  The state is the FP32 master parameters, the two Adam
  * moment vectors (sc_unet_param_count floats each, same flat layout) and the Adam step count, which
  * sets the bias corrections of the next step.  Restoring all of it and repeating the same calls

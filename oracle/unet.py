@@ -248,6 +248,26 @@ def loss(pred, target):
     return value, grad
 
 
+def loss_bce(pred, target):
+    """Segmentation loss (Sec. IV trains a U-Net to segment transparent objects and caustics):
+    binary cross-entropy with the logit in channel 0 and the label in target channel 0, mean over
+    pixels of -[t log s(y) + (1 - t) log(1 - s(y))], s the logistic function; channels 1 and 2 take
+    no part.  Returns (loss, d loss / d pred)."""
+    y = pred[..., 0].astype(np.float64)
+    t = target[..., 0].astype(np.float64)
+    s = 1.0 / (1.0 + np.exp(-y))
+    n = y.size
+
+    def softplus(z):  # log(1 + e^z) without overflow or cancellation
+        return np.maximum(z, 0.0) + np.log1p(np.exp(-np.abs(z)))
+
+    # log s(y) = -softplus(-y), log(1 - s(y)) = -softplus(y)
+    value = float((t * softplus(-y) + (1.0 - t) * softplus(y)).sum() / n)
+    grad = np.zeros(pred.shape)
+    grad[..., 0] = (s - t) / n
+    return value, grad
+
+
 # ------------------------------------------------------------------------------------------
 # Adam
 # ------------------------------------------------------------------------------------------

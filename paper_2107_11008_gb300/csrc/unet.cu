@@ -564,6 +564,42 @@ __global__ void k_loss_final(const double *ps, int nps, const double *pl, int np
   if (threadIdx.x == 0 && loss) *loss = (float)(kL1W * L / n_px + kSsimW * (1.0 - S / n_win));
 }
 
+// Segmentation loss: binary cross-entropy with the logit in output channel 0 and a label in [0, 1]
+// in target channel 0 (channels 1 and 2 take no part: zero gradient).  Per pixel
+// softplus(y) - t y = max(y, 0) - t y + log1p(exp(-|y|)); d / d y = (sigmoid(y) - t) / n_px.
+// One block per 256 pixels; block partial sums in FP64, summed in a fixed order.
+__global__ void __launch_bounds__(256) k_bce(const float *p, const float *t, int64_t n_px, float inv_px, float *grad,
+                                             bf16 *gy8, double *part) {
+  __shared__ double red[256];
+  const int64_t pix = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  double acc = 0.0;
+  if (pix < n_px) {
+    const float y = p[pix * 3], tv = t[pix * 3];
+    const float g = (1.0f / (1.0f + expf(-y)) - tv) * inv_px;
+    const double yd = (double)y;
+    acc = fmax(yd, 0.0) - (double)tv * yd + log1p(exp(-fabs(yd)));
+    if (grad) {
+      grad[pix * 3] = g;
+      grad[pix * 3 + 1] = 0.0f;
+      grad[pix * 3 + 2] = 0.0f;
+    }
+    if (gy8) {
+      float v[8] = {g, 0, 0, 0, 0, 0, 0, 0};
+      *reinterpret_cast<uint4 *>(gy8 + pix * kGyCh) = pack8(v);
+    }
+  }
+  const double sblk = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = sblk;
+}
+
+__global__ void k_bce_final(const double *part, int np, double n_px, float *loss) {
+  __shared__ double red[256];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < np; i += 256) a += part[i];
+  const double S = block_sum(a, red);
+  if (threadIdx.x == 0 && loss) *loss = (float)(S / n_px);
+}
+
 // ---------------------------------------------------------------------------------------------
 // GEMM launcher
 // ---------------------------------------------------------------------------------------------
@@ -661,6 +697,7 @@ struct sc_unet {
   float *smap[3] = {};
   double *lpart = nullptr;
   int lpart_n = 0;
+  int loss_kind = SC_UNET_LOSS_L1_SSIM;  // sc_unet_set_loss
   float *loss = nullptr;
   // weight-gradient partials
   float *wpart = nullptr;
@@ -1116,6 +1153,16 @@ int run_forward(sc_ctx *c, sc_unet *u, const float *x, int n) {
 int run_loss(sc_ctx *c, sc_unet *u, const float *pred, const float *target, int n, int h, int w, float *loss,
              float *grad, bf16 *gy8, const char *where) {
   cudaStream_t s = sc::ctx_stream(c);
+  if (u->loss_kind == SC_UNET_LOSS_BCE) {
+    const int64_t n_px = (int64_t)n * h * w;
+    const int nb = (int)((n_px + 255) / 256);
+    if (nb > u->lpart_n) return fail(c, SC_ERR_INVALID_ARG, std::string(where) + ": loss workspace too small");
+    k_bce<<<nb, 256, 0, s>>>(pred, target, n_px, (float)(1.0 / (double)n_px), grad, gy8, u->lpart);
+    UCHK(cudaGetLastError());
+    k_bce_final<<<1, 256, 0, s>>>(u->lpart, nb, (double)n_px, loss);
+    UCHK(cudaGetLastError());
+    return SC_OK;
+  }
   const int Hv = h - 10, Wv = w - 10;
   dim3 gf((Wv + kSTW - 1) / kSTW, (Hv + kSTH - 1) / kSTH, n);
   dim3 gb((w + kSTW - 1) / kSTW, (h + kSTH - 1) / kSTH, n);
@@ -1718,6 +1765,14 @@ int sc_unet_load(sc_ctx *c, sc_unet *u, const char *path) {
   const int rc = refresh_bf16(c, u, 0, 0.0f);
   if (rc) return rc;
   UCHK(cudaStreamSynchronize(s));  // the host staging buffer is released on return
+  return SC_OK;
+}
+
+int sc_unet_set_loss(sc_ctx *c, sc_unet *u, int32_t kind) {
+  if (!c || !u) return SC_ERR_INVALID_ARG;
+  if (kind != SC_UNET_LOSS_L1_SSIM && kind != SC_UNET_LOSS_BCE)
+    return fail(c, SC_ERR_INVALID_ARG, "sc_unet_set_loss: unknown loss");
+  u->loss_kind = kind;
   return SC_OK;
 }
 

@@ -127,6 +127,10 @@ class UNet:
         N.sc_unet_set_state(self.ctx.handle, self.h, _ptr(p), _ptr(m), _ptr(v), int(step))
         self.ctx.stream.synchronize()
 
+    def set_loss(self, kind: int):
+        """N.SC_UNET_LOSS_L1_SSIM (denoising) or N.SC_UNET_LOSS_BCE (segmentation logits in channel 0)."""
+        N.sc_unet_set_loss(self.ctx.handle, self.h, int(kind))
+
     def save(self, path: str):
         N.sc_unet_save(self.ctx.handle, self.h, path)
 

@@ -136,6 +136,7 @@ SIGNATURES = {
     "sc_unet_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, P(C.c_int64)]),
     "sc_unet_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "sc_unet_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_char_p]),
+    "sc_unet_set_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "sc_unet_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_char_p]),
     "sc_photon_map_create": (C.c_int, [C.c_void_p, C.c_void_p, P(sc_light_params), C.c_float, P(C.c_void_p)]),
     "sc_photon_map_destroy": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -350,6 +351,14 @@ def sc_unet_get_state(ctx, net, m_dev, v_dev) -> int:
 
 def sc_unet_set_state(ctx, net, params_dev, m_dev, v_dev, step):
     check(load().sc_unet_set_state(ctx, net, params_dev, m_dev, v_dev, step), ctx)
+
+
+SC_UNET_LOSS_L1_SSIM = 0
+SC_UNET_LOSS_BCE = 1
+
+
+def sc_unet_set_loss(ctx, net, kind: int):
+    check(load().sc_unet_set_loss(ctx, net, kind), ctx)
 
 
 def sc_unet_save(ctx, net, path: str):

@@ -170,3 +170,68 @@ def denoise(net: D.UNet, x: torch.Tensor, add: torch.Tensor | None = None, batch
 def mse(a: torch.Tensor, b: torch.Tensor) -> float:
     """Mean squared error over the RGB channels (float64 on the device)."""
     return float(((a[..., :3].double() - b[..., :3].double()) ** 2).mean())
+
+
+# ----------------------------------------------------------------------------------------------
+# Caustic segmentation (the paper's Sec. IV-B experiment, synthetic -> synthetic): a U-Net trained
+# with the segmentation loss on rendered images labelled by the caustic mask ground truth
+# ----------------------------------------------------------------------------------------------
+
+@dataclass
+class SegData:
+    x: torch.Tensor       # [n, H, W, 11] network input: log1p of the rendered RGB, the rest zero
+    target: torch.Tensor  # [n, H, W, 3] label in channel 0: the non-local caustic mask (Sec. III-D)
+
+
+def seg_data(ctx: R.Context, scenes: list[Scene], spec: RenderSpec, seed: int = 0) -> SegData:
+    """Renders each scene (camera paths + guided light paths + resolve) and keeps its RGB image as
+    the input (the other ten input channels zero: the network sees the image only, as a
+    segmentation network deployed on photographs would) and its caustic mask as the label."""
+    h, w = scenes[0].camera.height, scenes[0].camera.width
+    n = len(scenes)
+    dev = torch.device("cuda", ctx.device)
+    x = torch.empty((n, h, w, D.IN_CH), dtype=torch.float32, device=dev)
+    t = torch.zeros((n, h, w, D.OUT_CH), dtype=torch.float32, device=dev)
+    f = R.Frame(w, h, device=dev)
+    for i, sc in enumerate(scenes):
+        gs = R.GpuScene(ctx, sc)
+        render(ctx, gs, f, spec, seed, scene_index=i, guide=guide_sphere(sc))
+        D.pack_frame(ctx, f, x, i, "rgb")
+        x[i, ..., 3:] = 0.0
+        t[i, ..., 0] = f["caustic_mask"].float()
+        ctx.stream.synchronize()
+        del gs
+    ctx.sync_status()
+    return SegData(x, t)
+
+
+def predict_masks(net: D.UNet, x: torch.Tensor) -> torch.Tensor:
+    """Boolean [n, H, W]: logit of output channel 0 above zero (probability above one half)."""
+    out = []
+    for s in range(0, x.shape[0], net.max_batch):
+        out.append(net.forward(x[s:s + net.max_batch].contiguous())[..., 0] > 0.0)
+    return torch.cat(out)
+
+
+def iou(pred: torch.Tensor, label: torch.Tensor) -> float:
+    """Intersection over union of two boolean masks over all their pixels."""
+    inter = (pred & label).sum().item()
+    union = (pred | label).sum().item()
+    return inter / union if union else 1.0
+
+
+def brightness_baseline(train: SegData, tests: list[SegData]) -> tuple[float, list[float]]:
+    """The method without a network: a pixel is a caustic when its log1p luminance exceeds a
+    threshold, the one (of 64 quantiles) with the best IoU on the training images."""
+    def lum(x):
+        return 0.2126 * x[..., 0] + 0.7152 * x[..., 1] + 0.0722 * x[..., 2]
+
+    lt = lum(train.x)
+    lab = train.target[..., 0] > 0.5
+    best, best_thr = -1.0, 0.0
+    for q in torch.linspace(0.5, 0.999, 64):
+        thr = float(torch.quantile(lt.flatten()[::7].float(), float(q)))
+        v = iou(lt > thr, lab)
+        if v > best:
+            best, best_thr = v, thr
+    return best_thr, [iou(lum(d.x) > best_thr, d.target[..., 0] > 0.5) for d in tests]

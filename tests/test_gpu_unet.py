@@ -13,6 +13,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import unet as U  # noqa: E402
 from paper_2107_11008_gb300 import denoiser as D  # noqa: E402
+from paper_2107_11008_gb300 import native as N_  # noqa: E402
 from paper_2107_11008_gb300 import renderer as R  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -372,3 +373,42 @@ def test_pack_frame_from_render(ctx):
     np.testing.assert_array_equal(xv[..., 6:9], f["normal_camera"].cpu().numpy()[..., :3])
     np.testing.assert_array_equal(xv[..., 9], f["depth_norm"].cpu().numpy())
     np.testing.assert_array_equal(xv[..., 10], (f["mask"].cpu().numpy() != 0).astype(np.float32))
+
+
+def test_bce_segmentation_loss_vs_oracle(ctx):
+    """The segmentation loss (logit in output channel 0, label in target channel 0): loss value and
+    output gradient against the FP64 oracle on the GPU's own prediction; the network's gradient
+    still matches the oracle backward (cosine) and training lowers the loss."""
+    n, h, w = 2, 32, 40
+    p = _params(41)
+    x, _ = _inputs(42, n, h, w)
+    rng = np.random.default_rng(43)
+    t = np.zeros((n, h, w, 3))
+    t[..., 0] = rng.random((n, h, w)) < 0.3
+    net = D.UNet(ctx, n, h, w)
+    net.set_params(torch.from_numpy(D.flatten(p)).float().cuda())
+    net.set_loss(N_.SC_UNET_LOSS_BCE)
+    y, loss = net.loss_grad(_dev(x), _dev(t))
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    yv = _np(y)
+    lref, gref = U.loss_bce(yv, t)
+    assert abs(float(loss.item()) - lref) <= 1e-5 * abs(lref)
+    gy = net.buffer("GOUT").float().cpu().numpy().astype(np.float64)
+    assert not gy[..., 1:].any()
+    assert np.abs(gy[..., 0] - gref[..., 0]).max() <= BF16_REL * np.abs(gref[..., 0]).max()
+    # end to end: gradient of the BCE loss through the whole network
+    pb = {k: (U.bf16(v) if not k.endswith("_b") else v) for k, v in p.items()}
+    yr, cache = U.forward(pb, U.bf16(x), CH)
+    _, gyr = U.loss_bce(yr, t)
+    gr, _ = U.backward(pb, cache, gyr, CH)
+    a = net.get_grads().cpu().numpy().astype(np.float64)
+    b = D.flatten(gr)
+    assert a @ b / np.linalg.norm(a) / np.linalg.norm(b) > 0.999
+    xd, td = _dev(x), _dev(t)
+    first = float(net.train_step(xd, td, 1e-3).item())
+    for _ in range(30):
+        last = net.train_step(xd, td, 1e-3)
+    ctx.sync_status()
+    assert float(last.item()) < 0.8 * first
+    net.close()

@@ -150,3 +150,31 @@ def test_bf16_rounding():
     np.testing.assert_array_equal(r[:3], [1.0, 1.0, 1.0 + 2 ** -7])
     assert r[3] == -3.140625  # exactly representable
     assert r[4] == 65536.0  # 65504 = 1.1111111111b x 2^15 rounds up to 2^16
+
+
+def test_bce_loss_closed_forms_and_finite_differences():
+    """Binary cross-entropy with logits: y = 0 gives log 2 whatever the label; a confident right
+    answer costs ~0, a confident wrong one ~|y|; the gradient matches central differences and
+    channels 1, 2 carry none."""
+    shape = (2, 5, 7, 3)
+    zero = np.zeros(shape)
+    t = np.zeros(shape)
+    t[..., 0] = (np.arange(2 * 5 * 7).reshape(2, 5, 7) % 3 == 0)
+    v, _ = U.loss_bce(zero, t)
+    assert abs(v - np.log(2.0)) < 1e-15
+    y = np.zeros(shape)
+    y[..., 0] = np.where(t[..., 0] > 0, 30.0, -30.0)
+    assert U.loss_bce(y, t)[0] < 1e-12
+    assert abs(U.loss_bce(-y, t)[0] - 30.0) < 1e-9
+    rng = np.random.default_rng(3)
+    p = rng.normal(0, 2, shape)
+    tt = rng.random(shape)
+    v, g = U.loss_bce(p, tt)
+    assert (g[..., 1:] == 0).all()
+    for idx in [(0, 1, 2, 0), (1, 4, 6, 0), (0, 0, 0, 1)]:
+        e = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[idx] += e
+        pm[idx] -= e
+        fd = (U.loss_bce(pp, tt)[0] - U.loss_bce(pm, tt)[0]) / (2 * e)
+        assert abs(fd - g[idx]) < 1e-8
