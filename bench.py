@@ -87,7 +87,7 @@ def parse():
     ap.add_argument("--den-steps", type=int, default=48000, help="denoise workload: training steps")
     ap.add_argument("--seg-steps", type=int, default=4000, help="caustic_seg workload: training steps")
     ap.add_argument("--workload", default="glass512",
-                    choices=["glass512", "batch64", "unet_train", "denoise", "caustic_seg"],
+                    choices=["glass512", "batch64", "unet_train", "denoise", "denoise_dense", "caustic_seg"],
                     help="batch64: 64 randomised scenes (1k-200k tris, 128^2..1024^2, 64 spp) in one graph-captured "
                          "persistent launch vs 64 sequential launches; unet_train: U-Net training steps on batches "
                          "of 16 x 256^2 render pairs; denoise: 4-spp render + U-Net vs the plain tracer at matched MSE")
@@ -492,6 +492,155 @@ def run_denoise(args):
         print(json.dumps(line), flush=True)
 
 
+def run_denoise_dense(args):
+    """The dense comparison: 1024^2 frames of 16 overlapping glass objects (~1M triangles), 16
+    wavelength bins, 32M guided light paths per frame.  Denoised frame = 8 camera spp + 32M light
+    paths, the U-Net (trained on 256^2 renders of other dense scenes, 8 -> 512 spp, camera estimate
+    only) on the camera estimate and the light-traced caustics added back.  Plain frames = N spp +
+    the same light paths per camera sample.  MSEs against a two-half reference (2048 spp + 4x that in
+    light paths per pixel each) with the reference's own variance subtracted; the plain tracer's
+    matched spp interpolated from a sweep up to 1024 spp (its MSE at 1024 spp measured directly)."""
+    import numpy as np
+    import torch
+
+    from paper_2107_11008_gb300 import denoiser as D
+    from paper_2107_11008_gb300 import renderer as R
+    from paper_2107_11008_gb300 import scenes as S
+    from paper_2107_11008_gb300 import training as T
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hw, train_hw, n_train, n_test, nb, depth = 1024, 256, 96, 2, 16, 12
+    lpp = 32e6 / (hw * hw)        # light paths per pixel of the denoised frame (32M per frame)
+    ratio = lpp / 8.0             # light paths per camera sample, kept for every plain budget
+    lo = T.RenderSpec(8, lpp, max_depth=depth, n_bins=nb)
+    stream = torch.cuda.current_stream(dev)
+    ctx = R.Context(local, stream)
+    t0 = time.perf_counter()
+    train_scenes = [S.dense_scene(100 + i, train_hw, train_hw, tris_per_object=16000) for i in range(n_train)]
+    train = T.make_pairs(ctx, train_scenes, lo, T.RenderSpec(512, 0, max_depth=depth, n_bins=nb), seed=1,
+                         source="direct")
+    del train_scenes
+    test_scenes = [S.dense_scene(10_000 + i, hw, hw) for i in range(n_test)]
+    gss = [R.GpuScene(ctx, sc) for sc in test_scenes]
+    guides = [S.guide_sphere(sc) for sc in test_scenes]
+    f = R.Frame(hw, hw, device=dev)
+    test_x = torch.empty((n_test, hw, hw, D.IN_CH), dtype=torch.float32, device=dev)
+    test_caustic = torch.empty((n_test, hw, hw, 4), dtype=torch.float32, device=dev)
+    test_rgb = torch.empty((n_test, hw, hw, 4), dtype=torch.float32, device=dev)
+    for i, g in enumerate(gss):
+        T.render(ctx, g, f, lo, seed=2, scene_index=i, guide=guides[i])
+        D.pack_frame(ctx, f, test_x, i, "direct")
+        test_caustic[i].copy_(f["caustic"])
+        test_rgb[i].copy_(f["rgb"])
+    half = T.RenderSpec(2048, 2048 * ratio, max_depth=depth, n_bins=nb)
+    ref_a = torch.empty_like(test_rgb)
+    ref_b = torch.empty_like(test_rgb)
+    for i, g in enumerate(gss):
+        for k, dst in enumerate((ref_a, ref_b)):
+            T.render(ctx, g, f, half, seed=3, sample_offset=(1 << 24) + k * half.spp,
+                     path_offset=(1 << 42) + k * int(half.lights_per_pixel * hw * hw), scene_index=i, guide=guides[i])
+            dst[i].copy_(f["rgb"])
+    ref = 0.5 * (ref_a + ref_b)
+    var_ref = T.mse(ref_a, ref_b) / 4.0
+    gen_s = time.perf_counter() - t0
+    trainer = D.UNet(ctx, 16, 128, 128)
+    trainer.set_params(D.he_init(0).to(dev))
+    t0 = time.perf_counter()
+    T.train(trainer, train, steps=args.den_steps, batch=16, crop=128, lr=1.5e-3, lr_final=5e-5, seed=0)
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    trainer_params = trainer.get_params()
+    trainer.close()
+    del train
+    net = D.UNet(ctx, 1, hw, hw)
+    net.set_params(trainer_params)
+    den = T.denoise(net, test_x, test_caustic, batch=1)
+    m_den = T.mse(den, ref) - var_ref
+    m_in = T.mse(test_rgb, ref) - var_ref
+    sweep = {}
+    for spp in (8, 16, 32, 64, 128, 256, 512, 1024):
+        out = torch.empty_like(ref)
+        for i, g in enumerate(gss):
+            T.render(ctx, g, f, T.RenderSpec(spp, spp * ratio, max_depth=depth, n_bins=nb), seed=7, scene_index=i,
+                     guide=guides[i])
+            out[i].copy_(f["rgb"])
+        sweep[spp] = T.mse(out, ref) - var_ref
+    ctx.sync_status()
+    budgets = sorted(sweep)
+    above = [b for b in budgets if sweep[b] > m_den]
+    below = [b for b in budgets if sweep[b] <= m_den]
+    if below and above:
+        s_lo, s_hi = max(above), min(below)
+        a, b = np.log(sweep[s_lo]), np.log(sweep[s_hi])
+        spp_match = float(np.exp(np.log(s_lo) + (np.log(m_den) - a) / (b - a) * (np.log(s_hi) - np.log(s_lo))))
+    elif below:
+        spp_match = float(budgets[0])
+    else:
+        spp_match = budgets[-1] * sweep[budgets[-1]] / m_den
+    g0 = gss[0]
+    x1 = torch.empty((1, hw, hw, D.IN_CH), dtype=torch.float32, device=dev)
+    y1 = torch.empty((1, hw, hw, D.OUT_CH), dtype=torch.float32, device=dev)
+    rgb1 = torch.empty((1, hw, hw, 4), dtype=torch.float32, device=dev)
+
+    def denoised_frame():
+        T.render(ctx, g0, f, lo, seed=11, guide=guides[0], chunked=False)
+        D.pack_frame(ctx, f, x1, 0, source="direct")
+        net.forward(x1, y1)
+        D.output_rgb(ctx, y1, f["caustic"], out=rgb1)
+
+    spp_int = max(1, int(np.ceil(spp_match)))
+    plain_spec = T.RenderSpec(spp_int, spp_int * ratio, max_depth=depth, n_bins=nb)
+    spec_1024 = T.RenderSpec(1024, 1024 * ratio, max_depth=depth, n_bins=nb)
+
+    def plain_frame(spec):
+        T.render(ctx, g0, f, spec, seed=11, guide=guides[0], chunked=False)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(max(3, args.warmup)):
+        denoised_frame()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+
+    def timed(fn, reps):
+        ev[0].record(stream)
+        for _ in range(reps):
+            fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    den_ms = timed(denoised_frame, args.steps)
+    plain_frame(plain_spec)
+    plain_ms = timed(lambda: plain_frame(plain_spec), max(1, min(args.steps, 3)))
+    plain1024_ms = timed(lambda: plain_frame(spec_1024), 1)
+    net_ms = timed(lambda: net.forward(x1, y1), args.steps)
+    clocks = sampler.stop()
+    ctx.sync_status()
+    if rank == 0:
+        line = {"metric": "denoised fps at the plain tracer's matched MSE (dense 1024^2 scene, 16 objects, ~1M tris)",
+                "value": world * 1e3 / den_ms, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": den_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic (scenes.dense_scene)",
+                "config": {"workload": "denoise_dense: 1024^2 scenes.dense_scene (16 glass objects, 1.08M tris), 16 bins, "
+                                       "depth 12, 8 spp + 32M guided light paths; U-Net on the camera estimate trained "
+                                       f"{args.den_steps} steps on 128^2 crops of {n_train} 256^2 dense-scene pairs "
+                                       "(8 -> 512 spp), light-traced caustics added back; 2 held-out scenes; reference "
+                                       "2 x (2048 spp + 4x light paths per sample)",
+                           "light_paths_per_camera_sample": ratio},
+                "mse": {"denoised": m_den, "input": m_in, "reference_variance": var_ref, "plain_sweep": sweep,
+                        "plain_1024spp": sweep[1024], "denoised_reaches_plain_1024": m_den <= sweep[1024]},
+                "matched_spp": spp_match,
+                "plain_frame": {"spp": spp_int, "ms": plain_ms, "fps": world * 1e3 / plain_ms},
+                "plain_1024spp_frame": {"ms": plain1024_ms, "fps": world * 1e3 / plain1024_ms},
+                "fps_ratio_denoised_over_plain_matched": plain_ms / den_ms,
+                "fps_ratio_denoised_over_plain_1024": plain1024_ms / den_ms,
+                "unet_forward_ms": net_ms, "setup_s": {"data_and_reference": gen_s, "training": train_s},
+                "gpu_launches": None, "clocks": clocks, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+
+
 def run_caustic_seg(args):
     """The paper's caustic-segmentation experiment (Sec. IV-B, Table II), synthetic -> synthetic: the
     BF16 U-Net trained with the segmentation loss on rendered 128^2 glass scenes labelled by their
@@ -794,6 +943,9 @@ def main():
         return
     if args.workload == "caustic_seg":
         run_caustic_seg(args)
+        return
+    if args.workload == "denoise_dense":
+        run_denoise_dense(args)
         return
     import torch
     import torch.distributed as dist

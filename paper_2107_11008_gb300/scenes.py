@@ -541,6 +541,27 @@ def glass_scene(seed=0, width=512, height=512, n_objects=4, tris_per_object=2048
     return b.build(cam, name=f"glass_scene_s{seed}_{width}x{height}")
 
 
+def dense_scene(seed=0, width=1024, height=1024, n_objects=16, tris_per_object=62500, cauchy=(1.5, 0.004),
+                light_size=1.0, light_radiance=20.0) -> Scene:
+    """The dense variant of glass_scene: n_objects transparent meshes of the four families (about 1M
+    triangles at the defaults) spread over a 6 x 6 m patch of the checkered floor, smaller
+    (scale 0.3-0.55) so that they crowd the view and overlap in the image, same backdrop and rect light;
+    the camera stands back to frame them all."""
+    rng = np.random.default_rng(50_000 + seed)
+    b = SceneBuilder()
+    _backdrop(b)
+    items = []
+    for i in range(n_objects):
+        fam = FAMILIES[i % len(FAMILIES)]
+        mat = b.material(Material(MAT_DIELECTRIC, cauchy_a=cauchy[0], cauchy_b=cauchy[1]))
+        items.append((_family_mesh(fam, tris_per_object, rng), mat))
+    _place_objects(b, items, rng, floor_y=0.0, xz_range=2.6, scale_range=(0.3, 0.55), max_tries=2000)
+    h = light_size / 2
+    b.add_rect_light((-h, 4.0, -h), (light_size, 0, 0), (0, 0, light_size), (light_radiance,) * 3)
+    cam = Camera((0.0, 3.4, 7.0), (0.0, 0.2, 0.0), (0.0, 1.0, 0.0), 45.0, width, height)
+    return b.build(cam, name=f"dense_scene_s{seed}_{width}x{height}")
+
+
 def random_scene(seed: int, resolutions=(128, 256, 512, 1024), tri_range=(1000, 200000)) -> Scene:
     """A randomised dataset scene: 1-6 transparent objects, total triangles uniform in tri_range,
     random IOR in [1.33, 1.9] per object, random resolution, point or rect light."""
