@@ -30,7 +30,11 @@ namespace sc {
 namespace {
 
 constexpr int kWfBlock = 128;
-constexpr int kWfChunk = 12;  // node visits per traversal chunk before a lane may refill
+// node visits per traversal chunk before a lane whose query ended may take the next one
+#ifndef SC_WF_CHUNK
+#define SC_WF_CHUNK 12
+#endif
+constexpr int kWfChunk = SC_WF_CHUNK;
 enum : uint32_t {
   W_SPEC_ONLY = 1u, W_DIFFUSE_FIRST = 2u, W_LAST_SPECULAR = 4u, W_FIXUP = 8u, W_HAS_NEXT = 16u
 };
