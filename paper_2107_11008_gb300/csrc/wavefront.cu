@@ -43,7 +43,7 @@ enum { C_EXT0 = 0, C_EXT1 = 1, C_DIEL = 2, C_DIFF = 3, C_SHADOW = 4, C_TICKET_EX
 
 struct Wave {
   float4 *o;      // ray origin; w: the path's bin draw u
-  float4 *d;      // ray direction
+  float4 *d;      // ray direction; w: the path's scene in the batch (int bits)
   float4 *beta;   // throughput
   float4 *L;      // radiance so far; w: 1 once the path has ended
   float4 *nee;    // pending next-event contribution; w: shadow ray length limit
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_generate(WfArgs a, Wave w) {
         const float ul = u01(x0.z);
         const float3 d = cam_dir(cam, (px + u01(x0.x)) / cam.W, (py + u01(x0.y)) / cam.H);
         w.o[p] = make_float4(cam.eye.x, cam.eye.y, cam.eye.z, ul);
-        w.d[p] = make_float4(d.x, d.y, d.z, 0.0f);
+        w.d[p] = make_float4(d.x, d.y, d.z, __int_as_float(sc));
         w.beta[p] = make_float4(1.f, 1.f, 1.f, 0.f);
         w.m0[p] = make_uint4(2166136261u, kMiss, 0u, 0u);
         w.m1[p] = make_uint4(0u, 0u, W_SPEC_ONLY, (uint32_t)sc);
@@ -196,8 +196,8 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_extend(WfArgs a, Wave w, int cu
         const unsigned t = base + (unsigned)__popc(wmask & ((1u << lane) - 1u));
         if (t < nq_total) {
           p = (int)q[t];
-          if (B) sc = (int)w.m1[p].w;
           const float4 o4 = w.o[p], d4 = w.d[p];
+          if (B) sc = __float_as_int(d4.w);
           o = f3(o4.x, o4.y, o4.z);
           d = f3(d4.x, d4.y, d4.z);
           trav_begin(ts, 3.0e38f, false);
@@ -213,44 +213,46 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_extend(WfArgs a, Wave w, int cu
       done = trav_step(scene_of<B>(a, sc), make_wray(o, d), 3.0e38f, ts, stack, kWfChunk, a.status, tc);
       if (done) tracing = false;
     }
-    // a finished query: record the hit, end the path or queue it for its material
+    // a finished query: record the hit and queue the path for its material, or end it (a miss, an
+    // emitter); the hit's signature entry and query count are added by whichever kernel takes the hit
     bool to_diel = false, to_diff = false;
     if (done) {
       const DevScene &S = scene_of<B>(a, sc);
-      const float3 env = f3(S.env);
       ++tc.queries;
       const Hit h = ts.h;
-      uint4 m0 = w.m0[p];
-      const uint4 m1 = w.m1[p];
-      m0.z += 1u;                    // closest-hit queries
-      m0.x = fnv(m0.x, h.id);        // signature
-      if (m1.x == 0u) m0.y = h.id;   // first hit
-      w.m0[p] = m0;
-      if (h.prim < 0) {
-        const float4 L4 = w.L[p], b4 = w.beta[p];
-        end_path(w, p, f3(L4.x, L4.y, L4.z) + f3(b4.x, b4.y, b4.z) * env);
-      } else if (!SC_IN_RANGE(a.status, 5, h.prim, S.n_tris) || !SC_IN_RANGE(a.status, 6, h.id, S.n_tris)) {
-        const float4 L4 = w.L[p];
-        end_path(w, p, f3(L4.x, L4.y, L4.z));
-      } else {
+      bool ends = true;
+      float3 Ladd = f3(0.f, 0.f, 0.f);
+      if (h.prim >= 0 && SC_IN_RANGE(a.status, 5, h.prim, S.n_tris) && SC_IN_RANGE(a.status, 6, h.id, S.n_tris)) {
         w.hit[p] = make_float4(h.t, h.b1, h.b2, __int_as_float(h.prim));
         w.hid[p] = h.id;
         const int mat = __float_as_int(__ldg(&S.shade2[h.id]).w);
         const sc_material m = S.mats[SC_IN_RANGE(a.status, 7, mat, S.n_mats) ? mat : 0];
         if (m.kind == SC_MAT_DIELECTRIC) {
           to_diel = true;
-        } else if (m.kind == SC_MAT_EMISSIVE) {
+          ends = false;
+        } else if (m.kind != SC_MAT_EMISSIVE) {
+          to_diff = true;
+          ends = false;
+        } else {
+          const uint4 m1 = w.m1[p];
           const Surf f = interact(S, d, h);
           const bool count = (m1.z & W_SPEC_ONLY) ||
                              ((a.P.flags & SC_FLAG_EMITTER_AFTER_DS) && (m1.z & W_DIFFUSE_FIRST) && m1.y == 1u &&
                               (m1.z & W_LAST_SPECULAR));
-          const float4 L4 = w.L[p], b4 = w.beta[p];
-          float3 L = f3(L4.x, L4.y, L4.z);
-          if (f.cosg < 0.0f && count) L = L + f3(b4.x, b4.y, b4.z) * f3(m.emission);
-          end_path(w, p, L);
-        } else {
-          to_diff = true;
+          if (f.cosg < 0.0f && count) Ladd = f3(w.beta[p].x, w.beta[p].y, w.beta[p].z) * f3(m.emission);
         }
+      } else if (h.prim < 0) {
+        const float4 b4 = w.beta[p];
+        Ladd = f3(b4.x, b4.y, b4.z) * f3(S.env);
+      }
+      if (ends) {
+        uint4 m0 = w.m0[p];
+        m0.z += 1u;                          // closest-hit queries
+        m0.x = fnv(m0.x, h.id);              // signature
+        if (w.m1[p].x == 0u) m0.y = h.id;    // first hit
+        w.m0[p] = m0;
+        const float4 L4 = w.L[p];
+        end_path(w, p, f3(L4.x, L4.y, L4.z) + Ladd);
       }
     }
     warp_push(w.q_diel, w.cnt + C_DIEL, to_diel, (uint32_t)p);
@@ -302,6 +304,9 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_dielectric(WfArgs a, Wave w, in
       const float3 d = f3(d4.x, d4.y, d4.z);
       float3 beta = f3(b4.x, b4.y, b4.z);
       const Hit h = load_hit(w, p);
+      m0.z += 1u;                        // closest-hit queries
+      m0.x = fnv(m0.x, h.id);            // signature
+      if (m1.x == 0u) m0.y = h.id;       // first hit
       const Surf f = interact(S, d, h);
       const sc_material m = S.mats[SC_IN_RANGE(a.status, 7, f.mat, S.n_mats) ? f.mat : 0];
       // the segment ended on the glass's inner side: it ran through the glass (Beer-Lambert)
@@ -332,7 +337,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_dielectric(WfArgs a, Wave w, in
         m1.x += 1u;
         const float3 no = offset_along(f.p, f.ng, nd);
         w.o[p] = make_float4(no.x, no.y, no.z, ul);
-        w.d[p] = make_float4(nd.x, nd.y, nd.z, 0.0f);
+        w.d[p] = make_float4(nd.x, nd.y, nd.z, d4.w);
         w.m1[p] = m1;
         if ((int)m1.x >= a.P.max_depth) {
           const float4 L4 = w.L[p];
@@ -367,6 +372,9 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_diffuse(WfArgs a, Wave w, int n
       const float3 d = f3(d4.x, d4.y, d4.z);
       float3 beta = f3(b4.x, b4.y, b4.z);
       const Hit h = load_hit(w, p);
+      m0.z += 1u;                        // closest-hit queries
+      m0.x = fnv(m0.x, h.id);            // signature
+      if (m1.x == 0u) m0.y = h.id;       // first hit
       const Surf f = interact(S, d, h);
       const sc_material m = S.mats[SC_IN_RANGE(a.status, 7, f.mat, S.n_mats) ? f.mat : 0];
       uint32_t pix, smp;
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_diffuse(WfArgs a, Wave w, int n
         beta = beta * alb;
         const float3 no = f.p + f.ngf * eps_of(f.p);
         w.o[p] = make_float4(no.x, no.y, no.z, ul);
-        w.d[p] = make_float4(nd.x, nd.y, nd.z, 0.0f);
+        w.d[p] = make_float4(nd.x, nd.y, nd.z, d4.w);
         w.beta[p] = make_float4(beta.x, beta.y, beta.z, 0.0f);
         fl |= W_HAS_NEXT;
       }
@@ -433,7 +441,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_diffuse(WfArgs a, Wave w, int n
       m1.z = fl;
       if (shadow) {
         w.so[p] = make_float4(so.x, so.y, so.z, 0.0f);
-        w.sd[p] = make_float4(sd.x, sd.y, sd.z, 0.0f);
+        w.sd[p] = make_float4(sd.x, sd.y, sd.z, d4.w);
         w.nee[p] = make_float4(nee.x, nee.y, nee.z, sdist * (1.0f - 1e-4f));
       } else {
         m0.x = fnv(m0.x, EV_UNLIT);
@@ -478,8 +486,8 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_shadow(WfArgs a, Wave w, int ne
         const unsigned t = base + (unsigned)__popc(wmask & ((1u << lane) - 1u));
         if (t < nq_total) {
           p = (int)w.q_shadow[t];
-          if (B) sc = (int)w.m1[p].w;
           const float4 o4 = w.so[p], d4 = w.sd[p];
+          if (B) sc = __float_as_int(d4.w);
           o = f3(o4.x, o4.y, o4.z);
           d = f3(d4.x, d4.y, d4.z);
           tmax = w.nee[p].w;
