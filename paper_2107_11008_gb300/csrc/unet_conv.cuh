@@ -107,8 +107,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
   uint8_t *sW = sm;
   uint8_t *sA = sm + align_up(wbytes, 1024);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sA + 2 * astride);
-  // bar[0] weights full, [1,2] A full, [3,4] A empty, [5,6] accumulator full, [7,8] accumulator empty
-  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 9);
+  // bar[0] weights full, [1,2] A full, [3,4] A empty, [5,6] accumulator full, [7,8] accumulator empty,
+  // [9] drain: the MMAs still in flight when the issuer gives up (10 barriers + 2 words fit the 128
+  // bytes conv_smem_bytes reserves)
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 10);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(slot + 1);
   const int tiles_x = G.narrow ? 1 : w / 128;
   const int tiles_y = G.narrow ? h / G.th : h;
@@ -123,6 +125,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
       tc::mbar_init(tc::smem_addr(&bar[5 + i]), 1);
       tc::mbar_init(tc::smem_addr(&bar[7 + i]), 4);
     }
+    tc::mbar_init(tc::smem_addr(&bar[9]), 1);
     *abort_flag = 0;
   }
   if (warp == 1) {
@@ -236,7 +239,16 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
         }
         if (ok) tc::mma_commit(tc::smem_addr(&bar[5 + a]));  // accumulator full
       }
-      if (!ok) *abort_flag = 1;
+      if (!ok) {
+        *abort_flag = 1;
+        // MMAs already issued may still be writing the accumulators: commit them to the drain
+        // barrier and wait (bounded) before the CTA frees its TMEM.  On the normal path the epilogue
+        // has waited for every accumulator, so nothing is in flight there.
+        if (staged > 0) {
+          tc::mma_commit(tc::smem_addr(&bar[9]));
+          tc::mbar_wait(tc::smem_addr(&bar[9]), 0);
+        }
+      }
     }
   } else {
     // ---- epilogue (warps 2..5; warp w reads TMEM lanes 32 * (w % 4) ..) -------------------------
