@@ -28,6 +28,15 @@ def ctx():
     c.close()
 
 
+def fp32_point_err(sc):
+    """Bound on the FP32 hit point's distance from the FP64 one, in metres: the point is the
+    barycentric interpolation of the hit triangle's vertices, so its error scales with their
+    coordinates V, not with the point: about 3u*V from the barycentrics' own rounding, u*V from
+    b0 = 1 - b1 - b2 and 4u*V from the three products and two sums (u = 2^-24).  With the floors
+    of these scenes at +-10 m that is 4.8e-6 m, 1.6e-4 of the slab's gather radius."""
+    return 8 * 2.0 ** -24 * float(np.abs(sc.positions).max())
+
+
 def _glass(width=40, height=32):
     return S.glass_scene(seed=1, width=width, height=height, n_objects=3, tris_per_object=2000)
 
@@ -72,14 +81,17 @@ def test_photons_match_oracle_light_records(ctx, which):
 def test_gather_matches_oracle_with_the_same_photons(ctx, which):
     """The gather kernel against the oracle's density estimate on the GPU's own photons, per camera
     path: signatures of the prefix bit for bit and radiance within 1e-4, away from grazing prefixes and
-    from photons within 2e-5 r of the radius (the FP32 gather point is within ~3e-6 r of the FP64 one)."""
+    from gather points with a photon within FP32_POINT_ERR of the gather sphere."""
     if which.startswith("slab"):
         sc, flags, guide = _beam_through_slab(), O.FLAG_FORCE_TRANSMIT, None
         nb = 4 if which == "slab_bins" else 1
     else:
         sc, flags, guide, nb = _glass(), 0, None, 8
         guide = S.guide_sphere(sc)
-    n_light, spp, radius = 1 << 17, (2 if which.startswith("slab") else 4), (RADIUS if which.startswith("slab") else 0.1)
+    # the slab's photons are dense (r = 0.03 over a uniform beam): 2^15 of them keep the share of
+    # gather points with a photon near the sphere small at this margin
+    n_light = (1 << 15) if which.startswith("slab") else (1 << 17)
+    spp, radius = (2 if which.startswith("slab") else 4), (RADIUS if which.startswith("slab") else 0.1)
     _, pm, fr = _run(ctx, sc, n_light, spp, nb, flags, radius, guide=guide)
     ph = pm.export()
     g = R.path_records_numpy(fr.path_records)
@@ -88,7 +100,7 @@ def test_gather_matches_oracle_with_the_same_photons(ctx, which):
     L, margin = O.local_caustic_gather(gr, {k: ph[k] for k in ("x", "n", "beta", "bin")} | {"photon": ph["photon"]},
                                        radius, n_light, nb)
     grazing = (gr["amb"] != 0)
-    ok = ~grazing & (margin > 2e-5)
+    ok = ~grazing & (margin * radius > fp32_point_err(sc))
     assert ok.mean() > 0.9
     np.testing.assert_array_equal(g["signature"][ok], gr["signature"][ok])
     assert rel_close(g["L"][ok], L[ok], REL, floor=1e-7).all()
