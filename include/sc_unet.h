@@ -138,6 +138,20 @@ int sc_unet_pack_target(sc_ctx *ctx, const sc_frame *frame, int32_t source, floa
  * rgb float4 [n_px] (all device). */
 int sc_unet_output_rgb(sc_ctx *ctx, const float *y, int64_t n_px, const float *add, float *rgb);
 
+/* Self-test of the failure path shared by the tensor-core kernels (test use).  One CTA takes
+ * the roles of a convolution CTA: a producer with a bulk copy in flight, an MMA issuer with one
+ * MMA in flight (128 x 32 x 16, all-ones operands) and two epilogue warps; then each role waits on
+ * an mbarrier that nothing arrives at.  After poll_limit polls (1 .. 2^24; the kernels use 2^24)
+ * every wait gives up and raises the CTA's abort flag; the producer then waits (bounded) for its
+ * copy, the issuer commits its MMA to a drain barrier and waits for it, the CTA frees its TMEM and
+ * latches SC_STATUS_WATCHDOG in the context's status word, so the next sc_sync_status returns
+ * SC_ERR_TIMEOUT (and clears it); the context stays usable.  out_host (host, 8 x int64):
+ * [0] producer gave up, [1] its copy completed, [2] issuer gave up, [3] its MMA drained,
+ * [4] the drained accumulator holds 16 everywhere, [5] epilogue warps that gave up (2),
+ * [6] the copied bytes arrived intact, [7] nanoseconds the issuer spent in the abandoned wait.
+ * Synchronises the context's stream. */
+int sc_unet_wait_selftest(sc_ctx *ctx, uint32_t poll_limit, int64_t *out_host);
+
 /* Internal tensors, for inspection by tests: id below, level 0..3. */
 enum {
   SC_UNET_BUF_INPUT = 0,  /* BF16 network input, 16 channels (11 + zero padding), level 0 */

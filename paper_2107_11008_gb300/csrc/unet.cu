@@ -1418,6 +1418,106 @@ int refresh_bf16(sc_ctx *c, sc_unet *u, int update, float lr) {
   return SC_OK;
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Self-test of the abort protocol the tensor-core kernels share.  One CTA of four warps in the
+// conv kernel's roles: the producer (warp 0) has a bulk copy in flight, the MMA issuer (warp 1)
+// one MMA (A = B = ones, 128 x 32 x 16, so every accumulator entry becomes 16), and then each
+// role, the two epilogue warps too, waits on barrier `never`, which nothing arrives at.  Each wait
+// gives up after `limit` polls and raises the abort flag; the producer then waits (bounded) for
+// its copy and the issuer commits its MMA to the drain barrier and waits for it, as in
+// k_conv_tma; warp 1 reads the drained accumulator back before the CTA frees its TMEM, and
+// thread 0 latches the watchdog bit.  out[8]: see sc_unet_wait_selftest.
+__global__ void __launch_bounds__(128) k_wait_selftest(const uint4 *src, uint32_t limit, int64_t *out,
+                                                       unsigned *status) {
+  __shared__ __align__(1024) uint8_t sA[128 * 16 * 2];
+  __shared__ __align__(1024) uint8_t sB[32 * 16 * 2];
+  __shared__ __align__(128) uint4 sC[64];
+  __shared__ __align__(8) uint64_t bar[4];  // [0] copy full, [1] never, [2] drain, [3] never (epilogue)
+  __shared__ uint32_t slot;
+  __shared__ int abort_flag, epi_gave_up;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t one2 = 0x3F803F80u;  // two BF16 ones
+  for (int i = threadIdx.x; i < (int)(sizeof(sA) / 4); i += blockDim.x) reinterpret_cast<uint32_t *>(sA)[i] = one2;
+  for (int i = threadIdx.x; i < (int)(sizeof(sB) / 4); i += blockDim.x) reinterpret_cast<uint32_t *>(sB)[i] = one2;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 4; ++i) sc::tc::mbar_init(sc::tc::smem_addr(&bar[i]), 1);
+    abort_flag = 0;
+    epi_gave_up = 0;
+  }
+  if (warp == 1) {
+    sc::tc::tmem_alloc(sc::tc::smem_addr(&slot), 32);
+    sc::tc::tmem_relinquish();
+  }
+  sc::tc::fence_async_smem();
+  sc::tc::fence_before();
+  __syncthreads();
+  sc::tc::fence_after();
+  const uint32_t taddr = slot;
+  volatile int *ab = &abort_flag;
+  if (warp == 0) {
+    if (lane == 0) {
+      sc::tc::mbar_expect_tx(sc::tc::smem_addr(&bar[0]), sizeof(sC));
+      sc::tc::bulk_load(sc::tc::smem_addr(sC), src, sizeof(sC), sc::tc::smem_addr(&bar[0]));
+      const bool got = sc::tc::mbar_wait(sc::tc::smem_addr(&bar[1]), 0, limit);
+      if (!got) *ab = 1;
+      out[0] = got ? 0 : 1;
+      out[1] = sc::tc::mbar_wait(sc::tc::smem_addr(&bar[0]), 0) ? 1 : 0;  // the copy in flight, drained
+    }
+    __syncwarp();
+    bool same = true;
+    for (int i = lane; i < 64; i += 32) {
+      const uint4 a = sC[i], b = src[i];
+      same &= a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w;
+    }
+    same = __all_sync(0xffffffffu, same);
+    if (lane == 0) out[6] = same ? 1 : 0;
+  } else if (warp == 1) {
+    int drained = 0;
+    if (lane == 0) {
+      // K-major, no swizzle: core matrices along K 128 bytes apart, along M / N 256 bytes apart
+      const uint64_t ad = sc::tc::smem_desc(sc::tc::smem_addr(sA), 128u, 256u);
+      const uint64_t bd = sc::tc::smem_desc(sc::tc::smem_addr(sB), 128u, 256u);
+      sc::tc::mma_bf16(taddr, ad, bd, sc::tc::idesc_bf16_f32(128, 32), 0u);
+      const uint64_t t0 = global_ns();
+      const bool got = sc::tc::mbar_wait_or_abort(sc::tc::smem_addr(&bar[1]), 0, ab, limit);
+      out[7] = (int64_t)(global_ns() - t0);
+      if (!got) *ab = 1;
+      out[2] = got ? 0 : 1;
+      sc::tc::mma_commit(sc::tc::smem_addr(&bar[2]));
+      drained = sc::tc::mbar_wait(sc::tc::smem_addr(&bar[2]), 0) ? 1 : 0;
+      out[3] = drained;
+    }
+    drained = __shfl_sync(0xffffffffu, drained, 0);
+    sc::tc::fence_after();
+    bool ok = false;
+    if (drained) {
+      float v[16];
+      sc::tc::tmem_ld16(taddr + (32u << 16), v);  // warp 1 reads TMEM lanes 32..63
+      ok = true;
+      for (int j = 0; j < 16; ++j) ok &= v[j] == 16.0f;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) out[4] = ok ? 1 : 0;
+  } else {
+    if (lane == 0 && !sc::tc::mbar_wait(sc::tc::smem_addr(&bar[3]), 0, limit)) {
+      *ab = 1;
+      atomicAdd(&epi_gave_up, 1);
+    }
+  }
+  sc::tc::fence_before();
+  __syncthreads();
+  if (warp == 1) sc::tc::tmem_dealloc(taddr, 32);
+  if (threadIdx.x == 0) {
+    out[5] = epi_gave_up;
+    if (*ab) atomicOr(status, SC_STATUS_WATCHDOG);
+  }
+}
+
 }  // namespace
 
 // =============================================================================================
@@ -1971,6 +2071,29 @@ int sc_unet_copy_buffer(sc_ctx *c, const sc_unet *u, int32_t id, int32_t level, 
     UCHK(cudaGetLastError());
   }
   return SC_OK;
+}
+
+int sc_unet_wait_selftest(sc_ctx *c, uint32_t poll_limit, int64_t *out_host) {
+  if (!c || !out_host) return SC_ERR_INVALID_ARG;
+  if (poll_limit < 1 || poll_limit > (1u << 24))
+    return fail(c, SC_ERR_INVALID_ARG, "sc_unet_wait_selftest: poll_limit must be in [1, 2^24]");
+  const char *where = "sc_unet_wait_selftest";
+  cudaStream_t s = sc::ctx_stream(c);
+  uint8_t *buf = static_cast<uint8_t *>(sc::ctx_alloc(c, 1024 + 8 * sizeof(int64_t)));
+  if (!buf) return fail(c, SC_ERR_OOM, "sc_unet_wait_selftest: device allocation failed");
+  int64_t *out = reinterpret_cast<int64_t *>(buf + 1024);
+  int rc = SC_OK;
+  cudaError_t e = cudaMemsetAsync(buf, 0x5A, 1024, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, 8 * sizeof(int64_t), s);
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 128, 0, s>>>(reinterpret_cast<const uint4 *>(buf), poll_limit, out, sc::ctx_status(c));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, out, 8 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) rc = fail(c, SC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  sc::ctx_free(c, buf);
+  return rc;
 }
 
 }  // extern "C"

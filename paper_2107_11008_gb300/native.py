@@ -137,6 +137,7 @@ SIGNATURES = {
     "sc_unet_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "sc_unet_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_char_p]),
     "sc_unet_set_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "sc_unet_wait_selftest": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p]),
     "sc_unet_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_char_p]),
     "sc_photon_map_create": (C.c_int, [C.c_void_p, C.c_void_p, P(sc_light_params), C.c_float, P(C.c_void_p)]),
     "sc_photon_map_destroy": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -359,6 +360,13 @@ SC_UNET_LOSS_BCE = 1
 
 def sc_unet_set_loss(ctx, net, kind: int):
     check(load().sc_unet_set_loss(ctx, net, kind), ctx)
+
+
+def sc_unet_wait_selftest(ctx, poll_limit: int):
+    """Runs the tensor-core kernels' abort path once (see sc_unet.h); returns the 8 outcome words."""
+    out = (C.c_int64 * 8)()
+    check(load().sc_unet_wait_selftest(ctx, poll_limit, out), ctx)
+    return list(out)
 
 
 def sc_unet_save(ctx, net, path: str):

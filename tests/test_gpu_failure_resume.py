@@ -5,6 +5,11 @@ kernel latches a status bit and sc_sync_status returns SC_ERR_TIMEOUT / SC_ERR_S
 context stays usable and the next launch with the default limits renders what it rendered before
 (up to the order of its float additions).  No kernel traps: the limits only end loops early.
 
+Tensor-core waits: every mbarrier wait of the U-Net kernels is bounded; on giving up a role raises
+its CTA's abort flag, waits (bounded) for the copies and MMAs it has in flight, and the CTA frees its
+TMEM and latches the watchdog bit.  A self-test CTA runs that path for real (its waits are on a
+barrier nothing arrives at) and the network computes the same output afterwards.
+
 Resume: U-Net training for N steps straight equals N/2 steps, a checkpoint written to a file and
 read into a new network, and N/2 more steps -- bit for bit in parameters, Adam moments and step.
 """
@@ -146,3 +151,32 @@ def test_state_round_trip_and_bad_checkpoints(ctx, tmp_path):
     assert other.get_state()[3] == 2
     with pytest.raises(N.ScError):
         net.save(str(tmp_path / "no_such_dir" / "x.ckpt"))
+
+
+@pytest.mark.parametrize("limit", [1 << 8, 1 << 14])
+def test_tensor_core_wait_gives_up_and_the_context_recovers(ctx, limit):
+    net = D.UNet(ctx, 2, 32, 32)
+    net.set_params(D.he_init(5).cuda())
+    x, _ = _batch(11)
+    before = net.forward(x).clone()
+    ctx.sync_status()
+    out = N.sc_unet_wait_selftest(ctx.handle, limit)
+    # every role gave up, the copy and the MMA in flight completed before the CTA freed its TMEM
+    assert out[:7] == [1, 1, 1, 1, 1, 2, 1], out
+    print(f"{limit} polls of an abandoned wait: {out[7] / 1e3:.1f} us")
+    assert out[7] > 0
+    with pytest.raises(N.ScError) as e:
+        ctx.sync_status()
+    assert e.value.code == -5, N.sc_last_error(ctx.handle)
+    ctx.sync_status()  # reported once, then cleared
+    after = net.forward(x)
+    ctx.sync_status()
+    torch.testing.assert_close(after, before, rtol=0, atol=0)
+    net.close()
+
+
+def test_tensor_core_wait_selftest_rejects_bad_limits(ctx):
+    for bad in (0, (1 << 24) + 1):
+        with pytest.raises(N.ScError) as e:
+            N.sc_unet_wait_selftest(ctx.handle, bad)
+        assert e.value.code == -1
