@@ -197,7 +197,8 @@ typedef struct {
 } sc_light_record;
 
 /* Frame buffers, all device pointers owned by the caller, any may be NULL (not produced).
- * float4 buffers hold rgb (or xyz) in .xyz.  width/height must match the scene camera. */
+ * float4 buffers hold rgb (or xyz) in .xyz and must be 16-byte aligned (SC_ERR_INVALID_ARG
+ * otherwise).  width/height must match the scene camera. */
 typedef struct {
   float *accum_camera;      /* float4[W*H], radiance sums added by sc_trace_camera */
   float *accum_caustic;     /* float4[W*H], splat sums added by sc_trace_lights */

@@ -107,6 +107,17 @@ DevScene scene_launch_view(const sc_ctx *c, const sc_scene *s) { return launch_s
 int trace_light_photons(sc_ctx *c, const sc_scene *s, const sc_light_params *p, float4 *photons);
 }  // namespace sc
 
+namespace sc {
+// float4 buffers are read and written (and splatted into) as 16-byte vectors
+bool frame_vectors_aligned(const sc_frame *f) {
+  const float *vec[] = {f->accum_camera, f->accum_caustic, f->rgb, f->direct, f->caustic, f->normal_world,
+                        f->normal_camera, f->albedo, f->accum_local_caustic, f->local_caustic};
+  for (const float *v : vec)
+    if (reinterpret_cast<uintptr_t>(v) % 16 != 0) return false;
+  return true;
+}
+}  // namespace sc
+
 extern "C" {
 
 int sc_abi_version(void) { return SC_ABI_VERSION; }
@@ -199,7 +210,8 @@ int sc_sync_status(sc_ctx *c) {
       return fail(c, SC_ERR_BOUNDS, "range check failed at site " + std::to_string(w[8]) + ": value " +
                                         std::to_string((int)w[9]) + ", thread " + std::to_string(w[10]));
     if (st & SC_STATUS_STACK_OVERFLOW) return fail(c, SC_ERR_STACK_OVERFLOW, "traversal stack overflow");
-    if (st & SC_STATUS_WATCHDOG) return fail(c, SC_ERR_TIMEOUT, "traversal watchdog expired");
+    if (st & SC_STATUS_WATCHDOG)
+      return fail(c, SC_ERR_TIMEOUT, "watchdog: a traversal exceeded its visit budget or a tensor-core wait gave up");
     if (st & SC_STATUS_QUEUE_OVERFLOW) return fail(c, SC_ERR_QUEUE_OVERFLOW, "work queue overflow");
   }
   return SC_OK;
@@ -482,6 +494,8 @@ static int check_frame(sc_ctx *c, const sc_scene *s, const sc_frame *f, const ch
   if (!c || !valid_scene(s) || !f) return fail(c, SC_ERR_INVALID_ARG, std::string(who) + ": null argument");
   if (f->width != s->dev.cam.width || f->height != s->dev.cam.height)
     return fail(c, SC_ERR_INVALID_ARG, std::string(who) + ": frame size differs from the scene camera");
+  if (!sc::frame_vectors_aligned(f))
+    return fail(c, SC_ERR_INVALID_ARG, std::string(who) + ": float4 frame buffers must be 16-byte aligned");
   return SC_OK;
 }
 
@@ -565,9 +579,10 @@ static int batch_table(sc_ctx *c, const sc_scene *const *scenes, const sc_frame 
   int64_t slots = 0;
   for (int i = 0; i < n; ++i) {
     const sc_scene *s = scenes[i];
-    if (!valid_scene(s) || frames[i].width != s->dev.cam.width || frames[i].height != s->dev.cam.height) {
+    if (!valid_scene(s) || frames[i].width != s->dev.cam.width || frames[i].height != s->dev.cam.height ||
+        !sc::frame_vectors_aligned(&frames[i])) {
       delete[] h;
-      return fail(c, SC_ERR_INVALID_ARG, "batch: scene " + std::to_string(i) + " invalid or its frame size differs");
+      return fail(c, SC_ERR_INVALID_ARG, "batch: scene " + std::to_string(i) + " invalid, its frame size differs or a float4 buffer is not 16-byte aligned");
     }
     const unsigned t = sc::scene_blocks(s->dev.cam);
     if (begin > 0x7FFFFFFFu - t) {

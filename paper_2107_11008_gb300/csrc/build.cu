@@ -5,7 +5,8 @@
 //      attributes, centroids, and the centroid bounds (block reduce + sortable-int atomics).
 //   2. morton: 63-bit Morton code of each centroid in the normalised bounds (21 bits/axis;
 //      10 bits/axis would give ~2 cm cells over a 20 m backdrop, coarser than the glass
-//      triangles, and a poor hierarchy over them).
+//      triangles, and a poor hierarchy over them), with bit 63 set for oversized triangles
+//      (a size class in the key, after Vinkler et al. 2017, "Extended Morton codes").
 //   3. radix sort of (code, index), least-significant digit first, 8 passes of 8 bits; each
 //      pass is histogram -> exclusive scan -> stable scatter (the tile is ranked by 8 one-bit
 //      stable splits in shared memory), so equal codes keep input order.
@@ -50,11 +51,13 @@ __global__ void k_gather(BuildBuffers b) {
   if (t < b.n_tris) {
     const int i0 = b.indices[3 * t], i1 = b.indices[3 * t + 1], i2 = b.indices[3 * t + 2];
     const int vi[3] = {i0, i1, i2};
-    float3 c = f3(0.f, 0.f, 0.f);
+    float3 c = f3(0.f, 0.f, 0.f), plo = f3(FLT_MAX, FLT_MAX, FLT_MAX), phi = f3(-FLT_MAX, -FLT_MAX, -FLT_MAX);
     for (int j = 0; j < 3; ++j) {
       const float3 p = f3(b.positions + 3 * vi[j]);
       b.tris_in[3 * t + j] = make_float4(p.x, p.y, p.z, j == 0 ? __int_as_float(t) : 0.0f);
       c = c + p;
+      plo = f3(fminf(plo.x, p.x), fminf(plo.y, p.y), fminf(plo.z, p.z));
+      phi = f3(fmaxf(phi.x, p.x), fmaxf(phi.y, p.y), fmaxf(phi.z, p.z));
       const float3 n = b.normals ? f3(b.normals + 3 * vi[j]) : f3(0.f, 0.f, 0.f);
       const float ux = b.uvs ? b.uvs[2 * vi[j]] : 0.0f;
       b.shade[3 * t + j] = make_float4(n.x, n.y, n.z, ux);
@@ -65,7 +68,8 @@ __global__ void k_gather(BuildBuffers b) {
                               b.uvs ? b.uvs[2 * i2 + 1] : 0.0f, __int_as_float(mat));
     b.tri_obj[t] = obj;
     c = c * (1.0f / 3.0f);
-    b.centroids[t] = make_float4(c.x, c.y, c.z, 0.0f);
+    // w: the triangle's largest box extent (the size class of its Morton key)
+    b.centroids[t] = make_float4(c.x, c.y, c.z, fmaxf(fmaxf(phi.x - plo.x, phi.y - plo.y), phi.z - plo.z));
     lo[0] = hi[0] = c.x;
     lo[1] = hi[1] = c.y;
     lo[2] = hi[2] = c.z;
@@ -119,7 +123,13 @@ __global__ void k_morton(BuildBuffers b) {
     const float u = ext > 0.0f ? (cc[k] - l[k]) / ext : 0.5f;
     q[k] = (uint32_t)fminf(fmaxf(u * 2097152.0f, 0.0f), 2097151.0f);
   }
-  b.keys[t] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+  // Bit 63 (above the 63 Morton bits) marks triangles whose box spans more than an eighth of the
+  // largest centroid extent: they sort after all others, so the root separates them and their
+  // boxes (a backdrop quad's is metres wide) stay out of the subtrees of the small triangles;
+  // mixed into those subtrees by centroid, every ancestor box would span the backdrop.
+  const float span = fmaxf(fmaxf(h[0] - l[0], h[1] - l[1]), h[2] - l[2]);
+  const unsigned long long big = (span > 0.0f && c.w > 0.125f * span) ? (1ull << 63) : 0ull;
+  b.keys[t] = big | (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
   b.vals[t] = (uint32_t)t;
 }
 

@@ -9,6 +9,7 @@
 namespace sc {
 
 struct DevScene;
+bool frame_vectors_aligned(const sc_frame *f);  // every float4 buffer 16-byte aligned (or NULL)
 struct BatchEntry;
 
 // ---- LBVH build (build.cu) ----------------------------------------------------------------

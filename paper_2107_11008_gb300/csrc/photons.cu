@@ -317,6 +317,8 @@ int sc_gather_local_caustics(sc_ctx *c, const sc_scene *s, const sc_photon_map *
   const DevScene S = scene_launch_view(c, s);
   if (f->width != S.cam.width || f->height != S.cam.height)
     return fail(c, SC_ERR_INVALID_ARG, "sc_gather_local_caustics: frame size differs from the scene camera");
+  if (!frame_vectors_aligned(f))
+    return fail(c, SC_ERR_INVALID_ARG, "sc_gather_local_caustics: float4 frame buffers must be 16-byte aligned");
   if (p->spp < 0 || p->sample_offset < 0 || p->max_depth < 0 || p->n_bins < 1 || p->n_bins > kMaxBins)
     return fail(c, SC_ERR_INVALID_ARG, "sc_gather_local_caustics: bad parameters (n_bins must be 1..64)");
   if (p->n_bins != m->n_bins)

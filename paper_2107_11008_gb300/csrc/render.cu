@@ -491,12 +491,8 @@ __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_pa
         const float g = cs / (dc * dc * apix * cc * cc * cc) / kPi;
         C = beta * g * alb * (jitter ? jitter_weight(ul, jn) : wts[bin]);
         pixel = iy * cam.W + ix;
-        if (F.accum_caustic) {
-          float *a = F.accum_caustic + 4 * (int64_t)pixel;
-          atomicAdd(a + 0, C.x);
-          atomicAdd(a + 1, C.y);
-          atomicAdd(a + 2, C.z);
-        }
+        if (F.accum_caustic)  // one 16-byte vector atomic per splat (the entry's 4th word gets +0)
+          atomicAdd(reinterpret_cast<float4 *>(F.accum_caustic) + pixel, make_float4(C.x, C.y, C.z, 0.0f));
         break;
       }
     }

@@ -70,3 +70,50 @@ def test_trained_denoiser_beats_the_noisy_input(ctx, source, lights):
     assert l_den < (0.7 if source == "rgb" else 0.5) * l_noisy
     net.close()
 
+
+
+def test_denoised_frame_beats_the_plain_tracer_at_several_times_its_samples(ctx):
+    """The matched-MSE ordering of the denoising pipeline on held-out scenes: 4 camera spp + the
+    light-traced caustics, the camera estimate denoised, against the plain tracer spending the same
+    light paths per camera sample at 4, 8, 12, 16 and 32 spp; MSEs against a two-half reference
+    with the reference's own variance subtracted.  The denoised frame must beat the plain one at 3x
+    its samples (the full-size comparison, with its timing, is the bench's denoise workloads)."""
+    hw, ratio = 128, 16
+    lo = T.RenderSpec(4, 4 * ratio)
+    train = T.make_pairs(ctx, [S.denoise_scene(i, hw, hw) for i in range(64)], lo, T.RenderSpec(1024, 0), seed=1,
+                         source="direct")
+    scenes = [S.denoise_scene(20_000 + i, hw, hw) for i in range(4)]
+    test = T.make_pairs(ctx, scenes, lo, T.RenderSpec(0, 0), seed=2, source="direct")
+    gss = [R.GpuScene(ctx, s) for s in scenes]
+    guides = [S.guide_sphere(s) for s in scenes]
+    f = R.Frame(hw, hw)
+    half = T.RenderSpec(1024, 1024 * ratio)
+    ref_ab = [torch.empty_like(test.rgb_lo) for _ in range(2)]
+    for i, g in enumerate(gss):
+        for k, dst in enumerate(ref_ab):
+            T.render(ctx, g, f, half, seed=3, sample_offset=(1 << 24) + k * half.spp,
+                     path_offset=(1 << 42) + k * int(half.lights_per_pixel) * hw * hw, scene_index=i, guide=guides[i])
+            dst[i].copy_(f["rgb"])
+    ref = 0.5 * (ref_ab[0] + ref_ab[1])
+    var_ref = T.mse(ref_ab[0], ref_ab[1]) / 4.0
+    net = D.UNet(ctx, 16, 64, 64)
+    net.set_params(D.he_init(0).cuda())
+    T.train(net, train, steps=4000, batch=16, crop=64, lr=1.5e-3, lr_final=5e-5, seed=0)
+    full = D.UNet(ctx, 4, hw, hw)
+    full.set_params(net.get_params())
+    m_den = T.mse(T.denoise(full, test.x, test.add()), ref) - var_ref
+    sweep = {}
+    for spp in (4, 8, 12, 16, 32):
+        out = torch.empty_like(ref)
+        for i, g in enumerate(gss):
+            T.render(ctx, g, f, T.RenderSpec(spp, spp * ratio), seed=7, scene_index=i, guide=guides[i])
+            out[i].copy_(f["rgb"])
+        sweep[spp] = T.mse(out, ref) - var_ref
+    ctx.sync_status()
+    print(f"held-out MSE: denoised {m_den:.4g}; plain {', '.join(f'{s} spp {m:.4g}' for s, m in sweep.items())}; "
+          f"reference variance {var_ref:.3g}")
+    assert var_ref < 0.1 * sweep[32]  # the reference resolves the errors it measures
+    assert sweep[4] > sweep[8] > sweep[16] > sweep[32]  # the plain tracer converges
+    assert m_den < sweep[12]
+    net.close()
+    full.close()

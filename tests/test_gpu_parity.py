@@ -5,6 +5,8 @@ per-path radiance within 1e-4 relative, image MSE within 1e-5 at equal spp and s
 """
 import math
 
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -486,6 +488,16 @@ def test_invalid_arguments_are_rejected(ctx):
             R.trace_camera(ctx, gs, good, 1, 4, n_bins=nb)
     with pytest.raises(N.ScError):
         R.trace_lights(ctx, gs, good, -1, 4)
+    # float4 buffers are accessed as 16-byte vectors: a misaligned one is refused before any launch
+    p = N.sc_light_params(16, 0, 4, 1, 0, 0, 0, (C.c_float * 4)())
+    for field in ("accum_caustic", "accum_camera", "rgb"):
+        f = good.struct()
+        setattr(f, field, getattr(f, field) + 4)
+        for call in ((lambda: N.sc_trace_lights(ctx.handle, gs.handle, p, f)),
+                     (lambda: N.sc_resolve(ctx.handle, gs.handle, N.sc_resolve_params(1.0, 1.0, 10.0, 0.25, 1, 0.05), f))):
+            with pytest.raises(N.ScError) as e:
+                call()
+            assert e.value.code == -1 and "16-byte" in N.sc_last_error(ctx.handle)
     bad = S.ball_on_plane(16, 16)
     bad.indices = bad.indices.copy()
     bad.indices[0, 0] = 10 ** 6
