@@ -65,7 +65,7 @@ def camera_launches(engine, width, height, spp, depth):
 # of the 16-spp frame (the traffic is path state and queues, proportional to the paths):
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
 #       -k regex:k_wf_ -s 248 -c 62 python bench.py --steps 1 --warmup 3 --spp 16 --no-cpu-baseline --no-sub
-CAMERA_DRAM_BYTES = {"persistent": 24.5e6, "wavefront": None}
+CAMERA_DRAM_BYTES = {"persistent": 24.5e6, "wavefront": 16 * 9.685e9}
 
 
 def parse():
