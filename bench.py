@@ -537,11 +537,15 @@ def run_denoise_dense(args):
     half = T.RenderSpec(2048, 2048 * ratio, max_depth=depth, n_bins=nb)
     ref_a = torch.empty_like(test_rgb)
     ref_b = torch.empty_like(test_rgb)
+    ref_direct = torch.zeros_like(test_rgb)  # the reference's two parts (mean of the halves)
+    ref_caustic = torch.zeros_like(test_rgb)
     for i, g in enumerate(gss):
         for k, dst in enumerate((ref_a, ref_b)):
             T.render(ctx, g, f, half, seed=3, sample_offset=(1 << 24) + k * half.spp,
                      path_offset=(1 << 42) + k * int(half.lights_per_pixel * hw * hw), scene_index=i, guide=guides[i])
             dst[i].copy_(f["rgb"])
+            ref_direct[i] += 0.5 * f["direct"]
+            ref_caustic[i] += 0.5 * f["caustic"]
     ref = 0.5 * (ref_a + ref_b)
     var_ref = T.mse(ref_a, ref_b) / 4.0
     gen_s = time.perf_counter() - t0
@@ -559,6 +563,12 @@ def run_denoise_dense(args):
     den = T.denoise(net, test_x, test_caustic, batch=1)
     m_den = T.mse(den, ref) - var_ref
     m_in = T.mse(test_rgb, ref) - var_ref
+    # where the denoised frame's error sits: the network's camera estimate against the reference's
+    # camera part, and the light-traced caustic buffer (added back unchanged) against its caustic part
+    # (each still carries its share of the reference's own variance)
+    m_parts = {"network_camera_estimate": T.mse(T.denoise(net, test_x, None, batch=1), ref_direct),
+               "caustic_buffer": T.mse(test_caustic, ref_caustic),
+               "input_camera_estimate": T.mse(test_rgb - test_caustic, ref_direct)}
     sweep = {}
     for spp in (8, 16, 32, 64, 128, 256, 512, 1024):
         out = torch.empty_like(ref)
@@ -630,7 +640,8 @@ def run_denoise_dense(args):
                                        "2 x (2048 spp + 4x light paths per sample)",
                            "light_paths_per_camera_sample": ratio},
                 "mse": {"denoised": m_den, "input": m_in, "reference_variance": var_ref, "plain_sweep": sweep,
-                        "plain_1024spp": sweep[1024], "denoised_reaches_plain_1024": m_den <= sweep[1024]},
+                        "plain_1024spp": sweep[1024], "denoised_reaches_plain_1024": m_den <= sweep[1024],
+                        "parts": m_parts},
                 "matched_spp": spp_match,
                 "plain_frame": {"spp": spp_int, "ms": plain_ms, "fps": world * 1e3 / plain_ms},
                 "plain_1024spp_frame": {"ms": plain1024_ms, "fps": world * 1e3 / plain1024_ms},
