@@ -268,6 +268,18 @@ def loss_bce(pred, target):
     return value, grad
 
 
+def loss_l2_linear(pred, target):
+    """Squared error in linear radiance: prediction and target are in the network's log1p domain,
+    the loss is the mean over pixels and the three channels of (expm1(y) - expm1(t))^2, so the
+    minimiser over noisy targets is their mean in linear radiance (what an MSE against a reference
+    measures), not a median in the log domain.  Returns (loss, d loss / d pred)."""
+    y = pred.astype(np.float64)
+    t = target.astype(np.float64)
+    e = np.expm1(y) - np.expm1(t)
+    n = y.size
+    return float((e * e).sum() / n), 2.0 * e * np.exp(y) / n
+
+
 # ------------------------------------------------------------------------------------------
 # Adam
 # ------------------------------------------------------------------------------------------

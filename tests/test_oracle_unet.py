@@ -178,3 +178,30 @@ def test_bce_loss_closed_forms_and_finite_differences():
         pm[idx] -= e
         fd = (U.loss_bce(pp, tt)[0] - U.loss_bce(pm, tt)[0]) / (2 * e)
         assert abs(fd - g[idx]) < 1e-8
+
+
+def test_linear_l2_loss_closed_forms_mean_minimiser_and_finite_differences():
+    """Squared error in linear radiance on log1p-domain values: zero at the target, 1 where every
+    linear value is off by 1, minimised over one prediction by the linear mean of noisy targets
+    (not their log-domain median), gradient equal to central differences."""
+    shape = (2, 3, 4, 3)
+    rng = np.random.default_rng(5)
+    t = np.log1p(rng.random(shape) * 4.0)
+    assert U.loss_l2_linear(t, t)[0] == 0.0
+    assert abs(U.loss_l2_linear(np.log1p(np.expm1(t) + 1.0), t)[0] - 1.0) < 1e-12
+    # sparse, bright samples of one pixel: the linear mean minimises the loss
+    samples = np.array([0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 20.0])
+    tt = np.log1p(samples).reshape(-1, 1)
+    grid = np.linspace(0.0, 5.0, 5001)
+    losses = [U.loss_l2_linear(np.full_like(tt, np.log1p(v)), tt)[0] for v in grid]
+    assert abs(grid[int(np.argmin(losses))] - samples.mean()) <= 1e-3
+    assert abs(grid[int(np.argmin(losses))] - np.median(samples)) > 2.0
+    p = rng.normal(0.5, 0.8, shape)
+    v, g = U.loss_l2_linear(p, t)
+    for idx in [(0, 1, 2, 0), (1, 2, 3, 2), (0, 0, 0, 1)]:
+        e = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[idx] += e
+        pm[idx] -= e
+        fd = (U.loss_l2_linear(pp, t)[0] - U.loss_l2_linear(pm, t)[0]) / (2 * e)
+        assert abs(fd - g[idx]) < 1e-8 * max(1.0, abs(fd))
