@@ -89,8 +89,12 @@ int sc_unet_train_step(sc_ctx *ctx, sc_unet *net, const float *x, const float *t
  * transparent objects and caustics): output channel 0 is a logit, target channel 0 a label in
  * [0, 1], loss = mean over pixels of softplus(y) - t y (binary cross-entropy with logits, FP64
  * partial sums in a fixed order); output channels 1 and 2 and target channels 1 and 2 take no part
- * (zero gradient).  The loss stays set until changed. */
-enum { SC_UNET_LOSS_L1_SSIM = 0, SC_UNET_LOSS_BCE = 1 };
+ * (zero gradient).
+ * SC_UNET_LOSS_L2_LINEAR: squared error in linear radiance, outputs and targets being log1p values:
+ * mean over pixels and the three channels of (expm1(y) - expm1(t))^2 (FP64 partial sums in a fixed
+ * order).  Trained on noisy targets it converges to their linear mean, which is what an MSE against
+ * a converged reference rewards.  The loss stays set until changed. */
+enum { SC_UNET_LOSS_L1_SSIM = 0, SC_UNET_LOSS_BCE = 1, SC_UNET_LOSS_L2_LINEAR = 2 };
 int sc_unet_set_loss(sc_ctx *ctx, sc_unet *net, int32_t kind);
 
 /* Training state (checkpoint / resume).  The state is the FP32 master parameters, the two Adam

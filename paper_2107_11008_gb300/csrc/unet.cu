@@ -592,6 +592,31 @@ __global__ void __launch_bounds__(256) k_bce(const float *p, const float *t, int
   if (threadIdx.x == 0) part[blockIdx.x] = sblk;
 }
 
+// Squared error in linear radiance on log1p-domain values: per element e = expm1(y) - expm1(t),
+// loss = mean of e^2 over pixels and channels, d / d y = 2 e exp(y) / (3 n_px).  Its minimiser over
+// noisy targets is their linear mean.  Same block partials as k_bce (k_bce_final sums them; the
+// mean there divides by 3 n_px).
+__global__ void __launch_bounds__(256) k_l2lin(const float *p, const float *t, int64_t n_px, float inv_n, float *grad,
+                                               bf16 *gy8, double *part) {
+  __shared__ double red[256];
+  const int64_t pix = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  double acc = 0.0;
+  if (pix < n_px) {
+    float g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int ch = 0; ch < 3; ++ch) {
+      const float y = p[pix * 3 + ch], tv = t[pix * 3 + ch];
+      const float e = expm1f(y) - expm1f(tv);
+      g[ch] = 2.0f * e * expf(y) * inv_n;
+      const double ed = expm1((double)y) - expm1((double)tv);
+      acc += ed * ed;
+      if (grad) grad[pix * 3 + ch] = g[ch];
+    }
+    if (gy8) *reinterpret_cast<uint4 *>(gy8 + pix * kGyCh) = pack8(g);
+  }
+  const double sblk = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = sblk;
+}
+
 __global__ void k_bce_final(const double *part, int np, double n_px, float *loss) {
   __shared__ double red[256];
   double a = 0.0;
@@ -1153,13 +1178,19 @@ int run_forward(sc_ctx *c, sc_unet *u, const float *x, int n) {
 int run_loss(sc_ctx *c, sc_unet *u, const float *pred, const float *target, int n, int h, int w, float *loss,
              float *grad, bf16 *gy8, const char *where) {
   cudaStream_t s = sc::ctx_stream(c);
-  if (u->loss_kind == SC_UNET_LOSS_BCE) {
+  if (u->loss_kind == SC_UNET_LOSS_BCE || u->loss_kind == SC_UNET_LOSS_L2_LINEAR) {
     const int64_t n_px = (int64_t)n * h * w;
     const int nb = (int)((n_px + 255) / 256);
     if (nb > u->lpart_n) return fail(c, SC_ERR_INVALID_ARG, std::string(where) + ": loss workspace too small");
-    k_bce<<<nb, 256, 0, s>>>(pred, target, n_px, (float)(1.0 / (double)n_px), grad, gy8, u->lpart);
-    UCHK(cudaGetLastError());
-    k_bce_final<<<1, 256, 0, s>>>(u->lpart, nb, (double)n_px, loss);
+    if (u->loss_kind == SC_UNET_LOSS_BCE) {
+      k_bce<<<nb, 256, 0, s>>>(pred, target, n_px, (float)(1.0 / (double)n_px), grad, gy8, u->lpart);
+      UCHK(cudaGetLastError());
+      k_bce_final<<<1, 256, 0, s>>>(u->lpart, nb, (double)n_px, loss);
+    } else {
+      k_l2lin<<<nb, 256, 0, s>>>(pred, target, n_px, (float)(1.0 / (3.0 * (double)n_px)), grad, gy8, u->lpart);
+      UCHK(cudaGetLastError());
+      k_bce_final<<<1, 256, 0, s>>>(u->lpart, nb, 3.0 * (double)n_px, loss);
+    }
     UCHK(cudaGetLastError());
     return SC_OK;
   }
@@ -1870,7 +1901,7 @@ int sc_unet_load(sc_ctx *c, sc_unet *u, const char *path) {
 
 int sc_unet_set_loss(sc_ctx *c, sc_unet *u, int32_t kind) {
   if (!c || !u) return SC_ERR_INVALID_ARG;
-  if (kind != SC_UNET_LOSS_L1_SSIM && kind != SC_UNET_LOSS_BCE)
+  if (kind != SC_UNET_LOSS_L1_SSIM && kind != SC_UNET_LOSS_BCE && kind != SC_UNET_LOSS_L2_LINEAR)
     return fail(c, SC_ERR_INVALID_ARG, "sc_unet_set_loss: unknown loss");
   u->loss_kind = kind;
   return SC_OK;

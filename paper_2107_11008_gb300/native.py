@@ -356,6 +356,7 @@ def sc_unet_set_state(ctx, net, params_dev, m_dev, v_dev, step):
 
 SC_UNET_LOSS_L1_SSIM = 0
 SC_UNET_LOSS_BCE = 1
+SC_UNET_LOSS_L2_LINEAR = 2
 
 
 def sc_unet_set_loss(ctx, net, kind: int):

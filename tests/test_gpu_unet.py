@@ -412,3 +412,40 @@ def test_bce_segmentation_loss_vs_oracle(ctx):
     ctx.sync_status()
     assert float(last.item()) < 0.8 * first
     net.close()
+
+
+def test_linear_l2_loss_vs_oracle(ctx):
+    """The squared error in linear radiance (log1p-domain outputs and targets): loss value and output
+    gradient against the FP64 oracle on the GPU's own prediction, the network gradient against the
+    oracle backward (cosine), and training lowers the loss."""
+    n, h, w = 2, 32, 40
+    p = _params(51)
+    x, _ = _inputs(52, n, h, w)
+    rng = np.random.default_rng(53)
+    t = np.log1p(rng.exponential(0.5, (n, h, w, 3)))
+    net = D.UNet(ctx, n, h, w)
+    net.set_params(torch.from_numpy(D.flatten(p)).float().cuda())
+    net.set_loss(N_.SC_UNET_LOSS_L2_LINEAR)
+    y, loss = net.loss_grad(_dev(x), _dev(t))
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    yv = _np(y)
+    lref, gref = U.loss_l2_linear(yv, t)
+    assert abs(float(loss.item()) - lref) <= 1e-5 * abs(lref)
+    gy = net.buffer("GOUT").float().cpu().numpy().astype(np.float64)
+    assert not gy[..., 3:].any()
+    assert np.abs(gy[..., :3] - gref).max() <= BF16_REL * np.abs(gref).max()
+    pb = {k: (U.bf16(v) if not k.endswith("_b") else v) for k, v in p.items()}
+    yr, cache = U.forward(pb, U.bf16(x), CH)
+    _, gyr = U.loss_l2_linear(yr, t)
+    gr, _ = U.backward(pb, cache, gyr, CH)
+    a = net.get_grads().cpu().numpy().astype(np.float64)
+    b = D.flatten(gr)
+    assert a @ b / np.linalg.norm(a) / np.linalg.norm(b) > 0.999
+    xd, td = _dev(x), _dev(t)
+    first = float(net.train_step(xd, td, 1e-3).item())
+    for _ in range(30):
+        last = net.train_step(xd, td, 1e-3)
+    ctx.sync_status()
+    assert float(last.item()) < 0.8 * first
+    net.close()
