@@ -125,9 +125,11 @@ int sc_ssim_l1_loss(sc_ctx *ctx, const float *pred, const float *target, int32_t
                     float *loss, float *grad);
 
 /* Which radiance estimate a network input / target is built from: the full image (camera paths
- * + light-traced caustics, sc_frame.rgb) or the camera estimator alone (sc_frame.direct), in
- * which case the caustic buffer is added back after denoising (sc_unet_output_rgb's `add`). */
-enum { SC_UNET_SRC_RGB = 0, SC_UNET_SRC_DIRECT = 1 };
+ * + light-traced caustics, sc_frame.rgb), the camera estimator alone (sc_frame.direct), in
+ * which case the caustic buffer is added back after denoising (sc_unet_output_rgb's `add`), or
+ * the light-traced caustic buffer alone (sc_frame.caustic), for a network that denoises the
+ * caustics beside one that denoises the camera estimate. */
+enum { SC_UNET_SRC_RGB = 0, SC_UNET_SRC_DIRECT = 1, SC_UNET_SRC_CAUSTIC = 2 };
 
 /* Builds the 11-channel network input from a rendered frame's buffers (supercaustics.h
  * sc_frame: rgb or direct, albedo, normal_camera, depth_norm, mask) for image `index` of a

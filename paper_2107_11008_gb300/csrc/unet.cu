@@ -1953,6 +1953,7 @@ static const float *frame_source(const sc_frame *f, int source) {
   switch (source) {
     case SC_UNET_SRC_RGB: return f->rgb;
     case SC_UNET_SRC_DIRECT: return f->direct;
+    case SC_UNET_SRC_CAUSTIC: return f->caustic;
     default: return nullptr;
   }
 }

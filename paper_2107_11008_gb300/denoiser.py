@@ -180,12 +180,13 @@ def ssim_l1_loss(ctx: Context, pred: torch.Tensor, target: torch.Tensor, want_gr
     return loss, grad
 
 
-SOURCES = {"rgb": N.SC_UNET_SRC_RGB, "direct": N.SC_UNET_SRC_DIRECT}
+SOURCES = {"rgb": N.SC_UNET_SRC_RGB, "direct": N.SC_UNET_SRC_DIRECT, "caustic": N.SC_UNET_SRC_CAUSTIC}
 
 
 def pack_frame(ctx: Context, frame: Frame, x: torch.Tensor, index: int = 0, source: str = "rgb"):
     """Writes the 11-channel network input of ``frame`` into image ``index`` of x [n, H, W, 11];
-    ``source`` picks the radiance estimate: the full image or the camera estimator alone."""
+    ``source`` picks the radiance estimate: the full image, the camera estimator alone or the
+    light-traced caustic buffer alone."""
     N.sc_unet_pack_frame(ctx.handle, frame.struct(), SOURCES[source], _ptr(x), index)
     return x
 

@@ -469,7 +469,7 @@ def sc_ssim_l1_loss(ctx, pred_dev, target_dev, n, h, w, loss_dev=None, grad_dev=
     return check(load().sc_ssim_l1_loss(ctx, pred_dev, target_dev, n, h, w, loss_dev, grad_dev), ctx)
 
 
-SC_UNET_SRC_RGB, SC_UNET_SRC_DIRECT = 0, 1
+SC_UNET_SRC_RGB, SC_UNET_SRC_DIRECT, SC_UNET_SRC_CAUSTIC = 0, 1, 2
 
 
 def sc_unet_pack_frame(ctx, frame: sc_frame, source, x_dev, index):

@@ -353,12 +353,20 @@ def test_pack_frame_from_render(ctx):
     gs = R.GpuScene(ctx, sc)
     f = R.Frame(24, 16)
     R.trace_camera(ctx, gs, f, 2, 8)
-    R.resolve(ctx, gs, f, 2.0, 1.0)
+    R.trace_lights(ctx, gs, f, 1 << 16, 8)
+    R.resolve(ctx, gs, f, 2.0, float(1 << 16))
     x = torch.zeros((2, 16, 24, 11), device="cuda")
     D.pack_frame(ctx, f, x, 0)
     D.pack_frame(ctx, f, x, 1, source="direct")
     t = torch.zeros((1, 16, 24, 3), device="cuda")
     D.pack_target(ctx, f, t, 0, source="direct")
+    xc = torch.zeros((1, 16, 24, 11), device="cuda")
+    D.pack_frame(ctx, f, xc, 0, source="caustic")
+    torch.cuda.synchronize()
+    cv = f["caustic"].cpu().numpy()[..., :3]
+    assert (cv > 0).any()
+    np.testing.assert_allclose(xc[0, ..., 0:3].cpu().numpy(), np.log1p(np.maximum(cv, 0)), rtol=1e-6)
+    np.testing.assert_array_equal(xc[0, ..., 3:].cpu().numpy(), x[0, ..., 3:].cpu().numpy())
     y = torch.log1p(torch.rand((16, 24, 3), device="cuda"))
     out = D.output_rgb(ctx, y, f["caustic"])
     torch.cuda.synchronize()
