@@ -495,15 +495,19 @@ def run_denoise(args):
 def run_denoise_dense(args):
     """The dense comparison: 1024^2 frames of 16 overlapping glass objects (~1M triangles), 16
     wavelength bins, 32M guided light paths per frame.  Denoised frame = 8 camera spp + 32M light
-    paths, the U-Net (trained on 256^2 renders of other dense scenes, 8 -> 512 spp, camera estimate
-    only) on the camera estimate and the light-traced caustics added back.  Plain frames = N spp +
-    the same light paths per camera sample.  MSEs against a two-half reference (2048 spp + 4x that in
-    light paths per pixel each) with the reference's own variance subtracted; the plain tracer's
-    matched spp interpolated from a sweep up to 1024 spp (its MSE at 1024 spp measured directly)."""
+    paths, a U-Net on the camera estimate (trained on 128^2 crops of 1024^2 renders of other dense
+    scenes, 8 -> 512 spp, so that objects have the test frames' size in pixels) and the light-traced
+    caustic buffer added back.  Two networks are trained, one with L1 + SSIM in the log domain and
+    one with the squared error in linear radiance (the loss the MSE comparison rewards); a
+    validation scene, not a test scene, picks the one used.  Plain frames = N spp + the same light
+    paths per camera sample.  MSEs against a two-half reference (2048 spp + 4x that in light paths
+    per pixel each) with the reference's own variance subtracted; the plain tracer's matched spp
+    interpolated from a sweep up to 1024 spp (its MSE at 1024 spp measured directly)."""
     import numpy as np
     import torch
 
     from paper_2107_11008_gb300 import denoiser as D
+    from paper_2107_11008_gb300 import native as N
     from paper_2107_11008_gb300 import renderer as R
     from paper_2107_11008_gb300 import scenes as S
     from paper_2107_11008_gb300 import training as T
@@ -511,17 +515,17 @@ def run_denoise_dense(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    hw, train_hw, n_train, n_test, nb, depth = 1024, 256, 96, 2, 16, 12
+    hw, n_train, n_test, nb, depth = 1024, 24, 2, 16, 12
     lpp = 32e6 / (hw * hw)        # light paths per pixel of the denoised frame (32M per frame)
     ratio = lpp / 8.0             # light paths per camera sample, kept for every plain budget
     lo = T.RenderSpec(8, lpp, max_depth=depth, n_bins=nb)
+    hi = T.RenderSpec(512, 0, max_depth=depth, n_bins=nb)
     stream = torch.cuda.current_stream(dev)
     ctx = R.Context(local, stream)
     t0 = time.perf_counter()
-    train_scenes = [S.dense_scene(100 + i, train_hw, train_hw, tris_per_object=16000) for i in range(n_train)]
-    train = T.make_pairs(ctx, train_scenes, lo, T.RenderSpec(512, 0, max_depth=depth, n_bins=nb), seed=1,
+    train = T.make_pairs(ctx, [S.dense_scene(100 + i, hw, hw) for i in range(n_train)], lo, hi, seed=1,
                          source="direct")
-    del train_scenes
+    val = T.make_pairs(ctx, [S.dense_scene(5_000, hw, hw)], lo, hi, seed=4, source="direct")
     test_scenes = [S.dense_scene(10_000 + i, hw, hw) for i in range(n_test)]
     gss = [R.GpuScene(ctx, sc) for sc in test_scenes]
     guides = [S.guide_sphere(sc) for sc in test_scenes]
@@ -534,6 +538,7 @@ def run_denoise_dense(args):
         D.pack_frame(ctx, f, test_x, i, "direct")
         test_caustic[i].copy_(f["caustic"])
         test_rgb[i].copy_(f["rgb"])
+    glass = test_x[..., 10] > 0.5  # transparent-object pixels (the mask channel of the input)
     half = T.RenderSpec(2048, 2048 * ratio, max_depth=depth, n_bins=nb)
     ref_a = torch.empty_like(test_rgb)
     ref_b = torch.empty_like(test_rgb)
@@ -550,25 +555,42 @@ def run_denoise_dense(args):
     var_ref = T.mse(ref_a, ref_b) / 4.0
     gen_s = time.perf_counter() - t0
     trainer = D.UNet(ctx, 16, 128, 128)
-    trainer.set_params(D.he_init(0).to(dev))
     t0 = time.perf_counter()
-    T.train(trainer, train, steps=args.den_steps, batch=16, crop=128, lr=1.5e-3, lr_final=5e-5, seed=0)
+    candidates = {}
+    for name, loss_kind, lr, init in (("l1_ssim", N.SC_UNET_LOSS_L1_SSIM, 1.5e-3, 0),
+                                      ("l2_linear", N.SC_UNET_LOSS_L2_LINEAR, 1e-3, 1)):
+        trainer.set_params(D.he_init(init).to(dev))
+        trainer.set_loss(loss_kind)
+        T.train(trainer, train, steps=args.den_steps, batch=16, crop=128, lr=lr, lr_final=5e-5, seed=init)
+        candidates[name] = trainer.get_params()
     torch.cuda.synchronize(dev)
     train_s = time.perf_counter() - t0
-    trainer_params = trainer.get_params()
     trainer.close()
     del train
     net = D.UNet(ctx, 1, hw, hw)
-    net.set_params(trainer_params)
+    val_mse, test_mse = {}, {}
+    for name, prm in candidates.items():
+        net.set_params(prm)
+        # validation: the network's camera estimate against the validation scene's 512-spp one
+        val_mse[name] = T.mse(T.denoise(net, val.x, None, batch=1), torch.expm1(val.target))
+        test_mse[name] = T.mse(T.denoise(net, test_x, test_caustic, batch=1), ref) - var_ref
+    chosen = min(val_mse, key=val_mse.get)
+    net.set_params(candidates[chosen])
+    del val
     den = T.denoise(net, test_x, test_caustic, batch=1)
     m_den = T.mse(den, ref) - var_ref
     m_in = T.mse(test_rgb, ref) - var_ref
     # where the denoised frame's error sits: the network's camera estimate against the reference's
-    # camera part, and the light-traced caustic buffer (added back unchanged) against its caustic part
-    # (each still carries its share of the reference's own variance)
-    m_parts = {"network_camera_estimate": T.mse(T.denoise(net, test_x, None, batch=1), ref_direct),
+    # camera part, the caustic buffer (added back unchanged) against its caustic part, and the
+    # transparent-object pixels against the rest (each still carries its share of the reference's
+    # own variance)
+    den_cam = T.denoise(net, test_x, None, batch=1)
+    sq = ((den[..., :3].double() - ref[..., :3].double()) ** 2).sum(-1)
+    m_parts = {"network_camera_estimate": T.mse(den_cam, ref_direct),
                "caustic_buffer": T.mse(test_caustic, ref_caustic),
-               "input_camera_estimate": T.mse(test_rgb - test_caustic, ref_direct)}
+               "input_camera_estimate": T.mse(test_rgb - test_caustic, ref_direct),
+               "glass_pixel_share_of_squared_error": float(sq[glass].sum() / sq.sum()),
+               "glass_pixel_fraction": float(glass.double().mean())}
     sweep = {}
     for spp in (8, 16, 32, 64, 128, 256, 512, 1024):
         out = torch.empty_like(ref)
@@ -635,13 +657,15 @@ def run_denoise_dense(args):
                 "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic (scenes.dense_scene)",
                 "config": {"workload": "denoise_dense: 1024^2 scenes.dense_scene (16 glass objects, 1.08M tris), 16 bins, "
                                        "depth 12, 8 spp + 32M guided light paths; U-Net on the camera estimate trained "
-                                       f"{args.den_steps} steps on 128^2 crops of {n_train} 256^2 dense-scene pairs "
-                                       "(8 -> 512 spp), light-traced caustics added back; 2 held-out scenes; reference "
+                                       f"{args.den_steps} steps on 128^2 crops of {n_train} 1024^2 dense-scene pairs "
+                                       "(8 -> 512 spp; L1 + SSIM or linear squared error, picked on a validation "
+                                       "scene), light-traced caustics added back; 2 held-out scenes; reference "
                                        "2 x (2048 spp + 4x light paths per sample)",
                            "light_paths_per_camera_sample": ratio},
                 "mse": {"denoised": m_den, "input": m_in, "reference_variance": var_ref, "plain_sweep": sweep,
                         "plain_1024spp": sweep[1024], "denoised_reaches_plain_1024": m_den <= sweep[1024],
-                        "parts": m_parts},
+                        "parts": m_parts, "by_loss": {"validation": val_mse, "test": test_mse,
+                                                      "chosen": chosen}},
                 "matched_spp": spp_match,
                 "plain_frame": {"spp": spp_int, "ms": plain_ms, "fps": world * 1e3 / plain_ms},
                 "plain_1024spp_frame": {"ms": plain1024_ms, "fps": world * 1e3 / plain1024_ms},
