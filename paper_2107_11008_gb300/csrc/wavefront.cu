@@ -34,6 +34,14 @@ constexpr int kWfBlock = 128;
 #ifndef SC_WF_CHUNK
 #define SC_WF_CHUNK 12
 #endif
+// Launch bounds of the two persistent traversal kernels: by default the compiler's register
+// choice; a build with SC_WF_TRAV_MINB set asks for that many resident blocks per SM instead
+// (fewer registers each, more warps to hide node-fetch latency).
+#ifdef SC_WF_TRAV_MINB
+#define SC_WF_TRAV_BOUNDS __launch_bounds__(kWfBlock, SC_WF_TRAV_MINB)
+#else
+#define SC_WF_TRAV_BOUNDS __launch_bounds__(kWfBlock)
+#endif
 constexpr int kWfChunk = SC_WF_CHUNK;
 enum : uint32_t {
   W_SPEC_ONLY = 1u, W_DIFFUSE_FIRST = 2u, W_LAST_SPECULAR = 4u, W_FIXUP = 8u, W_HAS_NEXT = 16u
@@ -172,7 +180,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_generate(WfArgs a, Wave w) {
 
 // ---- extend: closest hits of the extend queue, classified by material ----------------------------
 template <bool B>
-__global__ void __launch_bounds__(kWfBlock) k_wf_extend(WfArgs a, Wave w, int cur) {
+__global__ void SC_WF_TRAV_BOUNDS k_wf_extend(WfArgs a, Wave w, int cur) {
   const uint32_t *q = w.q_ext[cur];
   const unsigned nq_total = w.cnt[cur ? C_EXT1 : C_EXT0];
   unsigned *ticket = w.cnt + C_TICKET_EXT;
@@ -463,7 +471,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_diffuse(WfArgs a, Wave w, int n
 
 // ---- shadow rays of the next-event estimates -----------------------------------------------------
 template <bool B>
-__global__ void __launch_bounds__(kWfBlock) k_wf_shadow(WfArgs a, Wave w, int next) {
+__global__ void SC_WF_TRAV_BOUNDS k_wf_shadow(WfArgs a, Wave w, int next) {
   const unsigned nq_total = w.cnt[C_SHADOW];
   unsigned *ticket = w.cnt + C_TICKET_SHADOW;
   const int lane = threadIdx.x & 31;
