@@ -15,6 +15,7 @@ bounded sample of the same workload.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -38,10 +39,15 @@ FLOPS_PER_NODE = 48
 FLOPS_PER_TRI = 43
 BYTES_PER_NODE = 112
 BYTES_PER_TRI = 48
-# our kernels per step besides the camera estimator: LBVH build (bounds init, gather, morton,
-# 8 x (hist, scan, scatter), reorder, karras, refit, depth, 4-wide collapse) + lights + resolve +
-# outline/occlusion pass
-LAUNCHES_PER_STEP_BASE = 31 + 3
+
+
+def launches_per_step_base(n_tris):
+    """Our kernels per step besides the camera estimator: the BVH build (bounds init, gather,
+    morton, 8 x (hist, scan, scatter), reorder, PLOC init, 4 launches per grid-wide round, the
+    single-block finish, depth, 4-wide collapse) + lights + resolve + outline/occlusion pass.  The
+    grid-wide rounds follow the library's rule: enough to bring ~0.84^k * n below 1024 clusters."""
+    rounds = 0 if n_tris <= 1024 else math.ceil(math.log(n_tris / 1024) / math.log(1 / 0.84))
+    return 3 + 24 + 1 + (2 + 4 * rounds) + 2 + 3
 
 
 def camera_launches(engine, width, height, spp, depth):
@@ -1162,7 +1168,8 @@ def main():
                           "camera_l2_side_gbs": cam_bytes / cam_s / 1e9},
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": (LAUNCHES_PER_STEP_BASE + camera_launches(args.camera_engine, res, res, spp, depth)) *
+            "gpu_launches": (launches_per_step_base(scene.n_tris) + camera_launches(args.camera_engine, res, res, spp,
+                                                                                     depth)) *
                             args.steps,
             "clocks": clocks,
             "cpu_baseline": cb,
