@@ -443,10 +443,13 @@ def test_linear_l2_loss_vs_oracle(ctx):
     gy = net.buffer("GOUT").float().cpu().numpy().astype(np.float64)
     assert not gy[..., 3:].any()
     assert np.abs(gy[..., :3] - gref).max() <= BF16_REL * np.abs(gref).max()
+    # the network gradient: the oracle backward seeded with the loss gradient at the GPU's own
+    # prediction (checked above).  Its own forward's output differs from the GPU's BF16 one by
+    # ~1e-2, and the exp(y) in this loss's gradient passes that into the seed unreduced, which is
+    # a property of the loss, not of the backward pass under test.
     pb = {k: (U.bf16(v) if not k.endswith("_b") else v) for k, v in p.items()}
-    yr, cache = U.forward(pb, U.bf16(x), CH)
-    _, gyr = U.loss_l2_linear(yr, t)
-    gr, _ = U.backward(pb, cache, gyr, CH)
+    _, cache = U.forward(pb, U.bf16(x), CH)
+    gr, _ = U.backward(pb, cache, gref, CH)
     a = net.get_grads().cpu().numpy().astype(np.float64)
     b = D.flatten(gr)
     assert a @ b / np.linalg.norm(a) / np.linalg.norm(b) > 0.999
