@@ -428,6 +428,10 @@ def test_linear_l2_loss_vs_oracle(ctx):
     oracle backward (cosine), and training lowers the loss."""
     n, h, w = 2, 32, 40
     p = _params(51)
+    # outputs in the range a denoiser's log1p radiance has (-1 .. 2 here): with the output layer at
+    # its initial scale they reach 8.6, exp(y) puts 94 % of the gradient on 1 % of the entries, and
+    # the whole-network comparison would weigh a handful of pixels instead of the backward pass
+    p["out_w"] = p["out_w"] * 0.25
     x, _ = _inputs(52, n, h, w)
     rng = np.random.default_rng(53)
     t = np.log1p(rng.exponential(0.5, (n, h, w, 3)))
@@ -443,13 +447,10 @@ def test_linear_l2_loss_vs_oracle(ctx):
     gy = net.buffer("GOUT").float().cpu().numpy().astype(np.float64)
     assert not gy[..., 3:].any()
     assert np.abs(gy[..., :3] - gref).max() <= BF16_REL * np.abs(gref).max()
-    # the network gradient: the oracle backward seeded with the loss gradient at the GPU's own
-    # prediction (checked above).  Its own forward's output differs from the GPU's BF16 one by
-    # ~1e-2, and the exp(y) in this loss's gradient passes that into the seed unreduced, which is
-    # a property of the loss, not of the backward pass under test.
     pb = {k: (U.bf16(v) if not k.endswith("_b") else v) for k, v in p.items()}
-    _, cache = U.forward(pb, U.bf16(x), CH)
-    gr, _ = U.backward(pb, cache, gref, CH)
+    yr, cache = U.forward(pb, U.bf16(x), CH)
+    _, gyr = U.loss_l2_linear(yr, t)
+    gr, _ = U.backward(pb, cache, gyr, CH)
     a = net.get_grads().cpu().numpy().astype(np.float64)
     b = D.flatten(gr)
     assert a @ b / np.linalg.norm(a) / np.linalg.norm(b) > 0.999
