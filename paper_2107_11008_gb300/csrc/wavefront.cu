@@ -43,11 +43,6 @@ constexpr int kWfBlock = 128;
 #define SC_WF_TRAV_BOUNDS __launch_bounds__(kWfBlock)
 #endif
 constexpr int kWfChunk = SC_WF_CHUNK;
-// queries per persistent lane at or above which the traversal kernels look one query ahead
-#ifndef SC_WF_LOOKAHEAD
-#define SC_WF_LOOKAHEAD 16
-#endif
-constexpr int kWfLookahead = SC_WF_LOOKAHEAD;
 __device__ __forceinline__ void prefetch_l2(const void *ptr) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
 }
@@ -197,35 +192,35 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_extend(WfArgs a, Wave w, int cur) {
   TravState ts;
   int stack[kStack];
   int p = -1, sc = 0;
-  // With a long queue, one query of look-ahead per lane: its queue entry is read (without waiting
-  // for it) when the ticket is taken and its path state prefetched into L2 one loop turn later, so
-  // that a lane whose query ends starts the next one from L2 instead of two dependent trips to
-  // HBM.  With a short queue a held-back query would leave another lane idle, so none is taken.
-  const bool ahead = nq_total >= (unsigned)kWfLookahead * gridDim.x * blockDim.x;
+  // one query of look-ahead per lane: its queue entry is read (without waiting for it) when the
+  // ticket is taken, its path state prefetched into L2 one loop turn later, so that a lane whose
+  // query ends starts the next one from L2 instead of two dependent trips to HBM
   int nxt = -1;
   bool nxt_pref = false, tickets_done = false;
   bool tracing = false, exhausted = false;
   float3 o = f3(0.f, 0.f, 0.f), d = o;
   for (;;) {
-    if (!tracing && !exhausted && nxt >= 0) {
-      p = nxt;
-      nxt = -1;
-      const float4 o4 = w.o[p], d4 = w.d[p];
-      if (B) sc = __float_as_int(d4.w);
-      o = f3(o4.x, o4.y, o4.z);
-      d = f3(d4.x, d4.y, d4.z);
-      trav_begin(ts, 3.0e38f, false);
-      tracing = true;
+    if (!tracing && !exhausted) {
+      if (nxt >= 0) {
+        p = nxt;
+        nxt = -1;
+        const float4 o4 = w.o[p], d4 = w.d[p];
+        if (B) sc = __float_as_int(d4.w);
+        o = f3(o4.x, o4.y, o4.z);
+        d = f3(d4.x, d4.y, d4.z);
+        trav_begin(ts, 3.0e38f, false);
+        tracing = true;
+      } else if (tickets_done) {
+        exhausted = true;
+      }
     }
     if (nxt >= 0 && !nxt_pref) {  // its index arrived during the last traversal chunk
       prefetch_l2(w.o + nxt);
       prefetch_l2(w.d + nxt);
       nxt_pref = true;
     }
-    // tickets (one atomic per warp): for lanes without a query, taken at once; with a long queue
-    // also for lanes without a look-ahead query
-    const bool now = !tracing && !exhausted;
-    const bool want = now || (ahead && nxt < 0 && !tickets_done);
+    // lanes without a next query take a ticket (one atomic per warp)
+    const bool want = nxt < 0 && !tickets_done;
     const unsigned wmask = __ballot_sync(0xFFFFFFFFu, want);
     if (wmask) {
       const int leader = __ffs(wmask) - 1;
@@ -234,20 +229,11 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_extend(WfArgs a, Wave w, int cur) {
       base = __shfl_sync(0xFFFFFFFFu, base, leader);
       if (want) {
         const unsigned t = base + (unsigned)__popc(wmask & ((1u << lane) - 1u));
-        if (t >= nq_total) {
-          tickets_done = true;
-          if (now) exhausted = true;
-        } else if (now) {
-          p = (int)q[t];
-          const float4 o4 = w.o[p], d4 = w.d[p];
-          if (B) sc = __float_as_int(d4.w);
-          o = f3(o4.x, o4.y, o4.z);
-          d = f3(d4.x, d4.y, d4.z);
-          trav_begin(ts, 3.0e38f, false);
-          tracing = true;
-        } else {
+        if (t < nq_total) {
           nxt = (int)q[t];
           nxt_pref = false;
+        } else {
+          tickets_done = true;
         }
       }
     }
@@ -515,26 +501,30 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_shadow(WfArgs a, Wave w, int next) {
   TravState ts;
   int stack[kStack];
   int p = -1, sc = 0;
-  const bool ahead = nq_total >= (unsigned)kWfLookahead * gridDim.x * blockDim.x;  // as in k_wf_extend
-  int nxt = -1;
+  int nxt = -1;  // one query of look-ahead per lane, as in k_wf_extend
   bool nxt_pref = false, tickets_done = false;
   bool tracing = false, exhausted = false;
   float3 o = f3(0.f, 0.f, 0.f), d = o;
   float tmax = 0.0f;
-  auto begin = [&](int q_p) {
-    p = q_p;
-    const float4 o4 = w.so[p], d4 = w.sd[p];
-    if (B) sc = __float_as_int(d4.w);
-    o = f3(o4.x, o4.y, o4.z);
-    d = f3(d4.x, d4.y, d4.z);
-    tmax = w.nee[p].w;
-    trav_begin(ts, tmax, true);
-    tracing = true;
-  };
   for (;;) {
-    if (!tracing && !exhausted && nxt >= 0) {
-      begin(nxt);
-      nxt = -1;
+    if (!tracing && !exhausted) {
+      if (nxt >= 0) {
+        p = nxt;
+        nxt = -1;
+        const float4 o4 = w.so[p], d4 = w.sd[p];
+        if (B) sc = __float_as_int(d4.w);
+        o = f3(o4.x, o4.y, o4.z);
+        d = f3(d4.x, d4.y, d4.z);
+        tmax = w.nee[p].w;
+        trav_begin(ts, tmax, true);
+        tracing = true;
+        // what the query's end reads, on its way to L2 while the query traverses
+        prefetch_l2(w.L + p);
+        prefetch_l2(w.m0 + p);
+        prefetch_l2(w.m1 + p);
+      } else if (tickets_done) {
+        exhausted = true;
+      }
     }
     if (nxt >= 0 && !nxt_pref) {
       prefetch_l2(w.so + nxt);
@@ -542,8 +532,7 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_shadow(WfArgs a, Wave w, int next) {
       prefetch_l2(w.nee + nxt);
       nxt_pref = true;
     }
-    const bool now = !tracing && !exhausted;
-    const bool want = now || (ahead && nxt < 0 && !tickets_done);
+    const bool want = nxt < 0 && !tickets_done;
     const unsigned wmask = __ballot_sync(0xFFFFFFFFu, want);
     if (wmask) {
       const int leader = __ffs(wmask) - 1;
@@ -552,14 +541,11 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_shadow(WfArgs a, Wave w, int next) {
       base = __shfl_sync(0xFFFFFFFFu, base, leader);
       if (want) {
         const unsigned t = base + (unsigned)__popc(wmask & ((1u << lane) - 1u));
-        if (t >= nq_total) {
-          tickets_done = true;
-          if (now) exhausted = true;
-        } else if (now) {
-          begin((int)w.q_shadow[t]);
-        } else {
+        if (t < nq_total) {
           nxt = (int)w.q_shadow[t];
           nxt_pref = false;
+        } else {
+          tickets_done = true;
         }
       }
     }
