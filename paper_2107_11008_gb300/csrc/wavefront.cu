@@ -43,9 +43,6 @@ constexpr int kWfBlock = 128;
 #define SC_WF_TRAV_BOUNDS __launch_bounds__(kWfBlock)
 #endif
 constexpr int kWfChunk = SC_WF_CHUNK;
-__device__ __forceinline__ void prefetch_l2(const void *ptr) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
-}
 enum : uint32_t {
   W_SPEC_ONLY = 1u, W_DIFFUSE_FIRST = 2u, W_LAST_SPECULAR = 4u, W_FIXUP = 8u, W_HAS_NEXT = 16u
 };
@@ -192,35 +189,11 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_extend(WfArgs a, Wave w, int cur) {
   TravState ts;
   int stack[kStack];
   int p = -1, sc = 0;
-  // one query of look-ahead per lane: its queue entry is read (without waiting for it) when the
-  // ticket is taken, its path state prefetched into L2 one loop turn later, so that a lane whose
-  // query ends starts the next one from L2 instead of two dependent trips to HBM
-  int nxt = -1;
-  bool nxt_pref = false, tickets_done = false;
   bool tracing = false, exhausted = false;
   float3 o = f3(0.f, 0.f, 0.f), d = o;
   for (;;) {
-    if (!tracing && !exhausted) {
-      if (nxt >= 0) {
-        p = nxt;
-        nxt = -1;
-        const float4 o4 = w.o[p], d4 = w.d[p];
-        if (B) sc = __float_as_int(d4.w);
-        o = f3(o4.x, o4.y, o4.z);
-        d = f3(d4.x, d4.y, d4.z);
-        trav_begin(ts, 3.0e38f, false);
-        tracing = true;
-      } else if (tickets_done) {
-        exhausted = true;
-      }
-    }
-    if (nxt >= 0 && !nxt_pref) {  // its index arrived during the last traversal chunk
-      prefetch_l2(w.o + nxt);
-      prefetch_l2(w.d + nxt);
-      nxt_pref = true;
-    }
-    // lanes without a next query take a ticket (one atomic per warp)
-    const bool want = nxt < 0 && !tickets_done;
+    // refill lanes without a query from the queue (one atomic per warp)
+    const bool want = !tracing && !exhausted;
     const unsigned wmask = __ballot_sync(0xFFFFFFFFu, want);
     if (wmask) {
       const int leader = __ffs(wmask) - 1;
@@ -230,10 +203,15 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_extend(WfArgs a, Wave w, int cur) {
       if (want) {
         const unsigned t = base + (unsigned)__popc(wmask & ((1u << lane) - 1u));
         if (t < nq_total) {
-          nxt = (int)q[t];
-          nxt_pref = false;
+          p = (int)q[t];
+          const float4 o4 = w.o[p], d4 = w.d[p];
+          if (B) sc = __float_as_int(d4.w);
+          o = f3(o4.x, o4.y, o4.z);
+          d = f3(d4.x, d4.y, d4.z);
+          trav_begin(ts, 3.0e38f, false);
+          tracing = true;
         } else {
-          tickets_done = true;
+          exhausted = true;
         }
       }
     }
@@ -501,38 +479,11 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_shadow(WfArgs a, Wave w, int next) {
   TravState ts;
   int stack[kStack];
   int p = -1, sc = 0;
-  int nxt = -1;  // one query of look-ahead per lane, as in k_wf_extend
-  bool nxt_pref = false, tickets_done = false;
   bool tracing = false, exhausted = false;
   float3 o = f3(0.f, 0.f, 0.f), d = o;
   float tmax = 0.0f;
   for (;;) {
-    if (!tracing && !exhausted) {
-      if (nxt >= 0) {
-        p = nxt;
-        nxt = -1;
-        const float4 o4 = w.so[p], d4 = w.sd[p];
-        if (B) sc = __float_as_int(d4.w);
-        o = f3(o4.x, o4.y, o4.z);
-        d = f3(d4.x, d4.y, d4.z);
-        tmax = w.nee[p].w;
-        trav_begin(ts, tmax, true);
-        tracing = true;
-        // what the query's end reads, on its way to L2 while the query traverses
-        prefetch_l2(w.L + p);
-        prefetch_l2(w.m0 + p);
-        prefetch_l2(w.m1 + p);
-      } else if (tickets_done) {
-        exhausted = true;
-      }
-    }
-    if (nxt >= 0 && !nxt_pref) {
-      prefetch_l2(w.so + nxt);
-      prefetch_l2(w.sd + nxt);
-      prefetch_l2(w.nee + nxt);
-      nxt_pref = true;
-    }
-    const bool want = nxt < 0 && !tickets_done;
+    const bool want = !tracing && !exhausted;
     const unsigned wmask = __ballot_sync(0xFFFFFFFFu, want);
     if (wmask) {
       const int leader = __ffs(wmask) - 1;
@@ -542,10 +493,16 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_shadow(WfArgs a, Wave w, int next) {
       if (want) {
         const unsigned t = base + (unsigned)__popc(wmask & ((1u << lane) - 1u));
         if (t < nq_total) {
-          nxt = (int)w.q_shadow[t];
-          nxt_pref = false;
+          p = (int)w.q_shadow[t];
+          const float4 o4 = w.so[p], d4 = w.sd[p];
+          if (B) sc = __float_as_int(d4.w);
+          o = f3(o4.x, o4.y, o4.z);
+          d = f3(d4.x, d4.y, d4.z);
+          tmax = w.nee[p].w;
+          trav_begin(ts, tmax, true);
+          tracing = true;
         } else {
-          tickets_done = true;
+          exhausted = true;
         }
       }
     }
