@@ -521,7 +521,7 @@ int sc_trace_camera(sc_ctx *c, const sc_scene *s, const sc_trace_params *p, cons
     // waves of whole pixels of up to 2^24 paths (at least one 8x4 tile with all its samples)
     const int64_t tiles = (int64_t)((f->width + 7) / 8) * ((f->height + 3) / 4);
     const int64_t one_tile = 32 * (int64_t)p->spp;
-    const int64_t max_paths = std::max<int64_t>(one_tile, std::min<int64_t>(tiles * one_tile, int64_t(1) << 24));
+    const int64_t max_paths = std::max<int64_t>(one_tile, std::min<int64_t>(tiles * one_tile, sc::kWfMaxWavePaths));
     if (max_paths > INT32_MAX / 2) return fail(c, SC_ERR_INVALID_ARG, "sc_trace_camera: spp too large");
     void *ws = dalloc(c, sc::wavefront_workspace_bytes(max_paths));
     if (!ws) return fail(c, SC_ERR_OOM, "sc_trace_camera: no device memory for the path wavefront");
@@ -622,7 +622,7 @@ static int batch_table(sc_ctx *c, const sc_scene *const *scenes, const sc_frame 
 // wavefront workspace of a batch: waves of up to 2^24 paths, at least one 32-slot tile of all samples
 static int64_t batch_wave_paths(const sc_trace_params *p, int64_t total_slots) {
   const int64_t one_tile = 32 * (int64_t)std::max(p->spp, 1);
-  return std::max<int64_t>(one_tile, std::min<int64_t>(total_slots * (int64_t)std::max(p->spp, 1), int64_t(1) << 24));
+  return std::max<int64_t>(one_tile, std::min<int64_t>(total_slots * (int64_t)std::max(p->spp, 1), sc::kWfMaxWavePaths));
 }
 
 int sc_trace_batch(sc_ctx *c, const sc_scene *const *scenes, const sc_frame *frames, int32_t n,

@@ -65,6 +65,11 @@ cudaError_t launch_occluded(const DevScene &S, const float *rays, int64_t n, int
                             cudaStream_t s);
 // the camera estimator as a wavefront (wavefront.cu): waves of whole pixels of at most max_paths
 // paths, path state and queues in `workspace` (wavefront_workspace_bytes(max_paths) bytes)
+// paths of one wave at most (whole pixels of all their samples; the path state is ~230 B a path)
+#ifndef SC_WF_MAX_WAVE_LOG2
+#define SC_WF_MAX_WAVE_LOG2 24
+#endif
+constexpr int64_t kWfMaxWavePaths = int64_t(1) << SC_WF_MAX_WAVE_LOG2;
 size_t wavefront_workspace_bytes(int64_t max_paths);
 cudaError_t launch_trace_camera_wavefront(const DevScene &S, const sc_trace_params &p, const sc_frame &f,
                                           unsigned *status, unsigned long long *counters, void *workspace,
