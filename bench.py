@@ -52,13 +52,13 @@ def launches_per_step_base(n_tris):
 
 def camera_launches(engine, width, height, spp, depth):
     """Kernel launches of one sc_trace_camera call: one persistent kernel, or per wave of whole
-    pixels (at most 2^24 paths) generate + depth x (extend, dielectric, diffuse, shadow, rotate) +
+    pixels (at most 2^25 paths) generate + depth x (extend, dielectric, diffuse, shadow, rotate) +
     reduce."""
     if engine == "persistent":
         return 1
     tiles = ((width + 7) // 8) * ((height + 3) // 4)
     one_tile = 32 * spp
-    max_paths = max(one_tile, min(tiles * one_tile, 1 << 24))
+    max_paths = max(one_tile, min(tiles * one_tile, 1 << 25))
     wave_tiles = max(1, max_paths // one_tile)
     waves = -(-tiles // wave_tiles)
     return waves * (2 + 5 * depth)

@@ -65,9 +65,12 @@ cudaError_t launch_occluded(const DevScene &S, const float *rays, int64_t n, int
                             cudaStream_t s);
 // the camera estimator as a wavefront (wavefront.cu): waves of whole pixels of at most max_paths
 // paths, path state and queues in `workspace` (wavefront_workspace_bytes(max_paths) bytes)
-// paths of one wave at most (whole pixels of all their samples; the path state is ~230 B a path)
+// paths of one wave at most (whole pixels of all their samples; the path state is ~230 B a path,
+// 7.7 GB at 2^25).  Larger waves measured faster down the line (512^2 glass frame at 256 spp,
+// camera phase: 2^21 165 ms, 2^22 134, 2^23 123, 2^24 117, 2^25 115.4, 2^26 115.7): fewer waves
+// mean fewer bounces whose last queries leave the GPU idle.
 #ifndef SC_WF_MAX_WAVE_LOG2
-#define SC_WF_MAX_WAVE_LOG2 24
+#define SC_WF_MAX_WAVE_LOG2 25
 #endif
 constexpr int64_t kWfMaxWavePaths = int64_t(1) << SC_WF_MAX_WAVE_LOG2;
 size_t wavefront_workspace_bytes(int64_t max_paths);

@@ -686,15 +686,15 @@ def test_camera_engines_agree_bit_for_bit(ctx, which):
 
 
 def test_wavefront_splits_large_frames_into_waves(ctx):
-    """A frame larger than one wave (2^24 paths): 512^2 at 80 spp is two waves; against the persistent
-    engine on sampled pixels' accumulators (bit for bit)."""
+    """A frame larger than one wave (2^25 paths): 512^2 at 160 spp is two waves; against the persistent
+    engine, every pixel's accumulator bit for bit."""
     sc = S.ball_on_plane(512, 512)
     gs = R.GpuScene(ctx, sc)
     acc = {}
     for engine in (N.SC_CAMERA_WAVEFRONT, N.SC_CAMERA_PERSISTENT):
         N.sc_set_camera_engine(ctx.handle, engine)
         fr = R.Frame(512, 512, fields=("accum_camera",))
-        R.trace_camera(ctx, gs, fr, 80, 8)
+        R.trace_camera(ctx, gs, fr, 160, 8)
         ctx.sync_status()
         acc[engine] = fr["accum_camera"].cpu().numpy()
     N.sc_set_camera_engine(ctx.handle, N.SC_CAMERA_WAVEFRONT)
