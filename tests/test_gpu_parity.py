@@ -17,13 +17,13 @@ from paper_2107_11008_gb300 import native as N  # noqa: E402
 from paper_2107_11008_gb300 import renderer as R  # noqa: E402
 from paper_2107_11008_gb300 import scenes as S  # noqa: E402
 
-from .parity import MSE, compare_camera, compare_lights, rel_close  # noqa: E402
+from .parity import MSE, compare_camera, compare_lights, grazing_bound, rel_close  # noqa: E402
 
-# The 512^2 scene's meshes have ~20k triangles each: the tolerance band around triangle edges
-# (2e-5 max(1, |p|)) covers a larger share of their surface, and a path through glass meets several
-# of them.  The oracle alone measures 0.76 % grazing paths on the sampled rows below (1.25 % over
-# the frame, tests/test_oracle_pins.py); this scene's bound is 2 %.
-MAX_GRAZING_DENSE_MESH = 0.02
+# The full-size glass scenes' meshes have 20k to 62k triangles each: the tolerance band around
+# triangle edges (2e-5 max(1, |p|)) covers 0.9-3 % of each glass hit, and a path through glass
+# meets several.  Their grazing share is bounded by what that band predicts for the paths' glass
+# hits plus 0.5 % (parity.grazing_bound; the oracle alone matches the prediction in
+# tests/test_oracle_pins.py).
 
 pytestmark = pytest.mark.gpu
 
@@ -522,14 +522,61 @@ def test_full_size_glass_scene_sampled_rows(ctx):
     rows = [0, 137, 300, 511]
     orc = O.OracleScene(sc)
     n_paths = n_grazing = 0
+    nspec = []
     for y in rows:
         _, rec = orc.trace_camera(spp, depth, nbins=nb, window=(0, 512, y, y + 1))
         sel = slice(y * 512 * spp, (y + 1) * 512 * spp)
-        # per-path checks row by row; the grazing share is bounded over the sampled rows together
+        # per-path checks row by row; the grazing share is bounded over the sampled rows together,
+        # by the share the glass mesh's edge band predicts (+ 0.5 % for the other flag kinds)
         st = compare_camera({k: v[sel] for k, v in g.items()}, rec, max_grazing=1.0)
         n_paths += st["n"]
         n_grazing += round(st["grazing"] * st["n"])
-    assert n_grazing / n_paths <= MAX_GRAZING_DENSE_MESH
+        nspec.append(rec["n_specular"])
+    assert n_grazing / n_paths <= grazing_bound(sc, np.concatenate(nspec), O.default_tol().pos)
+
+
+def _window_records(g, W, spp, x0, x1, y0, y1):
+    """The GPU records of a pixel window, in the oracle's order (rows, then pixels, then samples)."""
+    ys, xs, ss = np.meshgrid(np.arange(y0, y1), np.arange(x0, x1), np.arange(spp), indexing="ij")
+    idx = ((ys * W + xs) * spp + ss).ravel()
+    return {k: v[idx] for k, v in g.items()}
+
+
+def test_dense_1024_scene_parity(ctx):
+    """The benchmark spec's dense workload (1024^2, 16 glass objects of ~62k triangles, 16 bins, depth
+    12, guided light paths): the camera estimator path by path on a 64^2 window and two full rows
+    of the frame traced at full size, and 2^15 light paths of the frame's caustic buffer, against the
+    oracle.  The denoising comparison's reference is this estimator at 4096 samples, so this is its
+    check against the oracle; the grazing share is bounded by the glass mesh's edge band."""
+    sc = S.dense_scene(10_000, 1024, 1024)
+    spp, depth, nb = 2, 12, 16
+    gs = R.GpuScene(ctx, sc)
+    fr = R.Frame(1024, 1024, fields=("accum_camera",))
+    fr.alloc_path_records(spp)
+    R.trace_camera(ctx, gs, fr, spp, depth, nb, 0)
+    ctx.sync_status()
+    g = R.path_records_numpy(fr.path_records)
+    orc = O.OracleScene(sc)
+    pos = O.default_tol().pos
+    n_paths = n_grazing = 0
+    nspec = []
+    for w in [(480, 544, 480, 544), (0, 1024, 300, 301), (0, 1024, 700, 701)]:
+        _, rec = orc.trace_camera(spp, depth, nbins=nb, window=w)
+        st = compare_camera(_window_records(g, 1024, spp, *w), rec, max_grazing=1.0)
+        n_paths += st["n"]
+        n_grazing += round(st["grazing"] * st["n"])
+        nspec.append(rec["n_specular"])
+    assert n_grazing / n_paths <= grazing_bound(sc, np.concatenate(nspec), pos)
+    guide = S.guide_sphere(sc)
+    n = 1 << 15
+    fl = R.Frame(1024, 1024, fields=("accum_caustic",))
+    fl.alloc_light_records(n)
+    R.trace_lights(ctx, gs, fl, n, depth, nb, seed=5, guide=guide)
+    ctx.sync_status()
+    gl = R.light_records_numpy(fl.light_records)
+    _, lrec = orc.trace_lights(n, depth, nbins=nb, seed=5, guide=guide)
+    st = compare_lights(gl, lrec, max_grazing=grazing_bound(sc, lrec["n_specular"], pos))
+    assert st["splatted"] > 0.01
 
 
 # ------------------------------------------------------------------------------------------
