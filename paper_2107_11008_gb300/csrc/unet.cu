@@ -1386,14 +1386,6 @@ int backward_body(sc_ctx *c, sc_unet *u) {
   for (int l = kLevels - 1; l >= 0; --l) {
     const int h = u->hl[l], w = u->wl[l], cl = kChans[l];
     const Layer &c2 = u->L[enc_layer(l, 1)], &c1 = u->L[enc_layer(l, 0)];
-    if (l == 0 && red.n > 0) {
-      // every partial so far, reduced while level 0's data gradients run on the context stream:
-      // only level 0's two layers are left for the reduce that ends the pass
-      k_wgrad_reduce<<<(unsigned)red_blocks, kRedEntries * kRedGroups, 0, ws>>>(red, u->wpart, u->grads);
-      UCHK(cudaGetLastError());
-      red.n = 0;
-      red_blocks = 0;
-    }
     UCHK(fork());
     rc = wgrad(c, u, c2, tpix(u->a1[l], cl, 0, h, w, cl, 9, 0, 9 * cl, 1, kTM),
                tpix(u->ge2[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws, red, red_blocks);
@@ -1424,7 +1416,7 @@ int backward_body(sc_ctx *c, sc_unet *u) {
       UCHK(conv3x3(u, u->ge1[l], cl, 0, cl, h, w, n, cp, c1.wd, c1.wtd, c1.wtd2, -1, pb, st, s));
     }
   }
-  // the remaining split-K partials (encoder level 0), on the weight-gradient stream
+  // every layer's split-K partials, reduced in one launch on the weight-gradient stream
   if (red.n > 0) {
     k_wgrad_reduce<<<(unsigned)red_blocks, kRedEntries * kRedGroups, 0, ws>>>(red, u->wpart, u->grads);
     UCHK(cudaGetLastError());
