@@ -326,20 +326,6 @@ __device__ __forceinline__ bool box_test_nf(const WRay &w, float nx, float fx, f
   return t0 <= t1;
 }
 
-// The same test with the far planes' safety factor folded into a second reciprocal direction
-// (invf = inv * 1.0000004, tmaxf = tmax * 1.0000004): one multiply per box less; its extra
-// rounding (half an ulp) stays well inside the factor's ~7 ulps.
-__device__ __forceinline__ bool box_test_nf2(const WRay &w, float3 invf, float nx, float fx, float ny, float fy, float nz,
-                                             float fz, float tmaxf, float &tnear) {
-  const float tnx = (nx - w.o.x) * w.inv.x, tfx = (fx - w.o.x) * invf.x;
-  const float tny = (ny - w.o.y) * w.inv.y, tfy = (fy - w.o.y) * invf.y;
-  const float tnz = (nz - w.o.z) * w.inv.z, tfz = (fz - w.o.z) * invf.z;
-  const float t0 = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, 0.0f));
-  const float t1 = fminf(fminf(tfx, tfy), fminf(tfz, tmaxf));
-  tnear = t0;
-  return t0 <= t1;
-}
-
 struct Hit {
   float t, b1, b2;
   int prim;     // leaf order, -1 = miss
@@ -471,14 +457,6 @@ __device__ __forceinline__ bool trav_step(const DevScene &S, const WRay &w, floa
 // The closest hit (with its tie-break on the input id) does not depend on the visit order.
 // ------------------------------------------------------------------------------------------
 constexpr int kEmptyRef = 0x7FFFFFFF;
-// SC_TRAV_FOLD: far-plane safety factor folded into a second reciprocal (box_test_nf2);
-// SC_TRAV_SORT: hit children visited nearest first with the others sorted (1) or in slot order (0)
-#ifndef SC_TRAV_FOLD
-#define SC_TRAV_FOLD 1
-#endif
-#ifndef SC_TRAV_SORT
-#define SC_TRAV_SORT 1
-#endif
 
 __device__ __forceinline__ float comp4(const float4 &v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
@@ -497,9 +475,6 @@ __device__ __forceinline__ void sort_pair(float &ka, int &ra, float &kb, int &rb
 __device__ __forceinline__ bool trav_step4(const DevScene &S, const WRay &w, float tmax, TravState &ts, int *stack,
                                            int budget, unsigned *status, TravCount &tc) {
   const float kInf = __int_as_float(0x7f800000);
-#if SC_TRAV_FOLD
-  const float3 invf = w.inv * 1.0000004f;
-#endif
   for (int it = 0; it < budget; ++it) {
     ++tc.nodes;
     if (++ts.visits > S.max_visits) {
@@ -523,20 +498,12 @@ __device__ __forceinline__ bool trav_step4(const DevScene &S, const WRay &w, flo
     const float4 nz = __ldg(nd + 4 + sz), fz = __ldg(nd + 5 - sz), rr = __ldg(nd + 6);
     int ref[4] = {__float_as_int(rr.x), __float_as_int(rr.y), __float_as_int(rr.z), __float_as_int(rr.w)};
     float key[4];
-#if SC_TRAV_FOLD
-    const float tmaxf = ts.h.t * 1.0000004f;
-#endif
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       float tn;
       // empty slots hold inverted boxes and never pass
-#if SC_TRAV_FOLD
-      const bool hb = box_test_nf2(w, invf, comp4(nx, i), comp4(fx, i), comp4(ny, i), comp4(fy, i), comp4(nz, i),
-                                   comp4(fz, i), tmaxf, tn);
-#else
       const bool hb = box_test_nf(w, comp4(nx, i), comp4(fx, i), comp4(ny, i), comp4(fy, i), comp4(nz, i), comp4(fz, i),
                                   ts.h.t, tn);
-#endif
       key[i] = hb ? tn : kInf;
     }
     // leaves (one triangle each) are tested right away, the hit ones of this lane in one compact
@@ -571,19 +538,12 @@ __device__ __forceinline__ bool trav_step4(const DevScene &S, const WRay &w, flo
         }
       }
     }
-#if SC_TRAV_SORT
     // internal children by entry distance (misses sort last)
     sort_pair(key[0], ref[0], key[1], ref[1]);
     sort_pair(key[2], ref[2], key[3], ref[3]);
     sort_pair(key[0], ref[0], key[2], ref[2]);
     sort_pair(key[1], ref[1], key[3], ref[3]);
     sort_pair(key[1], ref[1], key[2], ref[2]);
-#else
-    // the nearest internal child first, the others in slot order
-    sort_pair(key[0], ref[0], key[1], ref[1]);
-    sort_pair(key[0], ref[0], key[2], ref[2]);
-    sort_pair(key[0], ref[0], key[3], ref[3]);
-#endif
     const int cnt = (key[0] < kInf) + (key[1] < kInf) + (key[2] < kInf) + (key[3] < kInf);
     if (cnt == 0) {
       if (ts.sp == 0) {
@@ -600,15 +560,9 @@ __device__ __forceinline__ bool trav_step4(const DevScene &S, const WRay &w, flo
       ts.h.t = tmax;
       return true;
     }
-#if SC_TRAV_SORT
     if (cnt > 3) stack[ts.sp++] = ref[3];
     if (cnt > 2) stack[ts.sp++] = ref[2];
     if (cnt > 1) stack[ts.sp++] = ref[1];
-#else
-    if (key[3] < kInf) stack[ts.sp++] = ref[3];
-    if (key[2] < kInf) stack[ts.sp++] = ref[2];
-    if (key[1] < kInf) stack[ts.sp++] = ref[1];
-#endif
     ts.node = ref[0];
   }
   return false;
