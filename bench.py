@@ -348,15 +348,17 @@ def run_denoise(args):
     Both pipelines spend the same ratio of light paths to camera samples (``--den-ratio``, 16),
     light paths aimed into the sphere around the glass (guided emission): the denoised frame is
     4 camera spp + 4 x ratio light paths per pixel, the U-Net removing the camera estimate's noise
-    (trained --den-steps (48000) steps on 16 random 128^2 crops of 256 pairs: that estimate at 4 -> 1024 spp)
-    and the light-traced caustic buffer added back; the plain frame is N spp + N x ratio light
-    paths.
+    (trained --den-steps (48000) steps on 16 random 128^2 crops of 256 pairs: that estimate at 4 -> 1024 spp;
+    one network with L1 + SSIM and one with the squared error in linear radiance, two validation
+    scenes pick one) and the light-traced caustic buffer added back; the plain frame is N spp + N x
+    ratio light paths.
     MSEs are against a reference of two independent halves (2048 spp + 8192 light paths / px
     each), with the reference's own variance, MSE(half_a, half_b) / 4, subtracted."""
     import numpy as np
     import torch
 
     from paper_2107_11008_gb300 import denoiser as D
+    from paper_2107_11008_gb300 import native as N
     from paper_2107_11008_gb300 import renderer as R
     from paper_2107_11008_gb300 import scenes as S
     from paper_2107_11008_gb300 import training as T
@@ -371,6 +373,8 @@ def run_denoise(args):
     t0 = time.perf_counter()
     train = T.make_pairs(ctx, [S.denoise_scene(i, hw, hw) for i in range(n_train)], lo, T.RenderSpec(1024, 0),
                          seed=1, source="direct")
+    val = T.make_pairs(ctx, [S.denoise_scene(5_000 + i, hw, hw) for i in range(2)], lo, T.RenderSpec(1024, 0),
+                       seed=4, source="direct")
     test_scenes = [S.denoise_scene(10_000 + i, hw, hw) for i in range(n_test)]
     test = T.make_pairs(ctx, test_scenes, lo, T.RenderSpec(0, 0), seed=2, source="direct")
     gss = [R.GpuScene(ctx, s) for s in test_scenes]
@@ -388,14 +392,26 @@ def run_denoise(args):
     var_ref = T.mse(ref_a, ref_b) / 4.0
     gen_s = time.perf_counter() - t0
     trainer = D.UNet(ctx, 16, 128, 128)  # 128^2 random crops of the 256^2 pairs, 16 per step
-    trainer.set_params(D.he_init(0).to(dev))
     t0 = time.perf_counter()
-    T.train(trainer, train, steps=args.den_steps, batch=16, crop=128, lr=1.5e-3, lr_final=5e-5, seed=0)
+    # one network per loss; validation scenes (not test scenes) pick the one used
+    candidates = {}
+    for name, loss_kind, lr, init in (("l1_ssim", N.SC_UNET_LOSS_L1_SSIM, 1.5e-3, 0),
+                                      ("l2_linear", N.SC_UNET_LOSS_L2_LINEAR, 1e-3, 1)):
+        trainer.set_params(D.he_init(init).to(dev))
+        trainer.set_loss(loss_kind)
+        T.train(trainer, train, steps=args.den_steps, batch=16, crop=128, lr=lr, lr_final=5e-5, seed=init)
+        candidates[name] = trainer.get_params()
     torch.cuda.synchronize(dev)
     train_s = time.perf_counter() - t0
     ctx.sync_status()
     net = D.UNet(ctx, 8, hw, hw)
-    net.set_params(trainer.get_params())
+    val_mse, test_mse = {}, {}
+    for name, prm in candidates.items():
+        net.set_params(prm)
+        val_mse[name] = T.mse(T.denoise(net, val.x, None), torch.expm1(val.target))
+        test_mse[name] = T.mse(T.denoise(net, test.x, test.add()), ref) - var_ref
+    chosen = min(val_mse, key=val_mse.get)
+    net.set_params(candidates[chosen])
     den = T.denoise(net, test.x, test.add())
     m_den = T.mse(den, ref) - var_ref
     m_in = T.mse(test.rgb_lo, ref) - var_ref
@@ -481,12 +497,14 @@ def run_denoise(args):
                 "warmup": max(3, args.warmup), "ms_per_step": den_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic (scenes.denoise_scene)",
                 "config": {"workload": "denoise: 256^2 config-1-type scenes; U-Net on the camera estimate trained "
-                                       f"{args.den_steps} steps x 16 crops of 128^2 from 256 pairs (4 -> 1024 spp), guided "
+                                       f"{args.den_steps} steps x 16 crops of 128^2 from 256 pairs (4 -> 1024 spp; L1 + "
+                                       "SSIM or linear squared error, picked on 2 validation scenes), guided "
                                        "light-traced caustics added back; 8 held-out scenes; reference 2 x (2048 spp "
                                        "+ 8192 guided light paths/px)",
                            "input": f"{lo.spp} camera spp + {lo.lights_per_pixel} light paths/px",
                            "light_paths_per_camera_sample": ratio},
-                "mse": {"denoised": m_den, "input": m_in, "reference_variance": var_ref, "plain_sweep": sweep},
+                "mse": {"denoised": m_den, "input": m_in, "reference_variance": var_ref, "plain_sweep": sweep,
+                        "by_loss": {"validation": val_mse, "test": test_mse, "chosen": chosen}},
                 "matched_spp": spp_match, "plain_frame": {"spp": spp_int, "light_paths_per_px": spp_int * ratio,
                                                           "ms": plain_ms, "fps": world * 1e3 / plain_ms},
                 "fps_ratio_denoised_over_plain": plain_ms / den_ms, "unet_forward_ms": net_ms,

@@ -6,6 +6,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from paper_2107_11008_gb300 import denoiser as D  # noqa: E402
+from paper_2107_11008_gb300 import native as N  # noqa: E402
 from paper_2107_11008_gb300 import renderer as R  # noqa: E402
 from paper_2107_11008_gb300 import scenes as S  # noqa: E402
 from paper_2107_11008_gb300 import training as T  # noqa: E402
@@ -72,7 +73,8 @@ def test_trained_denoiser_beats_the_noisy_input(ctx, source, lights):
 
 
 
-def test_denoised_frame_beats_the_plain_tracer_at_several_times_its_samples(ctx):
+@pytest.mark.parametrize("loss", ["l1_ssim", "l2_linear"])
+def test_denoised_frame_beats_the_plain_tracer_at_several_times_its_samples(ctx, loss):
     """The matched-MSE ordering of the denoising pipeline on held-out scenes: 4 camera spp + the
     light-traced caustics, the camera estimate denoised, against the plain tracer spending the same
     light paths per camera sample at 4, 8, 12, 16 and 32 spp; MSEs against a two-half reference
@@ -98,7 +100,9 @@ def test_denoised_frame_beats_the_plain_tracer_at_several_times_its_samples(ctx)
     var_ref = T.mse(ref_ab[0], ref_ab[1]) / 4.0
     net = D.UNet(ctx, 16, 64, 64)
     net.set_params(D.he_init(0).cuda())
-    T.train(net, train, steps=4000, batch=16, crop=64, lr=1.5e-3, lr_final=5e-5, seed=0)
+    if loss == "l2_linear":
+        net.set_loss(N.SC_UNET_LOSS_L2_LINEAR)
+    T.train(net, train, steps=4000, batch=16, crop=64, lr=1.5e-3 if loss == "l1_ssim" else 1e-3, lr_final=5e-5, seed=0)
     full = D.UNet(ctx, 4, hw, hw)
     full.set_params(net.get_params())
     m_den = T.mse(T.denoise(full, test.x, test.add()), ref) - var_ref
@@ -110,7 +114,7 @@ def test_denoised_frame_beats_the_plain_tracer_at_several_times_its_samples(ctx)
             out[i].copy_(f["rgb"])
         sweep[spp] = T.mse(out, ref) - var_ref
     ctx.sync_status()
-    print(f"held-out MSE: denoised {m_den:.4g}; plain {', '.join(f'{s} spp {m:.4g}' for s, m in sweep.items())}; "
+    print(f"[{loss}] held-out MSE: denoised {m_den:.4g}; plain {', '.join(f'{s} spp {m:.4g}' for s, m in sweep.items())}; "
           f"reference variance {var_ref:.3g}")
     assert var_ref < 0.1 * sweep[32]  # the reference resolves the errors it measures
     assert sweep[4] > sweep[8] > sweep[16] > sweep[32]  # the plain tracer converges
