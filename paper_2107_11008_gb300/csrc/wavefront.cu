@@ -48,6 +48,14 @@ enum : uint32_t {
 };
 // counters of a wave (device words): queue sizes and the persistent kernels' ticket
 enum { C_EXT0 = 0, C_EXT1 = 1, C_DIEL = 2, C_DIFF = 3, C_SHADOW = 4, C_TICKET_EXT = 5, C_TICKET_SHADOW = 6, C_WORDS = 8 };
+enum { BM_DIEL = 0, BM_DIFF = 1, BM_SHADOW = 2, BM_EXT = 3 };
+// Queues in path-slot order (1): producers set the path's bit and a compaction emits the set bits
+// in order, so that the kernels reading a queue touch path state in runs of neighbouring slots
+// and a warp's rays come from neighbouring pixels; (0) appended in the order they are produced.
+#ifndef SC_WF_ORDERED
+#define SC_WF_ORDERED 1
+#endif
+constexpr int kBmWordsPerBlock = 1024;  // bitmap words per compaction block (256 threads x 4)
 
 struct Wave {
   float4 *o;      // ray origin; w: the path's bin draw u
@@ -62,6 +70,10 @@ struct Wave {
   float4 *hit;    // t, b1, b2, leaf index (int bits)
   uint32_t *hid;  // input triangle id of the hit
   uint32_t *q_ext[2], *q_diel, *q_diff, *q_shadow;
+  // ordered queues: one bit per path slot for each queue being filled, emitted in slot order
+  uint32_t *bm[4];  // BM_DIEL, BM_DIFF, BM_SHADOW, BM_EXT: contiguous, bm_words apart
+  uint32_t *bmblk;  // per-block bit counts of the compaction (two bitmaps at a time)
+  int bm_words;     // words of each bitmap (sized for the largest wave)
   unsigned *cnt;
   int t0;         // first pixel of the wave in tile order
   int wave_px;    // tile-order pixel slots in the wave
@@ -131,6 +143,18 @@ __device__ __forceinline__ void warp_push(uint32_t *q, unsigned *count, bool pre
   if (lane == leader) base = atomicAdd(count, (unsigned)__popc(mask));
   base = __shfl_sync(0xFFFFFFFFu, base, leader);
   if (pred) q[base + __popc(mask & ((1u << lane) - 1u))] = v;
+}
+
+// Adds path p to a queue for every lane with pred set (the whole warp calls it together): its
+// bit in the queue's bitmap (ordered queues), else warp_push.
+__device__ __forceinline__ void enqueue(const Wave &w, int bm, uint32_t *q, unsigned *count, bool pred, int p) {
+#if SC_WF_ORDERED
+  (void)q;
+  (void)count;
+  if (pred) atomicOr(w.bm[bm] + (p >> 5), 1u << (p & 31));
+#else
+  warp_push(q, count, pred, (uint32_t)p);
+#endif
 }
 
 __device__ __forceinline__ void end_path(const Wave &w, int p, float3 L) {
@@ -263,8 +287,8 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_extend(WfArgs a, Wave w, int cur) {
         end_path(w, p, f3(L4.x, L4.y, L4.z) + Ladd);
       }
     }
-    warp_push(w.q_diel, w.cnt + C_DIEL, to_diel, (uint32_t)p);
-    warp_push(w.q_diff, w.cnt + C_DIFF, to_diff, (uint32_t)p);
+    enqueue(w, BM_DIEL, w.q_diel, w.cnt + C_DIEL, to_diel, p);
+    enqueue(w, BM_DIFF, w.q_diff, w.cnt + C_DIFF, to_diff, p);
   }
   flush_counts(a, tc);
 }
@@ -357,7 +381,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_dielectric(WfArgs a, Wave w, in
       w.beta[p] = make_float4(beta.x, beta.y, beta.z, 0.0f);
       w.m0[p] = m0;
     }
-    warp_push(w.q_ext[next], w.cnt + (next ? C_EXT1 : C_EXT0), cont, (uint32_t)p);
+    enqueue(w, BM_EXT, w.q_ext[next], w.cnt + (next ? C_EXT1 : C_EXT0), cont, p);
   }
 }
 
@@ -464,8 +488,8 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_diffuse(WfArgs a, Wave w, int n
       w.m0[p] = m0;
       w.m1[p] = m1;
     }
-    warp_push(w.q_shadow, w.cnt + C_SHADOW, shadow, (uint32_t)p);
-    warp_push(w.q_ext[next], w.cnt + (next ? C_EXT1 : C_EXT0), cont, (uint32_t)p);
+    enqueue(w, BM_SHADOW, w.q_shadow, w.cnt + C_SHADOW, shadow, p);
+    enqueue(w, BM_EXT, w.q_ext[next], w.cnt + (next ? C_EXT1 : C_EXT0), cont, p);
   }
 }
 
@@ -534,12 +558,103 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_shadow(WfArgs a, Wave w, int next) {
         end_path(w, p, L);
       }
     }
-    warp_push(w.q_ext[next], w.cnt + (next ? C_EXT1 : C_EXT0), cont, (uint32_t)p);
+    enqueue(w, BM_EXT, w.q_ext[next], w.cnt + (next ? C_EXT1 : C_EXT0), cont, p);
   }
   flush_counts(a, tc);
 }
 
 // Between bounces: the next extend queue becomes current, the others are emptied.
+// ---- ordered queues: compaction of a bitmap into the queue, in slot order ---------------------
+// blockIdx.y picks one of up to two bitmaps compacted together (which[y]); a block covers
+// kBmWordsPerBlock words, thread t words 4t .. 4t + 3 of them.
+struct Compact {
+  const uint32_t *bm[2];  // bitmap (cleared by the emit kernel)
+  uint32_t *q[2];         // queue written in slot order
+  unsigned *count[2];     // queue size
+  int nwords;             // bitmap words of the wave
+  int nblk;               // blocks per bitmap
+};
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *ws, uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t s = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0u;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < (int)(blockDim.x >> 5)) ws[lane] = s;
+  }
+  __syncthreads();
+  const uint32_t before = warp == 0 ? 0u : ws[warp - 1];
+  *total = ws[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(256) k_wf_compact_count(Compact c, uint32_t *blk) {
+  __shared__ uint32_t ws[32];
+  const int y = blockIdx.y;
+  const int w0 = blockIdx.x * kBmWordsPerBlock + 4 * threadIdx.x;
+  uint32_t n = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (w0 + k < c.nwords) n += (uint32_t)__popc(c.bm[y][w0 + k]);
+  uint32_t total;
+  block_excl_scan(n, ws, &total);
+  if (threadIdx.x == 0) blk[y * c.nblk + blockIdx.x] = total;
+}
+
+// one block of 1024 per bitmap: exclusive prefix of the block counts, the queue size
+__global__ void __launch_bounds__(1024) k_wf_compact_scan(Compact c, uint32_t *blk) {
+  __shared__ uint32_t ws[32];
+  uint32_t *b = blk + blockIdx.x * c.nblk;
+  uint32_t carry = 0;
+  for (int base = 0; base < c.nblk; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const uint32_t v = i < c.nblk ? b[i] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_excl_scan(v, ws, &total);
+    if (i < c.nblk) b[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) *c.count[blockIdx.x] = carry;
+}
+
+__global__ void __launch_bounds__(256) k_wf_compact_emit(Compact c, const uint32_t *blk) {
+  __shared__ uint32_t ws[32];
+  const int y = blockIdx.y;
+  uint32_t *bm = const_cast<uint32_t *>(c.bm[y]);
+  const int w0 = blockIdx.x * kBmWordsPerBlock + 4 * threadIdx.x;
+  uint32_t wd[4];
+  uint32_t n = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    wd[k] = w0 + k < c.nwords ? bm[w0 + k] : 0u;
+    n += (uint32_t)__popc(wd[k]);
+  }
+  uint32_t total;
+  uint32_t pos = block_excl_scan(n, ws, &total) + blk[y * c.nblk + blockIdx.x];
+  uint32_t *q = c.q[y];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    uint32_t v = wd[k];
+    while (v) {
+      const int bit = __ffs(v) - 1;
+      v &= v - 1u;
+      q[pos++] = (uint32_t)((w0 + k) * 32 + bit);
+    }
+    if (wd[k] && w0 + k < c.nwords) bm[w0 + k] = 0u;  // ready for the next round
+  }
+}
+
 __global__ void k_wf_rotate(Wave w, int cur) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     w.cnt[cur ? C_EXT1 : C_EXT0] = 0u;
@@ -635,7 +750,13 @@ bool carve_wave(void *workspace, int64_t max_paths, Wave &w) {
   w.m0 = reinterpret_cast<uint4 *>(take(16 * n));
   w.m1 = reinterpret_cast<uint4 *>(take(16 * n));
   w.hit = reinterpret_cast<float4 *>(take(16 * n));
-  take(16 * n);  // reserved (keeps the layout of wavefront_workspace_bytes)
+  {  // the reserved 16 n bytes: four bitmaps of n bits and the compaction's block counts
+    char *r = take(16 * n);
+    const size_t words = (n + 31) / 32;
+    for (int k = 0; k < 4; ++k) w.bm[k] = reinterpret_cast<uint32_t *>(r) + k * words;
+    w.bm_words = (int)words;
+    w.bmblk = reinterpret_cast<uint32_t *>(r) + 4 * words;  // 2 x blocks (n / 32768 + 1) words
+  }
   w.hid = reinterpret_cast<uint32_t *>(take(4 * n));
   w.q_ext[0] = reinterpret_cast<uint32_t *>(take(4 * n));
   w.q_ext[1] = reinterpret_cast<uint32_t *>(take(4 * n));
@@ -644,6 +765,25 @@ bool carve_wave(void *workspace, int64_t max_paths, Wave &w) {
   w.q_shadow = reinterpret_cast<uint32_t *>(take(4 * n));
   w.cnt = reinterpret_cast<unsigned *>(take(4 * C_WORDS));
   return off <= wavefront_workspace_bytes(max_paths);
+}
+
+// Emits bitmaps into their queues (one or two at a time), clearing the bitmaps.
+cudaError_t compact(const Wave &w, int nq, const int *which, uint32_t *const *queues, const int *counts,
+                    cudaStream_t s) {
+  Compact c;
+  c.nwords = (w.n + 31) / 32;
+  c.nblk = (c.nwords + kBmWordsPerBlock - 1) / kBmWordsPerBlock;
+  for (int k = 0; k < 2; ++k) {
+    const int j = k < nq ? k : 0;
+    c.bm[k] = w.bm[which[j]];
+    c.q[k] = queues[j];
+    c.count[k] = w.cnt + counts[j];
+  }
+  const dim3 g((unsigned)c.nblk, (unsigned)nq);
+  k_wf_compact_count<<<g, 256, 0, s>>>(c, w.bmblk);
+  k_wf_compact_scan<<<nq, 1024, 0, s>>>(c, w.bmblk);
+  k_wf_compact_emit<<<g, 256, 0, s>>>(c, w.bmblk);
+  return cudaGetLastError();
 }
 
 // Waves of whole pixel slots over [0, total_slots): each wave's kernels, bounce by bounce.
@@ -663,13 +803,38 @@ cudaError_t run_waves(const WfArgs &a, Wave w, int64_t total_slots, int64_t wave
     w.n = w.wave_px * a.P.spp;
     e = cudaMemsetAsync(w.cnt, 0, 4 * C_WORDS, s);
     if (e != cudaSuccess) return e;
+#if SC_WF_ORDERED
+    e = cudaMemsetAsync(w.bm[0], 0, 4 * sizeof(uint32_t) * (size_t)w.bm_words, s);  // the four bitmaps
+    if (e != cudaSuccess) return e;
+#endif
     k_wf_generate<B><<<std::max(1, std::min(wide, (w.n + kWfBlock - 1) / kWfBlock)), kWfBlock, 0, s>>>(a, w);
     for (int b = 0; b < a.P.max_depth; ++b) {
       const int cur = b & 1, next = cur ^ 1;
       k_wf_extend<B><<<persistent, kWfBlock, 0, s>>>(a, w, cur);
+#if SC_WF_ORDERED
+      {
+        const int which[2] = {BM_DIEL, BM_DIFF}, counts[2] = {C_DIEL, C_DIFF};
+        uint32_t *const queues[2] = {w.q_diel, w.q_diff};
+        if ((e = compact(w, 2, which, queues, counts, s)) != cudaSuccess) return e;
+      }
+#endif
       k_wf_dielectric<B><<<wide, kWfBlock, 0, s>>>(a, w, next);
       k_wf_diffuse<B><<<wide, kWfBlock, 0, s>>>(a, w, next);
+#if SC_WF_ORDERED
+      {
+        const int which[1] = {BM_SHADOW}, counts[1] = {C_SHADOW};
+        uint32_t *const queues[1] = {w.q_shadow};
+        if ((e = compact(w, 1, which, queues, counts, s)) != cudaSuccess) return e;
+      }
+#endif
       k_wf_shadow<B><<<persistent, kWfBlock, 0, s>>>(a, w, next);
+#if SC_WF_ORDERED
+      {
+        const int which[1] = {BM_EXT}, counts[1] = {next ? C_EXT1 : C_EXT0};
+        uint32_t *const queues[1] = {w.q_ext[next]};
+        if ((e = compact(w, 1, which, queues, counts, s)) != cudaSuccess) return e;
+      }
+#endif
       k_wf_rotate<<<1, 32, 0, s>>>(w, cur);
     }
     k_wf_reduce<B><<<(w.wave_px + kWfBlock - 1) / kWfBlock, kWfBlock, 0, s>>>(a, w);
