@@ -53,7 +53,8 @@ def launches_per_step_base(n_tris):
 def camera_launches(engine, width, height, spp, depth):
     """Kernel launches of one sc_trace_camera call: one persistent kernel, or per wave of whole
     pixels (at most 2^25 paths) generate + depth x (extend, dielectric, diffuse, shadow, rotate, and
-    three compactions of 3 launches each that emit the ordered queues) + reduce."""
+    for waves of at least 2^18 paths three compactions of 3 launches each that emit the ordered
+    queues) + reduce."""
     if engine == "persistent":
         return 1
     tiles = ((width + 7) // 8) * ((height + 3) // 4)
@@ -61,7 +62,8 @@ def camera_launches(engine, width, height, spp, depth):
     max_paths = max(one_tile, min(tiles * one_tile, 1 << 25))
     wave_tiles = max(1, max_paths // one_tile)
     waves = -(-tiles // wave_tiles)
-    return waves * (2 + 14 * depth)
+    per_bounce = 14 if min(wave_tiles, tiles) * one_tile >= 1 << 18 else 5
+    return waves * (2 + per_bounce * depth)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size camera launch, from
 # one ncu capture of this kernel version:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
@@ -70,8 +72,8 @@ def camera_launches(engine, width, height, spp, depth):
 # wavefront: all kernels of one 256-spp camera phase, scaled by the path count (x16) from one ncu capture
 # of the 16-spp frame (the traffic is path state and queues, proportional to the paths):
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
-#       -k regex:k_wf_ -s 248 -c 62 python bench.py --steps 1 --warmup 3 --spp 16 --no-cpu-baseline --no-sub
-CAMERA_DRAM_BYTES = {"persistent": 24.5e6, "wavefront": None}
+#       -k regex:k_wf_ -s 680 -c 170 python bench.py --steps 1 --warmup 3 --spp 16 --no-cpu-baseline --no-sub
+CAMERA_DRAM_BYTES = {"persistent": 24.5e6, "wavefront": 16 * 8.5297e9}
 
 
 def parse():

@@ -49,11 +49,14 @@ enum : uint32_t {
 // counters of a wave (device words): queue sizes and the persistent kernels' ticket
 enum { C_EXT0 = 0, C_EXT1 = 1, C_DIEL = 2, C_DIFF = 3, C_SHADOW = 4, C_TICKET_EXT = 5, C_TICKET_SHADOW = 6, C_WORDS = 8 };
 enum { BM_DIEL = 0, BM_DIFF = 1, BM_SHADOW = 2, BM_EXT = 3 };
-// Queues in path-slot order (1): producers set the path's bit and a compaction emits the set bits
-// in order, so that the kernels reading a queue touch path state in runs of neighbouring slots
-// and a warp's rays come from neighbouring pixels; (0) appended in the order they are produced.
-#ifndef SC_WF_ORDERED
-#define SC_WF_ORDERED 1
+// Queues in path-slot order: producers set the path's bit and a compaction emits the set bits in
+// order, so that the kernels reading a queue touch path state in runs of neighbouring slots and a
+// warp's rays come from neighbouring pixels (512^2 glass frame: camera phase 115.2 -> 99.7 ms).
+// Used for waves of at least SC_WF_ORDERED_MIN paths: on small waves the compactions' nine
+// launches per bounce cost more than they save (64^2 ball frame: 1.10 -> 1.39 ms), and the queues
+// are appended in the order paths are produced.  0 = always appended.
+#ifndef SC_WF_ORDERED_MIN
+#define SC_WF_ORDERED_MIN (1 << 18)
 #endif
 constexpr int kBmWordsPerBlock = 1024;  // bitmap words per compaction block (256 threads x 4)
 
@@ -74,6 +77,7 @@ struct Wave {
   uint32_t *bm[4];  // BM_DIEL, BM_DIFF, BM_SHADOW, BM_EXT: contiguous, bm_words apart
   uint32_t *bmblk;  // per-block bit counts of the compaction (two bitmaps at a time)
   int bm_words;     // words of each bitmap (sized for the largest wave)
+  int ordered;      // this wave's queues are ordered (bitmaps + compaction), else appended
   unsigned *cnt;
   int t0;         // first pixel of the wave in tile order
   int wave_px;    // tile-order pixel slots in the wave
@@ -148,13 +152,11 @@ __device__ __forceinline__ void warp_push(uint32_t *q, unsigned *count, bool pre
 // Adds path p to a queue for every lane with pred set (the whole warp calls it together): its
 // bit in the queue's bitmap (ordered queues), else warp_push.
 __device__ __forceinline__ void enqueue(const Wave &w, int bm, uint32_t *q, unsigned *count, bool pred, int p) {
-#if SC_WF_ORDERED
-  (void)q;
-  (void)count;
-  if (pred) atomicOr(w.bm[bm] + (p >> 5), 1u << (p & 31));
-#else
-  warp_push(q, count, pred, (uint32_t)p);
-#endif
+  if (w.ordered) {  // uniform over the launch
+    if (pred) atomicOr(w.bm[bm] + (p >> 5), 1u << (p & 31));
+  } else {
+    warp_push(q, count, pred, (uint32_t)p);
+  }
 }
 
 __device__ __forceinline__ void end_path(const Wave &w, int p, float3 L) {
@@ -801,40 +803,35 @@ cudaError_t run_waves(const WfArgs &a, Wave w, int64_t total_slots, int64_t wave
     w.t0 = (int)t0;
     w.wave_px = (int)std::min<int64_t>(wave_px, total_slots - t0);
     w.n = w.wave_px * a.P.spp;
+    w.ordered = SC_WF_ORDERED_MIN > 0 && w.n >= SC_WF_ORDERED_MIN;
     e = cudaMemsetAsync(w.cnt, 0, 4 * C_WORDS, s);
     if (e != cudaSuccess) return e;
-#if SC_WF_ORDERED
-    e = cudaMemsetAsync(w.bm[0], 0, 4 * sizeof(uint32_t) * (size_t)w.bm_words, s);  // the four bitmaps
-    if (e != cudaSuccess) return e;
-#endif
+    if (w.ordered) {
+      e = cudaMemsetAsync(w.bm[0], 0, 4 * sizeof(uint32_t) * (size_t)w.bm_words, s);  // the four bitmaps
+      if (e != cudaSuccess) return e;
+    }
     k_wf_generate<B><<<std::max(1, std::min(wide, (w.n + kWfBlock - 1) / kWfBlock)), kWfBlock, 0, s>>>(a, w);
     for (int b = 0; b < a.P.max_depth; ++b) {
       const int cur = b & 1, next = cur ^ 1;
       k_wf_extend<B><<<persistent, kWfBlock, 0, s>>>(a, w, cur);
-#if SC_WF_ORDERED
-      {
+      if (w.ordered) {
         const int which[2] = {BM_DIEL, BM_DIFF}, counts[2] = {C_DIEL, C_DIFF};
         uint32_t *const queues[2] = {w.q_diel, w.q_diff};
         if ((e = compact(w, 2, which, queues, counts, s)) != cudaSuccess) return e;
       }
-#endif
       k_wf_dielectric<B><<<wide, kWfBlock, 0, s>>>(a, w, next);
       k_wf_diffuse<B><<<wide, kWfBlock, 0, s>>>(a, w, next);
-#if SC_WF_ORDERED
-      {
+      if (w.ordered) {
         const int which[1] = {BM_SHADOW}, counts[1] = {C_SHADOW};
         uint32_t *const queues[1] = {w.q_shadow};
         if ((e = compact(w, 1, which, queues, counts, s)) != cudaSuccess) return e;
       }
-#endif
       k_wf_shadow<B><<<persistent, kWfBlock, 0, s>>>(a, w, next);
-#if SC_WF_ORDERED
-      {
+      if (w.ordered) {
         const int which[1] = {BM_EXT}, counts[1] = {next ? C_EXT1 : C_EXT0};
         uint32_t *const queues[1] = {w.q_ext[next]};
         if ((e = compact(w, 1, which, queues, counts, s)) != cudaSuccess) return e;
       }
-#endif
       k_wf_rotate<<<1, 32, 0, s>>>(w, cur);
     }
     k_wf_reduce<B><<<(w.wave_px + kWfBlock - 1) / kWfBlock, kWfBlock, 0, s>>>(a, w);
