@@ -48,16 +48,7 @@ enum : uint32_t {
 };
 // counters of a wave (device words): queue sizes and the persistent kernels' ticket
 enum { C_EXT0 = 0, C_EXT1 = 1, C_DIEL = 2, C_DIFF = 3, C_SHADOW = 4, C_TICKET_EXT = 5, C_TICKET_SHADOW = 6, C_WORDS = 8 };
-enum { BM_DIEL = 0, BM_DIFF = 1, BM_SHADOW = 2, BM_EXT = 3, BM_COUNT = 11 };  // BM_EXT + direction octant
-// The next extend queue grouped by the ray direction's octant (eight bitmaps emitted one after
-// another, each in slot order): a warp's rays share their signs as well as their pixels' region.
-#ifndef SC_WF_OCTANTS
-#define SC_WF_OCTANTS 1
-#endif
-constexpr uint32_t kOctShift = 8;  // the octant of the next ray in m1.z bits 8..10 (shadow -> extend)
-__device__ __forceinline__ int octant_of(float3 d) {
-  return SC_WF_OCTANTS ? (int)(d.x < 0.0f) | ((int)(d.y < 0.0f) << 1) | ((int)(d.z < 0.0f) << 2) : 0;
-}
+enum { BM_DIEL = 0, BM_DIFF = 1, BM_SHADOW = 2, BM_EXT = 3 };
 // Queues in path-slot order: producers set the path's bit and a compaction emits the set bits in
 // order, so that the kernels reading a queue touch path state in runs of neighbouring slots and a
 // warp's rays come from neighbouring pixels (512^2 glass frame: camera phase 115.2 -> 99.7 ms).
@@ -83,7 +74,7 @@ struct Wave {
   uint32_t *hid;  // input triangle id of the hit
   uint32_t *q_ext[2], *q_diel, *q_diff, *q_shadow;
   // ordered queues: one bit per path slot for each queue being filled, emitted in slot order
-  uint32_t *bm[BM_COUNT];  // BM_DIEL, BM_DIFF, BM_SHADOW, BM_EXT + octant: contiguous, bm_words apart
+  uint32_t *bm[4];  // BM_DIEL, BM_DIFF, BM_SHADOW, BM_EXT: contiguous, bm_words apart
   uint32_t *bmblk;  // per-block bit counts of the compaction (two bitmaps at a time)
   int bm_words;     // words of each bitmap (sized for the largest wave)
   int ordered;      // this wave's queues are ordered (bitmaps + compaction), else appended
@@ -161,8 +152,8 @@ __device__ __forceinline__ void warp_push(uint32_t *q, unsigned *count, bool pre
 // Adds path p to a queue for every lane with pred set (the whole warp calls it together): its
 // bit in the queue's bitmap (ordered queues), else warp_push.
 __device__ __forceinline__ void enqueue(const Wave &w, int bm, uint32_t *q, unsigned *count, bool pred, int p) {
-  if (w.ordered) {  // uniform over the launch; the bitmaps are contiguous, bm_words apart
-    if (pred) atomicOr(w.bm[0] + (size_t)bm * w.bm_words + (p >> 5), 1u << (p & 31));
+  if (w.ordered) {  // uniform over the launch
+    if (pred) atomicOr(w.bm[bm] + (p >> 5), 1u << (p & 31));
   } else {
     warp_push(q, count, pred, (uint32_t)p);
   }
@@ -336,7 +327,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_dielectric(WfArgs a, Wave w, in
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < (int)n; base += stride) {
     const int i = base + (threadIdx.x & 31);
     bool cont = false;
-    int p = 0, oct = 0;
+    int p = 0;
     if (i < (int)n) {
       p = (int)w.q_diel[i];
       uint4 m0 = w.m0[p], m1 = w.m1[p];
@@ -387,13 +378,12 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_dielectric(WfArgs a, Wave w, in
           end_path(w, p, f3(L4.x, L4.y, L4.z));
         } else {
           cont = true;
-          oct = octant_of(nd);
         }
       }
       w.beta[p] = make_float4(beta.x, beta.y, beta.z, 0.0f);
       w.m0[p] = m0;
     }
-    enqueue(w, BM_EXT + oct, w.q_ext[next], w.cnt + (next ? C_EXT1 : C_EXT0), cont, p);
+    enqueue(w, BM_EXT, w.q_ext[next], w.cnt + (next ? C_EXT1 : C_EXT0), cont, p);
   }
 }
 
@@ -405,7 +395,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_diffuse(WfArgs a, Wave w, int n
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < (int)n; base += stride) {
     const int i = base + (threadIdx.x & 31);
     bool cont = false, shadow = false;
-    int p = 0, oct = 0;
+    int p = 0;
     if (i < (int)n) {
       p = (int)w.q_diff[i];
       uint4 m0 = w.m0[p], m1 = w.m1[p];
@@ -467,7 +457,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_diffuse(WfArgs a, Wave w, int n
       uint32_t fl = m1.z;
       if (k == 0u) fl |= W_DIFFUSE_FIRST;
       m1.y += 1u;  // diffuse vertices
-      fl &= ~(W_SPEC_ONLY | W_LAST_SPECULAR | W_FIXUP | W_HAS_NEXT | (7u << kOctShift));
+      fl &= ~(W_SPEC_ONLY | W_LAST_SPECULAR | W_FIXUP | W_HAS_NEXT);
       if ((int)k < a.P.max_depth - 1) {
         float3 nd = cosine_dir(f.nsf, u01(xs.y), u01(xs.z));
         if (!(dot(nd, f.ngf) > 0.0f)) {
@@ -480,8 +470,6 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_diffuse(WfArgs a, Wave w, int n
         w.d[p] = make_float4(nd.x, nd.y, nd.z, d4.w);
         w.beta[p] = make_float4(beta.x, beta.y, beta.z, 0.0f);
         fl |= W_HAS_NEXT;
-        oct = octant_of(nd);
-        fl |= (uint32_t)oct << kOctShift;  // for the shadow kernel, which queues the next ray
       }
       m1.x = k + 1u;
       m1.z = fl;
@@ -503,7 +491,7 @@ __global__ void __launch_bounds__(kWfBlock) k_wf_diffuse(WfArgs a, Wave w, int n
       w.m1[p] = m1;
     }
     enqueue(w, BM_SHADOW, w.q_shadow, w.cnt + C_SHADOW, shadow, p);
-    enqueue(w, BM_EXT + oct, w.q_ext[next], w.cnt + (next ? C_EXT1 : C_EXT0), cont, p);
+    enqueue(w, BM_EXT, w.q_ext[next], w.cnt + (next ? C_EXT1 : C_EXT0), cont, p);
   }
 }
 
@@ -551,7 +539,6 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_shadow(WfArgs a, Wave w, int next) {
       if (done) tracing = false;
     }
     bool cont = false;
-    int oct = 0;
     if (done) {
       ++tc.queries;
       const bool lit = ts.h.prim < 0;
@@ -569,12 +556,11 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_shadow(WfArgs a, Wave w, int next) {
       if (fl & W_HAS_NEXT) {
         w.L[p] = make_float4(L.x, L.y, L.z, 0.0f);
         cont = true;
-        oct = (int)((fl >> kOctShift) & 7u);
       } else {
         end_path(w, p, L);
       }
     }
-    enqueue(w, BM_EXT + oct, w.q_ext[next], w.cnt + (next ? C_EXT1 : C_EXT0), cont, p);
+    enqueue(w, BM_EXT, w.q_ext[next], w.cnt + (next ? C_EXT1 : C_EXT0), cont, p);
   }
   flush_counts(a, tc);
 }
@@ -587,8 +573,7 @@ struct Compact {
   const uint32_t *bm[2];  // bitmap (cleared by the emit kernel)
   uint32_t *q[2];         // queue written in slot order
   unsigned *count[2];     // queue size
-  int nwords;             // bitmap words compacted (the eight octant bitmaps: one run of 8 x period)
-  int period;             // words per bitmap: path index = (word % period) * 32 + bit
+  int nwords;             // bitmap words of the wave
   int nblk;               // blocks per bitmap
 };
 
@@ -666,7 +651,7 @@ __global__ void __launch_bounds__(256) k_wf_compact_emit(Compact c, const uint32
     while (v) {
       const int bit = __ffs(v) - 1;
       v &= v - 1u;
-      q[pos++] = (uint32_t)(((w0 + k) % c.period) * 32 + bit);
+      q[pos++] = (uint32_t)((w0 + k) * 32 + bit);
     }
     if (wd[k] && w0 + k < c.nwords) bm[w0 + k] = 0u;  // ready for the next round
   }
@@ -767,12 +752,12 @@ bool carve_wave(void *workspace, int64_t max_paths, Wave &w) {
   w.m0 = reinterpret_cast<uint4 *>(take(16 * n));
   w.m1 = reinterpret_cast<uint4 *>(take(16 * n));
   w.hit = reinterpret_cast<float4 *>(take(16 * n));
-  {  // the reserved 16 n bytes: eleven bitmaps of n bits and the compaction's block counts
+  {  // the reserved 16 n bytes: four bitmaps of n bits and the compaction's block counts
     char *r = take(16 * n);
     const size_t words = (n + 31) / 32;
-    for (int k = 0; k < BM_COUNT; ++k) w.bm[k] = reinterpret_cast<uint32_t *>(r) + k * words;
+    for (int k = 0; k < 4; ++k) w.bm[k] = reinterpret_cast<uint32_t *>(r) + k * words;
     w.bm_words = (int)words;
-    w.bmblk = reinterpret_cast<uint32_t *>(r) + BM_COUNT * words;  // 2 x blocks (8 n / 32768 + 1) words
+    w.bmblk = reinterpret_cast<uint32_t *>(r) + 4 * words;  // 2 x blocks (n / 32768 + 1) words
   }
   w.hid = reinterpret_cast<uint32_t *>(take(4 * n));
   w.q_ext[0] = reinterpret_cast<uint32_t *>(take(4 * n));
@@ -786,10 +771,9 @@ bool carve_wave(void *workspace, int64_t max_paths, Wave &w) {
 
 // Emits bitmaps into their queues (one or two at a time), clearing the bitmaps.
 cudaError_t compact(const Wave &w, int nq, const int *which, uint32_t *const *queues, const int *counts,
-                    cudaStream_t s, int octants = 0) {
+                    cudaStream_t s) {
   Compact c;
-  c.nwords = octants ? 8 * w.bm_words : (w.n + 31) / 32;
-  c.period = octants ? w.bm_words : c.nwords;
+  c.nwords = (w.n + 31) / 32;
   c.nblk = (c.nwords + kBmWordsPerBlock - 1) / kBmWordsPerBlock;
   for (int k = 0; k < 2; ++k) {
     const int j = k < nq ? k : 0;
@@ -823,7 +807,7 @@ cudaError_t run_waves(const WfArgs &a, Wave w, int64_t total_slots, int64_t wave
     e = cudaMemsetAsync(w.cnt, 0, 4 * C_WORDS, s);
     if (e != cudaSuccess) return e;
     if (w.ordered) {
-      e = cudaMemsetAsync(w.bm[0], 0, BM_COUNT * sizeof(uint32_t) * (size_t)w.bm_words, s);  // all bitmaps
+      e = cudaMemsetAsync(w.bm[0], 0, 4 * sizeof(uint32_t) * (size_t)w.bm_words, s);  // the four bitmaps
       if (e != cudaSuccess) return e;
     }
     k_wf_generate<B><<<std::max(1, std::min(wide, (w.n + kWfBlock - 1) / kWfBlock)), kWfBlock, 0, s>>>(a, w);
@@ -846,7 +830,7 @@ cudaError_t run_waves(const WfArgs &a, Wave w, int64_t total_slots, int64_t wave
       if (w.ordered) {
         const int which[1] = {BM_EXT}, counts[1] = {next ? C_EXT1 : C_EXT0};
         uint32_t *const queues[1] = {w.q_ext[next]};
-        if ((e = compact(w, 1, which, queues, counts, s, SC_WF_OCTANTS)) != cudaSuccess) return e;
+        if ((e = compact(w, 1, which, queues, counts, s)) != cudaSuccess) return e;
       }
       k_wf_rotate<<<1, 32, 0, s>>>(w, cur);
     }
