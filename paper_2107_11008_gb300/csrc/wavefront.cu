@@ -43,11 +43,6 @@ constexpr int kWfBlock = 128;
 #define SC_WF_TRAV_BOUNDS __launch_bounds__(kWfBlock)
 #endif
 constexpr int kWfChunk = SC_WF_CHUNK;
-// idle lanes a warp of the extend kernel waits for before taking new queries
-#ifndef SC_WF_REFILL
-#define SC_WF_REFILL 1
-#endif
-constexpr int kWfRefill = SC_WF_REFILL;
 enum : uint32_t {
   W_SPEC_ONLY = 1u, W_DIFFUSE_FIRST = 2u, W_LAST_SPECULAR = 4u, W_FIXUP = 8u, W_HAS_NEXT = 16u
 };
@@ -224,12 +219,7 @@ __global__ void SC_WF_TRAV_BOUNDS k_wf_extend(WfArgs a, Wave w, int cur) {
   float3 o = f3(0.f, 0.f, 0.f), d = o;
   for (;;) {
     // refill lanes without a query from the queue (one atomic per warp)
-    const bool idle = !tracing && !exhausted;
-    // refill once at least kWfRefill lanes are idle (or none is tracing): consecutive tickets of the
-    // ordered queue, i.e. neighbouring pixels, enter the warp together
-    const unsigned imask = __ballot_sync(0xFFFFFFFFu, idle);
-    const unsigned busy = __ballot_sync(0xFFFFFFFFu, tracing);
-    const bool want = idle && (__popc(imask) >= kWfRefill || busy == 0u);
+    const bool want = !tracing && !exhausted;
     const unsigned wmask = __ballot_sync(0xFFFFFFFFu, want);
     if (wmask) {
       const int leader = __ffs(wmask) - 1;
