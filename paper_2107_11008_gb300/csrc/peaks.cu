@@ -1,9 +1,9 @@
 // peaks.cu -- measurement kernels for the roofline denominators of the traversal kernels.
 //
 // BVH traversal runs on the CUDA cores' FP32 pipes and reads its nodes and triangles from L2
-// (the 512^2 scene's 14 MB of BVH stays resident).  The measured peaks cover HBM copy
-// bandwidth and BF16 GEMM throughput only, so these two kernels measure the other two ceilings
-// on the device they run on: FP32 fused multiply-add throughput and L2 read bandwidth.
+// (the 512^2 scene's 14 MB of BVH stays resident).  A STREAM-style copy and a BF16 GEMM give the
+// HBM and tensor ceilings; these two kernels measure the other two on the device they run on:
+// FP32 fused multiply-add throughput and L2 read bandwidth.
 #include <string>
 
 #include "internal.h"

@@ -543,7 +543,7 @@ def _window_records(g, W, spp, x0, x1, y0, y1):
 
 
 def test_dense_1024_scene_parity(ctx):
-    """The benchmark spec's dense workload (1024^2, 16 glass objects of ~62k triangles, 16 bins, depth
+    """The dense comparison workload (1024^2, 16 glass objects of ~62k triangles, 16 bins, depth
     12, guided light paths): the camera estimator path by path on a 64^2 window and two full rows
     of the frame traced at full size, and 2^15 light paths of the frame's caustic buffer, against the
     oracle.  The denoising comparison's reference is this estimator at 4096 samples, so this is its
