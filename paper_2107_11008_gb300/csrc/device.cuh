@@ -577,20 +577,6 @@ __device__ __forceinline__ bool any_hit(const DevScene &S, float3 o, float3 d, f
   return trace(S, o, d, tmax, true, status, tc).prim >= 0;
 }
 
-// The same two queries over the four-wide nodes, one whole query per call (trav_step4 until done).
-__device__ __forceinline__ Hit trace4(const DevScene &S, float3 o, float3 d, float tmax, bool anyhit,
-                                      unsigned *status, TravCount &tc) {
-  ++tc.queries;
-  TravState ts;
-  trav_begin(ts, tmax, anyhit);
-  if (S.n_tris <= 0) return ts.h;
-  const WRay w = make_wray(o, d);
-  int stack[kStack];
-  while (!trav_step4(S, w, tmax, ts, stack, 1 << 20, status, tc)) {
-  }
-  return ts.h;
-}
-
 // ------------------------------------------------------------------------------------------
 // Surface interaction
 // ------------------------------------------------------------------------------------------

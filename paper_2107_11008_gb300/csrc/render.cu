@@ -327,19 +327,6 @@ __global__ void __launch_bounds__(kBlock, SC_CAM_MIN_BLOCKS)
 // One light path: emission, specular chain, splat at the first diffuse vertex after glass.
 // photons (optional): three float4 per path -- (position, bin as int bits), (shading normal on the
 // side the light arrived from, 1 if deposited), (throughput, 0) -- at that same vertex.
-// The light tracer's queries: over the binary nodes, or (SC_LIGHT_WIDE) the four-wide ones.
-#ifndef SC_LIGHT_WIDE
-#define SC_LIGHT_WIDE 0
-#endif
-__device__ __forceinline__ Hit light_closest(const DevScene &S, float3 o, float3 d, float tmax, unsigned *status,
-                                             TravCount &tc) {
-  return SC_LIGHT_WIDE ? trace4(S, o, d, tmax, false, status, tc) : closest_hit(S, o, d, tmax, status, tc);
-}
-__device__ __forceinline__ bool light_any(const DevScene &S, float3 o, float3 d, float tmax, unsigned *status,
-                                          TravCount &tc) {
-  return SC_LIGHT_WIDE ? trace4(S, o, d, tmax, true, status, tc).prim >= 0 : any_hit(S, o, d, tmax, status, tc);
-}
-
 __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_params P, sc_frame F,
                                                          unsigned *status, unsigned long long *ticket,
                                                          unsigned long long *counters, JitterNorm jn,
@@ -440,7 +427,7 @@ __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_pa
       }
       bool had_spec = false;
       for (int k = 0; emitted && k < P.max_depth; ++k) {
-        const Hit h = light_closest(S, o, d, 3.0e38f, status, tc);
+        const Hit h = closest_hit(S, o, d, 3.0e38f, status, tc);
         sig = fnv(sig, h.id);
         if (h.prim < 0) break;
         const Surf f = interact(S, d, h);
@@ -496,7 +483,7 @@ __global__ void __launch_bounds__(kBlock) k_trace_lights(DevScene S, sc_light_pa
         const float3 so = f.p + f.ngf * eps_of(f.p);
         const float3 wsv = cam.eye - so;
         const float dist = length(wsv);
-        if (light_any(S, so, wsv * (1.0f / dist), dist * (1.0f - 1e-4f), status, tc)) {
+        if (any_hit(S, so, wsv * (1.0f / dist), dist * (1.0f - 1e-4f), status, tc)) {
           sig = fnv(sig, EV_UNLIT);
           break;
         }
