@@ -5,7 +5,7 @@ Workload (one "step" = one frame of the whole hot path): the 512x512 glass scene
 procedural transparent meshes of ~20k triangles (sphere, hollow cylinder glass, torus,
 superellipsoid) with random pose from seed 0 over a checkered floor and back wall, a 1x1 m
 rect light, Cauchy glass A=1.5 B=0.004 um^2 over 8 wavelength bins, max depth 12.  Per step:
-LBVH build from device-resident triangles, 256 camera samples per pixel (67.1M camera paths),
+BVH build from device-resident triangles, 256 camera samples per pixel (67.1M camera paths),
 4M light paths splatted as caustics, and the resolve pass with every ground-truth buffer.
 
 Metric: Mpaths/s (camera + light paths per second, all ranks) with frames/s beside it.

@@ -18,7 +18,9 @@
 // Every path draws the same random numbers, takes the same decisions in the same order and does
 // the same float operations as in the per-lane state machine (both call the same device
 // functions), so path records and accumulators are bit for bit the same.  Path state lives in
-// HBM as structure of arrays; queues are compacted with warp-aggregated atomics.
+// HBM as structure of arrays.  Queues of large waves are kept in path-slot order (producers set
+// a bit per path, a compaction emits the set bits in order); small waves append with
+// warp-aggregated atomics.
 #include <algorithm>
 #include <cstring>
 
