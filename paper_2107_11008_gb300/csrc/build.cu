@@ -11,10 +11,12 @@
 //      pass is histogram -> exclusive scan -> stable scatter (the tile is ranked by 8 one-bit
 //      stable splits in shared memory), so equal codes keep input order.
 //   4. reorder: triangles into leaf order.
-//   5. hierarchy: Karras (HPG 2012) -- internal node i covers a key range found from the
-//      longest-common-prefix function delta(i, j) (ties broken by index).
-//   6. refit: each leaf climbs to the root; the second arrival at a node merges both boxes
-//      (ordering through __threadfence + an atomic counter per node).
+//   5. hierarchy: PLOC agglomerative clustering over the leaves in key order (below), which
+//      writes every node's boxes as it makes it.  With SC_BVH_PLOC=0 instead: Karras (HPG 2012)
+//      -- internal node i covers a key range found from the longest-common-prefix function
+//      delta(i, j) (ties broken by index) -- and a refit in which each leaf climbs to the root and
+//      the second arrival at a node merges both boxes (__threadfence + an atomic counter per node).
+//   6. depth of the deepest leaf; the 4-wide collapse.
 #include <cfloat>
 
 #include <algorithm>
