@@ -185,9 +185,10 @@ def run_batch(args):
 UNET_CHANS = (32, 48, 64, 128)
 # our kernels per training step (counted from an ncu launch list of one step): forward 23 (input
 # pack, 9 encoder conv launches -- the 128 -> 128 conv runs as two halves --, 3 pools, 3 x
-# (transposed conv, 2 convs), output layer); loss 3; backward 38 (output layer 3, decoder 3 x 6,
-# encoder 16, one split-K reduce); Adam 1
-UNET_TRAIN_LAUNCHES = 23 + 3 + 38 + 1
+# (transposed conv, 2 convs), output layer); loss 3; backward 41 (output layer 3, decoder 3 x 6,
+# encoder 19 -- 8 weight gradients, 8 data-gradient convs, 3 pool routings --, one split-K
+# reduce); Adam 1
+UNET_TRAIN_LAUNCHES = 23 + 3 + 41 + 1
 UNET_FWD_LAUNCHES = 23
 # DRAM bytes of one training step (all its kernels, dram__bytes_read.sum + dram__bytes_write.sum
 # summed over launches 1-65 = the first step; launch 0 is the parameter refresh), from one ncu

@@ -24,6 +24,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// the same with both A and B MN-major (transpose bits [15] for A, [16] for B).  An MN-major
+// operand without swizzling is read as core matrices of 8 K-rows x 16 bytes (8 consecutive M/N
+// elements per row, rows 16 bytes apart); the descriptor's stride offset (SBO) steps to the next
+// 8 M/N elements and its leading offset (LBO) to the next 8 K-rows (the swizzled MN-major layouts
+// use the two fields the other way round)
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N) {
+  return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
+}
 
 // ---- tensor memory ----------------------------------------------------------------------
 // called by one full warp; writes the allocated TMEM address to *smem_dst
@@ -116,6 +124,10 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const void *tmap, int 
       "[%7];" ::"r"(dst),
       "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mbar)
       : "memory");
+}
+// bring a tensor map (a kernel parameter) into the TMA unit's descriptor cache ahead of its first use
+__device__ __forceinline__ void prefetch_tmap(const void *tmap) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
 }
 // contiguous global -> shared copy (16-byte aligned addresses, size a multiple of 16)
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {

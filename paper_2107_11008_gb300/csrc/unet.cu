@@ -1,7 +1,8 @@
 // unet.cu -- the BF16 U-Net denoiser (include/sc_unet.h): forward, L1 + SSIM loss, backward,
 // Adam, all on the GPU.  Every 3x3 convolution (forward, data gradient, weight gradient) and the
-// transposed convolutions run on the tensor cores (tcgen05: the TMA kernels of unet_conv.cuh and
-// unet_wgrad.cuh, else the gathering GEMM of unet_gemm.cuh); the 1x1 output layer (HBM-bound),
+// transposed convolutions run on the tensor cores (tcgen05: the TMA kernels of unet_conv.cuh,
+// unet_wgrad_mn.cuh and unet_wgrad.cuh, else the gathering GEMM of unet_gemm.cuh); the 1x1 output
+// layer (HBM-bound),
 // pooling, the loss, the weight-gradient reduction and Adam are plain CUDA.
 #include <algorithm>
 #include <climits>
@@ -9,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -18,7 +20,7 @@
 #include "sc_unet.h"
 #include "unet_conv.cuh"
 #include "unet_gemm.cuh"
-#include "unet_wgrad.cuh"
+#include "unet_wgrad_mn.cuh"
 
 namespace sc {
 int ctx_device(const sc_ctx *c);
@@ -130,6 +132,82 @@ __global__ void k_pool(const bf16 *src, int cs, int co, int C, int n, int h, int
     for (int j = 0; j < 8; ++j) best[j] = k == 0 ? v[j] : fmaxf(best[j], v[j]);
   }
   *reinterpret_cast<uint4 *>(dst + rb_off(ro, x, g * 8, C, wo)) = pack8(best);
+}
+
+// gradient through the 2x2 max pool, the inverse routing of k_pool: gp, the FP32 gradient of the
+// pooled tensor ([pooled pixel][N]), goes to the first maximum of each window in row-major order,
+// plus the FP32 skip gradient of the pool input ([pixel][scs], may be null), times the pool
+// input's ReLU mask, rounded once to BF16 into out (row-blocked, N channels, rows of 2 wo pixels).
+// e: the pool input (row-blocked slice: ecs channels, slice at eco).
+__global__ void k_pool_back(const float *gp, int N, const bf16 *e, int ecs, int eco, const float *skip, int scs,
+                            bf16 *out, int n, int ho, int wo) {
+  const int groups = N / 8;
+  const int w = 2 * wo;
+  const int64_t total = (int64_t)n * ho * wo * groups;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int x = (int)(i % wo);
+  const int64_t t = i / wo;
+  const int g = (int)(t % groups);
+  const int64_t ro = t / groups;  // img * ho + y
+  const int64_t ri = ro / ho * (2 * ho) + 2 * (ro % ho);
+  const int c = 8 * g;
+  float gv[8];
+  {
+    const float4 *p = reinterpret_cast<const float4 *>(gp + (ro * wo + x) * N + c);
+    const float4 a = __ldg(p), b = __ldg(p + 1);
+    gv[0] = a.x;
+    gv[1] = a.y;
+    gv[2] = a.z;
+    gv[3] = a.w;
+    gv[4] = b.x;
+    gv[5] = b.y;
+    gv[6] = b.z;
+    gv[7] = b.w;
+  }
+  float ev[4][8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) unpack8(ldg16(e + rb_off(ri + (q >> 1), 2 * x + (q & 1), eco + c, ecs, w)), ev[q]);
+  int win[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    int b = 0;
+    float best = ev[0][j];
+#pragma unroll
+    for (int q = 1; q < 4; ++q)
+      if (ev[q][j] > best) {
+        best = ev[q][j];
+        b = q;
+      }
+    win[j] = b;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t r2 = ri + (q >> 1);
+    const int x2 = 2 * x + (q & 1);
+    float o[8];
+    if (skip) {
+      const float4 *sp = reinterpret_cast<const float4 *>(skip + (r2 * w + x2) * scs + c);
+      const float4 f0 = __ldg(sp), f1 = __ldg(sp + 1);
+      o[0] = f0.x;
+      o[1] = f0.y;
+      o[2] = f0.z;
+      o[3] = f0.w;
+      o[4] = f1.x;
+      o[5] = f1.y;
+      o[6] = f1.z;
+      o[7] = f1.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) o[j] = 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (win[j] == q) o[j] += gv[j];
+      if (!(ev[q][j] > 0.0f)) o[j] = 0.0f;
+    }
+    *reinterpret_cast<uint4 *>(out + rb_off(r2, x2, c, N, w)) = pack8(o);
+  }
 }
 
 enum { KIND_BIAS = 0, KIND_CONV = 1, KIND_UP = 2, KIND_OUT = 3 };
@@ -263,15 +341,29 @@ __global__ void __launch_bounds__(128) k_out_wgrad_final(const float *part, int 
 
 // Sum of the K-split partial products in a fixed order, scattered to the flat FP32 gradient.
 // part[(s * Mpad + r) * np + n]; rows r: conv (tap * cin_p + c) | ones; up: c | ones.
-// Block = 32 consecutive entries (r, n) x 8 split groups; group g sums splits
-// g, g + 8, ... (coalesced 128-byte reads), then the 8 group sums are added in order.
-constexpr int kRedEntries = 32, kRedGroups = 8;
+// Block = 32 lanes x 4 consecutive entries (r, n..n+3; np is a multiple of 16) x 8 split groups;
+// group g sums splits g, g + 8, ... (one 16-byte load per lane, 512 bytes per warp), then the 8
+// group sums are added in order.
+constexpr int kRedEntries = 32, kRedVec = 4, kRedGroups = 8;
+constexpr int kRedBlockEntries = kRedEntries * kRedVec;
 
-__device__ __forceinline__ float split_sum(const float *part, int splits, int Mpad, int np, int r, int n, int g) {
-  float s = 0.0f;
+__device__ __forceinline__ float4 split_sum4(const float *part, int splits, int Mpad, int np, int r, int n, int g) {
+  float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll 8
-  for (int k = g; k < splits; k += kRedGroups) s += part[((int64_t)k * Mpad + r) * np + n];
+  for (int k = g; k < splits; k += kRedGroups) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(part + ((int64_t)k * Mpad + r) * np + n));
+    s.x += v.x;
+    s.y += v.y;
+    s.z += v.z;
+    s.w += v.w;
+  }
   return s;
+}
+__device__ __forceinline__ void add4(float4 &a, const float4 &b) {
+  a.x += b.x;
+  a.y += b.y;
+  a.z += b.z;
+  a.w += b.w;
 }
 
 // One launch reduces the split-K partials of every layer of a backward pass: segment t covers
@@ -288,7 +380,7 @@ struct RedTable {
 
 __global__ void __launch_bounds__(kRedEntries *kRedGroups) k_wgrad_reduce(const __grid_constant__ RedTable T,
                                                                            const float *wpart, float *grads) {
-  __shared__ float sh[kRedGroups][kRedEntries];
+  __shared__ float4 sh[kRedGroups][kRedEntries];
   int lo = 0, hi = T.n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -301,41 +393,48 @@ __global__ void __launch_bounds__(kRedEntries *kRedGroups) k_wgrad_reduce(const 
   const int splits = S.splits, Mpad = S.Mpad, np = S.np, rows = S.rows, kind = S.kind, cout = S.cout, cin = S.cin,
             cin_p = S.cin_p;
   const int e = threadIdx.x % kRedEntries, g = threadIdx.x / kRedEntries;
-  const int64_t i = (int64_t)((int)blockIdx.x - S.first_block) * kRedEntries + e;
+  const int64_t i = ((int64_t)((int)blockIdx.x - S.first_block) * kRedEntries + e) * kRedVec;
   const int64_t total = (int64_t)(rows + 1) * np;
   const int r = (int)(i / np), n = (int)(i % np);
   const bool valid = i < total;
-  // the bias of a transposed conv sums its four (a, e) column blocks of the ones row
-  float v = 0.0f;
+  // the bias of a transposed conv sums its four (a, e) column blocks of the ones row (cout is a
+  // multiple of 4, so the 4 entries are all below cout or all at or above it)
+  float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   if (valid) {
     if (kind == KIND_UP && r == rows) {
       if (n < cout)
-        for (int ae = 0; ae < 4; ++ae) v += split_sum(part, splits, Mpad, np, r, ae * cout + n, g);
+        for (int ae = 0; ae < 4; ++ae) add4(v, split_sum4(part, splits, Mpad, np, r, ae * cout + n, g));
     } else {
-      v = split_sum(part, splits, Mpad, np, r, n, g);
+      v = split_sum4(part, splits, Mpad, np, r, n, g);
     }
   }
   sh[g][e] = v;
   __syncthreads();
   if (g != 0 || !valid) return;
-  float t = 0.0f;
-  for (int k = 0; k < kRedGroups; ++k) t += sh[k][e];
-  if (kind == KIND_CONV) {
-    if (n >= cout) return;
-    if (r == rows) {
-      gb[n] = t;
-      return;
+  float4 t4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (int k = 0; k < kRedGroups; ++k) add4(t4, sh[k][e]);
+  const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+  for (int q = 0; q < kRedVec; ++q) {
+    const int nq = n + q;
+    const float t = tv[q];
+    if (kind == KIND_CONV) {
+      if (nq >= cout) continue;
+      if (r == rows) {
+        gb[nq] = t;
+        continue;
+      }
+      const int tap = r / cin_p, c = r - tap * cin_p;
+      if (c < cin) gw[((int64_t)nq * 9 + tap) * cin + c] = t;
+    } else {  // KIND_UP
+      if (r == rows) {
+        if (nq < cout) gb[nq] = t;
+        continue;
+      }
+      if (nq >= 4 * cout) continue;
+      const int ae = nq / cout, o = nq - ae * cout;
+      gw[((int64_t)r * 4 + ae) * cout + o] = t;
     }
-    const int tap = r / cin_p, c = r - tap * cin_p;
-    if (c < cin) gw[((int64_t)n * 9 + tap) * cin + c] = t;
-  } else {  // KIND_UP
-    if (r == rows) {
-      if (n < cout) gb[n] = t;
-      return;
-    }
-    if (n >= 4 * cout) return;
-    const int ae = n / cout, o = n - ae * cout;
-    gw[((int64_t)r * 4 + ae) * cout + o] = t;
   }
 }
 
@@ -718,6 +817,7 @@ struct sc_unet {
   bf16 *gy8 = nullptr, *gd2[kLevels] = {}, *gd1[kLevels] = {}, *gup[kLevels] = {}, *ge2[kLevels] = {},
        *ge1[kLevels] = {};
   float *gskip[kLevels] = {};
+  float *gpool = nullptr;  // FP32 gradient of one level's pool output (backward)
   // loss
   float *smap[3] = {};
   double *lpart = nullptr;
@@ -977,6 +1077,21 @@ bool encode_rb_map(CUtensorMap *map, const bf16 *src, int co, int channels, int 
                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Each channel group's image row of a row-blocked BF16 slice as one run of 8 w values: (8 w,
+// groups, h, n, 1), box (256, gb, 1, 1, 1), so that a one-pixel shift is an element offset of 8
+// (16 bytes) and one copy brings 32 pixels of gb channel groups in rows of 512 bytes.
+bool encode_flat_map(CUtensorMap *map, const bf16 *src, int co, int channels, int cs, int w, int h, int n, int gb) {
+  const cuuint64_t row = (cuuint64_t)cs * w * 2;
+  const cuuint64_t dims[5] = {(cuuint64_t)8 * w, (cuuint64_t)(channels / 8), (cuuint64_t)h, (cuuint64_t)n, 1};
+  const cuuint64_t strides[4] = {(cuuint64_t)w * 16, row, row * h, row * h * n};
+  const cuuint32_t box[5] = {256, (cuuint32_t)gb, 1, 1, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  auto enc = tensor_map_encoder();
+  return enc && enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(src + (int64_t)co * w), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // groups of 8 input channels per A stage (0: the layer does not fit in 227 KB next to its
 // resident weights).  Among the even divisors of cin / 8 that fit, the one that lets the most CTAs
 // share an SM (shared memory, TMEM, at most 4 by registers) when SC_CONV_MAXOCC, else the largest;
@@ -1041,7 +1156,6 @@ struct ColSplit<EGrad> {  // BF16 columns only (split == N)
 };
 bool col_splittable(const EBiasAct &, int) { return true; }
 bool col_splittable(const EGrad &e, int N) { return e.split == N && !e.out2; }
-bool col_splittable(const EPoolBack &, int) { return false; }
 
 template <class EP>
 cudaError_t conv3x3_tma(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h, int w, int n, int N,
@@ -1222,9 +1336,21 @@ int wgrad_tma_stages(int cin, int cout, int mtiles, uint32_t gstride) {
   return 0;
 }
 
+// ring slots of the MN-major weight-gradient kernel that fit (0: it does not fit)
+#ifndef SC_WG_MN
+#define SC_WG_MN 0
+#endif
+int wgrad_mn_slots(int cout, int mtiles) {
+  if ((uint32_t)mtiles * wg_cstride(cout) > 512u) return 0;
+  for (int s = kMnMaxSlots; s >= 2; --s)
+    if (mn_smem_bytes(cout, s) <= 227 * 1024) return s;
+  return 0;
+}
+
 // weight gradient of one layer: A (rows = (tap, c) | c, + ones row), B (rows = output channels),
 // contracted over the pixels, reduced deterministically into the flat gradient.  3x3 layers on
-// rows of 128k pixels take the TMA kernel (x: the layer input, gz: its output gradient).
+// rows of 128k pixels (or 128 / w whole rows) take a TMA kernel (x: the layer input, gz: its
+// output gradient): the MN-major one where its accumulators fit in TMEM, else the transposing one.
 int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, int64_t K, cudaStream_t ws,
           RedTable &red, int &red_blocks) {
   const char *where = "sc_unet wgrad";
@@ -1235,13 +1361,42 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
   // the persistent TMA kernel pays a pipeline fill per CTA: worth it with >= SC_WG_MIN_TILES
   // tiles per CTA
   const int64_t tiles = K / 128;
-  const int rst = ly.kind == KIND_CONV && A.mode == 0 && A.ntaps == 9 && conv_rows_ok(A.w, A.h) && B.co == 0 &&
-                          B.cs == ly.cout && tiles >= (int64_t)SC_WG_MIN_TILES * u->num_sms &&
-                          tensor_map_encoder() != nullptr
-                      ? wgrad_tma_stages(A.cin, ly.cout, g.Mtiles, G.gstride)
-                      : 0;
+  const bool tma_ok = ly.kind == KIND_CONV && A.mode == 0 && A.ntaps == 9 && conv_rows_ok(A.w, A.h) && B.co == 0 &&
+                      B.cs == ly.cout && A.cin * 9 == g.rows && tiles >= (int64_t)SC_WG_MIN_TILES * u->num_sms &&
+                      tensor_map_encoder() != nullptr;
+  const int mslots = SC_WG_MN && tma_ok && A.w >= 32 ? wgrad_mn_slots(ly.cout, g.Mtiles) : 0;
+  const int rst = tma_ok && mslots == 0 ? wgrad_tma_stages(A.cin, ly.cout, g.Mtiles, G.gstride) : 0;
   int splits;
-  if (rst > 0) {
+  if (mslots > 0) {
+    const int n_img = G.n_img;
+    const int ntiles = G.narrow ? n_img * (A.h / G.th) : n_img * A.h * (A.w / 128);
+    splits = std::min(ntiles, u->num_sms);
+    if ((size_t)splits * Mpad * g.np > ly.part_floats)
+      return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
+    CUtensorMap xm, gm;
+    // x: quarters of gb channel groups, pixel-granular (a tap's shift is an element offset)
+    const int gb = std::gcd(A.cin / 8, 16);
+    if (!encode_flat_map(&xm, A.src, A.co, A.cin, A.cs, A.w, A.h, n_img, gb) ||
+        !encode_rb_map(&gm, B.src, 0, ly.cout, ly.cout, A.w, A.h, n_img, true, G.narrow ? A.w : 128, G.th))
+      return fail(c, SC_ERR_CUDA, "sc_unet wgrad: tensor map encoding failed");
+    const int smem = (int)mn_smem_bytes(ly.cout, mslots);
+    static bool attr[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (dev >= 0 && dev < kMaxDev && !attr[dev]) {
+        UCHK(cudaFuncSetAttribute(k_wgrad_mn<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        UCHK(cudaFuncSetAttribute(k_wgrad_mn<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr[dev] = true;
+      }
+    }
+    auto kern = G.narrow ? k_wgrad_mn<true> : k_wgrad_mn<false>;
+    kern<<<splits, kMnThreads, smem, ws>>>(xm, gm, A.cin, ly.cout, g.Mtiles, mslots, gb, G, part,
+                                           sc::ctx_status(c));
+    UCHK(cudaGetLastError());
+  } else if (rst > 0) {
     const int n_img = G.n_img;
     const int ntiles = G.narrow ? n_img * (A.h / G.th) : n_img * A.h * (A.w / 128);
     splits = std::min(ntiles, u->num_sms);
@@ -1297,7 +1452,7 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
   sg.cin = ly.cin;
   sg.cin_p = ly.cin_p;
   sg.first_block = red_blocks;
-  red_blocks += (int)(((int64_t)(g.rows + 1) * g.np + kRedEntries - 1) / kRedEntries);
+  red_blocks += (int)(((int64_t)(g.rows + 1) * g.np + kRedBlockEntries - 1) / kRedBlockEntries);
   UCHK(cudaGetLastError());
   return SC_OK;
 }
@@ -1399,21 +1554,19 @@ int backward_body(sc_ctx *c, sc_unet *u) {
                tpix(u->ge1[l], cl, 0, h, w, cl, 1, 0, cl, 0, pad16(cl)), P[l], ws, red, red_blocks);
     if (rc) return rc;
     if (l > 0) {
-      // through the pool into the level above, plus its skip gradient, times its ReLU mask
+      // the gradient of the pool output (FP32), then through the pool into the level above, plus
+      // its skip gradient, times its ReLU mask
       const int cp = kChans[l - 1];
       const View e = enc_out(u, l - 1);
-      EPoolBack pb;
-      pb.out = u->ge2[l - 1];
-      pb.ocs = cp;
-      pb.e = e.p;
-      pb.ecs = e.cs;
-      pb.eco = e.co;
-      pb.skip = u->gskip[l - 1];
-      pb.scs = cp;
-      pb.h = h;
-      pb.w = w;
-      pb.N = cp;
-      UCHK(conv3x3(u, u->ge1[l], cl, 0, cl, h, w, n, cp, c1.wd, c1.wtd, c1.wtd2, -1, pb, st, s));
+      EGrad eg = egrad(nullptr, cp, nullptr, 0, 0, cp, w);
+      eg.split = 0;
+      eg.out2 = u->gpool;
+      eg.o2cs = cp;
+      UCHK(conv3x3(u, u->ge1[l], cl, 0, cl, h, w, n, cp, c1.wd, c1.wtd, c1.wtd2, -1, eg, st, s));
+      const int64_t tot = P[l] * (cp / 8);
+      k_pool_back<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(u->gpool, cp, e.p, e.cs, e.co, u->gskip[l - 1], cp,
+                                                              u->ge2[l - 1], n, h, w);
+      UCHK(cudaGetLastError());
     }
   }
   // every layer's split-K partials, reduced in one launch on the weight-gradient stream
@@ -1672,6 +1825,8 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
       u->ge2[l] = cv.take<bf16>(P[l] * cl);
       u->ge1[l] = cv.take<bf16>(P[l] * cl);
     }
+    // the FP32 gradient of a pool output (the largest: level 1, kChans[0] channels)
+    u->gpool = cv.take<float>(P[1] * kChans[0]);
     u->y = cv.take<float>(P[0] * kOutCh);
     u->gy8 = cv.take<bf16>(P[0] * kGyCh);
     for (int k = 0; k < 3; ++k) u->smap[k] = cv.take<float>((size_t)max_batch * Hv * Wv * 3);

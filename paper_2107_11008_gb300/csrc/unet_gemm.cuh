@@ -469,74 +469,6 @@ struct EGrad {
   }
 };
 
-// data gradient w.r.t. the output of a 2x2 max pool (row = pooled pixel, h x w), routed to the
-// first maximum of its window in row-major order, plus the skip gradient of the pool input
-// (FP32, [pixel][scs]), times the ReLU mask of the pool input; written in BF16 at the pool
-// input's resolution.  e and out are row-blocked at that resolution (rows of 2w pixels).
-struct EPoolBack {
-  bf16 *out;
-  int ocs;
-  const bf16 *e;  // pool input
-  int ecs, eco;
-  const float *skip;  // FP32 skip gradient at the pool input's resolution (may be null)
-  int scs;
-  int h, w, N;
-  __device__ __forceinline__ void store(int row, int n0, const float *v, int) const {
-    if (n0 >= N) return;
-    const int x = row % w, t = row / w, y = t % h, img = t / h;
-    // two halves of 8 channels, one after the other, so that few values are live at once
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      const int c = n0 + 8 * hh;
-      float ev[4][8];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        unpack8(ldg16(e + rb_off((int64_t)img * 2 * h + 2 * y + (q >> 1), 2 * x + (q & 1), eco + c, ecs, 2 * w)),
-                ev[q]);
-      int win[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        int b = 0;
-        float best = ev[0][i];
-#pragma unroll
-        for (int q = 1; q < 4; ++q)
-          if (ev[q][i] > best) {
-            best = ev[q][i];
-            b = q;
-          }
-        win[i] = b;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t r2 = (int64_t)img * 2 * h + 2 * y + (q >> 1);
-        const int x2 = 2 * x + (q & 1);
-        float o[8];
-        if (skip) {
-          const float4 *sp = reinterpret_cast<const float4 *>(skip + (r2 * (2 * w) + x2) * scs + c);
-          const float4 f0 = __ldg(sp), f1 = __ldg(sp + 1);
-          o[0] = f0.x;
-          o[1] = f0.y;
-          o[2] = f0.z;
-          o[3] = f0.w;
-          o[4] = f1.x;
-          o[5] = f1.y;
-          o[6] = f1.z;
-          o[7] = f1.w;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 8; ++i) o[i] = 0.0f;
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          if (win[i] == q) o[i] += v[8 * hh + i];
-          if (!(ev[q][i] > 0.0f)) o[i] = 0.0f;
-        }
-        *reinterpret_cast<uint4 *>(out + rb_off(r2, x2, c, ocs, 2 * w)) = pack8(o);
-      }
-    }
-  }
-};
-
 // FP32 partial products of a K split: part[(split * Mpad + row) * ld + n]
 struct EPartial {
   float *part;

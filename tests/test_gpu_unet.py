@@ -305,9 +305,28 @@ def test_training_reduces_loss(ctx):
     net.close()
 
 
-def test_full_size_step_sampled_weight_gradients(ctx):
-    """16 x 256^2 (the training workload): the split-K weight gradients of the output layer and the
-    first conv, recomputed over all 2^20 pixels from the GPU's own BF16 operands."""
+def _wgrad_ref(x, gz):
+    """gw[o, dy, dx, c] = sum_p gz[p, o] x[p + (dy - 1, dx - 1), c] (zero outside the image) and
+    gb[o] = sum_p gz[p, o] in FP64 on the device, with the same sums over absolute values."""
+    n, h, w, c = x.shape
+    xp = torch.nn.functional.pad(x, (0, 0, 1, 1, 1, 1))
+    g = gz.reshape(-1, gz.shape[-1])
+    ga = g.abs()
+    gw = torch.empty(g.shape[1], 3, 3, c, dtype=torch.float64, device=x.device)
+    aw = torch.empty_like(gw)
+    for dy in range(3):
+        for dx in range(3):
+            xs = xp[:, dy:dy + h, dx:dx + w, :].reshape(-1, c)
+            gw[:, dy, dx, :] = g.T @ xs
+            aw[:, dy, dx, :] = ga.T @ xs.abs()
+    return gw.cpu().numpy(), aw.cpu().numpy(), g.sum(0).cpu().numpy(), ga.sum(0).cpu().numpy()
+
+
+def test_full_size_step_weight_gradients(ctx):
+    """16 x 256^2 (the training workload): the split-K weight gradients of the output layer and of
+    every 3x3 convolution (all taps, channels and outputs, and the biases), recomputed over all
+    2^20 pixels of each level from the GPU's own BF16 operands.  At this size the convolutions of
+    levels 0-2 take the TMA weight-gradient kernels and level 3 the gathering GEMM."""
     n, h, w = 16, 256, 256
     rng = np.random.default_rng(9)
     x = rng.random((n, h, w, 11)).astype(np.float32)
@@ -324,13 +343,18 @@ def test_full_size_step_sampled_weight_gradients(ctx):
     ref = (gy.T @ d2).cpu().numpy()
     absum = (gy.abs().T @ d2.abs()).cpu().numpy()
     _check_f32(G["out_w"], ref, absum, "out_w full size")
-    # enc0 conv 1, centre tap, all 11 input channels, all 32 outputs
-    xin = net.buffer("INPUT").float()[..., :11].reshape(-1, 11).double()
-    ge1 = net.buffer("GENC1", 0).float().reshape(-1, 32).double()
-    ref = (ge1.T @ xin).cpu().numpy()
-    absum = (ge1.abs().T @ xin.abs()).cpu().numpy()
-    _check_f32(G["enc0_c1_w"][:, 1, 1, :], ref, absum, "enc0_c1 centre tap full size")
-    _check_f32(G["enc0_c1_b"], ge1.sum(0).cpu().numpy(), ge1.abs().sum(0).cpu().numpy(), "enc0_c1_b full size")
+    buf = lambda name, lvl=0: net.buffer(name, lvl).double()  # noqa: E731
+    cases = []
+    for l in range(4):
+        cases.append((f"enc{l}_c1", buf("INPUT")[..., :11] if l == 0 else buf("POOL", l), buf("GENC1", l)))
+        cases.append((f"enc{l}_c2", buf("ENC1", l), buf("GENC2", l)))
+    for l in range(3):
+        cases.append((f"dec{l}_c1", torch.cat([buf("UP", l), buf("ENC2", l)], dim=-1), buf("GDEC1", l)))
+        cases.append((f"dec{l}_c2", buf("DEC1", l), buf("GDEC2", l)))
+    for name, xin, gz in cases:
+        gw, aw, gb, ab = _wgrad_ref(xin, gz)
+        _check_f32(G[f"{name}_w"], gw, aw, f"{name}_w full size")
+        _check_f32(G[f"{name}_b"], gb, ab, f"{name}_b full size")
     net.close()
 
 
