@@ -1077,17 +1077,19 @@ bool encode_rb_map(CUtensorMap *map, const bf16 *src, int co, int channels, int 
                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Each channel group's image row of a row-blocked BF16 slice as one run of 8 w values: (8 w,
-// groups, h, n, 1), box (256, gb, 1, 1, 1), so that a one-pixel shift is an element offset of 8
-// (16 bytes) and one copy brings 32 pixels of gb channel groups in rows of 512 bytes.
-bool encode_flat_map(CUtensorMap *map, const bf16 *src, int co, int channels, int cs, int w, int h, int n, int gb) {
+// A row-blocked BF16 slice (cs channels, slice at co, `channels` of them) seen with 8-byte elements
+// (half a pixel's 8 channels) as (2 w, h, channel groups, n, 1), box (2 box_w, box_h, box_g, 1, 1):
+// a one-pixel shift is an element offset of 2 (16 bytes), and one copy brings box_g channel groups
+// of box_h rows of box_w pixels, each group's pixels contiguous (box_h box_w x 16 bytes).
+bool encode_px_map(CUtensorMap *map, const bf16 *src, int co, int channels, int cs, int w, int h, int n, int box_w,
+                   int box_h, int box_g) {
   const cuuint64_t row = (cuuint64_t)cs * w * 2;
-  const cuuint64_t dims[5] = {(cuuint64_t)8 * w, (cuuint64_t)(channels / 8), (cuuint64_t)h, (cuuint64_t)n, 1};
-  const cuuint64_t strides[4] = {(cuuint64_t)w * 16, row, row * h, row * h * n};
-  const cuuint32_t box[5] = {256, (cuuint32_t)gb, 1, 1, 1};
+  const cuuint64_t dims[5] = {(cuuint64_t)2 * w, (cuuint64_t)h, (cuuint64_t)(channels / 8), (cuuint64_t)n, 1};
+  const cuuint64_t strides[4] = {row, (cuuint64_t)w * 16, row * h, row * h * n};
+  const cuuint32_t box[5] = {(cuuint32_t)(2 * box_w), (cuuint32_t)box_h, (cuuint32_t)box_g, 1, 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   auto enc = tensor_map_encoder();
-  return enc && enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(src + (int64_t)co * w), dims, strides,
+  return enc && enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<bf16 *>(src + (int64_t)co * w), dims, strides,
                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -1336,12 +1338,11 @@ int wgrad_tma_stages(int cin, int cout, int mtiles, uint32_t gstride) {
   return 0;
 }
 
-// ring slots of the MN-major weight-gradient kernel that fit (0: it does not fit)
+// ring slots of the MN-major weight-gradient kernel that fit next to its two gz tiles
 #ifndef SC_WG_MN
-#define SC_WG_MN 0
+#define SC_WG_MN 1
 #endif
-int wgrad_mn_slots(int cout, int mtiles) {
-  if ((uint32_t)mtiles * wg_cstride(cout) > 512u) return 0;
+int wgrad_mn_slots(int cout) {
   for (int s = kMnMaxSlots; s >= 2; --s)
     if (mn_smem_bytes(cout, s) <= 227 * 1024) return s;
   return 0;
@@ -1362,10 +1363,13 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
   // tiles per CTA
   const int64_t tiles = K / 128;
   const bool tma_ok = ly.kind == KIND_CONV && A.mode == 0 && A.ntaps == 9 && conv_rows_ok(A.w, A.h) && B.co == 0 &&
-                      B.cs == ly.cout && A.cin * 9 == g.rows && tiles >= (int64_t)SC_WG_MIN_TILES * u->num_sms &&
-                      tensor_map_encoder() != nullptr;
-  const int mslots = SC_WG_MN && tma_ok && A.w >= 32 ? wgrad_mn_slots(ly.cout, g.Mtiles) : 0;
-  const int rst = tma_ok && mslots == 0 ? wgrad_tma_stages(A.cin, ly.cout, g.Mtiles, G.gstride) : 0;
+                      B.cs == ly.cout && A.cin * 9 == g.rows && tensor_map_encoder() != nullptr;
+  // rows narrower than 128 pixels: the MN-major kernel (its per-tap copies cost least there);
+  // wide rows: the transposing kernel, with >= SC_WG_MIN_TILES tiles per CTA
+  const int mslots = SC_WG_MN && tma_ok && A.w < 128 && tiles >= 64 ? wgrad_mn_slots(ly.cout) : 0;
+  const int rst = tma_ok && A.w >= 128 && tiles >= (int64_t)SC_WG_MIN_TILES * u->num_sms
+                      ? wgrad_tma_stages(A.cin, ly.cout, g.Mtiles, G.gstride)
+                      : 0;
   int splits;
   if (mslots > 0) {
     const int n_img = G.n_img;
@@ -1374,10 +1378,11 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
     if ((size_t)splits * Mpad * g.np > ly.part_floats)
       return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
     CUtensorMap xm, gm;
-    // x: quarters of gb channel groups, pixel-granular (a tap's shift is an element offset)
+    // x: gb channel groups of a tap per copy (a tap's shift is an element offset); gz: the whole tile
     const int gb = std::gcd(A.cin / 8, 16);
-    if (!encode_flat_map(&xm, A.src, A.co, A.cin, A.cs, A.w, A.h, n_img, gb) ||
-        !encode_rb_map(&gm, B.src, 0, ly.cout, ly.cout, A.w, A.h, n_img, true, G.narrow ? A.w : 128, G.th))
+    const int bw = G.narrow ? A.w : 128;
+    if (!encode_px_map(&xm, A.src, A.co, A.cin, A.cs, A.w, A.h, n_img, bw, G.th, gb) ||
+        !encode_px_map(&gm, B.src, 0, ly.cout, ly.cout, A.w, A.h, n_img, bw, G.th, ly.cout / 8))
       return fail(c, SC_ERR_CUDA, "sc_unet wgrad: tensor map encoding failed");
     const int smem = (int)mn_smem_bytes(ly.cout, mslots);
     static bool attr[kMaxDev] = {};
@@ -1392,9 +1397,13 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
         attr[dev] = true;
       }
     }
+    // 128-row blocks per CTA: as many accumulators as fit in TMEM, in balanced chunks
+    const int per = 512 / (int)wg_cstride(ly.cout);
+    const int nchunk = (g.Mtiles + per - 1) / per;
+    const int mchunk = (g.Mtiles + nchunk - 1) / nchunk;
     auto kern = G.narrow ? k_wgrad_mn<true> : k_wgrad_mn<false>;
-    kern<<<splits, kMnThreads, smem, ws>>>(xm, gm, A.cin, ly.cout, g.Mtiles, mslots, gb, G, part,
-                                           sc::ctx_status(c));
+    kern<<<dim3(splits, nchunk), kMnThreads, smem, ws>>>(xm, gm, A.cin, ly.cout, g.Mtiles, mchunk, mslots, gb, G,
+                                                         part, sc::ctx_status(c));
     UCHK(cudaGetLastError());
   } else if (rst > 0) {
     const int n_img = G.n_img;

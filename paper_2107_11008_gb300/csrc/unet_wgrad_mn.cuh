@@ -1,29 +1,29 @@
 // unet_wgrad_mn.cuh -- weight gradient of a 3x3 convolution on tcgen05 with MN-major operands
 // that TMA delivers ready to use (tiles of 128 pixels: part of a row of 128k pixels, or 128 / w
-// whole rows of w = 32 or 64 pixels).
+// whole narrower rows, as in unet_conv.cuh).
 //
 //   gw[o][tap][c] = sum_p gz[p][o] * x[p + offset(tap)][c],   gb[o] = sum_p gz[p][o]
 //
 // as D[(tap, c) | ones][o] = sum over pixels.  The tensors hold 8 consecutive channels per 16
 // bytes, which is the row of an MN-major core matrix when M (or N) is the channel and K the pixel:
-// 8 consecutive pixels x 8 channels = one 128-byte core matrix.  So nothing is transposed.  One MMA
-// (K = 16) reads 16 pixels, so the operand is staged per quarter of the tile (32 pixels): a ring
-// slot holds one 128-row block of A as [quarter][16 pairs (tap, channel group)][32 pixels x 16
-// bytes], and the pairs of an MMA are 512 bytes apart.  Each channel group's image row is one
-// contiguous run of 8 w BF16 values, so a tap's pixel shift is an element offset of 8 (16 bytes)
-// in a (8 w, groups, rows, images) view: one TMA copy (256 values x gb groups, zeros outside the
-// image) brings a quarter of gb consecutive pairs of one tap, in rows of 512 bytes; gb = gcd(cin /
-// 8, 16), so that no copy straddles two blocks.  The bias row 9 cin is a pair whose channel 0 is
-// one, copied from a constant.  The gz tile arrives as one 2 KB block per group of 8 output
-// channels (K-row stride 16 bytes, 128 pixels).  One thread issues the MMAs; the accumulators of
-// all 128-row blocks (cout columns each, 32/64/128 apart) stay in TMEM across the CTA's contiguous
+// 8 consecutive pixels x 8 channels = one 128-byte core matrix.  So nothing is transposed.  A ring
+// slot holds one 128-row block of A: 16 pairs (tap, channel group), tap-major, each the tile's 128
+// pixels shifted by the tap's offset (2 KB, pairs 2 KB apart).  The tensors are viewed with 8-byte
+// elements (half a pixel) as (2 w, rows, groups, images): a one-pixel shift is an element offset of
+// 2 (16 bytes), and one TMA copy (zeros outside the image) brings gb consecutive pairs of one tap
+// whole, gb = gcd(cin / 8, 16) so that no copy straddles two blocks; the cost of a copy hardly
+// depends on its size, so few large copies matter more than anything else here.  The bias row
+// 9 cin is a pair whose channel 0 is one, copied from a constant; the gz tile is one copy (one 2 KB
+// block per group of 8 output channels).  One thread issues the MMAs; the accumulators of all
+// 128-row blocks (cout columns each, 32/64/128 apart) stay in TMEM across the CTA's contiguous
 // range of tiles, and at the end the epilogue warps write them as this CTA's partial sums
-// ([split][128 mtiles][cout], the layout k_wgrad_reduce sums in a fixed order).  Every wait is
-// bounded.
+// ([split][128 mtiles][cout], the layout k_wgrad_reduce sums in a fixed order).  Where all blocks'
+// accumulators do not fit in TMEM, the grid's y dimension splits them into chunks of `mchunk`
+// blocks, one CTA per (tile range, chunk).  Every wait is bounded.
 //
-// Operand extents (LBO = 128 bytes: the next 8 pixels; SBO = the next 8 channels: 512 bytes in A,
-// 2 KB in gz): one MMA reads 16 pairs x 256 bytes of one quarter of its slot, and cout / 8 blocks x
-// 256 bytes of its gz tile.
+// Operand extents (LBO = 128 bytes: the next 8 pixels; SBO = 2 KB: the next 8 channels): one MMA
+// (K = 16) reads 16 (or cout / 8) pairs x 256 bytes from its start, which moves 256 bytes per K
+// step, so every read stays inside its own 32 KB A slot or gz tile.
 #pragma once
 #include "unet_wgrad.cuh"
 
@@ -31,9 +31,7 @@ namespace sc {
 namespace unet {
 
 constexpr uint32_t kMnPair = 128 * 16;      // one (tap, channel group) pair: 128 pixels x 16 bytes
-constexpr uint32_t kMnQRow = 32 * 16;       // a pair's quarter: 32 pixels x 16 bytes
-constexpr uint32_t kMnQuarter = 16 * kMnQRow;  // one quarter of a slot: 16 pairs
-constexpr uint32_t kMnSlot = 16 * kMnPair;  // one 128-row A block (4 quarters)
+constexpr uint32_t kMnSlot = 16 * kMnPair;  // one 128-row A block
 constexpr int kMnThreads = 192;             // producer, MMA issuer, 4 epilogue warps
 constexpr int kMnMaxSlots = 6;
 
@@ -53,15 +51,14 @@ __host__ __device__ constexpr size_t mn_smem_bytes(int cout, int slots) {
   return (size_t)slots * kMnSlot + 2 * mn_b_bytes(cout) + 256;
 }
 
-// xmap: the layer input as (8 w values, groups, h, images, 1), box (256, gb, 1, 1, 1); gmap: the
-// output gradient, row-blocked (64, w / 8, groups, h, images), box (64, 16 or w / 8, 1, 1 or th,
-// 1).  cin, cout multiples of 8, gb a divisor of both cin / 8 and 16; mtiles = ceil((9 cin + 1) /
-// 128); w a multiple of 128, or 32 or 64.
+// xmap: the layer input, gmap: its output gradient, both as (2 w, h, groups, images, 1) of 8-byte
+// elements with boxes (256 or 2 w, 1 or th, gb or cout / 8, 1, 1).  cin, cout multiples of 8, gb a
+// divisor of both cin / 8 and 16; mtiles = ceil((9 cin + 1) / 128).
 template <bool NARROW>
 __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constant__ CUtensorMap xmap,
                                                               const __grid_constant__ CUtensorMap gmap, int cin,
-                                                              int cout, int mtiles, int slots, int gb,
-                                                              ConvGeo G, float *part, unsigned *status) {
+                                                              int cout, int mtiles, int mchunk, int slots,
+                                                              int gb, ConvGeo G, float *part, unsigned *status) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ngx = cin / 8, ngz = cout / 8;
@@ -81,8 +78,10 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
   const int t1 = (int)((int64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
   const int mine = t1 - t0;
   const uint32_t cstride = wg_cstride(cout);
+  // this CTA's 128-row blocks [mb0, mb1)
+  const int mb0 = (int)blockIdx.y * mchunk, mb1 = min(mb0 + mchunk, mtiles), nmb = mb1 - mb0;
   uint32_t cols = 32;
-  while (cols < (uint32_t)mtiles * cstride) cols <<= 1;
+  while (cols < (uint32_t)nmb * cstride) cols <<= 1;
   if (threadIdx.x == 0) {
     for (int s = 0; s < slots; ++s) {
       tc::mbar_init(tc::smem_addr(&bar[s]), 1);
@@ -121,12 +120,10 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
         }
         const uint32_t bfull = tc::smem_addr(&bar[12 + bs]);
         tc::mbar_expect_tx(bfull, (uint32_t)ngz * kMnPair);
-        const uint32_t bdst = tc::smem_addr(sB + bs * bb);
-        for (int g = 0; g < ngz; ++g)
-          tc::tma_load_5d(bdst + g * kMnPair, &gmap, 0, xt * (128 / 8), g, y, img, bfull);
-        ++nb;
         const int x0 = NARROW ? 0 : xt * 128;
-        for (int m = 0; m < mtiles; ++m) {
+        tc::tma_load_5d(tc::smem_addr(sB + bs * bb), &gmap, 2 * x0, y, 0, img, 0, bfull);
+        ++nb;
+        for (int m = mb0; m < mb1; ++m) {
           const int s = na % slots, u = na / slots;
           if (u > 0 && !tc::mbar_wait(tc::smem_addr(&bar[kMnMaxSlots + s]), (u - 1) & 1)) {
             stop = true;
@@ -136,19 +133,12 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
           const uint32_t afull = tc::smem_addr(&bar[s]);
           tc::mbar_expect_tx(afull, (uint32_t)(j1 - j0) * kMnPair);
           const uint32_t adst = tc::smem_addr(sA + s * kMnSlot);
-          for (int q = 0; q < 4; ++q) {
-            // the quarter's first pixel (row offset within the tile, column)
-            const int p0 = 32 * q;
-            const int xx = NARROW ? p0 % w : x0 + p0, yy = NARROW ? y + p0 / w : y;
-            const uint32_t qd = adst + (uint32_t)q * kMnQuarter;
-            for (int j = j0; j < min(j1, npair); j += gb) {
-              const int tap = j / ngx, g = j - tap * ngx;
-              const int dy = tap / 3, dx = tap - 3 * dy;
-              tc::tma_load_5d(qd + (uint32_t)(j - j0) * kMnQRow, &xmap, 8 * (xx + dx - 1), g, yy + dy - 1, img, 0,
-                              afull);
-            }
-            if (npair < j1) tc::bulk_load(qd + (uint32_t)(npair - j0) * kMnQRow, &g_mn_ones, kMnQRow, afull);
+          for (int j = j0; j < min(j1, npair); j += gb) {
+            const int tap = j / ngx, g = j - tap * ngx;
+            const int dy = tap / 3, dx = tap - 3 * dy;
+            tc::tma_load_5d(adst + (uint32_t)(j - j0) * kMnPair, &xmap, 2 * (x0 + dx - 1), y + dy - 1, g, img, 0, afull);
           }
+          if (npair < j1) tc::bulk_load(adst + (uint32_t)(npair - j0) * kMnPair, &g_mn_ones, kMnPair, afull);
           ++na;
         }
       }
@@ -164,12 +154,11 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
     if (lane == 0) {
       // ---- MMA issuer ---------------------------------------------------------------------------
       const uint32_t idesc = tc::idesc_bf16_f32_mn(kTM, cout);
-      // MN-major without swizzle: LBO = 128 bytes (next 8 pixels), SBO = next 8 channels (the next
-      // pair of a quarter in A, the next 2 KB block in gz); descriptors advanced by start-field
-      // adds of byte offsets / 16.  K step ks (16 pixels): A quarter ks / 2, half ks % 2.
-      const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(sA), 128u, kMnQRow);
+      // MN-major without swizzle: LBO = 128 bytes (next 8 pixels), SBO = one pair (next 8
+      // channels); descriptors advanced by start-field adds of byte offsets / 16
+      const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(sA), 128u, kMnPair);
       const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(sB), 128u, kMnPair);
-      const uint32_t kstep = 256u >> 4;  // 16 pixels of gz
+      const uint32_t kstep = 256u >> 4;  // 16 pixels
       const uint32_t alo0 = (uint32_t)adesc0, ahi = (uint32_t)(adesc0 >> 32);
       const uint32_t blo0 = (uint32_t)bdesc0, bhi = (uint32_t)(bdesc0 >> 32);
       auto desc = [](uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | lo; };
@@ -179,7 +168,7 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
         const int bs = i & 1;
         if (!tc::mbar_wait_or_abort(tc::smem_addr(&bar[12 + bs]), (i >> 1) & 1, abort_flag)) ok = false;
         const uint32_t bd = blo0 + (((uint32_t)bs * bb) >> 4);
-        for (int m = 0; ok && m < mtiles; ++m, ++na) {
+        for (int m = mb0; ok && m < mb1; ++m, ++na) {
           const int s = na % slots;
           if (!tc::mbar_wait_or_abort(tc::smem_addr(&bar[s]), (na / slots) & 1, abort_flag)) {
             ok = false;
@@ -189,8 +178,7 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
           const uint32_t ad = alo0 + (((uint32_t)s * kMnSlot) >> 4);
 #pragma unroll
           for (int ks = 0; ks < 8; ++ks)
-            tc::mma_bf16(taddr + (uint32_t)m * cstride,
-                         desc(ad + (((uint32_t)(ks >> 1) * kMnQuarter + (uint32_t)(ks & 1) * 256u) >> 4), ahi),
+            tc::mma_bf16(taddr + (uint32_t)(m - mb0) * cstride, desc(ad + (uint32_t)ks * kstep, ahi),
                          desc(bd + (uint32_t)ks * kstep, bhi), idesc, (i > 0 || ks > 0) ? 1u : 0u);
           tc::mma_commit(tc::smem_addr(&bar[kMnMaxSlots + s]));  // A slot free
         }
@@ -205,10 +193,10 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
     const bool done = tc::mbar_wait(tc::smem_addr(&bar[16]), 0);
     tc::fence_after();
     const int Mpad = mtiles * kTM;
-    for (int k = 0; k < mtiles; ++k)
+    for (int k = mb0; k < mb1; ++k)
       for (int n0 = 0; n0 < cout; n0 += 16) {
         float v[16];
-        tc::tmem_ld16(taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)k * cstride + (uint32_t)n0, v);
+        tc::tmem_ld16(taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)(k - mb0) * cstride + (uint32_t)n0, v);
         if (done && !*abort_flag && mine > 0) {
           float4 *p = reinterpret_cast<float4 *>(part + ((int64_t)blockIdx.x * Mpad + 128 * k + 32 * qd + lane) * cout + n0);
 #pragma unroll
