@@ -1342,9 +1342,21 @@ int wgrad_tma_stages(int cin, int cout, int mtiles, uint32_t gstride) {
 #ifndef SC_WG_MN
 #define SC_WG_MN 1
 #endif
-int wgrad_mn_slots(int cout) {
+// ring slots of the MN-major weight-gradient kernel that fit next to its two gz tiles at `ctas`
+// CTAs per SM.  Rows of 128k pixels run two CTAs per SM (two or three slots each): the copies of
+// one CTA are served about one after another, so two CTAs stream nearly twice the bytes (2.25 ->
+// 2.08 ms per 16 x 256^2 step, e.g. 105 -> 70 us for a 32 -> 32 layer); narrow rows, with few tiles
+// per CTA and more TMEM chunks at two CTAs, keep one CTA per SM with more slots.
+#ifndef SC_WG_MN
+#define SC_WG_MN 1
+#endif
+#ifndef SC_WG_MN_CTAS
+#define SC_WG_MN_CTAS 2
+#endif
+int wgrad_mn_slots(int cout, int ctas) {
+  const int budget = ctas == 1 ? 227 * 1024 : 228 * 1024 / ctas - 1024;  // 1 KB per CTA is the system's
   for (int s = kMnMaxSlots; s >= 2; --s)
-    if (mn_smem_bytes(cout, s) <= 227 * 1024) return s;
+    if ((int)mn_smem_bytes(cout, s) <= budget) return s;
   return 0;
 }
 
@@ -1364,17 +1376,19 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
   const int64_t tiles = K / 128;
   const bool tma_ok = ly.kind == KIND_CONV && A.mode == 0 && A.ntaps == 9 && conv_rows_ok(A.w, A.h) && B.co == 0 &&
                       B.cs == ly.cout && A.cin * 9 == g.rows && tensor_map_encoder() != nullptr;
-  // rows narrower than 128 pixels: the MN-major kernel (its per-tap copies cost least there);
-  // wide rows: the transposing kernel, with >= SC_WG_MIN_TILES tiles per CTA
-  const int mslots = SC_WG_MN && tma_ok && A.w < 128 && tiles >= 64 ? wgrad_mn_slots(ly.cout) : 0;
-  const int rst = tma_ok && A.w >= 128 && tiles >= (int64_t)SC_WG_MIN_TILES * u->num_sms
+  // the MN-major kernel (tap-shifted copies by TMA, nothing transposed); with it switched off, the
+  // transposing kernel on rows of 128k pixels with >= SC_WG_MIN_TILES tiles per CTA
+  const int mctas =
+      A.w >= 128 && SC_WG_MN_CTAS > 1 && wgrad_mn_slots(ly.cout, SC_WG_MN_CTAS) > 0 ? SC_WG_MN_CTAS : 1;
+  const int mslots = SC_WG_MN && tma_ok && tiles >= 64 ? wgrad_mn_slots(ly.cout, mctas) : 0;
+  const int rst = tma_ok && mslots == 0 && A.w >= 128 && tiles >= (int64_t)SC_WG_MIN_TILES * u->num_sms
                       ? wgrad_tma_stages(A.cin, ly.cout, g.Mtiles, G.gstride)
                       : 0;
   int splits;
   if (mslots > 0) {
     const int n_img = G.n_img;
     const int ntiles = G.narrow ? n_img * (A.h / G.th) : n_img * A.h * (A.w / 128);
-    splits = std::min(ntiles, u->num_sms);
+    splits = std::min(ntiles, u->num_sms * mctas);
     if ((size_t)splits * Mpad * g.np > ly.part_floats)
       return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
     CUtensorMap xm, gm;
@@ -1398,7 +1412,7 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
       }
     }
     // 128-row blocks per CTA: as many accumulators as fit in TMEM, in balanced chunks
-    const int per = 512 / (int)wg_cstride(ly.cout);
+    const int per = 512 / mctas / (int)wg_cstride(ly.cout);
     const int nchunk = (g.Mtiles + per - 1) / per;
     const int mchunk = (g.Mtiles + nchunk - 1) / nchunk;
     auto kern = G.narrow ? k_wgrad_mn<true> : k_wgrad_mn<false>;
@@ -1764,7 +1778,8 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
     }
     int splits, ks;
     split_k(g.Mtiles, P[lvl], u->num_sms, &splits, &ks);
-    splits = std::max(splits, u->num_sms);  // the TMA weight-gradient kernel: one split per SM
+    // the TMA weight-gradient kernels: one split per CTA, up to SC_WG_MN_CTAS per SM
+    splits = std::max(splits, u->num_sms * SC_WG_MN_CTAS);
     size_t need = (size_t)splits * g.Mtiles * kTM * g.np;
     if (i == kOutLayer) need = (size_t)2 * u->num_sms * kOutParts;  // k_out_wgrad's block partials
     ly.part_off = wpart;
