@@ -1,8 +1,10 @@
-// tc.cuh -- thin wrappers over the sm_100-family tensor-core (tcgen05) and mbarrier PTX used by
-// the U-Net kernels.  Operands live in shared memory in the canonical K-major layout without
+// tc.cuh -- thin wrappers over the sm_100-family tensor-core (tcgen05), mbarrier and TMA PTX used
+// by the U-Net kernels.  Operands live in shared memory in the canonical layouts without
 // swizzling: an R x K BF16 tile is made of 8x8 "core matrices" (8 rows of 16 bytes, 128 contiguous
-// bytes); core matrix (r/8, k/8) sits at (r/8)*SBO + (k/8)*LBO.  Accumulators live in tensor
-// memory (TMEM): row i of a 128-row tile is TMEM lane i, column j is TMEM column j (FP32).
+// bytes), K-major (a 16-byte row holds 8 K-consecutive elements of one of the R rows) or MN-major
+// (a 16-byte row holds 8 R-consecutive elements at one K); in both, core matrix (r/8, k/8) sits at
+// (r/8)*SBO + (k/8)*LBO.  Accumulators live in tensor memory (TMEM): row i of a 128-row tile is
+// TMEM lane i, column j is TMEM column j (FP32).
 #pragma once
 #include <cstdint>
 
@@ -134,17 +136,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(mbar)
                : "memory");
-}
-
-// four 8x8 BF16 matrices from shared memory, transposed: lane L supplies the address of row L % 8
-// of matrix L / 8 (16 bytes); register i of lane L receives elements (2 (L % 4), 2 (L % 4) + 1) of
-// row L / 4 of the transpose of matrix i
-// (no memory clobber: the caller orders it against writes of the source with its own barriers,
-// which lets several of these be in flight at once)
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
 }
 
 // make generic-proxy shared-memory writes visible to the tensor cores (async proxy)

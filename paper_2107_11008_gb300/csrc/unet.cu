@@ -1,8 +1,7 @@
 // unet.cu -- the BF16 U-Net denoiser (include/sc_unet.h): forward, L1 + SSIM loss, backward,
 // Adam, all on the GPU.  Every 3x3 convolution (forward, data gradient, weight gradient) and the
-// transposed convolutions run on the tensor cores (tcgen05: the TMA kernels of unet_conv.cuh,
-// unet_wgrad_mn.cuh and unet_wgrad.cuh, else the gathering GEMM of unet_gemm.cuh); the 1x1 output
-// layer (HBM-bound),
+// transposed convolutions run on the tensor cores (tcgen05: the TMA kernels of unet_conv.cuh and
+// unet_wgrad_mn.cuh, else the gathering GEMM of unet_gemm.cuh); the 1x1 output layer (HBM-bound),
 // pooling, the loss, the weight-gradient reduction and Adam are plain CUDA.
 #include <algorithm>
 #include <climits>
@@ -1327,29 +1326,11 @@ int run_loss(sc_ctx *c, sc_unet *u, const float *pred, const float *target, int 
   return SC_OK;
 }
 
-#ifndef SC_WG_MIN_TILES
-#define SC_WG_MIN_TILES 2
-#endif
-// raw stages of the TMA weight-gradient kernel that fit (0: it does not fit)
-int wgrad_tma_stages(int cin, int cout, int mtiles, uint32_t gstride) {
-  if ((uint32_t)mtiles * wg_cstride(cout) > 512u) return 0;
-  if (wg_smem_bytes(cin, cout, 2, gstride) <= 227 * 1024) return 2;
-  if (wg_smem_bytes(cin, cout, 1, gstride) <= 227 * 1024) return 1;
-  return 0;
-}
-
-// ring slots of the MN-major weight-gradient kernel that fit next to its two gz tiles
-#ifndef SC_WG_MN
-#define SC_WG_MN 1
-#endif
 // ring slots of the MN-major weight-gradient kernel that fit next to its two gz tiles at `ctas`
 // CTAs per SM.  Rows of 128k pixels run two CTAs per SM (two or three slots each): the copies of
 // one CTA are served about one after another, so two CTAs stream nearly twice the bytes (2.25 ->
 // 2.08 ms per 16 x 256^2 step, e.g. 105 -> 70 us for a 32 -> 32 layer); narrow rows, with few tiles
 // per CTA and more TMEM chunks at two CTAs, keep one CTA per SM with more slots.
-#ifndef SC_WG_MN
-#define SC_WG_MN 1
-#endif
 #ifndef SC_WG_MN_CTAS
 #define SC_WG_MN_CTAS 2
 #endif
@@ -1362,8 +1343,8 @@ int wgrad_mn_slots(int cout, int ctas) {
 
 // weight gradient of one layer: A (rows = (tap, c) | c, + ones row), B (rows = output channels),
 // contracted over the pixels, reduced deterministically into the flat gradient.  3x3 layers on
-// rows of 128k pixels (or 128 / w whole rows) take a TMA kernel (x: the layer input, gz: its
-// output gradient): the MN-major one where its accumulators fit in TMEM, else the transposing one.
+// rows of 128k pixels (or 128 / w whole rows) with at least 64 tiles take the MN-major TMA kernel
+// (x: the layer input, gz: its output gradient), everything else the gathering GEMM.
 int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, int64_t K, cudaStream_t ws,
           RedTable &red, int &red_blocks) {
   const char *where = "sc_unet wgrad";
@@ -1371,19 +1352,12 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
   const Wgrad g = wgrad_shape(ly);
   const int Mpad = g.Mtiles * kTM;
   const ConvGeo G = conv_geo((int)(K / ((int64_t)A.h * A.w)), A.h, A.w);
-  // the persistent TMA kernel pays a pipeline fill per CTA: worth it with >= SC_WG_MIN_TILES
-  // tiles per CTA
   const int64_t tiles = K / 128;
   const bool tma_ok = ly.kind == KIND_CONV && A.mode == 0 && A.ntaps == 9 && conv_rows_ok(A.w, A.h) && B.co == 0 &&
                       B.cs == ly.cout && A.cin * 9 == g.rows && tensor_map_encoder() != nullptr;
-  // the MN-major kernel (tap-shifted copies by TMA, nothing transposed); with it switched off, the
-  // transposing kernel on rows of 128k pixels with >= SC_WG_MIN_TILES tiles per CTA
   const int mctas =
       A.w >= 128 && SC_WG_MN_CTAS > 1 && wgrad_mn_slots(ly.cout, SC_WG_MN_CTAS) > 0 ? SC_WG_MN_CTAS : 1;
-  const int mslots = SC_WG_MN && tma_ok && tiles >= 64 ? wgrad_mn_slots(ly.cout, mctas) : 0;
-  const int rst = tma_ok && mslots == 0 && A.w >= 128 && tiles >= (int64_t)SC_WG_MIN_TILES * u->num_sms
-                      ? wgrad_tma_stages(A.cin, ly.cout, g.Mtiles, G.gstride)
-                      : 0;
+  const int mslots = tma_ok && tiles >= 64 ? wgrad_mn_slots(ly.cout, mctas) : 0;
   int splits;
   if (mslots > 0) {
     const int n_img = G.n_img;
@@ -1418,35 +1392,6 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
     auto kern = G.narrow ? k_wgrad_mn<true> : k_wgrad_mn<false>;
     kern<<<dim3(splits, nchunk), kMnThreads, smem, ws>>>(xm, gm, A.cin, ly.cout, g.Mtiles, mchunk, mslots, gb, G,
                                                          part, sc::ctx_status(c));
-    UCHK(cudaGetLastError());
-  } else if (rst > 0) {
-    const int n_img = G.n_img;
-    const int ntiles = G.narrow ? n_img * (A.h / G.th) : n_img * A.h * (A.w / 128);
-    splits = std::min(ntiles, u->num_sms);
-    if ((size_t)splits * Mpad * g.np > ly.part_floats)
-      return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
-    CUtensorMap xm, gm;
-    const bool xok = G.narrow ? encode_rb_map(&xm, A.src, A.co, A.cin, A.cs, A.w, A.h, n_img, false, A.w, G.th + 2)
-                              : encode_rb_map(&xm, A.src, A.co, A.cin, A.cs, A.w, A.h, n_img, true, kHaloW, kHaloH);
-    if (!xok ||
-        !encode_rb_map(&gm, B.src, 0, ly.cout, ly.cout, A.w, A.h, n_img, true, G.narrow ? A.w : 128, G.narrow ? G.th : 1))
-      return fail(c, SC_ERR_CUDA, "sc_unet wgrad: tensor map encoding failed");
-    const int smem = (int)wg_smem_bytes(A.cin, ly.cout, rst, G.gstride);
-    static bool attr[kMaxDev] = {};
-    static std::mutex mu;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    {
-      std::lock_guard<std::mutex> lk(mu);
-      if (dev >= 0 && dev < kMaxDev && !attr[dev]) {
-        UCHK(cudaFuncSetAttribute(k_wgrad_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        UCHK(cudaFuncSetAttribute(k_wgrad_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr[dev] = true;
-      }
-    }
-    auto kern = G.narrow ? k_wgrad_tma<true> : k_wgrad_tma<false>;
-    kern<<<splits, kWgThreads, smem, ws>>>(xm, gm, A.cin, ly.cout, g.Mtiles, rst, G, part,
-                                                           sc::ctx_status(c));
     UCHK(cudaGetLastError());
   } else {
     int ks;

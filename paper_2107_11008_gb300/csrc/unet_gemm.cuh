@@ -1,8 +1,8 @@
 // unet_gemm.cuh -- the general gathering tensor-core GEMM of the U-Net denoiser, plus the layout
-// helpers, loaders and epilogue functors the TMA kernels (unet_conv.cuh, unet_wgrad.cuh) share.
-// It serves the contractions the TMA kernels do not: the transposed convolutions' data gradient,
-// the weight gradients of the transposed and the deepest 3x3 layers, and convolutions on rows that
-// fit neither TMA tiling.
+// helpers, loaders and epilogue functors the TMA kernels (unet_conv.cuh, unet_wgrad_mn.cuh) share.
+// It serves the contractions the TMA kernels do not: the transposed convolutions' data gradient
+// and weight gradient, the weight gradients of 3x3 layers with fewer than 64 pixel tiles, and
+// convolutions on rows that fit neither TMA tiling.
 //
 //   D[m][n] = sum_k A(m, k) * B(n, k),   m in a 128-row tile, n < N <= 256, k in a K range
 //

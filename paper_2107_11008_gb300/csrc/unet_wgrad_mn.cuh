@@ -25,7 +25,7 @@
 // (K = 16) reads 16 (or cout / 8) pairs x 256 bytes from its start, which moves 256 bytes per K
 // step, so every read stays inside its own 32 KB A slot or gz tile.
 #pragma once
-#include "unet_wgrad.cuh"
+#include "unet_conv.cuh"
 
 namespace sc {
 namespace unet {
@@ -34,6 +34,8 @@ constexpr uint32_t kMnPair = 128 * 16;      // one (tap, channel group) pair: 12
 constexpr uint32_t kMnSlot = 16 * kMnPair;  // one 128-row A block
 constexpr int kMnThreads = 192;             // producer, MMA issuer, 4 epilogue warps
 constexpr int kMnMaxSlots = 6;
+// TMEM columns between the accumulators of consecutive 128-row blocks (cout FP32 columns each)
+__host__ __device__ constexpr uint32_t wg_cstride(int cout) { return cout <= 32 ? 32u : (cout <= 64 ? 64u : 128u); }
 
 // the bias row's block: channel 0 of every pixel is one (BF16 0x3F80), the other channels zero
 struct MnOnes {

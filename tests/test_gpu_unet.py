@@ -326,10 +326,10 @@ def _wgrad_ref(x, gz):
 def test_full_size_step_weight_gradients(ctx, n, h, w):
     """The training workload (16 x 256^2) and a smaller one: the split-K weight gradients of the
     output layer and of every 3x3 convolution (all taps, channels and outputs, and the biases),
-    recomputed over every pixel of each level from the GPU's own BF16 operands.  At 16 x 256^2,
-    levels 0-1 (rows of 256 and 128 pixels) take the transposing TMA weight-gradient kernel and
-    levels 2-3 the MN-major one (level 3 and dec2 conv 1 in two or three TMEM chunks); at 8 x 128^2
-    levels 1-2 take the MN-major kernel."""
+    recomputed over every pixel of each level from the GPU's own BF16 operands.  At 16 x 256^2 the
+    3x3 layers of every level take the MN-major TMA weight-gradient kernel (levels 0-1 at two CTAs
+    per SM, level 3 and dec2 conv 1 in two or three TMEM chunks); at 8 x 128^2 levels 0-2 do and
+    level 3 (16 tiles) takes the gathering GEMM."""
     rng = np.random.default_rng(9)
     x = rng.random((n, h, w, 11)).astype(np.float32)
     t = rng.random((n, h, w, 3)).astype(np.float32)
