@@ -191,12 +191,12 @@ UNET_CHANS = (32, 48, 64, 128)
 UNET_TRAIN_LAUNCHES = 23 + 3 + 41 + 1
 UNET_FWD_LAUNCHES = 23
 # DRAM bytes of one training step (all its kernels, dram__bytes_read.sum + dram__bytes_write.sum
-# summed over launches 1-65 = the first step; launch 0 is the parameter refresh), from one ncu
+# summed over launches 1-68 = the first step; launch 0 is the parameter refresh), from one ncu
 # capture of these kernel versions:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
-#       -k regex:"k_(gemm|conv_tma|wgrad_tma|ssim|pool|adam|wgrad_reduce|loss_final|pack_input|out_)" -c 66 \
-#       python bench.py --workload unet_train --steps 1 --warmup 3 --no-cpu-baseline
-UNET_STEP_DRAM_BYTES = 3.62e9
+#       -k regex:"k_(gemm|conv_tma|wgrad_mn|ssim|pool|adam|wgrad_reduce|loss_final|pack_input|out_)" -c 70 \
+#       --csv python bench.py --workload unet_train --steps 1 --warmup 3 --no-cpu-baseline
+UNET_STEP_DRAM_BYTES = 3.97e9
 
 
 def unet_macs(h, w, in_ch=11, out_ch=3):
