@@ -145,10 +145,11 @@ __global__ void k_pool_back(const float *gp, int N, const bf16 *e, int ecs, int 
   const int64_t total = (int64_t)n * ho * wo * groups;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= total) return;
-  const int x = (int)(i % wo);
-  const int64_t t = i / wo;
-  const int g = (int)(t % groups);
-  const int64_t ro = t / groups;  // img * ho + y
+  // channel group fastest: the lanes of a warp read whole 128-byte rows of the FP32 tensors
+  const int g = (int)(i % groups);
+  const int64_t t = i / groups;
+  const int x = (int)(t % wo);
+  const int64_t ro = t / wo;  // img * ho + y
   const int64_t ri = ro / ho * (2 * ho) + 2 * (ro % ho);
   const int c = 8 * g;
   float gv[8];
@@ -370,6 +371,7 @@ __device__ __forceinline__ void add4(float4 &a, const float4 &b) {
 struct RedSeg {
   int64_t part_off, w_off, b_off;  // floats into the workspace / into the flat gradient
   int splits, Mpad, np, rows, kind, cout, cin, cin_p, first_block;
+  int col, cgb, nu, cpb, ncopy;  // conv rows in the MN-major kernel's column order (col = 1)
 };
 constexpr int kMaxRedSegs = 20;
 struct RedTable {
@@ -423,7 +425,19 @@ __global__ void __launch_bounds__(kRedEntries *kRedGroups) k_wgrad_reduce(const 
         gb[nq] = t;
         continue;
       }
-      const int tap = r / cin_p, c = r - tap * cin_p;
+      int tap, c;
+      if (S.col) {
+        // pair j = r / 8 of block j / 16: copy k = block * cpb + (j % 16) / (3 cgb), then (group, dy)
+        const int j = r >> 3, m = j >> 4, p = j & 15, kk = p / (3 * S.cgb), rem = p - kk * 3 * S.cgb;
+        const int k = m * S.cpb + kk;
+        if (kk >= S.cpb || k >= S.ncopy) continue;  // padding of a block
+        const int gi = rem / 3, dy = rem - 3 * gi, dx = k / S.nu, un = k - dx * S.nu;
+        tap = 3 * dy + dx;
+        c = 8 * (un * S.cgb + gi) + (r & 7);
+      } else {
+        tap = r / cin_p;
+        c = r - tap * cin_p;
+      }
       if (c < cin) gw[((int64_t)nq * 9 + tap) * cin + c] = t;
     } else {  // KIND_UP
       if (r == rows) {
@@ -1358,18 +1372,23 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
   const int mctas =
       A.w >= 128 && SC_WG_MN_CTAS > 1 && wgrad_mn_slots(ly.cout, SC_WG_MN_CTAS) > 0 ? SC_WG_MN_CTAS : 1;
   const int mslots = tma_ok && tiles >= 64 ? wgrad_mn_slots(ly.cout, mctas) : 0;
+  // the MN-major kernel's row layout (columns on rows of 128k pixels with at most 48 input
+  // channels) sets the partials' rows
+  const MnLayout L = mn_layout(A.cin, A.w >= 128 && A.cin <= 48);
+  const int seg_Mpad = mslots > 0 ? L.mtiles * kTM : Mpad;
+  const int seg_rows = mslots > 0 ? 8 * L.jones : g.rows;
   int splits;
   if (mslots > 0) {
     const int n_img = G.n_img;
     const int ntiles = G.narrow ? n_img * (A.h / G.th) : n_img * A.h * (A.w / 128);
     splits = std::min(ntiles, u->num_sms * mctas);
-    if ((size_t)splits * Mpad * g.np > ly.part_floats)
+    if ((size_t)splits * seg_Mpad * g.np > ly.part_floats)
       return fail(c, SC_ERR_INVALID_ARG, "sc_unet: weight-gradient workspace too small");
     CUtensorMap xm, gm;
-    // x: gb channel groups of a tap per copy (a tap's shift is an element offset); gz: the whole tile
-    const int gb = std::gcd(A.cin / 8, 16);
+    // x: a column copy (3 rows of L.gb channel groups) or L.gb groups of one tap (a tap's shift is an
+    // element offset); gz: the whole tile
     const int bw = G.narrow ? A.w : 128;
-    if (!encode_px_map(&xm, A.src, A.co, A.cin, A.cs, A.w, A.h, n_img, bw, G.th, gb) ||
+    if (!encode_px_map(&xm, A.src, A.co, A.cin, A.cs, A.w, A.h, n_img, bw, L.col ? 3 : G.th, L.gb) ||
         !encode_px_map(&gm, B.src, 0, ly.cout, ly.cout, A.w, A.h, n_img, bw, G.th, ly.cout / 8))
       return fail(c, SC_ERR_CUDA, "sc_unet wgrad: tensor map encoding failed");
     const int smem = (int)mn_smem_bytes(ly.cout, mslots);
@@ -1387,10 +1406,10 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
     }
     // 128-row blocks per CTA: as many accumulators as fit in TMEM, in balanced chunks
     const int per = 512 / mctas / (int)wg_cstride(ly.cout);
-    const int nchunk = (g.Mtiles + per - 1) / per;
-    const int mchunk = (g.Mtiles + nchunk - 1) / nchunk;
+    const int nchunk = (L.mtiles + per - 1) / per;
+    const int mchunk = (L.mtiles + nchunk - 1) / nchunk;
     auto kern = G.narrow ? k_wgrad_mn<true> : k_wgrad_mn<false>;
-    kern<<<dim3(splits, nchunk), kMnThreads, smem, ws>>>(xm, gm, A.cin, ly.cout, g.Mtiles, mchunk, mslots, gb, G,
+    kern<<<dim3(splits, nchunk), kMnThreads, smem, ws>>>(xm, gm, A.cin, ly.cout, L.mtiles, mchunk, mslots, L, G,
                                                          part, sc::ctx_status(c));
     UCHK(cudaGetLastError());
   } else {
@@ -1412,15 +1431,20 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
   sg.w_off = ly.w_off;
   sg.b_off = ly.b_off;
   sg.splits = splits;
-  sg.Mpad = Mpad;
+  sg.Mpad = seg_Mpad;
   sg.np = g.np;
-  sg.rows = g.rows;
+  sg.rows = seg_rows;
+  sg.col = mslots > 0 ? L.col : 0;
+  sg.cgb = L.gb;
+  sg.nu = L.nu;
+  sg.cpb = L.cpb;
+  sg.ncopy = L.ncopy;
   sg.kind = ly.kind;
   sg.cout = ly.cout;
   sg.cin = ly.cin;
   sg.cin_p = ly.cin_p;
   sg.first_block = red_blocks;
-  red_blocks += (int)(((int64_t)(g.rows + 1) * g.np + kRedBlockEntries - 1) / kRedBlockEntries);
+  red_blocks += (int)(((int64_t)(seg_rows + 1) * g.np + kRedBlockEntries - 1) / kRedBlockEntries);
   UCHK(cudaGetLastError());
   return SC_OK;
 }
@@ -1725,7 +1749,9 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
     split_k(g.Mtiles, P[lvl], u->num_sms, &splits, &ks);
     // the TMA weight-gradient kernels: one split per CTA, up to SC_WG_MN_CTAS per SM
     splits = std::max(splits, u->num_sms * SC_WG_MN_CTAS);
-    size_t need = (size_t)splits * g.Mtiles * kTM * g.np;
+    // the MN-major kernel's column layout may take more 128-row blocks than the plain one
+    const int mt = ly.kind == KIND_CONV ? std::max(g.Mtiles, mn_layout(ly.cin_p, true).mtiles) : g.Mtiles;
+    size_t need = (size_t)splits * mt * kTM * g.np;
     if (i == kOutLayer) need = (size_t)2 * u->num_sms * kOutParts;  // k_out_wgrad's block partials
     ly.part_off = wpart;
     ly.part_floats = need;

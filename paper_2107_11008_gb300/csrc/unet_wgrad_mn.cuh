@@ -10,11 +10,21 @@
 // slot holds one 128-row block of A: 16 pairs (tap, channel group), tap-major, each the tile's 128
 // pixels shifted by the tap's offset (2 KB, pairs 2 KB apart).  The tensors are viewed with 8-byte
 // elements (half a pixel) as (2 w, rows, groups, images): a one-pixel shift is an element offset of
-// 2 (16 bytes), and one TMA copy (zeros outside the image) brings gb consecutive pairs of one tap
-// whole, gb = gcd(cin / 8, 16) so that no copy straddles two blocks; the cost of a copy hardly
-// depends on its size, so few large copies matter more than anything else here.  The bias row
-// 9 cin is a pair whose channel 0 is one, copied from a constant; the gz tile is one copy (one 2 KB
-// block per group of 8 output channels).  One thread issues the MMAs; the accumulators of all
+// 2 (16 bytes), and one TMA copy (zeros outside the image) brings several pairs whole.  A CTA's
+// copies are served about one after another, at a cost that grows slowly with their size, so few
+// large copies matter more than anything else here:
+//  * columns (rows of 128k pixels, at most 48 input channels): one copy brings, for one dx and gb
+//    channel groups, the three rows dy = 0..2 ((256, 3, gb) box: pairs ordered (group, dy)); a
+//    block holds cpb = 16 / (3 gb) such copies (gb = 4, 2 or 1, so 12, 12 or 15 pairs; the rest
+//    of the block is padding, whose accumulator rows are never read), blocks in copy order k = dx *
+//    (cin / 8 / gb) + unit.  With more channels the padding costs more blocks (MMAs, partials,
+//    TMEM chunks) than the fewer copies save (measured: 64 channels 89.6 -> 98.1 us);
+//  * tap-major (all other layers): pairs ordered (tap, group), one copy brings gb = gcd(cin / 8,
+//    16) pairs of one tap (th rows of w pixels each), so that no copy straddles two blocks.
+// The bias row is a pair whose channel 0 is one, copied from a constant (the first pair after the
+// data: in the last block's padding for columns, pair 9 cin / 8 for the tap-major order); the gz
+// tile is one copy (one 2 KB block per group of 8 output channels).  mn_layout() gives both
+// layouts' block counts and the bias pair for the host, the kernel and the reduce.  One thread issues the MMAs; the accumulators of all
 // 128-row blocks (cout columns each, 32/64/128 apart) stay in TMEM across the CTA's contiguous
 // range of tiles, and at the end the epilogue warps write them as this CTA's partial sums
 // ([split][128 mtiles][cout], the layout k_wgrad_reduce sums in a fixed order).  Where all blocks'
@@ -48,23 +58,62 @@ __host__ __device__ constexpr MnOnes mn_ones() {
 }
 __device__ __align__(128) const MnOnes g_mn_ones = mn_ones();
 
+// layout of the A rows: blocks (mtiles), the bias pair, and for columns the copy shape
+struct MnLayout {
+  int col;     // 1: columns (rows of 128k pixels), 0: tap-major
+  int gb;      // channel groups per copy
+  int nu;      // column copies per dx (cin / 8 / gb)
+  int cpb;     // column copies per block
+  int ncopy;   // column copies (3 nu)
+  int mtiles;  // 128-row blocks
+  int jones;   // the bias pair (its channel 0 is D row 8 jones)
+};
+__host__ __device__ inline MnLayout mn_layout(int cin, bool col) {
+  MnLayout L;
+  const int ng = cin / 8;
+  L.col = col ? 1 : 0;
+  if (col) {
+    L.gb = ng % 4 == 0 ? 4 : (ng % 2 == 0 ? 2 : 1);
+    L.nu = ng / L.gb;
+    L.cpb = 16 / (3 * L.gb);
+    L.ncopy = 3 * L.nu;
+    L.mtiles = (L.ncopy + L.cpb - 1) / L.cpb;
+    L.jones = 16 * (L.mtiles - 1) + (L.ncopy - (L.mtiles - 1) * L.cpb) * 3 * L.gb;
+  } else {
+    int g = ng, b = 16;  // gcd(ng, 16)
+    while (b) {
+      const int r = g % b;
+      g = b;
+      b = r;
+    }
+    L.gb = g;
+    L.nu = L.cpb = L.ncopy = 0;
+    L.jones = 9 * ng;
+    L.mtiles = (8 * L.jones + 1 + 127) / 128;
+  }
+  return L;
+}
+
 __host__ __device__ constexpr uint32_t mn_b_bytes(int cout) { return align_up((uint32_t)(cout / 8) * kMnPair, 1024); }
 __host__ __device__ constexpr size_t mn_smem_bytes(int cout, int slots) {
   return (size_t)slots * kMnSlot + 2 * mn_b_bytes(cout) + 256;
 }
 
 // xmap: the layer input, gmap: its output gradient, both as (2 w, h, groups, images, 1) of 8-byte
-// elements with boxes (256 or 2 w, 1 or th, gb or cout / 8, 1, 1).  cin, cout multiples of 8, gb a
-// divisor of both cin / 8 and 16; mtiles = ceil((9 cin + 1) / 128).
+// elements with boxes (256, 3, L.gb, 1, 1) for columns or (256 or 2 w, 1 or th, L.gb, 1, 1), and
+// (256 or 2 w, 1 or th, cout / 8, 1, 1).  cin, cout multiples of 8; L = mn_layout(cin, columns)
+// with columns only on rows of 128k pixels; mtiles = L.mtiles.
 template <bool NARROW>
 __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constant__ CUtensorMap xmap,
                                                               const __grid_constant__ CUtensorMap gmap, int cin,
                                                               int cout, int mtiles, int mchunk, int slots,
-                                                              int gb, ConvGeo G, float *part, unsigned *status) {
+                                                              MnLayout L, ConvGeo G, float *part,
+                                                              unsigned *status) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ngx = cin / 8, ngz = cout / 8;
-  const int npair = 9 * ngx;  // data blocks; block npair carries the bias row
+  const int npair = 9 * ngx;  // data pairs (tap-major: pair npair carries the bias row)
+  const int gb = L.gb;
   const uint32_t bb = mn_b_bytes(cout);
   const int h = G.h, w = G.w;
   uint8_t *sA = sm;
@@ -131,10 +180,24 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
             stop = true;
             break;
           }
-          const int j0 = 16 * m, j1 = min(j0 + 16, npair + 1);
           const uint32_t afull = tc::smem_addr(&bar[s]);
-          tc::mbar_expect_tx(afull, (uint32_t)(j1 - j0) * kMnPair);
           const uint32_t adst = tc::smem_addr(sA + s * kMnSlot);
+          if (L.col) {
+            // columns: copies k0..k1-1 of 3 gb pairs each, then (last block) the bias pair
+            const int k0 = m * L.cpb, k1 = min(k0 + L.cpb, L.ncopy);
+            const bool last = m == mtiles - 1;
+            tc::mbar_expect_tx(afull, ((uint32_t)(k1 - k0) * 3u * (uint32_t)gb + (last ? 1u : 0u)) * kMnPair);
+            for (int k = k0; k < k1; ++k) {
+              const int dx = k / L.nu, un = k - dx * L.nu;
+              tc::tma_load_5d(adst + (uint32_t)((k - k0) * 3 * gb) * kMnPair, &xmap, 2 * (x0 + dx - 1), y - 1, un * gb,
+                              img, 0, afull);
+            }
+            if (last) tc::bulk_load(adst + (uint32_t)((k1 - k0) * 3 * gb) * kMnPair, &g_mn_ones, kMnPair, afull);
+            ++na;
+            continue;
+          }
+          const int j0 = 16 * m, j1 = min(j0 + 16, npair + 1);
+          tc::mbar_expect_tx(afull, (uint32_t)(j1 - j0) * kMnPair);
           for (int j = j0; j < min(j1, npair); j += gb) {
             const int tap = j / ngx, g = j - tap * ngx;
             const int dy = tap / 3, dx = tap - 3 * dy;
