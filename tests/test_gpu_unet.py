@@ -158,9 +158,12 @@ def test_forward_end_to_end_vs_fp64_oracle(ctx):
     N.net.close()
 
 
-def test_ssim_l1_loss_kernel(ctx):
+@pytest.mark.parametrize("shape", [(2, 40, 48), (1, 77, 70)], ids=["40x48", "77x70"])
+def test_ssim_l1_loss_kernel(ctx, shape):
+    """Loss and gradient against the oracle; 77 x 70 spans several ragged row and column strips of
+    both column-sweep kernels (67 window rows: strips of 32, 32, 3)."""
     rng = np.random.default_rng(5)
-    p = rng.random((2, 40, 48, 3))
+    p = rng.random(shape + (3,))
     t = np.clip(p + 0.1 * rng.normal(size=p.shape), 0, None)
     loss, grad = D.ssim_l1_loss(ctx, _dev(p), _dev(t))
     torch.cuda.synchronize()
