@@ -401,7 +401,14 @@ __global__ void __launch_bounds__(kRedEntries *kRedGroups) k_wgrad_reduce(const 
   // the bias of a transposed conv sums its four (a, e) column blocks of the ones row (cout is a
   // multiple of 4, so the 4 entries are all below cout or all at or above it)
   float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  if (valid) {
+  // padding rows of a column-ordered block were never written: skip them (r == rows, the bias row,
+  // is not padding)
+  bool pad = false;
+  if (S.col && r < rows) {
+    const int p = (r >> 3) & 15, kk = p / (3 * S.cgb);
+    pad = kk >= S.cpb || (r >> 7) * S.cpb + kk >= S.ncopy;
+  }
+  if (valid && !pad) {
     if (kind == KIND_UP && r == rows) {
       if (n < cout)
         for (int ae = 0; ae < 4; ++ae) add4(v, split_sum4(part, splits, Mpad, np, r, ae * cout + n, g));

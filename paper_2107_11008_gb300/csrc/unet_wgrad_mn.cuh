@@ -258,16 +258,21 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
     const bool done = tc::mbar_wait(tc::smem_addr(&bar[16]), 0);
     tc::fence_after();
     const int Mpad = mtiles * kTM;
-    for (int k = mb0; k < mb1; ++k)
+    for (int k = mb0; k < mb1; ++k) {
+      // rows of a column block past its copies and its bias pair are padding: not written (the
+      // reduce never reads them)
+      const int pair = (32 * qd + lane) >> 3;
+      const int used = L.col ? (min(L.cpb, L.ncopy - k * L.cpb) * 3 * gb + (k == mtiles - 1 ? 1 : 0)) : 16;
       for (int n0 = 0; n0 < cout; n0 += 16) {
         float v[16];
         tc::tmem_ld16(taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)(k - mb0) * cstride + (uint32_t)n0, v);
-        if (done && !*abort_flag && mine > 0) {
+        if (done && !*abort_flag && mine > 0 && pair < used) {
           float4 *p = reinterpret_cast<float4 *>(part + ((int64_t)blockIdx.x * Mpad + 128 * k + 32 * qd + lane) * cout + n0);
 #pragma unroll
           for (int j = 0; j < 4; ++j) p[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         }
       }
+    }
   }
   tc::fence_before();
   __syncthreads();
