@@ -1114,6 +1114,23 @@ bool encode_px_map(CUtensorMap *map, const bf16 *src, int co, int channels, int 
                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The output gradient of a 2x2 stride-2 transposed conv (row-blocked BF16, cs channels, rows of wc
+// pixels, hc rows per image) seen as (2 half-pixels, pixel parity e, parent column, row, channel
+// group) with 8-byte elements: one copy with e and the row parity a fixed brings, for bw parent
+// columns of th parent rows (rows 2y + a, a row stride of 2), the children (2y + a, 2x + e) of
+// box_g channel groups, each group's 128 children contiguous.
+bool encode_parity_map(CUtensorMap *map, const bf16 *src, int channels, int cs, int wc, int hc, int n, int bw, int th,
+                       int box_g) {
+  const cuuint64_t dims[5] = {2, 2, (cuuint64_t)(wc / 2), (cuuint64_t)n * hc, (cuuint64_t)(channels / 8)};
+  const cuuint64_t strides[4] = {16, 32, (cuuint64_t)cs * wc * 2, (cuuint64_t)wc * 16};
+  const cuuint32_t box[5] = {2, 1, (cuuint32_t)bw, (cuuint32_t)(th > 1 ? 2 * th : 1), (cuuint32_t)box_g};
+  const cuuint32_t estr[5] = {1, 1, 1, (cuuint32_t)(th > 1 ? 2 : 1), 1};
+  auto enc = tensor_map_encoder();
+  return enc && enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<bf16 *>(src), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // groups of 8 input channels per A stage (0: the layer does not fit in 227 KB next to its
 // resident weights).  Among the even divisors of cin / 8 that fit, the one that lets the most CTAs
 // share an SM (shared memory, TMEM, at most 4 by registers) when SC_CONV_MAXOCC, else the largest;
@@ -1355,10 +1372,10 @@ int run_loss(sc_ctx *c, sc_unet *u, const float *pred, const float *target, int 
 #ifndef SC_WG_MN_CTAS
 #define SC_WG_MN_CTAS 2
 #endif
-int wgrad_mn_slots(int cout, int ctas) {
+int wgrad_mn_slots(int cout, int ctas, int slack = 0) {
   const int budget = ctas == 1 ? 227 * 1024 : 228 * 1024 / ctas - 1024;  // 1 KB per CTA is the system's
   for (int s = kMnMaxSlots; s >= 2; --s)
-    if ((int)mn_smem_bytes(cout, s) <= budget) return s;
+    if ((int)mn_smem_bytes(cout, s, slack) <= budget) return s;
   return 0;
 }
 
@@ -1376,12 +1393,16 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
   const int64_t tiles = K / 128;
   const bool tma_ok = ly.kind == KIND_CONV && A.mode == 0 && A.ntaps == 9 && conv_rows_ok(A.w, A.h) && B.co == 0 &&
                       B.cs == ly.cout && A.cin * 9 == g.rows && tensor_map_encoder() != nullptr;
-  const int mctas =
-      A.w >= 128 && SC_WG_MN_CTAS > 1 && wgrad_mn_slots(ly.cout, SC_WG_MN_CTAS) > 0 ? SC_WG_MN_CTAS : 1;
-  const int mslots = tma_ok && tiles >= 64 ? wgrad_mn_slots(ly.cout, mctas) : 0;
+  // the transposed conv (A: its input at the parents' resolution; B: the children's gradients)
+  const bool up_ok = ly.kind == KIND_UP && A.mode == 0 && A.ntaps == 1 && conv_rows_ok(A.w, A.h) && B.co == 0 &&
+                     B.cs == ly.cout && A.cin == g.rows && 4 * ly.cout <= 256 && tensor_map_encoder() != nullptr;
+  const int Nmn = up_ok ? 4 * ly.cout : ly.cout;  // accumulator columns
+  const int mctas = A.w >= 128 && SC_WG_MN_CTAS > 1 && wgrad_mn_slots(Nmn, SC_WG_MN_CTAS) > 0 ? SC_WG_MN_CTAS : 1;
+  const int slack = up_ok && A.w < 128 ? 1 : 0;
+  const int mslots = (tma_ok || up_ok) && tiles >= 64 ? wgrad_mn_slots(Nmn, mctas, slack) : 0;
   // the MN-major kernel's row layout (columns on rows of 128k pixels with at most 48 input
   // channels) sets the partials' rows
-  const MnLayout L = mn_layout(A.cin, A.w >= 128 && A.cin <= 48);
+  const MnLayout L = up_ok ? mn_layout_up(A.cin) : mn_layout(A.cin, A.w >= 128 && A.cin <= 48);
   const int seg_Mpad = mslots > 0 ? L.mtiles * kTM : Mpad;
   const int seg_rows = mslots > 0 ? 8 * L.jones : g.rows;
   int splits;
@@ -1395,10 +1416,12 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
     // x: a column copy (3 rows of L.gb channel groups) or L.gb groups of one tap (a tap's shift is an
     // element offset); gz: the whole tile
     const int bw = G.narrow ? A.w : 128;
-    if (!encode_px_map(&xm, A.src, A.co, A.cin, A.cs, A.w, A.h, n_img, bw, L.col ? 3 : G.th, L.gb) ||
-        !encode_px_map(&gm, B.src, 0, ly.cout, ly.cout, A.w, A.h, n_img, bw, G.th, ly.cout / 8))
+    const bool gok = up_ok ? encode_parity_map(&gm, B.src, ly.cout, ly.cout, 2 * A.w, 2 * A.h, n_img, bw, G.th,
+                                               ly.cout / 8)
+                           : encode_px_map(&gm, B.src, 0, ly.cout, ly.cout, A.w, A.h, n_img, bw, G.th, ly.cout / 8);
+    if (!encode_px_map(&xm, A.src, A.co, A.cin, A.cs, A.w, A.h, n_img, bw, L.col ? 3 : G.th, L.gb) || !gok)
       return fail(c, SC_ERR_CUDA, "sc_unet wgrad: tensor map encoding failed");
-    const int smem = (int)mn_smem_bytes(ly.cout, mslots);
+    const int smem = (int)mn_smem_bytes(Nmn, mslots, slack);
     static bool attr[kMaxDev] = {};
     static std::mutex mu;
     int dev = 0;
@@ -1412,12 +1435,12 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
       }
     }
     // 128-row blocks per CTA: as many accumulators as fit in TMEM, in balanced chunks
-    const int per = 512 / mctas / (int)wg_cstride(ly.cout);
+    const int per = 512 / mctas / (int)wg_cstride(Nmn);
     const int nchunk = (L.mtiles + per - 1) / per;
     const int mchunk = (L.mtiles + nchunk - 1) / nchunk;
     auto kern = G.narrow ? k_wgrad_mn<true> : k_wgrad_mn<false>;
-    kern<<<dim3(splits, nchunk), kMnThreads, smem, ws>>>(xm, gm, A.cin, ly.cout, L.mtiles, mchunk, mslots, L, G,
-                                                         part, sc::ctx_status(c));
+    kern<<<dim3(splits, nchunk), kMnThreads, smem, ws>>>(xm, gm, A.cin, Nmn, L.mtiles, mchunk, mslots, L, G, part,
+                                                         sc::ctx_status(c));
     UCHK(cudaGetLastError());
   } else {
     int ks;

@@ -44,8 +44,10 @@ constexpr uint32_t kMnPair = 128 * 16;      // one (tap, channel group) pair: 12
 constexpr uint32_t kMnSlot = 16 * kMnPair;  // one 128-row A block
 constexpr int kMnThreads = 192;             // producer, MMA issuer, 4 epilogue warps
 constexpr int kMnMaxSlots = 6;
-// TMEM columns between the accumulators of consecutive 128-row blocks (cout FP32 columns each)
-__host__ __device__ constexpr uint32_t wg_cstride(int cout) { return cout <= 32 ? 32u : (cout <= 64 ? 64u : 128u); }
+// TMEM columns between the accumulators of consecutive 128-row blocks (N FP32 columns each)
+__host__ __device__ constexpr uint32_t wg_cstride(int n) {
+  return n <= 32 ? 32u : (n <= 64 ? 64u : (n <= 128 ? 128u : 256u));
+}
 
 // the bias row's block: channel 0 of every pixel is one (BF16 0x3F80), the other channels zero
 struct MnOnes {
@@ -60,6 +62,7 @@ __device__ __align__(128) const MnOnes g_mn_ones = mn_ones();
 
 // layout of the A rows: blocks (mtiles), the bias pair, and for columns the copy shape
 struct MnLayout {
+  int up;      // 1: a 2x2 stride-2 transposed conv (one tap, B = the four children's gradients)
   int col;     // 1: columns (rows of 128k pixels), 0: tap-major
   int gb;      // channel groups per copy
   int nu;      // column copies per dx (cin / 8 / gb)
@@ -71,6 +74,7 @@ struct MnLayout {
 __host__ __device__ inline MnLayout mn_layout(int cin, bool col) {
   MnLayout L;
   const int ng = cin / 8;
+  L.up = 0;
   L.col = col ? 1 : 0;
   if (col) {
     L.gb = ng % 4 == 0 ? 4 : (ng % 2 == 0 ? 2 : 1);
@@ -94,9 +98,24 @@ __host__ __device__ inline MnLayout mn_layout(int cin, bool col) {
   return L;
 }
 
+// the transposed conv: A rows c | ones (its pairs are the channel groups, 16 per copy), N = 4 cout
+__host__ __device__ inline MnLayout mn_layout_up(int cin) {
+  MnLayout L;
+  const int ng = cin / 8;
+  L.up = 1;
+  L.col = 0;
+  L.gb = ng < 16 ? ng : 16;
+  L.nu = L.cpb = L.ncopy = 0;
+  L.jones = ng;
+  L.mtiles = (8 * L.jones + 1 + 127) / 128;
+  return L;
+}
+
 __host__ __device__ constexpr uint32_t mn_b_bytes(int cout) { return align_up((uint32_t)(cout / 8) * kMnPair, 1024); }
-__host__ __device__ constexpr size_t mn_smem_bytes(int cout, int slots) {
-  return (size_t)slots * kMnSlot + 2 * mn_b_bytes(cout) + 256;
+// shared memory: the A ring, 1 KB of barriers, the two gz tiles, and `slack` gz tiles of room after
+// them (transposed convs on narrow rows, whose child copies step rows with a traversal stride)
+__host__ __device__ constexpr size_t mn_smem_bytes(int cout, int slots, int slack = 0) {
+  return (size_t)slots * kMnSlot + 1024 + (size_t)(2 + slack) * mn_b_bytes(cout);
 }
 
 // xmap: the layer input, gmap: its output gradient, both as (2 w, h, groups, images, 1) of 8-byte
@@ -112,13 +131,13 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
   extern __shared__ __align__(1024) uint8_t sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ngx = cin / 8, ngz = cout / 8;
-  const int npair = 9 * ngx;  // data pairs (tap-major: pair npair carries the bias row)
+  const int npair = (L.up ? 1 : 9) * ngx;  // data pairs (tap-major: pair npair carries the bias row)
   const int gb = L.gb;
   const uint32_t bb = mn_b_bytes(cout);
   const int h = G.h, w = G.w;
   uint8_t *sA = sm;
-  uint8_t *sB = sA + slots * kMnSlot;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sB + 2 * bb);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sA + slots * kMnSlot);
+  uint8_t *sB = sA + slots * kMnSlot + 1024;
   // [0, 6) A full, [6, 12) A empty, [12, 14) gz full, [14, 16) gz empty, [16] all MMAs done
   uint32_t *slotw = reinterpret_cast<uint32_t *>(bar + 17);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(slotw + 1);
@@ -172,7 +191,16 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
         const uint32_t bfull = tc::smem_addr(&bar[12 + bs]);
         tc::mbar_expect_tx(bfull, (uint32_t)ngz * kMnPair);
         const int x0 = NARROW ? 0 : xt * 128;
-        tc::tma_load_5d(tc::smem_addr(sB + bs * bb), &gmap, 2 * x0, y, 0, img, 0, bfull);
+        if (L.up) {
+          // the children (2y + a, 2x + e) of the tile's parents, one copy per (a, e): N columns
+          // ordered (a, e, output channel)
+          const int gq = ngz / 4;
+          for (int ae = 0; ae < 4; ++ae)
+            tc::tma_load_5d(tc::smem_addr(sB + bs * bb) + (uint32_t)(ae * gq) * kMnPair, &gmap, 0, ae & 1, x0,
+                            img * 2 * h + 2 * y + (ae >> 1), 0, bfull);
+        } else {
+          tc::tma_load_5d(tc::smem_addr(sB + bs * bb), &gmap, 2 * x0, y, 0, img, 0, bfull);
+        }
         ++nb;
         for (int m = mb0; m < mb1; ++m) {
           const int s = na % slots, u = na / slots;
@@ -199,7 +227,7 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
           const int j0 = 16 * m, j1 = min(j0 + 16, npair + 1);
           tc::mbar_expect_tx(afull, (uint32_t)(j1 - j0) * kMnPair);
           for (int j = j0; j < min(j1, npair); j += gb) {
-            const int tap = j / ngx, g = j - tap * ngx;
+            const int tap = L.up ? 4 : j / ngx, g = L.up ? j : j - tap * ngx;  // the up conv: no shift
             const int dy = tap / 3, dx = tap - 3 * dy;
             tc::tma_load_5d(adst + (uint32_t)(j - j0) * kMnPair, &xmap, 2 * (x0 + dx - 1), y + dy - 1, g, img, 0, afull);
           }

@@ -328,11 +328,12 @@ def _wgrad_ref(x, gz):
 @pytest.mark.parametrize("n,h,w", [(16, 256, 256), (8, 128, 128)], ids=["16x256", "8x128"])
 def test_full_size_step_weight_gradients(ctx, n, h, w):
     """The training workload (16 x 256^2) and a smaller one: the split-K weight gradients of the
-    output layer and of every 3x3 convolution (all taps, channels and outputs, and the biases),
-    recomputed over every pixel of each level from the GPU's own BF16 operands.  At 16 x 256^2 the
-    3x3 layers of every level take the MN-major TMA weight-gradient kernel (levels 0-1 at two CTAs
-    per SM, level 3 and dec2 conv 1 in two or three TMEM chunks); at 8 x 128^2 levels 0-2 do and
-    level 3 (16 tiles) takes the gathering GEMM."""
+    output layer, of every 3x3 convolution (all taps, channels and outputs, and the biases) and of
+    the transposed convolutions, recomputed over every pixel of each level from the GPU's own BF16
+    operands.  At 16 x 256^2 the 3x3 layers of every level take the MN-major TMA weight-gradient
+    kernel (levels 0-1 at two CTAs per SM, level 3 and dec2 conv 1 in two or three TMEM chunks) and
+    so do the transposed convs onto levels 0 and 1 (the one onto level 2 takes the gathering GEMM);
+    at 8 x 128^2 levels 0-2 do and level 3 (16 tiles) takes the gathering GEMM."""
     rng = np.random.default_rng(9)
     x = rng.random((n, h, w, 11)).astype(np.float32)
     t = rng.random((n, h, w, 3)).astype(np.float32)
@@ -360,6 +361,22 @@ def test_full_size_step_weight_gradients(ctx, n, h, w):
         gw, aw, gb, ab = _wgrad_ref(xin, gz)
         _check_f32(G[f"{name}_w"], gw, aw, f"{name}_w full size")
         _check_f32(G[f"{name}_b"], gb, ab, f"{name}_b full size")
+    # the 2x2 stride-2 transposed convs: w[c, a, e, o] = sum over parents p of ui[p, c] gup[child, o]
+    for l in range(3):
+        ui = buf("ENC2", 3) if l == 2 else buf("DEC2", l + 1)
+        gu = buf("GUP", l)
+        cn, co = ui.shape[-1], gu.shape[-1]
+        x2 = ui.reshape(-1, cn)
+        gw = np.zeros((cn, 2, 2, co))
+        aw = np.zeros_like(gw)
+        for a in range(2):
+            for e in range(2):
+                ch = gu[:, a::2, e::2, :].reshape(-1, co)
+                gw[:, a, e, :] = (x2.T @ ch).cpu().numpy()
+                aw[:, a, e, :] = (x2.abs().T @ ch.abs()).cpu().numpy()
+        g2 = gu.reshape(-1, co)
+        _check_f32(G[f"up{l}_w"], gw, aw, f"up{l}_w full size")
+        _check_f32(G[f"up{l}_b"], g2.sum(0).cpu().numpy(), g2.abs().sum(0).cpu().numpy(), f"up{l}_b full size")
     net.close()
 
 
