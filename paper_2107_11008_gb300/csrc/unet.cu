@@ -512,6 +512,7 @@ __global__ void k_adam(const Seg *segs, int nseg, float *p, const float *g, floa
     S.wf[(int64_t)rem * S.cin + c] = b;
     S.wd[i] = b;
     S.wtf[((int64_t)(c / 8) * (4 * S.cout) + rem) * 8 + (c & 7)] = b;
+    if (S.wtd) S.wtd[((int64_t)(rem / 8) * S.cin + c) * 8 + (rem & 7)] = b;  // [(a, e, o) group][c][8]
   } else if (S.kind == KIND_OUT) {
     S.wf[i] = b;
   }
@@ -1198,7 +1199,8 @@ bool col_splittable(const EGrad &e, int N) { return e.split == N && !e.out2; }
 
 template <class EP>
 cudaError_t conv3x3_tma(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h, int w, int n, int N,
-                        const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s, int taps = 9);
+                        const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s, int taps = 9,
+                        int up_ngc = 0);
 
 // src: row-blocked BF16 slice (cs channels, slice at co) with `cin` channels per tap; N output
 // channels; wdense: [N][9][cin] (gathering GEMM), wtma: [tap][cin/8][N][8] (TMA kernel), wtma2:
@@ -1223,13 +1225,19 @@ cudaError_t conv3x3(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h,
 }
 
 // The TMA kernel for a 3x3 convolution (taps 9) or a pointwise contraction of each pixel's
-// channels (taps 1; wtma [cin/8][N][8]).
+// channels (taps 1; wtma [cin/8][N][8]).  up_ngc > 0: the data gradient of a 2x2 stride-2
+// transposed conv, src = its output gradient at the children's resolution (2h x 2w, cs channels,
+// up_ngc groups of 8), h x w the parents', cin = 4 * 8 up_ngc, wtma [(a, e, o) group][N][8].
 template <class EP>
 cudaError_t conv3x3_tma(sc_unet *u, const bf16 *src, int cs, int co, int cin, int h, int w, int n, int N,
-                        const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s, int taps) {
+                        const bf16 *wtma, int sign, const EP &e, unsigned *st, cudaStream_t s, int taps, int up_ngc) {
   CUtensorMap map;
-  const ConvGeo G = conv_geo(n, h, w, taps);
-  const bool mapped = taps == 1 ? encode_rb_map(&map, src, co, cin, cs, w, h, n, true, G.narrow ? w : 128, G.th)
+  ConvGeo G = conv_geo(n, h, w, taps);
+  G.up = up_ngc > 0 ? 1 : 0;
+  G.ngc = up_ngc;
+  const bool mapped = up_ngc > 0 ? encode_parity_map(&map, src, 8 * up_ngc, cs, 2 * w, 2 * h, n, G.narrow ? w : 128,
+                                                     G.th, 1)
+                      : taps == 1 ? encode_rb_map(&map, src, co, cin, cs, w, h, n, true, G.narrow ? w : 128, G.th)
                       : G.narrow ? encode_rb_map(&map, src, co, cin, cs, w, h, n, false, w, G.th + 2)
                                  : encode_rb_map(&map, src, co, cin, cs, w, h, n, true, kHaloW, kHaloH);
   if (!mapped) return cudaErrorInvalidValue;
@@ -1556,8 +1564,13 @@ int backward_body(sc_ctx *c, sc_unet *u) {
     // gradient w.r.t. up_in, masked by its ReLU: the next decoder conv 2's output gradient,
     // or at the deepest level the encoder's last conv output gradient
     bf16 *dst = l + 1 == kLevels - 1 ? u->ge2[l + 1] : u->gd2[l + 1];
-    UCHK(gemm(ag, dense(up.wd, 4 * cl, cn), egrad(dst, cn, ui.p, ui.cs, ui.co, cn, wn), (int)P[l + 1], cn, 4 * cl, 1,
-              4 * cl, st, s));
+    const EGrad eu = egrad(dst, cn, ui.p, ui.cs, ui.co, cn, wn);
+    if (conv_tma_ok(4 * cl, cn, wn, hn, 1)) {
+      // the TMA convolution's pointwise mode over the children (K = (a, e, output channel))
+      UCHK(conv3x3_tma(u, u->gup[l], cl, 0, 4 * cl, hn, wn, n, cn, up.wtd, 1, eu, st, s, 1, cl / 8));
+    } else {
+      UCHK(gemm(ag, dense(up.wd, 4 * cl, cn), eu, (int)P[l + 1], cn, 4 * cl, 1, 4 * cl, st, s));
+    }
   }
   // encoder, deep to shallow; ge2[l] holds d loss / d (pre-ReLU) encoder conv 2 output
   for (int l = kLevels - 1; l >= 0; --l) {
@@ -1821,7 +1834,10 @@ int sc_unet_create(sc_ctx *c, int32_t max_batch, int32_t height, int32_t width, 
     for (int i = 0; i < kNumLayers; ++i) {
       u->L[i].wf = cv.take<bf16>(u->L[i].wf_elems);
       u->L[i].wd = u->L[i].wd_elems ? cv.take<bf16>(u->L[i].wd_elems) : nullptr;
-      if (u->L[i].kind == KIND_UP) u->L[i].wtf = cv.take<bf16>(u->L[i].wf_elems);
+      if (u->L[i].kind == KIND_UP) {
+        u->L[i].wtf = cv.take<bf16>(u->L[i].wf_elems);
+        u->L[i].wtd = cv.take<bf16>(u->L[i].wf_elems);
+      }
       if (u->L[i].kind == KIND_CONV) {
         u->L[i].wtf = cv.take<bf16>(u->L[i].wf_elems);
         u->L[i].wtd = u->L[i].wd_elems ? cv.take<bf16>(u->L[i].wd_elems) : nullptr;

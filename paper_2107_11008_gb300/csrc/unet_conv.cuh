@@ -66,6 +66,9 @@ struct ConvGeo {
   uint32_t slab;     // bytes of one dx slab (narrow)
   uint32_t gstride;  // bytes of one channel group in a stage
   uint32_t tx;       // bytes the TMA copies of one channel group deliver
+  int up;            // pointwise on a transposed conv's children (the data gradient): A through the
+                     // parity view, K group kg = (a, e) * ngc + child channel group
+  int ngc;           // child channel groups (up only)
 };
 __host__ __device__ inline ConvGeo conv_geo(int n_img, int h, int w, int taps = 9) {
   ConvGeo g;
@@ -73,6 +76,8 @@ __host__ __device__ inline ConvGeo conv_geo(int n_img, int h, int w, int taps = 
   g.h = h;
   g.w = w;
   g.taps = taps;
+  g.up = 0;
+  g.ngc = 0;
   g.narrow = w < 128;
   g.th = g.narrow ? 128 / w : 1;
   if (taps == 1) {  // 128 pixels x 16 bytes per channel group, whole 8-pixel blocks
@@ -156,7 +161,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tma(const __grid_const
           tc::mbar_expect_tx(full, (uint32_t)gs * G.tx);
           const uint32_t dst = tc::smem_addr(sA + s * astride);
           for (int g = 0; g < gs; ++g) {
-            if (G.taps == 1) {
+            if (G.up) {
+              // the children (2y + a, 2x + e) of the tile's parents for K group (a, e, child group)
+              const int kg = ch * gs + g, ae = kg / G.ngc, og = kg - ae * G.ngc;
+              tc::tma_load_5d(dst + g * G.gstride, &amap, 0, ae & 1, G.narrow ? 0 : xt * 128,
+                              img * 2 * h + 2 * y + (ae >> 1), og, full);
+            } else if (G.taps == 1) {
               tc::tma_load_5d(dst + g * G.gstride, &amap, 0, G.narrow ? 0 : xt * (128 / 8), ch * gs + g, y, img, full);
             } else if (G.narrow) {
               for (int dx = 0; dx < 3; ++dx)
