@@ -1,38 +1,44 @@
-// unet_wgrad_mn.cuh -- weight gradient of a 3x3 convolution on tcgen05 with MN-major operands
-// that TMA delivers ready to use (tiles of 128 pixels: part of a row of 128k pixels, or 128 / w
-// whole narrower rows, as in unet_conv.cuh).
+// unet_wgrad_mn.cuh -- weight gradients of the 3x3 convolutions and of the 2x2 stride-2 transposed
+// convolutions on tcgen05, with MN-major operands that TMA delivers ready to use (tiles of 128
+// pixels: part of a row of 128k pixels, or 128 / w whole narrower rows, as in unet_conv.cuh).
 //
-//   gw[o][tap][c] = sum_p gz[p][o] * x[p + offset(tap)][c],   gb[o] = sum_p gz[p][o]
+//   3x3:  gw[o][tap][c] = sum_p gz[p][o] * x[p + offset(tap)][c],   gb[o] = sum_p gz[p][o]
+//   up:   gw[c][a][e][o] = sum_p x[p][c] * gz[(2y + a, 2x + e)][o],  gb[o] = sum over all children
 //
-// as D[(tap, c) | ones][o] = sum over pixels.  The tensors hold 8 consecutive channels per 16
-// bytes, which is the row of an MN-major core matrix when M (or N) is the channel and K the pixel:
-// 8 consecutive pixels x 8 channels = one 128-byte core matrix.  So nothing is transposed.  A ring
-// slot holds one 128-row block of A: 16 pairs (tap, channel group), tap-major, each the tile's 128
-// pixels shifted by the tap's offset (2 KB, pairs 2 KB apart).  The tensors are viewed with 8-byte
-// elements (half a pixel) as (2 w, rows, groups, images): a one-pixel shift is an element offset of
-// 2 (16 bytes), and one TMA copy (zeros outside the image) brings several pairs whole.  A CTA's
-// copies are served about one after another, at a cost that grows slowly with their size, so few
-// large copies matter more than anything else here:
-//  * columns (rows of 128k pixels, at most 48 input channels): one copy brings, for one dx and gb
-//    channel groups, the three rows dy = 0..2 ((256, 3, gb) box: pairs ordered (group, dy)); a
+// as D[A rows | ones][N columns] = sum over the tile's pixels (parents for the transposed conv).
+// The tensors hold 8 consecutive channels per 16 bytes, which is the row of an MN-major core
+// matrix when M (or N) is the channel and K the pixel: 8 consecutive pixels x 8 channels = one
+// 128-byte core matrix.  So nothing is transposed.  A ring slot holds one 128-row block of A: 16
+// pairs (tap, channel group), each the tile's 128 pixels shifted by the tap's offset (2 KB, pairs
+// 2 KB apart).  The tensors are viewed with 8-byte elements (half a pixel) as (2 w, rows, groups,
+// images): a one-pixel shift is an element offset of 2 (16 bytes), and one TMA copy (zeros outside
+// the image) brings several pairs whole.  A CTA's copies are served about one after another, at a
+// cost that grows slowly with their size, so few large copies matter more than anything else:
+//  * columns (3x3, rows of 128k pixels, at most 48 input channels): one copy brings, for one dx and
+//    gb channel groups, the three rows dy = 0..2 ((256, 3, gb) box: pairs ordered (group, dy)); a
 //    block holds cpb = 16 / (3 gb) such copies (gb = 4, 2 or 1, so 12, 12 or 15 pairs; the rest
-//    of the block is padding, whose accumulator rows are never read), blocks in copy order k = dx *
-//    (cin / 8 / gb) + unit.  With more channels the padding costs more blocks (MMAs, partials,
-//    TMEM chunks) than the fewer copies save (measured: 64 channels 89.6 -> 98.1 us);
-//  * tap-major (all other layers): pairs ordered (tap, group), one copy brings gb = gcd(cin / 8,
-//    16) pairs of one tap (th rows of w pixels each), so that no copy straddles two blocks.
+//    of the block is padding, whose accumulator rows are neither written nor read), blocks in copy
+//    order k = dx * (cin / 8 / gb) + unit.  With more channels the padding costs more blocks
+//    (MMAs, partials, TMEM chunks) than the fewer copies save (64 channels: 89.6 -> 98.1 us);
+//  * tap-major (other 3x3 layers): pairs ordered (tap, group), one copy brings gb = gcd(cin / 8,
+//    16) pairs of one tap (th rows of w pixels each), so that no copy straddles two blocks;
+//  * up (the transposed conv): one tap, pairs = the input's channel groups; B is the output
+//    gradient of each parent's four children, one copy per (a, e) through the parity view of the
+//    child tensor (mn_layout_up; N = 4 cout columns ordered (a, e, o)).
 // The bias row is a pair whose channel 0 is one, copied from a constant (the first pair after the
-// data: in the last block's padding for columns, pair 9 cin / 8 for the tap-major order); the gz
-// tile is one copy (one 2 KB block per group of 8 output channels).  mn_layout() gives both
-// layouts' block counts and the bias pair for the host, the kernel and the reduce.  One thread issues the MMAs; the accumulators of all
-// 128-row blocks (cout columns each, 32/64/128 apart) stay in TMEM across the CTA's contiguous
-// range of tiles, and at the end the epilogue warps write them as this CTA's partial sums
-// ([split][128 mtiles][cout], the layout k_wgrad_reduce sums in a fixed order).  Where all blocks'
-// accumulators do not fit in TMEM, the grid's y dimension splits them into chunks of `mchunk`
-// blocks, one CTA per (tile range, chunk).  Every wait is bounded.
+// data).  mn_layout() / mn_layout_up() give the block counts and the bias pair for the host, the
+// kernel and the reduce.  Shared memory: the A ring, 1 KB of barriers, the two gz tiles and, for
+// the transposed conv on narrow rows, one gz tile of slack, so that a box read wrongly could only
+// overwrite data.  One thread issues the MMAs; the accumulators of all 128-row blocks (N columns
+// each, 32/64/128/256 apart) stay in TMEM across the CTA's contiguous range of tiles, and at the
+// end the epilogue warps write them as this CTA's partial sums ([split][128 mtiles][N], the layout
+// k_wgrad_reduce sums in a fixed order).  Where all blocks' accumulators do not fit in TMEM, the
+// grid's y dimension splits them into chunks of `mchunk` blocks, one CTA per (tile range, chunk).
+// The host runs two CTAs per SM on rows of 128k pixels where two ring slots each still fit.
+// Every wait is bounded.
 //
 // Operand extents (LBO = 128 bytes: the next 8 pixels; SBO = 2 KB: the next 8 channels): one MMA
-// (K = 16) reads 16 (or cout / 8) pairs x 256 bytes from its start, which moves 256 bytes per K
+// (K = 16) reads 16 (or N / 8) pairs x 256 bytes from its start, which moves 256 bytes per K
 // step, so every read stays inside its own 32 KB A slot or gz tile.
 #pragma once
 #include "unet_conv.cuh"
@@ -229,7 +235,8 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
           for (int j = j0; j < min(j1, npair); j += gb) {
             const int tap = L.up ? 4 : j / ngx, g = L.up ? j : j - tap * ngx;  // the up conv: no shift
             const int dy = tap / 3, dx = tap - 3 * dy;
-            tc::tma_load_5d(adst + (uint32_t)(j - j0) * kMnPair, &xmap, 2 * (x0 + dx - 1), y + dy - 1, g, img, 0, afull);
+            tc::tma_load_5d(adst + (uint32_t)(j - j0) * kMnPair, &xmap, 2 * (x0 + dx - 1), y + dy - 1, g, img, 0,
+                            afull);
           }
           if (npair < j1) tc::bulk_load(adst + (uint32_t)(npair - j0) * kMnPair, &g_mn_ones, kMnPair, afull);
           ++na;
@@ -295,7 +302,8 @@ __global__ void __launch_bounds__(kMnThreads, 1) k_wgrad_mn(const __grid_constan
         float v[16];
         tc::tmem_ld16(taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)(k - mb0) * cstride + (uint32_t)n0, v);
         if (done && !*abort_flag && mine > 0 && pair < used) {
-          float4 *p = reinterpret_cast<float4 *>(part + ((int64_t)blockIdx.x * Mpad + 128 * k + 32 * qd + lane) * cout + n0);
+          float4 *p = reinterpret_cast<float4 *>(part + ((int64_t)blockIdx.x * Mpad + 128 * k + 32 * qd + lane) * cout +
+                                                 n0);
 #pragma unroll
           for (int j = 0; j < 4; ++j) p[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         }
