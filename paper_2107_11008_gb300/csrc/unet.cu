@@ -1380,10 +1380,10 @@ int run_loss(sc_ctx *c, sc_unet *u, const float *pred, const float *target, int 
 #ifndef SC_WG_MN_CTAS
 #define SC_WG_MN_CTAS 2
 #endif
-int wgrad_mn_slots(int cout, int ctas, int slack = 0) {
+int wgrad_mn_slots(int cout, int ctas) {
   const int budget = ctas == 1 ? 227 * 1024 : 228 * 1024 / ctas - 1024;  // 1 KB per CTA is the system's
   for (int s = kMnMaxSlots; s >= 2; --s)
-    if ((int)mn_smem_bytes(cout, s, slack) <= budget) return s;
+    if ((int)mn_smem_bytes(cout, s) <= budget) return s;
   return 0;
 }
 
@@ -1406,8 +1406,7 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
                      B.cs == ly.cout && A.cin == g.rows && 4 * ly.cout <= 256 && tensor_map_encoder() != nullptr;
   const int Nmn = up_ok ? 4 * ly.cout : ly.cout;  // accumulator columns
   const int mctas = A.w >= 128 && SC_WG_MN_CTAS > 1 && wgrad_mn_slots(Nmn, SC_WG_MN_CTAS) > 0 ? SC_WG_MN_CTAS : 1;
-  const int slack = up_ok && A.w < 128 ? 1 : 0;
-  const int mslots = (tma_ok || up_ok) && tiles >= 64 ? wgrad_mn_slots(Nmn, mctas, slack) : 0;
+  const int mslots = (tma_ok || up_ok) && tiles >= 64 ? wgrad_mn_slots(Nmn, mctas) : 0;
   // the MN-major kernel's row layout (columns on rows of 128k pixels with at most 48 input
   // channels) sets the partials' rows
   const MnLayout L = up_ok ? mn_layout_up(A.cin) : mn_layout(A.cin, A.w >= 128 && A.cin <= 48);
@@ -1429,7 +1428,7 @@ int wgrad(sc_ctx *c, sc_unet *u, const Layer &ly, const TPix &A, const TPix &B, 
                            : encode_px_map(&gm, B.src, 0, ly.cout, ly.cout, A.w, A.h, n_img, bw, G.th, ly.cout / 8);
     if (!encode_px_map(&xm, A.src, A.co, A.cin, A.cs, A.w, A.h, n_img, bw, L.col ? 3 : G.th, L.gb) || !gok)
       return fail(c, SC_ERR_CUDA, "sc_unet wgrad: tensor map encoding failed");
-    const int smem = (int)mn_smem_bytes(Nmn, mslots, slack);
+    const int smem = (int)mn_smem_bytes(Nmn, mslots);
     static bool attr[kMaxDev] = {};
     static std::mutex mu;
     int dev = 0;

@@ -27,9 +27,8 @@
 //    child tensor (mn_layout_up; N = 4 cout columns ordered (a, e, o)).
 // The bias row is a pair whose channel 0 is one, copied from a constant (the first pair after the
 // data).  mn_layout() / mn_layout_up() give the block counts and the bias pair for the host, the
-// kernel and the reduce.  Shared memory: the A ring, 1 KB of barriers, the two gz tiles and, for
-// the transposed conv on narrow rows, one gz tile of slack, so that a box read wrongly could only
-// overwrite data.  One thread issues the MMAs; the accumulators of all 128-row blocks (N columns
+// kernel and the reduce.  Shared memory: the A ring, 1 KB of barriers, the two gz tiles.  One
+// thread issues the MMAs; the accumulators of all 128-row blocks (N columns
 // each, 32/64/128/256 apart) stay in TMEM across the CTA's contiguous range of tiles, and at the
 // end the epilogue warps write them as this CTA's partial sums ([split][128 mtiles][N], the layout
 // k_wgrad_reduce sums in a fixed order).  Where all blocks' accumulators do not fit in TMEM, the
@@ -118,10 +117,9 @@ __host__ __device__ inline MnLayout mn_layout_up(int cin) {
 }
 
 __host__ __device__ constexpr uint32_t mn_b_bytes(int cout) { return align_up((uint32_t)(cout / 8) * kMnPair, 1024); }
-// shared memory: the A ring, 1 KB of barriers, the two gz tiles, and `slack` gz tiles of room after
-// them (transposed convs on narrow rows, whose child copies step rows with a traversal stride)
-__host__ __device__ constexpr size_t mn_smem_bytes(int cout, int slots, int slack = 0) {
-  return (size_t)slots * kMnSlot + 1024 + (size_t)(2 + slack) * mn_b_bytes(cout);
+// shared memory: the A ring, 1 KB of barriers, the two gz tiles
+__host__ __device__ constexpr size_t mn_smem_bytes(int cout, int slots) {
+  return (size_t)slots * kMnSlot + 1024 + 2 * (size_t)mn_b_bytes(cout);
 }
 
 // xmap: the layer input, gmap: its output gradient, both as (2 w, h, groups, images, 1) of 8-byte

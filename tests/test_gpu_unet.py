@@ -332,7 +332,7 @@ def test_full_size_step_weight_gradients(ctx, n, h, w):
     the transposed convolutions, recomputed over every pixel of each level from the GPU's own BF16
     operands.  At 16 x 256^2 the 3x3 layers of every level take the MN-major TMA weight-gradient
     kernel (levels 0-1 at two CTAs per SM, level 3 and dec2 conv 1 in two or three TMEM chunks) and
-    so do the transposed convs onto levels 0 and 1 (the one onto level 2 takes the gathering GEMM);
+    so do the three transposed convs;
     at 8 x 128^2 levels 0-2 do and level 3 (16 tiles) takes the gathering GEMM."""
     rng = np.random.default_rng(9)
     x = rng.random((n, h, w, 11)).astype(np.float32)
